@@ -1,0 +1,196 @@
+"""CPU oracle of the Adaptive Multi-NeRF rendering hot path (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline leg
+of the benchmark are the only users.  The product path (the CUDA library and its
+Python binding) never imports this package, and this package never imports the
+product.  The arithmetic lives in ``amnerf_oracle.c`` (plain C, FP64 definition
+plus an FP32 mode in the GPU's operation order); ``build()`` compiles it with gcc.
+
+Parity status per function (what pins it is in tests/test_oracle_pins.py):
+  build_tree  pinned: tiling invariants, brute-force median over k, hand-derived
+              G=4 fixture, leaf rule.
+  traverse    pinned: point-in-box brute force along the ray, sorted-all-leaves form,
+              contiguity, union = root interval.
+  samples     pinned: every sample inside its leaf box; sum of deltas = hit length.
+  group       pinned: permutation, histogram, exclusive scan, stable order.
+  encode      pinned: exact values at dyadic points, double-angle identities.
+  mlp_eval    pinned: numpy float64 matmul chain; zero-weight closed form.
+  render      pinned: constant-density closed form, sum(w) + T = 1, midpoint-rule
+              depth limit, early termination.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "amnerf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+F32 = np.float32
+F64 = np.float64
+I32 = np.int32
+I64 = np.int64
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-pthread", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            V, I, L, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+            _lib.or_build_tree.argtypes = [V, I, V, I, D, I, V, V, V, V, V, V]
+            _lib.or_traverse.argtypes = [V, V, V, I, V, V, L, I, I, I, V, V, V, V]
+            _lib.or_samples.argtypes = [V, V, L, V, V, V, I, I, I, I, V, V, V]
+            _lib.or_group.argtypes = [V, V, L, I, I, I, V, V, V]
+            _lib.or_encode.argtypes = [V, I, I, V]
+            _lib.or_encode.restype = None
+            _lib.or_mlp_eval.argtypes = [V, I, I, I, I, V, V, L, I, V, V]
+            _lib.or_render.argtypes = [V, V, V, I, V, I, I, I, I, V, V, L, I, I, D, V, I, I,
+                                       V, V, V, V, V, V, V, V, V]
+    return _lib
+
+
+class Tree:
+    """Flat preorder node arrays (see amnerf_oracle.c for the field meaning)."""
+
+    def __init__(self, box, cells, info, split, mass, n_leaves):
+        self.box, self.cells, self.info, self.split, self.mass = box, cells, info, split, mass
+        self.n_leaves = int(n_leaves)
+
+    @property
+    def n_nodes(self) -> int:
+        return len(self.split)
+
+    def leaves(self) -> np.ndarray:
+        """Node indices of the leaves, ordered by leaf id."""
+        idx = np.nonzero(self.info[:, 0] < 0)[0]
+        return idx[np.argsort(self.info[idx, 3])]
+
+    def leaf_cells(self) -> np.ndarray:
+        return self.cells[self.leaves()]
+
+
+def build_tree(grid: np.ndarray, max_depth: int, leaf_frac: float = 0.0,
+               bbox=(-1.0, -1.0, -1.0, 1.0, 1.0, 1.0)) -> Tree:
+    grid = np.ascontiguousarray(grid, dtype=F32)
+    G = grid.shape[0]
+    cap = 2 ** (max_depth + 1) + 1
+    box = np.zeros((cap, 6), F32); cells = np.zeros((cap, 6), I32); info = np.zeros((cap, 6), I32)
+    split = np.zeros(cap, F32); mass = np.zeros(cap, F64); nl = np.zeros(1, I32)
+    bb = np.asarray(bbox, dtype=F64)
+    n = lib().or_build_tree(_p(grid), G, _p(bb), max_depth, float(leaf_frac), cap,
+                            _p(box), _p(cells), _p(info), _p(split), _p(mass), _p(nl))
+    if n <= 0:
+        raise RuntimeError("oracle tree build failed")
+    return Tree(box[:n].copy(), cells[:n].copy(), info[:n].copy(), split[:n].copy(), mass[:n].copy(), nl[0])
+
+
+def make_tree(box, info, split) -> Tree:
+    """Tree from hand-written arrays (used by pin tests)."""
+    box = np.ascontiguousarray(box, F32); info = np.ascontiguousarray(info, I32)
+    split = np.ascontiguousarray(split, F32)
+    n = len(split)
+    return Tree(box, np.zeros((n, 6), I32), info, split, np.zeros(n, F64), int((info[:, 0] < 0).sum()))
+
+
+def traverse(tree: Tree, o, d, maxc: int, mode: int = 0, method: int = 0):
+    """Per ray: crossing count, leaf ids, entries, exits (ray-major, stride maxc)."""
+    o = np.ascontiguousarray(o, F32); d = np.ascontiguousarray(d, F32)
+    n = len(o)
+    nx = np.zeros(n, I32); leaf = np.full((n, maxc), -1, I32)
+    tin = np.zeros((n, maxc), F64); tout = np.zeros((n, maxc), F64)
+    rc = lib().or_traverse(_p(tree.box), _p(tree.info), _p(tree.split), tree.n_nodes, _p(o), _p(d), n,
+                           maxc, mode, method, _p(nx), _p(leaf), _p(tin), _p(tout))
+    if rc != 0:
+        raise RuntimeError("oracle traversal failed")
+    return nx, leaf, tin, tout
+
+
+def samples(o, d, nx, tin, tout, maxc: int, steps: int, cap: int, mode: int = 0):
+    """Slot arrays t, delta (n, cap) and x (n, cap, 3); unused slots are zero."""
+    o = np.ascontiguousarray(o, F32); d = np.ascontiguousarray(d, F32)
+    n = len(o)
+    t = np.zeros((n, cap), F64); dl = np.zeros((n, cap), F64); x = np.zeros((n, cap, 3), F64)
+    lib().or_samples(_p(o), _p(d), n, _p(np.ascontiguousarray(nx, I32)), _p(np.ascontiguousarray(tin, F64)),
+                     _p(np.ascontiguousarray(tout, F64)), maxc, steps, cap, mode, _p(t), _p(dl), _p(x))
+    return t, dl, x
+
+
+def group(nx, leaf, maxc: int, steps: int, n_leaves: int):
+    nx = np.ascontiguousarray(nx, I32); leaf = np.ascontiguousarray(leaf, I32)
+    n = len(nx)
+    counts = np.zeros(n_leaves, I64); offsets = np.zeros(n_leaves + 1, I64)
+    order = np.zeros(int(nx.sum()), I64)
+    rc = lib().or_group(_p(nx), _p(leaf), n, maxc, steps, n_leaves, _p(counts), _p(offsets), _p(order))
+    if rc != 0:
+        raise RuntimeError("oracle grouping failed")
+    return counts, offsets, order
+
+
+def encode(p, L: int, mode: int = 0) -> np.ndarray:
+    p = np.ascontiguousarray(p, F64).reshape(3)
+    out = np.zeros(3 + 6 * L, F64)
+    lib().or_encode(_p(p), L, mode, _p(out))
+    return out
+
+
+def mlp_eval(params_leaf, width: int, hidden: int, lx: int, ld: int, x, d, mode: int = 0):
+    P = np.ascontiguousarray(params_leaf, F32)
+    x = np.ascontiguousarray(x, F64).reshape(-1, 3); d = np.ascontiguousarray(d, F64).reshape(-1, 3)
+    n = len(x)
+    out = np.zeros((n, 4), F64); raw = np.zeros((n, 4), F64)
+    rc = lib().or_mlp_eval(_p(P), width, hidden, lx, ld, _p(x), _p(d), n, mode, _p(out), _p(raw))
+    if rc != 0:
+        raise RuntimeError("oracle mlp failed")
+    return out, raw
+
+
+def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, steps: int, cap: int,
+           t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), mode: int = 0, threads: int = 1, full: bool = False):
+    """Full render of every ray; returns a dict of float64 / int32 arrays."""
+    params = np.ascontiguousarray(params, F32)
+    o = np.ascontiguousarray(o, F32); d = np.ascontiguousarray(d, F32)
+    n = len(o)
+    res = {
+        "rgb": np.zeros((n, 3), F64), "depth": np.zeros(n, F64), "opacity": np.zeros(n, F64),
+        "n_gen": np.zeros(n, I32), "n_eval": np.zeros(n, I32), "ert_margin": np.zeros(n, F64),
+        "t_final": np.zeros(n, F64),
+    }
+    so = sw = None
+    if full:
+        so = np.zeros((n, cap, 4), F64); sw = np.zeros((n, cap), F64)
+        res["slot_out"] = so; res["slot_w"] = sw
+    bgv = np.asarray(bg, F64)
+    rc = lib().or_render(_p(tree.box), _p(tree.info), _p(tree.split), tree.n_nodes, _p(params), width, hidden,
+                         lx, ld, _p(o), _p(d), n, steps, cap, float(t_term), _p(bgv), mode, threads,
+                         _p(res["rgb"]), _p(res["depth"]), _p(res["opacity"]), _p(res["n_gen"]),
+                         _p(res["n_eval"]), _p(res["ert_margin"]),
+                         _p(so) if so is not None else None, _p(sw) if sw is not None else None,
+                         _p(res["t_final"]))
+    if rc != 0:
+        raise RuntimeError("oracle render failed")
+    return res

@@ -1,0 +1,704 @@
+/*
+ * amnerf_oracle.c -- plain, slow CPU oracle of the Adaptive Multi-NeRF rendering
+ * hot path (arXiv 2310.01881).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this file.  It shares no code, header, table
+ * or helper with the CUDA library; both sides only consume the seeded arrays built
+ * by the input generator.
+ *
+ * Every function exists in two modes:
+ *   mode 0 (FP64): the definition, evaluated in double precision;
+ *   mode 1 (FP32): the same steps in float, in a fixed operation order with no
+ *                  fused multiply-add (the file is compiled with -ffp-contract=off),
+ *                  so that tree, leaf ids, crossings and sample positions can be
+ *                  compared bit for bit against a GPU path that follows the order.
+ *
+ * Steps and where they come from (paper sections):
+ *   tree       Sec. 3.4 (BuildKDTree: split at the median of the cumulative density,
+ *              recurse left then right; node index = binary path code, Sec. 3.1).
+ *              TestLeaf (Sec. 3.4) needs a trained teacher; here a node is a leaf
+ *              when it reaches the depth limit, when its mass is at most a fraction
+ *              of the total, or when it is one cell wide.
+ *   traversal  Sec. 3.5, Algorithm 1 (Traverse), read as ordered front-to-back
+ *              KD-tree traversal that records one interval per leaf crossed.
+ *   sampling   Sec. 3.5, Algorithm 1 (Sampling) and Fig. "prop": every interval is
+ *              normalised and gets the same number of samples, stored per ray at
+ *              ray * max_cell_count + j; placed at stratum midpoints.
+ *   grouping   Sec. 3.5 and Fig. "parallel": samples sorted by node id so that each
+ *              node's network runs as one batch.
+ *   network    Sec. 3.1 (F_Theta(x, d) -> (c, sigma)), Sec. 3.3/4.1 (one small
+ *              same-shaped MLP per node), frequency positional encoding (Fig.
+ *              "complex" caption).
+ *   composite  Sec. 3.1 ("traditional volumetric rendering"): NeRF quadrature with
+ *              early ray termination.
+ *   proposal   not in the paper (related work, Sec. 2.2: sampling networks);
+ *              defined in the proposal section of this file.
+ *
+ * Parity pins live in the test suite (brute-force ray/box classification, closed
+ * forms, invariants, library matmul chains, finite differences).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAX_STACK 128
+
+/* ======================================================================== */
+/* Tree build (Sec. 3.4)                                                     */
+/* ======================================================================== */
+
+/* Flat node record used by every oracle entry point.
+ *   box[6]   = lo x, lo y, lo z, hi x, hi y, hi z   (float)
+ *   cells[6] = cell range x0, y0, z0, x1, y1, z1     (half-open)
+ *   info[6]  = axis (-1 for a leaf), left, right, leaf id (-1 inner), code, depth
+ *   split    = split coordinate (float), mass = node mass (double)
+ * Nodes are stored in preorder (node, left subtree, right subtree). */
+typedef struct {
+    const float *grid;
+    int G;
+    double blo[3], bhi[3];
+    int max_depth;
+    double leaf_frac;
+    double total;
+    int cap, n, n_leaves, err;
+    float *box;
+    int *cells, *info;
+    float *split;
+    double *mass;
+    double *slice; /* scratch, G doubles */
+} or_build;
+
+static float or_coord(const or_build *b, int a, int i)
+{
+    /* cell boundary i along axis a, rounded once from double */
+    double v = b->blo[a] + (b->bhi[a] - b->blo[a]) * ((double)i / (double)b->G);
+    return (float)v;
+}
+
+/* longest axis in cells, ties to the lowest index */
+static int or_longest(const int lo[3], const int hi[3])
+{
+    int a = 0;
+    for (int k = 1; k < 3; k++)
+        if (hi[k] - lo[k] > hi[a] - lo[a]) a = k;
+    return a;
+}
+
+/* slice[i] = sum of the node's cells whose index along a is lo[a] + i; cells are
+ * added in z-major, x-minor order.  Node mass = slice[0] + slice[1] + ... in order. */
+static double or_slices(const or_build *b, const int lo[3], const int hi[3], int a, double *slice)
+{
+    int n = hi[a] - lo[a];
+    for (int i = 0; i < n; i++) slice[i] = 0.0;
+    for (int z = lo[2]; z < hi[2]; z++)
+        for (int y = lo[1]; y < hi[1]; y++)
+            for (int x = lo[0]; x < hi[0]; x++) {
+                int idx = (a == 0) ? x : (a == 1) ? y : z;
+                slice[idx - lo[a]] += (double)b->grid[((size_t)z * b->G + y) * b->G + x];
+            }
+    double m = 0.0;
+    for (int i = 0; i < n; i++) m += slice[i];
+    return m;
+}
+
+static int or_build_rec(or_build *b, const int lo[3], const int hi[3], int depth, uint32_t code)
+{
+    if (b->n >= b->cap) { b->err = 1; return -1; }
+    int id = b->n++;
+    int a = or_longest(lo, hi);
+    int n = hi[a] - lo[a];
+    double m = or_slices(b, lo, hi, a, b->slice);
+    if (depth == 0) b->total = m;
+    for (int k = 0; k < 3; k++) {
+        b->box[6 * id + k] = or_coord(b, k, lo[k]);
+        b->box[6 * id + 3 + k] = or_coord(b, k, hi[k]);
+        b->cells[6 * id + k] = lo[k];
+        b->cells[6 * id + 3 + k] = hi[k];
+    }
+    b->mass[id] = m;
+    int *inf = b->info + 6 * id;
+    inf[4] = (int)code;
+    inf[5] = depth;
+    int leaf = depth >= b->max_depth || n <= 1 || (b->leaf_frac > 0.0 && m <= b->leaf_frac * b->total);
+    if (leaf) {
+        inf[0] = -1; inf[1] = -1; inf[2] = -1; inf[3] = b->n_leaves++;
+        b->split[id] = 0.0f;
+        return id;
+    }
+    /* density-weighted median: the smallest k in [1, n-1] whose prefix mass reaches
+     * half of the node mass; an empty node is halved */
+    int ks;
+    if (m == 0.0) {
+        ks = n / 2;
+    } else {
+        double half = 0.5 * m, pre = 0.0;
+        ks = n - 1;
+        for (int k = 1; k <= n - 1; k++) {
+            pre += b->slice[k - 1];
+            if (pre >= half) { ks = k; break; }
+        }
+    }
+    inf[0] = a; inf[3] = -1;
+    b->split[id] = or_coord(b, a, lo[a] + ks);
+    int llo[3] = {lo[0], lo[1], lo[2]}, lhi[3] = {hi[0], hi[1], hi[2]};
+    int rlo[3] = {lo[0], lo[1], lo[2]}, rhi[3] = {hi[0], hi[1], hi[2]};
+    lhi[a] = lo[a] + ks;
+    rlo[a] = lo[a] + ks;
+    int l = or_build_rec(b, llo, lhi, depth + 1, 2u * code);
+    int r = or_build_rec(b, rlo, rhi, depth + 1, 2u * code + 1u);
+    inf = b->info + 6 * id;
+    inf[1] = l; inf[2] = r;
+    return id;
+}
+
+/* Returns the node count (>0), or -1 when max_nodes is too small / input invalid. */
+int or_build_tree(const float *grid, int G, const double *bbox6, int max_depth, double leaf_frac,
+                  int max_nodes, float *box, int *cells, int *info, float *split, double *mass,
+                  int *n_leaves)
+{
+    if (G < 1 || max_depth < 0) return -1;
+    or_build b;
+    memset(&b, 0, sizeof b);
+    b.grid = grid; b.G = G; b.max_depth = max_depth; b.leaf_frac = leaf_frac; b.cap = max_nodes;
+    for (int k = 0; k < 3; k++) { b.blo[k] = bbox6[k]; b.bhi[k] = bbox6[3 + k]; }
+    b.box = box; b.cells = cells; b.info = info; b.split = split; b.mass = mass;
+    b.slice = (double *)malloc(sizeof(double) * (size_t)G);
+    int lo[3] = {0, 0, 0}, hi[3] = {G, G, G};
+    or_build_rec(&b, lo, hi, 0, 1u);
+    free(b.slice);
+    if (b.err) return -1;
+    *n_leaves = b.n_leaves;
+    return b.n;
+}
+
+/* ======================================================================== */
+/* Ray / box slab test and traversal (Sec. 3.5, Algorithm 1 Traverse)       */
+/* ======================================================================== */
+
+/* FP32: t0 = (lo - o) * inv, t1 = (hi - o) * inv per axis (subtract, round, multiply,
+ * round); entry = max over x, y, z of min(t0, t1), exit = min of max(t0, t1), with
+ * NaN-ignoring min/max; entry clamped at 0; a crossing exists iff exit > entry. */
+static int or_slab32(const float *box, const float o[3], const float inv[3], float *tin, float *tout)
+{
+    float tmin[3], tmax[3];
+    for (int a = 0; a < 3; a++) {
+        float s0 = box[a] - o[a];
+        float s1 = box[3 + a] - o[a];
+        float t0 = s0 * inv[a];
+        float t1 = s1 * inv[a];
+        tmin[a] = fminf(t0, t1);
+        tmax[a] = fmaxf(t0, t1);
+    }
+    float e = fmaxf(fmaxf(tmin[0], tmin[1]), tmin[2]);
+    float x = fminf(fminf(tmax[0], tmax[1]), tmax[2]);
+    e = fmaxf(e, 0.0f);
+    *tin = e; *tout = x;
+    return x > e;
+}
+
+static int or_slab64(const float *box, const double o[3], const double inv[3], double *tin, double *tout)
+{
+    double tmin[3], tmax[3];
+    for (int a = 0; a < 3; a++) {
+        double t0 = ((double)box[a] - o[a]) * inv[a];
+        double t1 = ((double)box[3 + a] - o[a]) * inv[a];
+        tmin[a] = fmin(t0, t1);
+        tmax[a] = fmax(t0, t1);
+    }
+    double e = fmax(fmax(tmin[0], tmin[1]), tmin[2]);
+    double x = fmin(fmin(tmax[0], tmax[1]), tmax[2]);
+    e = fmax(e, 0.0);
+    *tin = e; *tout = x;
+    return x > e;
+}
+
+/* One ray: ordered list of leaf crossings, at most maxc.  method 0 = stack
+ * traversal (near child first: the child on the origin's side of the split plane;
+ * an origin on the plane goes left when d <= 0 along the axis), method 1 = every
+ * leaf tested, positive crossings sorted by entry (the definition the stack form
+ * must reproduce). */
+static int or_trav_ray(const float *box, const int *info, const float *split, int n_nodes,
+                       const float of[3], const float df[3], int maxc, int mode, int method,
+                       int *leaf, double *tin, double *tout)
+{
+    float inv32[3];
+    double o64[3], inv64[3];
+    for (int a = 0; a < 3; a++) {
+        inv32[a] = 1.0f / df[a];
+        o64[a] = (double)of[a];
+        inv64[a] = 1.0 / (double)df[a];
+    }
+    int cnt = 0;
+    if (method == 1) {
+        int nl = 0;
+        for (int i = 0; i < n_nodes; i++) {
+            if (info[6 * i] != -1) continue;
+            double a0, a1;
+            int hit;
+            if (mode == 1) {
+                float e, x;
+                hit = or_slab32(box + 6 * i, of, inv32, &e, &x);
+                a0 = e; a1 = x;
+            } else {
+                hit = or_slab64(box + 6 * i, o64, inv64, &a0, &a1);
+            }
+            if (!hit) continue;
+            /* insertion into the entry-sorted list (stable for equal entries) */
+            int p = nl;
+            while (p > 0 && tin[p - 1] > a0) {
+                if (p < maxc) { leaf[p] = leaf[p - 1]; tin[p] = tin[p - 1]; tout[p] = tout[p - 1]; }
+                p--;
+            }
+            if (p < maxc) { leaf[p] = info[6 * i + 3]; tin[p] = a0; tout[p] = a1; }
+            if (nl < maxc) nl++;
+        }
+        return nl;
+    }
+    int stack[OR_MAX_STACK], sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0 && cnt < maxc) {
+        int nd = stack[--sp];
+        double a0, a1;
+        int hit;
+        if (mode == 1) {
+            float e, x;
+            hit = or_slab32(box + 6 * nd, of, inv32, &e, &x);
+            a0 = e; a1 = x;
+        } else {
+            hit = or_slab64(box + 6 * nd, o64, inv64, &a0, &a1);
+        }
+        if (!hit) continue;
+        const int *inf = info + 6 * nd;
+        if (inf[0] < 0) {
+            leaf[cnt] = inf[3]; tin[cnt] = a0; tout[cnt] = a1; cnt++;
+            continue;
+        }
+        int ax = inf[0];
+        int near_left = of[ax] < split[nd] || (of[ax] == split[nd] && df[ax] <= 0.0f);
+        int nearc = near_left ? inf[1] : inf[2];
+        int farc = near_left ? inf[2] : inf[1];
+        if (sp + 2 > OR_MAX_STACK) return -1;
+        stack[sp++] = farc;
+        stack[sp++] = nearc;
+    }
+    return cnt;
+}
+
+int or_traverse(const float *box, const int *info, const float *split, int n_nodes,
+                const float *o, const float *d, int64_t n, int maxc, int mode, int method,
+                int *n_x, int *leaf, double *tin, double *tout)
+{
+    for (int64_t r = 0; r < n; r++) {
+        int c = or_trav_ray(box, info, split, n_nodes, o + 3 * r, d + 3 * r, maxc, mode, method,
+                            leaf + r * maxc, tin + r * maxc, tout + r * maxc);
+        if (c < 0) return -1;
+        n_x[r] = c;
+    }
+    return 0;
+}
+
+/* ======================================================================== */
+/* Sampling (Sec. 3.5, Algorithm 1 Sampling; Fig. "prop")                   */
+/* ======================================================================== */
+
+/* Sample j of a crossing: delta = (exit - entry) / steps, t_j = entry + (j + 1/2) delta,
+ * x_j = o + t_j d per component (multiply, round, add, round). */
+static void or_sample32(float e, float x, int steps, int j, const float o[3], const float d[3],
+                        float *t, float *dl, float p[3])
+{
+    float len = x - e;
+    float delta = len / (float)steps;
+    float fj = (float)j + 0.5f;
+    float off = fj * delta;
+    float tj = e + off;
+    for (int a = 0; a < 3; a++) {
+        float m = tj * d[a];
+        p[a] = o[a] + m;
+    }
+    *t = tj; *dl = delta;
+}
+
+static void or_sample64(double e, double x, int steps, int j, const double o[3], const double d[3],
+                        double *t, double *dl, double p[3])
+{
+    double delta = (x - e) / (double)steps;
+    double tj = e + ((double)j + 0.5) * delta;
+    for (int a = 0; a < 3; a++) p[a] = o[a] + tj * d[a];
+    *t = tj; *dl = delta;
+}
+
+/* Samples of every ray in slot layout (slot = ray * cap + k * steps + j). */
+int or_samples(const float *o, const float *d, int64_t n, const int *n_x, const double *tin,
+               const double *tout, int maxc, int steps, int cap, int mode,
+               double *t_out, double *delta_out, double *x_out)
+{
+    for (int64_t r = 0; r < n; r++) {
+        for (int k = 0; k < n_x[r]; k++) {
+            for (int j = 0; j < steps; j++) {
+                int64_t s = r * cap + (int64_t)k * steps + j;
+                if (mode == 1) {
+                    float t, dl, p[3];
+                    or_sample32((float)tin[r * maxc + k], (float)tout[r * maxc + k], steps, j,
+                                o + 3 * r, d + 3 * r, &t, &dl, p);
+                    t_out[s] = t; delta_out[s] = dl;
+                    for (int a = 0; a < 3; a++) x_out[3 * s + a] = p[a];
+                } else {
+                    double o64[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
+                    double d64[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
+                    double t, dl, p[3];
+                    or_sample64(tin[r * maxc + k], tout[r * maxc + k], steps, j, o64, d64, &t, &dl, p);
+                    t_out[s] = t; delta_out[s] = dl;
+                    for (int a = 0; a < 3; a++) x_out[3 * s + a] = p[a];
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+/* ======================================================================== */
+/* Grouping by leaf (Sec. 3.5, Fig. "parallel")                             */
+/* ======================================================================== */
+
+/* counts[l] = samples whose crossing lies in leaf l (= steps x crossings);
+ * offsets = exclusive scan of counts (n_leaves + 1 entries);
+ * order = crossing ids (ray * maxc + k) grouped by leaf, ascending inside a leaf. */
+int or_group(const int *n_x, const int *leaf, int64_t n, int maxc, int steps, int n_leaves,
+             int64_t *counts, int64_t *offsets, int64_t *order)
+{
+    int64_t *cur = (int64_t *)calloc((size_t)n_leaves + 1, sizeof(int64_t));
+    for (int l = 0; l < n_leaves; l++) counts[l] = 0;
+    for (int64_t r = 0; r < n; r++)
+        for (int k = 0; k < n_x[r]; k++) {
+            int l = leaf[r * maxc + k];
+            if (l < 0 || l >= n_leaves) { free(cur); return -1; }
+            counts[l] += steps;
+        }
+    offsets[0] = 0;
+    for (int l = 0; l < n_leaves; l++) offsets[l + 1] = offsets[l] + counts[l];
+    for (int l = 0; l < n_leaves; l++) cur[l] = offsets[l] / steps;
+    for (int64_t r = 0; r < n; r++)
+        for (int k = 0; k < n_x[r]; k++) {
+            int l = leaf[r * maxc + k];
+            order[cur[l]++] = r * maxc + k;
+        }
+    free(cur);
+    return 0;
+}
+
+/* ======================================================================== */
+/* Frequency positional encoding and the per-leaf MLP (Sec. 3.1, 3.3, 4.1)   */
+/* ======================================================================== */
+
+/* gamma_L(p) = [p, sin(pi 2^0 p), cos(pi 2^0 p), ..., sin(pi 2^(L-1) p), cos(pi 2^(L-1) p)],
+ * each term a 3-vector.  2^k p is exact; it is reduced exactly to r in [-1, 1]
+ * (remainder by 2) before sin(pi r), cos(pi r) are taken in double. */
+static void or_encode64(const double p[3], int L, double *out)
+{
+    for (int a = 0; a < 3; a++) out[a] = p[a];
+    for (int k = 0; k < L; k++)
+        for (int a = 0; a < 3; a++) {
+            double r = remainder(ldexp(p[a], k), 2.0);
+            out[3 + 6 * k + a] = sin(M_PI * r);
+            out[3 + 6 * k + 3 + a] = cos(M_PI * r);
+        }
+}
+
+static void or_encode32(const float p[3], int L, float *out)
+{
+    for (int a = 0; a < 3; a++) out[a] = p[a];
+    for (int k = 0; k < L; k++)
+        for (int a = 0; a < 3; a++) {
+            float r = remainderf(ldexpf(p[a], k), 2.0f);
+            out[3 + 6 * k + a] = (float)sin(M_PI * (double)r);
+            out[3 + 6 * k + 3 + a] = (float)cos(M_PI * (double)r);
+        }
+}
+
+void or_encode(const double *p, int L, int mode, double *out)
+{
+    if (mode == 1) {
+        float pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
+        float tmp[3 + 6 * 32];
+        or_encode32(pf, L, tmp);
+        for (int i = 0; i < 3 + 6 * L; i++) out[i] = tmp[i];
+    } else {
+        or_encode64(p, L, out);
+    }
+}
+
+static double or_softplus64(double z) { return z > 20.0 ? z : log1p(exp(z)); }
+static double or_sigmoid64(double z) { return 1.0 / (1.0 + exp(-z)); }
+static float or_softplus32(float z) { return z > 20.0f ? z : log1pf(expf(z)); }
+static float or_sigmoid32(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+#define OR_MAXW 256
+#define OR_MAXK 512
+
+/* h_0 = input (k0 wide); h_{l+1} = ReLU(W_l h_l + b_l) for `hidden` layers of `width`;
+ * raw = W_o h_H + b_o (4 wide); sigma = softplus(raw_0), rgb = sigmoid(raw_1..3).
+ * Each dot product is summed over the input index in ascending order, then the bias
+ * is added.  out = sigma, r, g, b; raw (may be NULL) = pre-activation head. */
+static void or_mlp64(const float *P, int width, int hidden, int k0, const double *in, double *out, double *raw)
+{
+    double h[OR_MAXK], g[OR_MAXW];
+    int kin = k0;
+    for (int i = 0; i < k0; i++) h[i] = in[i];
+    const float *w = P;
+    for (int l = 0; l < hidden; l++) {
+        const float *b = w + (size_t)width * kin;
+        for (int o = 0; o < width; o++) {
+            double acc = 0.0;
+            for (int i = 0; i < kin; i++) acc += (double)w[(size_t)o * kin + i] * h[i];
+            acc += (double)b[o];
+            g[o] = acc > 0.0 ? acc : 0.0;
+        }
+        for (int o = 0; o < width; o++) h[o] = g[o];
+        w = b + width;
+        kin = width;
+    }
+    const float *b = w + 4 * width;
+    double z[4];
+    for (int o = 0; o < 4; o++) {
+        double acc = 0.0;
+        for (int i = 0; i < width; i++) acc += (double)w[o * width + i] * h[i];
+        z[o] = acc + (double)b[o];
+    }
+    if (raw) for (int o = 0; o < 4; o++) raw[o] = z[o];
+    out[0] = or_softplus64(z[0]);
+    for (int o = 1; o < 4; o++) out[o] = or_sigmoid64(z[o]);
+}
+
+static void or_mlp32(const float *P, int width, int hidden, int k0, const float *in, float *out, float *raw)
+{
+    float h[OR_MAXK], g[OR_MAXW];
+    int kin = k0;
+    for (int i = 0; i < k0; i++) h[i] = in[i];
+    const float *w = P;
+    for (int l = 0; l < hidden; l++) {
+        const float *b = w + (size_t)width * kin;
+        for (int o = 0; o < width; o++) {
+            float acc = 0.0f;
+            for (int i = 0; i < kin; i++) {
+                float m = w[(size_t)o * kin + i] * h[i];
+                acc = acc + m;
+            }
+            acc = acc + b[o];
+            g[o] = acc > 0.0f ? acc : 0.0f;
+        }
+        for (int o = 0; o < width; o++) h[o] = g[o];
+        w = b + width;
+        kin = width;
+    }
+    const float *b = w + 4 * width;
+    float z[4];
+    for (int o = 0; o < 4; o++) {
+        float acc = 0.0f;
+        for (int i = 0; i < width; i++) {
+            float m = w[o * width + i] * h[i];
+            acc = acc + m;
+        }
+        z[o] = acc + b[o];
+    }
+    if (raw) for (int o = 0; o < 4; o++) raw[o] = z[o];
+    out[0] = or_softplus32(z[0]);
+    for (int o = 1; o < 4; o++) out[o] = or_sigmoid32(z[o]);
+}
+
+/* Network of one leaf on n (x, d) pairs: encodes gamma_lx(x) ++ gamma_ld(d) and runs the
+ * MLP.  out is (n, 4): sigma, r, g, b; raw (may be NULL) is (n, 4) pre-activations. */
+int or_mlp_eval(const float *P, int width, int hidden, int lx, int ld, const double *x, const double *d,
+                int64_t n, int mode, double *out, double *raw)
+{
+    int kx = 3 + 6 * lx, kd = 3 + 6 * ld, k0 = kx + kd;
+    if (width > OR_MAXW || k0 > OR_MAXK || lx > 32 || ld > 32) return -1;
+    for (int64_t s = 0; s < n; s++) {
+        if (mode == 1) {
+            float px[3] = {(float)x[3 * s], (float)x[3 * s + 1], (float)x[3 * s + 2]};
+            float pd[3] = {(float)d[3 * s], (float)d[3 * s + 1], (float)d[3 * s + 2]};
+            float in[OR_MAXK], o4[4], r4[4];
+            or_encode32(px, lx, in);
+            or_encode32(pd, ld, in + kx);
+            or_mlp32(P, width, hidden, k0, in, o4, r4);
+            for (int i = 0; i < 4; i++) { out[4 * s + i] = o4[i]; if (raw) raw[4 * s + i] = r4[i]; }
+        } else {
+            double in[OR_MAXK];
+            or_encode64(x + 3 * s, lx, in);
+            or_encode64(d + 3 * s, ld, in + kx);
+            or_mlp64(P, width, hidden, k0, in, out + 4 * s, raw ? raw + 4 * s : NULL);
+        }
+    }
+    return 0;
+}
+
+/* ======================================================================== */
+/* Full render: traversal, sampling, network, compositing (Sec. 3.1, 3.5)   */
+/* ======================================================================== */
+
+typedef struct {
+    /* tree */
+    const float *box; const int *info; const float *split; int n_nodes;
+    /* networks */
+    const float *params; int64_t per_leaf; int width, hidden, lx, ld;
+    /* rays */
+    const float *o, *d; int64_t n;
+    /* render params */
+    int steps, cap; double t_term; double bg[3]; int mode;
+    /* outputs */
+    double *rgb, *depth, *opacity; int *n_gen, *n_eval; double *ert_margin;
+    double *slot_out; /* (n, cap, 4) sigma rgb; may be NULL */
+    double *slot_w;   /* (n, cap) compositing weight; may be NULL */
+    double *t_final;  /* (n) final transmittance; may be NULL */
+    /* threading */
+    int64_t r0, r1; int err;
+} or_job;
+
+/* Compositing (NeRF quadrature, Sec. 3.1): T = 1; per sample in ray order, stop once
+ * T < t_term; tau = sigma * delta, e = exp(-tau), alpha = 1 - e, w = T alpha,
+ * C += w c, D += w t, T = T e.  rgb = C + T bg, depth = D, opacity = 1 - T. */
+static void or_render_ray(const or_job *J, int64_t r)
+{
+    int maxc = J->cap / J->steps;
+    int leaf[256];
+    double tin[256], tout[256];
+    int kx = 3 + 6 * J->lx, k0 = kx + 3 + 6 * J->ld;
+    int nx = or_trav_ray(J->box, J->info, J->split, J->n_nodes, J->o + 3 * r, J->d + 3 * r,
+                         maxc, J->mode, 0, leaf, tin, tout);
+    if (nx < 0) nx = 0;
+    const float *of = J->o + 3 * r, *df = J->d + 3 * r;
+    int full = J->slot_out != NULL || J->slot_w != NULL;
+    int nev = 0, stopped = 0;
+    double margin = INFINITY;
+    double lt = log(J->t_term);
+    if (J->slot_w) for (int s = 0; s < J->cap; s++) J->slot_w[r * J->cap + s] = 0.0;
+    if (J->mode == 1) {
+        float T = 1.0f, C[3] = {0, 0, 0}, D = 0.0f;
+        float tterm = (float)J->t_term;
+        float din[OR_MAXK];
+        or_encode32(df, J->ld, din + kx);
+        for (int k = 0; k < nx && !(stopped && !full); k++) {
+            const float *P = J->params + (size_t)leaf[k] * J->per_leaf;
+            for (int j = 0; j < J->steps; j++) {
+                int s = k * J->steps + j;
+                if (!stopped) {
+                    double m = fabs(log((double)T) - lt);
+                    if (m < margin) margin = m;
+                    if (T < tterm) stopped = 1;
+                }
+                if (stopped && !full) break;
+                float t, dl, p[3], o4[4];
+                or_sample32((float)tin[k], (float)tout[k], J->steps, j, of, df, &t, &dl, p);
+                or_encode32(p, J->lx, din);
+                or_mlp32(P, J->width, J->hidden, k0, din, o4, NULL);
+                if (J->slot_out) for (int i = 0; i < 4; i++) J->slot_out[(r * J->cap + s) * 4 + i] = o4[i];
+                if (stopped) continue;
+                float tau = o4[0] * dl;
+                float e = expf(-tau);
+                float al = 1.0f - e;
+                float w = T * al;
+                for (int c = 0; c < 3; c++) { float wc = w * o4[1 + c]; C[c] = C[c] + wc; }
+                float wt = w * t;
+                D = D + wt;
+                T = T * e;
+                nev++;
+                if (J->slot_w) J->slot_w[r * J->cap + s] = w;
+            }
+        }
+        for (int c = 0; c < 3; c++) { float tb = T * (float)J->bg[c]; J->rgb[3 * r + c] = C[c] + tb; }
+        J->depth[r] = D;
+        J->opacity[r] = 1.0f - T;
+        if (J->t_final) J->t_final[r] = T;
+    } else {
+        double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
+        double o64[3] = {of[0], of[1], of[2]}, d64[3] = {df[0], df[1], df[2]};
+        double din[OR_MAXK];
+        or_encode64(d64, J->ld, din + kx);
+        for (int k = 0; k < nx && !(stopped && !full); k++) {
+            const float *P = J->params + (size_t)leaf[k] * J->per_leaf;
+            for (int j = 0; j < J->steps; j++) {
+                int s = k * J->steps + j;
+                if (!stopped) {
+                    double m = fabs(log(T) - lt);
+                    if (m < margin) margin = m;
+                    if (T < J->t_term) stopped = 1;
+                }
+                if (stopped && !full) break;
+                double t, dl, p[3], o4[4];
+                or_sample64(tin[k], tout[k], J->steps, j, o64, d64, &t, &dl, p);
+                or_encode64(p, J->lx, din);
+                or_mlp64(P, J->width, J->hidden, k0, din, o4, NULL);
+                if (J->slot_out) for (int i = 0; i < 4; i++) J->slot_out[(r * J->cap + s) * 4 + i] = o4[i];
+                if (stopped) continue;
+                double e = exp(-o4[0] * dl);
+                double w = T * (1.0 - e);
+                for (int c = 0; c < 3; c++) C[c] += w * o4[1 + c];
+                D += w * t;
+                T *= e;
+                nev++;
+                if (J->slot_w) J->slot_w[r * J->cap + s] = w;
+            }
+        }
+        for (int c = 0; c < 3; c++) J->rgb[3 * r + c] = C[c] + T * J->bg[c];
+        J->depth[r] = D;
+        J->opacity[r] = 1.0 - T;
+        if (J->t_final) J->t_final[r] = T;
+    }
+    J->n_gen[r] = nx * J->steps;
+    J->n_eval[r] = nev;
+    J->ert_margin[r] = margin;
+}
+
+static void *or_render_worker(void *arg)
+{
+    or_job *J = (or_job *)arg;
+    for (int64_t r = J->r0; r < J->r1; r++) or_render_ray(J, r);
+    return NULL;
+}
+
+int or_render(const float *box, const int *info, const float *split, int n_nodes,
+              const float *params, int width, int hidden, int lx, int ld,
+              const float *o, const float *d, int64_t n,
+              int steps, int cap, double t_term, const double *bg, int mode, int n_threads,
+              double *rgb, double *depth, double *opacity, int *n_gen, int *n_eval, double *ert_margin,
+              double *slot_out, double *slot_w, double *t_final)
+{
+    if (steps < 1 || cap < steps || cap / steps > 256 || width > OR_MAXW || lx > 32 || ld > 32) return -1;
+    if (n_threads < 1) n_threads = 1;
+    int k0 = 3 + 6 * lx + 3 + 6 * ld;
+    or_job base;
+    memset(&base, 0, sizeof base);
+    base.box = box; base.info = info; base.split = split; base.n_nodes = n_nodes;
+    base.params = params; base.width = width; base.hidden = hidden; base.lx = lx; base.ld = ld;
+    base.per_leaf = (int64_t)width * k0 + width + (int64_t)(hidden - 1) * (width * width + width) + 4 * width + 4;
+    base.o = o; base.d = d; base.n = n; base.steps = steps; base.cap = cap; base.t_term = t_term;
+    for (int c = 0; c < 3; c++) base.bg[c] = bg[c];
+    base.mode = mode;
+    base.rgb = rgb; base.depth = depth; base.opacity = opacity; base.n_gen = n_gen; base.n_eval = n_eval;
+    base.ert_margin = ert_margin; base.slot_out = slot_out; base.slot_w = slot_w; base.t_final = t_final;
+    if (n_threads == 1 || n < 64) {
+        base.r0 = 0; base.r1 = n;
+        or_render_worker(&base);
+        return 0;
+    }
+    or_job *jobs = (or_job *)malloc(sizeof(or_job) * (size_t)n_threads);
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    int64_t chunk = (n + n_threads - 1) / n_threads;
+    int started = 0;
+    for (int i = 0; i < n_threads; i++) {
+        jobs[i] = base;
+        jobs[i].r0 = (int64_t)i * chunk;
+        jobs[i].r1 = jobs[i].r0 + chunk < n ? jobs[i].r0 + chunk : n;
+        if (jobs[i].r0 >= n) break;
+        if (pthread_create(&th[i], NULL, or_render_worker, &jobs[i]) != 0) {
+            or_render_worker(&jobs[i]);
+            th[i] = 0;
+        }
+        started = i + 1;
+    }
+    for (int i = 0; i < started; i++) if (th[i]) pthread_join(th[i], NULL);
+    free(jobs); free(th);
+    return 0;
+}
