@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Benchmark of the Adaptive Multi-NeRF rendering hot path on one GB300 (or N ranks).
+
+Workload (one "step"): the paper-scale scene -- 8 anisotropic Gaussians plus a thin
+shell on a 128^3 guidance grid, KD tree of depth <= 8 with leaf mass <= total/256,
+one 4 x 64 MLP per leaf (frequency encoding L=10 / L=4), 8 views of 800 x 800 rays,
+8 samples per leaf crossing, cap 192 samples per ray -- rendered end to end through
+the library: traversal, grouping, per-leaf networks and compositing.  Inputs are
+synthetic and seeded; the per-step working set (5.12 M rays, ~10 GB of per-sample
+records) is far larger than L2, so no extra flush is needed.
+
+Two network paths are timed: the plain FP32 SIMT path and the BF16 tcgen05 grouped
+path (the headline `value`).  Pixels of a seeded ray subset are compared with the
+FP64 oracle (PSNR, max abs), and the same oracle, timed on the host cores on that
+subset, is reported as `cpu_baseline`.
+
+--impl reference runs the oracle itself (the CPU program the GPU path is checked
+against) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2310_01881_gb300 import scenes as S  # noqa: E402
+
+METRIC = "Msamples/s, Mrays/s at 800x800: plain FP32 vs BF16 grouped @ PSNR≥45dB vs FP64"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES = 128
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self) -> dict:
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[0]) for r in self.rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(cfg, rank: int):
+    """Scene, rays of this rank's 8 views (rank r renders views 8r .. 8r+7)."""
+    grid = S.density_grid(S.scene_for(cfg.scene, 0), cfg.G)
+    os_, ds_ = [], []
+    for v in range(cfg.views):
+        o, d = S.view_rays(cfg, 0, rank * cfg.views + v)
+        os_.append(o)
+        ds_.append(d)
+    return grid, np.concatenate(os_), np.concatenate(ds_)
+
+
+def _algorithmic(cfg, st):
+    """Algorithmic work of one step (bytes / flops), per the unit counts of the step."""
+    rays, xs, samples = st["rays"], st["crossings"], st["samples_generated"]
+    k0 = S.mlp_input_width(cfg.lx, cfg.ld)
+    w, h = cfg.width, cfg.hidden
+    flops_per_sample = 2 * (k0 * w + (h - 1) * w * w + 4 * w)
+    return {
+        "traverse_bytes": 24 * rays + 1 * rays + 10 * xs,
+        "group_bytes": 1 * rays + 6 * xs,
+        "network_bytes": 24 * rays + 12 * xs + 16 * samples,
+        "composite_bytes": 21 * rays + 8 * xs + 16 * samples,
+        "network_flops": flops_per_sample * samples,
+        "flops_per_sample": flops_per_sample,
+    }
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2310_01881_gb300 import amnerf, build
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    cfg = S.CONFIGS[args.config]
+    grid, o_np, d_np = workload(cfg, rank)
+    n = len(o_np)
+    R = amnerf.Renderer(local)
+    R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    P = S.xavier_weights(0, S.leaf_mean_density(grid, R.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    o = torch.from_numpy(o_np).cuda()
+    d = torch.from_numpy(d_np).cuda()
+    out = (torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"), torch.empty(n, device="cuda"))
+    stream = torch.cuda.current_stream()
+    peaks, peak_src = _peaks()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    precs = [p for p in args.prec.split(",") if p]
+    for prec in precs:
+        try:
+            R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, prec)
+        except amnerf.AmnerfError as e:
+            if e.status == amnerf.E_UNSUPPORTED:
+                continue
+            raise
+        for _ in range(args.warmup):
+            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out)
+        _, _, _, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        R.sync()
+        # per-stage CUDA-event times on the launching stream (second pass, synchronised per step)
+        amnerf.amnerf_set_timing(R.ctx, True)
+        stage = np.zeros(4)
+        for _ in range(args.steps):
+            *_, s2 = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out)
+            stage += np.array(s2["ms"])
+        amnerf.amnerf_set_timing(R.ctx, False)
+        stage /= args.steps
+        pix = [t.cpu().numpy() for t in out]
+        results[prec] = {"ms": ms, "stats": st, "stage_ms": stage.tolist(), "pixels": pix, "clocks": clk.summary()}
+
+    if not results:
+        raise RuntimeError("no network precision could be loaded")
+    head = "bf16" if "bf16" in results else next(iter(results))
+    hr = results[head]
+    st = hr["stats"]
+    samples_all = st["samples_generated"] * world
+    rays_all = n * world
+    value = samples_all / (hr["ms"] * 1e-3) / 1e6
+
+    # end to end through the host-buffer entry point (pinned host memory, copies timed)
+    R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, head)
+    ho = torch.from_numpy(o_np).pin_memory().numpy()
+    hd = torch.from_numpy(d_np).pin_memory().numpy()
+    hout = [torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy(),
+            torch.empty(n, dtype=torch.float32).pin_memory().numpy(),
+            torch.empty(n, dtype=torch.float32).pin_memory().numpy()]
+    for _ in range(max(1, args.warmup)):
+        amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
+    barrier()
+
+    if rank != 0:
+        R.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # accuracy against the FP64 oracle on a seeded ray subset + the oracle's own speed
+    import oracle as O
+    tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    P_or = S.xavier_weights(0, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    idx = S.ray_subset(n, args.psnr_rays, 7)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref = O.render(tree, P_or, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps, cfg.cap,
+                   cfg.t_term, mode=0, threads=cores)
+    cpu_s = time.perf_counter() - t0
+    cpu_samples = int(ref["n_gen"].sum())
+    acc = {}
+    for prec, r in results.items():
+        rgb = r["pixels"][0][idx].astype(np.float64)
+        mse = float(np.mean((rgb - ref["rgb"]) ** 2))
+        acc[prec] = {"psnr_db": 10 * np.log10(1.0 / max(mse, 1e-30)),
+                     "max_abs_rgb": float(np.abs(rgb - ref["rgb"]).max()),
+                     "max_abs_opacity": float(np.abs(r["pixels"][2][idx] - ref["opacity"]).max())}
+
+    alg = _algorithmic(cfg, st)
+    net_ms = hr["stage_ms"][2]
+    if head == "fp32":
+        peak = N_SM * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": alg["network_flops"] / (net_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        peak = peaks["bf16_tflops_sustained"] if head == "bf16" else 2 * peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": alg["network_flops"] / (net_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": f"{peak_src} sustained bf16" + (" x2 (fp8)" if head == "fp8" else "")}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = "k_mlp_tc" if head != "fp32" else "k_mlp_simt"
+    roof["kernel_ms"] = net_ms
+    roof["traffic"] = None
+    hbm = peaks["hbm_gbs"]
+    stages = {}
+    for i, (name, key) in enumerate((("traverse", "traverse_bytes"), ("group", "group_bytes"),
+                                     ("network", "network_bytes"), ("composite", "composite_bytes"))):
+        ms_i = hr["stage_ms"][i]
+        gbs = alg[key] / (ms_i * 1e-3) / 1e9 if ms_i > 0 else None
+        stages[name] = {"ms": ms_i, "algorithmic_bytes": alg[key], "GB/s": gbs,
+                        "frac_hbm": gbs / hbm if gbs else None}
+
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "Msamples/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(hr["ms"], 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[head],
+        "data": "synthetic",
+        "config": {"workload": f"{cfg.name}: 800x800 x {cfg.views} views per GPU, 128^3 guidance grid, "
+                               f"depth<=8 (mass<=1/256), 4x64 MLP per leaf, 8 samples/crossing, cap 192",
+                   "rays_per_step": rays_all, "samples_per_step": samples_all, "leaves": R.n_leaves,
+                   "l2": "inputs larger than L2 (per-step working set ~10 GB)", "parallelism": f"replicas x{world}"},
+        "mrays_per_s": round(rays_all / (hr["ms"] * 1e-3) / 1e6, 3),
+        "paths": {p: {"Msamples/s": round(samples_all / (r["ms"] * 1e-3) / 1e6, 3),
+                      "Mrays/s": round(rays_all / (r["ms"] * 1e-3) / 1e6, 3), "ms_per_step": round(r["ms"], 4),
+                      "stage_ms": [round(x, 4) for x in r["stage_ms"]], "vs_fp64": acc[p]}
+                  for p, r in results.items()},
+        "roofline": roof,
+        "stages_hbm": stages,
+        "e2e": {"value": round(samples_all / (e2e_ms * 1e-3) / 1e6, 3), "unit": "Msamples/s",
+                "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(24 * n), "d2h_bytes_per_step": int(20 * n)},
+        "gpu_launches": 5 * args.steps,
+        "clocks": hr["clocks"],
+        "cpu_baseline": {"value": round(cpu_samples / cpu_s / 1e6, 6), "unit": "Msamples/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"FP64 oracle on {len(idx)} seeded rays of view set 0 ({cpu_samples} samples, "
+                                   f"{cpu_s:.1f} s)"},
+    }
+    if "fp32" in results and head != "fp32":
+        line["speedup_vs_fp32"] = round(results["fp32"]["ms"] / hr["ms"], 3)
+    print(json.dumps(line))
+    R.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle (FP64 CPU program) on a bounded sample of the same workload."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle as O
+    cfg = S.CONFIGS[args.config]
+    grid, o_np, d_np = workload(cfg, 0)
+    tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    P = S.xavier_weights(0, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    cores = os.cpu_count() or 1
+    per_step = args.ref_rays
+    times, samples = [], []
+    for i in range(args.warmup + args.steps):
+        idx = S.ray_subset(len(o_np), per_step, 100 + i)
+        t0 = time.perf_counter()
+        ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps, cfg.cap,
+                       cfg.t_term, mode=0, threads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            samples.append(int(ref["n_gen"].sum()))
+    tot_t, tot_s = sum(times), sum(samples)
+    value = tot_s / tot_t / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Msamples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t * 1e3 / len(times), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{cfg.name}: 800x800 x {cfg.views} views, {per_step} seeded rays per step"},
+        "mrays_per_s": round(per_step * len(times) / tot_t / 1e6, 6),
+        "cpu_baseline": {"value": round(value, 6), "unit": "Msamples/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} seeded rays per step of the 800x800x8 workload"},
+        "e2e": {"value": round(value, 6), "unit": "Msamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--prec", default="fp32,bf16")
+    ap.add_argument("--psnr-rays", type=int, default=32768)
+    ap.add_argument("--ref-rays", type=int, default=16384)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * amnerf.h -- C ABI of the GB300 (sm_103a) Adaptive Multi-NeRF rendering library.
+ *
+ * The library renders a batch of camera rays through a density-guided KD tree of
+ * axis-aligned boxes, one small same-shaped MLP per leaf (arXiv 2310.01881):
+ *   1. traversal   every ray is intersected with the tree front to back and one
+ *                  interval is recorded per leaf crossed (Sec. 3.5, Algorithm 1
+ *                  "Traverse");
+ *   2. sampling    each interval gets the same number of samples at stratum
+ *                  midpoints (Sec. 3.5, Algorithm 1 "Sampling", Fig. "prop");
+ *   3. grouping    crossings are grouped by leaf so every leaf network runs as one
+ *                  dense batch (Sec. 3.5, Fig. "parallel");
+ *   4. network     frequency encoding + per-leaf MLP -> density and colour
+ *                  (Sec. 3.1 F_Theta, Sec. 3.3 same-shaped networks);
+ *   5. composite   front-to-back NeRF quadrature with early ray termination
+ *                  (Sec. 3.1 "traditional volumetric rendering").
+ * The tree comes from a guidance density grid (Sec. 3.3-3.4, BuildKDTree).
+ *
+ * Conventions
+ *   - Every function returns an amnerf_status; no C++ exception crosses the ABI.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global
+ *     memory of the context's device.  The caller owns every buffer it passes; the
+ *     library owns the tree, the weights and its scratch memory.
+ *   - Rendering is asynchronous on the context's stream unless stated otherwise;
+ *     device-side failures (a bounded wait that ran out) are recorded in a sticky
+ *     status word that amnerf_sync() returns.
+ *   - Not thread-safe: one context must not be used from two host threads at once.
+ */
+#ifndef AMNERF_H
+#define AMNERF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AMNERF_API __attribute__((visibility("default")))
+#else
+#define AMNERF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amnerf_ctx amnerf_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    AMNERF_OK = 0,
+    AMNERF_E_INVAL = 1,       /* an argument is out of range or NULL */
+    AMNERF_E_NOMEM = 2,       /* device or host allocation failed; nothing was written */
+    AMNERF_E_CUDA = 3,        /* a CUDA runtime call failed */
+    AMNERF_E_NOTREE = 4,      /* amnerf_build_tree has not succeeded on this context */
+    AMNERF_E_NOMLP = 5,       /* no networks loaded, or loaded for another tree */
+    AMNERF_E_TIMEOUT = 6,     /* a bounded device-side wait ran out (sticky) */
+    AMNERF_E_DEVICE = 7,      /* no usable sm_100-class device */
+    AMNERF_E_UNSUPPORTED = 8  /* valid request that this build does not implement */
+} amnerf_status;
+
+typedef enum {
+    AMNERF_FP32 = 0,     /* plain path: FP32 SIMT network */
+    AMNERF_BF16 = 1,     /* tcgen05 tensor cores, BF16 operands, FP32 accumulation */
+    AMNERF_FP8E4M3 = 2   /* tcgen05, E4M3 operands with per-channel scales, FP32 accumulation */
+} amnerf_precision;
+
+/* Subdivision rule (Sec. 3.4).  A node becomes a leaf when depth == max_depth, when
+ * its guidance mass is <= leaf_mass_frac * total mass (leaf_mass_frac > 0), or when
+ * it is one grid cell wide along its longest axis.  max_depth in [0, 12]. */
+typedef struct {
+    int max_depth;
+    double leaf_mass_frac;
+} amnerf_tree_params;
+
+/* One tree node as returned by amnerf_get_tree (preorder: node, left subtree,
+ * right subtree; the left child of an inner node i is node i + 1). */
+typedef struct {
+    float lo[3], hi[3];          /* axis-aligned box */
+    int32_t cell_lo[3];          /* guidance-grid cell range, half-open, x y z */
+    int32_t cell_hi[3];
+    int32_t axis;                /* split axis 0..2, -1 for a leaf */
+    float split;                 /* split coordinate (inner nodes) */
+    int32_t left, right;         /* child node indices, -1 for a leaf */
+    int32_t leaf_id;             /* dense leaf index in left-first order, -1 for inner */
+    uint32_t code;               /* binary path code: root 1, children 2c and 2c+1 (Sec. 3.1) */
+    int32_t depth;
+    int32_t reserved;
+    double mass;                 /* guidance mass of the node */
+} amnerf_node;
+
+/* Shape of every leaf network (all leaves share it, Sec. 3.3):
+ * input gamma_lx(x) ++ gamma_ld(d), (3 + 6 lx) + (3 + 6 ld) wide; `hidden` ReLU
+ * layers of `width`; a 4-wide head: sigma = softplus(z0), rgb = sigmoid(z1..3).
+ * Supported: width in {32, 64}, hidden in [1, 8], lx in [0, 12], ld in [0, 6]. */
+typedef struct {
+    int lx, ld, hidden, width;
+    amnerf_precision prec;
+} amnerf_mlp_desc;
+
+/* Sampling and compositing parameters (Sec. 3.5).
+ * steps_per_leaf: samples per leaf crossing, a power of two in [1, 32].
+ * max_samples:    cap per ray; whole crossings are kept while they fit, so at most
+ *                 floor(max_samples / steps_per_leaf) <= 255 crossings per ray.
+ * t_term:         a sample is composited only while transmittance >= t_term.
+ * bg:             background colour added with the residual transmittance. */
+typedef struct {
+    int steps_per_leaf;
+    int max_samples;
+    float t_term;
+    float bg[3];
+} amnerf_render_params;
+
+/* Filled by a render when a non-NULL pointer is passed (this synchronises). */
+typedef struct {
+    uint64_t rays;
+    uint64_t crossings;           /* leaf crossings kept after the cap */
+    uint64_t samples_generated;   /* steps_per_leaf x crossings */
+    uint64_t samples_composited;  /* samples reached before early termination */
+    uint64_t tiles;               /* network tiles of 128 samples launched */
+    float ms[4];                  /* stage times: traverse, group, network, composite */
+} amnerf_stats;
+
+/* Optional copies of the intermediate results of one render (all DEVICE pointers
+ * owned by the caller; any may be NULL).  maxc = floor(max_samples / steps).
+ *   n_x      uint8  [n_rays]              crossings per ray
+ *   leaf     uint16 [n_rays * maxc]       leaf id of crossing k of ray r at r*maxc+k
+ *   t_in     float  [n_rays * maxc]       crossing entry
+ *   t_out    float  [n_rays * maxc]       crossing exit
+ *   counts   uint32 [n_leaves]            crossings per leaf (samples = steps x counts)
+ *   offsets  uint32 [n_leaves + 1]        exclusive scan of counts
+ *   order    uint32 [n_rays * maxc]       crossing ids r*maxc+k grouped by leaf; the
+ *                                         order inside a leaf is unspecified
+ *   slot_out float  [n_rays * max_samples * 4]  sigma, r, g, b of sample j of ray r at
+ *                                         slot r*max_samples+j (unused slots untouched)
+ * Entries past the valid ones are left untouched. */
+typedef struct {
+    uint8_t *n_x;
+    uint16_t *leaf;
+    float *t_in;
+    float *t_out;
+    uint32_t *counts;
+    uint32_t *offsets;
+    uint32_t *order;
+    float *slot_out;
+} amnerf_debug;
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *out receives the context.
+ * Errors: E_INVAL (out NULL), E_DEVICE (device missing or not compute capability
+ * 10.x), E_NOMEM. */
+AMNERF_API amnerf_status amnerf_create(amnerf_ctx **out, int device, void *cuda_stream);
+
+/* Change the stream later renders enqueue on. */
+AMNERF_API amnerf_status amnerf_set_stream(amnerf_ctx *ctx, void *cuda_stream);
+
+/* Build the density-guided KD tree (Sec. 3.4 BuildKDTree) on the host and upload it.
+ * grid_host: HOST float32 [G][G][G] indexed [z][y][x] (x fastest), finite and >= 0,
+ *            the guidance density at cell centres; G in [2, 1024].
+ * bbox:      HOST double[6] = lo x, lo y, lo z, hi x, hi y, hi z, lo < hi.
+ * Splits: axis = longest in cells (ties to x < y < z); position = the smallest cell
+ * boundary k >= 1 whose prefix mass reaches half the node mass (k = n - 1 when none
+ * does; k = n / 2 for an empty node).  Cell boundary i on axis a is
+ * (float)(lo_a + (hi_a - lo_a) * (i / G)) computed in double.  Masses are double
+ * sums: cells into their slice in z-major, x-minor order, slices in order.
+ * Synchronous.  Replaces any previous tree and invalidates loaded networks.
+ * Errors: E_INVAL (bad sizes, negative / non-finite density), E_NOMEM, E_CUDA. */
+AMNERF_API amnerf_status amnerf_build_tree(amnerf_ctx *ctx, const float *grid_host, int G, const double bbox[6],
+                                const amnerf_tree_params *params, int *n_leaves_out);
+
+/* Copy the current tree into HOST nodes_out (capacity `cap` records); *n_nodes gets
+ * the node count.  E_INVAL when cap is too small (*n_nodes still set). */
+AMNERF_API amnerf_status amnerf_get_tree(amnerf_ctx *ctx, amnerf_node *nodes_out, int cap, int *n_nodes);
+
+/* Load one network per leaf (Sec. 3.3: same shape for all leaves).
+ * weights_host: HOST float32, leaf-major; per leaf, for each hidden layer W_l
+ *               (width x fan_in, row = output, row-major) then b_l (width); then the
+ *               head W_o (4 x width) and b_o (4).  n_leaves must equal the tree's.
+ * The library repacks the weights into the layout of desc->prec (FP32 transposed
+ * tiles, BF16 or E4M3 tcgen05 core-matrix tiles; E4M3 per-leaf, per-layer,
+ * per-output-channel scales s = max|W_row| / 448).  Synchronous.
+ * Errors: E_NOTREE, E_INVAL (shape unsupported or n_leaves mismatch), E_NOMEM. */
+AMNERF_API amnerf_status amnerf_load_mlps(amnerf_ctx *ctx, const amnerf_mlp_desc *desc, int n_leaves,
+                               const float *weights_host);
+
+/* Render n_rays rays (the whole hot path: traverse, sample, group, network,
+ * composite; Sec. 3.5 and Algorithm 1).
+ * rays_o, rays_d: DEVICE float32 [n_rays][3] (x y z per ray); d need not be unit
+ *                 length (the encoding uses it as given).
+ * rgb: DEVICE float32 [n_rays][3]; depth, opacity: DEVICE float32 [n_rays].
+ *      rgb = sum w c + T bg, depth = sum w t (not normalised), opacity = 1 - T.
+ * stats: HOST, may be NULL; when given the call synchronises and fills it.
+ * Asynchronous on the context stream otherwise.  Rays with NaN components are
+ * memory-safe and give NaN pixels.  n_rays * maxc must be < 2^32.
+ * Errors: E_NOTREE, E_NOMLP, E_INVAL, E_NOMEM (scratch growth), E_CUDA. */
+AMNERF_API amnerf_status amnerf_render(amnerf_ctx *ctx, const float *rays_o, const float *rays_d, int64_t n_rays,
+                            const amnerf_render_params *params, float *rgb, float *depth, float *opacity,
+                            amnerf_stats *stats);
+
+/* amnerf_render plus copies of the intermediate results into `dbg` (see
+ * amnerf_debug).  For tests; slower. */
+AMNERF_API amnerf_status amnerf_render_debug(amnerf_ctx *ctx, const float *rays_o, const float *rays_d, int64_t n_rays,
+                                  const amnerf_render_params *params, float *rgb, float *depth,
+                                  float *opacity, const amnerf_debug *dbg, amnerf_stats *stats);
+
+/* amnerf_render with HOST inputs and outputs (same layouts): copies the rays to
+ * library-owned device buffers, renders, copies the pixels back and synchronises.
+ * Page-locked host buffers make the copies asynchronous DMA. */
+AMNERF_API amnerf_status amnerf_render_host(amnerf_ctx *ctx, const float *rays_o_host, const float *rays_d_host,
+                                 int64_t n_rays, const amnerf_render_params *params, float *rgb_host,
+                                 float *depth_host, float *opacity_host, amnerf_stats *stats);
+
+/* Wait for the context stream and return (then clear) the sticky device status:
+ * E_TIMEOUT when a bounded device wait ran out, E_CUDA on an asynchronous CUDA error. */
+AMNERF_API amnerf_status amnerf_sync(amnerf_ctx *ctx);
+
+/* Record per-stage CUDA-event timing in later renders (amnerf_stats.ms). */
+AMNERF_API amnerf_status amnerf_set_timing(amnerf_ctx *ctx, int enable);
+
+/* Human-readable name of a status code (static string). */
+AMNERF_API const char *amnerf_status_string(amnerf_status s);
+
+/* Last error message recorded on this context (static until the next call). */
+AMNERF_API const char *amnerf_last_error(amnerf_ctx *ctx);
+
+/* Free everything the context owns.  NULL is accepted. */
+AMNERF_API void amnerf_destroy(amnerf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMNERF_H */

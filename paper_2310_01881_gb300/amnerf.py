@@ -1,0 +1,311 @@
+"""Thin ctypes binding of libamnerf (include/amnerf.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Device buffers
+are torch CUDA tensors (PyTorch provides memory and streams); all arithmetic of the
+rendering path runs in the library's CUDA kernels.  There is no fallback: when the
+library is missing or does not load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libamnerf.so")
+
+OK, E_INVAL, E_NOMEM, E_CUDA, E_NOTREE, E_NOMLP, E_TIMEOUT, E_DEVICE, E_UNSUPPORTED = range(9)
+FP32, BF16, FP8E4M3 = 0, 1, 2
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp8": FP8E4M3}
+
+
+class AmnerfError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str = ""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({_status_name(status)}) {msg}".rstrip())
+
+
+class amnerf_tree_params(ctypes.Structure):
+    _fields_ = [("max_depth", ctypes.c_int), ("leaf_mass_frac", ctypes.c_double)]
+
+
+class amnerf_node(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("cell_lo", ctypes.c_int32 * 3),
+                ("cell_hi", ctypes.c_int32 * 3), ("axis", ctypes.c_int32), ("split", ctypes.c_float),
+                ("left", ctypes.c_int32), ("right", ctypes.c_int32), ("leaf_id", ctypes.c_int32),
+                ("code", ctypes.c_uint32), ("depth", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mass", ctypes.c_double)]
+
+
+class amnerf_mlp_desc(ctypes.Structure):
+    _fields_ = [("lx", ctypes.c_int), ("ld", ctypes.c_int), ("hidden", ctypes.c_int), ("width", ctypes.c_int),
+                ("prec", ctypes.c_int)]
+
+
+class amnerf_render_params(ctypes.Structure):
+    _fields_ = [("steps_per_leaf", ctypes.c_int), ("max_samples", ctypes.c_int), ("t_term", ctypes.c_float),
+                ("bg", ctypes.c_float * 3)]
+
+
+class amnerf_stats(ctypes.Structure):
+    _fields_ = [("rays", ctypes.c_uint64), ("crossings", ctypes.c_uint64), ("samples_generated", ctypes.c_uint64),
+                ("samples_composited", ctypes.c_uint64), ("tiles", ctypes.c_uint64), ("ms", ctypes.c_float * 4)]
+
+    def as_dict(self) -> dict:
+        return {"rays": self.rays, "crossings": self.crossings, "samples_generated": self.samples_generated,
+                "samples_composited": self.samples_composited, "tiles": self.tiles, "ms": list(self.ms)}
+
+
+class amnerf_debug(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("n_x", "leaf", "t_in", "t_out", "counts", "offsets", "order",
+                                               "slot_out")]
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libamnerf (build it first with paper_2310_01881_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libamnerf is not built ({p} missing); run paper_2310_01881_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    V, I, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    S = ctypes.c_int
+    sig = {
+        "amnerf_create": ([ctypes.POINTER(V), I, V], S),
+        "amnerf_set_stream": ([V, V], S),
+        "amnerf_build_tree": ([V, V, I, V, ctypes.POINTER(amnerf_tree_params), ctypes.POINTER(I)], S),
+        "amnerf_get_tree": ([V, V, I, ctypes.POINTER(I)], S),
+        "amnerf_load_mlps": ([V, ctypes.POINTER(amnerf_mlp_desc), I, V], S),
+        "amnerf_render": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V, V], S),
+        "amnerf_render_debug": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V,
+                                 ctypes.POINTER(amnerf_debug), V], S),
+        "amnerf_render_host": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V, V], S),
+        "amnerf_sync": ([V], S),
+        "amnerf_set_timing": ([V, I], S),
+        "amnerf_status_string": ([S], ctypes.c_char_p),
+        "amnerf_last_error": ([V], ctypes.c_char_p),
+        "amnerf_destroy": ([V], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _status_name(s: int) -> str:
+    try:
+        return load().amnerf_status_string(s).decode()
+    except Exception:  # pragma: no cover - only used in messages
+        return "?"
+
+
+def _check(ctx, status: int, where: str):
+    if status != OK:
+        msg = load().amnerf_last_error(ctx).decode() if ctx else ""
+        raise AmnerfError(status, where, msg)
+
+
+def _ptr(t) -> int | None:
+    """Device pointer of a contiguous CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _hptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+# --------------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# --------------------------------------------------------------------------------------
+
+def amnerf_create(device: int = 0, stream: int | None = None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    st = load().amnerf_create(ctypes.byref(ctx), device, stream)
+    _check(None, st, "amnerf_create")
+    return ctx
+
+
+def amnerf_destroy(ctx) -> None:
+    load().amnerf_destroy(ctx)
+
+
+def amnerf_set_stream(ctx, stream: int | None) -> None:
+    _check(ctx, load().amnerf_set_stream(ctx, stream), "amnerf_set_stream")
+
+
+def amnerf_set_timing(ctx, enable: bool) -> None:
+    _check(ctx, load().amnerf_set_timing(ctx, int(enable)), "amnerf_set_timing")
+
+
+def amnerf_build_tree(ctx, grid: np.ndarray, max_depth: int, leaf_mass_frac: float = 0.0,
+                      bbox=(-1.0, -1.0, -1.0, 1.0, 1.0, 1.0)) -> int:
+    g = np.ascontiguousarray(grid, dtype=np.float32)
+    if g.ndim != 3 or not (g.shape[0] == g.shape[1] == g.shape[2]):
+        raise ValueError("grid must be (G, G, G)")
+    bb = np.ascontiguousarray(bbox, dtype=np.float64)
+    tp = amnerf_tree_params(max_depth, leaf_mass_frac)
+    nl = ctypes.c_int()
+    st = load().amnerf_build_tree(ctx, _hptr(g), g.shape[0], _hptr(bb), ctypes.byref(tp), ctypes.byref(nl))
+    _check(ctx, st, "amnerf_build_tree")
+    return nl.value
+
+
+def amnerf_get_tree(ctx) -> list:
+    n = ctypes.c_int()
+    load().amnerf_get_tree(ctx, None, 0, ctypes.byref(n))
+    arr = (amnerf_node * max(n.value, 1))()
+    _check(ctx, load().amnerf_get_tree(ctx, arr, n.value, ctypes.byref(n)), "amnerf_get_tree")
+    return list(arr[: n.value])
+
+
+def amnerf_load_mlps(ctx, weights: np.ndarray, n_leaves: int, width: int, hidden: int, lx: int, ld: int,
+                     prec: int = FP32) -> None:
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    desc = amnerf_mlp_desc(lx, ld, hidden, width, prec)
+    _check(ctx, load().amnerf_load_mlps(ctx, ctypes.byref(desc), n_leaves, _hptr(w)), "amnerf_load_mlps")
+
+
+def _params(steps: int, cap: int, t_term: float, bg) -> amnerf_render_params:
+    return amnerf_render_params(steps, cap, t_term, (ctypes.c_float * 3)(*bg))
+
+
+def amnerf_render(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
+                  bg=(0.0, 0.0, 0.0), stats: bool = False):
+    """Enqueue a render of CUDA tensors o, d (n, 3) into rgb (n, 3), depth, opacity (n,)."""
+    p = _params(steps, cap, t_term, bg)
+    sp = amnerf_stats() if stats else None
+    st = load().amnerf_render(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
+                              _ptr(opacity), ctypes.byref(sp) if sp is not None else None)
+    _check(ctx, st, "amnerf_render")
+    return sp.as_dict() if sp is not None else None
+
+
+def amnerf_render_debug(ctx, o, d, rgb, depth, opacity, dbg: dict, steps: int = 8, cap: int = 64,
+                        t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), stats: bool = True):
+    p = _params(steps, cap, t_term, bg)
+    db = amnerf_debug(*[_ptr(dbg.get(k)) for k, _ in amnerf_debug._fields_])
+    sp = amnerf_stats() if stats else None
+    st = load().amnerf_render_debug(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
+                                    _ptr(opacity), ctypes.byref(db), ctypes.byref(sp) if sp is not None else None)
+    _check(ctx, st, "amnerf_render_debug")
+    return sp.as_dict() if sp is not None else None
+
+
+def amnerf_render_host(ctx, o: np.ndarray, d: np.ndarray, rgb: np.ndarray, depth: np.ndarray,
+                       opacity: np.ndarray, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
+                       bg=(0.0, 0.0, 0.0), stats: bool = False):
+    """Render from HOST arrays (page-locked buffers make the copies asynchronous)."""
+    for a in (o, d, rgb, depth, opacity):
+        if a.dtype != np.float32 or not a.flags.c_contiguous:
+            raise ValueError("host buffers must be contiguous float32")
+    p = _params(steps, cap, t_term, bg)
+    sp = amnerf_stats() if stats else None
+    st = load().amnerf_render_host(ctx, _hptr(o), _hptr(d), o.shape[0], ctypes.byref(p), _hptr(rgb),
+                                   _hptr(depth), _hptr(opacity), ctypes.byref(sp) if sp is not None else None)
+    _check(ctx, st, "amnerf_render_host")
+    return sp.as_dict() if sp is not None else None
+
+
+def amnerf_sync(ctx) -> None:
+    _check(ctx, load().amnerf_sync(ctx), "amnerf_sync")
+
+
+# --------------------------------------------------------------------------------------
+# convenience wrapper
+# --------------------------------------------------------------------------------------
+
+@dataclass
+class Renderer:
+    """Owns one context; all methods call the entry points above."""
+
+    device: int = 0
+
+    def __post_init__(self):
+        import torch
+        self._torch = torch
+        torch.cuda.set_device(self.device)
+        self.ctx = amnerf_create(self.device, torch.cuda.current_stream(self.device).cuda_stream)
+        self.n_leaves = 0
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            amnerf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_tree(self, grid, max_depth, leaf_mass_frac=0.0, bbox=(-1.0, -1.0, -1.0, 1.0, 1.0, 1.0)) -> int:
+        self.n_leaves = amnerf_build_tree(self.ctx, grid, max_depth, leaf_mass_frac, bbox)
+        return self.n_leaves
+
+    def tree(self) -> list:
+        return amnerf_get_tree(self.ctx)
+
+    def leaf_cells(self) -> np.ndarray:
+        nodes = [n for n in self.tree() if n.axis < 0]
+        nodes.sort(key=lambda n: n.leaf_id)
+        return np.array([list(n.cell_lo) + list(n.cell_hi) for n in nodes], dtype=np.int64)
+
+    def load_mlps(self, weights, width, hidden, lx, ld, prec="fp32") -> None:
+        amnerf_load_mlps(self.ctx, weights, self.n_leaves, width, hidden, lx, ld, PRECISIONS.get(prec, prec))
+
+    def render(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0), stats=False, out=None):
+        torch = self._torch
+        n = o.shape[0]
+        if out is None:
+            out = (torch.empty((n, 3), device=o.device, dtype=torch.float32),
+                   torch.empty((n,), device=o.device, dtype=torch.float32),
+                   torch.empty((n,), device=o.device, dtype=torch.float32))
+        amnerf_set_stream(self.ctx, torch.cuda.current_stream(o.device).cuda_stream)
+        s = amnerf_render(self.ctx, o, d, *out, steps=steps, cap=cap, t_term=t_term, bg=bg, stats=stats)
+        return (*out, s) if stats else out
+
+    def render_debug(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0)):
+        torch = self._torch
+        n = o.shape[0]
+        maxc = cap // steps
+        dev = o.device
+        dbg = {
+            "n_x": torch.zeros(n, dtype=torch.uint8, device=dev),
+            "leaf": torch.zeros(n * maxc, dtype=torch.int16, device=dev),
+            "t_in": torch.zeros(n * maxc, dtype=torch.float32, device=dev),
+            "t_out": torch.zeros(n * maxc, dtype=torch.float32, device=dev),
+            "counts": torch.zeros(max(self.n_leaves, 1), dtype=torch.int32, device=dev),
+            "offsets": torch.zeros(self.n_leaves + 1, dtype=torch.int32, device=dev),
+            "order": torch.zeros(max(n * maxc, 1), dtype=torch.int32, device=dev),
+            "slot_out": torch.zeros(max(n * cap * 4, 1), dtype=torch.float32, device=dev),
+        }
+        rgb = torch.empty((n, 3), device=dev, dtype=torch.float32)
+        depth = torch.empty((n,), device=dev, dtype=torch.float32)
+        opac = torch.empty((n,), device=dev, dtype=torch.float32)
+        amnerf_set_stream(self.ctx, torch.cuda.current_stream(dev).cuda_stream)
+        s = amnerf_render_debug(self.ctx, o, d, rgb, depth, opac, dbg, steps=steps, cap=cap, t_term=t_term, bg=bg)
+        host = {k: v.cpu().numpy() for k, v in dbg.items()}
+        host["leaf"] = host["leaf"].view(np.uint16).astype(np.int64).reshape(n, maxc)
+        host["t_in"] = host["t_in"].reshape(n, maxc)
+        host["t_out"] = host["t_out"].reshape(n, maxc)
+        host["order"] = host["order"].view(np.uint32).astype(np.int64)
+        host["counts"] = host["counts"].view(np.uint32).astype(np.int64)[: self.n_leaves]
+        host["offsets"] = host["offsets"].view(np.uint32).astype(np.int64)
+        host["slot_out"] = host["slot_out"][: n * cap * 4].reshape(n, cap, 4)
+        return rgb.cpu().numpy(), depth.cpu().numpy(), opac.cpu().numpy(), host, s
+
+    def sync(self):
+        amnerf_sync(self.ctx)

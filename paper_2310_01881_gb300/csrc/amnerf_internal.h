@@ -1,0 +1,77 @@
+// amnerf_internal.h -- private declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/amnerf.h"
+
+namespace amnerf {
+
+// Device tree node: two float4 per node.
+//   a = (lo.x, lo.y, lo.z, split)
+//   b = (hi.x, hi.y, hi.z, meta) with meta bits: [0,2) axis + 1 (0 = leaf),
+//       [2,32) right-child index (inner) or leaf id (leaf).  Left child = node + 1.
+struct DevNode {
+    float4 a, b;
+};
+
+constexpr int kTileRows = 128;   // samples per network tile (tcgen05 M)
+constexpr int kMaxLeaves = 4096; // 2^12 leaves at depth 12
+constexpr int kMaxDepth = 12;
+constexpr int kStackDepth = 16;  // traversal stack (depth + 1 entries suffice)
+
+// Error word values written by kernels (first error wins).
+constexpr int kDevErrTimeout = 1;
+constexpr int kDevErrStack = 2;
+constexpr int kDevErrBounds = 3;
+
+// ---- kernels (enqueue only; return cudaGetLastError) ------------------------------
+
+// K-a: traversal + crossing list + per-leaf crossing histogram.
+cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
+                            int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
+                            int n_leaves, int* err);
+
+// K-b: exclusive scans (crossings and network tiles per leaf) and the grouped scatter.
+cudaError_t launch_scan(cudaStream_t s, const uint32_t* counts, int n_leaves, int cpt, uint32_t* offsets,
+                        uint32_t* tile_off, uint32_t* cursor, uint64_t* stats);
+cudaError_t launch_scatter(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
+                           uint32_t* cursor, uint32_t* order, int n_leaves);
+
+// K-c: per-leaf networks over leaf-grouped tiles of 128 samples.
+struct MlpArgs {
+    const uint32_t* order;
+    const uint32_t* offsets;
+    const uint32_t* tile_off;
+    const uint64_t* stats;  // [1] = total tiles
+    int n_leaves;
+    const float2* xing;
+    const float* ro;
+    const float* rd;
+    const void* weights;    // packed per leaf, layout depends on precision
+    size_t leaf_stride;     // bytes per leaf
+    int width, hidden, lx, ld, k0;
+    int steps, maxc, cap;
+    float4* slot_out;
+    int* err;
+};
+cudaError_t launch_mlp_simt(cudaStream_t s, const MlpArgs& a, int grid);
+cudaError_t launch_mlp_tc(cudaStream_t s, const MlpArgs& a, int grid, int prec);
+size_t tc_leaf_stride_bytes(int width, int hidden, int k0, int prec);
+size_t simt_leaf_stride_floats(int width, int hidden, int k0);
+
+// K-d: per-ray compositing.
+cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* xing, const float4* slot_out,
+                             uint32_t n, int steps, int maxc, int cap, float t_term, float bg0, float bg1,
+                             float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats);
+
+// ---- host tree builder -------------------------------------------------------------
+// Returns false on invalid input (message in err).
+bool build_kdtree(const float* grid, int G, const double bbox[6], int max_depth, double leaf_frac,
+                  std::vector<amnerf_node>& out, int& n_leaves, std::string& err);
+
+}  // namespace amnerf

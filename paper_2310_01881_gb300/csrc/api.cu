@@ -1,0 +1,496 @@
+// api.cu -- the C ABI (include/amnerf.h): context, tree and weight upload, scratch
+// management and the render pipeline K-a -> K-b -> K-c -> K-d on one stream.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "amnerf_internal.h"
+
+using namespace amnerf;
+
+struct amnerf_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    // tree
+    std::vector<amnerf_node> nodes;
+    int n_leaves = 0;
+    DevNode* d_nodes = nullptr;
+    // networks
+    bool mlp_loaded = false;
+    amnerf_mlp_desc desc{};
+    int k0 = 0;
+    size_t leaf_stride = 0;  // bytes
+    void* d_weights = nullptr;
+    // per-leaf scratch (sized for kMaxLeaves)
+    uint32_t* d_counts = nullptr;
+    uint32_t* d_offsets = nullptr;
+    uint32_t* d_tile_off = nullptr;
+    uint32_t* d_cursor = nullptr;
+    uint64_t* d_stats = nullptr;  // [0] crossings [1] tiles [2] composited
+    int* d_err = nullptr;
+    // per-ray scratch
+    size_t cap_slots = 0;   // n_rays * maxc capacity
+    size_t cap_samples = 0; // n_rays * cap capacity
+    size_t cap_rays = 0;
+    uint8_t* d_nx = nullptr;
+    float2* d_xing = nullptr;
+    uint16_t* d_xleaf = nullptr;
+    uint32_t* d_order = nullptr;
+    float4* d_slot = nullptr;
+    // host-buffer path
+    size_t cap_host_rays = 0;
+    float* d_hbuf = nullptr;  // o, d, rgb, depth, opacity
+    // timing
+    bool timing = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+amnerf_status fail(amnerf_ctx* c, amnerf_status s, const std::string& msg) {
+    if (c) c->last_error = msg;
+    return s;
+}
+
+amnerf_status cuda_fail(amnerf_ctx* c, cudaError_t e, const char* what) {
+    if (c) c->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? AMNERF_E_NOMEM : AMNERF_E_CUDA;
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+void free_ray_scratch(amnerf_ctx* ctx) {
+    dfree(ctx->d_nx);
+    dfree(ctx->d_xing);
+    dfree(ctx->d_xleaf);
+    dfree(ctx->d_order);
+    dfree(ctx->d_slot);
+    ctx->cap_slots = ctx->cap_samples = ctx->cap_rays = 0;
+}
+
+// Grow the per-ray scratch to hold n rays x maxc crossings x cap slots.
+amnerf_status ensure_scratch(amnerf_ctx* ctx, size_t n, int maxc, int cap) {
+    const size_t slots = n * (size_t)maxc, samples = n * (size_t)cap;
+    if (n <= ctx->cap_rays && slots <= ctx->cap_slots && samples <= ctx->cap_samples) return AMNERF_OK;
+    free_ray_scratch(ctx);
+    const size_t rn = std::max(n, ctx->cap_rays), rs = std::max(slots, ctx->cap_slots),
+                 rm = std::max(samples, ctx->cap_samples);
+    cudaError_t e;
+    if ((e = cudaMalloc((void**)&ctx->d_nx, rn)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_xing, rs * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_xleaf, rs * sizeof(uint16_t))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_order, rs * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_slot, rm * sizeof(float4))) != cudaSuccess) {
+        free_ray_scratch(ctx);
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "scratch allocation");
+    }
+    ctx->cap_rays = rn;
+    ctx->cap_slots = rs;
+    ctx->cap_samples = rm;
+    return AMNERF_OK;
+}
+
+amnerf_status check_params(amnerf_ctx* ctx, const amnerf_render_params* p, int64_t n, int& maxc) {
+    if (!p) return fail(ctx, AMNERF_E_INVAL, "params is NULL");
+    const int st = p->steps_per_leaf;
+    if (st < 1 || st > 32 || (st & (st - 1)) != 0)
+        return fail(ctx, AMNERF_E_INVAL, "steps_per_leaf must be a power of two in [1, 32]");
+    if (p->max_samples < st) return fail(ctx, AMNERF_E_INVAL, "max_samples must be >= steps_per_leaf");
+    maxc = p->max_samples / st;
+    if (maxc > 255) return fail(ctx, AMNERF_E_INVAL, "max_samples / steps_per_leaf must be <= 255");
+    if (!(p->t_term >= 0.0f) || !std::isfinite(p->t_term)) return fail(ctx, AMNERF_E_INVAL, "t_term must be >= 0");
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(p->bg[c])) return fail(ctx, AMNERF_E_INVAL, "bg must be finite");
+    if (n < 0) return fail(ctx, AMNERF_E_INVAL, "n_rays < 0");
+    if ((uint64_t)n * (uint64_t)maxc >= (1ull << 32) || (uint64_t)n * (uint64_t)p->max_samples >= (1ull << 32))
+        return fail(ctx, AMNERF_E_INVAL, "n_rays * max_samples must be < 2^32 (split the batch)");
+    return AMNERF_OK;
+}
+
+// Repack the FP32 master weights of one leaf into the FP32 SIMT layout (transposed).
+void pack_simt(const float* src, float* dst, int width, int hidden, int k0) {
+    const float* w = src;
+    float* o = dst;
+    int kin = k0;
+    for (int l = 0; l < hidden; ++l) {
+        for (int k = 0; k < kin; ++k)
+            for (int n = 0; n < width; ++n) o[(size_t)k * width + n] = w[(size_t)n * kin + k];
+        o += (size_t)kin * width;
+        w += (size_t)kin * width;
+        for (int n = 0; n < width; ++n) o[n] = w[n];
+        o += width;
+        w += width;
+        kin = width;
+    }
+    for (int k = 0; k < width; ++k)
+        for (int n = 0; n < 4; ++n) o[(size_t)k * 4 + n] = w[(size_t)n * width + k];
+    o += 4 * width;
+    w += 4 * width;
+    for (int n = 0; n < 4; ++n) o[n] = w[n];
+}
+
+}  // namespace
+
+// Tensor-core layouts are produced by the tensor-core translation unit.
+namespace amnerf {
+void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0, int prec);
+}
+
+extern "C" {
+
+const char* amnerf_status_string(amnerf_status s) {
+    switch (s) {
+        case AMNERF_OK: return "ok";
+        case AMNERF_E_INVAL: return "invalid argument";
+        case AMNERF_E_NOMEM: return "out of memory";
+        case AMNERF_E_CUDA: return "CUDA error";
+        case AMNERF_E_NOTREE: return "no tree built";
+        case AMNERF_E_NOMLP: return "no networks loaded";
+        case AMNERF_E_TIMEOUT: return "device wait timed out";
+        case AMNERF_E_DEVICE: return "no usable sm_100-class device";
+        case AMNERF_E_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* amnerf_last_error(amnerf_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+amnerf_status amnerf_create(amnerf_ctx** out, int device, void* cuda_stream) {
+    if (!out) return AMNERF_E_INVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return AMNERF_E_DEVICE;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess || prop.major != 10) return AMNERF_E_DEVICE;
+    amnerf_ctx* ctx = new (std::nothrow) amnerf_ctx();
+    if (!ctx) return AMNERF_E_NOMEM;
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e;
+    if ((e = cudaSetDevice(device)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_counts, sizeof(uint32_t) * kMaxLeaves)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_offsets, sizeof(uint32_t) * (kMaxLeaves + 1))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_tile_off, sizeof(uint32_t) * (kMaxLeaves + 1))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_cursor, sizeof(uint32_t) * kMaxLeaves)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_stats, sizeof(uint64_t) * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_err, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(ctx->d_err, 0, sizeof(int))) != cudaSuccess) {
+        amnerf_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? AMNERF_E_NOMEM : AMNERF_E_CUDA;
+    }
+    for (int i = 0; i < 5; ++i) cudaEventCreate(&ctx->ev[i]);
+    *out = ctx;
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_set_stream(amnerf_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return AMNERF_E_INVAL;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_set_timing(amnerf_ctx* ctx, int enable) {
+    if (!ctx) return AMNERF_E_INVAL;
+    ctx->timing = enable != 0;
+    return AMNERF_OK;
+}
+
+void amnerf_destroy(amnerf_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    free_ray_scratch(ctx);
+    dfree(ctx->d_nodes);
+    dfree(ctx->d_weights);
+    dfree(ctx->d_counts);
+    dfree(ctx->d_offsets);
+    dfree(ctx->d_tile_off);
+    dfree(ctx->d_cursor);
+    dfree(ctx->d_stats);
+    dfree(ctx->d_err);
+    dfree(ctx->d_hbuf);
+    for (int i = 0; i < 5; ++i)
+        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    delete ctx;
+}
+
+amnerf_status amnerf_build_tree(amnerf_ctx* ctx, const float* grid_host, int G, const double bbox[6],
+                                const amnerf_tree_params* params, int* n_leaves_out) {
+    if (!ctx || !params || !bbox) return fail(ctx, AMNERF_E_INVAL, "NULL argument");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    std::vector<amnerf_node> nodes;
+    int nl = 0;
+    std::string err;
+    if (!build_kdtree(grid_host, G, bbox, params->max_depth, params->leaf_mass_frac, nodes, nl, err))
+        return fail(ctx, AMNERF_E_INVAL, err);
+    std::vector<DevNode> dn(nodes.size());
+    for (size_t i = 0; i < nodes.size(); ++i) {
+        const amnerf_node& s = nodes[i];
+        const uint32_t payload = s.axis < 0 ? (uint32_t)s.leaf_id : (uint32_t)s.right;
+        const uint32_t meta = (uint32_t)(s.axis + 1) | (payload << 2);
+        dn[i].a = make_float4(s.lo[0], s.lo[1], s.lo[2], s.split);
+        float fmeta;
+        std::memcpy(&fmeta, &meta, sizeof fmeta);
+        dn[i].b = make_float4(s.hi[0], s.hi[1], s.hi[2], fmeta);
+    }
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    dfree(ctx->d_nodes);
+    CK(cudaMalloc((void**)&ctx->d_nodes, sizeof(DevNode) * dn.size()), "tree allocation");
+    CK(cudaMemcpy(ctx->d_nodes, dn.data(), sizeof(DevNode) * dn.size(), cudaMemcpyHostToDevice), "tree upload");
+    ctx->nodes.swap(nodes);
+    ctx->n_leaves = nl;
+    ctx->mlp_loaded = false;
+    dfree(ctx->d_weights);
+    if (n_leaves_out) *n_leaves_out = nl;
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_get_tree(amnerf_ctx* ctx, amnerf_node* nodes_out, int cap, int* n_nodes) {
+    if (!ctx || !n_nodes) return fail(ctx, AMNERF_E_INVAL, "NULL argument");
+    if (ctx->nodes.empty()) return fail(ctx, AMNERF_E_NOTREE, "no tree");
+    *n_nodes = (int)ctx->nodes.size();
+    if (!nodes_out || cap < (int)ctx->nodes.size()) return fail(ctx, AMNERF_E_INVAL, "capacity too small");
+    std::memcpy(nodes_out, ctx->nodes.data(), sizeof(amnerf_node) * ctx->nodes.size());
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_load_mlps(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int n_leaves,
+                               const float* weights_host) {
+    if (!ctx || !desc || !weights_host) return fail(ctx, AMNERF_E_INVAL, "NULL argument");
+    if (ctx->nodes.empty()) return fail(ctx, AMNERF_E_NOTREE, "build the tree first");
+    if (n_leaves != ctx->n_leaves) return fail(ctx, AMNERF_E_INVAL, "n_leaves does not match the tree");
+    const amnerf_mlp_desc& m = *desc;
+    if ((m.width != 32 && m.width != 64) || m.hidden < 1 || m.hidden > 8 || m.lx < 0 || m.lx > 12 || m.ld < 0 ||
+        m.ld > 6)
+        return fail(ctx, AMNERF_E_INVAL, "unsupported network shape");
+    if (m.prec != AMNERF_FP32 && m.prec != AMNERF_BF16 && m.prec != AMNERF_FP8E4M3)
+        return fail(ctx, AMNERF_E_INVAL, "unknown precision");
+    const int k0 = (3 + 6 * m.lx) + (3 + 6 * m.ld);
+    const size_t per = (size_t)m.width * k0 + m.width + (size_t)(m.hidden - 1) * (m.width * m.width + m.width) +
+                       4 * (size_t)m.width + 4;
+    for (size_t i = 0; i < per * (size_t)n_leaves; ++i)
+        if (!std::isfinite(weights_host[i])) return fail(ctx, AMNERF_E_INVAL, "non-finite weight");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    size_t stride;
+    std::vector<uint8_t> blob;
+    if (m.prec == AMNERF_FP32) {
+        stride = simt_leaf_stride_floats(m.width, m.hidden, k0) * sizeof(float);
+        blob.assign(stride * n_leaves, 0);
+        for (int l = 0; l < n_leaves; ++l)
+            pack_simt(weights_host + per * l, reinterpret_cast<float*>(blob.data() + stride * l), m.width, m.hidden,
+                      k0);
+    } else {
+        stride = tc_leaf_stride_bytes(m.width, m.hidden, k0, (int)m.prec);
+        if (stride == 0) return fail(ctx, AMNERF_E_UNSUPPORTED, "precision not built");
+        blob.assign(stride * n_leaves, 0);
+        for (int l = 0; l < n_leaves; ++l)
+            pack_tc_leaf(weights_host + per * l, blob.data() + stride * l, m.width, m.hidden, k0, (int)m.prec);
+    }
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    dfree(ctx->d_weights);
+    ctx->mlp_loaded = false;
+    CK(cudaMalloc(&ctx->d_weights, blob.size()), "weight allocation");
+    CK(cudaMemcpy(ctx->d_weights, blob.data(), blob.size(), cudaMemcpyHostToDevice), "weight upload");
+    ctx->desc = m;
+    ctx->k0 = k0;
+    ctx->leaf_stride = stride;
+    ctx->mlp_loaded = true;
+    return AMNERF_OK;
+}
+
+static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* rd, int64_t n,
+                                 const amnerf_render_params* p, float* rgb, float* depth, float* opacity,
+                                 const amnerf_debug* dbg, amnerf_stats* stats) {
+    if (!ctx) return AMNERF_E_INVAL;
+    if (ctx->nodes.empty()) return fail(ctx, AMNERF_E_NOTREE, "build the tree first");
+    if (!ctx->mlp_loaded) return fail(ctx, AMNERF_E_NOMLP, "load the networks first");
+    int maxc = 0;
+    amnerf_status st = check_params(ctx, p, n, maxc);
+    if (st != AMNERF_OK) return st;
+    if (n > 0 && (!ro || !rd || !rgb || !depth || !opacity)) return fail(ctx, AMNERF_E_INVAL, "NULL buffer");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int steps = p->steps_per_leaf, cap = p->max_samples;
+    if (n > 0) {
+        st = ensure_scratch(ctx, (size_t)n, maxc, cap);
+        if (st != AMNERF_OK) return st;
+    }
+    cudaStream_t s = ctx->stream;
+    const int L = ctx->n_leaves;
+    const uint32_t nn = (uint32_t)n;
+    if (ctx->timing) cudaEventRecord(ctx->ev[0], s);
+    CK(cudaMemsetAsync(ctx->d_counts, 0, sizeof(uint32_t) * L, s), "memset");
+    CK(cudaMemsetAsync(ctx->d_stats, 0, sizeof(uint64_t) * 8, s), "memset");
+    CK(launch_traverse(s, ro, rd, nn, ctx->d_nodes, maxc, ctx->d_nx, ctx->d_xing, ctx->d_xleaf, ctx->d_counts, L,
+                       ctx->d_err),
+       "traverse launch");
+    if (ctx->timing) cudaEventRecord(ctx->ev[1], s);
+    CK(launch_scan(s, ctx->d_counts, L, kTileRows / steps, ctx->d_offsets, ctx->d_tile_off, ctx->d_cursor,
+                   ctx->d_stats),
+       "scan launch");
+    CK(launch_scatter(s, ctx->d_nx, ctx->d_xleaf, nn, maxc, ctx->d_cursor, ctx->d_order, L), "scatter launch");
+    if (ctx->timing) cudaEventRecord(ctx->ev[2], s);
+    if (n > 0) {
+        MlpArgs a;
+        a.order = ctx->d_order;
+        a.offsets = ctx->d_offsets;
+        a.tile_off = ctx->d_tile_off;
+        a.stats = ctx->d_stats;
+        a.n_leaves = L;
+        a.xing = ctx->d_xing;
+        a.ro = ro;
+        a.rd = rd;
+        a.weights = ctx->d_weights;
+        a.leaf_stride = ctx->leaf_stride;
+        a.width = ctx->desc.width;
+        a.hidden = ctx->desc.hidden;
+        a.lx = ctx->desc.lx;
+        a.ld = ctx->desc.ld;
+        a.k0 = ctx->k0;
+        a.steps = steps;
+        a.maxc = maxc;
+        a.cap = cap;
+        a.slot_out = ctx->d_slot;
+        a.err = ctx->d_err;
+        cudaError_t e = ctx->desc.prec == AMNERF_FP32 ? launch_mlp_simt(s, a, ctx->sm_count)
+                                                      : launch_mlp_tc(s, a, ctx->sm_count, (int)ctx->desc.prec);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "network launch");
+    }
+    if (ctx->timing) cudaEventRecord(ctx->ev[3], s);
+    CK(launch_composite(s, ctx->d_nx, ctx->d_xing, ctx->d_slot, nn, steps, maxc, cap, p->t_term, p->bg[0], p->bg[1],
+                        p->bg[2], rgb, depth, opacity, ctx->d_stats),
+       "composite launch");
+    if (ctx->timing) cudaEventRecord(ctx->ev[4], s);
+
+    if (dbg && n > 0) {
+        const size_t slots = (size_t)n * maxc;
+        if (dbg->n_x) CK(cudaMemcpyAsync(dbg->n_x, ctx->d_nx, (size_t)n, cudaMemcpyDeviceToDevice, s), "debug copy");
+        if (dbg->leaf)
+            CK(cudaMemcpyAsync(dbg->leaf, ctx->d_xleaf, slots * 2, cudaMemcpyDeviceToDevice, s), "debug copy");
+        if (dbg->t_in)
+            CK(cudaMemcpy2DAsync(dbg->t_in, sizeof(float), ctx->d_xing, sizeof(float2), sizeof(float), slots,
+                                 cudaMemcpyDeviceToDevice, s),
+               "debug copy");
+        if (dbg->t_out)
+            CK(cudaMemcpy2DAsync(dbg->t_out, sizeof(float), reinterpret_cast<const float*>(ctx->d_xing) + 1,
+                                 sizeof(float2), sizeof(float), slots, cudaMemcpyDeviceToDevice, s),
+               "debug copy");
+        if (dbg->counts)
+            CK(cudaMemcpyAsync(dbg->counts, ctx->d_counts, 4 * (size_t)L, cudaMemcpyDeviceToDevice, s), "debug copy");
+        if (dbg->offsets)
+            CK(cudaMemcpyAsync(dbg->offsets, ctx->d_offsets, 4 * (size_t)(L + 1), cudaMemcpyDeviceToDevice, s),
+               "debug copy");
+        if (dbg->order)
+            CK(cudaMemcpyAsync(dbg->order, ctx->d_order, slots * 4, cudaMemcpyDeviceToDevice, s), "debug copy");
+        if (dbg->slot_out)
+            CK(cudaMemcpyAsync(dbg->slot_out, ctx->d_slot, (size_t)n * cap * 16, cudaMemcpyDeviceToDevice, s),
+               "debug copy");
+    }
+    if (stats) {
+        uint64_t h[8];
+        CK(cudaMemcpyAsync(h, ctx->d_stats, sizeof h, cudaMemcpyDeviceToHost, s), "stats copy");
+        CK(cudaStreamSynchronize(s), "stream sync");
+        stats->rays = (uint64_t)n;
+        stats->crossings = h[0];
+        stats->samples_generated = h[0] * (uint64_t)steps;
+        stats->tiles = h[1];
+        stats->samples_composited = h[2];
+        for (int i = 0; i < 4; ++i) {
+            float ms = 0.f;
+            if (ctx->timing) cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]);
+            stats->ms[i] = ms;
+        }
+        int herr = 0;
+        CK(cudaMemcpy(&herr, ctx->d_err, sizeof herr, cudaMemcpyDeviceToHost), "status copy");
+        if (herr) {
+            cudaMemset(ctx->d_err, 0, sizeof(int));
+            return fail(ctx, herr == kDevErrTimeout ? AMNERF_E_TIMEOUT : AMNERF_E_CUDA, "device status word set");
+        }
+    }
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_render(amnerf_ctx* ctx, const float* rays_o, const float* rays_d, int64_t n_rays,
+                            const amnerf_render_params* params, float* rgb, float* depth, float* opacity,
+                            amnerf_stats* stats) {
+    return render_impl(ctx, rays_o, rays_d, n_rays, params, rgb, depth, opacity, nullptr, stats);
+}
+
+amnerf_status amnerf_render_debug(amnerf_ctx* ctx, const float* rays_o, const float* rays_d, int64_t n_rays,
+                                  const amnerf_render_params* params, float* rgb, float* depth, float* opacity,
+                                  const amnerf_debug* dbg, amnerf_stats* stats) {
+    return render_impl(ctx, rays_o, rays_d, n_rays, params, rgb, depth, opacity, dbg, stats);
+}
+
+amnerf_status amnerf_render_host(amnerf_ctx* ctx, const float* ro, const float* rd, int64_t n,
+                                 const amnerf_render_params* p, float* rgb, float* depth, float* opacity,
+                                 amnerf_stats* stats) {
+    if (!ctx) return AMNERF_E_INVAL;
+    if (n < 0) return fail(ctx, AMNERF_E_INVAL, "n_rays < 0");
+    if (n > 0 && (!ro || !rd || !rgb || !depth || !opacity)) return fail(ctx, AMNERF_E_INVAL, "NULL buffer");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t nn = (size_t)n;
+    if (nn > ctx->cap_host_rays) {
+        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+        dfree(ctx->d_hbuf);
+        ctx->cap_host_rays = 0;
+        CK(cudaMalloc((void**)&ctx->d_hbuf, nn * 11 * sizeof(float)), "host-path buffers");
+        ctx->cap_host_rays = nn;
+    }
+    float* dro = ctx->d_hbuf;
+    float* drd = dro + 3 * ctx->cap_host_rays;
+    float* drgb = drd + 3 * ctx->cap_host_rays;
+    float* ddep = drgb + 3 * ctx->cap_host_rays;
+    float* dop = ddep + ctx->cap_host_rays;
+    cudaStream_t s = ctx->stream;
+    if (nn) {
+        CK(cudaMemcpyAsync(dro, ro, nn * 12, cudaMemcpyHostToDevice, s), "ray upload");
+        CK(cudaMemcpyAsync(drd, rd, nn * 12, cudaMemcpyHostToDevice, s), "ray upload");
+    }
+    amnerf_status st = render_impl(ctx, dro, drd, n, p, drgb, ddep, dop, nullptr, stats);
+    if (st != AMNERF_OK) return st;
+    if (nn) {
+        CK(cudaMemcpyAsync(rgb, drgb, nn * 12, cudaMemcpyDeviceToHost, s), "pixel download");
+        CK(cudaMemcpyAsync(depth, ddep, nn * 4, cudaMemcpyDeviceToHost, s), "pixel download");
+        CK(cudaMemcpyAsync(opacity, dop, nn * 4, cudaMemcpyDeviceToHost, s), "pixel download");
+    }
+    CK(cudaStreamSynchronize(s), "stream sync");
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_sync(amnerf_ctx* ctx) {
+    if (!ctx) return AMNERF_E_INVAL;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize(), "stream sync");
+    int herr = 0;
+    CK(cudaMemcpy(&herr, ctx->d_err, sizeof herr, cudaMemcpyDeviceToHost), "status copy");
+    if (herr) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        return fail(ctx, herr == kDevErrTimeout ? AMNERF_E_TIMEOUT : AMNERF_E_CUDA, "device status word set");
+    }
+    return AMNERF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// k_group.cu -- K-b: group crossings by leaf (Sec. 3.5 and Fig. "parallel": samples
+// are sorted by node id so that every node's network runs as one dense batch).
+//
+// The keys are small integers (leaf ids < 4096), so the sort is a one-digit counting
+// sort.  Per-leaf totals come from K-a's histogram; one CTA scans them into crossing
+// offsets and network-tile offsets (a tile holds 128 / steps crossings of one leaf).
+// The scatter stages its binning in shared memory: each CTA ranks its crossings per
+// leaf with shared atomics, reserves one contiguous range per touched leaf with a
+// single global atomic, then writes every crossing id into its leaf's segment.
+// Counts and offsets are exact; the order inside a segment is not specified (the
+// network result of a sample does not depend on its position in the batch).
+#include "amnerf_internal.h"
+
+namespace amnerf {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = kMaxLeaves / kScanThreads;  // 4 leaves per thread
+
+__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restrict__ counts, int n_leaves, int cpt,
+                                                       uint32_t* __restrict__ offsets,
+                                                       uint32_t* __restrict__ tile_off,
+                                                       uint32_t* __restrict__ cursor, uint64_t* __restrict__ stats) {
+    __shared__ uint32_t s_c[32], s_t[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t c[kScanPer], t[kScanPer];
+    uint32_t sc = 0, st = 0;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+        const int i = tid * kScanPer + j;
+        c[j] = i < n_leaves ? counts[i] : 0u;
+        t[j] = (c[j] + (uint32_t)cpt - 1u) / (uint32_t)cpt;
+        sc += c[j];
+        st += t[j];
+    }
+    // inclusive warp scan of the per-thread sums
+    uint32_t ic = sc, it = st;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t yc = __shfl_up_sync(0xffffffffu, ic, o);
+        const uint32_t yt = __shfl_up_sync(0xffffffffu, it, o);
+        if (lane >= o) {
+            ic += yc;
+            it += yt;
+        }
+    }
+    if (lane == 31) {
+        s_c[warp] = ic;
+        s_t[warp] = it;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t wc = s_c[lane], wt = s_t[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t yc = __shfl_up_sync(0xffffffffu, wc, o);
+            const uint32_t yt = __shfl_up_sync(0xffffffffu, wt, o);
+            if (lane >= o) {
+                wc += yc;
+                wt += yt;
+            }
+        }
+        s_c[lane] = wc;  // inclusive over warps
+        s_t[lane] = wt;
+    }
+    __syncthreads();
+    uint32_t rc = (warp ? s_c[warp - 1] : 0u) + ic - sc;  // exclusive start of this thread
+    uint32_t rt = (warp ? s_t[warp - 1] : 0u) + it - st;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+        const int i = tid * kScanPer + j;
+        if (i < n_leaves) {
+            offsets[i] = rc;
+            cursor[i] = rc;
+            tile_off[i] = rt;
+        }
+        rc += c[j];
+        rt += t[j];
+    }
+    if (tid == kScanThreads - 1) {
+        offsets[n_leaves] = rc;
+        tile_off[n_leaves] = rt;
+        stats[0] = rc;  // crossings
+        stats[1] = rt;  // tiles
+    }
+}
+
+constexpr int kScatterThreads = 256;
+constexpr int kScatterItems = 16;
+
+__global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __restrict__ n_x,
+                                                             const uint16_t* __restrict__ xleaf, uint32_t n_slots,
+                                                             int maxc, uint32_t* __restrict__ cursor,
+                                                             uint32_t* __restrict__ order, int n_leaves) {
+    extern __shared__ uint32_t sm[];
+    uint32_t* s_cnt = sm;
+    uint32_t* s_base = sm + n_leaves;
+    for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) s_cnt[i] = 0u;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * (uint32_t)(kScatterThreads * kScatterItems);
+    uint16_t lf[kScatterItems];
+    uint32_t rk[kScatterItems];
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        const uint32_t s = base + (uint32_t)(i * kScatterThreads) + threadIdx.x;
+        rk[i] = 0xffffffffu;
+        lf[i] = 0;
+        if (s < n_slots) {
+            const uint32_t ray = s / (uint32_t)maxc;
+            const uint32_t k = s - ray * (uint32_t)maxc;
+            if (k < (uint32_t)__ldg(n_x + ray)) {
+                lf[i] = __ldg(xleaf + s);
+                rk[i] = atomicAdd(&s_cnt[lf[i]], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) {
+        const uint32_t c = s_cnt[i];
+        s_base[i] = c ? atomicAdd(&cursor[i], c) : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        if (rk[i] != 0xffffffffu) {
+            const uint32_t s = base + (uint32_t)(i * kScatterThreads) + threadIdx.x;
+            order[s_base[lf[i]] + rk[i]] = s;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_scan(cudaStream_t s, const uint32_t* counts, int n_leaves, int cpt, uint32_t* offsets,
+                        uint32_t* tile_off, uint32_t* cursor, uint64_t* stats) {
+    k_scan<<<1, kScanThreads, 0, s>>>(counts, n_leaves, cpt, offsets, tile_off, cursor, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
+                           uint32_t* cursor, uint32_t* order, int n_leaves) {
+    const uint64_t n_slots = (uint64_t)n_rays * (uint64_t)maxc;
+    if (n_slots == 0) return cudaSuccess;
+    const uint64_t per = (uint64_t)kScatterThreads * kScatterItems;
+    const unsigned blocks = (unsigned)((n_slots + per - 1) / per);
+    const size_t smem = 2 * sizeof(uint32_t) * (size_t)n_leaves;
+    k_scatter<<<blocks, kScatterThreads, smem, s>>>(n_x, xleaf, (uint32_t)n_slots, maxc, cursor, order, n_leaves);
+    return cudaGetLastError();
+}
+
+}  // namespace amnerf

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Bit-exact: tree, per-ray crossings (leaf ids, entries, exits), per-leaf counts and
+offsets, and the grouped crossing sets.  Floating point (FP32 path): pixels within
+1e-5 max abs of the FP32-mode oracle, which follows the same sample positions; the
+only difference left is the order of the network's sums and of the transmittance
+products.  Rays whose transmittance passes within 0.1% of the termination threshold
+may legitimately stop one sample apart (both results are correct roundings), and
+are held to 2e-4 instead (one sample's weight is at most t_term = 1e-4).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2310_01881_gb300 import scenes as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 1e-5
+ERT_TOL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2310_01881_gb300 import amnerf, build
+    build.build()
+    r = amnerf.Renderer(0)
+    yield r
+    r.close()
+
+
+def _setup(R, cfg, seed=0, G=None, prec="fp32"):
+    grid = S.density_grid(S.scene_for(cfg.scene, seed), G or cfg.G)
+    nl = R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    assert nl == tree.n_leaves
+    # each side derives its weights from its own tree (the trees are compared bit for bit)
+    P_gpu = S.xavier_weights(seed, S.leaf_mean_density(grid, R.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    P_or = S.xavier_weights(seed, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx,
+                            cfg.ld)
+    R.load_mlps(P_gpu, cfg.width, cfg.hidden, cfg.lx, cfg.ld, prec)
+    return grid, tree, P_or
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def _compare_tree(R, tree):
+    nodes = R.tree()
+    assert len(nodes) == tree.n_nodes
+    for i, n in enumerate(nodes):
+        np.testing.assert_array_equal(np.array(list(n.lo) + list(n.hi), np.float32), tree.box[i])
+        np.testing.assert_array_equal(np.array(list(n.cell_lo) + list(n.cell_hi)), tree.cells[i])
+        assert [n.axis, n.left, n.right, n.leaf_id, n.code, n.depth] == list(tree.info[i])
+        assert n.mass == tree.mass[i]
+        if n.axis >= 0:
+            assert n.split == tree.split[i]
+
+
+def _adversarial_rays():
+    s3 = 1 / np.sqrt(3.0)
+    o = [(-3, 0.1, 0.2), (0.3, -3, -0.4), (-3, -3, -3), (-3, 5, 0), (0, 0, 0), (0.2, -0.3, 0.1),
+         (-3, 1, 1), (-3, 0, 0), (0, -3, 0), (0, 0, -3), (-1, -1, -1), (1.5, 0.25, -0.125)]
+    d = [(1, 0, 0), (0, 1, 0), (s3, s3, s3), (1, 0, 0), (0, 0, 1), (-s3, s3, -s3),
+         (1, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (s3, s3, s3), (-1, 0, 0)]
+    return np.array(o, np.float32), np.array(d, np.float32)
+
+
+def _rays(cfg, seed, views=1, w=None, h=None):
+    os_, ds_ = [], []
+    for v in range(views):
+        o, d = S.view_rays(cfg, seed, v, w, h)
+        os_.append(o); ds_.append(d)
+    return np.concatenate(os_), np.concatenate(ds_)
+
+
+def _check_crossings(dbg, tree, o, d, maxc, steps):
+    nx, leaf, tin, tout = O.traverse(tree, o, d, maxc, mode=1)
+    np.testing.assert_array_equal(dbg["n_x"].astype(np.int64), nx)
+    valid = np.arange(maxc)[None, :] < nx[:, None]
+    np.testing.assert_array_equal(dbg["leaf"][valid], leaf[valid])
+    np.testing.assert_array_equal(dbg["t_in"][valid], tin[valid].astype(np.float32))
+    np.testing.assert_array_equal(dbg["t_out"][valid], tout[valid].astype(np.float32))
+    counts, offsets, order = O.group(nx, leaf, maxc, steps, tree.n_leaves)
+    np.testing.assert_array_equal(dbg["counts"] * steps, counts)
+    np.testing.assert_array_equal(dbg["offsets"] * steps, offsets)
+    tot = int(nx.sum())
+    got = dbg["order"][:tot]
+    for l in range(tree.n_leaves):
+        a, b = offsets[l] // steps, offsets[l + 1] // steps
+        np.testing.assert_array_equal(np.sort(got[a:b]), np.sort(order[a:b]))
+
+
+def _check_pixels(rgb, depth, opac, ref, tol=PIX_TOL):
+    amb = ref["ert_margin"] < 1e-3
+    for got, exp in ((rgb, ref["rgb"]), (depth[:, None], ref["depth"][:, None]), (opac[:, None], ref["opacity"][:, None])):
+        err = np.abs(got.astype(np.float64) - exp).max(axis=1)
+        assert err[~amb].max(initial=0.0) <= tol, err[~amb].max()
+        assert err[amb].max(initial=0.0) <= ERT_TOL
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
+def test_c1_tree_traversal_grouping_bit_exact(R, seed):
+    cfg = S.CONFIGS["c1"]
+    _, tree, _ = _setup(R, cfg, seed)
+    _compare_tree(R, tree)
+    o, d = _rays(cfg, seed)
+    ao, ad = _adversarial_rays()
+    o = np.concatenate([o, ao]); d = np.concatenate([d, ad])
+    *_, dbg, st = R.render_debug(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)
+    _check_crossings(dbg, tree, o, d, cfg.cap // cfg.steps, cfg.steps)
+    assert st["samples_generated"] == int(dbg["n_x"].astype(np.int64).sum()) * cfg.steps
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_c1_fp32_pixels_match_fp32_oracle(R, seed):
+    cfg = S.CONFIGS["c1"]
+    _, tree, P = _setup(R, cfg, seed)
+    o, d = _rays(cfg, seed)
+    rgb, depth, opac, dbg, st = R.render_debug(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1, threads=8,
+                   full=True)
+    _check_pixels(rgb, depth, opac, ref)
+    # per-sample network outputs at every generated slot
+    gen = np.arange(cfg.cap)[None, :] < ref["n_gen"][:, None]
+    so = dbg["slot_out"][gen].astype(np.float64)
+    ro = ref["slot_out"][gen]
+    assert np.max(np.abs(so[:, 1:] - ro[:, 1:])) <= 2e-6
+    assert np.max(np.abs(so[:, 0] - ro[:, 0]) / np.maximum(1.0, ro[:, 0])) <= 2e-6
+    assert st["samples_composited"] == int(ref["n_eval"].sum()) or \
+        abs(st["samples_composited"] - int(ref["n_eval"].sum())) <= int((ref["ert_margin"] < 1e-3).sum())
+
+
+def test_c1_fp32_close_to_fp64_definition(R):
+    cfg = S.CONFIGS["c1"]
+    _, tree, P = _setup(R, cfg, 0)
+    o, d = _rays(cfg, 0)
+    rgb, depth, opac = [t.cpu().numpy() for t in R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)]
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=0, threads=8)
+    mse = np.mean((rgb - ref["rgb"]) ** 2)
+    assert 10 * np.log10(1.0 / max(mse, 1e-30)) > 80.0
+
+
+@pytest.mark.parametrize("steps,cap", [(1, 24), (2, 32), (4, 16), (8, 8), (16, 64), (32, 96), (8, 2040)])
+def test_sampling_rates_and_caps(R, steps, cap):
+    cfg = S.CONFIGS["c1"]
+    _, tree, P = _setup(R, cfg, 1)
+    o, d = _rays(cfg, 1, 1, 24, 24)
+    rgb, depth, opac, dbg, _ = R.render_debug(_dev(o), _dev(d), steps=steps, cap=cap)
+    _check_crossings(dbg, tree, o, d, cap // steps, steps)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, steps, cap, mode=1, threads=8)
+    _check_pixels(rgb, depth, opac, ref)
+
+
+def test_single_leaf_tree_and_inside_origins(R):
+    cfg = S.CONFIGS["c1"]
+    grid = S.density_grid(S.scene_for("c1", 2), 16)
+    assert R.build_tree(grid, 0) == 1
+    tree = O.build_tree(grid, 0)
+    P = S.xavier_weights(5, np.array([3.0]), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, "fp32")
+    rng = np.random.default_rng(4)
+    o = rng.uniform(-0.9, 0.9, (300, 3)).astype(np.float32)
+    d = rng.normal(size=(300, 3)); d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    rgb, depth, opac, dbg, _ = R.render_debug(_dev(o), _dev(d), steps=8, cap=64)
+    _check_crossings(dbg, tree, o, d, 8, 8)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, 8, 64, bg=(0.2, 0.4, 0.6), mode=1)
+    rgb2, depth2, opac2 = [t.cpu().numpy() for t in R.render(_dev(o), _dev(d), steps=8, cap=64, bg=(0.2, 0.4, 0.6))]
+    _check_pixels(rgb2, depth2, opac2, ref)
+
+
+def test_empty_batch_and_all_miss(R):
+    cfg = S.CONFIGS["c1"]
+    _setup(R, cfg, 0)
+    e = torch.zeros((0, 3), device="cuda")
+    rgb, depth, opac, st = R.render(e, e, stats=True)
+    assert rgb.shape == (0, 3) and st["samples_generated"] == 0
+    o = np.tile(np.array([[-3, 5, 0]], np.float32), (1000, 1))
+    d = np.tile(np.array([[1, 0, 0]], np.float32), (1000, 1))
+    rgb, depth, opac, st = R.render(_dev(o), _dev(d), bg=(0.25, 0.5, 0.75), stats=True)
+    assert st["samples_generated"] == 0
+    np.testing.assert_array_equal(rgb.cpu().numpy(), np.tile([[0.25, 0.5, 0.75]], (1000, 1)).astype(np.float32))
+    assert float(depth.abs().max()) == 0.0 and float(opac.abs().max()) == 0.0
+
+
+def test_c2_scale_tree_and_sampled_pixels(R):
+    """Paper-scale workload (800x800 x 8 views, <=256 leaves, 4x64 MLP, cap 192) in the
+    launch configuration of the benchmark; a seeded sample of rays is checked against
+    the FP32-mode oracle, and properties are checked on all rays."""
+    cfg = S.CONFIGS["c2"]
+    _, tree, P = _setup(R, cfg, 0)
+    _compare_tree(R, tree)
+    o, d = _rays(cfg, 0, cfg.views)
+    do, dd = _dev(o), _dev(d)
+    rgb, depth, opac, st = R.render(do, dd, steps=cfg.steps, cap=cfg.cap, stats=True)
+    rgb, depth, opac = rgb.cpu().numpy(), depth.cpu().numpy(), opac.cpu().numpy()
+    assert np.all(np.isfinite(rgb)) and np.all((opac >= 0) & (opac <= 1 + 1e-6))
+    assert np.all(rgb >= -1e-6) and np.all(rgb <= 1 + 1e-6)
+    idx = S.ray_subset(len(o), 2048, 1)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o[idx], d[idx], cfg.steps, cfg.cap, mode=1,
+                   threads=16)
+    _check_pixels(rgb[idx], depth[idx], opac[idx], ref)
+    nx, *_ = O.traverse(tree, o[idx], d[idx], cfg.cap // cfg.steps, mode=1)
+    assert st["samples_generated"] >= int(nx.sum()) * cfg.steps
+
+
+def test_host_buffer_entry_point_matches_device(R):
+    from paper_2310_01881_gb300 import amnerf
+    cfg = S.CONFIGS["c1"]
+    _setup(R, cfg, 0)
+    o, d = _rays(cfg, 0)
+    rgb, depth, opac = [t.cpu().numpy() for t in R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)]
+    h = [np.zeros((len(o), 3), np.float32), np.zeros(len(o), np.float32), np.zeros(len(o), np.float32)]
+    amnerf.amnerf_render_host(R.ctx, o, d, *h, steps=cfg.steps, cap=cfg.cap)
+    np.testing.assert_array_equal(h[0], rgb)
+    np.testing.assert_array_equal(h[1], depth)
+    np.testing.assert_array_equal(h[2], opac)
+
+
+def test_invalid_arguments_are_rejected(R):
+    from paper_2310_01881_gb300 import amnerf
+    cfg = S.CONFIGS["c1"]
+    ctx = amnerf.amnerf_create(0, None)
+    try:
+        o = _dev(np.zeros((4, 3)))
+        out = (torch.empty((4, 3), device="cuda"), torch.empty(4, device="cuda"), torch.empty(4, device="cuda"))
+        with pytest.raises(amnerf.AmnerfError) as ei:
+            amnerf.amnerf_render(ctx, o, o, *out)
+        assert ei.value.status == amnerf.E_NOTREE
+        grid = S.density_grid(S.scene_for("c1", 0), 16)
+        with pytest.raises(amnerf.AmnerfError) as ei:
+            amnerf.amnerf_build_tree(ctx, grid, 13)
+        assert ei.value.status == amnerf.E_INVAL
+        bad = grid.copy(); bad[0, 0, 0] = -1
+        with pytest.raises(amnerf.AmnerfError):
+            amnerf.amnerf_build_tree(ctx, bad, 3)
+        nl = amnerf.amnerf_build_tree(ctx, grid, 3)
+        with pytest.raises(amnerf.AmnerfError) as ei:
+            amnerf.amnerf_render(ctx, o, o, *out)
+        assert ei.value.status == amnerf.E_NOMLP
+        P = S.xavier_weights(0, np.ones(nl), 32, 2, 10, 4)
+        with pytest.raises(amnerf.AmnerfError):
+            amnerf.amnerf_load_mlps(ctx, P, nl + 1, 32, 2, 10, 4)
+        with pytest.raises(amnerf.AmnerfError):
+            amnerf.amnerf_load_mlps(ctx, P, nl, 48, 2, 10, 4)
+        amnerf.amnerf_load_mlps(ctx, P, nl, 32, 2, 10, 4)
+        for kw in ({"steps": 3}, {"steps": 8, "cap": 4}, {"steps": 1, "cap": 300}, {"t_term": -1.0}):
+            with pytest.raises(amnerf.AmnerfError) as ei:
+                amnerf.amnerf_render(ctx, o, o, *out, **kw)
+            assert ei.value.status == amnerf.E_INVAL
+        amnerf.amnerf_render(ctx, o, _dev(np.tile([[1, 0, 0]], (4, 1))), *out)
+        amnerf.amnerf_sync(ctx)
+    finally:
+        amnerf.amnerf_destroy(ctx)
