@@ -1,8 +1,501 @@
-// k_mlp_tc.cu -- K-c on tcgen05 tensor cores (placeholder until the kernel lands).
+// k_mlp_tc.cu -- K-c on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Same network and work unit as the FP32 path (Sec. 3.1 F_Theta; one small
+// same-shaped MLP per leaf, Sec. 3.3; samples grouped by node, Sec. 3.5): a tile is
+// 128 samples = 128 / steps crossings of one leaf.  Here every layer is one
+// 128 x N x K tensor-core contraction:
+//
+//   A (activations, 128 x K, BF16)  -- written by the CUDA cores into shared memory
+//   B (layer weights, N x K, BF16)  -- the leaf's weights, bulk-copied (TMA engine)
+//                                      into shared memory once per leaf change
+//   D (128 x N, FP32)               -- accumulator in tensor memory (TMEM)
+//
+// Both operands use the K-major, non-swizzled core-matrix layout: an 8-row x 16-byte
+// core matrix is 128 contiguous bytes; core matrices adjacent along K are 128 B
+// apart (leading byte offset) and 8-row groups are K * 16 B apart (stride byte
+// offset).  Thread r of a warpgroup owns sample row r: it rebuilds the sample,
+// encodes gamma(x) ++ gamma(d) into row r of A, and after each MMA reads its row of
+// D (tcgen05.ld 32x32b: warp q of the group reads TMEM lanes 32q..32q+31), adds the
+// bias, applies ReLU while converting to BF16 (cvt.rn.relu.bf16x2) and writes the
+// next layer's A row.  The head is a 128 x 16 x width MMA whose first 4 columns are
+// (z_sigma, z_r, z_g, z_b); sigma = softplus, rgb = sigmoid in FP32.
+//
+// Several warpgroups per CTA work on different tiles, so one group's epilogue
+// overlaps another's MMA.  Each group issues its own MMAs from one thread and
+// tracks completion with tcgen05.commit on its own mbarrier.  Every wait is bounded
+// (clock64 deadline); on expiry the group records AMNERF_E_TIMEOUT in the status
+// word, leaves its tile loop, and the CTA still frees its TMEM before returning.
+//
+// Encoding: sin/cos(pi 2^k p) for k >= 1 come from the k = 0 pair by the double-angle
+// recurrence (s' = 2 s c, c' = 1 - 2 s^2).  Its error grows about 2x per octave,
+// i.e. below 1e-4 at k = 9, far under the BF16 rounding of the feature (2^-9).
+#include <cuda_bf16.h>
+
+#include <cstring>
+
 #include "amnerf_internal.h"
 
 namespace amnerf {
-size_t tc_leaf_stride_bytes(int, int, int, int) { return 0; }
-void pack_tc_leaf(const float*, uint8_t*, int, int, int, int) {}
-cudaError_t launch_mlp_tc(cudaStream_t, const MlpArgs&, int, int) { return cudaErrorNotSupported; }
+namespace {
+
+constexpr int kLX = 10;  // encodings this kernel is instantiated for
+constexpr int kLD = 4;
+constexpr int kMaxGroups = 4;
+constexpr unsigned long long kWaitCycles = 4000000000ull;  // ~2 s at 2 GHz
+
+__host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ---- per-leaf BF16 blob layout (bytes) ---------------------------------------------
+struct TcLayout {
+    int width, hidden, k0, k0p;
+    size_t w0, wh, wo, bias, stride;  // offsets of W0, W1.., Wo, biases; total stride
+    __host__ __device__ TcLayout(int w, int h, int k) : width(w), hidden(h), k0(k), k0p(round_up(k, 16)) {
+        w0 = 0;
+        wh = w0 + (size_t)w * k0p * 2;
+        wo = wh + (size_t)(h - 1) * w * w * 2;
+        bias = wo + (size_t)16 * w * 2;
+        const size_t end = bias + (size_t)h * w * 4 + 16;
+        stride = (end + 127) / 128 * 128;
+    }
+};
+
+// Core-matrix byte offset of element (row n, column k) of an N x K K-major operand.
+__host__ __device__ inline size_t cm_offset(int n, int k, int K) {
+    return (size_t)(n >> 3) * (K * 16) + (size_t)(k >> 3) * 128 + (size_t)(n & 7) * 16 + (size_t)(k & 7) * 2;
+}
+
+uint16_t f2bf(float f) {  // round to nearest even (inputs are finite)
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t r = ((u >> 16) & 1u) + 0x7fffu;
+    return (uint16_t)((u + r) >> 16);
+}
+
+// ---- PTX helpers -----------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false when the deadline passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
+    if (mbar_test(bar, phase)) return true;
+    const unsigned long long t0 = clock64();
+    while (!mbar_test(bar, phase)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void wg_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+// Warpgroup-wide AND of a predicate (named barrier reduction).
+__device__ __forceinline__ bool wg_all(int id, bool mine) {
+    uint32_t all;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 q, %1, 0;\n\tbar.red.and.pred p, %2, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(all)
+        : "r"((uint32_t)mine), "r"(id)
+        : "memory");
+    return all != 0;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle, LBO = 128 B, SBO = sbo bytes.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3fffu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) |
+           (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128.
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane (load + wait in one block).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%"
+        "20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+    uint32_t r[4];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+__device__ __forceinline__ float softplus_f(float z) { return z > 20.0f ? z : log1pf(expf(z)); }
+__device__ __forceinline__ float sigmoid_f(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+__device__ __forceinline__ int leaf_of_tile(const uint32_t* __restrict__ tile_off, int n_leaves, uint32_t t) {
+    int lo = 0, hi = n_leaves;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(tile_off + mid) <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Encoder: features of gamma_LX(x) ++ gamma_LD(d), emitted in order into 8-wide
+// BF16 chunks of row `row` of the A tile (K0P columns).
+template <int K0P>
+struct RowWriter {
+    uint32_t row_base;  // shared address of (row, k = 0)
+    float buf[8];
+    int n = 0, chunk = 0;
+    __device__ __forceinline__ void push(float f) {
+        buf[n++] = f;
+        if (n == 8) flush();
+    }
+    __device__ __forceinline__ void flush() {
+        st_shared_v4(row_base + (uint32_t)chunk * 128u, pack_bf16(buf[0], buf[1]), pack_bf16(buf[2], buf[3]),
+                     pack_bf16(buf[4], buf[5]), pack_bf16(buf[6], buf[7]));
+        ++chunk;
+        n = 0;
+    }
+};
+
+template <int L, class Wr>
+__device__ __forceinline__ void encode_freq(const float p[3], Wr& w) {
+    w.push(p[0]);
+    w.push(p[1]);
+    w.push(p[2]);
+    float s[3], c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sincospif(p[a], &s[a], &c[a]);
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        if (k > 0) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float t = s[a] + s[a];
+                const float sn = t * c[a];
+                c[a] = fmaf(-t, s[a], 1.0f);
+                s[a] = sn;
+            }
+        }
+        w.push(s[0]);
+        w.push(s[1]);
+        w.push(s[2]);
+        w.push(c[0]);
+        w.push(c[1]);
+        w.push(c[2]);
+    }
+}
+
+struct TcShared {
+    uint64_t bar_w[kMaxGroups];
+    uint64_t bar_m[kMaxGroups];
+    uint32_t tmem_base;
+};
+
+template <int W>
+__global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n_groups, uint32_t tmem_cols) {
+    constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
+    constexpr int K0P = round_up(K0, 16);
+    constexpr int KA = K0P > W ? K0P : W;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const TcLayout lay(W, g.hidden, K0);
+    const size_t a_bytes = (size_t)kTileRows * KA * 2;
+    const size_t per_group = a_bytes + lay.stride;
+    TcShared* sh = reinterpret_cast<TcShared*>(smem + per_group * n_groups);
+
+    const int grp = threadIdx.x >> 7;
+    const int tig = threadIdx.x & 127;  // row within the tile
+    const int warp = threadIdx.x >> 5;
+    const int q = warp & 3;             // TMEM lane quadrant of this warp
+    const int bar_id = 1 + grp;
+    const bool active_group = grp < n_groups;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n_groups; ++i) {
+            mbar_init(smem_u32(&sh->bar_w[i]), 1);
+            mbar_init(smem_u32(&sh->bar_m[i]), 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    if (active_group) {
+        uint8_t* a_tile = smem + per_group * grp;
+        uint8_t* wbuf = a_tile + a_bytes;
+        const uint32_t a_addr = smem_u32(a_tile);
+        const uint32_t w_addr = smem_u32(wbuf);
+        const uint32_t bar_w = smem_u32(&sh->bar_w[grp]);
+        const uint32_t bar_m = smem_u32(&sh->bar_m[grp]);
+        const uint32_t d_col = tmem + (uint32_t)(grp * 64);              // lane 0, this group's columns
+        const uint32_t d_row = d_col + ((uint32_t)(32 * q) << 16);        // this warp's lanes
+        const float* bias = reinterpret_cast<const float*>(wbuf + lay.bias);
+        const uint8_t* wall = reinterpret_cast<const uint8_t*>(g.weights);
+
+        const uint32_t total = (uint32_t)g.stats[1];
+        const uint32_t workers = gridDim.x * (uint32_t)n_groups;
+        const uint32_t wid = blockIdx.x * (uint32_t)n_groups + (uint32_t)grp;
+        const uint32_t per = (total + workers - 1) / workers;
+        const uint32_t t0 = min(wid * per, total);
+        const uint32_t t1 = min(t0 + per, total);
+        const int cpt = kTileRows / g.steps;
+        uint32_t ph_w = 0, ph_m = 0;
+        int cur = -1;
+        bool ok = true;
+
+        for (uint32_t t = t0; t < t1 && ok; ++t) {
+            const int leaf = leaf_of_tile(g.tile_off, g.n_leaves, t);
+            if (leaf != cur) {
+                wg_bar(bar_id);  // every row is done with the previous leaf's weights and biases
+                if (tig == 0) {
+                    fence_proxy_async();
+                    bulk_load(w_addr, wall + (size_t)leaf * lay.stride, (uint32_t)lay.stride, bar_w);
+                }
+                ok = wg_all(bar_id, mbar_wait_bounded(bar_w, ph_w));
+                ph_w ^= 1u;
+                if (!ok) break;
+                cur = leaf;
+            }
+            // ---- rebuild the sample of this row and encode it into A (layer-0 input)
+            const uint32_t first = __ldg(g.offsets + leaf) + (t - __ldg(g.tile_off + leaf)) * (uint32_t)cpt;
+            const uint32_t endc = __ldg(g.offsets + leaf + 1);
+            const int ci = tig / g.steps;
+            const int j = tig - ci * g.steps;
+            const uint32_t c = first + (uint32_t)ci;
+            uint32_t slot = 0xffffffffu;
+            float x[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f};
+            if (c < endc) {
+                const uint32_t id = __ldg(g.order + c);
+                const uint32_t ray = id / (uint32_t)g.maxc;
+                const uint32_t k = id - ray * (uint32_t)g.maxc;
+                const float2 xi = __ldg(g.xing + id);
+                const float delta = __fdiv_rn(__fsub_rn(xi.y, xi.x), (float)g.steps);
+                const float tj = __fadd_rn(xi.x, __fmul_rn((float)j + 0.5f, delta));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float o = __ldg(g.ro + 3 * (size_t)ray + a);
+                    d[a] = __ldg(g.rd + 3 * (size_t)ray + a);
+                    x[a] = __fadd_rn(o, __fmul_rn(tj, d[a]));
+                }
+                slot = ray * (uint32_t)g.cap + k * (uint32_t)g.steps + (uint32_t)j;
+            }
+            {
+                RowWriter<K0P> wr;
+                wr.row_base = a_addr + (uint32_t)((tig >> 3) * (K0P * 16) + (tig & 7) * 16);
+                encode_freq<kLX>(x, wr);
+                encode_freq<kLD>(d, wr);
+#pragma unroll
+                for (int i = K0; i < K0P; ++i) wr.push(0.0f);
+            }
+            fence_proxy_async();
+            tc_fence_before();
+            wg_bar(bar_id);
+
+            // ---- hidden layers and head
+            int kin = K0P;
+            for (int l = 0; l <= g.hidden && ok; ++l) {
+                const bool head = l == g.hidden;
+                const int n = head ? 16 : W;
+                if (tig == 0) {
+                    tc_fence_after();
+                    const uint32_t b_base =
+                        w_addr + (uint32_t)(head ? lay.wo : (l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * W * W * 2));
+                    const uint32_t sbo = (uint32_t)kin * 16u;
+                    const uint32_t id = idesc_bf16(n);
+                    for (int kk = 0; kk < kin / 16; ++kk)
+                        mma_bf16(d_col, sdesc(a_addr + 256u * kk, sbo), sdesc(b_base + 256u * kk, sbo), id,
+                                 kk > 0 ? 1u : 0u);
+                    mma_commit(bar_m);
+                }
+                ok = wg_all(bar_id, mbar_wait_bounded(bar_m, ph_m));
+                ph_m ^= 1u;
+                if (!ok) break;
+                tc_fence_after();
+                if (!head) {
+                    const float* b = bias + (size_t)l * W;
+                    const uint32_t row_base = a_addr + (uint32_t)((tig >> 3) * (W * 16) + (tig & 7) * 16);
+#pragma unroll
+                    for (int h = 0; h < W / 32; ++h) {
+                        float v[32];
+                        tmem_ld32(d_row + 32u * h, v);
+#pragma unroll
+                        for (int cidx = 0; cidx < 4; ++cidx) {
+                            const int c0 = 32 * h + 8 * cidx;
+                            const float4 b0 = *reinterpret_cast<const float4*>(b + c0);
+                            const float4 b1 = *reinterpret_cast<const float4*>(b + c0 + 4);
+                            const float* u = v + 8 * cidx;
+                            st_shared_v4(row_base + (uint32_t)(c0 / 8) * 128u, pack_relu_bf16(u[0] + b0.x, u[1] + b0.y),
+                                         pack_relu_bf16(u[2] + b0.z, u[3] + b0.w),
+                                         pack_relu_bf16(u[4] + b1.x, u[5] + b1.y),
+                                         pack_relu_bf16(u[6] + b1.z, u[7] + b1.w));
+                        }
+                    }
+                    fence_proxy_async();
+                    tc_fence_before();
+                    wg_bar(bar_id);
+                    kin = W;
+                } else {
+                    float z[4];
+                    tmem_ld4(d_row, z);
+                    const float* bo = bias + (size_t)g.hidden * W;
+                    if (slot != 0xffffffffu) {
+                        float4 o;
+                        o.x = softplus_f(z[0] + bo[0]);
+                        o.y = sigmoid_f(z[1] + bo[1]);
+                        o.z = sigmoid_f(z[2] + bo[2]);
+                        o.w = sigmoid_f(z[3] + bo[3]);
+                        g.slot_out[slot] = o;
+                    }
+                    tc_fence_before();
+                }
+            }
+        }
+        if (!ok && tig == 0) atomicCAS(g.err, 0, kDevErrTimeout);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+template <int W>
+cudaError_t launch_w(cudaStream_t s, const MlpArgs& a, int grid) {
+    constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
+    constexpr int K0P = round_up(K0, 16);
+    constexpr int KA = K0P > W ? K0P : W;
+    const TcLayout lay(W, a.hidden, K0);
+    const size_t per_group = (size_t)kTileRows * KA * 2 + lay.stride;
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t reserve = sizeof(TcShared) + 64;
+    int groups = (int)((max_smem - reserve) / per_group);
+    if (groups > kMaxGroups) groups = kMaxGroups;
+    if (groups < 1) return cudaErrorInvalidConfiguration;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)(64 * groups)) cols <<= 1;
+    const size_t smem = per_group * groups + reserve;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_mlp_tc<W><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc_leaf_stride_bytes(int width, int hidden, int k0, int prec) {
+    if (prec != 1) return 0;  // BF16 only in this build
+    if (k0 != (3 + 6 * kLX) + (3 + 6 * kLD)) return 0;
+    return TcLayout(width, hidden, k0).stride;
+}
+
+void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0, int prec) {
+    (void)prec;
+    const TcLayout lay(width, hidden, k0);
+    std::memset(dst, 0, lay.stride);
+    const float* w = src;
+    float* bias = reinterpret_cast<float*>(dst + lay.bias);
+    int kin = k0;
+    for (int l = 0; l < hidden; ++l) {
+        const int K = l == 0 ? lay.k0p : width;
+        uint8_t* base = dst + (l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * width * width * 2);
+        for (int n = 0; n < width; ++n)
+            for (int k = 0; k < kin; ++k) {
+                const uint16_t b = f2bf(w[(size_t)n * kin + k]);
+                std::memcpy(base + cm_offset(n, k, K), &b, 2);
+            }
+        w += (size_t)width * kin;
+        for (int n = 0; n < width; ++n) bias[(size_t)l * width + n] = w[n];
+        w += width;
+        kin = width;
+    }
+    for (int n = 0; n < 4; ++n)
+        for (int k = 0; k < width; ++k) {
+            const uint16_t b = f2bf(w[(size_t)n * width + k]);
+            std::memcpy(dst + lay.wo + cm_offset(n, k, width), &b, 2);
+        }
+    w += 4 * width;
+    for (int n = 0; n < 4; ++n) bias[(size_t)hidden * width + n] = w[n];
+}
+
+cudaError_t launch_mlp_tc(cudaStream_t s, const MlpArgs& a, int grid, int prec) {
+    if (prec != 1) return cudaErrorNotSupported;
+    if (a.width == 64) return launch_w<64>(s, a, grid);
+    if (a.width == 32) return launch_w<32>(s, a, grid);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace amnerf
