@@ -114,12 +114,14 @@ def _dist():
     return world, rank, local
 
 
-def workload(cfg, rank: int):
-    """Scene, rays of this rank's 8 views (rank r renders views 8r .. 8r+7)."""
+def workload(cfg, rank: int, views: int | None = None, px: int | None = None):
+    """Scene, rays of this rank's views (rank r renders views V r .. V r + V - 1).
+    `views` / `px` shrink the workload for profiling runs (defaults: the config's)."""
     grid = S.density_grid(S.scene_for(cfg.scene, 0), cfg.G)
+    nv = views or cfg.views
     os_, ds_ = [], []
-    for v in range(cfg.views):
-        o, d = S.view_rays(cfg, 0, rank * cfg.views + v)
+    for v in range(nv):
+        o, d = S.view_rays(cfg, 0, rank * nv + v, px, px)
         os_.append(o)
         ds_.append(d)
     return grid, np.concatenate(os_), np.concatenate(ds_)
@@ -153,7 +155,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     cfg = S.CONFIGS[args.config]
-    grid, o_np, d_np = workload(cfg, rank)
+    grid, o_np, d_np = workload(cfg, rank, args.views, args.px)
     n = len(o_np)
     R = amnerf.Renderer(local)
     R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
@@ -297,7 +299,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[head],
         "data": "synthetic",
-        "config": {"workload": f"{cfg.name}: 800x800 x {cfg.views} views per GPU, 128^3 guidance grid, "
+        "config": {"workload": f"{cfg.name}: {args.px or cfg.px_w}x{args.px or cfg.px_h} x {args.views or cfg.views} views per GPU, "
+                               f"{cfg.G}^3 guidance grid, "
                                f"depth<=8 (mass<=1/256), 4x64 MLP per leaf, 8 samples/crossing, cap 192",
                    "rays_per_step": rays_all, "samples_per_step": samples_all, "leaves": R.n_leaves,
                    "l2": "inputs larger than L2 (per-step working set ~10 GB)", "parallelism": f"replicas x{world}"},
@@ -372,6 +375,8 @@ def main():
     ap.add_argument("--prec", default="fp32,bf16")
     ap.add_argument("--psnr-rays", type=int, default=32768)
     ap.add_argument("--ref-rays", type=int, default=16384)
+    ap.add_argument("--views", type=int, default=None, help="views per GPU (default: the config's)")
+    ap.add_argument("--px", type=int, default=None, help="square image size (default: the config's)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
