@@ -11,7 +11,7 @@
  *   3. grouping    crossings are grouped by leaf so every leaf network runs as one
  *                  dense batch (Sec. 3.5, Fig. "parallel");
  *   4. network     frequency encoding + per-leaf MLP -> density and colour
- *                  (Sec. 3.1 F_Theta, Sec. 3.3 same-shaped networks);
+ *                  (Sec. 3.1 F_Theta, Sec. 3.2 same-shaped networks);
  *   5. composite   front-to-back NeRF quadrature with early ray termination
  *                  (Sec. 3.1 "traditional volumetric rendering").
  * The tree comes from a guidance density grid (Sec. 3.3-3.4, BuildKDTree).
@@ -86,7 +86,7 @@ typedef struct {
     double mass;                 /* guidance mass of the node */
 } amnerf_node;
 
-/* Shape of every leaf network (all leaves share it, Sec. 3.3):
+/* Shape of every leaf network (all leaves share it, Sec. 3.2):
  * input gamma_lx(x) ++ gamma_ld(d), (3 + 6 lx) + (3 + 6 ld) wide; `hidden` ReLU
  * layers of `width`; a 4-wide head: sigma = softplus(z0), rgb = sigmoid(z1..3).
  * Supported: width in {32, 64}, hidden in [1, 8], lx in [0, 12], ld in [0, 6]. */
@@ -169,7 +169,7 @@ AMNERF_API amnerf_status amnerf_build_tree(amnerf_ctx *ctx, const float *grid_ho
  * the node count.  E_INVAL when cap is too small (*n_nodes still set). */
 AMNERF_API amnerf_status amnerf_get_tree(amnerf_ctx *ctx, amnerf_node *nodes_out, int cap, int *n_nodes);
 
-/* Load one network per leaf (Sec. 3.3: same shape for all leaves).
+/* Load one network per leaf (Sec. 3.2: same shape for all leaves).
  * weights_host: HOST float32, leaf-major; per leaf, for each hidden layer W_l
  *               (width x fan_in, row = output, row-major) then b_l (width); then the
  *               head W_o (4 x width) and b_o (4).  n_leaves must equal the tree's.

@@ -27,12 +27,12 @@
  *              ray * max_cell_count + j; placed at stratum midpoints.
  *   grouping   Sec. 3.5 and Fig. "parallel": samples sorted by node id so that each
  *              node's network runs as one batch.
- *   network    Sec. 3.1 (F_Theta(x, d) -> (c, sigma)), Sec. 3.3/4.1 (one small
+ *   network    Sec. 3.1 (F_Theta(x, d) -> (c, sigma)), Sec. 3.2 and 4.1 (one small
  *              same-shaped MLP per node), frequency positional encoding (Fig.
  *              "complex" caption).
  *   composite  Sec. 3.1 ("traditional volumetric rendering"): NeRF quadrature with
  *              early ray termination.
- *   proposal   not in the paper (related work, Sec. 2.2: sampling networks);
+ *   proposal   not in the paper (related work, Sec. 2.1: sampling networks);
  *              defined in the proposal section of this file.
  *
  * Parity pins live in the test suite (brute-force ray/box classification, closed

@@ -1,6 +1,6 @@
 // k_mlp_simt.cu -- K-c, plain FP32 path: per-leaf networks on CUDA cores.
 //
-// Network (Sec. 3.1 F_Theta, one small same-shaped MLP per leaf, Sec. 3.3/4.1):
+// Network (Sec. 3.1 F_Theta, one small same-shaped MLP per leaf, Sec. 3.2 and 4.1):
 // input gamma_lx(x) ++ gamma_ld(d) with gamma_L(p) = [p, sin(pi 2^k p), cos(pi 2^k p)]
 // for k = 0..L-1 (frequency positional encoding, Fig. "complex"); `hidden` ReLU layers
 // of `width`; head sigma = softplus(z0), rgb = sigmoid(z1..3).

@@ -1,7 +1,7 @@
 // k_mlp_tc.cu -- K-c on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
 // Same network and work unit as the FP32 path (Sec. 3.1 F_Theta; one small
-// same-shaped MLP per leaf, Sec. 3.3; samples grouped by node, Sec. 3.5): a tile is
+// same-shaped MLP per leaf, Sec. 3.2; samples grouped by node, Sec. 3.5): a tile is
 // 128 samples = 128 / steps crossings of one leaf.  Here every layer is one
 // 128 x N x K tensor-core contraction:
 //
