@@ -214,6 +214,27 @@ AMNERF_API amnerf_status amnerf_sync(amnerf_ctx *ctx);
 /* Record per-stage CUDA-event timing in later renders (amnerf_stats.ms). */
 AMNERF_API amnerf_status amnerf_set_timing(amnerf_ctx *ctx, int enable);
 
+/* Group crossings by leaf without allocating anything (no counterpart in the paper;
+ * a variant of the render's grouping step for callers that may not allocate device
+ * memory when they call -- e.g. a frame loop with a fixed memory budget, or a render
+ * thread where cudaMalloc/cudaFree are banned because they can synchronise the
+ * device and stall other streams).
+ * n_x:     DEVICE uint8  [n_rays]         crossings per ray (<= maxc)
+ * leaf:    DEVICE uint16 [n_rays * maxc]  leaf id of crossing k of ray r at r*maxc+k
+ * counts:  DEVICE uint32 [n_leaves]       out: crossings per leaf (cleared by the call)
+ * offsets: DEVICE uint32 [n_leaves + 1]   out: exclusive scan of counts
+ * order:   DEVICE uint32 [n_rays * maxc]  out: crossing ids r*maxc+k grouped by leaf,
+ *                                          order inside a leaf unspecified
+ * Leaf ids >= n_leaves are ignored.  Enqueued on cuda_stream of the current device;
+ * asynchronous.  Scratch: one file-scope device array of about 33 KB per device,
+ * resident until exit, sized for n_leaves <= 4096 (E_INVAL beyond).  The first call
+ * on a device looks the array up with cudaGetSymbolAddress -- make it before any
+ * stream capture.  Calls share the array: calls that overlap on the GPU race.
+ * Errors: E_INVAL (sizes, NULL buffers), E_CUDA. */
+AMNERF_API amnerf_status amnerf_group_by_leaf_static(const uint8_t *n_x, const uint16_t *leaf, int64_t n_rays,
+                                                     int maxc, int n_leaves, uint32_t *counts, uint32_t *offsets,
+                                                     uint32_t *order, void *cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 AMNERF_API const char *amnerf_status_string(amnerf_status s);
 

@@ -88,6 +88,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                  ctypes.POINTER(amnerf_debug), V], S),
         "amnerf_render_host": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V, V], S),
         "amnerf_sync": ([V], S),
+        "amnerf_group_by_leaf_static": ([V, V, L, I, I, V, V, V, V], S),
         "amnerf_set_timing": ([V, I], S),
         "amnerf_status_string": ([S], ctypes.c_char_p),
         "amnerf_last_error": ([V], ctypes.c_char_p),
@@ -217,6 +218,14 @@ def amnerf_render_host(ctx, o: np.ndarray, d: np.ndarray, rgb: np.ndarray, depth
                                    _hptr(depth), _hptr(opacity), ctypes.byref(sp) if sp is not None else None)
     _check(ctx, st, "amnerf_render_host")
     return sp.as_dict() if sp is not None else None
+
+
+def amnerf_group_by_leaf_static(n_x, leaf, n_rays: int, maxc: int, n_leaves: int, counts, offsets, order,
+                                stream: int | None = None) -> None:
+    """Grouping without any allocation (scratch in a static device array); CUDA tensors."""
+    st = load().amnerf_group_by_leaf_static(_ptr(n_x), _ptr(leaf), n_rays, maxc, n_leaves, _ptr(counts),
+                                            _ptr(offsets), _ptr(order), stream)
+    _check(None, st, "amnerf_group_by_leaf_static")
 
 
 def amnerf_sync(ctx) -> None:
