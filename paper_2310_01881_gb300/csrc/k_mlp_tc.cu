@@ -26,9 +26,10 @@
 // (clock64 deadline); on expiry the group records AMNERF_E_TIMEOUT in the status
 // word, leaves its tile loop, and the CTA still frees its TMEM before returning.
 //
-// Encoding: sin/cos(pi 2^k p) for k >= 1 come from the k = 0 pair by the double-angle
-// recurrence (s' = 2 s c, c' = 1 - 2 s^2).  Its error grows about 2x per octave,
-// i.e. below 1e-4 at k = 9, far under the BF16 rounding of the feature (2^-9).
+// Encoding: sin/cos(pi 2^k p) at k = 0 and k = 5 come from the SFU after an exact
+// argument reduction; the other octaves follow by the double-angle recurrence
+// (s' = 2 s c, c' = 1 - 2 s^2), whose error roughly doubles per octave: below 1e-5
+// after 4 doublings, far under the BF16 rounding of a feature (2^-9 relative).
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -98,17 +99,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) 
     return true;
 }
 
-__device__ __forceinline__ void wg_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void wg_bar(int id) { asm volatile("barrier.sync %0, 128;" ::"r"(id) : "memory"); }
 
-// Warpgroup-wide AND of a predicate (named barrier reduction).
-__device__ __forceinline__ bool wg_all(int id, bool mine) {
-    uint32_t all;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 q, %1, 0;\n\tbar.red.and.pred p, %2, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(all)
-        : "r"((uint32_t)mine), "r"(id)
-        : "memory");
-    return all != 0;
+// One thread of the group polls the mbarrier (bounded) while the other 127 sleep at
+// the group's named barrier, so waiting groups take no issue slots from working ones.
+// The flag carries the outcome to the whole group.
+__device__ __forceinline__ bool group_wait(uint32_t bar, uint32_t phase, int bar_id, volatile int* flag, int tig) {
+    if (tig == 0) *flag = mbar_wait_bounded(bar, phase) ? 1 : 0;
+    wg_bar(bar_id);
+    return *flag != 0;
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -221,6 +220,18 @@ struct RowWriter {
     }
 };
 
+// sin(pi 2^k p), cos(pi 2^k p): the argument is reduced exactly to r in [-1, 1]
+// (2^k p - 2 rint(2^(k-1) p)), then the SFU sine/cosine of pi r (abs. error ~4e-7).
+__device__ __forceinline__ void sincospi_anchor(float p, int k, float* s, float* c) {
+    const float y = p * (float)(1 << k);
+    const float r = y - 2.0f * rintf(0.5f * y);
+    const float a = r * 3.14159265358979f;
+    *s = __sinf(a);
+    *c = __cosf(a);
+}
+
+// gamma_L(p) pushed feature by feature; frequencies k = 0 and k = 5 are anchors, the
+// others follow by the double-angle recurrence (at most 4 doublings: error < 1e-5).
 template <int L, class Wr>
 __device__ __forceinline__ void encode_freq(const float p[3], Wr& w) {
     w.push(p[0]);
@@ -228,10 +239,13 @@ __device__ __forceinline__ void encode_freq(const float p[3], Wr& w) {
     w.push(p[2]);
     float s[3], c[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) sincospif(p[a], &s[a], &c[a]);
+    for (int a = 0; a < 3; ++a) sincospi_anchor(p[a], 0, &s[a], &c[a]);
 #pragma unroll
     for (int k = 0; k < L; ++k) {
-        if (k > 0) {
+        if (k == 5) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sincospi_anchor(p[a], 5, &s[a], &c[a]);
+        } else if (k > 0) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const float t = s[a] + s[a];
@@ -252,8 +266,28 @@ __device__ __forceinline__ void encode_freq(const float p[3], Wr& w) {
 struct TcShared {
     uint64_t bar_w[kMaxGroups];
     uint64_t bar_m[kMaxGroups];
+    int flag[kMaxGroups];
     uint32_t tmem_base;
 };
+
+// Crossing of this row in tile t of `leaf` (0xffffffff past the leaf's end).
+__device__ __forceinline__ uint32_t row_crossing(const MlpArgs& g, int leaf, uint32_t t, int ci) {
+    const uint32_t first = __ldg(g.offsets + leaf) + (t - __ldg(g.tile_off + leaf)) * (uint32_t)(kTileRows / g.steps);
+    const uint32_t c = first + (uint32_t)ci;
+    return c < __ldg(g.offsets + leaf + 1) ? __ldg(g.order + c) : 0xffffffffu;
+}
+
+// Crossing interval and ray of crossing `id`.
+__device__ __forceinline__ void crossing_data(const MlpArgs& g, uint32_t id, float2& xi, float o[3], float d[3]) {
+    if (id == 0xffffffffu) return;
+    const uint32_t ray = id / (uint32_t)g.maxc;
+    xi = __ldg(g.xing + id);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = __ldg(g.ro + 3 * (size_t)ray + a);
+        d[a] = __ldg(g.rd + 3 * (size_t)ray + a);
+    }
+}
 
 template <int W>
 __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n_groups, uint32_t tmem_cols) {
@@ -310,44 +344,45 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         const uint32_t per = (total + workers - 1) / workers;
         const uint32_t t0 = min(wid * per, total);
         const uint32_t t1 = min(t0 + per, total);
-        const int cpt = kTileRows / g.steps;
+        volatile int* flag = &sh->flag[grp];
+        const int ci = tig / g.steps;          // crossing of this row within a tile
+        const int j = tig - ci * g.steps;      // sample of this row within its crossing
         uint32_t ph_w = 0, ph_m = 0;
         int cur = -1;
         bool ok = true;
 
+        // software pipeline: the crossing id of tile t+1 is fetched after tile t is
+        // encoded, its interval and ray after the first MMA of tile t has been waited for
+        int leaf = t0 < t1 ? leaf_of_tile(g.tile_off, g.n_leaves, t0) : 0;
+        uint32_t id = t0 < t1 ? row_crossing(g, leaf, t0, ci) : 0xffffffffu;
+        float2 xi = make_float2(0.f, 0.f);
+        float ro[3] = {0.f, 0.f, 0.f}, rd[3] = {0.f, 0.f, 0.f};
+        crossing_data(g, id, xi, ro, rd);
+
         for (uint32_t t = t0; t < t1 && ok; ++t) {
-            const int leaf = leaf_of_tile(g.tile_off, g.n_leaves, t);
             if (leaf != cur) {
                 wg_bar(bar_id);  // every row is done with the previous leaf's weights and biases
                 if (tig == 0) {
                     fence_proxy_async();
                     bulk_load(w_addr, wall + (size_t)leaf * lay.stride, (uint32_t)lay.stride, bar_w);
                 }
-                ok = wg_all(bar_id, mbar_wait_bounded(bar_w, ph_w));
+                ok = group_wait(bar_w, ph_w, bar_id, flag, tig);
                 ph_w ^= 1u;
                 if (!ok) break;
                 cur = leaf;
             }
             // ---- rebuild the sample of this row and encode it into A (layer-0 input)
-            const uint32_t first = __ldg(g.offsets + leaf) + (t - __ldg(g.tile_off + leaf)) * (uint32_t)cpt;
-            const uint32_t endc = __ldg(g.offsets + leaf + 1);
-            const int ci = tig / g.steps;
-            const int j = tig - ci * g.steps;
-            const uint32_t c = first + (uint32_t)ci;
             uint32_t slot = 0xffffffffu;
             float x[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f};
-            if (c < endc) {
-                const uint32_t id = __ldg(g.order + c);
+            if (id != 0xffffffffu) {
                 const uint32_t ray = id / (uint32_t)g.maxc;
                 const uint32_t k = id - ray * (uint32_t)g.maxc;
-                const float2 xi = __ldg(g.xing + id);
                 const float delta = __fdiv_rn(__fsub_rn(xi.y, xi.x), (float)g.steps);
                 const float tj = __fadd_rn(xi.x, __fmul_rn((float)j + 0.5f, delta));
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const float o = __ldg(g.ro + 3 * (size_t)ray + a);
-                    d[a] = __ldg(g.rd + 3 * (size_t)ray + a);
-                    x[a] = __fadd_rn(o, __fmul_rn(tj, d[a]));
+                    d[a] = rd[a];
+                    x[a] = __fadd_rn(ro[a], __fmul_rn(tj, rd[a]));
                 }
                 slot = ray * (uint32_t)g.cap + k * (uint32_t)g.steps + (uint32_t)j;
             }
@@ -363,6 +398,14 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             tc_fence_before();
             wg_bar(bar_id);
 
+            // ---- next tile: leaf (walked forward) and crossing id, loads in flight
+            int leaf_n = leaf;
+            uint32_t id_n = 0xffffffffu;
+            if (t + 1 < t1) {
+                while (__ldg(g.tile_off + leaf_n + 1) <= t + 1) ++leaf_n;
+                id_n = row_crossing(g, leaf_n, t + 1, ci);
+            }
+
             // ---- hidden layers and head
             int kin = K0P;
             for (int l = 0; l <= g.hidden && ok; ++l) {
@@ -373,16 +416,17 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     const uint32_t b_base =
                         w_addr + (uint32_t)(head ? lay.wo : (l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * W * W * 2));
                     const uint32_t sbo = (uint32_t)kin * 16u;
-                    const uint32_t id = idesc_bf16(n);
+                    const uint32_t idd = idesc_bf16(n);
                     for (int kk = 0; kk < kin / 16; ++kk)
-                        mma_bf16(d_col, sdesc(a_addr + 256u * kk, sbo), sdesc(b_base + 256u * kk, sbo), id,
+                        mma_bf16(d_col, sdesc(a_addr + 256u * kk, sbo), sdesc(b_base + 256u * kk, sbo), idd,
                                  kk > 0 ? 1u : 0u);
                     mma_commit(bar_m);
                 }
-                ok = wg_all(bar_id, mbar_wait_bounded(bar_m, ph_m));
+                ok = group_wait(bar_m, ph_m, bar_id, flag, tig);
                 ph_m ^= 1u;
                 if (!ok) break;
                 tc_fence_after();
+                if (l == 0) crossing_data(g, id_n, xi, ro, rd);  // next tile's interval and ray
                 if (!head) {
                     const float* b = bias + (size_t)l * W;
                     const uint32_t row_base = a_addr + (uint32_t)((tig >> 3) * (W * 16) + (tig & 7) * 16);
@@ -421,6 +465,8 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     tc_fence_before();
                 }
             }
+            leaf = leaf_n;
+            id = id_n;
         }
         if (!ok && tig == 0) atomicCAS(g.err, 0, kDevErrTimeout);
     }
