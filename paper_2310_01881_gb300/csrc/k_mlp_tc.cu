@@ -3,22 +3,28 @@
 // Same network and work unit as the FP32 path (Sec. 3.1 F_Theta; one small
 // same-shaped MLP per leaf, Sec. 3.2; samples grouped by node, Sec. 3.5): a tile is
 // 128 samples = 128 / steps crossings of one leaf.  Here every layer is one
-// 128 x N x K tensor-core contraction:
+// 128 x N x K tensor-core contraction with
 //
-//   A (activations, 128 x K, BF16)  -- written by the CUDA cores into shared memory
-//   B (layer weights, N x K, BF16)  -- the leaf's weights, bulk-copied (TMA engine)
-//                                      into shared memory once per leaf change
-//   D (128 x N, FP32)               -- accumulator in tensor memory (TMEM)
+//   A (activations, 128 x K, BF16)  -- kept in tensor memory (TMEM): row r of the
+//                                      tile is TMEM lane r, two BF16 per 32-bit
+//                                      column (even k in the low half)
+//   B (layer weights, N x K, BF16)  -- the leaf's weights in shared memory, K-major
+//                                      no-swizzle core matrices (8 rows x 16 B =
+//                                      128 contiguous bytes; K-adjacent core matrices
+//                                      128 B apart, 8-row groups K * 16 B apart),
+//                                      bulk-copied (TMA engine) once per leaf change
+//   D (128 x N, FP32)               -- accumulator in TMEM
 //
-// Both operands use the K-major, non-swizzled core-matrix layout: an 8-row x 16-byte
-// core matrix is 128 contiguous bytes; core matrices adjacent along K are 128 B
-// apart (leading byte offset) and 8-row groups are K * 16 B apart (stride byte
-// offset).  Thread r of a warpgroup owns sample row r: it rebuilds the sample,
-// encodes gamma(x) ++ gamma(d) into row r of A, and after each MMA reads its row of
-// D (tcgen05.ld 32x32b: warp q of the group reads TMEM lanes 32q..32q+31), adds the
-// bias, applies ReLU while converting to BF16 (cvt.rn.relu.bf16x2) and writes the
-// next layer's A row.  The head is a 128 x 16 x width MMA whose first 4 columns are
-// (z_sigma, z_r, z_g, z_b); sigma = softplus, rgb = sigmoid in FP32.
+// The tensor core streams shared-memory operands at about 128 B per cycle, so a
+// 128 x 64 x 16 MMA with both operands in shared memory (6 KB) is bound near 48
+// cycles; with A in TMEM only the 2 KB weight slice is read and the MMA runs near
+// its 32-cycle compute time.  Thread r of a warpgroup owns sample row r: it rebuilds
+// the sample, encodes gamma(x) ++ gamma(d) and writes it into its TMEM lane
+// (tcgen05.st 32x32b); after each MMA it reads its row of D (tcgen05.ld 32x32b:
+// warp q of the group owns lanes 32q..32q+31), adds the bias (packed f32x2 adds),
+// applies ReLU while converting to BF16 (cvt.rn.relu.bf16x2) and writes the next
+// layer's A back into TMEM.  The head is a 128 x 16 x width MMA whose first 4
+// columns are (z_sigma, z_r, z_g, z_b); sigma = softplus, rgb = sigmoid in FP32.
 //
 // Several warpgroups per CTA work on different tiles, so one group's epilogue
 // overlaps another's MMA.  Each group issues its own MMAs from one thread and
@@ -132,12 +138,36 @@ __device__ __forceinline__ uint32_t idesc_bf16(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// A operand in TMEM (column address a_tmem), B from a shared-memory descriptor.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(
             d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* w) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]), "r"(w[9]),
+        "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// (a0 + b0, a1 + b1) with one packed FP32 instruction.
+__device__ __forceinline__ float2 add_f32x2(float2 a, float2 b) {
+    unsigned long long ua, ub, ud;
+    memcpy(&ua, &a, 8);
+    memcpy(&ub, &b, 8);
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(ud) : "l"(ua), "l"(ub));
+    float2 d;
+    memcpy(&d, &ud, 8);
+    return d;
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -185,10 +215,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return d;
 }
 
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
-}
-
 __device__ __forceinline__ float softplus_f(float z) { return z > 20.0f ? z : log1pf(expf(z)); }
 __device__ __forceinline__ float sigmoid_f(float z) { return 1.0f / (1.0f + expf(-z)); }
 
@@ -201,25 +227,6 @@ __device__ __forceinline__ int leaf_of_tile(const uint32_t* __restrict__ tile_of
     return lo;
 }
 
-// Encoder: features of gamma_LX(x) ++ gamma_LD(d), emitted in order into 8-wide
-// BF16 chunks of row `row` of the A tile (K0P columns).
-template <int K0P>
-struct RowWriter {
-    uint32_t row_base;  // shared address of (row, k = 0)
-    float buf[8];
-    int n = 0, chunk = 0;
-    __device__ __forceinline__ void push(float f) {
-        buf[n++] = f;
-        if (n == 8) flush();
-    }
-    __device__ __forceinline__ void flush() {
-        st_shared_v4(row_base + (uint32_t)chunk * 128u, pack_bf16(buf[0], buf[1]), pack_bf16(buf[2], buf[3]),
-                     pack_bf16(buf[4], buf[5]), pack_bf16(buf[6], buf[7]));
-        ++chunk;
-        n = 0;
-    }
-};
-
 // sin(pi 2^k p), cos(pi 2^k p): the argument is reduced exactly to r in [-1, 1]
 // (2^k p - 2 rint(2^(k-1) p)), then the SFU sine/cosine of pi r (abs. error ~4e-7).
 __device__ __forceinline__ void sincospi_anchor(float p, int k, float* s, float* c) {
@@ -230,13 +237,14 @@ __device__ __forceinline__ void sincospi_anchor(float p, int k, float* s, float*
     *c = __cosf(a);
 }
 
-// gamma_L(p) pushed feature by feature; frequencies k = 0 and k = 5 are anchors, the
-// others follow by the double-angle recurrence (at most 4 doublings: error < 1e-5).
-template <int L, class Wr>
-__device__ __forceinline__ void encode_freq(const float p[3], Wr& w) {
-    w.push(p[0]);
-    w.push(p[1]);
-    w.push(p[2]);
+// gamma_L(p) into f[F0 .. F0 + 3 + 6L) (compile-time indices, so f stays in registers):
+// [p, sin(pi 2^k p), cos(pi 2^k p) for k < L], each a 3-vector.  Octaves 0 and 5 are
+// anchors; the others follow by the double-angle recurrence (at most 4 doublings from
+// an anchor: error < 1e-5).
+template <int L, int F0, int N>
+__device__ __forceinline__ void encode_freq(const float p[3], float (&f)[N]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[F0 + a] = p[a];
     float s[3], c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) sincospi_anchor(p[a], 0, &s[a], &c[a]);
@@ -254,13 +262,25 @@ __device__ __forceinline__ void encode_freq(const float p[3], Wr& w) {
                 s[a] = sn;
             }
         }
-        w.push(s[0]);
-        w.push(s[1]);
-        w.push(s[2]);
-        w.push(c[0]);
-        w.push(c[1]);
-        w.push(c[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            f[F0 + 3 + 6 * k + a] = s[a];
+            f[F0 + 6 + 6 * k + a] = c[a];
+        }
     }
+}
+
+// Features [32 c, 32 c + 32) of f packed two per word (even feature in the low half)
+// and written to this thread's TMEM lane at A column 16 c.
+template <int C, int N>
+__device__ __forceinline__ void store_chunk(uint32_t a_row, const float (&f)[N]) {
+    uint32_t w[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int f0 = 32 * C + 2 * i, f1 = f0 + 1;
+        w[i] = pack_bf16(f0 < N ? f[f0 < N ? f0 : 0] : 0.0f, f1 < N ? f[f1 < N ? f1 : 0] : 0.0f);
+    }
+    tmem_st16(a_row + 16u * C, w);
 }
 
 struct TcShared {
@@ -289,23 +309,26 @@ __device__ __forceinline__ void crossing_data(const MlpArgs& g, uint32_t id, flo
     }
 }
 
+// TMEM columns per warpgroup: D (accumulator, up to 64 FP32 columns) then A (up to
+// 48 columns = 96 BF16 features per lane).
+constexpr uint32_t kGroupCols = 128;
+constexpr uint32_t kACol = 64;
+
 template <int W>
 __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n_groups, uint32_t tmem_cols) {
     constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
     constexpr int K0P = round_up(K0, 16);
-    constexpr int KA = K0P > W ? K0P : W;
+    static_assert(K0P / 2 <= (int)(kGroupCols - kACol), "layer-0 input does not fit the A columns");
+    static_assert(W <= (int)kACol, "accumulator does not fit the D columns");
     extern __shared__ __align__(1024) uint8_t smem[];
     const TcLayout lay(W, g.hidden, K0);
-    const size_t a_bytes = (size_t)kTileRows * KA * 2;
-    const size_t per_group = a_bytes + lay.stride;
-    TcShared* sh = reinterpret_cast<TcShared*>(smem + per_group * n_groups);
+    TcShared* sh = reinterpret_cast<TcShared*>(smem + lay.stride * n_groups);
 
     const int grp = threadIdx.x >> 7;
-    const int tig = threadIdx.x & 127;  // row within the tile
+    const int tig = threadIdx.x & 127;  // row within the tile = TMEM lane
     const int warp = threadIdx.x >> 5;
     const int q = warp & 3;             // TMEM lane quadrant of this warp
     const int bar_id = 1 + grp;
-    const bool active_group = grp < n_groups;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < n_groups; ++i) {
@@ -326,15 +349,16 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
     tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
 
-    if (active_group) {
-        uint8_t* a_tile = smem + per_group * grp;
-        uint8_t* wbuf = a_tile + a_bytes;
-        const uint32_t a_addr = smem_u32(a_tile);
+    if (grp < n_groups) {
+        uint8_t* wbuf = smem + lay.stride * grp;
         const uint32_t w_addr = smem_u32(wbuf);
         const uint32_t bar_w = smem_u32(&sh->bar_w[grp]);
         const uint32_t bar_m = smem_u32(&sh->bar_m[grp]);
-        const uint32_t d_col = tmem + (uint32_t)(grp * 64);              // lane 0, this group's columns
-        const uint32_t d_row = d_col + ((uint32_t)(32 * q) << 16);        // this warp's lanes
+        const uint32_t lane = (uint32_t)(32 * q) << 16;
+        const uint32_t d_col = tmem + kGroupCols * (uint32_t)grp;  // lane 0: MMA operand addresses
+        const uint32_t a_col = d_col + kACol;
+        const uint32_t d_row = d_col + lane;                          // this warp's lanes
+        const uint32_t a_row = a_col + lane;
         const float* bias = reinterpret_cast<const float*>(wbuf + lay.bias);
         const uint8_t* wall = reinterpret_cast<const uint8_t*>(g.weights);
 
@@ -371,7 +395,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 if (!ok) break;
                 cur = leaf;
             }
-            // ---- rebuild the sample of this row and encode it into A (layer-0 input)
+            // ---- rebuild the sample of this row and encode it into its TMEM lane (layer-0 A)
             uint32_t slot = 0xffffffffu;
             float x[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f};
             if (id != 0xffffffffu) {
@@ -387,14 +411,16 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 slot = ray * (uint32_t)g.cap + k * (uint32_t)g.steps + (uint32_t)j;
             }
             {
-                RowWriter<K0P> wr;
-                wr.row_base = a_addr + (uint32_t)((tig >> 3) * (K0P * 16) + (tig & 7) * 16);
-                encode_freq<kLX>(x, wr);
-                encode_freq<kLD>(d, wr);
-#pragma unroll
-                for (int i = K0; i < K0P; ++i) wr.push(0.0f);
+                constexpr int NX = 3 + 6 * kLX;
+                float f[K0];
+                encode_freq<kLX, 0>(x, f);
+                encode_freq<kLD, NX>(d, f);
+                static_assert(K0P % 32 == 0, "layer-0 input is stored in 32-feature chunks");
+                store_chunk<0>(a_row, f);
+                store_chunk<1>(a_row, f);
+                store_chunk<2>(a_row, f);
             }
-            fence_proxy_async();
+            tmem_st_wait();
             tc_fence_before();
             wg_bar(bar_id);
 
@@ -418,8 +444,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     const uint32_t sbo = (uint32_t)kin * 16u;
                     const uint32_t idd = idesc_bf16(n);
                     for (int kk = 0; kk < kin / 16; ++kk)
-                        mma_bf16(d_col, sdesc(a_addr + 256u * kk, sbo), sdesc(b_base + 256u * kk, sbo), idd,
-                                 kk > 0 ? 1u : 0u);
+                        mma_bf16_ts(d_col, a_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd, kk > 0 ? 1u : 0u);
                     mma_commit(bar_m);
                 }
                 ok = group_wait(bar_m, ph_m, bar_id, flag, tig);
@@ -429,24 +454,22 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 if (l == 0) crossing_data(g, id_n, xi, ro, rd);  // next tile's interval and ray
                 if (!head) {
                     const float* b = bias + (size_t)l * W;
-                    const uint32_t row_base = a_addr + (uint32_t)((tig >> 3) * (W * 16) + (tig & 7) * 16);
 #pragma unroll
                     for (int h = 0; h < W / 32; ++h) {
                         float v[32];
+                        uint32_t pk[16];
                         tmem_ld32(d_row + 32u * h, v);
 #pragma unroll
-                        for (int cidx = 0; cidx < 4; ++cidx) {
-                            const int c0 = 32 * h + 8 * cidx;
-                            const float4 b0 = *reinterpret_cast<const float4*>(b + c0);
-                            const float4 b1 = *reinterpret_cast<const float4*>(b + c0 + 4);
-                            const float* u = v + 8 * cidx;
-                            st_shared_v4(row_base + (uint32_t)(c0 / 8) * 128u, pack_relu_bf16(u[0] + b0.x, u[1] + b0.y),
-                                         pack_relu_bf16(u[2] + b0.z, u[3] + b0.w),
-                                         pack_relu_bf16(u[4] + b1.x, u[5] + b1.y),
-                                         pack_relu_bf16(u[6] + b1.z, u[7] + b1.w));
+                        for (int c = 0; c < 8; ++c) {
+                            const float4 bb = *reinterpret_cast<const float4*>(b + 32 * h + 4 * c);
+                            const float2 s0 = add_f32x2(make_float2(v[4 * c + 0], v[4 * c + 1]), make_float2(bb.x, bb.y));
+                            const float2 s1 = add_f32x2(make_float2(v[4 * c + 2], v[4 * c + 3]), make_float2(bb.z, bb.w));
+                            pk[2 * c + 0] = pack_relu_bf16(s0.x, s0.y);
+                            pk[2 * c + 1] = pack_relu_bf16(s1.x, s1.y);
                         }
+                        tmem_st16(a_row + 16u * h, pk);
                     }
-                    fence_proxy_async();
+                    tmem_st_wait();
                     tc_fence_before();
                     wg_bar(bar_id);
                     kin = W;
@@ -480,20 +503,19 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
 template <int W>
 cudaError_t launch_w(cudaStream_t s, const MlpArgs& a, int grid) {
     constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
-    constexpr int K0P = round_up(K0, 16);
-    constexpr int KA = K0P > W ? K0P : W;
     const TcLayout lay(W, a.hidden, K0);
-    const size_t per_group = (size_t)kTileRows * KA * 2 + lay.stride;
     int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t reserve = sizeof(TcShared) + 64;
-    int groups = (int)((max_smem - reserve) / per_group);
+    int groups = (int)((max_smem - reserve) / lay.stride);
     if (groups > kMaxGroups) groups = kMaxGroups;
     if (groups < 1) return cudaErrorInvalidConfiguration;
-    uint32_t cols = 32;
-    while (cols < (uint32_t)(64 * groups)) cols <<= 1;
-    const size_t smem = per_group * groups + reserve;
+    const uint32_t cols = 512;  // kGroupCols per group: the whole TMEM, so one CTA per SM
+    // at least half of the SM's shared memory, so that a second CTA can never become
+    // resident on the SM and wait in tcgen05.alloc for columns this CTA holds
+    size_t smem = lay.stride * groups + reserve;
+    if (smem < (size_t)max_smem / 2 + 1024) smem = (size_t)max_smem / 2 + 1024;
     cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_mlp_tc<W><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
