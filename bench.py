@@ -372,7 +372,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2")
-    ap.add_argument("--prec", default="fp32,bf16")
+    ap.add_argument("--prec", default="fp32,bf16,fp8")
     ap.add_argument("--psnr-rays", type=int, default=32768)
     ap.add_argument("--ref-rays", type=int, default=16384)
     ap.add_argument("--views", type=int, default=None, help="views per GPU (default: the config's)")

@@ -15,16 +15,19 @@
 //                                      bulk-copied (TMA engine) once per leaf change
 //   D (128 x N, FP32)               -- accumulator in TMEM
 //
-// The tensor core streams shared-memory operands at about 128 B per cycle, so a
-// 128 x 64 x 16 MMA with both operands in shared memory (6 KB) is bound near 48
-// cycles; with A in TMEM only the 2 KB weight slice is read and the MMA runs near
-// its 32-cycle compute time.  Thread r of a warpgroup owns sample row r: it rebuilds
+// Measured on GB300, an SM retires one 128 x 64 x 16 MMA about every 50 cycles
+// whichever warp issues it, so these small layers are bound by MMA instruction
+// count and by the latency of the per-layer chain; keeping A in TMEM removes the
+// shared-memory activation stores and proxy fences from that chain.
+//
+// Thread r of a warpgroup owns sample row r: it rebuilds
 // the sample, encodes gamma(x) ++ gamma(d) and writes it into its TMEM lane
 // (tcgen05.st 32x32b); after each MMA it reads its row of D (tcgen05.ld 32x32b:
 // warp q of the group owns lanes 32q..32q+31), adds the bias (packed f32x2 adds),
 // applies ReLU while converting to BF16 (cvt.rn.relu.bf16x2) and writes the next
-// layer's A back into TMEM.  The head is a 128 x 16 x width MMA whose first 4
-// columns are (z_sigma, z_r, z_g, z_b); sigma = softplus, rgb = sigmoid in FP32.
+// layer's A back into TMEM.  The 4-wide head is too narrow for an MMA: the last
+// hidden epilogue computes z = Wo relu(h) + bo in FP32 from the activations it holds
+// in registers (FP32 head weights), then sigma = softplus, rgb = sigmoid.
 //
 // Several warpgroups per CTA work on different tiles, so one group's epilogue
 // overlaps another's MMA.  Each group issues its own MMAs from one thread and
@@ -38,6 +41,7 @@
 // after 4 doublings, far under the BF16 rounding of a feature (2^-9 relative).
 #include <cuda_bf16.h>
 
+#include <cmath>
 #include <cstring>
 
 #include "amnerf_internal.h"
@@ -52,15 +56,20 @@ constexpr unsigned long long kWaitCycles = 4000000000ull;  // ~2 s at 2 GHz
 
 __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// ---- per-leaf BF16 blob layout (bytes) ---------------------------------------------
+// ---- per-leaf weight blob layout (bytes) -------------------------------------------
+// W0 [width x k0p], W1.. [width x width] in the operand type (BF16, or E4M3 with FP32
+// per-output-channel scales sw [hidden][width]); head Wo FP32 [width][4]; FP32 biases
+// b_0..b_{hidden-1} [width] and bo [4].
 struct TcLayout {
-    int width, hidden, k0, k0p;
-    size_t w0, wh, wo, bias, stride;  // offsets of W0, W1.., Wo, biases; total stride
-    __host__ __device__ TcLayout(int w, int h, int k) : width(w), hidden(h), k0(k), k0p(round_up(k, 16)) {
+    int width, hidden, k0, k0p, es;
+    size_t w0, wh, wo, sw, bias, stride;
+    __host__ __device__ TcLayout(int w, int h, int k, bool f8)
+        : width(w), hidden(h), k0(k), k0p(round_up(k, f8 ? 32 : 16)), es(f8 ? 1 : 2) {
         w0 = 0;
-        wh = w0 + (size_t)w * k0p * 2;
-        wo = wh + (size_t)(h - 1) * w * w * 2;
-        bias = wo + (size_t)16 * w * 2;
+        wh = w0 + (size_t)w * k0p * es;
+        wo = wh + (size_t)(h - 1) * w * w * es;  // head: FP32, [width][4] (output-fastest)
+        sw = wo + (size_t)w * 4 * 4;
+        bias = sw + (f8 ? (size_t)h * w * 4 : 0);
         const size_t end = bias + (size_t)h * w * 4 + 16;
         stride = (end + 127) / 128 * 128;
     }
@@ -69,6 +78,32 @@ struct TcLayout {
 // Core-matrix byte offset of element (row n, column k) of an N x K K-major operand.
 __host__ __device__ inline size_t cm_offset(int n, int k, int K) {
     return (size_t)(n >> 3) * (K * 16) + (size_t)(k >> 3) * 128 + (size_t)(n & 7) * 16 + (size_t)(k & 7) * 2;
+}
+
+// E4M3 (K-major, 8-bit): a core matrix is 8 rows x 16 elements.
+__host__ __device__ inline size_t cm_offset8(int n, int k, int K) {
+    return (size_t)(n >> 3) * (K * 8) + (size_t)(k >> 4) * 128 + (size_t)(n & 7) * 16 + (size_t)(k & 15);
+}
+
+// FP32 -> E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; no infinities),
+// round to nearest even, saturating at +-448.  Inputs are finite.
+uint8_t f2e4m3(float x) {
+    const uint8_t sign = std::signbit(x) ? 0x80 : 0x00;
+    const float a = std::fabs(x);
+    if (a == 0.0f) return sign;
+    if (a >= 448.0f) return sign | 0x7e;
+    int e = 0;
+    std::frexp(a, &e);
+    int E = e - 1;                                   // 2^E <= a < 2^(E+1)
+    if (E < -6) E = -6;                              // subnormal spacing 2^-9
+    float r = std::nearbyint(a / std::ldexp(1.0f, E - 3));
+    if (r >= 16.0f) {                                // rounded up into the next binade
+        E += 1;
+        r = 8.0f;
+    }
+    if (E > 8 || (E == 8 && r > 14.0f)) return sign | 0x7e;
+    if (r < 8.0f) return sign | (uint8_t)r;          // subnormal (E == -6)
+    return sign | (uint8_t)(((E + 7) << 3) | ((int)r - 8));
 }
 
 uint16_t f2bf(float f) {  // round to nearest even (inputs are finite)
@@ -138,6 +173,20 @@ __device__ __forceinline__ uint32_t idesc_bf16(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3, both K-major, M = 128.
+__device__ __forceinline__ uint32_t idesc_e4m3(int n) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(
+            d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 // A operand in TMEM (column address a_tmem), B from a shared-memory descriptor.
 __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
                                             uint32_t acc) {
@@ -157,6 +206,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* w) {
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* w) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(w[0]),
+                 "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // (a0 + b0, a1 + b1) with one packed FP32 instruction.
@@ -165,6 +220,30 @@ __device__ __forceinline__ float2 add_f32x2(float2 a, float2 b) {
     memcpy(&ua, &a, 8);
     memcpy(&ub, &b, 8);
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(ud) : "l"(ua), "l"(ub));
+    float2 d;
+    memcpy(&d, &ud, 8);
+    return d;
+}
+
+// (a0 * b0, a1 * b1) with one packed FP32 instruction.
+__device__ __forceinline__ float2 mul_f32x2(float2 a, float2 b) {
+    unsigned long long ua, ub, ud;
+    memcpy(&ua, &a, 8);
+    memcpy(&ub, &b, 8);
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(ud) : "l"(ua), "l"(ub));
+    float2 d;
+    memcpy(&d, &ud, 8);
+    return d;
+}
+
+// (a * b0 + c0, a * b1 + c1) with one packed FP32 instruction.
+__device__ __forceinline__ float2 fma_f32x2(float a, float2 b, float2 c) {
+    const float2 aa = make_float2(a, a);
+    unsigned long long ua, ub, uc, ud;
+    memcpy(&ua, &aa, 8);
+    memcpy(&ub, &b, 8);
+    memcpy(&uc, &c, 8);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(ud) : "l"(ua), "l"(ub), "l"(uc));
     float2 d;
     memcpy(&d, &ud, 8);
     return d;
@@ -191,18 +270,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
-    uint32_t r[4];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
     uint32_t d;
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
@@ -215,8 +282,18 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return d;
 }
 
-__device__ __forceinline__ float softplus_f(float z) { return z > 20.0f ? z : log1pf(expf(z)); }
-__device__ __forceinline__ float sigmoid_f(float z) { return 1.0f / (1.0f + expf(-z)); }
+// Four values to E4M3 (round to nearest even, saturating), first value in the low byte.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+// Head activations with the SFU exp/log (relative error ~1e-6, far below the BF16/E4M3
+// operand rounding of this path).
+__device__ __forceinline__ float softplus_f(float z) { return z > 20.0f ? z : __logf(1.0f + __expf(z)); }
+__device__ __forceinline__ float sigmoid_f(float z) { return __frcp_rn(1.0f + __expf(-z)); }
 
 __device__ __forceinline__ int leaf_of_tile(const uint32_t* __restrict__ tile_off, int n_leaves, uint32_t t) {
     int lo = 0, hi = n_leaves;
@@ -314,14 +391,21 @@ __device__ __forceinline__ void crossing_data(const MlpArgs& g, uint32_t id, flo
 constexpr uint32_t kGroupCols = 128;
 constexpr uint32_t kACol = 64;
 
-template <int W>
+// F8 = false: BF16 operands (kind::f16, K = 16 per MMA, 2 features per TMEM column).
+// F8 = true:  E4M3 operands (kind::f8f6f4, K = 32 per MMA, 4 features per column) with
+//             per-output-channel weight scales and a per-row activation scale: each
+//             row is quantized as q = h * 448 / max|h_row| and the next accumulator is
+//             rescaled by (max|h_row| / 448) * sw[n] before its bias is added.
+template <int W, bool F8>
 __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n_groups, uint32_t tmem_cols) {
     constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
-    constexpr int K0P = round_up(K0, 16);
-    static_assert(K0P / 2 <= (int)(kGroupCols - kACol), "layer-0 input does not fit the A columns");
+    constexpr int KI = F8 ? 32 : 16;        // K per MMA instruction
+    constexpr int EPW = F8 ? 4 : 2;         // elements per 32-bit TMEM column
+    constexpr int K0P = round_up(K0, KI);
+    static_assert(K0P / EPW <= (int)(kGroupCols - kACol), "layer-0 input does not fit the A columns");
     static_assert(W <= (int)kACol, "accumulator does not fit the D columns");
     extern __shared__ __align__(1024) uint8_t smem[];
-    const TcLayout lay(W, g.hidden, K0);
+    const TcLayout lay(W, g.hidden, K0, F8);
     TcShared* sh = reinterpret_cast<TcShared*>(smem + lay.stride * n_groups);
 
     const int grp = threadIdx.x >> 7;
@@ -410,79 +494,170 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 }
                 slot = ray * (uint32_t)g.cap + k * (uint32_t)g.steps + (uint32_t)j;
             }
+            float s_a = 1.0f;  // FP8 only: this row's activation scale for the next MMA
             {
                 constexpr int NX = 3 + 6 * kLX;
                 float f[K0];
                 encode_freq<kLX, 0>(x, f);
                 encode_freq<kLD, NX>(d, f);
-                static_assert(K0P % 32 == 0, "layer-0 input is stored in 32-feature chunks");
-                store_chunk<0>(a_row, f);
-                store_chunk<1>(a_row, f);
-                store_chunk<2>(a_row, f);
+                if constexpr (!F8) {
+                    static_assert(K0P % 32 == 0, "layer-0 input is stored in 32-feature chunks");
+                    store_chunk<0>(a_row, f);
+                    store_chunk<1>(a_row, f);
+                    store_chunk<2>(a_row, f);
+                } else {
+                    static_assert(K0P == 96, "E4M3 layer-0 input is stored as 16 + 8 columns");
+                    float m = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < K0; ++i) m = fmaxf(m, fabsf(f[i]));
+                    const float inv = m > 0.0f ? 448.0f / m : 0.0f;
+                    s_a = m > 0.0f ? m / 448.0f : 0.0f;
+                    uint32_t w[24];
+#pragma unroll
+                    for (int i = 0; i < 24; ++i) {
+                        float e[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) e[u] = (4 * i + u < K0) ? f[(4 * i + u < K0) ? 4 * i + u : 0] * inv : 0.0f;
+                        w[i] = pack_e4m3x4(e[0], e[1], e[2], e[3]);
+                    }
+                    tmem_st16(a_row, w);
+                    tmem_st8(a_row + 16u, w + 16);
+                }
             }
             tmem_st_wait();
             tc_fence_before();
             wg_bar(bar_id);
 
-            // ---- next tile: leaf (walked forward) and crossing id, loads in flight
             int leaf_n = leaf;
             uint32_t id_n = 0xffffffffu;
-            if (t + 1 < t1) {
-                while (__ldg(g.tile_off + leaf_n + 1) <= t + 1) ++leaf_n;
-                id_n = row_crossing(g, leaf_n, t + 1, ci);
-            }
 
-            // ---- hidden layers and head
+            // ---- hidden layers; the head runs on the CUDA cores in the last epilogue
             int kin = K0P;
-            for (int l = 0; l <= g.hidden && ok; ++l) {
-                const bool head = l == g.hidden;
-                const int n = head ? 16 : W;
+            for (int l = 0; l < g.hidden && ok; ++l) {
                 if (tig == 0) {
                     tc_fence_after();
                     const uint32_t b_base =
-                        w_addr + (uint32_t)(head ? lay.wo : (l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * W * W * 2));
-                    const uint32_t sbo = (uint32_t)kin * 16u;
-                    const uint32_t idd = idesc_bf16(n);
-                    for (int kk = 0; kk < kin / 16; ++kk)
-                        mma_bf16_ts(d_col, a_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd, kk > 0 ? 1u : 0u);
+                        w_addr + (uint32_t)(l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * W * W * lay.es);
+                    const uint32_t sbo = (uint32_t)kin * (F8 ? 8u : 16u);  // 8-row group stride in bytes
+                    if constexpr (F8) {
+                        const uint32_t idd = idesc_e4m3(W);
+                        for (int kk = 0; kk < kin / KI; ++kk)
+                            mma_e4m3_ts(d_col, a_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd, kk > 0 ? 1u : 0u);
+                    } else {
+                        const uint32_t idd = idesc_bf16(W);
+                        for (int kk = 0; kk < kin / KI; ++kk)
+                            mma_bf16_ts(d_col, a_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd, kk > 0 ? 1u : 0u);
+                    }
                     mma_commit(bar_m);
+                }
+                if (l == 0 && t + 1 < t1) {
+                    // next tile's leaf (walked forward) and crossing id; issued while the
+                    // first MMA of this tile runs
+                    while (__ldg(g.tile_off + leaf_n + 1) <= t + 1) ++leaf_n;
+                    id_n = row_crossing(g, leaf_n, t + 1, ci);
                 }
                 ok = group_wait(bar_m, ph_m, bar_id, flag, tig);
                 ph_m ^= 1u;
                 if (!ok) break;
                 tc_fence_after();
-                if (l == 0) crossing_data(g, id_n, xi, ro, rd);  // next tile's interval and ray
-                if (!head) {
-                    const float* b = bias + (size_t)l * W;
+                // next tile's interval and ray, one layer after its id was requested
+                if (l == (g.hidden > 1 ? 1 : 0)) crossing_data(g, id_n, xi, ro, rd);
+                const float* b = bias + (size_t)l * W;
+                const float* sw = reinterpret_cast<const float*>(wbuf + lay.sw) + (size_t)l * W;
+                const bool last = l + 1 == g.hidden;
+                // pre-activation of 4 consecutive columns c0..c0+3 of this row
+                auto pre4 = [&](const float* v, int c0, float2& p01, float2& p23) {
+                    const float4 bb = *reinterpret_cast<const float4*>(b + c0);
+                    if constexpr (F8) {
+                        const float4 ss = *reinterpret_cast<const float4*>(sw + c0);
+                        p01 = fma_f32x2(s_a, mul_f32x2(make_float2(v[0], v[1]), make_float2(ss.x, ss.y)),
+                                        make_float2(bb.x, bb.y));
+                        p23 = fma_f32x2(s_a, mul_f32x2(make_float2(v[2], v[3]), make_float2(ss.z, ss.w)),
+                                        make_float2(bb.z, bb.w));
+                    } else {
+                        p01 = add_f32x2(make_float2(v[0], v[1]), make_float2(bb.x, bb.y));
+                        p23 = add_f32x2(make_float2(v[2], v[3]), make_float2(bb.z, bb.w));
+                    }
+                };
+                if (!last) {
+                    if constexpr (!F8) {
 #pragma unroll
-                    for (int h = 0; h < W / 32; ++h) {
-                        float v[32];
-                        uint32_t pk[16];
-                        tmem_ld32(d_row + 32u * h, v);
+                        for (int h = 0; h < W / 32; ++h) {
+                            float v[32];
+                            uint32_t pk[16];
+                            tmem_ld32(d_row + 32u * h, v);
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            const float4 bb = *reinterpret_cast<const float4*>(b + 32 * h + 4 * c);
-                            const float2 s0 = add_f32x2(make_float2(v[4 * c + 0], v[4 * c + 1]), make_float2(bb.x, bb.y));
-                            const float2 s1 = add_f32x2(make_float2(v[4 * c + 2], v[4 * c + 3]), make_float2(bb.z, bb.w));
-                            pk[2 * c + 0] = pack_relu_bf16(s0.x, s0.y);
-                            pk[2 * c + 1] = pack_relu_bf16(s1.x, s1.y);
+                            for (int c = 0; c < 8; ++c) {
+                                float2 p01, p23;
+                                pre4(v + 4 * c, 32 * h + 4 * c, p01, p23);
+                                pk[2 * c + 0] = pack_relu_bf16(p01.x, p01.y);
+                                pk[2 * c + 1] = pack_relu_bf16(p23.x, p23.y);
+                            }
+                            tmem_st16(a_row + 16u * h, pk);
                         }
-                        tmem_st16(a_row + 16u * h, pk);
+                    } else {
+                        float hv[W];
+#pragma unroll
+                        for (int h = 0; h < W / 32; ++h) {
+                            float v[32];
+                            tmem_ld32(d_row + 32u * h, v);
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                float2 p01, p23;
+                                pre4(v + 4 * c, 32 * h + 4 * c, p01, p23);
+                                hv[32 * h + 4 * c + 0] = fmaxf(p01.x, 0.f);
+                                hv[32 * h + 4 * c + 1] = fmaxf(p01.y, 0.f);
+                                hv[32 * h + 4 * c + 2] = fmaxf(p23.x, 0.f);
+                                hv[32 * h + 4 * c + 3] = fmaxf(p23.y, 0.f);
+                            }
+                        }
+                        float m = 0.0f;
+#pragma unroll
+                        for (int n = 0; n < W; ++n) m = fmaxf(m, hv[n]);
+                        const float inv = m > 0.0f ? 448.0f / m : 0.0f;
+                        s_a = m > 0.0f ? m / 448.0f : 0.0f;
+                        uint32_t pk[W / 4];
+#pragma unroll
+                        for (int i = 0; i < W / 4; ++i)
+                            pk[i] = pack_e4m3x4(hv[4 * i] * inv, hv[4 * i + 1] * inv, hv[4 * i + 2] * inv,
+                                                hv[4 * i + 3] * inv);
+                        if constexpr (W / 4 == 16) tmem_st16(a_row, pk);
+                        else tmem_st8(a_row, pk);
                     }
                     tmem_st_wait();
                     tc_fence_before();
                     wg_bar(bar_id);
                     kin = W;
                 } else {
-                    float z[4];
-                    tmem_ld4(d_row, z);
+                    // head: z = Wo relu(pre) + bo in FP32 (Wo stored [width][4])
+                    const float4* wo = reinterpret_cast<const float4*>(wbuf + lay.wo);
                     const float* bo = bias + (size_t)g.hidden * W;
+                    float2 z01 = make_float2(bo[0], bo[1]);
+                    float2 z23 = make_float2(bo[2], bo[3]);
+#pragma unroll
+                    for (int h = 0; h < W / 32; ++h) {
+                        float v[32];
+                        tmem_ld32(d_row + 32u * h, v);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            float2 p01, p23;
+                            pre4(v + 4 * c, 32 * h + 4 * c, p01, p23);
+                            const float hq[4] = {fmaxf(p01.x, 0.f), fmaxf(p01.y, 0.f), fmaxf(p23.x, 0.f),
+                                                 fmaxf(p23.y, 0.f)};
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const float4 w4 = wo[32 * h + 4 * c + i];
+                                z01 = fma_f32x2(hq[i], make_float2(w4.x, w4.y), z01);
+                                z23 = fma_f32x2(hq[i], make_float2(w4.z, w4.w), z23);
+                            }
+                        }
+                    }
                     if (slot != 0xffffffffu) {
                         float4 o;
-                        o.x = softplus_f(z[0] + bo[0]);
-                        o.y = sigmoid_f(z[1] + bo[1]);
-                        o.z = sigmoid_f(z[2] + bo[2]);
-                        o.w = sigmoid_f(z[3] + bo[3]);
+                        o.x = softplus_f(z01.x);
+                        o.y = sigmoid_f(z01.y);
+                        o.z = sigmoid_f(z23.x);
+                        o.w = sigmoid_f(z23.y);
                         g.slot_out[slot] = o;
                     }
                     tc_fence_before();
@@ -500,10 +675,10 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
-template <int W>
+template <int W, bool F8>
 cudaError_t launch_w(cudaStream_t s, const MlpArgs& a, int grid) {
     constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
-    const TcLayout lay(W, a.hidden, K0);
+    const TcLayout lay(W, a.hidden, K0, F8);
     int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -516,53 +691,63 @@ cudaError_t launch_w(cudaStream_t s, const MlpArgs& a, int grid) {
     // resident on the SM and wait in tcgen05.alloc for columns this CTA holds
     size_t smem = lay.stride * groups + reserve;
     if (smem < (size_t)max_smem / 2 + 1024) smem = (size_t)max_smem / 2 + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<W, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_mlp_tc<W><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
+    k_mlp_tc<W, F8><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t tc_leaf_stride_bytes(int width, int hidden, int k0, int prec) {
-    if (prec != 1) return 0;  // BF16 only in this build
-    if (k0 != (3 + 6 * kLX) + (3 + 6 * kLD)) return 0;
-    return TcLayout(width, hidden, k0).stride;
+    if (prec != 1 && prec != 2) return 0;
+    if (k0 != (3 + 6 * kLX) + (3 + 6 * kLD)) return 0;  // the encodings this build instantiates
+    return TcLayout(width, hidden, k0, prec == 2).stride;
 }
 
 void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0, int prec) {
-    (void)prec;
-    const TcLayout lay(width, hidden, k0);
+    const bool f8 = prec == 2;
+    const TcLayout lay(width, hidden, k0, f8);
     std::memset(dst, 0, lay.stride);
     const float* w = src;
     float* bias = reinterpret_cast<float*>(dst + lay.bias);
+    float* sw = reinterpret_cast<float*>(dst + lay.sw);
     int kin = k0;
     for (int l = 0; l < hidden; ++l) {
         const int K = l == 0 ? lay.k0p : width;
-        uint8_t* base = dst + (l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * width * width * 2);
-        for (int n = 0; n < width; ++n)
-            for (int k = 0; k < kin; ++k) {
-                const uint16_t b = f2bf(w[(size_t)n * kin + k]);
-                std::memcpy(base + cm_offset(n, k, K), &b, 2);
+        uint8_t* base = dst + (l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * width * width * lay.es);
+        for (int n = 0; n < width; ++n) {
+            const float* row = w + (size_t)n * kin;
+            if (f8) {
+                float m = 0.0f;
+                for (int k = 0; k < kin; ++k) m = std::fmax(m, std::fabs(row[k]));
+                const float s = m > 0.0f ? m / 448.0f : 1.0f;  // per-leaf, per-layer, per-output-channel
+                sw[(size_t)l * width + n] = s;
+                for (int k = 0; k < kin; ++k) base[cm_offset8(n, k, K)] = f2e4m3(row[k] / s);
+            } else {
+                for (int k = 0; k < kin; ++k) {
+                    const uint16_t b = f2bf(row[k]);
+                    std::memcpy(base + cm_offset(n, k, K), &b, 2);
+                }
             }
+        }
         w += (size_t)width * kin;
         for (int n = 0; n < width; ++n) bias[(size_t)l * width + n] = w[n];
         w += width;
         kin = width;
     }
-    for (int n = 0; n < 4; ++n)
-        for (int k = 0; k < width; ++k) {
-            const uint16_t b = f2bf(w[(size_t)n * width + k]);
-            std::memcpy(dst + lay.wo + cm_offset(n, k, width), &b, 2);
-        }
+    float* wo = reinterpret_cast<float*>(dst + lay.wo);
+    for (int k = 0; k < width; ++k)
+        for (int n = 0; n < 4; ++n) wo[(size_t)k * 4 + n] = w[(size_t)n * width + k];
     w += 4 * width;
     for (int n = 0; n < 4; ++n) bias[(size_t)hidden * width + n] = w[n];
 }
 
 cudaError_t launch_mlp_tc(cudaStream_t s, const MlpArgs& a, int grid, int prec) {
-    if (prec != 1) return cudaErrorNotSupported;
-    if (a.width == 64) return launch_w<64>(s, a, grid);
-    if (a.width == 32) return launch_w<32>(s, a, grid);
+    const bool f8 = prec == 2;
+    if (prec != 1 && prec != 2) return cudaErrorNotSupported;
+    if (a.width == 64) return f8 ? launch_w<64, true>(s, a, grid) : launch_w<64, false>(s, a, grid);
+    if (a.width == 32) return f8 ? launch_w<32, true>(s, a, grid) : launch_w<32, false>(s, a, grid);
     return cudaErrorInvalidValue;
 }
 

@@ -313,3 +313,39 @@ def test_bf16_sampling_rates(R, steps, cap):
     _check_crossings(dbg, tree, o, d, cap // steps, steps)
     ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, steps, cap, mode=0)
     assert _psnr(rgb, ref["rgb"]) >= 45.0
+
+
+# ----------------------------------------------------------------------------------
+# FP8 E4M3 tcgen05 path (per-output-channel weight scales, per-row activation
+# scales, FP32 accumulation).  E4M3 keeps 4 significant bits (relative rounding
+# 2^-4 per operand), so the bar is a stated error, not BF16's: PSNR >= 30 dB and
+# colour error below 0.1 on these scenes; the numbers are printed.
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 2])
+def test_c1_fp8_against_fp64_oracle(R, seed):
+    cfg = S.CONFIGS["c1"]
+    _, tree, P = _setup(R, cfg, seed, prec="fp8")
+    o, d = _rays(cfg, seed)
+    rgb, depth, opac, dbg, st = R.render_debug(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)
+    _check_crossings(dbg, tree, o, d, cfg.cap // cfg.steps, cfg.steps)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=0, threads=8)
+    psnr = _psnr(rgb, ref["rgb"])
+    err = np.abs(rgb - ref["rgb"]).max()
+    print(f"fp8 c1 seed {seed}: PSNR {psnr:.2f} dB, max abs rgb {err:.3e}")
+    assert np.all(np.isfinite(rgb))
+    assert psnr >= 30.0
+    assert err <= 0.1
+
+
+def test_c2_fp8_sampled_psnr(R):
+    cfg = S.CONFIGS["c2"]
+    _, tree, P = _setup(R, cfg, 0, prec="fp8")
+    o, d = _rays(cfg, 0, cfg.views)
+    rgb = R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)[0].cpu().numpy()
+    idx = S.ray_subset(len(o), 4096, 2)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o[idx], d[idx], cfg.steps, cfg.cap, mode=0,
+                   threads=16)
+    psnr = _psnr(rgb[idx], ref["rgb"])
+    print(f"fp8 c2: PSNR {psnr:.2f} dB, max abs {np.abs(rgb[idx] - ref['rgb']).max():.3e}")
+    assert np.all(np.isfinite(rgb)) and psnr >= 30.0
