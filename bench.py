@@ -328,6 +328,118 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _zipf_exponent(counts: np.ndarray) -> float:
+    """Least-squares slope of log(count) against log(rank) over the non-empty leaves."""
+    c = np.sort(np.asarray(counts, np.float64))[::-1]
+    c = c[c > 0]
+    r = np.arange(1, len(c) + 1, dtype=np.float64)
+    slope = np.polyfit(np.log(r), np.log(c), 1)[0]
+    return float(-slope)
+
+
+def run_c4(args):
+    """Imbalanced batching workload: 4096-leaf tree, 16 views of 1920x1080 (33.2 M rays)
+    rendered as ONE batch (one persistent grouped network launch), autotuned, replayed
+    from a CUDA graph, next to the per-leaf-launch baseline."""
+    import ctypes
+
+    import torch
+
+    from paper_2310_01881_gb300 import amnerf, build
+
+    torch.cuda.set_device(0)
+    build.build()
+    cfg = S.CONFIGS["c4"]
+    views = args.views or cfg.views
+    grid, o_np, d_np = workload(cfg, 0, views, None)
+    if args.px:
+        grid, o_np, d_np = workload(cfg, 0, views, args.px)
+    n = len(o_np)
+    R = amnerf.Renderer(0)
+    nl = R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    P = S.xavier_weights(0, S.leaf_mean_density(grid, R.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, "bf16")
+    o = torch.from_numpy(o_np).cuda()
+    d = torch.from_numpy(d_np).cuda()
+    out = (torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"), torch.empty(n, device="cuda"))
+    # autotune on the first view, then fix the configuration
+    nv = n // views
+    g_best, s_best, ms_best = amnerf.amnerf_autotune(R.ctx, o[:nv], d[:nv], out[0][:nv], out[1][:nv], out[2][:nv],
+                                                     steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term, reps=2)
+    _, _, _, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out)
+    # realised per-leaf crossing counts
+    counts = torch.zeros(nl, dtype=torch.int32, device="cuda")
+    dbg = amnerf.amnerf_debug(None, None, None, None, counts.data_ptr(), None, None, None)
+    p = amnerf._params(cfg.steps, cfg.cap, cfg.t_term, (0.0, 0.0, 0.0))
+    rc = amnerf.load().amnerf_render_debug(R.ctx, o.data_ptr(), d.data_ptr(), n, ctypes.byref(p), out[0].data_ptr(),
+                                          out[1].data_ptr(), out[2].data_ptr(), ctypes.byref(dbg), None)
+    assert rc == 0
+    cnt = counts.cpu().numpy().astype(np.int64)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    graph, gout = R.capture(o, d, cfg.steps, cfg.cap, cfg.t_term)
+    with ClockSampler(0) as clk:
+        ms_graph = timed(graph.replay, args.steps)
+    ms_plain = timed(lambda: R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out), args.steps)
+    amnerf.amnerf_set_timing(R.ctx, True)
+    stage = np.zeros(4)
+    for _ in range(2):
+        *_, s2 = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out)
+        stage += np.array(s2["ms"]) / 2
+    # per-leaf-launch baseline (one network launch per leaf)
+    amnerf.amnerf_set_tuning(R.ctx, g_best, amnerf.SCHED_PER_LEAF)
+    stage_pl = np.zeros(4)
+    for _ in range(2):
+        *_, s3 = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out)
+        stage_pl += np.array(s3["ms"]) / 2
+    amnerf.amnerf_set_timing(R.ctx, False)
+    ms_pl = timed(lambda: R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out), max(1, args.steps // 2))
+    amnerf.amnerf_set_tuning(R.ctx, g_best, s_best)
+    R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out)
+    rgb = out[0].cpu().numpy().astype(np.float64)
+    import oracle as O
+    tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    P_or = S.xavier_weights(0, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    idx = S.ray_subset(n, args.psnr_rays // 4, 9)
+    ref = O.render(tree, P_or, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps, cfg.cap,
+                   cfg.t_term, mode=0, threads=os.cpu_count() or 1)
+    mse = float(np.mean((rgb[idx] - ref["rgb"]) ** 2))
+    samples = st["samples_generated"]
+    names = {0: "contiguous", 1: "interleaved", 2: "dynamic"}
+    line = {
+        "metric": "Msamples/s (c4 batching: one persistent grouped launch under CUDA graph vs per-leaf launches)",
+        "value": round(samples / (ms_graph * 1e-3) / 1e6, 3), "unit": "Msamples/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_graph, 3), "higher_is_better": True,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"c4: {views} views x {o_np.shape[0] // views} rays, 256^3 grid, depth<=12, "
+                               f"{nl} leaves, 4x64 MLP, cap 192", "rays_per_step": n, "samples_per_step": samples},
+        "mrays_per_s": round(n / (ms_graph * 1e-3) / 1e6, 3),
+        "graph_ms": round(ms_graph, 3), "stream_ms": round(ms_plain, 3), "per_leaf_launch_ms": round(ms_pl, 3),
+        "speedup_vs_per_leaf": round(ms_pl / ms_graph, 3),
+        "stage_ms": [round(x, 3) for x in stage], "stage_ms_per_leaf": [round(x, 3) for x in stage_pl],
+        "autotuned": {"groups": g_best, "schedule": names.get(s_best, s_best), "ms_one_view": round(ms_best, 3)},
+        "leaf_counts": {"leaves": nl, "nonempty": int((cnt > 0).sum()), "max": int(cnt.max()),
+                        "median_nonempty": float(np.median(cnt[cnt > 0])), "zipf_exponent_fit": round(_zipf_exponent(cnt), 3)},
+        "vs_fp64": {"psnr_db": round(10 * np.log10(1.0 / max(mse, 1e-30)), 2),
+                    "max_abs_rgb": float(np.abs(rgb[idx] - ref["rgb"]).max()), "rays": int(len(idx))},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    R.close()
+
+
 def run_reference(args):
     """The oracle (FP64 CPU program) on a bounded sample of the same workload."""
     world, rank, _ = _dist()
@@ -382,6 +494,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "c4":
+        run_c4(args)
     else:
         run_ours(args)
 

@@ -108,6 +108,22 @@ typedef struct {
     float bg[3];
 } amnerf_render_params;
 
+/* Schedule of the network step's tiles over the persistent workers (warpgroups). */
+typedef enum {
+    AMNERF_SCHED_CONTIGUOUS = 0,   /* each worker takes one contiguous range of tiles (default) */
+    AMNERF_SCHED_INTERLEAVED = 1,  /* worker w takes tiles w, w + workers, ... */
+    AMNERF_SCHED_DYNAMIC = 2,      /* workers take the next tile from a device counter */
+    AMNERF_SCHED_PER_LEAF = 3      /* one kernel launch per leaf (a per-node baseline; the
+                                      render then synchronises once to read tile offsets) */
+} amnerf_schedule;
+
+/* Launch configuration of the network step.  groups = tensor-core warpgroups per CTA
+ * (tiles in flight per SM), 0 = the largest that fits; ignored on the FP32 path. */
+typedef struct {
+    int groups;
+    amnerf_schedule schedule;
+} amnerf_tuning;
+
 /* Filled by a render when a non-NULL pointer is passed (this synchronises). */
 typedef struct {
     uint64_t rays;
@@ -188,7 +204,11 @@ AMNERF_API amnerf_status amnerf_load_mlps(amnerf_ctx *ctx, const amnerf_mlp_desc
  *      rgb = sum w c + T bg, depth = sum w t (not normalised), opacity = 1 - T.
  * stats: HOST, may be NULL; when given the call synchronises and fills it.
  * Asynchronous on the context stream otherwise.  Rays with NaN components are
- * memory-safe and give NaN pixels.  n_rays * maxc must be < 2^32.
+ * memory-safe and give NaN pixels.  n_rays * floor(max_samples / steps_per_leaf)
+ * must be < 2^32 (crossing ids are 32-bit; sample slots are 64-bit).  Renders
+ * contain no host synchronisation and no allocation once the scratch is large
+ * enough (so they can be captured in a CUDA graph), except with the per-leaf
+ * schedule or a non-NULL stats pointer.
  * Errors: E_NOTREE, E_NOMLP, E_INVAL, E_NOMEM (scratch growth), E_CUDA. */
 AMNERF_API amnerf_status amnerf_render(amnerf_ctx *ctx, const float *rays_o, const float *rays_d, int64_t n_rays,
                             const amnerf_render_params *params, float *rgb, float *depth, float *opacity,
@@ -234,6 +254,21 @@ AMNERF_API amnerf_status amnerf_set_timing(amnerf_ctx *ctx, int enable);
 AMNERF_API amnerf_status amnerf_group_by_leaf_static(const uint8_t *n_x, const uint16_t *leaf, int64_t n_rays,
                                                      int maxc, int n_leaves, uint32_t *counts, uint32_t *offsets,
                                                      uint32_t *order, void *cuda_stream);
+
+/* Set / read the network step's launch configuration (see amnerf_tuning).
+ * amnerf_get_tuning also reports the largest group count the loaded shape allows. */
+AMNERF_API amnerf_status amnerf_set_tuning(amnerf_ctx *ctx, const amnerf_tuning *tuning);
+AMNERF_API amnerf_status amnerf_get_tuning(amnerf_ctx *ctx, amnerf_tuning *tuning, int *max_groups);
+
+/* Autotuner: renders the caller's batch (DEVICE buffers as in amnerf_render) once
+ * per candidate configuration to warm up, then `reps` times under CUDA events, for
+ * every group count 1..max and the contiguous, interleaved and dynamic schedules
+ * (FP32 path: one candidate), keeps the fastest in the context and returns it with
+ * its time per render.  Synchronous; the outputs hold the last render.
+ * Errors: as amnerf_render, E_INVAL (reps < 1). */
+AMNERF_API amnerf_status amnerf_autotune(amnerf_ctx *ctx, const float *rays_o, const float *rays_d, int64_t n_rays,
+                                         const amnerf_render_params *params, float *rgb, float *depth,
+                                         float *opacity, int reps, amnerf_tuning *best, float *best_ms);
 
 /* Human-readable name of a status code (static string). */
 AMNERF_API const char *amnerf_status_string(amnerf_status s);

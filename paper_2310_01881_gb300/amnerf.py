@@ -49,6 +49,13 @@ class amnerf_render_params(ctypes.Structure):
                 ("bg", ctypes.c_float * 3)]
 
 
+SCHED_CONTIGUOUS, SCHED_INTERLEAVED, SCHED_DYNAMIC, SCHED_PER_LEAF = range(4)
+
+
+class amnerf_tuning(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_int), ("schedule", ctypes.c_int)]
+
+
 class amnerf_stats(ctypes.Structure):
     _fields_ = [("rays", ctypes.c_uint64), ("crossings", ctypes.c_uint64), ("samples_generated", ctypes.c_uint64),
                 ("samples_composited", ctypes.c_uint64), ("tiles", ctypes.c_uint64), ("ms", ctypes.c_float * 4)]
@@ -90,6 +97,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "amnerf_sync": ([V], S),
         "amnerf_group_by_leaf_static": ([V, V, L, I, I, V, V, V, V], S),
         "amnerf_set_timing": ([V, I], S),
+        "amnerf_set_tuning": ([V, ctypes.POINTER(amnerf_tuning)], S),
+        "amnerf_get_tuning": ([V, ctypes.POINTER(amnerf_tuning), ctypes.POINTER(I)], S),
+        "amnerf_autotune": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V, I,
+                             ctypes.POINTER(amnerf_tuning), ctypes.POINTER(ctypes.c_float)], S),
         "amnerf_status_string": ([S], ctypes.c_char_p),
         "amnerf_last_error": ([V], ctypes.c_char_p),
         "amnerf_destroy": ([V], None),
@@ -228,6 +239,31 @@ def amnerf_group_by_leaf_static(n_x, leaf, n_rays: int, maxc: int, n_leaves: int
     _check(None, st, "amnerf_group_by_leaf_static")
 
 
+def amnerf_set_tuning(ctx, groups: int = 0, schedule: int = SCHED_CONTIGUOUS) -> None:
+    t = amnerf_tuning(groups, schedule)
+    _check(ctx, load().amnerf_set_tuning(ctx, ctypes.byref(t)), "amnerf_set_tuning")
+
+
+def amnerf_get_tuning(ctx) -> tuple[int, int, int]:
+    """(groups, schedule, largest group count the loaded network shape allows)."""
+    t = amnerf_tuning()
+    mg = ctypes.c_int()
+    _check(ctx, load().amnerf_get_tuning(ctx, ctypes.byref(t), ctypes.byref(mg)), "amnerf_get_tuning")
+    return t.groups, t.schedule, mg.value
+
+
+def amnerf_autotune(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
+                    bg=(0.0, 0.0, 0.0), reps: int = 3) -> tuple[int, int, float]:
+    """Time every launch configuration on this batch; returns (groups, schedule, ms)."""
+    p = _params(steps, cap, t_term, bg)
+    best = amnerf_tuning()
+    ms = ctypes.c_float()
+    st = load().amnerf_autotune(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
+                                _ptr(opacity), reps, ctypes.byref(best), ctypes.byref(ms))
+    _check(ctx, st, "amnerf_autotune")
+    return best.groups, best.schedule, ms.value
+
+
 def amnerf_sync(ctx) -> None:
     _check(ctx, load().amnerf_sync(ctx), "amnerf_sync")
 
@@ -318,3 +354,21 @@ class Renderer:
 
     def sync(self):
         amnerf_sync(self.ctx)
+
+    def capture(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0)):
+        """Capture one render of (o, d) in a CUDA graph; returns (graph, (rgb, depth, opacity)).
+        Replaying the graph re-renders whatever o and d hold.  Renders once first so
+        that the library's scratch is allocated outside the capture."""
+        torch = self._torch
+        out = self.render(o, d, steps, cap, t_term, bg)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(o.device)
+        side.wait_stream(torch.cuda.current_stream(o.device))
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+                amnerf_set_stream(self.ctx, side.cuda_stream)
+                amnerf_render(self.ctx, o, d, *out, steps=steps, cap=cap, t_term=t_term, bg=bg)
+        torch.cuda.current_stream(o.device).wait_stream(side)
+        amnerf_set_stream(self.ctx, torch.cuda.current_stream(o.device).cuda_stream)
+        return g, out

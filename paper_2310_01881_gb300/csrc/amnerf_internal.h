@@ -42,12 +42,22 @@ cudaError_t launch_scan(cudaStream_t s, const uint32_t* counts, int n_leaves, in
 cudaError_t launch_scatter(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
                            uint32_t* cursor, uint32_t* order, int n_leaves);
 
+// Tile schedules of the network kernels (values of amnerf_tuning.schedule).
+constexpr int kSchedContiguous = 0;   // worker w takes tiles [w * per, (w + 1) * per)
+constexpr int kSchedInterleaved = 1;  // worker w takes tiles w, w + workers, ...
+constexpr int kSchedDynamic = 2;      // workers take the next tile from a device counter
+constexpr int kSchedPerLeaf = 3;      // one launch per leaf (host loop; baseline)
+
 // K-c: per-leaf networks over leaf-grouped tiles of 128 samples.
 struct MlpArgs {
     const uint32_t* order;
     const uint32_t* offsets;
     const uint32_t* tile_off;
     const uint64_t* stats;  // [1] = total tiles
+    uint32_t* tile_counter; // dynamic schedule: next free tile (zeroed before the launch)
+    uint32_t t_begin, t_end;// tile range of this launch (t_end == 0xffffffff: up to stats[1])
+    int schedule;           // kSched*
+    int groups;             // tcgen05 kernel: warpgroups per CTA (1..4)
     int n_leaves;
     const float2* xing;
     const float* ro;
@@ -61,6 +71,10 @@ struct MlpArgs {
 };
 cudaError_t launch_mlp_simt(cudaStream_t s, const MlpArgs& a, int grid);
 cudaError_t launch_mlp_tc(cudaStream_t s, const MlpArgs& a, int grid, int prec);
+// Kernel attributes (dynamic shared memory) and the largest group count the tcgen05
+// kernel supports for this shape; called at weight-load time, outside any capture.
+cudaError_t prepare_mlp_tc(int width, int hidden, int k0, int prec, int* max_groups);
+cudaError_t prepare_mlp_simt(int width, int hidden, int k0);
 size_t tc_leaf_stride_bytes(int width, int hidden, int k0, int prec);
 size_t simt_leaf_stride_floats(int width, int hidden, int k0);
 

@@ -47,6 +47,10 @@ struct amnerf_ctx {
     // host-buffer path
     size_t cap_host_rays = 0;
     float* d_hbuf = nullptr;  // o, d, rgb, depth, opacity
+    // network kernel schedule (autotuned or set by the caller)
+    int max_groups = 1;
+    amnerf_tuning tuning{0, AMNERF_SCHED_CONTIGUOUS};
+    std::vector<uint32_t> h_tile_off;  // per-leaf launches: host copy of tile offsets
     // timing
     bool timing = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -120,8 +124,8 @@ amnerf_status check_params(amnerf_ctx* ctx, const amnerf_render_params* p, int64
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(p->bg[c])) return fail(ctx, AMNERF_E_INVAL, "bg must be finite");
     if (n < 0) return fail(ctx, AMNERF_E_INVAL, "n_rays < 0");
-    if ((uint64_t)n * (uint64_t)maxc >= (1ull << 32) || (uint64_t)n * (uint64_t)p->max_samples >= (1ull << 32))
-        return fail(ctx, AMNERF_E_INVAL, "n_rays * max_samples must be < 2^32 (split the batch)");
+    if ((uint64_t)n * (uint64_t)maxc >= (1ull << 32))
+        return fail(ctx, AMNERF_E_INVAL, "n_rays * floor(max_samples / steps_per_leaf) must be < 2^32 (split the batch)");
     return AMNERF_OK;
 }
 
@@ -309,6 +313,12 @@ amnerf_status amnerf_load_mlps(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int
         for (int l = 0; l < n_leaves; ++l)
             pack_tc_leaf(weights_host + per * l, blob.data() + stride * l, m.width, m.hidden, k0, (int)m.prec);
     }
+    int max_groups = 1;
+    if (m.prec == AMNERF_FP32) {
+        CK(prepare_mlp_simt(m.width, m.hidden, k0), "network kernel setup");
+    } else {
+        CK(prepare_mlp_tc(m.width, m.hidden, k0, (int)m.prec, &max_groups), "network kernel setup");
+    }
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     dfree(ctx->d_weights);
     ctx->mlp_loaded = false;
@@ -317,6 +327,7 @@ amnerf_status amnerf_load_mlps(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int
     ctx->desc = m;
     ctx->k0 = k0;
     ctx->leaf_stride = stride;
+    ctx->max_groups = max_groups;
     ctx->mlp_loaded = true;
     return AMNERF_OK;
 }
@@ -374,9 +385,34 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         a.cap = cap;
         a.slot_out = ctx->d_slot;
         a.err = ctx->d_err;
-        cudaError_t e = ctx->desc.prec == AMNERF_FP32 ? launch_mlp_simt(s, a, ctx->sm_count)
-                                                      : launch_mlp_tc(s, a, ctx->sm_count, (int)ctx->desc.prec);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "network launch");
+        a.tile_counter = reinterpret_cast<uint32_t*>(ctx->d_stats + 6);
+        a.t_begin = 0;
+        a.t_end = 0xffffffffu;
+        const bool tc = ctx->desc.prec != AMNERF_FP32;
+        a.groups = ctx->tuning.groups > 0 ? std::min(ctx->tuning.groups, ctx->max_groups) : ctx->max_groups;
+        int sched = ctx->tuning.schedule;
+        if (!tc && sched != AMNERF_SCHED_PER_LEAF) sched = AMNERF_SCHED_CONTIGUOUS;
+        a.schedule = sched == AMNERF_SCHED_PER_LEAF ? kSchedContiguous : sched;
+        if (sched != AMNERF_SCHED_PER_LEAF) {
+            cudaError_t e = tc ? launch_mlp_tc(s, a, ctx->sm_count, (int)ctx->desc.prec) : launch_mlp_simt(s, a, ctx->sm_count);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "network launch");
+        } else {
+            // baseline: one launch per leaf, as a per-node library call would do
+            ctx->h_tile_off.resize((size_t)L + 1);
+            CK(cudaMemcpyAsync(ctx->h_tile_off.data(), ctx->d_tile_off, 4 * ((size_t)L + 1), cudaMemcpyDeviceToHost, s),
+               "tile offsets");
+            CK(cudaStreamSynchronize(s), "stream sync");
+            for (int l = 0; l < L; ++l) {
+                const uint32_t tb = ctx->h_tile_off[l], te = ctx->h_tile_off[l + 1];
+                if (te == tb) continue;
+                a.t_begin = tb;
+                a.t_end = te;
+                const uint32_t per_cta = tc ? (uint32_t)a.groups : 1u;
+                const int grid = (int)std::min<uint32_t>((uint32_t)ctx->sm_count, (te - tb + per_cta - 1) / per_cta);
+                cudaError_t e = tc ? launch_mlp_tc(s, a, grid, (int)ctx->desc.prec) : launch_mlp_simt(s, a, grid);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "network launch");
+            }
+        }
     }
     if (ctx->timing) cudaEventRecord(ctx->ev[3], s);
     CK(launch_composite(s, ctx->d_nx, ctx->d_xing, ctx->d_slot, nn, steps, maxc, cap, p->t_term, p->bg[0], p->bg[1],
@@ -478,6 +514,79 @@ amnerf_status amnerf_render_host(amnerf_ctx* ctx, const float* ro, const float* 
     }
     CK(cudaStreamSynchronize(s), "stream sync");
     return AMNERF_OK;
+}
+
+amnerf_status amnerf_set_tuning(amnerf_ctx* ctx, const amnerf_tuning* t) {
+    if (!ctx || !t) return AMNERF_E_INVAL;
+    if (t->groups < 0 || t->groups > 4 || t->schedule < AMNERF_SCHED_CONTIGUOUS || t->schedule > AMNERF_SCHED_PER_LEAF)
+        return fail(ctx, AMNERF_E_INVAL, "tuning out of range");
+    ctx->tuning = *t;
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_get_tuning(amnerf_ctx* ctx, amnerf_tuning* t, int* max_groups) {
+    if (!ctx || !t) return AMNERF_E_INVAL;
+    *t = ctx->tuning;
+    if (max_groups) *max_groups = ctx->max_groups;
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_autotune(amnerf_ctx* ctx, const float* ro, const float* rd, int64_t n,
+                              const amnerf_render_params* p, float* rgb, float* depth, float* opacity, int reps,
+                              amnerf_tuning* best_out, float* best_ms_out) {
+    if (!ctx || reps < 1) return fail(ctx, AMNERF_E_INVAL, "bad arguments");
+    if (!ctx->mlp_loaded) return fail(ctx, AMNERF_E_NOMLP, "load the networks first");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const bool tc = ctx->desc.prec != AMNERF_FP32;
+    std::vector<amnerf_tuning> cand;
+    if (tc) {
+        for (int g = 1; g <= ctx->max_groups; ++g)
+            for (int sc = AMNERF_SCHED_CONTIGUOUS; sc <= AMNERF_SCHED_DYNAMIC; ++sc)
+                cand.push_back(amnerf_tuning{g, (amnerf_schedule)sc});
+    } else {
+        cand.push_back(amnerf_tuning{0, AMNERF_SCHED_CONTIGUOUS});
+    }
+    const amnerf_tuning saved = ctx->tuning;
+    const bool saved_timing = ctx->timing;
+    ctx->timing = false;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    float best = 1e30f;
+    amnerf_tuning best_t = cand[0];
+    amnerf_status st = AMNERF_OK;
+    for (const amnerf_tuning& c : cand) {
+        ctx->tuning = c;
+        st = render_impl(ctx, ro, rd, n, p, rgb, depth, opacity, nullptr, nullptr);  // warm-up
+        if (st != AMNERF_OK) break;
+        cudaEventRecord(e0, ctx->stream);
+        for (int r = 0; r < reps && st == AMNERF_OK; ++r)
+            st = render_impl(ctx, ro, rd, n, p, rgb, depth, opacity, nullptr, nullptr);
+        cudaEventRecord(e1, ctx->stream);
+        if (st != AMNERF_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = fail(ctx, AMNERF_E_CUDA, "autotune timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)reps;
+        if (ms < best) {
+            best = ms;
+            best_t = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->timing = saved_timing;
+    if (st != AMNERF_OK) {
+        ctx->tuning = saved;
+        return st;
+    }
+    ctx->tuning = best_t;
+    if (best_out) *best_out = best_t;
+    if (best_ms_out) *best_ms_out = best;
+    return amnerf_sync(ctx);
 }
 
 amnerf_status amnerf_sync(amnerf_ctx* ctx) {

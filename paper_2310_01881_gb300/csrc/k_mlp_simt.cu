@@ -117,12 +117,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
     float* sW = sm;                                   // [wstride]
     float* sA = sW + wstride;                         // [max(k0, W)][128]
     float* sH = sA + (size_t)kMaxK0 * kTileRows;      // [W][128]
-    uint32_t* sSlot = reinterpret_cast<uint32_t*>(sH + (size_t)W * kTileRows);  // [128]
+    uint64_t* sSlot = reinterpret_cast<uint64_t*>(sH + (size_t)W * kTileRows);  // [128]
 
-    const uint32_t total = (uint32_t)g.stats[1];
-    const uint32_t per = (total + gridDim.x - 1) / gridDim.x;
-    const uint32_t t0 = blockIdx.x * per;
-    const uint32_t t1 = min(t0 + per, total);
+    // contiguous tile ranges (also each launch of the per-leaf loop)
+    const uint32_t t_end = g.t_end == 0xffffffffu ? (uint32_t)g.stats[1] : g.t_end;
+    const uint32_t span = t_end > g.t_begin ? t_end - g.t_begin : 0u;
+    const uint32_t per = (span + gridDim.x - 1) / gridDim.x;
+    const uint32_t t0 = min(g.t_begin + blockIdx.x * per, t_end);
+    const uint32_t t1 = min(t0 + per, t_end);
     const int cpt = kTileRows / g.steps;
     const float* wall = reinterpret_cast<const float*>(g.weights);
     int cur = -1;
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
             const int ci = row / g.steps;
             const int j = row - ci * g.steps;
             const uint32_t c = first + (uint32_t)ci;
-            uint32_t slot = 0xffffffffu;
+            uint64_t slot = ~0ull;  // 64-bit: rays * cap may exceed 2^32
             float x[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f};
             if (c < endc) {
                 const uint32_t id = __ldg(g.order + c);
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
                     d[a] = __ldg(g.rd + 3 * (size_t)ray + a);
                     x[a] = __fadd_rn(o, __fmul_rn(tj, d[a]));
                 }
-                slot = ray * (uint32_t)g.cap + k * (uint32_t)g.steps + (uint32_t)j;
+                slot = (uint64_t)ray * (uint64_t)g.cap + (uint64_t)(k * (uint32_t)g.steps + (uint32_t)j);
             }
             encode_simt(x, g.lx, sA, 0, row);
             encode_simt(d, g.ld, sA, 3 + 6 * g.lx, row);
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
         }
         if (threadIdx.x < kTileRows) {
             const int row = threadIdx.x;
-            const uint32_t slot = sSlot[row];
+            const uint64_t slot = sSlot[row];
             const float* bo = w + 4 * W;
             float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
 #pragma unroll 8
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
                 z2 = fmaf(h, w4.z, z2);
                 z3 = fmaf(h, w4.w, z3);
             }
-            if (slot != 0xffffffffu) {
+            if (slot != ~0ull) {
                 float4 o;
                 o.x = softplus_f(z0 + bo[0]);
                 o.y = sigmoid_f(z1 + bo[1]);
@@ -207,21 +209,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
 template <int W>
 size_t simt_smem(int hidden, int k0) {
     return sizeof(float) * (simt_stride(W, hidden, k0) + (size_t)kMaxK0 * kTileRows + (size_t)W * kTileRows) +
-           sizeof(uint32_t) * kTileRows;
+           sizeof(uint64_t) * kTileRows;
+}
+
+template <int W>
+cudaError_t prepare_w(int hidden, int k0) {
+    const size_t smem = simt_smem<W>(hidden, k0);
+    return cudaFuncSetAttribute(k_mlp_simt<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <int W>
 cudaError_t launch_w(cudaStream_t s, const MlpArgs& a, int grid) {
-    const size_t smem = simt_smem<W>(a.hidden, a.k0);
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_simt<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_mlp_simt<W><<<grid, kThreads, smem, s>>>(a);
+    k_mlp_simt<W><<<grid, kThreads, simt_smem<W>(a.hidden, a.k0), s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t simt_leaf_stride_floats(int width, int hidden, int k0) { return simt_stride(width, hidden, k0); }
+
+cudaError_t prepare_mlp_simt(int width, int hidden, int k0) {
+    if (k0 > kMaxK0) return cudaErrorInvalidValue;
+    if (width == 64) return prepare_w<64>(hidden, k0);
+    if (width == 32) return prepare_w<32>(hidden, k0);
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_mlp_simt(cudaStream_t s, const MlpArgs& a, int grid) {
     if (a.k0 > kMaxK0) return cudaErrorInvalidValue;

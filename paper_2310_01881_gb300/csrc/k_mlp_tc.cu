@@ -364,6 +364,7 @@ struct TcShared {
     uint64_t bar_w[kMaxGroups];
     uint64_t bar_m[kMaxGroups];
     int flag[kMaxGroups];
+    uint32_t next_tile[kMaxGroups];  // dynamic schedule: tile grabbed by the group's thread 0
     uint32_t tmem_base;
 };
 
@@ -446,12 +447,24 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         const float* bias = reinterpret_cast<const float*>(wbuf + lay.bias);
         const uint8_t* wall = reinterpret_cast<const uint8_t*>(g.weights);
 
-        const uint32_t total = (uint32_t)g.stats[1];
+        // ---- tile schedule of this worker (one warpgroup)
+        const uint32_t t_end = g.t_end == 0xffffffffu ? (uint32_t)g.stats[1] : g.t_end;
         const uint32_t workers = gridDim.x * (uint32_t)n_groups;
         const uint32_t wid = blockIdx.x * (uint32_t)n_groups + (uint32_t)grp;
-        const uint32_t per = (total + workers - 1) / workers;
-        const uint32_t t0 = min(wid * per, total);
-        const uint32_t t1 = min(t0 + per, total);
+        uint32_t t_stop = t_end, t_step = 1, t_first;
+        if (g.schedule == kSchedInterleaved) {
+            t_first = g.t_begin + wid;
+            t_step = workers;
+        } else if (g.schedule == kSchedDynamic) {
+            if (tig == 0) sh->next_tile[grp] = atomicAdd(g.tile_counter, 1u) + g.t_begin;
+            wg_bar(bar_id);
+            t_first = sh->next_tile[grp];
+        } else {  // contiguous (also each launch of the per-leaf loop)
+            const uint32_t span = t_end > g.t_begin ? t_end - g.t_begin : 0u;
+            const uint32_t per = (span + workers - 1) / workers;
+            t_first = min(g.t_begin + wid * per, t_end);
+            t_stop = min(t_first + per, t_end);
+        }
         volatile int* flag = &sh->flag[grp];
         const int ci = tig / g.steps;          // crossing of this row within a tile
         const int j = tig - ci * g.steps;      // sample of this row within its crossing
@@ -459,15 +472,15 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         int cur = -1;
         bool ok = true;
 
-        // software pipeline: the crossing id of tile t+1 is fetched after tile t is
-        // encoded, its interval and ray after the first MMA of tile t has been waited for
-        int leaf = t0 < t1 ? leaf_of_tile(g.tile_off, g.n_leaves, t0) : 0;
-        uint32_t id = t0 < t1 ? row_crossing(g, leaf, t0, ci) : 0xffffffffu;
+        // software pipeline: the crossing id of the next tile is fetched after the first
+        // MMA of the current tile has been waited for, its interval and ray one layer later
+        int leaf = t_first < t_stop ? leaf_of_tile(g.tile_off, g.n_leaves, t_first) : 0;
+        uint32_t id = t_first < t_stop ? row_crossing(g, leaf, t_first, ci) : 0xffffffffu;
         float2 xi = make_float2(0.f, 0.f);
         float ro[3] = {0.f, 0.f, 0.f}, rd[3] = {0.f, 0.f, 0.f};
         crossing_data(g, id, xi, ro, rd);
 
-        for (uint32_t t = t0; t < t1 && ok; ++t) {
+        for (uint32_t t = t_first; t < t_stop && ok;) {
             if (leaf != cur) {
                 wg_bar(bar_id);  // every row is done with the previous leaf's weights and biases
                 if (tig == 0) {
@@ -480,7 +493,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 cur = leaf;
             }
             // ---- rebuild the sample of this row and encode it into its TMEM lane (layer-0 A)
-            uint32_t slot = 0xffffffffu;
+            uint64_t slot = ~0ull;  // 64-bit: rays * cap may exceed 2^32
             float x[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f};
             if (id != 0xffffffffu) {
                 const uint32_t ray = id / (uint32_t)g.maxc;
@@ -492,7 +505,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     d[a] = rd[a];
                     x[a] = __fadd_rn(ro[a], __fmul_rn(tj, rd[a]));
                 }
-                slot = ray * (uint32_t)g.cap + k * (uint32_t)g.steps + (uint32_t)j;
+                slot = (uint64_t)ray * (uint64_t)g.cap + (uint64_t)(k * (uint32_t)g.steps + (uint32_t)j);
             }
             float s_a = 1.0f;  // FP8 only: this row's activation scale for the next MMA
             {
@@ -530,6 +543,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
 
             int leaf_n = leaf;
             uint32_t id_n = 0xffffffffu;
+            uint32_t t_next = t_stop;
 
             // ---- hidden layers; the head runs on the CUDA cores in the last epilogue
             int kin = K0P;
@@ -550,16 +564,24 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     }
                     mma_commit(bar_m);
                 }
-                if (l == 0 && t + 1 < t1) {
-                    // next tile's leaf (walked forward) and crossing id; issued while the
-                    // first MMA of this tile runs
-                    while (__ldg(g.tile_off + leaf_n + 1) <= t + 1) ++leaf_n;
-                    id_n = row_crossing(g, leaf_n, t + 1, ci);
-                }
+                if (l == 0 && g.schedule == kSchedDynamic && tig == 0)
+                    sh->next_tile[grp] = atomicAdd(g.tile_counter, 1u) + g.t_begin;
                 ok = group_wait(bar_m, ph_m, bar_id, flag, tig);
                 ph_m ^= 1u;
                 if (!ok) break;
                 tc_fence_after();
+                if (l == 0) {
+                    // next tile of this worker, its leaf and this row's crossing id
+                    t_next = g.schedule == kSchedDynamic ? sh->next_tile[grp] : t + t_step;
+                    if (t_next < t_stop) {
+                        if (t_next - t <= 8u) {
+                            while (__ldg(g.tile_off + leaf_n + 1) <= t_next) ++leaf_n;
+                        } else {
+                            leaf_n = leaf_of_tile(g.tile_off, g.n_leaves, t_next);
+                        }
+                        id_n = row_crossing(g, leaf_n, t_next, ci);
+                    }
+                }
                 // next tile's interval and ray, one layer after its id was requested
                 if (l == (g.hidden > 1 ? 1 : 0)) crossing_data(g, id_n, xi, ro, rd);
                 const float* b = bias + (size_t)l * W;
@@ -652,7 +674,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                             }
                         }
                     }
-                    if (slot != 0xffffffffu) {
+                    if (slot != ~0ull) {
                         float4 o;
                         o.x = softplus_f(z01.x);
                         o.y = sigmoid_f(z01.y);
@@ -665,6 +687,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             }
             leaf = leaf_n;
             id = id_n;
+            t = t_next;
         }
         if (!ok && tig == 0) atomicCAS(g.err, 0, kDevErrTimeout);
     }
@@ -676,23 +699,39 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
 }
 
 template <int W, bool F8>
+int max_groups_for(int hidden, int max_smem) {
+    constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
+    const TcLayout lay(W, hidden, K0, F8);
+    int groups = (int)((max_smem - (int)sizeof(TcShared) - 64) / (int)lay.stride);
+    return groups > kMaxGroups ? kMaxGroups : groups;
+}
+
+template <int W, bool F8>
+cudaError_t prepare_w(int hidden, int* max_groups) {
+    int dev = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    *max_groups = max_groups_for<W, F8>(hidden, max_smem);
+    if (*max_groups < 1) return cudaErrorInvalidConfiguration;
+    return cudaFuncSetAttribute(k_mlp_tc<W, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+}
+
+template <int W, bool F8>
 cudaError_t launch_w(cudaStream_t s, const MlpArgs& a, int grid) {
     constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
     const TcLayout lay(W, a.hidden, K0, F8);
     int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t reserve = sizeof(TcShared) + 64;
-    int groups = (int)((max_smem - reserve) / lay.stride);
-    if (groups > kMaxGroups) groups = kMaxGroups;
-    if (groups < 1) return cudaErrorInvalidConfiguration;
+    const int groups = a.groups;
+    if (groups < 1 || groups > max_groups_for<W, F8>(a.hidden, max_smem)) return cudaErrorInvalidConfiguration;
     const uint32_t cols = 512;  // kGroupCols per group: the whole TMEM, so one CTA per SM
     // at least half of the SM's shared memory, so that a second CTA can never become
     // resident on the SM and wait in tcgen05.alloc for columns this CTA holds
-    size_t smem = lay.stride * groups + reserve;
+    size_t smem = lay.stride * groups + sizeof(TcShared) + 64;
     if (smem < (size_t)max_smem / 2 + 1024) smem = (size_t)max_smem / 2 + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<W, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     k_mlp_tc<W, F8><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
     return cudaGetLastError();
 }
@@ -741,6 +780,14 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
         for (int n = 0; n < 4; ++n) wo[(size_t)k * 4 + n] = w[(size_t)n * width + k];
     w += 4 * width;
     for (int n = 0; n < 4; ++n) bias[(size_t)hidden * width + n] = w[n];
+}
+
+cudaError_t prepare_mlp_tc(int width, int hidden, int k0, int prec, int* max_groups) {
+    if ((prec != 1 && prec != 2) || k0 != (3 + 6 * kLX) + (3 + 6 * kLD)) return cudaErrorNotSupported;
+    const bool f8 = prec == 2;
+    if (width == 64) return f8 ? prepare_w<64, true>(hidden, max_groups) : prepare_w<64, false>(hidden, max_groups);
+    if (width == 32) return f8 ? prepare_w<32, true>(hidden, max_groups) : prepare_w<32, false>(hidden, max_groups);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_mlp_tc(cudaStream_t s, const MlpArgs& a, int grid, int prec) {

@@ -349,3 +349,90 @@ def test_c2_fp8_sampled_psnr(R):
     psnr = _psnr(rgb[idx], ref["rgb"])
     print(f"fp8 c2: PSNR {psnr:.2f} dB, max abs {np.abs(rgb[idx] - ref['rgb']).max():.3e}")
     assert np.all(np.isfinite(rgb)) and psnr >= 30.0
+
+
+# ----------------------------------------------------------------------------------
+# Launch configurations, CUDA-graph capture and 64-bit sample slots.  A sample's
+# network output does not depend on which worker computes it, so every schedule
+# must give bit-identical pixels.
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8", "fp32"])
+def test_every_schedule_gives_identical_pixels(R, prec):
+    from paper_2310_01881_gb300 import amnerf
+    cfg = S.CONFIGS["c2"]
+    _setup(R, cfg, 0, prec=prec)
+    o, d = _rays(cfg, 0, 1, 256, 256)
+    do, dd = _dev(o), _dev(d)
+    amnerf.amnerf_set_tuning(R.ctx, 0, amnerf.SCHED_CONTIGUOUS)
+    ref = [t.cpu().numpy() for t in R.render(do, dd, cfg.steps, cfg.cap)]
+    _, _, max_groups = amnerf.amnerf_get_tuning(R.ctx)
+    groups = range(1, max_groups + 1) if prec != "fp32" else [0]
+    for g in groups:
+        for sched in (amnerf.SCHED_CONTIGUOUS, amnerf.SCHED_INTERLEAVED, amnerf.SCHED_DYNAMIC, amnerf.SCHED_PER_LEAF):
+            amnerf.amnerf_set_tuning(R.ctx, g, sched)
+            got = [t.cpu().numpy() for t in R.render(do, dd, cfg.steps, cfg.cap)]
+            for a, b in zip(got, ref):
+                np.testing.assert_array_equal(a, b, err_msg=f"groups {g} schedule {sched}")
+    amnerf.amnerf_set_tuning(R.ctx, 0, amnerf.SCHED_CONTIGUOUS)
+
+
+def test_autotune_picks_a_valid_configuration(R):
+    from paper_2310_01881_gb300 import amnerf
+    cfg = S.CONFIGS["c2"]
+    _setup(R, cfg, 0, prec="bf16")
+    o, d = _rays(cfg, 0, 1, 400, 400)
+    do, dd = _dev(o), _dev(d)
+    ref = [t.cpu().numpy() for t in R.render(do, dd, cfg.steps, cfg.cap)]
+    out = (torch.empty((len(o), 3), device="cuda"), torch.empty(len(o), device="cuda"), torch.empty(len(o), device="cuda"))
+    g, sched, ms = amnerf.amnerf_autotune(R.ctx, do, dd, *out, steps=cfg.steps, cap=cfg.cap, reps=2)
+    _, _, max_groups = amnerf.amnerf_get_tuning(R.ctx)
+    assert 1 <= g <= max_groups and sched in (0, 1, 2) and ms > 0
+    assert amnerf.amnerf_get_tuning(R.ctx)[:2] == (g, sched)
+    got = [t.cpu().numpy() for t in R.render(do, dd, cfg.steps, cfg.cap)]
+    for a, b in zip(got, ref):
+        np.testing.assert_array_equal(a, b)
+    amnerf.amnerf_set_tuning(R.ctx, 0, amnerf.SCHED_CONTIGUOUS)
+
+
+def test_cuda_graph_capture_and_replay(R):
+    cfg = S.CONFIGS["c2"]
+    _setup(R, cfg, 0, prec="bf16")
+    o1, d1 = _rays(cfg, 0, 1, 320, 320)
+    o2, d2 = _rays(cfg, 1, 1, 320, 320)
+    do, dd = _dev(o1), _dev(d1)
+    g, out = R.capture(do, dd, cfg.steps, cfg.cap)
+    for o, d in ((o2, d2), (o1, d1)):
+        do.copy_(_dev(o)); dd.copy_(_dev(d))
+        g.replay()
+        torch.cuda.synchronize()
+        got = [t.cpu().numpy() for t in out]
+        ref = [t.cpu().numpy() for t in R.render(_dev(o), _dev(d), cfg.steps, cfg.cap)]
+        for a, b in zip(got, ref):
+            np.testing.assert_array_equal(a, b)
+    R.sync()
+
+
+def test_sample_slots_beyond_32_bits(R):
+    """25.6 M rays x cap 192 = 4.9 G sample slots: the last copies of a repeated ray
+    set must render exactly like the first copies."""
+    cfg = S.CONFIGS["c2"]
+    _, tree, P = _setup(R, cfg, 0, prec="bf16")
+    o, d = _rays(cfg, 0, cfg.views)
+    reps = 5
+    assert len(o) * reps * cfg.cap > 2 ** 32
+    do = _dev(o).repeat(reps, 1)
+    dd = _dev(d).repeat(reps, 1)
+    rgb, depth, opac = R.render(do, dd, cfg.steps, cfg.cap)
+    torch.cuda.synchronize()
+    n = len(o)
+    first = rgb[:n].cpu().numpy()
+    last = rgb[(reps - 1) * n:].cpu().numpy()
+    np.testing.assert_array_equal(first, last)
+    np.testing.assert_array_equal(opac[:n].cpu().numpy(), opac[(reps - 1) * n:].cpu().numpy())
+    idx = S.ray_subset(n, 512, 3)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o[idx], d[idx], cfg.steps, cfg.cap, mode=0,
+                   threads=16)
+    assert _psnr(last[idx], ref["rgb"]) >= 45.0
+    del do, dd, rgb, depth, opac
+    torch.cuda.empty_cache()
