@@ -70,7 +70,11 @@ def lib():
             _lib.or_encode.restype = None
             _lib.or_mlp_eval.argtypes = [V, I, I, I, I, V, V, L, I, V, V]
             _lib.or_render.argtypes = [V, V, V, I, V, I, I, I, I, V, V, L, I, I, D, V, I, I,
-                                       V, V, V, V, V, V, V, V, V]
+                                       V, V, V, V, V, V, V, V, V, V, V, V]
+            _lib.or_prop_predict.argtypes = [V, V, V, V, L, V]
+            _lib.or_prop_loss_grad.argtypes = [V, V, V, V, V, L, V, V]
+            _lib.or_prop_adam.argtypes = [V, V, V, V, I, I, D, D, D, D]
+            _lib.or_prop_select.argtypes = [V, L, D, I, V, V]
     return _lib
 
 
@@ -170,8 +174,11 @@ def mlp_eval(params_leaf, width: int, hidden: int, lx: int, ld: int, x, d, mode:
 
 
 def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, steps: int, cap: int,
-           t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), mode: int = 0, threads: int = 1, full: bool = False):
-    """Full render of every ray; returns a dict of float64 / int32 arrays."""
+           t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), mode: int = 0, threads: int = 1, full: bool = False,
+           mask=None, fallback=None, bins: bool = False):
+    """Full render of every ray; returns a dict of float64 / int32 arrays.
+    mask/fallback (proposal sampler): per-ray kept-bin masks and fallback flags;
+    bins: also return the compositing weight per depth bin (n, 65)."""
     params = np.ascontiguousarray(params, F32)
     o = np.ascontiguousarray(o, F32); d = np.ascontiguousarray(d, F32)
     n = len(o)
@@ -184,13 +191,67 @@ def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, 
     if full:
         so = np.zeros((n, cap, 4), F64); sw = np.zeros((n, cap), F64)
         res["slot_out"] = so; res["slot_w"] = sw
+    mk = fb = None
+    if mask is not None:
+        mk = np.ascontiguousarray(mask, np.uint64)
+        fb = np.ascontiguousarray(fallback, I32)
+    if bins:
+        res["bins"] = np.zeros((n, 65), F64)
     bgv = np.asarray(bg, F64)
     rc = lib().or_render(_p(tree.box), _p(tree.info), _p(tree.split), tree.n_nodes, _p(params), width, hidden,
                          lx, ld, _p(o), _p(d), n, steps, cap, float(t_term), _p(bgv), mode, threads,
                          _p(res["rgb"]), _p(res["depth"]), _p(res["opacity"]), _p(res["n_gen"]),
                          _p(res["n_eval"]), _p(res["ert_margin"]),
                          _p(so) if so is not None else None, _p(sw) if sw is not None else None,
-                         _p(res["t_final"]))
+                         _p(res["t_final"]), _p(mk) if mk is not None else None, _p(fb) if fb is not None else None,
+                         _p(res["bins"]) if bins else None)
     if rc != 0:
         raise RuntimeError("oracle render failed")
     return res
+
+
+# ---------------------------------------------------------------------------------
+# proposal sampler (not in the paper)
+# ---------------------------------------------------------------------------------
+
+PROP_NPARAM = 32 * 90 + 32 + 32 * 32 + 32 + 65 * 32 + 65
+
+
+def root_interval(tree: Tree, o, d, mode: int = 0):
+    """(t0, t1, hit) of every ray against the root box (node 0)."""
+    box = tree.box[0:1]
+    info = np.array([[-1, -1, -1, 0, 1, 0]], I32)
+    split = np.zeros(1, F32)
+    nx, leaf, tin, tout = traverse(make_tree(box, info, split), o, d, 1, mode=mode)
+    return tin[:, 0], tout[:, 0], nx > 0
+
+
+def prop_predict(P, o, d, t0):
+    P = np.ascontiguousarray(P, F64); o = np.ascontiguousarray(o, F32); d = np.ascontiguousarray(d, F32)
+    t0 = np.ascontiguousarray(t0, F64)
+    q = np.zeros((len(o), 65), F64)
+    lib().or_prop_predict(_p(P), _p(o), _p(d), _p(t0), len(o), _p(q))
+    return q
+
+
+def prop_loss_grad(P, o, d, t0, targets):
+    P = np.ascontiguousarray(P, F64); o = np.ascontiguousarray(o, F32); d = np.ascontiguousarray(d, F32)
+    t0 = np.ascontiguousarray(t0, F64); tg = np.ascontiguousarray(targets, F64)
+    loss = np.zeros(1, F64); g = np.zeros(PROP_NPARAM, F64)
+    lib().or_prop_loss_grad(_p(P), _p(o), _p(d), _p(t0), _p(tg), len(o), _p(loss), _p(g))
+    return float(loss[0]), g
+
+
+def prop_adam(P, g, m, v, t: int, lr: float = 1e-3, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    """In-place Adam step on float64 arrays P, m, v."""
+    for a in (P, m, v):
+        assert a.dtype == F64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, F64)
+    lib().or_prop_adam(_p(P), _p(g), _p(m), _p(v), len(P), t, lr, b1, b2, eps)
+
+
+def prop_select(q, coverage: float = 0.99, max_bins: int = 16):
+    q = np.ascontiguousarray(q, F64)
+    mask = np.zeros(len(q), np.uint64); fb = np.zeros(len(q), I32)
+    lib().or_prop_select(_p(q), len(q), coverage, max_bins, _p(mask), _p(fb))
+    return mask, fb

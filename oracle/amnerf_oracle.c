@@ -552,9 +552,81 @@ typedef struct {
     double *slot_out; /* (n, cap, 4) sigma rgb; may be NULL */
     double *slot_w;   /* (n, cap) compositing weight; may be NULL */
     double *t_final;  /* (n) final transmittance; may be NULL */
+    /* proposal: per-ray kept-bin mask and fallback flag (both NULL = plain) */
+    const uint64_t *mask; const int *fallback;
+    double *bins;     /* (n, 65) compositing weight per depth bin + residual T; may be NULL */
     /* threading */
     int64_t r0, r1; int err;
 } or_job;
+
+/* ------------------------------------------------------------------------ */
+/* Proposal sampler support (not in the paper; a learned sampler in the      */
+/* spirit of the sampling networks of the related work, Sec. 2.1).  Depth    */
+/* bins: the ray's root interval [t0, t1] cut into 64 equal bins; bin k is    */
+/* [t0 + k w, t0 + (k + 1) w) with w = (t1 - t0) / 64, evaluated in the       */
+/* mode's precision in that operation order.                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Root interval of one ray (the slab test of node 0); 0 when the ray misses. */
+static int or_root(const float *box, const float *of, const float *df, int mode, double *t0, double *t1)
+{
+    if (mode == 1) {
+        float inv[3] = {1.0f / df[0], 1.0f / df[1], 1.0f / df[2]};
+        float e, x;
+        int hit = or_slab32(box, of, inv, &e, &x);
+        *t0 = hit ? e : 0.0; *t1 = hit ? x : 0.0;
+        return hit;
+    }
+    double o64[3] = {of[0], of[1], of[2]};
+    double inv[3] = {1.0 / (double)df[0], 1.0 / (double)df[1], 1.0 / (double)df[2]};
+    double e, x;
+    int hit = or_slab64(box, o64, inv, &e, &x);
+    *t0 = hit ? e : 0.0; *t1 = hit ? x : 0.0;
+    return hit;
+}
+
+/* Bin of a sample at t (training targets; clamped to [0, 63]): floor((t - t0) / w),
+ * in the mode's precision (FP32: w = (t1 - t0) * 2^-6, then subtract, divide, floor). */
+static int or_bin_of(int mode, double t0, double t1, double t)
+{
+    int k;
+    if (mode == 1) {
+        float w = ((float)t1 - (float)t0) * 0.015625f;
+        float q = ((float)t - (float)t0) / w;
+        k = w > 0.0f ? (int)floorf(q) : 0;
+    } else {
+        double w = (t1 - t0) / 64.0;
+        k = w > 0.0 ? (int)floor((t - t0) / w) : 0;
+    }
+    return k < 0 ? 0 : (k > 63 ? 63 : k);
+}
+
+/* Does crossing [a, b] overlap bin k?  a < hi_k and b > lo_k. */
+static int or_overlaps(int mode, double t0, double t1, int k, double a, double b)
+{
+    if (mode == 1) {
+        float w = ((float)t1 - (float)t0) * 0.015625f;
+        float lo = (float)t0 + (float)k * w;
+        float hi = (float)t0 + (float)(k + 1) * w;
+        return (float)a < hi && (float)b > lo;
+    }
+    double w = (t1 - t0) / 64.0;
+    return a < t0 + (k + 1) * w && b > t0 + k * w;
+}
+
+/* Keep, in order, the crossings that overlap a bin of `mask`, at most maxc. */
+static int or_keep_masked(int mode, double t0, double t1, uint64_t mask, int *leaf, double *tin, double *tout,
+                          int n, int maxc)
+{
+    int m = 0;
+    for (int i = 0; i < n && m < maxc; i++) {
+        int keep = 0;
+        for (int k = 0; k < 64 && !keep; k++)
+            if ((mask >> k) & 1ull) keep = or_overlaps(mode, t0, t1, k, tin[i], tout[i]);
+        if (keep) { leaf[m] = leaf[i]; tin[m] = tin[i]; tout[m] = tout[i]; m++; }
+    }
+    return m;
+}
 
 /* Compositing (NeRF quadrature, Sec. 3.1): T = 1; per sample in ray order, stop once
  * T < t_term; tau = sigma * delta, e = exp(-tau), alpha = 1 - e, w = T alpha,
@@ -565,9 +637,21 @@ static void or_render_ray(const or_job *J, int64_t r)
     int leaf[256];
     double tin[256], tout[256];
     int kx = 3 + 6 * J->lx, k0 = kx + 3 + 6 * J->ld;
-    int nx = or_trav_ray(J->box, J->info, J->split, J->n_nodes, J->o + 3 * r, J->d + 3 * r,
+    int nx;
+    double root0 = 0.0, root1 = 0.0;
+    int root_hit = or_root(J->box, J->o + 3 * r, J->d + 3 * r, J->mode, &root0, &root1);
+    if (J->mask && !J->fallback[r]) {
+        nx = or_trav_ray(J->box, J->info, J->split, J->n_nodes, J->o + 3 * r, J->d + 3 * r,
+                         256, J->mode, 0, leaf, tin, tout);
+        if (nx < 0) nx = 0;
+        nx = or_keep_masked(J->mode, root0, root1, J->mask[r], leaf, tin, tout, nx, maxc);
+    } else {
+        nx = or_trav_ray(J->box, J->info, J->split, J->n_nodes, J->o + 3 * r, J->d + 3 * r,
                          maxc, J->mode, 0, leaf, tin, tout);
-    if (nx < 0) nx = 0;
+        if (nx < 0) nx = 0;
+    }
+    double *bins = J->bins ? J->bins + r * 65 : NULL;
+    if (bins) for (int b = 0; b < 65; b++) bins[b] = 0.0;
     const float *of = J->o + 3 * r, *df = J->d + 3 * r;
     int full = J->slot_out != NULL || J->slot_w != NULL;
     int nev = 0, stopped = 0;
@@ -605,8 +689,10 @@ static void or_render_ray(const or_job *J, int64_t r)
                 T = T * e;
                 nev++;
                 if (J->slot_w) J->slot_w[r * J->cap + s] = w;
+                if (bins && root_hit) bins[or_bin_of(J->mode, root0, root1, t)] += w;
             }
         }
+        if (bins) bins[64] = T;
         for (int c = 0; c < 3; c++) { float tb = T * (float)J->bg[c]; J->rgb[3 * r + c] = C[c] + tb; }
         J->depth[r] = D;
         J->opacity[r] = 1.0f - T;
@@ -639,8 +725,10 @@ static void or_render_ray(const or_job *J, int64_t r)
                 T *= e;
                 nev++;
                 if (J->slot_w) J->slot_w[r * J->cap + s] = w;
+                if (bins && root_hit) bins[or_bin_of(J->mode, root0, root1, t)] += w;
             }
         }
+        if (bins) bins[64] = T;
         for (int c = 0; c < 3; c++) J->rgb[3 * r + c] = C[c] + T * J->bg[c];
         J->depth[r] = D;
         J->opacity[r] = 1.0 - T;
@@ -663,7 +751,8 @@ int or_render(const float *box, const int *info, const float *split, int n_nodes
               const float *o, const float *d, int64_t n,
               int steps, int cap, double t_term, const double *bg, int mode, int n_threads,
               double *rgb, double *depth, double *opacity, int *n_gen, int *n_eval, double *ert_margin,
-              double *slot_out, double *slot_w, double *t_final)
+              double *slot_out, double *slot_w, double *t_final, const uint64_t *mask, const int *fallback,
+              double *bins)
 {
     if (steps < 1 || cap < steps || cap / steps > 256 || width > OR_MAXW || lx > 32 || ld > 32) return -1;
     if (n_threads < 1) n_threads = 1;
@@ -678,6 +767,7 @@ int or_render(const float *box, const int *info, const float *split, int n_nodes
     base.mode = mode;
     base.rgb = rgb; base.depth = depth; base.opacity = opacity; base.n_gen = n_gen; base.n_eval = n_eval;
     base.ert_margin = ert_margin; base.slot_out = slot_out; base.slot_w = slot_w; base.t_final = t_final;
+    base.mask = mask; base.fallback = fallback; base.bins = bins;
     if (n_threads == 1 || n < 64) {
         base.r0 = 0; base.r1 = n;
         or_render_worker(&base);
@@ -700,5 +790,162 @@ int or_render(const float *box, const int *info, const float *split, int n_nodes
     }
     for (int i = 0; i < started; i++) if (th[i]) pthread_join(th[i], NULL);
     free(jobs); free(th);
+    return 0;
+}
+
+/* ======================================================================== */
+/* Proposal network (not in the paper; see the proposal sampler section).   */
+/* Input: gamma_10(entry point o + t0 d) ++ gamma_4(d) (90); two ReLU layers */
+/* of 32; 65 logits (64 depth bins + background); softmax.                   */
+/* Parameters, FP32 flat: W1 [32 x 90], b1 [32], W2 [32 x 32], b2 [32],      */
+/* W3 [65 x 32], b3 [65] (6113 values).  Loss: mean over rays of the cross-  */
+/* entropy -sum_b p_b log q_b against the binned compositing weights p.      */
+/* ======================================================================== */
+
+#define OR_PIN 90
+#define OR_PH 32
+#define OR_PO 65
+#define OR_PNPAR (OR_PH * OR_PIN + OR_PH + OR_PH * OR_PH + OR_PH + OR_PO * OR_PH + OR_PO)
+
+static void or_prop_input(const float *of, const float *df, double t0, double *in)
+{
+    double e[3], d[3];
+    for (int a = 0; a < 3; a++) { d[a] = df[a]; e[a] = (double)of[a] + t0 * d[a]; }
+    or_encode64(e, 10, in);
+    or_encode64(d, 4, in + 63);
+}
+
+/* Forward pass of one ray; h1, h2: post-ReLU activations, q: softmax output. */
+static void or_prop_forward(const double *P, const double *in, double *h1, double *h2, double *z, double *q)
+{
+    const double *W1 = P, *b1 = W1 + OR_PH * OR_PIN, *W2 = b1 + OR_PH, *b2 = W2 + OR_PH * OR_PH;
+    const double *W3 = b2 + OR_PH, *b3 = W3 + OR_PO * OR_PH;
+    for (int o = 0; o < OR_PH; o++) {
+        double acc = 0.0;
+        for (int i = 0; i < OR_PIN; i++) acc += W1[o * OR_PIN + i] * in[i];
+        acc += b1[o];
+        h1[o] = acc > 0.0 ? acc : 0.0;
+    }
+    for (int o = 0; o < OR_PH; o++) {
+        double acc = 0.0;
+        for (int i = 0; i < OR_PH; i++) acc += W2[o * OR_PH + i] * h1[i];
+        acc += b2[o];
+        h2[o] = acc > 0.0 ? acc : 0.0;
+    }
+    double m = -INFINITY;
+    for (int o = 0; o < OR_PO; o++) {
+        double acc = 0.0;
+        for (int i = 0; i < OR_PH; i++) acc += W3[o * OR_PH + i] * h2[i];
+        z[o] = acc + b3[o];
+        if (z[o] > m) m = z[o];
+    }
+    double s = 0.0;
+    for (int o = 0; o < OR_PO; o++) { q[o] = exp(z[o] - m); s += q[o]; }
+    for (int o = 0; o < OR_PO; o++) q[o] /= s;
+}
+
+/* Softmax outputs of n rays (q: n x 65).  t0: root entry per ray. */
+int or_prop_predict(const double *P, const float *o, const float *d, const double *t0, int64_t n, double *q)
+{
+    double in[OR_PIN], h1[OR_PH], h2[OR_PH], z[OR_PO];
+    for (int64_t r = 0; r < n; r++) {
+        or_prop_input(o + 3 * r, d + 3 * r, t0[r], in);
+        or_prop_forward(P, in, h1, h2, z, q + r * OR_PO);
+    }
+    return 0;
+}
+
+/* Mean cross-entropy of n rays against targets p (n x 65) and its exact gradient
+ * (backpropagation through softmax, the two ReLU layers and the affine maps). */
+int or_prop_loss_grad(const double *P, const float *o, const float *d, const double *t0, const double *p,
+                      int64_t n, double *loss, double *grad)
+{
+    const double *W2 = P + OR_PH * OR_PIN + OR_PH, *W3 = W2 + OR_PH * OR_PH + OR_PH;
+    double *gW1 = grad, *gb1 = gW1 + OR_PH * OR_PIN, *gW2 = gb1 + OR_PH, *gb2 = gW2 + OR_PH * OR_PH;
+    double *gW3 = gb2 + OR_PH, *gb3 = gW3 + OR_PO * OR_PH;
+    double in[OR_PIN], h1[OR_PH], h2[OR_PH], z[OR_PO], q[OR_PO], dz[OR_PO], dh2[OR_PH], dh1[OR_PH];
+    for (int i = 0; i < OR_PNPAR; i++) grad[i] = 0.0;
+    double L = 0.0;
+    for (int64_t r = 0; r < n; r++) {
+        const double *pr = p + r * OR_PO;
+        or_prop_input(o + 3 * r, d + 3 * r, t0[r], in);
+        or_prop_forward(P, in, h1, h2, z, q);
+        double ps = 0.0;
+        for (int b = 0; b < OR_PO; b++) {
+            if (pr[b] > 0.0) L -= pr[b] * log(q[b]);
+            ps += pr[b];
+        }
+        /* d/dz_b of -sum_c p_c log softmax(z)_c = q_b sum_c p_c - p_b */
+        for (int b = 0; b < OR_PO; b++) dz[b] = q[b] * ps - pr[b];
+        for (int b = 0; b < OR_PO; b++) {
+            gb3[b] += dz[b] / (double)n;
+            for (int i = 0; i < OR_PH; i++) gW3[b * OR_PH + i] += dz[b] * h2[i] / (double)n;
+        }
+        for (int i = 0; i < OR_PH; i++) {
+            double acc = 0.0;
+            for (int b = 0; b < OR_PO; b++) acc += W3[b * OR_PH + i] * dz[b];
+            dh2[i] = h2[i] > 0.0 ? acc : 0.0;
+        }
+        for (int o2 = 0; o2 < OR_PH; o2++) {
+            gb2[o2] += dh2[o2] / (double)n;
+            for (int i = 0; i < OR_PH; i++) gW2[o2 * OR_PH + i] += dh2[o2] * h1[i] / (double)n;
+        }
+        for (int i = 0; i < OR_PH; i++) {
+            double acc = 0.0;
+            for (int o2 = 0; o2 < OR_PH; o2++) acc += W2[o2 * OR_PH + i] * dh2[o2];
+            dh1[i] = h1[i] > 0.0 ? acc : 0.0;
+        }
+        for (int o1 = 0; o1 < OR_PH; o1++) {
+            gb1[o1] += dh1[o1] / (double)n;
+            for (int i = 0; i < OR_PIN; i++) gW1[o1 * OR_PIN + i] += dh1[o1] * in[i] / (double)n;
+        }
+    }
+    *loss = L / (double)n;
+    return 0;
+}
+
+/* One Adam step (Kingma and Ba): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * P -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps); t counts from 1. */
+int or_prop_adam(double *P, const double *g, double *m, double *v, int n_par, int t, double lr, double b1, double b2,
+                 double eps)
+{
+    double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+    for (int i = 0; i < n_par; i++) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        P[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+    return 0;
+}
+
+/* Kept depth bins of one ray: bins are visited by decreasing predicted mass (ties
+ * to the lower index); their mass is added until it reaches `coverage`; the
+ * background bin counts toward coverage but is not a depth bin.  When more than
+ * max_bins depth bins would be needed the ray falls back to the plain sampler. */
+int or_prop_select(const double *q, int64_t n, double coverage, int max_bins, uint64_t *mask, int *fallback)
+{
+    for (int64_t r = 0; r < n; r++) {
+        const double *qr = q + r * OR_PO;
+        int used[OR_PO] = {0};
+        double cum = 0.0;
+        int kept = 0;
+        uint64_t mk = 0;
+        int fb = 0;
+        while (cum < coverage) {
+            int best = -1;
+            for (int b = 0; b < OR_PO; b++)
+                if (!used[b] && (best < 0 || qr[b] > qr[best])) best = b;
+            if (best < 0) break;
+            used[best] = 1;
+            cum += qr[best];
+            if (best < 64) {
+                if (kept == max_bins) { fb = 1; break; }
+                mk |= 1ull << best;
+                kept++;
+            }
+        }
+        mask[r] = fb ? ~0ull : mk;
+        fallback[r] = fb;
+    }
     return 0;
 }

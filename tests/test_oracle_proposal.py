@@ -1,0 +1,148 @@
+"""Pins of the proposal-sampler oracle (a learned sampler; not in the paper).
+
+Gradient: central finite differences of the loss.  Cross-entropy: the closed form
+at q = p.  Adam: the first step from zero moments moves every parameter by lr
+against the sign of its gradient.  Bin selection: hand-worked cases.  Masked
+sampling: an all-bins mask reproduces the plain render, kept crossings are exactly
+those that overlap a kept bin, and the binned weights plus the residual
+transmittance sum to one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2310_01881_gb300 import scenes as S
+
+
+def _rays(n, seed):
+    rng = np.random.default_rng(seed)
+    u = rng.normal(size=(n, 3)); u /= np.linalg.norm(u, axis=1, keepdims=True)
+    o = 3.0 * u
+    d = rng.uniform(-0.7, 0.7, (n, 3)) - o; d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return o.astype(np.float32), d.astype(np.float32)
+
+
+def _params(seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    return rng.normal(0, scale, O.PROP_NPARAM)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    cfg = S.CONFIGS["c1"]
+    grid = S.density_grid(S.scene_for("c1", 0), cfg.G)
+    tree = O.build_tree(grid, cfg.max_depth)
+    P = S.xavier_weights(0, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    return cfg, tree, P
+
+
+def test_gradient_matches_central_differences():
+    o, d = _rays(6, 1)
+    t0 = np.random.default_rng(2).uniform(1.5, 2.5, 6)
+    tg = np.random.default_rng(3).dirichlet(np.ones(65) * 0.3, 6)
+    P = _params(4)
+    loss, g = O.prop_loss_grad(P, o, d, t0, tg)
+    idx = np.random.default_rng(5).choice(O.PROP_NPARAM, 120, replace=False)
+    bad = 0
+    for i in idx:
+        h = 1e-6 * max(1.0, abs(P[i]))
+        Pp = P.copy(); Pp[i] += h
+        Pm = P.copy(); Pm[i] -= h
+        fd = (O.prop_loss_grad(Pp, o, d, t0, tg)[0] - O.prop_loss_grad(Pm, o, d, t0, tg)[0]) / (2 * h)
+        if abs(fd - g[i]) > 1e-6 + 1e-5 * abs(g[i]):
+            bad += 1
+    assert bad <= 2  # a ReLU kink inside +-h is possible but rare
+    assert loss > 0
+
+
+def test_cross_entropy_closed_form_at_matching_prediction():
+    """W3 = 0 and b3 = log p make the prediction q = p: loss = H(p), zero bias gradient."""
+    p = np.random.default_rng(7).dirichlet(np.ones(65), 1)[0]
+    P = _params(8)
+    P[-65 - 65 * 32:-65] = 0.0
+    P[-65:] = np.log(p)
+    o, d = _rays(3, 9)
+    t0 = np.full(3, 2.0)
+    loss, g = O.prop_loss_grad(P, o, d, t0, np.tile(p, (3, 1)))
+    assert loss == pytest.approx(-np.sum(p * np.log(p)), rel=1e-12)
+    np.testing.assert_allclose(g[-65:], 0.0, atol=1e-15)
+    q = O.prop_predict(P, o, d, t0)
+    np.testing.assert_allclose(q, np.tile(p, (3, 1)), rtol=1e-12)
+
+
+def test_adam_first_step_moves_by_lr_against_gradient_sign():
+    P = _params(10)
+    P0 = P.copy()
+    g = np.random.default_rng(11).normal(size=P.size)
+    m = np.zeros_like(P); v = np.zeros_like(P)
+    O.prop_adam(P, g, m, v, 1, lr=1e-3)
+    np.testing.assert_allclose(P - P0, -1e-3 * np.sign(g) * np.abs(g) / (np.abs(g) + 1e-8), rtol=1e-12)
+    np.testing.assert_allclose(m, 0.1 * g, rtol=1e-12)
+    np.testing.assert_allclose(v, 0.001 * g * g, rtol=1e-12)
+
+
+def test_bin_selection_hand_cases():
+    q = np.zeros((4, 65))
+    # ray 0: bins 3 (0.6) and 10 (0.395) reach 0.995 >= 0.99
+    q[0, 3] = 0.6; q[0, 10] = 0.395; q[0, 64] = 0.005
+    # ray 1: background 0.9 and bin 5 0.095 -> 0.995 (background counts toward coverage)
+    q[1, 64] = 0.9; q[1, 5] = 0.095; q[1, 6] = 0.005
+    # ray 2: flat over 64 bins: more than 16 depth bins needed -> fallback
+    q[2, :64] = 1.0 / 64
+    # ray 3: tie between bins 1 and 2 (0.5 each): lower index first, both needed
+    q[3, 1] = 0.5; q[3, 2] = 0.5
+    mask, fb = O.prop_select(q, 0.99, 16)
+    assert mask[0] == (1 << 3) | (1 << 10) and fb[0] == 0
+    assert mask[1] == (1 << 5) and fb[1] == 0
+    assert fb[2] == 1 and mask[2] == np.uint64(2 ** 64 - 1)
+    assert mask[3] == (1 << 1) | (1 << 2) and fb[3] == 0
+    m2, f2 = O.prop_select(q[2:3], 0.99, 64)
+    assert f2[0] == 0 and bin(int(m2[0])).count("1") == 64
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_all_bins_mask_is_the_plain_render(c1, mode):
+    cfg, tree, P = c1
+    o, d = S.view_rays(cfg, 0, 0, 20, 20)
+    plain = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=mode)
+    ones = np.full(len(o), 2 ** 64 - 1, np.uint64)
+    masked = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=mode,
+                      mask=ones, fallback=np.zeros(len(o), np.int32))
+    for k in ("rgb", "depth", "opacity", "n_gen"):
+        np.testing.assert_array_equal(masked[k], plain[k])
+
+
+def test_masked_sampling_keeps_exactly_the_overlapping_crossings(c1):
+    cfg, tree, P = c1
+    o, d = S.view_rays(cfg, 0, 0, 16, 16)
+    t0, t1, hit = O.root_interval(tree, o, d, mode=0)
+    rng = np.random.default_rng(12)
+    mask = np.zeros(len(o), np.uint64)
+    for r in range(len(o)):
+        for k in rng.choice(64, 5, replace=False):
+            mask[r] |= np.uint64(1 << int(k))
+    res = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, 512, t_term=0.0, mode=0,
+                   mask=mask, fallback=np.zeros(len(o), np.int32))
+    nx, leaf, tin, tout = O.traverse(tree, o, d, 64, mode=0)
+    for r in np.nonzero(hit)[0]:
+        w = (t1[r] - t0[r]) / 64.0
+        bins = [j for j in range(64) if (int(mask[r]) >> j) & 1]
+        sure = maybe = 0
+        for k in range(nx[r]):
+            a, b = tin[r, k], tout[r, k]
+            ov = max(min(b, t0[r] + (j + 1) * w) - max(a, t0[r] + j * w) for j in bins)
+            sure += ov > 1e-9      # overlaps a kept bin by a positive length
+            maybe += ov > -1e-9    # or touches one within rounding of the bin edges
+        assert sure * cfg.steps <= res["n_gen"][r] <= maybe * cfg.steps
+
+
+def test_binned_weights_sum_to_one(c1):
+    cfg, tree, P = c1
+    o, d = S.view_rays(cfg, 0, 0, 24, 24)
+    for mode, tol in ((0, 1e-12), (1, 2e-6)):
+        res = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=mode,
+                       bins=True)
+        np.testing.assert_allclose(res["bins"].sum(1), 1.0, atol=tol)
+        np.testing.assert_allclose(res["bins"][:, 64], 1 - res["opacity"], atol=tol)
