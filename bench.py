@@ -446,6 +446,100 @@ def run_c4(args):
     R.close()
 
 
+def run_c5(args):
+    """Learned proposal on the imbalanced scene: trained on plain-rendered views,
+    evaluated on held-out views against the plain sampler and the FP64 oracle."""
+    import torch
+
+    from paper_2310_01881_gb300 import amnerf, build
+
+    torch.cuda.set_device(0)
+    build.build()
+    cfg = S.CONFIGS["c4"]
+    grid = S.density_grid(S.scene_for(cfg.scene, 0), cfg.G)
+    R = amnerf.Renderer(0)
+    R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    P = S.xavier_weights(0, S.leaf_mean_density(grid, R.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, "bf16")
+    n_train_views, tw, th = args.train_views, 480, 270
+    tr = [S.view_rays(cfg, 0, 1000 + v, tw, th) for v in range(n_train_views)]
+    o_tr = torch.from_numpy(np.concatenate([t[0] for t in tr])).cuda()
+    d_tr = torch.from_numpy(np.concatenate([t[1] for t in tr])).cuda()
+    n_tr = o_tr.shape[0]
+    out_tr = (torch.empty((n_tr, 3), device="cuda"), torch.empty(n_tr, device="cuda"), torch.empty(n_tr, device="cuda"))
+    tg = torch.empty((n_tr, 65), device="cuda")
+    root = torch.empty((n_tr, 2), device="cuda")
+    t0 = time.perf_counter()
+    amnerf.amnerf_proposal_targets(R.ctx, o_tr, d_tr, *out_tr, tg, root, steps=cfg.steps, cap=cfg.cap,
+                                   t_term=cfg.t_term)
+    t_targets = time.perf_counter() - t0
+    amnerf.amnerf_proposal_set(R.ctx, S.proposal_init(1))
+    t0 = time.perf_counter()
+    losses = amnerf.amnerf_proposal_train(R.ctx, o_tr, d_tr, root, tg, steps=args.train_steps, batch=8192, lr=3e-3,
+                                          seed=7)
+    t_train = time.perf_counter() - t0
+    del o_tr, d_tr, out_tr, tg, root
+    torch.cuda.empty_cache()
+    views = args.views or cfg.views
+    px_w, px_h = (args.px, args.px) if args.px else (cfg.px_w, cfg.px_h)
+    te = [S.view_rays(cfg, 0, 2000 + v, px_w, px_h) for v in range(views)]
+    o_np = np.concatenate([t[0] for t in te]); d_np = np.concatenate([t[1] for t in te])
+    n = len(o_np)
+    o = torch.from_numpy(o_np).cuda(); d = torch.from_numpy(d_np).cuda()
+    out = (torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"), torch.empty(n, device="cuda"))
+    stream = torch.cuda.current_stream()
+
+    def timed(prop):
+        for _ in range(args.warmup):
+            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, proposal=prop)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, proposal=prop)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        *_, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, proposal=prop, stats=True)
+        return e0.elapsed_time(e1) / args.steps, st, out[0].cpu().numpy().astype(np.float64)
+
+    with ClockSampler(0) as clk:
+        ms_plain, st_plain, rgb_plain = timed(False)
+        ms_prop, st_prop, rgb_prop = timed(True)
+    import oracle as O
+    tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    P_or = S.xavier_weights(0, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    idx = S.ray_subset(n, args.psnr_rays // 4, 11)
+    ref = O.render(tree, P_or, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps, cfg.cap,
+                   cfg.t_term, mode=0, threads=os.cpu_count() or 1)
+
+    def psnr(a, b):
+        return round(10 * np.log10(1.0 / max(float(np.mean((a - b) ** 2)), 1e-30)), 2)
+
+    p_plain, p_prop = psnr(rgb_plain[idx], ref["rgb"]), psnr(rgb_prop[idx], ref["rgb"])
+    line = {
+        "metric": "Mrays/s and samples per ray (c5 learned proposal vs plain sampler)",
+        "value": round(n / (ms_prop * 1e-3) / 1e6, 3), "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_prop, 3), "higher_is_better": True, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": f"c4 scene (4096 leaves, 4x64 BF16 MLPs); proposal trained on {n_train_views} views "
+                               f"at {tw}x{th}, evaluated on {views} held-out views at {px_w}x{px_h}",
+                   "rays_per_step": n, "coverage": 0.99, "max_bins": 16},
+        "plain": {"Mrays/s": round(n / (ms_plain * 1e-3) / 1e6, 3), "ms": round(ms_plain, 3),
+                  "samples_per_ray": round(st_plain["samples_generated"] / n, 3), "psnr_vs_fp64": p_plain},
+        "proposal": {"Mrays/s": round(n / (ms_prop * 1e-3) / 1e6, 3), "ms": round(ms_prop, 3),
+                     "samples_per_ray": round(st_prop["samples_generated"] / n, 3), "psnr_vs_fp64": p_prop,
+                     "psnr_vs_plain": psnr(rgb_prop, rgb_plain), "fallback_frac": round(st_prop["fallback_rays"] / n, 4)},
+        "spr_reduction": round(st_plain["samples_generated"] / max(st_prop["samples_generated"], 1), 3),
+        "delta_psnr_vs_fp64_db": round(p_plain - p_prop, 2),
+        "training": {"rays": n_tr, "steps": args.train_steps, "batch": 8192, "lr": 3e-3,
+                     "loss_first": round(float(losses[:50].mean()), 4), "loss_last": round(float(losses[-50:].mean()), 4),
+                     "targets_s": round(t_targets, 2), "train_s": round(t_train, 2)},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    R.close()
+
+
 def run_reference(args):
     """The oracle (FP64 CPU program) on a bounded sample of the same workload."""
     world, rank, _ = _dist()
@@ -494,6 +588,8 @@ def main():
     ap.add_argument("--psnr-rays", type=int, default=32768)
     ap.add_argument("--ref-rays", type=int, default=16384)
     ap.add_argument("--views", type=int, default=None, help="views per GPU (default: the config's)")
+    ap.add_argument("--train-views", type=int, default=64, help="c5: plain-rendered training views")
+    ap.add_argument("--train-steps", type=int, default=3000, help="c5: Adam steps")
     ap.add_argument("--px", type=int, default=None, help="square image size (default: the config's)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -502,6 +598,8 @@ def main():
         run_reference(args)
     elif args.config == "c4":
         run_c4(args)
+    elif args.config == "c5":
+        run_c5(args)
     else:
         run_ours(args)
 

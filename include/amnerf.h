@@ -106,6 +106,15 @@ typedef struct {
     int max_samples;
     float t_term;
     float bg[3];
+    /* Learned proposal sampler (not in the paper; see amnerf_proposal_set): when
+     * use_proposal != 0 a loaded proposal network predicts, per ray, the depth-bin
+     * distribution of its compositing weight; bins are kept by decreasing predicted
+     * mass until `coverage` is reached (the background bin counts toward it), and
+     * only leaf crossings overlapping a kept bin are sampled.  Rays needing more than
+     * max_bins depth bins fall back to the plain sampler. */
+    int use_proposal;
+    float coverage;   /* e.g. 0.99 */
+    int max_bins;     /* in [1, 64], e.g. 16 */
 } amnerf_render_params;
 
 /* Schedule of the network step's tiles over the persistent workers (warpgroups). */
@@ -131,6 +140,7 @@ typedef struct {
     uint64_t samples_generated;   /* steps_per_leaf x crossings */
     uint64_t samples_composited;  /* samples reached before early termination */
     uint64_t tiles;               /* network tiles of 128 samples launched */
+    uint64_t fallback_rays;       /* proposal sampler: rays that used the plain sampler */
     float ms[4];                  /* stage times: traverse, group, network, composite */
 } amnerf_stats;
 
@@ -146,6 +156,7 @@ typedef struct {
  *                                         order inside a leaf is unspecified
  *   slot_out float  [n_rays * max_samples * 4]  sigma, r, g, b of sample j of ray r at
  *                                         slot r*max_samples+j (unused slots untouched)
+ *   prop_mask, prop_fallback              the proposal sampler's per-ray decisions
  * Entries past the valid ones are left untouched. */
 typedef struct {
     uint8_t *n_x;
@@ -156,6 +167,8 @@ typedef struct {
     uint32_t *offsets;
     uint32_t *order;
     float *slot_out;
+    uint64_t *prop_mask;      /* [n_rays] kept depth bins (proposal renders only) */
+    uint8_t *prop_fallback;   /* [n_rays] 1 = plain sampler used (proposal renders only) */
 } amnerf_debug;
 
 /* Create a context on CUDA device `device`, enqueuing on `cuda_stream` (a
@@ -254,6 +267,53 @@ AMNERF_API amnerf_status amnerf_set_timing(amnerf_ctx *ctx, int enable);
 AMNERF_API amnerf_status amnerf_group_by_leaf_static(const uint8_t *n_x, const uint16_t *leaf, int64_t n_rays,
                                                      int maxc, int n_leaves, uint32_t *counts, uint32_t *offsets,
                                                      uint32_t *order, void *cuda_stream);
+
+/* ---- learned proposal sampler (not in the paper) --------------------------------
+ * Network: input gamma_10(o + t0 d) ++ gamma_4(d) (t0 = entry into the root box), two
+ * ReLU layers of 32, 65 logits (64 uniform depth bins of the ray's root interval and a
+ * background bin), softmax.  Parameters: FP32 W1 [32 x 90], b1 [32], W2 [32 x 32],
+ * b2 [32], W3 [65 x 32], b3 [65] = AMNERF_PROPOSAL_PARAMS values.  Training minimises
+ * the mean cross-entropy against the plain renderer's binned compositing weights with
+ * Adam (beta 0.9 / 0.999, eps 1e-8). */
+#define AMNERF_PROPOSAL_PARAMS 6113
+
+/* Load proposal parameters (HOST FP32, AMNERF_PROPOSAL_PARAMS values) and, for a
+ * resumed training run, the Adam moments m, v (HOST, same size; NULL = zero) and the
+ * number of steps already taken.  Synchronous. */
+AMNERF_API amnerf_status amnerf_proposal_set(amnerf_ctx *ctx, const float *params, const float *adam_m,
+                                             const float *adam_v, int step);
+
+/* Read back parameters, Adam moments (HOST, may be NULL) and the step count. */
+AMNERF_API amnerf_status amnerf_proposal_get(amnerf_ctx *ctx, float *params, float *adam_m, float *adam_v,
+                                             int *step);
+
+/* Training targets from the plain renderer: renders (DEVICE rays, outputs as in
+ * amnerf_render) and writes per ray the compositing weight of each depth bin plus
+ * the residual transmittance (DEVICE float [n_rays][65], sums to 1) and the root
+ * interval (DEVICE float [n_rays][2]; 0, 0 for rays that miss).  Synchronous. */
+AMNERF_API amnerf_status amnerf_proposal_targets(amnerf_ctx *ctx, const float *rays_o, const float *rays_d,
+                                                 int64_t n_rays, const amnerf_render_params *params, float *rgb,
+                                                 float *depth, float *opacity, float *targets, float *root);
+
+/* `steps` Adam steps with learning rate lr on minibatches of `batch` rays drawn
+ * with a counter-based hash of (seed, step, index) from n_rays rays (DEVICE rays,
+ * root intervals and targets as produced by amnerf_proposal_targets).  losses
+ * (HOST, may be NULL) receives the minibatch loss of every step.  Synchronous. */
+AMNERF_API amnerf_status amnerf_proposal_train(amnerf_ctx *ctx, const float *rays_o, const float *rays_d,
+                                               const float *root, const float *targets, int64_t n_rays, int steps,
+                                               int batch, float lr, uint64_t seed, float *losses);
+
+/* Full-batch mean loss and gradient (HOST, AMNERF_PROPOSAL_PARAMS) without updating
+ * anything (for checks).  Synchronous. */
+AMNERF_API amnerf_status amnerf_proposal_grad(amnerf_ctx *ctx, const float *rays_o, const float *rays_d,
+                                              const float *root, const float *targets, int64_t n_rays, float *grad,
+                                              float *loss);
+
+/* Inference only: softmax outputs (DEVICE float [n_rays][65], may be NULL), kept-bin
+ * masks (DEVICE uint64 [n_rays]) and fallback flags (DEVICE uint8 [n_rays]). */
+AMNERF_API amnerf_status amnerf_proposal_predict(amnerf_ctx *ctx, const float *rays_o, const float *rays_d,
+                                                 int64_t n_rays, float coverage, int max_bins, float *probs,
+                                                 uint64_t *mask, uint8_t *fallback);
 
 /* Set / read the network step's launch configuration (see amnerf_tuning).
  * amnerf_get_tuning also reports the largest group count the loaded shape allows. */

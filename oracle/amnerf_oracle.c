@@ -807,10 +807,18 @@ int or_render(const float *box, const int *info, const float *split, int n_nodes
 #define OR_PO 65
 #define OR_PNPAR (OR_PH * OR_PIN + OR_PH + OR_PH * OR_PH + OR_PH + OR_PO * OR_PH + OR_PO)
 
+/* The entry point is an FP32 quantity like the rays and the root interval it comes
+ * from: e = o + t0 d with the product and the sum each rounded to float; its
+ * encoding is then evaluated in double. */
 static void or_prop_input(const float *of, const float *df, double t0, double *in)
 {
     double e[3], d[3];
-    for (int a = 0; a < 3; a++) { d[a] = df[a]; e[a] = (double)of[a] + t0 * d[a]; }
+    for (int a = 0; a < 3; a++) {
+        float m = (float)t0 * df[a];
+        float ef = of[a] + m;
+        d[a] = df[a];
+        e[a] = ef;
+    }
     or_encode64(e, 10, in);
     or_encode64(d, 4, in + 63);
 }

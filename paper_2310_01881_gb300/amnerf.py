@@ -46,7 +46,11 @@ class amnerf_mlp_desc(ctypes.Structure):
 
 class amnerf_render_params(ctypes.Structure):
     _fields_ = [("steps_per_leaf", ctypes.c_int), ("max_samples", ctypes.c_int), ("t_term", ctypes.c_float),
-                ("bg", ctypes.c_float * 3)]
+                ("bg", ctypes.c_float * 3), ("use_proposal", ctypes.c_int), ("coverage", ctypes.c_float),
+                ("max_bins", ctypes.c_int)]
+
+
+PROPOSAL_PARAMS = 6113
 
 
 SCHED_CONTIGUOUS, SCHED_INTERLEAVED, SCHED_DYNAMIC, SCHED_PER_LEAF = range(4)
@@ -58,16 +62,18 @@ class amnerf_tuning(ctypes.Structure):
 
 class amnerf_stats(ctypes.Structure):
     _fields_ = [("rays", ctypes.c_uint64), ("crossings", ctypes.c_uint64), ("samples_generated", ctypes.c_uint64),
-                ("samples_composited", ctypes.c_uint64), ("tiles", ctypes.c_uint64), ("ms", ctypes.c_float * 4)]
+                ("samples_composited", ctypes.c_uint64), ("tiles", ctypes.c_uint64),
+                ("fallback_rays", ctypes.c_uint64), ("ms", ctypes.c_float * 4)]
 
     def as_dict(self) -> dict:
         return {"rays": self.rays, "crossings": self.crossings, "samples_generated": self.samples_generated,
-                "samples_composited": self.samples_composited, "tiles": self.tiles, "ms": list(self.ms)}
+                "samples_composited": self.samples_composited, "tiles": self.tiles,
+                "fallback_rays": self.fallback_rays, "ms": list(self.ms)}
 
 
 class amnerf_debug(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("n_x", "leaf", "t_in", "t_out", "counts", "offsets", "order",
-                                               "slot_out")]
+                                               "slot_out", "prop_mask", "prop_fallback")]
 
 
 _lib = None
@@ -96,6 +102,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "amnerf_render_host": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V, V], S),
         "amnerf_sync": ([V], S),
         "amnerf_group_by_leaf_static": ([V, V, L, I, I, V, V, V, V], S),
+        "amnerf_proposal_set": ([V, V, V, V, I], S),
+        "amnerf_proposal_get": ([V, V, V, V, ctypes.POINTER(I)], S),
+        "amnerf_proposal_targets": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V, V, V], S),
+        "amnerf_proposal_train": ([V, V, V, V, V, L, I, I, ctypes.c_float, ctypes.c_uint64, V], S),
+        "amnerf_proposal_grad": ([V, V, V, V, V, L, V, V], S),
+        "amnerf_proposal_predict": ([V, V, V, L, ctypes.c_float, I, V, V, V], S),
         "amnerf_set_timing": ([V, I], S),
         "amnerf_set_tuning": ([V, ctypes.POINTER(amnerf_tuning)], S),
         "amnerf_get_tuning": ([V, ctypes.POINTER(amnerf_tuning), ctypes.POINTER(I)], S),
@@ -190,14 +202,16 @@ def amnerf_load_mlps(ctx, weights: np.ndarray, n_leaves: int, width: int, hidden
     _check(ctx, load().amnerf_load_mlps(ctx, ctypes.byref(desc), n_leaves, _hptr(w)), "amnerf_load_mlps")
 
 
-def _params(steps: int, cap: int, t_term: float, bg) -> amnerf_render_params:
-    return amnerf_render_params(steps, cap, t_term, (ctypes.c_float * 3)(*bg))
+def _params(steps: int, cap: int, t_term: float, bg, proposal: bool = False, coverage: float = 0.99,
+            max_bins: int = 16) -> amnerf_render_params:
+    return amnerf_render_params(steps, cap, t_term, (ctypes.c_float * 3)(*bg), int(proposal), coverage, max_bins)
 
 
 def amnerf_render(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
-                  bg=(0.0, 0.0, 0.0), stats: bool = False):
+                  bg=(0.0, 0.0, 0.0), stats: bool = False, proposal: bool = False, coverage: float = 0.99,
+                  max_bins: int = 16):
     """Enqueue a render of CUDA tensors o, d (n, 3) into rgb (n, 3), depth, opacity (n,)."""
-    p = _params(steps, cap, t_term, bg)
+    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins)
     sp = amnerf_stats() if stats else None
     st = load().amnerf_render(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
                               _ptr(opacity), ctypes.byref(sp) if sp is not None else None)
@@ -206,8 +220,9 @@ def amnerf_render(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64,
 
 
 def amnerf_render_debug(ctx, o, d, rgb, depth, opacity, dbg: dict, steps: int = 8, cap: int = 64,
-                        t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), stats: bool = True):
-    p = _params(steps, cap, t_term, bg)
+                        t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), stats: bool = True, proposal: bool = False,
+                        coverage: float = 0.99, max_bins: int = 16):
+    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins)
     db = amnerf_debug(*[_ptr(dbg.get(k)) for k, _ in amnerf_debug._fields_])
     sp = amnerf_stats() if stats else None
     st = load().amnerf_render_debug(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
@@ -264,6 +279,57 @@ def amnerf_autotune(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 6
     return best.groups, best.schedule, ms.value
 
 
+def amnerf_proposal_set(ctx, params: np.ndarray, adam_m=None, adam_v=None, step: int = 0) -> None:
+    P = np.ascontiguousarray(params, np.float32)
+    assert P.size == PROPOSAL_PARAMS
+    m = None if adam_m is None else np.ascontiguousarray(adam_m, np.float32)
+    v = None if adam_v is None else np.ascontiguousarray(adam_v, np.float32)
+    st = load().amnerf_proposal_set(ctx, _hptr(P), _hptr(m) if m is not None else None,
+                                    _hptr(v) if v is not None else None, step)
+    _check(ctx, st, "amnerf_proposal_set")
+
+
+def amnerf_proposal_get(ctx):
+    """(params, adam_m, adam_v, step) as float32 numpy arrays."""
+    P = np.zeros(PROPOSAL_PARAMS, np.float32); m = np.zeros_like(P); v = np.zeros_like(P)
+    step = ctypes.c_int()
+    _check(ctx, load().amnerf_proposal_get(ctx, _hptr(P), _hptr(m), _hptr(v), ctypes.byref(step)),
+           "amnerf_proposal_get")
+    return P, m, v, step.value
+
+
+def amnerf_proposal_targets(ctx, o, d, rgb, depth, opacity, targets, root, steps: int = 8, cap: int = 64,
+                            t_term: float = 1e-4, bg=(0.0, 0.0, 0.0)) -> None:
+    p = _params(steps, cap, t_term, bg)
+    st = load().amnerf_proposal_targets(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
+                                        _ptr(opacity), _ptr(targets), _ptr(root))
+    _check(ctx, st, "amnerf_proposal_targets")
+
+
+def amnerf_proposal_train(ctx, o, d, root, targets, steps: int, batch: int, lr: float = 1e-3,
+                          seed: int = 1) -> np.ndarray:
+    losses = np.zeros(max(steps, 1), np.float32)
+    st = load().amnerf_proposal_train(ctx, _ptr(o), _ptr(d), _ptr(root), _ptr(targets), o.shape[0], steps, batch,
+                                      lr, seed, _hptr(losses))
+    _check(ctx, st, "amnerf_proposal_train")
+    return losses[:steps]
+
+
+def amnerf_proposal_grad(ctx, o, d, root, targets):
+    g = np.zeros(PROPOSAL_PARAMS, np.float32)
+    loss = np.zeros(1, np.float32)
+    st = load().amnerf_proposal_grad(ctx, _ptr(o), _ptr(d), _ptr(root), _ptr(targets), o.shape[0], _hptr(g),
+                                     _hptr(loss))
+    _check(ctx, st, "amnerf_proposal_grad")
+    return float(loss[0]), g
+
+
+def amnerf_proposal_predict(ctx, o, d, probs, mask, fallback, coverage: float = 0.99, max_bins: int = 16) -> None:
+    st = load().amnerf_proposal_predict(ctx, _ptr(o), _ptr(d), o.shape[0], coverage, max_bins, _ptr(probs),
+                                        _ptr(mask), _ptr(fallback))
+    _check(ctx, st, "amnerf_proposal_predict")
+
+
 def amnerf_sync(ctx) -> None:
     _check(ctx, load().amnerf_sync(ctx), "amnerf_sync")
 
@@ -311,7 +377,8 @@ class Renderer:
     def load_mlps(self, weights, width, hidden, lx, ld, prec="fp32") -> None:
         amnerf_load_mlps(self.ctx, weights, self.n_leaves, width, hidden, lx, ld, PRECISIONS.get(prec, prec))
 
-    def render(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0), stats=False, out=None):
+    def render(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0), stats=False, out=None,
+               proposal=False, coverage=0.99, max_bins=16):
         torch = self._torch
         n = o.shape[0]
         if out is None:
@@ -319,10 +386,12 @@ class Renderer:
                    torch.empty((n,), device=o.device, dtype=torch.float32),
                    torch.empty((n,), device=o.device, dtype=torch.float32))
         amnerf_set_stream(self.ctx, torch.cuda.current_stream(o.device).cuda_stream)
-        s = amnerf_render(self.ctx, o, d, *out, steps=steps, cap=cap, t_term=t_term, bg=bg, stats=stats)
+        s = amnerf_render(self.ctx, o, d, *out, steps=steps, cap=cap, t_term=t_term, bg=bg, stats=stats,
+                          proposal=proposal, coverage=coverage, max_bins=max_bins)
         return (*out, s) if stats else out
 
-    def render_debug(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0)):
+    def render_debug(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0), proposal=False, coverage=0.99,
+                     max_bins=16):
         torch = self._torch
         n = o.shape[0]
         maxc = cap // steps
@@ -337,11 +406,15 @@ class Renderer:
             "order": torch.zeros(max(n * maxc, 1), dtype=torch.int32, device=dev),
             "slot_out": torch.zeros(max(n * cap * 4, 1), dtype=torch.float32, device=dev),
         }
+        if proposal:
+            dbg["prop_mask"] = torch.zeros(max(n, 1), dtype=torch.int64, device=dev)
+            dbg["prop_fallback"] = torch.zeros(max(n, 1), dtype=torch.uint8, device=dev)
         rgb = torch.empty((n, 3), device=dev, dtype=torch.float32)
         depth = torch.empty((n,), device=dev, dtype=torch.float32)
         opac = torch.empty((n,), device=dev, dtype=torch.float32)
         amnerf_set_stream(self.ctx, torch.cuda.current_stream(dev).cuda_stream)
-        s = amnerf_render_debug(self.ctx, o, d, rgb, depth, opac, dbg, steps=steps, cap=cap, t_term=t_term, bg=bg)
+        s = amnerf_render_debug(self.ctx, o, d, rgb, depth, opac, dbg, steps=steps, cap=cap, t_term=t_term, bg=bg,
+                                proposal=proposal, coverage=coverage, max_bins=max_bins)
         host = {k: v.cpu().numpy() for k, v in dbg.items()}
         host["leaf"] = host["leaf"].view(np.uint16).astype(np.int64).reshape(n, maxc)
         host["t_in"] = host["t_in"].reshape(n, maxc)
@@ -350,6 +423,9 @@ class Renderer:
         host["counts"] = host["counts"].view(np.uint32).astype(np.int64)[: self.n_leaves]
         host["offsets"] = host["offsets"].view(np.uint32).astype(np.int64)
         host["slot_out"] = host["slot_out"][: n * cap * 4].reshape(n, cap, 4)
+        if proposal:
+            host["prop_mask"] = host["prop_mask"][:n].view(np.uint64)
+            host["prop_fallback"] = host["prop_fallback"][:n]
         return rgb.cpu().numpy(), depth.cpu().numpy(), opac.cpu().numpy(), host, s
 
     def sync(self):

@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libamnerf.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["api.cu", "tree.cpp", "k_traverse.cu", "k_group.cu", "k_mlp_simt.cu", "k_mlp_tc.cu",
-           "k_composite.cu", "group_static.cu"]
+           "k_composite.cu", "group_static.cu", "k_proposal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                 "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE]

@@ -34,7 +34,8 @@ constexpr int kDevErrBounds = 3;
 // K-a: traversal + crossing list + per-leaf crossing histogram.
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
                             int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
-                            int n_leaves, int* err);
+                            int n_leaves, int* err, const uint64_t* mask = nullptr,
+                            const uint8_t* fallback = nullptr, float2* root_out = nullptr);
 
 // K-b: exclusive scans (crossings and network tiles per leaf) and the grouped scatter.
 cudaError_t launch_scan(cudaStream_t s, const uint32_t* counts, int n_leaves, int cpt, uint32_t* offsets,
@@ -81,7 +82,19 @@ size_t simt_leaf_stride_floats(int width, int hidden, int k0);
 // K-d: per-ray compositing.
 cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* xing, const float4* slot_out,
                              uint32_t n, int steps, int maxc, int cap, float t_term, float bg0, float bg1,
-                             float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats);
+                             float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
+                             const float2* root = nullptr, float* bins = nullptr);
+
+// Proposal sampler (k_proposal.cu).
+int proposal_param_count();
+cudaError_t prepare_proposal();
+cudaError_t launch_prop_infer(cudaStream_t s, const float* params, const float root_box[6], const float* ro,
+                              const float* rd, uint32_t n, float coverage, int max_bins, uint64_t* mask,
+                              uint8_t* fallback, unsigned long long* n_fallback, float* q_out);
+cudaError_t launch_prop_grad(cudaStream_t s, const float* params, const float* ro, const float* rd,
+                             const float2* root, const float* targets, uint32_t n, uint32_t batch, uint64_t seed,
+                             uint64_t step, float* grad, float* loss);
+cudaError_t launch_prop_adam(cudaStream_t s, float* P, float* g, float* m, float* v, int t, float lr);
 
 // ---- host tree builder -------------------------------------------------------------
 // Returns false on invalid input (message in err).

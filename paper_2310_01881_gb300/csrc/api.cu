@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "amnerf_internal.h"
 
@@ -51,6 +52,14 @@ struct amnerf_ctx {
     int max_groups = 1;
     amnerf_tuning tuning{0, AMNERF_SCHED_CONTIGUOUS};
     std::vector<uint32_t> h_tile_off;  // per-leaf launches: host copy of tile offsets
+    // proposal sampler
+    bool prop_loaded = false;
+    int prop_step = 0;
+    float* d_prop = nullptr;  // params | m | v | grad | loss (5 x NPAR floats + 1)
+    size_t cap_prop_rays = 0;
+    uint64_t* d_mask = nullptr;
+    uint8_t* d_fallback = nullptr;
+    float2* d_root = nullptr;
     // timing
     bool timing = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -124,6 +133,10 @@ amnerf_status check_params(amnerf_ctx* ctx, const amnerf_render_params* p, int64
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(p->bg[c])) return fail(ctx, AMNERF_E_INVAL, "bg must be finite");
     if (n < 0) return fail(ctx, AMNERF_E_INVAL, "n_rays < 0");
+    if (p->use_proposal) {
+        if (!(p->coverage > 0.0f && p->coverage <= 1.0f)) return fail(ctx, AMNERF_E_INVAL, "coverage must be in (0, 1]");
+        if (p->max_bins < 1 || p->max_bins > 64) return fail(ctx, AMNERF_E_INVAL, "max_bins must be in [1, 64]");
+    }
     if ((uint64_t)n * (uint64_t)maxc >= (1ull << 32))
         return fail(ctx, AMNERF_E_INVAL, "n_rays * floor(max_samples / steps_per_leaf) must be < 2^32 (split the batch)");
     return AMNERF_OK;
@@ -152,6 +165,24 @@ void pack_simt(const float* src, float* dst, int width, int hidden, int k0) {
 }
 
 }  // namespace
+
+// Per-ray proposal scratch (masks, fallback flags, root intervals).
+static amnerf_status ensure_prop_scratch(amnerf_ctx* ctx, size_t n) {
+    if (n <= ctx->cap_prop_rays) return AMNERF_OK;
+    dfree(ctx->d_mask);
+    dfree(ctx->d_fallback);
+    dfree(ctx->d_root);
+    ctx->cap_prop_rays = 0;
+    cudaError_t e;
+    if ((e = cudaMalloc((void**)&ctx->d_mask, n * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_fallback, n)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_root, n * sizeof(float2))) != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "proposal scratch allocation");
+    }
+    ctx->cap_prop_rays = n;
+    return AMNERF_OK;
+}
 
 // Tensor-core layouts are produced by the tensor-core translation unit.
 namespace amnerf {
@@ -236,6 +267,10 @@ void amnerf_destroy(amnerf_ctx* ctx) {
     dfree(ctx->d_stats);
     dfree(ctx->d_err);
     dfree(ctx->d_hbuf);
+    dfree(ctx->d_prop);
+    dfree(ctx->d_mask);
+    dfree(ctx->d_fallback);
+    dfree(ctx->d_root);
     for (int i = 0; i < 5; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     delete ctx;
@@ -334,7 +369,8 @@ amnerf_status amnerf_load_mlps(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int
 
 static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* rd, int64_t n,
                                  const amnerf_render_params* p, float* rgb, float* depth, float* opacity,
-                                 const amnerf_debug* dbg, amnerf_stats* stats) {
+                                 const amnerf_debug* dbg, amnerf_stats* stats, float* bins_out = nullptr,
+                                 float2* root_out = nullptr) {
     if (!ctx) return AMNERF_E_INVAL;
     if (ctx->nodes.empty()) return fail(ctx, AMNERF_E_NOTREE, "build the tree first");
     if (!ctx->mlp_loaded) return fail(ctx, AMNERF_E_NOMLP, "load the networks first");
@@ -354,8 +390,22 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
     if (ctx->timing) cudaEventRecord(ctx->ev[0], s);
     CK(cudaMemsetAsync(ctx->d_counts, 0, sizeof(uint32_t) * L, s), "memset");
     CK(cudaMemsetAsync(ctx->d_stats, 0, sizeof(uint64_t) * 8, s), "memset");
+    const uint64_t* mask = nullptr;
+    const uint8_t* fallback = nullptr;
+    if (p->use_proposal && n > 0) {
+        if (!ctx->prop_loaded) return fail(ctx, AMNERF_E_INVAL, "use_proposal set but no proposal network loaded");
+        st = ensure_prop_scratch(ctx, (size_t)n);
+        if (st != AMNERF_OK) return st;
+        const amnerf_node& root = ctx->nodes[0];
+        const float box[6] = {root.lo[0], root.lo[1], root.lo[2], root.hi[0], root.hi[1], root.hi[2]};
+        CK(launch_prop_infer(s, ctx->d_prop, box, ro, rd, nn, p->coverage, p->max_bins, ctx->d_mask, ctx->d_fallback,
+                             reinterpret_cast<unsigned long long*>(ctx->d_stats + 3), nullptr),
+           "proposal launch");
+        mask = ctx->d_mask;
+        fallback = ctx->d_fallback;
+    }
     CK(launch_traverse(s, ro, rd, nn, ctx->d_nodes, maxc, ctx->d_nx, ctx->d_xing, ctx->d_xleaf, ctx->d_counts, L,
-                       ctx->d_err),
+                       ctx->d_err, mask, fallback, root_out),
        "traverse launch");
     if (ctx->timing) cudaEventRecord(ctx->ev[1], s);
     CK(launch_scan(s, ctx->d_counts, L, kTileRows / steps, ctx->d_offsets, ctx->d_tile_off, ctx->d_cursor,
@@ -416,7 +466,7 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
     }
     if (ctx->timing) cudaEventRecord(ctx->ev[3], s);
     CK(launch_composite(s, ctx->d_nx, ctx->d_xing, ctx->d_slot, nn, steps, maxc, cap, p->t_term, p->bg[0], p->bg[1],
-                        p->bg[2], rgb, depth, opacity, ctx->d_stats),
+                        p->bg[2], rgb, depth, opacity, ctx->d_stats, root_out, bins_out),
        "composite launch");
     if (ctx->timing) cudaEventRecord(ctx->ev[4], s);
 
@@ -443,6 +493,10 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         if (dbg->slot_out)
             CK(cudaMemcpyAsync(dbg->slot_out, ctx->d_slot, (size_t)n * cap * 16, cudaMemcpyDeviceToDevice, s),
                "debug copy");
+        if (dbg->prop_mask && mask)
+            CK(cudaMemcpyAsync(dbg->prop_mask, mask, (size_t)n * 8, cudaMemcpyDeviceToDevice, s), "debug copy");
+        if (dbg->prop_fallback && fallback)
+            CK(cudaMemcpyAsync(dbg->prop_fallback, fallback, (size_t)n, cudaMemcpyDeviceToDevice, s), "debug copy");
     }
     if (stats) {
         uint64_t h[8];
@@ -453,6 +507,7 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         stats->samples_generated = h[0] * (uint64_t)steps;
         stats->tiles = h[1];
         stats->samples_composited = h[2];
+        stats->fallback_rays = h[3];
         for (int i = 0; i < 4; ++i) {
             float ms = 0.f;
             if (ctx->timing) cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]);
@@ -513,6 +568,127 @@ amnerf_status amnerf_render_host(amnerf_ctx* ctx, const float* ro, const float* 
         CK(cudaMemcpyAsync(opacity, dop, nn * 4, cudaMemcpyDeviceToHost, s), "pixel download");
     }
     CK(cudaStreamSynchronize(s), "stream sync");
+    return AMNERF_OK;
+}
+
+static float* prop_params(amnerf_ctx* c) { return c->d_prop; }
+static float* prop_m(amnerf_ctx* c) { return c->d_prop + proposal_param_count(); }
+static float* prop_v(amnerf_ctx* c) { return c->d_prop + 2 * proposal_param_count(); }
+static float* prop_g(amnerf_ctx* c) { return c->d_prop + 3 * proposal_param_count(); }
+static float* prop_loss(amnerf_ctx* c) { return c->d_prop + 4 * proposal_param_count(); }
+
+amnerf_status amnerf_proposal_set(amnerf_ctx* ctx, const float* params, const float* m, const float* v, int step) {
+    if (!ctx || !params || step < 0) return fail(ctx, AMNERF_E_INVAL, "bad arguments");
+    const int np = proposal_param_count();
+    for (int i = 0; i < np; ++i)
+        if (!std::isfinite(params[i])) return fail(ctx, AMNERF_E_INVAL, "non-finite proposal parameter");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (!ctx->d_prop) {
+        CK(cudaMalloc((void**)&ctx->d_prop, sizeof(float) * (5 * (size_t)np + 1)), "proposal allocation");
+        CK(prepare_proposal(), "proposal kernel setup");
+    }
+    CK(cudaMemset(ctx->d_prop, 0, sizeof(float) * (5 * (size_t)np + 1)), "memset");
+    CK(cudaMemcpy(prop_params(ctx), params, sizeof(float) * np, cudaMemcpyHostToDevice), "proposal upload");
+    if (m) CK(cudaMemcpy(prop_m(ctx), m, sizeof(float) * np, cudaMemcpyHostToDevice), "proposal upload");
+    if (v) CK(cudaMemcpy(prop_v(ctx), v, sizeof(float) * np, cudaMemcpyHostToDevice), "proposal upload");
+    ctx->prop_step = step;
+    ctx->prop_loaded = true;
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_proposal_get(amnerf_ctx* ctx, float* params, float* m, float* v, int* step) {
+    if (!ctx) return AMNERF_E_INVAL;
+    if (!ctx->prop_loaded) return fail(ctx, AMNERF_E_INVAL, "no proposal network loaded");
+    const int np = proposal_param_count();
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize(), "stream sync");
+    if (params) CK(cudaMemcpy(params, prop_params(ctx), sizeof(float) * np, cudaMemcpyDeviceToHost), "download");
+    if (m) CK(cudaMemcpy(m, prop_m(ctx), sizeof(float) * np, cudaMemcpyDeviceToHost), "download");
+    if (v) CK(cudaMemcpy(v, prop_v(ctx), sizeof(float) * np, cudaMemcpyDeviceToHost), "download");
+    if (step) *step = ctx->prop_step;
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_proposal_targets(amnerf_ctx* ctx, const float* ro, const float* rd, int64_t n,
+                                      const amnerf_render_params* p, float* rgb, float* depth, float* opacity,
+                                      float* targets, float* root) {
+    if (!ctx || !p) return AMNERF_E_INVAL;
+    if (n > 0 && (!targets || !root)) return fail(ctx, AMNERF_E_INVAL, "NULL buffer");
+    amnerf_render_params q = *p;
+    q.use_proposal = 0;  // targets come from the plain sampler
+    amnerf_status st = render_impl(ctx, ro, rd, n, &q, rgb, depth, opacity, nullptr, nullptr, targets,
+                                   reinterpret_cast<float2*>(root));
+    if (st != AMNERF_OK) return st;
+    return amnerf_sync(ctx);
+}
+
+amnerf_status amnerf_proposal_train(amnerf_ctx* ctx, const float* ro, const float* rd, const float* root,
+                                    const float* targets, int64_t n, int steps, int batch, float lr, uint64_t seed,
+                                    float* losses) {
+    if (!ctx || n <= 0 || steps < 0 || batch < 1 || !(lr > 0.0f) || seed == 0 || !ro || !rd || !root || !targets)
+        return fail(ctx, AMNERF_E_INVAL, "bad arguments (seed must be nonzero)");
+    if (!ctx->prop_loaded) return fail(ctx, AMNERF_E_INVAL, "no proposal network loaded");
+    if (n >= (1ll << 32)) return fail(ctx, AMNERF_E_INVAL, "n_rays must be < 2^32");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = ctx->stream;
+    std::vector<float> h_loss((size_t)steps);
+    float* d_losses = nullptr;
+    if (steps > 0) CK(cudaMalloc((void**)&d_losses, sizeof(float) * (size_t)steps), "loss buffer");
+    CK(cudaMemsetAsync(prop_g(ctx), 0, sizeof(float) * proposal_param_count(), s), "memset");
+    if (steps > 0) CK(cudaMemsetAsync(d_losses, 0, sizeof(float) * (size_t)steps, s), "memset");
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < steps && e == cudaSuccess; ++i) {
+        const uint64_t step = (uint64_t)ctx->prop_step + 1;
+        e = launch_prop_grad(s, prop_params(ctx), ro, rd, reinterpret_cast<const float2*>(root), targets, (uint32_t)n,
+                             (uint32_t)batch, seed, step, prop_g(ctx), d_losses + i);
+        if (e == cudaSuccess) e = launch_prop_adam(s, prop_params(ctx), prop_g(ctx), prop_m(ctx), prop_v(ctx), (int)step, lr);
+        ctx->prop_step += 1;
+    }
+    if (e == cudaSuccess && steps > 0)
+        e = cudaMemcpyAsync(h_loss.data(), d_losses, sizeof(float) * (size_t)steps, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (d_losses) cudaFree(d_losses);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "proposal training");
+    if (losses) std::memcpy(losses, h_loss.data(), sizeof(float) * (size_t)steps);
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_proposal_grad(amnerf_ctx* ctx, const float* ro, const float* rd, const float* root,
+                                   const float* targets, int64_t n, float* grad, float* loss) {
+    if (!ctx || n <= 0 || !grad || !loss || !ro || !rd || !root || !targets) return fail(ctx, AMNERF_E_INVAL, "bad arguments");
+    if (!ctx->prop_loaded) return fail(ctx, AMNERF_E_INVAL, "no proposal network loaded");
+    if (n >= (1ll << 32)) return fail(ctx, AMNERF_E_INVAL, "n_rays must be < 2^32");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = ctx->stream;
+    const int np = proposal_param_count();
+    CK(cudaMemsetAsync(prop_g(ctx), 0, sizeof(float) * np, s), "memset");
+    CK(cudaMemsetAsync(prop_loss(ctx), 0, sizeof(float), s), "memset");
+    CK(launch_prop_grad(s, prop_params(ctx), ro, rd, reinterpret_cast<const float2*>(root), targets, (uint32_t)n,
+                        (uint32_t)n, 0, 0, prop_g(ctx), prop_loss(ctx)),
+       "proposal gradient");
+    CK(cudaMemcpyAsync(grad, prop_g(ctx), sizeof(float) * np, cudaMemcpyDeviceToHost, s), "download");
+    CK(cudaMemcpyAsync(loss, prop_loss(ctx), sizeof(float), cudaMemcpyDeviceToHost, s), "download");
+    CK(cudaMemsetAsync(prop_g(ctx), 0, sizeof(float) * np, s), "memset");
+    CK(cudaStreamSynchronize(s), "stream sync");
+    return AMNERF_OK;
+}
+
+amnerf_status amnerf_proposal_predict(amnerf_ctx* ctx, const float* ro, const float* rd, int64_t n, float coverage,
+                                      int max_bins, float* probs, uint64_t* mask, uint8_t* fallback) {
+    if (!ctx || n < 0 || !(coverage > 0.0f && coverage <= 1.0f) || max_bins < 1 || max_bins > 64)
+        return fail(ctx, AMNERF_E_INVAL, "bad arguments");
+    if (n > 0 && (!ro || !rd || !mask || !fallback)) return fail(ctx, AMNERF_E_INVAL, "NULL buffer");
+    if (!ctx->prop_loaded) return fail(ctx, AMNERF_E_INVAL, "no proposal network loaded");
+    if (ctx->nodes.empty()) return fail(ctx, AMNERF_E_NOTREE, "build the tree first");
+    if (n >= (1ll << 32)) return fail(ctx, AMNERF_E_INVAL, "n_rays must be < 2^32");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const amnerf_node& r = ctx->nodes[0];
+    const float box[6] = {r.lo[0], r.lo[1], r.lo[2], r.hi[0], r.hi[1], r.hi[2]};
+    CK(cudaMemsetAsync(ctx->d_stats + 3, 0, 8, ctx->stream), "memset");
+    CK(launch_prop_infer(ctx->stream, prop_params(ctx), box, ro, rd, (uint32_t)n, coverage, max_bins, mask, fallback,
+                         reinterpret_cast<unsigned long long*>(ctx->d_stats + 3), probs),
+       "proposal launch");
     return AMNERF_OK;
 }
 

@@ -11,7 +11,9 @@
 // lanes whose transmittance is below t_term are dropped (a prefix, since the
 // product only decreases), and the warp stops at the first chunk that terminates.
 // The sample position t and width delta are rebuilt from the crossing list in the
-// same FP32 operation order as the traversal/sampling step.
+// same FP32 operation order as the traversal/sampling step.  Optionally (training
+// targets of the proposal sampler) every composited weight is also added to the
+// depth bin of its sample, and the residual transmittance is stored as bin 64.
 #include "amnerf_internal.h"
 
 namespace amnerf {
@@ -23,12 +25,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_composite(
     const uint8_t* __restrict__ n_x, const float2* __restrict__ xing, const float4* __restrict__ slot_out,
     uint32_t n, int steps, int maxc, int cap, float t_term, float bg0, float bg1, float bg2,
     float* __restrict__ rgb, float* __restrict__ depth, float* __restrict__ opacity,
-    unsigned long long* __restrict__ n_comp) {
+    unsigned long long* __restrict__ n_comp, const float2* __restrict__ root, float* __restrict__ bins) {
     __shared__ uint32_t s_comp[kWarpsPerBlock];
+    __shared__ float s_bins[kWarpsPerBlock][65];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint32_t ray = blockIdx.x * kWarpsPerBlock + wib;
     uint32_t composited = 0;
+    float r0 = 0.f, bw = 0.f;
+    if (bins) {
+        for (int b = lane; b < 65; b += 32) s_bins[wib][b] = 0.0f;
+        if (ray < n) {
+            const float2 rt = __ldg(root + ray);
+            r0 = rt.x;
+            bw = __fmul_rn(__fsub_rn(rt.y, rt.x), 0.015625f);
+        }
+        __syncwarp();
+    }
     if (ray < n) {
         const int ns = (int)__ldg(n_x + ray) * steps;
         const float inv_steps = 1.0f / (float)steps;  // exact: steps is a power of two
@@ -68,6 +81,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_composite(
                 cg += w * v.z;
                 cb += w * v.w;
                 dd += w * t;
+                if (bins) {  // depth bin of the sample: floor((t - t0) / w), clamped to [0, 63]
+                    int k = bw > 0.0f ? (int)floorf(__fdiv_rn(__fsub_rn(t, r0), bw)) : 0;
+                    k = k < 0 ? 0 : (k > 63 ? 63 : k);
+                    atomicAdd(&s_bins[wib][k], w);
+                }
             }
             const unsigned act = __ballot_sync(0xffffffffu, active);
             const unsigned val = __ballot_sync(0xffffffffu, valid);
@@ -86,6 +104,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_composite(
             cg += __shfl_xor_sync(0xffffffffu, cg, o);
             cb += __shfl_xor_sync(0xffffffffu, cb, o);
             dd += __shfl_xor_sync(0xffffffffu, dd, o);
+        }
+        if (bins) {
+            __syncwarp();
+            if (lane == 0) s_bins[wib][64] = T;
+            __syncwarp();
+            for (int b = lane; b < 65; b += 32) bins[(size_t)ray * 65 + b] = s_bins[wib][b];
         }
         if (lane == 0) {
             rgb[3 * (size_t)ray + 0] = cr + T * bg0;
@@ -108,12 +132,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_composite(
 
 cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* xing, const float4* slot_out,
                              uint32_t n, int steps, int maxc, int cap, float t_term, float bg0, float bg1,
-                             float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats) {
+                             float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
+                             const float2* root, float* bins) {
     if (n == 0) return cudaSuccess;
     const unsigned blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
     k_composite<<<blocks, kWarpsPerBlock * 32, 0, s>>>(n_x, xing, slot_out, n, steps, maxc, cap, t_term, bg0, bg1,
                                                        bg2, rgb, depth, opacity,
-                                                       reinterpret_cast<unsigned long long*>(stats + 2));
+                                                       reinterpret_cast<unsigned long long*>(stats + 2), root, bins);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,352 @@
+// k_proposal.cu -- learned proposal sampler (not in the paper; a sampling network in
+// the spirit of the related work of Sec. 2.1): a small MLP predicts, per ray, how
+// the compositing weight is distributed over 64 uniform depth bins of the ray's root
+// interval plus a background bin, so that only the leaf crossings overlapping the
+// predicted bins are sampled.
+//
+// Network: input gamma_10(entry point o + t0 d) ++ gamma_4(d) (90), two ReLU layers of
+// 32, 65 logits, softmax.  Parameters (FP32, flat): W1 [32 x 90], b1 [32], W2 [32 x 32],
+// b2 [32], W3 [65 x 32], b3 [65] -- 6113 values.  Training minimises the mean cross-
+// entropy against the plain renderer's binned compositing weights with Adam.
+//
+// Kernels:
+//   k_prop_infer   thread per ray: root slab test (the traversal's FP32 operation
+//                  order), encoding, forward pass (weights in shared memory, read as
+//                  broadcasts), softmax, then the kept bins: bins by decreasing mass
+//                  (ties to the lower index) until the mass reaches `coverage` (the
+//                  background counts toward it); more than max_bins depth bins ->
+//                  fallback to the plain sampler.
+//   k_prop_grad    one CTA per 128 rays: each thread runs its ray forward and
+//                  backward and leaves its activations and deltas in shared memory;
+//                  the CTA then forms the gradient contractions (sum over its rays of
+//                  delta x activation) and adds them with one atomic per parameter.
+//   k_prop_adam    elementwise Adam update, then clears the gradient.
+#include "amnerf_internal.h"
+
+namespace amnerf {
+namespace {
+
+constexpr int PIN = 90, PH = 32, PO = 65;
+constexpr int NPAR = PH * PIN + PH + PH * PH + PH + PO * PH + PO;
+constexpr int OFF_W1 = 0, OFF_B1 = PH * PIN, OFF_W2 = OFF_B1 + PH, OFF_B2 = OFF_W2 + PH * PH,
+              OFF_W3 = OFF_B2 + PH, OFF_B3 = OFF_W3 + PO * PH;
+constexpr int kRays = 128;  // rays per CTA
+
+__device__ __forceinline__ bool root_slab(const float* box, const float o[3], const float d[3], float& t0,
+                                          float& t1) {
+    float tmin[3], tmax[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float inv = __frcp_rn(d[a]);
+        const float u0 = __fmul_rn(__fsub_rn(box[a], o[a]), inv);
+        const float u1 = __fmul_rn(__fsub_rn(box[3 + a], o[a]), inv);
+        tmin[a] = fminf(u0, u1);
+        tmax[a] = fmaxf(u0, u1);
+    }
+    float e = fmaxf(fmaxf(tmin[0], tmin[1]), tmin[2]);
+    const float x = fminf(fminf(tmax[0], tmax[1]), tmax[2]);
+    e = fmaxf(e, 0.0f);
+    t0 = e;
+    t1 = x;
+    return x > e;
+}
+
+// The 90 input features of one ray, in the oracle's order.
+__device__ __forceinline__ void prop_features(const float o[3], const float d[3], float t0, float* x) {
+    float e[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) e[a] = __fadd_rn(o[a], __fmul_rn(t0, d[a]));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = e[a];
+#pragma unroll
+    for (int k = 0; k < 10; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sincospif(e[a] * (float)(1 << k), &x[3 + 6 * k + a], &x[6 + 6 * k + a]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[63 + a] = d[a];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sincospif(d[a] * (float)(1 << k), &x[66 + 6 * k + a], &x[69 + 6 * k + a]);
+}
+
+// Forward pass from features in shared memory row xr (stride 1) with parameters in
+// shared memory P; h1, h2 post-ReLU, q softmax.
+__device__ __forceinline__ void prop_forward(const float* __restrict__ P, const float* xr, float* h1, float* h2,
+                                             float* q) {
+#pragma unroll
+    for (int o = 0; o < PH; ++o) h1[o] = P[OFF_B1 + o];
+    for (int f = 0; f < PIN; ++f) {
+        const float v = xr[f];
+#pragma unroll
+        for (int o = 0; o < PH; ++o) h1[o] = fmaf(P[OFF_W1 + o * PIN + f], v, h1[o]);
+    }
+#pragma unroll
+    for (int o = 0; o < PH; ++o) h1[o] = fmaxf(h1[o], 0.0f);
+#pragma unroll
+    for (int o = 0; o < PH; ++o) {
+        float acc = P[OFF_B2 + o];
+#pragma unroll
+        for (int i = 0; i < PH; ++i) acc = fmaf(P[OFF_W2 + o * PH + i], h1[i], acc);
+        h2[o] = fmaxf(acc, 0.0f);
+    }
+    float m = -INFINITY;
+#pragma unroll
+    for (int o = 0; o < PO; ++o) {
+        float acc = P[OFF_B3 + o];
+#pragma unroll
+        for (int i = 0; i < PH; ++i) acc = fmaf(P[OFF_W3 + o * PH + i], h2[i], acc);
+        q[o] = acc;
+        m = fmaxf(m, acc);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int o = 0; o < PO; ++o) {
+        q[o] = expf(q[o] - m);
+        s += q[o];
+    }
+    const float inv = 1.0f / s;
+#pragma unroll
+    for (int o = 0; o < PO; ++o) q[o] *= inv;
+}
+
+__global__ void __launch_bounds__(kRays) k_prop_infer(const float* __restrict__ params, float b0, float b1, float b2,
+                                                      float b3, float b4, float b5, const float* __restrict__ ro,
+                                                      const float* __restrict__ rd, uint32_t n, float coverage,
+                                                      int max_bins, uint64_t* __restrict__ mask,
+                                                      uint8_t* __restrict__ fallback,
+                                                      unsigned long long* __restrict__ n_fallback,
+                                                      float* __restrict__ q_out) {
+    extern __shared__ __align__(16) uint8_t smraw[];
+    float* P = reinterpret_cast<float*>(smraw);
+    float (*X)[PIN + 1] = reinterpret_cast<float (*)[PIN + 1]>(P + NPAR);
+    for (int i = threadIdx.x; i < NPAR; i += blockDim.x) P[i] = params[i];
+    const uint32_t r = blockIdx.x * kRays + threadIdx.x;
+    float o[3] = {0.f, 0.f, 0.f}, d[3] = {1.f, 0.f, 0.f}, t0 = 0.f, t1 = 0.f;
+    bool hit = false;
+    if (r < n) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = __ldg(ro + 3 * (size_t)r + a);
+            d[a] = __ldg(rd + 3 * (size_t)r + a);
+        }
+        const float box[6] = {b0, b1, b2, b3, b4, b5};
+        hit = root_slab(box, o, d, t0, t1);
+        if (!hit) t0 = t1 = 0.f;  // as the traversal reports the root interval of a miss
+    }
+    prop_features(o, d, t0, X[threadIdx.x]);
+    __syncthreads();
+    if (r >= n) return;
+    float h1[PH], h2[PH], q[PO];
+    prop_forward(P, X[threadIdx.x], h1, h2, q);
+    if (q_out) {
+#pragma unroll
+        for (int b = 0; b < PO; ++b) q_out[(size_t)r * PO + b] = q[b];
+    }
+    uint64_t mk = 0, used = 0;
+    bool used_bg = false, fb = false;
+    float cum = 0.0f;
+    int kept = 0;
+    while (cum < coverage) {
+        int best = -1;
+        float bv = -1.0f;
+#pragma unroll
+        for (int b = 0; b < PO; ++b) {
+            const bool u = b < 64 ? ((used >> b) & 1ull) != 0 : used_bg;
+            if (!u && q[b] > bv) {
+                bv = q[b];
+                best = b;
+            }
+        }
+        if (best < 0) break;
+        cum += bv;
+        if (best == 64) {
+            used_bg = true;
+            continue;
+        }
+        used |= 1ull << best;
+        if (kept == max_bins) {
+            fb = true;
+            break;
+        }
+        mk |= 1ull << best;
+        ++kept;
+    }
+    if (!hit) fb = false;
+    mask[r] = fb ? ~0ull : mk;
+    fallback[r] = fb ? 1 : 0;
+    if (fb) atomicAdd(n_fallback, 1ull);
+}
+
+// splitmix64 finaliser: the ray index of batch element i of step s.
+__device__ __forceinline__ uint32_t batch_ray(uint64_t seed, uint64_t s, uint32_t i, uint32_t n) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (s * 0x100000001ull + i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (uint32_t)(z % n);
+}
+
+struct GradSmem {
+    float P[NPAR];
+    float X[kRays][PIN + 1];
+    float H1[kRays][PH + 1];
+    float H2[kRays][PH + 1];
+    float DZ[kRays][PO];
+    float DH2[kRays][PH + 1];
+    float DH1[kRays][PH + 1];
+    float loss[kRays];
+};
+
+// Gradient of the mean cross-entropy over a batch of B rays (B may span CTAs):
+// ray indices come from `idx` (when non-NULL) or from the counter-based hash.
+__global__ void __launch_bounds__(kRays) k_prop_grad(const float* __restrict__ params, const float* __restrict__ ro,
+                                                     const float* __restrict__ rd, const float2* __restrict__ root,
+                                                     const float* __restrict__ targets, uint32_t n, uint32_t B,
+                                                     uint64_t seed, uint64_t step, float* __restrict__ grad,
+                                                     float* __restrict__ loss) {
+    extern __shared__ __align__(16) uint8_t smraw[];
+    GradSmem& S = *reinterpret_cast<GradSmem*>(smraw);
+    for (int i = threadIdx.x; i < NPAR; i += blockDim.x) S.P[i] = params[i];
+    const uint32_t bi = blockIdx.x * kRays + threadIdx.x;
+    const bool valid = bi < B;
+    const int t = threadIdx.x;
+    uint32_t r = 0;
+    float o[3] = {0.f, 0.f, 0.f}, d[3] = {1.f, 0.f, 0.f}, t0 = 0.f;
+    if (valid) {
+        r = B == n && seed == 0 ? bi : batch_ray(seed, step, bi, n);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = __ldg(ro + 3 * (size_t)r + a);
+            d[a] = __ldg(rd + 3 * (size_t)r + a);
+        }
+        t0 = root[r].x;
+    }
+    prop_features(o, d, t0, S.X[t]);
+    __syncthreads();
+    float h1[PH], h2[PH], q[PO];
+    prop_forward(S.P, S.X[t], h1, h2, q);
+    float L = 0.0f;
+    if (valid) {
+        float ps = 0.0f;
+#pragma unroll
+        for (int b = 0; b < PO; ++b) {
+            const float p = __ldg(targets + (size_t)r * PO + b);
+            if (p > 0.0f) L -= p * logf(q[b]);
+            ps += p;
+            S.DZ[t][b] = -p;
+        }
+#pragma unroll
+        for (int b = 0; b < PO; ++b) S.DZ[t][b] += q[b] * ps;  // dL/dz = q sum(p) - p
+    } else {
+        for (int b = 0; b < PO; ++b) S.DZ[t][b] = 0.0f;
+    }
+    S.loss[t] = L;
+#pragma unroll
+    for (int i = 0; i < PH; ++i) {
+        S.H1[t][i] = h1[i];
+        S.H2[t][i] = h2[i];
+    }
+    // back through layer 3 and the second ReLU, then layer 2 and the first ReLU
+    float dh2[PH];
+#pragma unroll
+    for (int i = 0; i < PH; ++i) {
+        float acc = 0.0f;
+        for (int b = 0; b < PO; ++b) acc = fmaf(S.P[OFF_W3 + b * PH + i], S.DZ[t][b], acc);
+        dh2[i] = h2[i] > 0.0f ? acc : 0.0f;
+        S.DH2[t][i] = dh2[i];
+    }
+#pragma unroll
+    for (int i = 0; i < PH; ++i) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int o2 = 0; o2 < PH; ++o2) acc = fmaf(S.P[OFF_W2 + o2 * PH + i], dh2[o2], acc);
+        S.DH1[t][i] = h1[i] > 0.0f ? acc : 0.0f;
+    }
+    __syncthreads();
+    // gradient contractions over this CTA's rays, scaled by 1 / B (mean loss)
+    const float sc = 1.0f / (float)B;
+    for (int e = threadIdx.x; e < NPAR; e += blockDim.x) {
+        float acc = 0.0f;
+        if (e < OFF_B1) {  // W1[o][f]: sum_r DH1[r][o] X[r][f]
+            const int o1 = e / PIN, f = e - o1 * PIN;
+            for (int rr = 0; rr < kRays; ++rr) acc = fmaf(S.DH1[rr][o1], S.X[rr][f], acc);
+        } else if (e < OFF_W2) {
+            const int o1 = e - OFF_B1;
+            for (int rr = 0; rr < kRays; ++rr) acc += S.DH1[rr][o1];
+        } else if (e < OFF_B2) {
+            const int k = e - OFF_W2, o2 = k / PH, i = k - o2 * PH;
+            for (int rr = 0; rr < kRays; ++rr) acc = fmaf(S.DH2[rr][o2], S.H1[rr][i], acc);
+        } else if (e < OFF_W3) {
+            const int o2 = e - OFF_B2;
+            for (int rr = 0; rr < kRays; ++rr) acc += S.DH2[rr][o2];
+        } else if (e < OFF_B3) {
+            const int k = e - OFF_W3, b = k / PH, i = k - b * PH;
+            for (int rr = 0; rr < kRays; ++rr) acc = fmaf(S.DZ[rr][b], S.H2[rr][i], acc);
+        } else {
+            const int b = e - OFF_B3;
+            for (int rr = 0; rr < kRays; ++rr) acc += S.DZ[rr][b];
+        }
+        atomicAdd(grad + e, acc * sc);
+    }
+    if (threadIdx.x < 32) {
+        float l = 0.0f;
+        for (int rr = threadIdx.x; rr < kRays; rr += 32) l += S.loss[rr];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+        if (threadIdx.x == 0) atomicAdd(loss, l * sc);
+    }
+}
+
+// Adam (Kingma and Ba) with bias correction; t counts from 1.  Clears the gradient.
+__global__ void k_prop_adam(float* __restrict__ P, float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int t, float lr, float b1, float b2, float eps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPAR) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+    P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    g[i] = 0.0f;
+}
+
+}  // namespace
+
+int proposal_param_count() { return NPAR; }
+
+constexpr size_t kInferSmem = sizeof(float) * (NPAR + kRays * (PIN + 1));
+
+cudaError_t launch_prop_infer(cudaStream_t s, const float* params, const float root_box[6], const float* ro,
+                              const float* rd, uint32_t n, float coverage, int max_bins, uint64_t* mask,
+                              uint8_t* fallback, unsigned long long* n_fallback, float* q_out) {
+    if (n == 0) return cudaSuccess;
+    k_prop_infer<<<(n + kRays - 1) / kRays, kRays, kInferSmem, s>>>(params, root_box[0], root_box[1], root_box[2],
+                                                           root_box[3], root_box[4], root_box[5], ro, rd, n,
+                                                           coverage, max_bins, mask, fallback, n_fallback, q_out);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_proposal() {
+    cudaError_t e = cudaFuncSetAttribute(k_prop_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_prop_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GradSmem));
+}
+
+cudaError_t launch_prop_grad(cudaStream_t s, const float* params, const float* ro, const float* rd,
+                             const float2* root, const float* targets, uint32_t n, uint32_t batch, uint64_t seed,
+                             uint64_t step, float* grad, float* loss) {
+    if (batch == 0) return cudaSuccess;
+    k_prop_grad<<<(batch + kRays - 1) / kRays, kRays, sizeof(GradSmem), s>>>(params, ro, rd, root, targets, n, batch,
+                                                                            seed, step, grad, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prop_adam(cudaStream_t s, float* P, float* g, float* m, float* v, int t, float lr) {
+    k_prop_adam<<<(NPAR + 255) / 256, 256, 0, s>>>(P, g, m, v, t, lr, 0.9f, 0.999f, 1e-8f);
+    return cudaGetLastError();
+}
+
+}  // namespace amnerf

@@ -12,6 +12,10 @@
 // (entry, exit) at crossing slot ray * maxc + k and counted in a per-CTA shared-memory
 // histogram that is flushed to the per-leaf totals with one atomic per touched leaf.
 // Traversal stops after maxc crossings (whole crossings are kept under the cap).
+// With the proposal sampler, a leaf crossing [t_in, t_out] is kept only when it
+// overlaps a kept depth bin [t0 + k w, t0 + (k + 1) w), w = (t1 - t0) / 64 of the
+// ray's root interval [t0, t1] (same FP32 operation order as the oracle); rays that
+// fell back keep every crossing.
 #include "amnerf_internal.h"
 
 namespace amnerf {
@@ -41,7 +45,9 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
                                                   uint32_t n, const DevNode* __restrict__ nodes, int maxc,
                                                   uint8_t* __restrict__ n_x, float2* __restrict__ xing,
                                                   uint16_t* __restrict__ xleaf, uint32_t* __restrict__ counts,
-                                                  int n_leaves, int* __restrict__ err) {
+                                                  int n_leaves, int* __restrict__ err,
+                                                  const uint64_t* __restrict__ mask,
+                                                  const uint8_t* __restrict__ fallback, float2* __restrict__ root_out) {
     extern __shared__ uint32_t s_cnt[];
     for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) s_cnt[i] = 0u;
     __syncthreads();
@@ -60,6 +66,17 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
         stack[sp++] = 0;
         int cnt = 0;
         const size_t base = (size_t)r * (size_t)maxc;
+        // proposal sampler: the root interval and this ray's kept depth bins
+        float r0 = 0.f, r1 = 0.f;
+        {
+            const float4 A = __ldg(&nodes[0].a);
+            const float4 B = __ldg(&nodes[0].b);
+            if (!slab(A, B, o, inv, r0, r1)) r0 = r1 = 0.f;
+            if (root_out) root_out[r] = make_float2(r0, r1);
+        }
+        const uint64_t kept_bins = (mask && !__ldg(fallback + r)) ? __ldg(mask + r) : 0ull;
+        const bool masked = mask && !__ldg(fallback + r);
+        const float bw = __fmul_rn(__fsub_rn(r1, r0), 0.015625f);  // bin width (t1 - t0) / 64
         while (sp > 0 && cnt < maxc) {
             const int nd = stack[--sp];
             const float4 A = __ldg(&nodes[nd].a);
@@ -69,6 +86,16 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
             const uint32_t meta = __float_as_uint(B.w);
             const int axis = (int)(meta & 3u) - 1;
             if (axis < 0) {
+                if (masked) {  // keep the crossing only if it overlaps a kept bin
+                    bool keep = false;
+                    for (uint64_t mm = kept_bins; mm && !keep; mm &= mm - 1) {
+                        const int k = __ffsll((long long)mm) - 1;
+                        const float lo = __fadd_rn(r0, __fmul_rn((float)k, bw));
+                        const float hi = __fadd_rn(r0, __fmul_rn((float)(k + 1), bw));
+                        keep = tin < hi && tout > lo;
+                    }
+                    if (!keep) continue;
+                }
                 const uint32_t leaf = meta >> 2;
                 xing[base + cnt] = make_float2(tin, tout);
                 xleaf[base + cnt] = (uint16_t)leaf;
@@ -101,12 +128,14 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
 
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
                             int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
-                            int n_leaves, int* err) {
+                            int n_leaves, int* err, const uint64_t* mask, const uint8_t* fallback,
+                            float2* root_out) {
     if (n == 0) return cudaSuccess;
     const int threads = 256;
     const unsigned blocks = (n + threads - 1) / threads;
     const size_t smem = sizeof(uint32_t) * (size_t)n_leaves;
-    k_traverse<<<blocks, threads, smem, s>>>(ro, rd, n, nodes, maxc, n_x, xing, xleaf, counts, n_leaves, err);
+    k_traverse<<<blocks, threads, smem, s>>>(ro, rd, n, nodes, maxc, n_x, xing, xleaf, counts, n_leaves, err, mask,
+                                             fallback, root_out);
     return cudaGetLastError();
 }
 

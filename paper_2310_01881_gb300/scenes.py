@@ -29,7 +29,7 @@ import numpy as np
 __all__ = [
     "Scene", "RenderConfig", "CONFIGS", "scene_for", "density_grid", "camera_rays",
     "view_rays", "params_per_leaf", "mlp_input_width", "leaf_mean_density",
-    "xavier_weights", "ray_subset",
+    "xavier_weights", "ray_subset", "proposal_init", "PROPOSAL_PARAMS",
 ]
 
 
@@ -255,3 +255,17 @@ def xavier_weights(seed: int, leaf_density: np.ndarray, width: int, hidden: int,
             parts += [W.ravel(), b]
         out[leaf] = np.concatenate(parts).astype(np.float32)
     return out.reshape(-1)
+
+
+PROPOSAL_PARAMS = 32 * 90 + 32 + 32 * 32 + 32 + 65 * 32 + 65
+
+
+def proposal_init(seed: int) -> np.ndarray:
+    """Xavier-uniform FP32 parameters of the proposal network (layers 90 -> 32 -> 32 ->
+    65; layout W1, b1, W2, b2, W3, b3, rows = outputs), zero biases."""
+    rng = np.random.default_rng([seed, 0x960905])
+    parts = []
+    for fo, fi in ((32, 90), (32, 32), (65, 32)):
+        a = math.sqrt(6.0 / (fi + fo))
+        parts += [rng.uniform(-a, a, size=(fo, fi)).ravel(), np.zeros(fo)]
+    return np.concatenate(parts).astype(np.float32)

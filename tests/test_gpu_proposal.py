@@ -1,0 +1,200 @@
+"""GPU proposal sampler (not in the paper) against the CPU oracle, and what training
+it gains over the method without it."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2310_01881_gb300 import scenes as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MASK64 = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2310_01881_gb300 import amnerf, build
+    build.build()
+    r = amnerf.Renderer(0)
+    yield r
+    r.close()
+
+
+def _dev(a, dtype=np.float32):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype)).cuda()
+
+
+def _c1(R, prec="fp32", seed=0):
+    cfg = S.CONFIGS["c1"]
+    grid = S.density_grid(S.scene_for("c1", seed), cfg.G)
+    R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    P_gpu = S.xavier_weights(seed, S.leaf_mean_density(grid, R.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    P_or = S.xavier_weights(seed, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    R.load_mlps(P_gpu, cfg.width, cfg.hidden, cfg.lx, cfg.ld, prec)
+    return cfg, tree, P_or
+
+
+def _targets(R, cfg, o, d):
+    from paper_2310_01881_gb300 import amnerf
+    n = len(o)
+    do, dd = _dev(o), _dev(d)
+    out = (torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"), torch.empty(n, device="cuda"))
+    tg = torch.empty((n, 65), device="cuda")
+    root = torch.empty((n, 2), device="cuda")
+    amnerf.amnerf_proposal_targets(R.ctx, do, dd, *out, tg, root, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term)
+    return do, dd, tg, root, out
+
+
+def test_targets_match_oracle_bins(R):
+    from paper_2310_01881_gb300 import amnerf
+    cfg, tree, P = _c1(R)
+    amnerf.amnerf_proposal_set(R.ctx, S.proposal_init(0))
+    o, d = S.view_rays(cfg, 0, 0)
+    _, _, tg, root, _ = _targets(R, cfg, o, d)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1, bins=True)
+    t0, t1, hit = O.root_interval(tree, o, d, mode=1)
+    rt = root.cpu().numpy()
+    np.testing.assert_array_equal(rt[:, 0], np.where(hit, t0, 0).astype(np.float32))
+    np.testing.assert_array_equal(rt[:, 1], np.where(hit, t1, 0).astype(np.float32))
+    got = tg.cpu().numpy().astype(np.float64)
+    ok = ref["ert_margin"] > 1e-3
+    assert np.abs(got - ref["bins"])[ok].max() <= 2e-5
+    np.testing.assert_allclose(got.sum(1), 1.0, atol=2e-6)
+
+
+def test_gradient_matches_fp64_backward(R):
+    from paper_2310_01881_gb300 import amnerf
+    cfg, tree, P = _c1(R)
+    params = S.proposal_init(3)
+    amnerf.amnerf_proposal_set(R.ctx, params)
+    o, d = S.view_rays(cfg, 0, 1, 32, 32)
+    do, dd, tg, root, _ = _targets(R, cfg, o, d)
+    loss, g = amnerf.amnerf_proposal_grad(R.ctx, do, dd, root, tg)
+    t0 = root.cpu().numpy()[:, 0].astype(np.float64)
+    l_ref, g_ref = O.prop_loss_grad(params.astype(np.float64), o, d, t0, tg.cpu().numpy().astype(np.float64))
+    assert loss == pytest.approx(l_ref, rel=1e-5)
+    err = np.abs(g.astype(np.float64) - g_ref)
+    assert np.linalg.norm(err) <= 1e-4 * np.linalg.norm(g_ref)
+    assert np.all(err <= 1e-6 + 1e-3 * np.abs(g_ref))
+
+
+def test_predictions_and_bin_selection_match_oracle(R):
+    from paper_2310_01881_gb300 import amnerf
+    cfg, tree, P = _c1(R)
+    params = S.proposal_init(5) * 3.0       # sharper distributions than at init
+    amnerf.amnerf_proposal_set(R.ctx, params)
+    o, d = S.view_rays(cfg, 0, 2, 48, 48)
+    n = len(o)
+    do, dd = _dev(o), _dev(d)
+    q = torch.empty((n, 65), device="cuda")
+    mask = torch.empty(n, dtype=torch.int64, device="cuda")
+    fb = torch.empty(n, dtype=torch.uint8, device="cuda")
+    for cov, mb in ((0.99, 16), (0.6, 64), (0.9, 8)):
+        amnerf.amnerf_proposal_predict(R.ctx, do, dd, q, mask, fb, coverage=cov, max_bins=mb)
+        t0, t1, hit = O.root_interval(tree, o, d, mode=1)
+        q_ref = O.prop_predict(params.astype(np.float64), o, d, np.where(hit, t0, 0.0))
+        qg = q.cpu().numpy().astype(np.float64)
+        assert np.abs(qg - q_ref).max() <= 2e-5
+        m_ref, f_ref = O.prop_select(q_ref, cov, mb)
+        mg = mask.cpu().numpy().view(np.uint64)
+        fg = fb.cpu().numpy().astype(np.int32)
+        f_ref = np.where(hit, f_ref, 0)
+        same = (mg == np.where(hit, m_ref, mg)) & (fg == f_ref)
+        assert same.mean() >= 0.99, (cov, mb, same.mean())   # the rest sit on FP32 ties
+
+
+def _splitmix_batch(seed, step, B, n):
+    """Ray indices of one training minibatch: splitmix64 of seed + golden * (step * 2^32
+    + step + i + 1) (Steele, Lea and Flood, 2014), modulo n."""
+    M = (1 << 64) - 1
+    out = np.empty(B, np.int64)
+    for i in range(B):
+        z = (seed + 0x9E3779B97F4A7C15 * (step * 0x100000001 + i + 1)) & M
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        z ^= z >> 31
+        out[i] = z % n
+    return out
+
+
+def test_one_adam_step_matches_oracle(R):
+    from paper_2310_01881_gb300 import amnerf
+    cfg, tree, P = _c1(R)
+    params = S.proposal_init(7)
+    amnerf.amnerf_proposal_set(R.ctx, params)
+    o, d = S.view_rays(cfg, 0, 3, 24, 24)
+    do, dd, tg, root, _ = _targets(R, cfg, o, d)
+    B, seed, lr = 300, 12345, 1e-3
+    losses = amnerf.amnerf_proposal_train(R.ctx, do, dd, root, tg, steps=1, batch=B, lr=lr, seed=seed)
+    P1, m1, v1, step = amnerf.amnerf_proposal_get(R.ctx)
+    assert step == 1
+    idx = _splitmix_batch(seed, 1, B, len(o))
+    t0 = root.cpu().numpy()[:, 0].astype(np.float64)
+    tgh = tg.cpu().numpy().astype(np.float64)
+    l_ref, g_ref = O.prop_loss_grad(params.astype(np.float64), o[idx], d[idx], t0[idx], tgh[idx])
+    assert losses[0] == pytest.approx(l_ref, rel=1e-5)
+    Pr = params.astype(np.float64).copy(); mr = np.zeros_like(Pr); vr = np.zeros_like(Pr)
+    O.prop_adam(Pr, g_ref, mr, vr, 1, lr=lr)
+    big = np.abs(g_ref) > 1e-5
+    np.testing.assert_allclose(P1[big], Pr[big], atol=1e-7 + 1e-3 * lr)
+    assert np.all(np.abs(P1 - Pr) <= 2 * lr + 1e-7)
+    np.testing.assert_allclose(m1, mr, atol=1e-6)
+
+
+def test_masked_render_matches_oracle_with_the_same_masks(R):
+    cfg, tree, P = _c1(R)
+    from paper_2310_01881_gb300 import amnerf
+    amnerf.amnerf_proposal_set(R.ctx, S.proposal_init(11) * 3.0)
+    o, d = S.view_rays(cfg, 0, 4)
+    for cov, mb in ((0.7, 64), (0.99, 16)):
+        rgb, depth, opac, dbg, st = R.render_debug(_dev(o), _dev(d), cfg.steps, cfg.cap, proposal=True,
+                                                   coverage=cov, max_bins=mb)
+        mask, fb = dbg["prop_mask"], dbg["prop_fallback"].astype(np.int32)
+        assert st["fallback_rays"] == int(fb.sum())
+        ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1,
+                       mask=mask, fallback=fb)
+        np.testing.assert_array_equal(dbg["n_x"].astype(np.int64) * cfg.steps, ref["n_gen"])
+        ok = ref["ert_margin"] > 1e-3
+        assert np.abs(rgb - ref["rgb"]).max(axis=1)[ok].max() <= 1e-5
+        assert np.abs(opac - ref["opacity"])[ok].max() <= 1e-5
+
+
+def test_training_gain_on_imbalanced_scene(R):
+    """Proposal trained on plain-rendered views of the 4096-leaf scene, evaluated on
+    held-out views: samples per ray against the plain sampler, image change against the
+    plain render, and the same for the untrained network."""
+    from paper_2310_01881_gb300 import amnerf
+    cfg = S.CONFIGS["c4"]
+    grid = S.density_grid(S.scene_for("c4", 0), cfg.G)
+    R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    Pw = S.xavier_weights(0, S.leaf_mean_density(grid, R.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    R.load_mlps(Pw, cfg.width, cfg.hidden, cfg.lx, cfg.ld, "bf16")
+    W, H = 192, 108
+    train = [S.view_rays(cfg, 0, 100 + v, W, H) for v in range(24)]
+    o_tr = np.concatenate([t[0] for t in train]); d_tr = np.concatenate([t[1] for t in train])
+    test = [S.view_rays(cfg, 0, 200 + v, W, H) for v in range(4)]
+    o_te = np.concatenate([t[0] for t in test]); d_te = np.concatenate([t[1] for t in test])
+    do, dd, tg, root, _ = _targets(R, cfg, o_tr, d_tr)
+    amnerf.amnerf_proposal_set(R.ctx, S.proposal_init(1))
+    dto, dtd = _dev(o_te), _dev(d_te)
+
+    def evaluate():
+        plain = R.render(dto, dtd, cfg.steps, cfg.cap, cfg.t_term, stats=True)
+        prop = R.render(dto, dtd, cfg.steps, cfg.cap, cfg.t_term, stats=True, proposal=True, coverage=0.99,
+                        max_bins=16)
+        a, b = plain[0].cpu().numpy(), prop[0].cpu().numpy()
+        mse = float(np.mean((a - b) ** 2))
+        return (plain[3]["samples_generated"] / len(o_te), prop[3]["samples_generated"] / len(o_te),
+                10 * np.log10(1.0 / max(mse, 1e-30)), prop[3]["fallback_rays"] / len(o_te))
+
+    spr_plain, spr_u, psnr_u, fb_u = evaluate()
+    losses = amnerf.amnerf_proposal_train(R.ctx, do, dd, root, tg, steps=1500, batch=4096, lr=3e-3, seed=7)
+    _, spr_t, psnr_t, fb_t = evaluate()
+    print(f"proposal gain: spr plain {spr_plain:.1f}; untrained {spr_u:.1f} (PSNR vs plain {psnr_u:.1f} dB, "
+          f"fallback {fb_u:.2f}); trained {spr_t:.1f} (PSNR vs plain {psnr_t:.1f} dB, fallback {fb_t:.2f}); "
+          f"loss {losses[:20].mean():.3f} -> {losses[-20:].mean():.3f}")
+    assert losses[-50:].mean() < 0.8 * losses[:50].mean()
+    assert spr_t < spr_plain
+    assert psnr_t > psnr_u or spr_t < spr_u
