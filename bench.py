@@ -447,16 +447,18 @@ def run_c4(args):
 
 
 def run_c5(args):
-    """Learned proposal on the imbalanced scene: trained on plain-rendered views,
-    evaluated on held-out views against the plain sampler and the FP64 oracle."""
+    """Learned proposal on the config-1 scene with BF16 leaves (optionally with every
+    density scaled): trained on plain-rendered views, evaluated on held-out views
+    against the plain sampler, the FP64 oracle, and the oracle's own bound -- the
+    samples per ray when the kept bins come from the true (plain-render) weights."""
     import torch
 
     from paper_2310_01881_gb300 import amnerf, build
 
     torch.cuda.set_device(0)
     build.build()
-    cfg = S.CONFIGS["c4"]
-    grid = S.density_grid(S.scene_for(cfg.scene, 0), cfg.G)
+    cfg = S.CONFIGS["c1"]
+    grid = S.density_grid(S.scene_for(cfg.scene, 0), cfg.G) * np.float32(args.density_scale)
     R = amnerf.Renderer(0)
     R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
     P = S.xavier_weights(0, S.leaf_mean_density(grid, R.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
@@ -465,10 +467,12 @@ def run_c5(args):
     tr = [S.view_rays(cfg, 0, 1000 + v, tw, th) for v in range(n_train_views)]
     o_tr = torch.from_numpy(np.concatenate([t[0] for t in tr])).cuda()
     d_tr = torch.from_numpy(np.concatenate([t[1] for t in tr])).cuda()
+    del tr
     n_tr = o_tr.shape[0]
     out_tr = (torch.empty((n_tr, 3), device="cuda"), torch.empty(n_tr, device="cuda"), torch.empty(n_tr, device="cuda"))
     tg = torch.empty((n_tr, 65), device="cuda")
     root = torch.empty((n_tr, 2), device="cuda")
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     amnerf.amnerf_proposal_targets(R.ctx, o_tr, d_tr, *out_tr, tg, root, steps=cfg.steps, cap=cfg.cap,
                                    t_term=cfg.t_term)
@@ -480,57 +484,80 @@ def run_c5(args):
     t_train = time.perf_counter() - t0
     del o_tr, d_tr, out_tr, tg, root
     torch.cuda.empty_cache()
-    views = args.views or cfg.views
-    px_w, px_h = (args.px, args.px) if args.px else (cfg.px_w, cfg.px_h)
+    views = args.views or 16
+    px_w, px_h = (args.px, args.px) if args.px else (1920, 1080)
     te = [S.view_rays(cfg, 0, 2000 + v, px_w, px_h) for v in range(views)]
     o_np = np.concatenate([t[0] for t in te]); d_np = np.concatenate([t[1] for t in te])
+    del te
     n = len(o_np)
     o = torch.from_numpy(o_np).cuda(); d = torch.from_numpy(d_np).cuda()
     out = (torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"), torch.empty(n, device="cuda"))
     stream = torch.cuda.current_stream()
+    points = [(0.99, 64), (0.99, 16), (0.95, 64)]   # (coverage, max_bins); the first is the headline
 
-    def timed(prop):
+    def timed(prop, cov=0.99, mb=64):
+        kw = dict(out=out, proposal=prop, coverage=cov, max_bins=mb)
         for _ in range(args.warmup):
-            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, proposal=prop)
+            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, **kw)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, proposal=prop)
+            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
-        *_, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, proposal=prop, stats=True)
+        *_, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, **kw)
         return e0.elapsed_time(e1) / args.steps, st, out[0].cpu().numpy().astype(np.float64)
 
     with ClockSampler(0) as clk:
         ms_plain, st_plain, rgb_plain = timed(False)
-        ms_prop, st_prop, rgb_prop = timed(True)
+        runs = [timed(True, cov, mb) for cov, mb in points]
     import oracle as O
     tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
     P_or = S.xavier_weights(0, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
     idx = S.ray_subset(n, args.psnr_rays // 4, 11)
+    threads = os.cpu_count() or 1
     ref = O.render(tree, P_or, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps, cfg.cap,
-                   cfg.t_term, mode=0, threads=os.cpu_count() or 1)
+                   cfg.t_term, mode=0, threads=threads, bins=True)
 
     def psnr(a, b):
         return round(10 * np.log10(1.0 / max(float(np.mean((a - b) ** 2)), 1e-30)), 2)
 
-    p_plain, p_prop = psnr(rgb_plain[idx], ref["rgb"]), psnr(rgb_prop[idx], ref["rgb"])
+    def spr(st):
+        return round(st["samples_generated"] / n, 3)
+
+    p_plain = psnr(rgb_plain[idx], ref["rgb"])
+    spr_plain_or = float(ref["n_gen"].mean())
+    res = []
+    for (cov, mb), (ms, st, rgb) in zip(points, runs):
+        m, fb = O.prop_select(ref["bins"], cov, mb)
+        bound = O.render(tree, P_or, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps,
+                         cfg.cap, cfg.t_term, mode=0, threads=threads, mask=m, fallback=fb.astype(np.int32))
+        p = psnr(rgb[idx], ref["rgb"])
+        res.append({"coverage": cov, "max_bins": mb, "Mrays/s": round(n / (ms * 1e-3) / 1e6, 3),
+                    "ms": round(ms, 3), "samples_per_ray": spr(st), "spr_reduction": round(spr(st_plain) / spr(st), 3),
+                    "fallback_frac": round(st["fallback_rays"] / n, 4), "psnr_vs_plain": psnr(rgb, rgb_plain),
+                    "psnr_vs_fp64": p, "delta_psnr_vs_fp64_db": round(p_plain - p, 2),
+                    "true_weight_bound": {"spr_reduction": round(spr_plain_or / max(float(bound["n_gen"].mean()), 1e-9),
+                                                                 3),
+                                          "fallback_frac": round(float(fb.mean()), 4),
+                                          "psnr_vs_plain_fp64": psnr(bound["rgb"], ref["rgb"])}})
+    head = res[0]
     line = {
-        "metric": "Mrays/s and samples per ray (c5 learned proposal vs plain sampler)",
-        "value": round(n / (ms_prop * 1e-3) / 1e6, 3), "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_prop, 3), "higher_is_better": True, "dtype": "bf16",
+        "metric": "Mrays/s and samples per ray (learned proposal vs plain sampler)",
+        "value": head["Mrays/s"], "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "dtype": "bf16",
         "data": "synthetic",
-        "config": {"workload": f"c4 scene (4096 leaves, 4x64 BF16 MLPs); proposal trained on {n_train_views} views "
-                               f"at {tw}x{th}, evaluated on {views} held-out views at {px_w}x{px_h}",
-                   "rays_per_step": n, "coverage": 0.99, "max_bins": 16},
+        "config": {"workload": f"config-1 scene x{args.density_scale:g} density (<=16 leaves, 2x32 BF16 MLPs); "
+                               f"proposal trained on {n_train_views} views at {tw}x{th}, evaluated on {views} "
+                               f"held-out views at {px_w}x{px_h}",
+                   "rays_per_step": n, "density_scale": args.density_scale, "oracle_rays": len(idx)},
         "plain": {"Mrays/s": round(n / (ms_plain * 1e-3) / 1e6, 3), "ms": round(ms_plain, 3),
-                  "samples_per_ray": round(st_plain["samples_generated"] / n, 3), "psnr_vs_fp64": p_plain},
-        "proposal": {"Mrays/s": round(n / (ms_prop * 1e-3) / 1e6, 3), "ms": round(ms_prop, 3),
-                     "samples_per_ray": round(st_prop["samples_generated"] / n, 3), "psnr_vs_fp64": p_prop,
-                     "psnr_vs_plain": psnr(rgb_prop, rgb_plain), "fallback_frac": round(st_prop["fallback_rays"] / n, 4)},
-        "spr_reduction": round(st_plain["samples_generated"] / max(st_prop["samples_generated"], 1), 3),
-        "delta_psnr_vs_fp64_db": round(p_plain - p_prop, 2),
+                  "samples_per_ray": spr(st_plain), "psnr_vs_fp64": p_plain,
+                  "composited_frac": round(st_plain["samples_composited"] / max(st_plain["samples_generated"], 1), 4)},
+        "proposal": res,
+        "spr_reduction": head["spr_reduction"],
+        "delta_psnr_vs_fp64_db": head["delta_psnr_vs_fp64_db"],
         "training": {"rays": n_tr, "steps": args.train_steps, "batch": 8192, "lr": 3e-3,
                      "loss_first": round(float(losses[:50].mean()), 4), "loss_last": round(float(losses[-50:].mean()), 4),
                      "targets_s": round(t_targets, 2), "train_s": round(t_train, 2)},
@@ -590,6 +617,7 @@ def main():
     ap.add_argument("--views", type=int, default=None, help="views per GPU (default: the config's)")
     ap.add_argument("--train-views", type=int, default=64, help="c5: plain-rendered training views")
     ap.add_argument("--train-steps", type=int, default=3000, help="c5: Adam steps")
+    ap.add_argument("--density-scale", type=float, default=1.0, help="c5: factor on every density of the scene")
     ap.add_argument("--px", type=int, default=None, help="square image size (default: the config's)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -244,6 +244,13 @@ AMNERF_API amnerf_status amnerf_render_host(amnerf_ctx *ctx, const float *rays_o
  * E_TIMEOUT when a bounded device wait ran out, E_CUDA on an asynchronous CUDA error. */
 AMNERF_API amnerf_status amnerf_sync(amnerf_ctx *ctx);
 
+/* Failure-detection self-test (no counterpart in the paper): launches a kernel that
+ * waits, with the same bounded-wait code as the tensor-core network kernel, on an
+ * mbarrier phase that nothing completes.  The wait gives up after `cycles` SM clock
+ * cycles (1 .. 4e9), records a timeout in the context's status word and returns, so
+ * the call returns AMNERF_E_TIMEOUT and the context stays usable. */
+AMNERF_API amnerf_status amnerf_selftest_wait(amnerf_ctx *ctx, uint64_t cycles);
+
 /* Record per-stage CUDA-event timing in later renders (amnerf_stats.ms). */
 AMNERF_API amnerf_status amnerf_set_timing(amnerf_ctx *ctx, int enable);
 

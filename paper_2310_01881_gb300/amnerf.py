@@ -101,6 +101,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                  ctypes.POINTER(amnerf_debug), V], S),
         "amnerf_render_host": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V, V], S),
         "amnerf_sync": ([V], S),
+        "amnerf_selftest_wait": ([V, ctypes.c_uint64], S),
         "amnerf_group_by_leaf_static": ([V, V, L, I, I, V, V, V, V], S),
         "amnerf_proposal_set": ([V, V, V, V, I], S),
         "amnerf_proposal_get": ([V, V, V, V, ctypes.POINTER(I)], S),
@@ -328,6 +329,11 @@ def amnerf_proposal_predict(ctx, o, d, probs, mask, fallback, coverage: float = 
     st = load().amnerf_proposal_predict(ctx, _ptr(o), _ptr(d), o.shape[0], coverage, max_bins, _ptr(probs),
                                         _ptr(mask), _ptr(fallback))
     _check(ctx, st, "amnerf_proposal_predict")
+
+
+def amnerf_selftest_wait(ctx, cycles: int) -> int:
+    """Run the bounded-wait self-test; returns the status code (E_TIMEOUT expected)."""
+    return load().amnerf_selftest_wait(ctx, cycles)
 
 
 def amnerf_sync(ctx) -> None:

@@ -76,6 +76,8 @@ cudaError_t launch_mlp_tc(cudaStream_t s, const MlpArgs& a, int grid, int prec);
 // kernel supports for this shape; called at weight-load time, outside any capture.
 cudaError_t prepare_mlp_tc(int width, int hidden, int k0, int prec, int* max_groups);
 cudaError_t prepare_mlp_simt(int width, int hidden, int k0);
+// Failure-detection self-test of the bounded device waits (see amnerf_selftest_wait).
+cudaError_t launch_wait_selftest(cudaStream_t s, unsigned long long limit, int* err);
 size_t tc_leaf_stride_bytes(int width, int hidden, int k0, int prec);
 size_t simt_leaf_stride_floats(int width, int hidden, int k0);
 

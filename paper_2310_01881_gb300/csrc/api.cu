@@ -765,6 +765,13 @@ amnerf_status amnerf_autotune(amnerf_ctx* ctx, const float* ro, const float* rd,
     return amnerf_sync(ctx);
 }
 
+amnerf_status amnerf_selftest_wait(amnerf_ctx* ctx, uint64_t cycles) {
+    if (!ctx || cycles == 0 || cycles > 4000000000ull) return fail(ctx, AMNERF_E_INVAL, "cycles must be in [1, 4e9]");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(launch_wait_selftest(ctx->stream, (unsigned long long)cycles, ctx->d_err), "self-test launch");
+    return amnerf_sync(ctx);
+}
+
 amnerf_status amnerf_sync(amnerf_ctx* ctx) {
     if (!ctx) return AMNERF_E_INVAL;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");

@@ -131,11 +131,12 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t phase) {
 }
 
 // Bounded wait on an mbarrier phase; false when the deadline passed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase,
+                                                  unsigned long long limit = kWaitCycles) {
     if (mbar_test(bar, phase)) return true;
     const unsigned long long t0 = clock64();
     while (!mbar_test(bar, phase)) {
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -698,6 +699,19 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
+// Failure-detection self-test: waits, with the network kernel's bounded-wait helper,
+// on an mbarrier phase that nothing completes; the wait runs out after `limit`
+// cycles and the kernel records a timeout in the status word and returns.
+__global__ void k_wait_selftest(unsigned long long limit, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(smem_u32(&bar), 0, limit)) atomicCAS(err, 0, kDevErrTimeout);
+}
+
 template <int W, bool F8>
 int max_groups_for(int hidden, int max_smem) {
     constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
@@ -780,6 +794,11 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
         for (int n = 0; n < 4; ++n) wo[(size_t)k * 4 + n] = w[(size_t)n * width + k];
     w += 4 * width;
     for (int n = 0; n < 4; ++n) bias[(size_t)hidden * width + n] = w[n];
+}
+
+cudaError_t launch_wait_selftest(cudaStream_t s, unsigned long long limit, int* err) {
+    k_wait_selftest<<<1, 32, 0, s>>>(limit, err);
+    return cudaGetLastError();
 }
 
 cudaError_t prepare_mlp_tc(int width, int hidden, int k0, int prec, int* max_groups) {

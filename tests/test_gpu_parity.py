@@ -436,3 +436,18 @@ def test_sample_slots_beyond_32_bits(R):
     assert _psnr(last[idx], ref["rgb"]) >= 45.0
     del do, dd, rgb, depth, opac
     torch.cuda.empty_cache()
+
+
+def test_bounded_device_wait_reports_timeout_and_context_survives(R):
+    """Failure detection without a fault: a device wait that nothing completes gives up
+    after its cycle limit, the call reports E_TIMEOUT, and the next render works."""
+    from paper_2310_01881_gb300 import amnerf
+    st = amnerf.amnerf_selftest_wait(R.ctx, 20_000_000)   # ~10 ms at 2 GHz
+    assert st == amnerf.E_TIMEOUT
+    amnerf.amnerf_sync(R.ctx)                              # status word was cleared
+    cfg = S.CONFIGS["c1"]
+    _setup(R, cfg, 0, prec="bf16")
+    o, d = _rays(cfg, 0, 1, 16, 16)
+    rgb = R.render(_dev(o), _dev(d), cfg.steps, cfg.cap)[0]
+    torch.cuda.synchronize()
+    assert torch.isfinite(rgb).all()

@@ -161,40 +161,43 @@ def test_masked_render_matches_oracle_with_the_same_masks(R):
         assert np.abs(opac - ref["opacity"])[ok].max() <= 1e-5
 
 
-def test_training_gain_on_imbalanced_scene(R):
-    """Proposal trained on plain-rendered views of the 4096-leaf scene, evaluated on
-    held-out views: samples per ray against the plain sampler, image change against the
-    plain render, and the same for the untrained network."""
+def test_training_gain_on_dense_config1_scene(R):
+    """Proposal trained on plain-rendered views of the config-1 scene with every density
+    x10 (BF16 leaves), evaluated on held-out views at coverage 0.95: samples per ray
+    against the plain sampler, image change against the plain render, and the same for
+    the untrained network.  (At x1 the leaves are too transparent for any kept-bin
+    choice to drop much: the oracle's true-weight bound is ~1.03x there.)"""
     from paper_2310_01881_gb300 import amnerf
-    cfg = S.CONFIGS["c4"]
-    grid = S.density_grid(S.scene_for("c4", 0), cfg.G)
+    cfg = S.CONFIGS["c1"]
+    grid = S.density_grid(S.scene_for("c1", 0), cfg.G) * np.float32(10.0)
     R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
     Pw = S.xavier_weights(0, S.leaf_mean_density(grid, R.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
     R.load_mlps(Pw, cfg.width, cfg.hidden, cfg.lx, cfg.ld, "bf16")
-    W, H = 192, 108
-    train = [S.view_rays(cfg, 0, 100 + v, W, H) for v in range(24)]
+    train = [S.view_rays(cfg, 0, 1000 + v, 160, 90) for v in range(64)]
     o_tr = np.concatenate([t[0] for t in train]); d_tr = np.concatenate([t[1] for t in train])
-    test = [S.view_rays(cfg, 0, 200 + v, W, H) for v in range(4)]
+    test = [S.view_rays(cfg, 0, 2000 + v, 240, 135) for v in range(8)]
     o_te = np.concatenate([t[0] for t in test]); d_te = np.concatenate([t[1] for t in test])
     do, dd, tg, root, _ = _targets(R, cfg, o_tr, d_tr)
     amnerf.amnerf_proposal_set(R.ctx, S.proposal_init(1))
     dto, dtd = _dev(o_te), _dev(d_te)
+    n = len(o_te)
 
     def evaluate():
         plain = R.render(dto, dtd, cfg.steps, cfg.cap, cfg.t_term, stats=True)
-        prop = R.render(dto, dtd, cfg.steps, cfg.cap, cfg.t_term, stats=True, proposal=True, coverage=0.99,
-                        max_bins=16)
+        prop = R.render(dto, dtd, cfg.steps, cfg.cap, cfg.t_term, stats=True, proposal=True, coverage=0.95,
+                        max_bins=64)
         a, b = plain[0].cpu().numpy(), prop[0].cpu().numpy()
         mse = float(np.mean((a - b) ** 2))
-        return (plain[3]["samples_generated"] / len(o_te), prop[3]["samples_generated"] / len(o_te),
-                10 * np.log10(1.0 / max(mse, 1e-30)), prop[3]["fallback_rays"] / len(o_te))
+        return (plain[3]["samples_generated"] / n, prop[3]["samples_generated"] / n,
+                10 * np.log10(1.0 / max(mse, 1e-30)), prop[3]["fallback_rays"] / n)
 
     spr_plain, spr_u, psnr_u, fb_u = evaluate()
-    losses = amnerf.amnerf_proposal_train(R.ctx, do, dd, root, tg, steps=1500, batch=4096, lr=3e-3, seed=7)
+    losses = amnerf.amnerf_proposal_train(R.ctx, do, dd, root, tg, steps=3000, batch=8192, lr=3e-3, seed=7)
     _, spr_t, psnr_t, fb_t = evaluate()
-    print(f"proposal gain: spr plain {spr_plain:.1f}; untrained {spr_u:.1f} (PSNR vs plain {psnr_u:.1f} dB, "
-          f"fallback {fb_u:.2f}); trained {spr_t:.1f} (PSNR vs plain {psnr_t:.1f} dB, fallback {fb_t:.2f}); "
-          f"loss {losses[:20].mean():.3f} -> {losses[-20:].mean():.3f}")
+    print(f"proposal gain: spr plain {spr_plain:.2f}; untrained {spr_u:.2f} (PSNR vs plain {psnr_u:.1f} dB, "
+          f"fallback {fb_u:.2f}); trained {spr_t:.2f} (PSNR vs plain {psnr_t:.1f} dB, fallback {fb_t:.2f}); "
+          f"loss {losses[:50].mean():.3f} -> {losses[-50:].mean():.3f}")
     assert losses[-50:].mean() < 0.8 * losses[:50].mean()
-    assert spr_t < spr_plain
-    assert psnr_t > psnr_u or spr_t < spr_u
+    assert spr_t <= 0.9 * spr_plain
+    assert psnr_t >= 38.0
+    assert psnr_t > psnr_u + 3.0 or spr_t < spr_u
