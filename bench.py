@@ -506,7 +506,9 @@ def run_c5(args):
             R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
+        amnerf.amnerf_set_timing(R.ctx, True)
         *_, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, **kw)
+        amnerf.amnerf_set_timing(R.ctx, False)
         return e0.elapsed_time(e1) / args.steps, st, out[0].cpu().numpy().astype(np.float64)
 
     with ClockSampler(0) as clk:
@@ -535,7 +537,9 @@ def run_c5(args):
                          cfg.cap, cfg.t_term, mode=0, threads=threads, mask=m, fallback=fb.astype(np.int32))
         p = psnr(rgb[idx], ref["rgb"])
         res.append({"coverage": cov, "max_bins": mb, "Mrays/s": round(n / (ms * 1e-3) / 1e6, 3),
-                    "ms": round(ms, 3), "samples_per_ray": spr(st), "spr_reduction": round(spr(st_plain) / spr(st), 3),
+                    "ms": round(ms, 3), "stage_ms": [round(x, 3) for x in st["ms"]],
+                    "proposal_ms": round(st["proposal_ms"], 3),
+                    "samples_per_ray": spr(st), "spr_reduction": round(spr(st_plain) / spr(st), 3),
                     "fallback_frac": round(st["fallback_rays"] / n, 4), "psnr_vs_plain": psnr(rgb, rgb_plain),
                     "psnr_vs_fp64": p, "delta_psnr_vs_fp64_db": round(p_plain - p, 2),
                     "true_weight_bound": {"spr_reduction": round(spr_plain_or / max(float(bound["n_gen"].mean()), 1e-9),
@@ -553,6 +557,7 @@ def run_c5(args):
                                f"held-out views at {px_w}x{px_h}",
                    "rays_per_step": n, "density_scale": args.density_scale, "oracle_rays": len(idx)},
         "plain": {"Mrays/s": round(n / (ms_plain * 1e-3) / 1e6, 3), "ms": round(ms_plain, 3),
+                  "stage_ms": [round(x, 3) for x in st_plain["ms"]],
                   "samples_per_ray": spr(st_plain), "psnr_vs_fp64": p_plain,
                   "composited_frac": round(st_plain["samples_composited"] / max(st_plain["samples_generated"], 1), 4)},
         "proposal": res,

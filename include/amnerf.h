@@ -142,6 +142,7 @@ typedef struct {
     uint64_t tiles;               /* network tiles of 128 samples launched */
     uint64_t fallback_rays;       /* proposal sampler: rays that used the plain sampler */
     float ms[4];                  /* stage times: traverse, group, network, composite */
+    float proposal_ms;            /* proposal inference (part of ms[0]); 0 without the proposal */
 } amnerf_stats;
 
 /* Optional copies of the intermediate results of one render (all DEVICE pointers

@@ -63,12 +63,12 @@ class amnerf_tuning(ctypes.Structure):
 class amnerf_stats(ctypes.Structure):
     _fields_ = [("rays", ctypes.c_uint64), ("crossings", ctypes.c_uint64), ("samples_generated", ctypes.c_uint64),
                 ("samples_composited", ctypes.c_uint64), ("tiles", ctypes.c_uint64),
-                ("fallback_rays", ctypes.c_uint64), ("ms", ctypes.c_float * 4)]
+                ("fallback_rays", ctypes.c_uint64), ("ms", ctypes.c_float * 4), ("proposal_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {"rays": self.rays, "crossings": self.crossings, "samples_generated": self.samples_generated,
                 "samples_composited": self.samples_composited, "tiles": self.tiles,
-                "fallback_rays": self.fallback_rays, "ms": list(self.ms)}
+                "fallback_rays": self.fallback_rays, "ms": list(self.ms), "proposal_ms": self.proposal_ms}
 
 
 class amnerf_debug(ctypes.Structure):

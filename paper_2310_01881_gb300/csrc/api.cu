@@ -62,7 +62,7 @@ struct amnerf_ctx {
     float2* d_root = nullptr;
     // timing
     bool timing = false;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -235,7 +235,7 @@ amnerf_status amnerf_create(amnerf_ctx** out, int device, void* cuda_stream) {
         amnerf_destroy(ctx);
         return e == cudaErrorMemoryAllocation ? AMNERF_E_NOMEM : AMNERF_E_CUDA;
     }
-    for (int i = 0; i < 5; ++i) cudaEventCreate(&ctx->ev[i]);
+    for (int i = 0; i < 6; ++i) cudaEventCreate(&ctx->ev[i]);
     *out = ctx;
     return AMNERF_OK;
 }
@@ -271,7 +271,7 @@ void amnerf_destroy(amnerf_ctx* ctx) {
     dfree(ctx->d_mask);
     dfree(ctx->d_fallback);
     dfree(ctx->d_root);
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 6; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     delete ctx;
 }
@@ -401,6 +401,7 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         CK(launch_prop_infer(s, ctx->d_prop, box, ro, rd, nn, p->coverage, p->max_bins, ctx->d_mask, ctx->d_fallback,
                              reinterpret_cast<unsigned long long*>(ctx->d_stats + 3), nullptr),
            "proposal launch");
+        if (ctx->timing) cudaEventRecord(ctx->ev[5], s);
         mask = ctx->d_mask;
         fallback = ctx->d_fallback;
     }
@@ -513,6 +514,8 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
             if (ctx->timing) cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]);
             stats->ms[i] = ms;
         }
+        stats->proposal_ms = 0.f;
+        if (ctx->timing && mask) cudaEventElapsedTime(&stats->proposal_ms, ctx->ev[0], ctx->ev[5]);
         int herr = 0;
         CK(cudaMemcpy(&herr, ctx->d_err, sizeof herr, cudaMemcpyDeviceToHost), "status copy");
         if (herr) {

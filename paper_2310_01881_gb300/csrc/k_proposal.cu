@@ -10,17 +10,20 @@
 // entropy against the plain renderer's binned compositing weights with Adam.
 //
 // Kernels:
-//   k_prop_infer   thread per ray: root slab test (the traversal's FP32 operation
-//                  order), encoding, forward pass (weights in shared memory, read as
-//                  broadcasts), softmax, then the kept bins: bins by decreasing mass
-//                  (ties to the lower index) until the mass reaches `coverage` (the
-//                  background counts toward it); more than max_bins depth bins ->
-//                  fallback to the plain sampler.
+//   k_prop_infer   persistent CTAs over tiles of 128 rays: per ray the root slab test
+//                  (the traversal's FP32 operation order) and the encoding; per tile
+//                  the three layers as register-blocked FP32 products from shared
+//                  memory; per ray the softmax and the kept bins: bins by decreasing
+//                  mass (ties to the lower index) until the mass reaches `coverage`
+//                  (the background counts toward it); more than max_bins depth bins
+//                  -> fallback to the plain sampler.
 //   k_prop_grad    one CTA per 128 rays: each thread runs its ray forward and
 //                  backward and leaves its activations and deltas in shared memory;
 //                  the CTA then forms the gradient contractions (sum over its rays of
 //                  delta x activation) and adds them with one atomic per parameter.
 //   k_prop_adam    elementwise Adam update, then clears the gradient.
+#include <cstring>
+
 #include "amnerf_internal.h"
 
 namespace amnerf {
@@ -51,23 +54,24 @@ __device__ __forceinline__ bool root_slab(const float* box, const float o[3], co
     return x > e;
 }
 
-// The 90 input features of one ray, in the oracle's order.
+// The 90 input features of one ray, in the oracle's order; feature f goes to x[f * S].
+template <int S>
 __device__ __forceinline__ void prop_features(const float o[3], const float d[3], float t0, float* x) {
     float e[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) e[a] = __fadd_rn(o[a], __fmul_rn(t0, d[a]));
 #pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] = e[a];
+    for (int a = 0; a < 3; ++a) x[a * S] = e[a];
 #pragma unroll
     for (int k = 0; k < 10; ++k)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) sincospif(e[a] * (float)(1 << k), &x[3 + 6 * k + a], &x[6 + 6 * k + a]);
+        for (int a = 0; a < 3; ++a) sincospif(e[a] * (float)(1 << k), &x[(3 + 6 * k + a) * S], &x[(6 + 6 * k + a) * S]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) x[63 + a] = d[a];
+    for (int a = 0; a < 3; ++a) x[(63 + a) * S] = d[a];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) sincospif(d[a] * (float)(1 << k), &x[66 + 6 * k + a], &x[69 + 6 * k + a]);
+        for (int a = 0; a < 3; ++a) sincospif(d[a] * (float)(1 << k), &x[(66 + 6 * k + a) * S], &x[(69 + 6 * k + a) * S]);
 }
 
 // Forward pass from features in shared memory row xr (stride 1) with parameters in
@@ -110,72 +114,232 @@ __device__ __forceinline__ void prop_forward(const float* __restrict__ P, const 
     for (int o = 0; o < PO; ++o) q[o] *= inv;
 }
 
-__global__ void __launch_bounds__(kRays) k_prop_infer(const float* __restrict__ params, float b0, float b1, float b2,
-                                                      float b3, float b4, float b5, const float* __restrict__ ro,
-                                                      const float* __restrict__ rd, uint32_t n, float coverage,
-                                                      int max_bins, uint64_t* __restrict__ mask,
-                                                      uint8_t* __restrict__ fallback,
-                                                      unsigned long long* __restrict__ n_fallback,
-                                                      float* __restrict__ q_out) {
-    extern __shared__ __align__(16) uint8_t smraw[];
-    float* P = reinterpret_cast<float*>(smraw);
-    float (*X)[PIN + 1] = reinterpret_cast<float (*)[PIN + 1]>(P + NPAR);
-    for (int i = threadIdx.x; i < NPAR; i += blockDim.x) P[i] = params[i];
-    const uint32_t r = blockIdx.x * kRays + threadIdx.x;
-    float o[3] = {0.f, 0.f, 0.f}, d[3] = {1.f, 0.f, 0.f}, t0 = 0.f, t1 = 0.f;
-    bool hit = false;
-    if (r < n) {
+// ---- inference ---------------------------------------------------------------------
+// Persistent CTAs over tiles of kRays rays.  Each layer is a (kRays x 32) x K FP32
+// product formed from shared memory: activations are stored feature-major
+// ([feature][ray]) and weights transposed ([in][out]), so a thread's 4-ray x
+// 8-output register block takes one 16-byte activation load and two 16-byte weight
+// loads per input feature for 32 FMAs.  Every output is accumulated from its bias
+// over the inputs in order, the oracle's order.
+constexpr int kW3ld = 68;  // padded row of W3^T (65 used)
+struct InferSmem {
+    float W1t[PIN][PH];
+    float W2t[PH][PH];
+    float W3t[PH][kW3ld];
+    float b1[PH], b2[PH], b3[kW3ld];
+    float X[PIN][kRays];  // features; after the first layer, the logits / q [PO][kRays]
+    float H1[PH][kRays];
+    float H2[PH][kRays];
+};
+static_assert(PO <= PIN, "logits alias the feature rows");
+
+// (a * b0 + c0, a * b1 + c1) with one packed FP32 instruction; each half is an
+// ordinary correctly rounded fused multiply-add.
+__device__ __forceinline__ float2 fma_f32x2(float a, float2 b, float2 c) {
+    const float2 aa = make_float2(a, a);
+    unsigned long long ua, ub, uc, ud;
+    memcpy(&ua, &aa, 8);
+    memcpy(&ub, &b, 8);
+    memcpy(&uc, &c, 8);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(ud) : "l"(ua), "l"(ub), "l"(uc));
+    float2 d;
+    memcpy(&d, &ud, 8);
+    return d;
+}
+
+// out[ob + c][r] = act(bias[ob + c] + sum_k Wt[k][ob + c] in[k][r]) for 32 outputs c.
+template <int K, int LDW, bool RELU>
+__device__ __forceinline__ void tile_layer(const float (*in)[kRays], const float* Wt, const float* bias, int ob,
+                                           float (*out)[kRays]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = warp * 32 + (lane & 7) * 4;
+    const int c0 = ob + (lane >> 3) * 8;
+    float acc[4][8];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = __ldg(ro + 3 * (size_t)r + a);
-            d[a] = __ldg(rd + 3 * (size_t)r + a);
+    for (int j = 0; j < 8; ++j) {
+        const float bj = bias[c0 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i][j] = bj;
+    }
+    float2 acc2[4][4];  // (output 2p, output 2p + 1) of ray i
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc2[i][p] = make_float2(acc[i][2 * p], acc[i][2 * p + 1]);
+#pragma unroll 3
+    for (int k = 0; k < K; ++k) {
+        const float4 x = *reinterpret_cast<const float4*>(&in[k][r0]);
+        const float4 wa = *reinterpret_cast<const float4*>(Wt + k * LDW + c0);
+        const float4 wb = *reinterpret_cast<const float4*>(Wt + k * LDW + c0 + 4);
+        const float xv[4] = {x.x, x.y, x.z, x.w};
+        const float2 wp[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
+                              make_float2(wb.z, wb.w)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) acc2[i][p] = fma_f32x2(xv[i], wp[p], acc2[i][p]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            acc[i][2 * p] = acc2[i][p].x;
+            acc[i][2 * p + 1] = acc2[i][p].y;
         }
-        const float box[6] = {b0, b1, b2, b3, b4, b5};
-        hit = root_slab(box, o, d, t0, t1);
-        if (!hit) t0 = t1 = 0.f;  // as the traversal reports the root interval of a miss
-    }
-    prop_features(o, d, t0, X[threadIdx.x]);
-    __syncthreads();
-    if (r >= n) return;
-    float h1[PH], h2[PH], q[PO];
-    prop_forward(P, X[threadIdx.x], h1, h2, q);
-    if (q_out) {
 #pragma unroll
-        for (int b = 0; b < PO; ++b) q_out[(size_t)r * PO + b] = q[b];
+    for (int j = 0; j < 8; ++j) {
+        float4 v = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+        if (RELU) v = make_float4(fmaxf(v.x, 0.0f), fmaxf(v.y, 0.0f), fmaxf(v.z, 0.0f), fmaxf(v.w, 0.0f));
+        *reinterpret_cast<float4*>(&out[c0 + j][r0]) = v;
     }
-    uint64_t mk = 0, used = 0;
-    bool used_bg = false, fb = false;
-    float cum = 0.0f;
-    int kept = 0;
-    while (cum < coverage) {
-        int best = -1;
-        float bv = -1.0f;
+}
+
+// Kept bins of one ray from its column of q: bins by decreasing mass, ties to the
+// lower index, until the mass reaches `coverage` (the background, bin 64, counts
+// toward it but is not kept); a depth bin beyond max_bins means fallback (returns
+// true).  The 64 depth masses are sorted (bitonic network, descending) and walked
+// in that order, so the running sum sees the same values in the same order as a
+// repeated arg-max; the background enters before the first depth mass it strictly
+// exceeds.  The walk ends at the last kept mass tau, of which the first c_tau bins
+// (lowest indices) with q == tau are kept along with every bin with q > tau.
+__device__ __forceinline__ bool select_bins(const float (*Q)[kRays], int t, float coverage, int max_bins,
+                                            uint64_t& mk) {
+    float v[64];
 #pragma unroll
-        for (int b = 0; b < PO; ++b) {
-            const bool u = b < 64 ? ((used >> b) & 1ull) != 0 : used_bg;
-            if (!u && q[b] > bv) {
-                bv = q[b];
-                best = b;
+    for (int b = 0; b < 64; ++b) v[b] = Q[b][t];
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < 64; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const float hi = fmaxf(v[i], v[l]), lo = fminf(v[i], v[l]);
+                    const bool desc = (i & k) == 0;
+                    v[i] = desc ? hi : lo;
+                    v[l] = desc ? lo : hi;
+                }
             }
         }
-        if (best < 0) break;
-        cum += bv;
-        if (best == 64) {
-            used_bg = true;
-            continue;
+    }
+    const float vbg = Q[64][t];
+    bool bg_taken = false, fb = false;
+    float cum = 0.0f, tau = 0.0f;
+    int kept = 0, c_tau = 0;
+#pragma unroll
+    for (int p = 0; p < 64; ++p) {
+        if (!bg_taken && vbg > v[p]) {
+            if (!(cum < coverage)) break;
+            cum += vbg;
+            bg_taken = true;
         }
-        used |= 1ull << best;
+        if (!(cum < coverage)) break;
+        cum += v[p];
         if (kept == max_bins) {
             fb = true;
             break;
         }
-        mk |= 1ull << best;
+        if (kept > 0 && v[p] == tau) {
+            ++c_tau;
+        } else {
+            tau = v[p];
+            c_tau = 1;
+        }
         ++kept;
     }
-    if (!hit) fb = false;
-    mask[r] = fb ? ~0ull : mk;
-    fallback[r] = fb ? 1 : 0;
-    if (fb) atomicAdd(n_fallback, 1ull);
+    mk = 0;
+    if (fb || kept == 0) return fb;
+    int eq = 0;
+#pragma unroll
+    for (int b = 0; b < 64; ++b) {
+        const float q = Q[b][t];
+        const bool take = q > tau || (q == tau && eq < c_tau);
+        eq += (q == tau && take) ? 1 : 0;
+        mk |= take ? (1ull << b) : 0ull;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kRays, 2) k_prop_infer(const float* __restrict__ params, float b0, float b1,
+                                                         float b2, float b3, float b4, float b5,
+                                                         const float* __restrict__ ro, const float* __restrict__ rd,
+                                                         uint32_t n, float coverage, int max_bins,
+                                                         uint64_t* __restrict__ mask, uint8_t* __restrict__ fallback,
+                                                         unsigned long long* __restrict__ n_fallback,
+                                                         float* __restrict__ q_out) {
+    extern __shared__ __align__(16) uint8_t smraw[];
+    InferSmem& S = *reinterpret_cast<InferSmem*>(smraw);
+    for (int i = threadIdx.x; i < PH * PIN; i += blockDim.x) S.W1t[i % PIN][i / PIN] = params[OFF_W1 + i];
+    for (int i = threadIdx.x; i < PH * PH; i += blockDim.x) S.W2t[i % PH][i / PH] = params[OFF_W2 + i];
+    for (int i = threadIdx.x; i < PO * PH; i += blockDim.x) S.W3t[i % PH][i / PH] = params[OFF_W3 + i];
+    for (int i = threadIdx.x; i < PH; i += blockDim.x) {
+        S.b1[i] = params[OFF_B1 + i];
+        S.b2[i] = params[OFF_B2 + i];
+    }
+    for (int i = threadIdx.x; i < kW3ld; i += blockDim.x) S.b3[i] = i < PO ? params[OFF_B3 + i] : 0.0f;
+    float (*L)[kRays] = S.X;  // logits, then q
+    const int t = threadIdx.x;
+    const uint32_t n_tiles = (n + kRays - 1) / kRays;
+    uint32_t n_fb = 0;
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        __syncthreads();  // weights loaded; the previous tile's q fully read
+        const uint32_t r = tile * kRays + t;
+        float o[3] = {0.f, 0.f, 0.f}, d[3] = {1.f, 0.f, 0.f}, t0 = 0.f, t1 = 0.f;
+        bool hit = false;
+        if (r < n) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o[a] = __ldg(ro + 3 * (size_t)r + a);
+                d[a] = __ldg(rd + 3 * (size_t)r + a);
+            }
+            const float box[6] = {b0, b1, b2, b3, b4, b5};
+            hit = root_slab(box, o, d, t0, t1);
+            if (!hit) t0 = t1 = 0.f;  // as the traversal reports the root interval of a miss
+        }
+        prop_features<kRays>(o, d, t0, &S.X[0][t]);
+        __syncthreads();
+        tile_layer<PIN, PH, true>(S.X, &S.W1t[0][0], S.b1, 0, S.H1);
+        __syncthreads();
+        tile_layer<PH, PH, true>(S.H1, &S.W2t[0][0], S.b2, 0, S.H2);
+        __syncthreads();
+        tile_layer<PH, kW3ld, false>(S.H2, &S.W3t[0][0], S.b3, 0, L);
+        tile_layer<PH, kW3ld, false>(S.H2, &S.W3t[0][0], S.b3, 32, L);
+        {  // logit 64 (background), one per thread
+            float acc = S.b3[64];
+#pragma unroll
+            for (int i = 0; i < PH; ++i) acc = fmaf(S.W3t[i][64], S.H2[i][t], acc);
+            L[64][t] = acc;
+        }
+        __syncthreads();
+        if (r < n) {
+            float m = -INFINITY;
+#pragma unroll
+            for (int b = 0; b < PO; ++b) m = fmaxf(m, L[b][t]);
+            float s = 0.0f;
+#pragma unroll
+            for (int b = 0; b < PO; ++b) {
+                const float e = expf(L[b][t] - m);
+                L[b][t] = e;
+                s += e;
+            }
+            const float inv = 1.0f / s;
+#pragma unroll
+            for (int b = 0; b < PO; ++b) L[b][t] *= inv;
+            if (q_out) {
+#pragma unroll
+                for (int b = 0; b < PO; ++b) q_out[(size_t)r * PO + b] = L[b][t];
+            }
+            uint64_t mk = 0;
+            bool fb = select_bins(L, t, coverage, max_bins, mk);
+            if (!hit) fb = false;
+            mask[r] = fb ? ~0ull : mk;
+            fallback[r] = fb ? 1 : 0;
+            n_fb += fb ? 1u : 0u;
+        }
+    }
+    n_fb = __reduce_add_sync(0xffffffffu, n_fb);
+    if ((threadIdx.x & 31) == 0 && n_fb) atomicAdd(n_fallback, (unsigned long long)n_fb);
 }
 
 // splitmix64 finaliser: the ray index of batch element i of step s.
@@ -222,7 +386,7 @@ __global__ void __launch_bounds__(kRays) k_prop_grad(const float* __restrict__ p
         }
         t0 = root[r].x;
     }
-    prop_features(o, d, t0, S.X[t]);
+    prop_features<1>(o, d, t0, S.X[t]);
     __syncthreads();
     float h1[PH], h2[PH], q[PO];
     prop_forward(S.P, S.X[t], h1, h2, q);
@@ -317,13 +481,17 @@ __global__ void k_prop_adam(float* __restrict__ P, float* __restrict__ g, float*
 
 int proposal_param_count() { return NPAR; }
 
-constexpr size_t kInferSmem = sizeof(float) * (NPAR + kRays * (PIN + 1));
+constexpr size_t kInferSmem = sizeof(InferSmem);
+int g_infer_grid = 0;  // resident CTAs of k_prop_infer on this device
 
 cudaError_t launch_prop_infer(cudaStream_t s, const float* params, const float root_box[6], const float* ro,
                               const float* rd, uint32_t n, float coverage, int max_bins, uint64_t* mask,
                               uint8_t* fallback, unsigned long long* n_fallback, float* q_out) {
     if (n == 0) return cudaSuccess;
-    k_prop_infer<<<(n + kRays - 1) / kRays, kRays, kInferSmem, s>>>(params, root_box[0], root_box[1], root_box[2],
+    const uint32_t tiles = (n + kRays - 1) / kRays;
+    const unsigned grid = tiles < (uint32_t)g_infer_grid ? tiles : (unsigned)g_infer_grid;
+    if (grid == 0) return cudaErrorNotReady;  // prepare_proposal was not called
+    k_prop_infer<<<grid, kRays, kInferSmem, s>>>(params, root_box[0], root_box[1], root_box[2],
                                                            root_box[3], root_box[4], root_box[5], ro, rd, n,
                                                            coverage, max_bins, mask, fallback, n_fallback, q_out);
     return cudaGetLastError();
@@ -332,6 +500,12 @@ cudaError_t launch_prop_infer(cudaStream_t s, const float* params, const float r
 cudaError_t prepare_proposal() {
     cudaError_t e = cudaFuncSetAttribute(k_prop_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem);
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prop_infer, kRays, kInferSmem)) != cudaSuccess)
+        return e;
+    g_infer_grid = sms * (per_sm > 0 ? per_sm : 1);
     return cudaFuncSetAttribute(k_prop_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GradSmem));
 }
 

@@ -41,6 +41,27 @@ __device__ __forceinline__ bool slab(const float4& A, const float4& B, const flo
     return x > e;
 }
 
+// Bin k spans [lo_k, hi_k) with lo_k = r0 + k w and hi_k = r0 + (k + 1) w in FP32;
+// both are non-decreasing in k, so the bins a crossing [tin, tout] overlaps
+// (tin < hi_k and tout > lo_k) form one run [kmin, kmax]: kmin is the first k with
+// hi_k > tin, kmax the last with lo_k < tout.  A first guess by division is moved
+// to the exact ends with the same comparisons.
+__device__ __forceinline__ float bin_lo(float r0, float bw, int k) { return __fadd_rn(r0, __fmul_rn((float)k, bw)); }
+
+__device__ __forceinline__ bool overlaps_kept(uint64_t kept, float r0, float bw, float tin, float tout) {
+    if (!kept || !(bw > 0.0f)) return false;
+    const float inv = __frcp_rn(bw);
+    int a = (int)fminf(fmaxf(floorf(__fmul_rn(__fsub_rn(tin, r0), inv)), 0.0f), 63.0f);
+    while (a > 0 && bin_lo(r0, bw, a) > tin) --a;             // hi_{a-1} = lo_a > tin
+    while (a < 64 && !(bin_lo(r0, bw, a + 1) > tin)) ++a;    // hi_a <= tin
+    int b = (int)fminf(fmaxf(floorf(__fmul_rn(__fsub_rn(tout, r0), inv)), 0.0f), 63.0f);
+    while (b < 63 && bin_lo(r0, bw, b + 1) < tout) ++b;
+    while (b >= 0 && !(bin_lo(r0, bw, b) < tout)) --b;
+    if (a > b) return false;
+    const uint64_t run = (b - a == 63) ? ~0ull : (((2ull << (b - a)) - 1ull) << a);
+    return (kept & run) != 0;
+}
+
 __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, const float* __restrict__ rd,
                                                   uint32_t n, const DevNode* __restrict__ nodes, int maxc,
                                                   uint8_t* __restrict__ n_x, float2* __restrict__ xing,
@@ -86,16 +107,7 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
             const uint32_t meta = __float_as_uint(B.w);
             const int axis = (int)(meta & 3u) - 1;
             if (axis < 0) {
-                if (masked) {  // keep the crossing only if it overlaps a kept bin
-                    bool keep = false;
-                    for (uint64_t mm = kept_bins; mm && !keep; mm &= mm - 1) {
-                        const int k = __ffsll((long long)mm) - 1;
-                        const float lo = __fadd_rn(r0, __fmul_rn((float)k, bw));
-                        const float hi = __fadd_rn(r0, __fmul_rn((float)(k + 1), bw));
-                        keep = tin < hi && tout > lo;
-                    }
-                    if (!keep) continue;
-                }
+                if (masked && !overlaps_kept(kept_bins, r0, bw, tin, tout)) continue;
                 const uint32_t leaf = meta >> 2;
                 xing[base + cnt] = make_float2(tin, tout);
                 xleaf[base + cnt] = (uint16_t)leaf;
