@@ -121,17 +121,24 @@ __device__ __forceinline__ void prop_forward(const float* __restrict__ P, const 
 // 8-output register block takes one 16-byte activation load and two 16-byte weight
 // loads per input feature for 32 FMAs.  Every output is accumulated from its bias
 // over the inputs in order, the oracle's order.
-constexpr int kW3ld = 68;  // padded row of W3^T (65 used)
-struct InferSmem {
+constexpr int kW3ld = 68;      // padded row of W3^T (65 used)
+constexpr int kInferGroups = 3;  // warpgroups per CTA, one tile each; one CTA per SM
+struct InferWeights {
     float W1t[PIN][PH];
     float W2t[PH][PH];
     float W3t[PH][kW3ld];
     float b1[PH], b2[PH], b3[kW3ld];
-    float X[PIN][kRays];  // features; after the first layer, the logits / q [PO][kRays]
-    float H1[PH][kRays];
-    float H2[PH][kRays];
 };
-static_assert(PO <= PIN, "logits alias the feature rows");
+// One warpgroup's tile buffers.  A holds the features [f][ray]; after the first
+// layer its rows 0..31 take H2, rows 32..64 the logits 32..64.  B holds H1, then the
+// logits 0..31.
+struct InferTile {
+    float A[PIN][kRays];
+    float B[PH][kRays];
+};
+static_assert(PO <= PIN, "logits 32..64 live in feature rows");
+
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(g + 1) : "memory"); }
 
 // (a * b0 + c0, a * b1 + c1) with one packed FP32 instruction; each half is an
 // ordinary correctly rounded fused multiply-add.
@@ -151,7 +158,7 @@ __device__ __forceinline__ float2 fma_f32x2(float a, float2 b, float2 c) {
 template <int K, int LDW, bool RELU>
 __device__ __forceinline__ void tile_layer(const float (*in)[kRays], const float* Wt, const float* bias, int ob,
                                            float (*out)[kRays]) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
     const int r0 = warp * 32 + (lane & 7) * 4;
     const int c0 = ob + (lane >> 3) * 8;
     float acc[4][8];
@@ -202,11 +209,12 @@ __device__ __forceinline__ void tile_layer(const float (*in)[kRays], const float
 // repeated arg-max; the background enters before the first depth mass it strictly
 // exceeds.  The walk ends at the last kept mass tau, of which the first c_tau bins
 // (lowest indices) with q == tau are kept along with every bin with q > tau.
-__device__ __forceinline__ bool select_bins(const float (*Q)[kRays], int t, float coverage, int max_bins,
-                                            uint64_t& mk) {
+__device__ __forceinline__ bool select_bins(const float (*QB)[kRays], const float (*QA)[kRays], int t,
+                                            float coverage, int max_bins, uint64_t& mk) {
+#define Q_(b) ((b) < 32 ? QB[(b)][t] : QA[(b)][t])
     float v[64];
 #pragma unroll
-    for (int b = 0; b < 64; ++b) v[b] = Q[b][t];
+    for (int b = 0; b < 64; ++b) v[b] = Q_(b);
 #pragma unroll
     for (int k = 2; k <= 64; k <<= 1) {
 #pragma unroll
@@ -223,7 +231,7 @@ __device__ __forceinline__ bool select_bins(const float (*Q)[kRays], int t, floa
             }
         }
     }
-    const float vbg = Q[64][t];
+    const float vbg = Q_(64);
     bool bg_taken = false, fb = false;
     float cum = 0.0f, tau = 0.0f;
     int kept = 0, c_tau = 0;
@@ -253,23 +261,22 @@ __device__ __forceinline__ bool select_bins(const float (*Q)[kRays], int t, floa
     int eq = 0;
 #pragma unroll
     for (int b = 0; b < 64; ++b) {
-        const float q = Q[b][t];
+        const float q = Q_(b);
         const bool take = q > tau || (q == tau && eq < c_tau);
         eq += (q == tau && take) ? 1 : 0;
         mk |= take ? (1ull << b) : 0ull;
     }
     return false;
+#undef Q_
 }
 
-__global__ void __launch_bounds__(kRays, 2) k_prop_infer(const float* __restrict__ params, float b0, float b1,
-                                                         float b2, float b3, float b4, float b5,
-                                                         const float* __restrict__ ro, const float* __restrict__ rd,
-                                                         uint32_t n, float coverage, int max_bins,
-                                                         uint64_t* __restrict__ mask, uint8_t* __restrict__ fallback,
-                                                         unsigned long long* __restrict__ n_fallback,
-                                                         float* __restrict__ q_out) {
+__global__ void __launch_bounds__(kRays * kInferGroups, 1) k_prop_infer(
+    const float* __restrict__ params, float b0, float b1, float b2, float b3, float b4, float b5,
+    const float* __restrict__ ro, const float* __restrict__ rd, uint32_t n, float coverage, int max_bins,
+    uint64_t* __restrict__ mask, uint8_t* __restrict__ fallback, unsigned long long* __restrict__ n_fallback,
+    float* __restrict__ q_out) {
     extern __shared__ __align__(16) uint8_t smraw[];
-    InferSmem& S = *reinterpret_cast<InferSmem*>(smraw);
+    InferWeights& S = *reinterpret_cast<InferWeights*>(smraw);
     for (int i = threadIdx.x; i < PH * PIN; i += blockDim.x) S.W1t[i % PIN][i / PIN] = params[OFF_W1 + i];
     for (int i = threadIdx.x; i < PH * PH; i += blockDim.x) S.W2t[i % PH][i / PH] = params[OFF_W2 + i];
     for (int i = threadIdx.x; i < PO * PH; i += blockDim.x) S.W3t[i % PH][i / PH] = params[OFF_W3 + i];
@@ -278,12 +285,14 @@ __global__ void __launch_bounds__(kRays, 2) k_prop_infer(const float* __restrict
         S.b2[i] = params[OFF_B2 + i];
     }
     for (int i = threadIdx.x; i < kW3ld; i += blockDim.x) S.b3[i] = i < PO ? params[OFF_B3 + i] : 0.0f;
-    float (*L)[kRays] = S.X;  // logits, then q
-    const int t = threadIdx.x;
+    __syncthreads();
+    const int g = threadIdx.x >> 7;   // warpgroup
+    const int t = threadIdx.x & 127;  // ray of the tile
+    InferTile& T = reinterpret_cast<InferTile*>(smraw + sizeof(InferWeights))[g];
     const uint32_t n_tiles = (n + kRays - 1) / kRays;
     uint32_t n_fb = 0;
-    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        __syncthreads();  // weights loaded; the previous tile's q fully read
+    for (uint32_t tile = blockIdx.x * kInferGroups + g; tile < n_tiles; tile += gridDim.x * kInferGroups) {
+        group_sync(g);  // the previous tile's q fully read
         const uint32_t r = tile * kRays + t;
         float o[3] = {0.f, 0.f, 0.f}, d[3] = {1.f, 0.f, 0.f}, t0 = 0.f, t1 = 0.f;
         bool hit = false;
@@ -297,41 +306,43 @@ __global__ void __launch_bounds__(kRays, 2) k_prop_infer(const float* __restrict
             hit = root_slab(box, o, d, t0, t1);
             if (!hit) t0 = t1 = 0.f;  // as the traversal reports the root interval of a miss
         }
-        prop_features<kRays>(o, d, t0, &S.X[0][t]);
-        __syncthreads();
-        tile_layer<PIN, PH, true>(S.X, &S.W1t[0][0], S.b1, 0, S.H1);
-        __syncthreads();
-        tile_layer<PH, PH, true>(S.H1, &S.W2t[0][0], S.b2, 0, S.H2);
-        __syncthreads();
-        tile_layer<PH, kW3ld, false>(S.H2, &S.W3t[0][0], S.b3, 0, L);
-        tile_layer<PH, kW3ld, false>(S.H2, &S.W3t[0][0], S.b3, 32, L);
-        {  // logit 64 (background), one per thread
+        prop_features<kRays>(o, d, t0, &T.A[0][t]);
+        group_sync(g);
+        tile_layer<PIN, PH, true>(T.A, &S.W1t[0][0], S.b1, 0, T.B);   // H1 -> B
+        group_sync(g);
+        tile_layer<PH, PH, true>(T.B, &S.W2t[0][0], S.b2, 0, T.A);    // H2 -> A rows 0..31
+        group_sync(g);
+        tile_layer<PH, kW3ld, false>(T.A, &S.W3t[0][0], S.b3, 0, T.B);   // logits 0..31 -> B
+        tile_layer<PH, kW3ld, false>(T.A, &S.W3t[0][0], S.b3, 32, T.A);  // logits 32..63 -> A rows 32..63
+        {  // logit 64 (background), one per thread, into A row 64
             float acc = S.b3[64];
 #pragma unroll
-            for (int i = 0; i < PH; ++i) acc = fmaf(S.W3t[i][64], S.H2[i][t], acc);
-            L[64][t] = acc;
+            for (int i = 0; i < PH; ++i) acc = fmaf(S.W3t[i][64], T.A[i][t], acc);
+            T.A[64][t] = acc;
         }
-        __syncthreads();
+        group_sync(g);
         if (r < n) {
+#define L_(b) (*((b) < 32 ? &T.B[(b)][t] : &T.A[(b)][t]))
             float m = -INFINITY;
 #pragma unroll
-            for (int b = 0; b < PO; ++b) m = fmaxf(m, L[b][t]);
+            for (int b = 0; b < PO; ++b) m = fmaxf(m, L_(b));
             float s = 0.0f;
 #pragma unroll
             for (int b = 0; b < PO; ++b) {
-                const float e = expf(L[b][t] - m);
-                L[b][t] = e;
+                const float e = expf(L_(b) - m);
+                L_(b) = e;
                 s += e;
             }
             const float inv = 1.0f / s;
 #pragma unroll
-            for (int b = 0; b < PO; ++b) L[b][t] *= inv;
+            for (int b = 0; b < PO; ++b) L_(b) *= inv;
             if (q_out) {
 #pragma unroll
-                for (int b = 0; b < PO; ++b) q_out[(size_t)r * PO + b] = L[b][t];
+                for (int b = 0; b < PO; ++b) q_out[(size_t)r * PO + b] = L_(b);
             }
+#undef L_
             uint64_t mk = 0;
-            bool fb = select_bins(L, t, coverage, max_bins, mk);
+            bool fb = select_bins(T.B, T.A, t, coverage, max_bins, mk);
             if (!hit) fb = false;
             mask[r] = fb ? ~0ull : mk;
             fallback[r] = fb ? 1 : 0;
@@ -481,7 +492,7 @@ __global__ void k_prop_adam(float* __restrict__ P, float* __restrict__ g, float*
 
 int proposal_param_count() { return NPAR; }
 
-constexpr size_t kInferSmem = sizeof(InferSmem);
+constexpr size_t kInferSmem = sizeof(InferWeights) + kInferGroups * sizeof(InferTile);
 int g_infer_grid = 0;  // resident CTAs of k_prop_infer on this device
 
 cudaError_t launch_prop_infer(cudaStream_t s, const float* params, const float root_box[6], const float* ro,
@@ -489,9 +500,10 @@ cudaError_t launch_prop_infer(cudaStream_t s, const float* params, const float r
                               uint8_t* fallback, unsigned long long* n_fallback, float* q_out) {
     if (n == 0) return cudaSuccess;
     const uint32_t tiles = (n + kRays - 1) / kRays;
-    const unsigned grid = tiles < (uint32_t)g_infer_grid ? tiles : (unsigned)g_infer_grid;
+    const uint32_t ctas = (tiles + kInferGroups - 1) / kInferGroups;
+    const unsigned grid = ctas < (uint32_t)g_infer_grid ? ctas : (unsigned)g_infer_grid;
     if (grid == 0) return cudaErrorNotReady;  // prepare_proposal was not called
-    k_prop_infer<<<grid, kRays, kInferSmem, s>>>(params, root_box[0], root_box[1], root_box[2],
+    k_prop_infer<<<grid, kRays * kInferGroups, kInferSmem, s>>>(params, root_box[0], root_box[1], root_box[2],
                                                            root_box[3], root_box[4], root_box[5], ro, rd, n,
                                                            coverage, max_bins, mask, fallback, n_fallback, q_out);
     return cudaGetLastError();
@@ -503,7 +515,7 @@ cudaError_t prepare_proposal() {
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prop_infer, kRays, kInferSmem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prop_infer, kRays * kInferGroups, kInferSmem)) != cudaSuccess)
         return e;
     g_infer_grid = sms * (per_sm > 0 ? per_sm : 1);
     return cudaFuncSetAttribute(k_prop_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GradSmem));
