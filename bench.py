@@ -131,6 +131,33 @@ def workload(cfg, rank: int, views: int | None = None, px: int | None = None):
     return grid, np.concatenate(os_), np.concatenate(ds_)
 
 
+def barrier():
+    """Barrier over the ranks of the default process group (no-op for one rank)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def _reduce(x: float, op: str, device) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def max_over_ranks(x: float, device="cuda") -> float:
+    """The slowest rank's time: the whole job's step time."""
+    return _reduce(x, "max", device)
+
+
+def sum_over_ranks(x: float, device="cuda") -> float:
+    """Units of all ranks (each rank renders different views, so counts differ)."""
+    return _reduce(x, "sum", device)
+
+
 def _algorithmic(cfg, st):
     """Algorithmic work of one step (bytes / flops), per the unit counts of the step."""
     rays, xs, samples = st["rays"], st["crossings"], st["samples_generated"]
@@ -169,17 +196,6 @@ def run_ours(args):
     out = (torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"), torch.empty(n, device="cuda"))
     stream = torch.cuda.current_stream()
     peaks, peak_src = _peaks()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     results = {}
     precs = [p for p in args.prec.split(",") if p]
@@ -222,8 +238,8 @@ def run_ours(args):
     head = "bf16" if "bf16" in results else next(iter(results))
     hr = results[head]
     st = hr["stats"]
-    samples_all = st["samples_generated"] * world
-    rays_all = n * world
+    samples_all = int(sum_over_ranks(float(st["samples_generated"])))
+    rays_all = int(sum_over_ranks(float(n)))
     value = samples_all / (hr["ms"] * 1e-3) / 1e6
 
     # end to end through the host-buffer entry point (pinned host memory, copies timed)
@@ -617,7 +633,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--prec", default="fp32,bf16,fp8")
-    ap.add_argument("--psnr-rays", type=int, default=32768)
+    ap.add_argument("--psnr-rays", type=int, default=262144)
     ap.add_argument("--ref-rays", type=int, default=16384)
     ap.add_argument("--views", type=int, default=None, help="views per GPU (default: the config's)")
     ap.add_argument("--train-views", type=int, default=64, help="c5: plain-rendered training views")
