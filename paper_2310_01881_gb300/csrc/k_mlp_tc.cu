@@ -57,17 +57,22 @@ constexpr unsigned long long kWaitCycles = 4000000000ull;  // ~2 s at 2 GHz
 __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // ---- per-leaf weight blob layout (bytes) -------------------------------------------
-// W0 [width x k0p], W1.. [width x width] in the operand type (BF16, or E4M3 with FP32
+// W0 [width x k0p], W1.. [width x kh] in the operand type (BF16, or E4M3 with FP32
 // per-output-channel scales sw [hidden][width]); head Wo FP32 [width][4]; FP32 biases
-// b_0..b_{hidden-1} [width] and bo [4].
+// b_0..b_{hidden-1} [width] and bo [4].  BF16 folds each hidden layer's bias into the
+// contraction: input column k_in (90 for layer 0, width for the others) holds the
+// bias and the activation row carries 1 there, so kh = width + 16 and the epilogue
+// adds nothing.  E4M3 keeps kh = width and adds the FP32 bias in the epilogue (an E4M3
+// bias would lose too much).
 struct TcLayout {
-    int width, hidden, k0, k0p, es;
+    int width, hidden, k0, k0p, kh, es;
     size_t w0, wh, wo, sw, bias, stride;
     __host__ __device__ TcLayout(int w, int h, int k, bool f8)
-        : width(w), hidden(h), k0(k), k0p(round_up(k, f8 ? 32 : 16)), es(f8 ? 1 : 2) {
+        : width(w), hidden(h), k0(k), k0p(round_up(f8 ? k : k + 1, f8 ? 32 : 16)), kh(f8 ? w : w + 16),
+          es(f8 ? 1 : 2) {
         w0 = 0;
         wh = w0 + (size_t)w * k0p * es;
-        wo = wh + (size_t)(h - 1) * w * w * es;  // head: FP32, [width][4] (output-fastest)
+        wo = wh + (size_t)(h - 1) * w * kh * es;  // head: FP32, [width][4] (output-fastest)
         sw = wo + (size_t)w * 4 * 4;
         bias = sw + (f8 ? (size_t)h * w * 4 : 0);
         const size_t end = bias + (size_t)h * w * 4 + 16;
@@ -349,14 +354,17 @@ __device__ __forceinline__ void encode_freq(const float p[3], float (&f)[N]) {
 }
 
 // Features [32 c, 32 c + 32) of f packed two per word (even feature in the low half)
-// and written to this thread's TMEM lane at A column 16 c.
+// and written to this thread's TMEM lane at A column 16 c; feature N (one past the
+// last) is the constant 1 that multiplies the folded bias.
 template <int C, int N>
 __device__ __forceinline__ void store_chunk(uint32_t a_row, const float (&f)[N]) {
     uint32_t w[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const int f0 = 32 * C + 2 * i, f1 = f0 + 1;
-        w[i] = pack_bf16(f0 < N ? f[f0 < N ? f0 : 0] : 0.0f, f1 < N ? f[f1 < N ? f1 : 0] : 0.0f);
+        const float v0 = f0 < N ? f[f0 < N ? f0 : 0] : (f0 == N ? 1.0f : 0.0f);
+        const float v1 = f1 < N ? f[f1 < N ? f1 : 0] : (f1 == N ? 1.0f : 0.0f);
+        w[i] = pack_bf16(v0, v1);
     }
     tmem_st16(a_row + 16u * C, w);
 }
@@ -403,7 +411,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
     constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
     constexpr int KI = F8 ? 32 : 16;        // K per MMA instruction
     constexpr int EPW = F8 ? 4 : 2;         // elements per 32-bit TMEM column
-    constexpr int K0P = round_up(K0, KI);
+    constexpr int K0P = round_up(F8 ? K0 : K0 + 1, KI);  // BF16: + the bias column
     static_assert(K0P / EPW <= (int)(kGroupCols - kACol), "layer-0 input does not fit the A columns");
     static_assert(W <= (int)kACol, "accumulator does not fit the D columns");
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -552,7 +560,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 if (tig == 0) {
                     tc_fence_after();
                     const uint32_t b_base =
-                        w_addr + (uint32_t)(l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * W * W * lay.es);
+                        w_addr + (uint32_t)(l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * W * lay.kh * lay.es);
                     const uint32_t sbo = (uint32_t)kin * (F8 ? 8u : 16u);  // 8-row group stride in bytes
                     if constexpr (F8) {
                         const uint32_t idd = idesc_e4m3(W);
@@ -590,16 +598,16 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 const bool last = l + 1 == g.hidden;
                 // pre-activation of 4 consecutive columns c0..c0+3 of this row
                 auto pre4 = [&](const float* v, int c0, float2& p01, float2& p23) {
-                    const float4 bb = *reinterpret_cast<const float4*>(b + c0);
                     if constexpr (F8) {
+                        const float4 bb = *reinterpret_cast<const float4*>(b + c0);
                         const float4 ss = *reinterpret_cast<const float4*>(sw + c0);
                         p01 = fma_f32x2(s_a, mul_f32x2(make_float2(v[0], v[1]), make_float2(ss.x, ss.y)),
                                         make_float2(bb.x, bb.y));
                         p23 = fma_f32x2(s_a, mul_f32x2(make_float2(v[2], v[3]), make_float2(ss.z, ss.w)),
                                         make_float2(bb.z, bb.w));
-                    } else {
-                        p01 = add_f32x2(make_float2(v[0], v[1]), make_float2(bb.x, bb.y));
-                        p23 = add_f32x2(make_float2(v[2], v[3]), make_float2(bb.z, bb.w));
+                    } else {  // the bias is already in the accumulator
+                        p01 = make_float2(v[0], v[1]);
+                        p23 = make_float2(v[2], v[3]);
                     }
                 };
                 if (!last) {
@@ -617,6 +625,10 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                                 pk[2 * c + 1] = pack_relu_bf16(p23.x, p23.y);
                             }
                             tmem_st16(a_row + 16u * h, pk);
+                        }
+                        if (l == 0) {  // input column W of the hidden layers: the constant 1 of the bias
+                            uint32_t c8[8] = {pack_bf16(1.0f, 0.0f), 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+                            tmem_st8(a_row + (uint32_t)(W / 2), c8);
                         }
                     } else {
                         float hv[W];
@@ -650,13 +662,14 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     tmem_st_wait();
                     tc_fence_before();
                     wg_bar(bar_id);
-                    kin = W;
+                    kin = lay.kh;
                 } else {
                     // head: z = Wo relu(pre) + bo in FP32 (Wo stored [width][4])
                     const float4* wo = reinterpret_cast<const float4*>(wbuf + lay.wo);
                     const float* bo = bias + (size_t)g.hidden * W;
                     float2 z01 = make_float2(bo[0], bo[1]);
                     float2 z23 = make_float2(bo[2], bo[3]);
+                    float2 y01 = make_float2(0.f, 0.f), y23 = make_float2(0.f, 0.f);  // odd inputs
 #pragma unroll
                     for (int h = 0; h < W / 32; ++h) {
                         float v[32];
@@ -670,11 +683,18 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
                                 const float4 w4 = wo[32 * h + 4 * c + i];
-                                z01 = fma_f32x2(hq[i], make_float2(w4.x, w4.y), z01);
-                                z23 = fma_f32x2(hq[i], make_float2(w4.z, w4.w), z23);
+                                if (i & 1) {
+                                    y01 = fma_f32x2(hq[i], make_float2(w4.x, w4.y), y01);
+                                    y23 = fma_f32x2(hq[i], make_float2(w4.z, w4.w), y23);
+                                } else {
+                                    z01 = fma_f32x2(hq[i], make_float2(w4.x, w4.y), z01);
+                                    z23 = fma_f32x2(hq[i], make_float2(w4.z, w4.w), z23);
+                                }
                             }
                         }
                     }
+                    z01 = add_f32x2(z01, y01);
+                    z23 = add_f32x2(z23, y23);
                     if (slot != ~0ull) {
                         float4 o;
                         o.x = softplus_f(z01.x);
@@ -767,8 +787,8 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
     float* sw = reinterpret_cast<float*>(dst + lay.sw);
     int kin = k0;
     for (int l = 0; l < hidden; ++l) {
-        const int K = l == 0 ? lay.k0p : width;
-        uint8_t* base = dst + (l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * width * width * lay.es);
+        const int K = l == 0 ? lay.k0p : lay.kh;
+        uint8_t* base = dst + (l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * width * lay.kh * lay.es);
         for (int n = 0; n < width; ++n) {
             const float* row = w + (size_t)n * kin;
             if (f8) {
@@ -782,6 +802,8 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
                     const uint16_t b = f2bf(row[k]);
                     std::memcpy(base + cm_offset(n, k, K), &b, 2);
                 }
+                const uint16_t bb = f2bf(w[(size_t)width * kin + n]);  // folded bias at input column kin
+                std::memcpy(base + cm_offset(n, kin, K), &bb, 2);
             }
         }
         w += (size_t)width * kin;
