@@ -49,16 +49,26 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_composite(
         const size_t sbase = (size_t)ray * cap;
         float T = 1.0f;
         float cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
+        // the next chunk's slot and crossing are loaded before this chunk is scanned
+        float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 xn = make_float2(0.f, 0.f);
+        if (lane < ns) {
+            vn = __ldg(slot_out + sbase + lane);
+            xn = __ldg(xing + xbase + lane / steps);
+        }
         for (int s0 = 0; s0 < ns; s0 += 32) {
             const int s = s0 + lane;
             const bool valid = s < ns;
             float e = 1.0f, sig = 0.f, t = 0.f;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 v = vn;
+            const float2 x = xn;
+            if (s + 32 < ns) {
+                vn = __ldg(slot_out + sbase + s + 32);
+                xn = __ldg(xing + xbase + (s + 32) / steps);
+            }
             if (valid) {
-                v = __ldg(slot_out + sbase + s);
                 const int k = s / steps;
                 const int j = s - k * steps;
-                const float2 x = __ldg(xing + xbase + k);
                 const float delta = __fmul_rn(__fsub_rn(x.y, x.x), inv_steps);
                 t = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
                 sig = __fmul_rn(v.x, delta);

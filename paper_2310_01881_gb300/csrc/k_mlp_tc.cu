@@ -62,8 +62,9 @@ __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / 
 // b_0..b_{hidden-1} [width] and bo [4].  BF16 folds each hidden layer's bias into the
 // contraction: input column k_in (90 for layer 0, width for the others) holds the
 // bias and the activation row carries 1 there, so kh = width + 16 and the epilogue
-// adds nothing.  E4M3 keeps kh = width and adds the FP32 bias in the epilogue (an E4M3
-// bias would lose too much).
+// adds nothing; its head is a 16-row BF16 matrix (rows 0..3 used, bias in column
+// width) run as one more MMA.  E4M3 keeps kh = width, adds the FP32 bias in the
+// epilogue (an E4M3 bias would lose too much) and computes the head in FP32.
 struct TcLayout {
     int width, hidden, k0, k0p, kh, es;
     size_t w0, wh, wo, sw, bias, stride;
@@ -72,8 +73,8 @@ struct TcLayout {
           es(f8 ? 1 : 2) {
         w0 = 0;
         wh = w0 + (size_t)w * k0p * es;
-        wo = wh + (size_t)(h - 1) * w * kh * es;  // head: FP32, [width][4] (output-fastest)
-        sw = wo + (size_t)w * 4 * 4;
+        wo = wh + (size_t)(h - 1) * w * kh * es;  // head: E4M3 path FP32 [width][4]; BF16 path 16 x kh BF16
+        sw = wo + (f8 ? (size_t)w * 4 * 4 : (size_t)16 * kh * 2);
         bias = sw + (f8 ? (size_t)h * w * 4 : 0);
         const size_t end = bias + (size_t)h * w * 4 + 16;
         stride = (end + 127) / 128 * 128;
@@ -276,6 +277,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 4 consecutive FP32 columns of this thread's TMEM lane (load + wait).
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+    uint32_t r[4];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
     uint32_t d;
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
@@ -400,6 +414,7 @@ __device__ __forceinline__ void crossing_data(const MlpArgs& g, uint32_t id, flo
 // 48 columns = 96 BF16 features per lane).
 constexpr uint32_t kGroupCols = 128;
 constexpr uint32_t kACol = 64;
+constexpr uint32_t kHeadCol = 48;  // BF16 head accumulator (16 columns) inside the D columns
 
 // F8 = false: BF16 operands (kind::f16, K = 16 per MMA, 2 features per TMEM column).
 // F8 = true:  E4M3 operands (kind::f8f6f4, K = 32 per MMA, 4 features per column) with
@@ -480,6 +495,30 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         uint32_t ph_w = 0, ph_m = 0;
         int cur = -1;
         bool ok = true;
+        // BF16: the head MMA of a tile runs while the group encodes its next tile; its
+        // outputs are read (and stored to slot_prev) just before that tile's first MMA
+        bool pending = false;
+        uint64_t slot_prev = ~0ull;
+        auto finish_head = [&]() -> bool {
+            const bool okh = group_wait(bar_m, ph_m, bar_id, flag, tig);
+            ph_m ^= 1u;
+            pending = false;
+            if (!okh) return false;
+            tc_fence_after();
+            float z[4];
+            tmem_ld4(d_row + kHeadCol, z);
+            if (slot_prev != ~0ull) {
+                float4 o;
+                o.x = softplus_f(z[0]);
+                o.y = sigmoid_f(z[1]);
+                o.z = sigmoid_f(z[2]);
+                o.w = sigmoid_f(z[3]);
+                g.slot_out[slot_prev] = o;
+            }
+            tc_fence_before();
+            wg_bar(bar_id);  // every row has read the head accumulator before D is reused
+            return true;
+        };
 
         // software pipeline: the crossing id of the next tile is fetched after the first
         // MMA of the current tile has been waited for, its interval and ray one layer later
@@ -491,6 +530,9 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
 
         for (uint32_t t = t_first; t < t_stop && ok;) {
             if (leaf != cur) {
+                if constexpr (!F8) {
+                    if (pending && !(ok = finish_head())) break;  // the head MMA still reads the weights
+                }
                 wg_bar(bar_id);  // every row is done with the previous leaf's weights and biases
                 if (tig == 0) {
                     fence_proxy_async();
@@ -549,6 +591,9 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             tmem_st_wait();
             tc_fence_before();
             wg_bar(bar_id);
+            if constexpr (!F8) {
+                if (pending && !(ok = finish_head())) break;
+            }
 
             int leaf_n = leaf;
             uint32_t id_n = 0xffffffffu;
@@ -663,6 +708,41 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     tc_fence_before();
                     wg_bar(bar_id);
                     kin = lay.kh;
+                } else if constexpr (!F8) {
+                    // relu(h) as BF16 into this group's D columns (each 32-column block is
+                    // read before it is overwritten), the constant 1 of the head bias after
+                    // it, then the head MMA (16 x kh) into D columns kHeadCol..+15
+#pragma unroll
+                    for (int h = 0; h < W / 32; ++h) {
+                        float v[32];
+                        uint32_t pk[16];
+                        tmem_ld32(d_row + 32u * h, v);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            pk[2 * c + 0] = pack_relu_bf16(v[4 * c + 0], v[4 * c + 1]);
+                            pk[2 * c + 1] = pack_relu_bf16(v[4 * c + 2], v[4 * c + 3]);
+                        }
+                        tmem_st16(d_row + 16u * h, pk);
+                    }
+                    {
+                        uint32_t c8[8] = {pack_bf16(1.0f, 0.0f), 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+                        tmem_st8(d_row + (uint32_t)(W / 2), c8);
+                    }
+                    tmem_st_wait();
+                    tc_fence_before();
+                    wg_bar(bar_id);
+                    if (tig == 0) {
+                        tc_fence_after();
+                        const uint32_t b_base = w_addr + (uint32_t)lay.wo;
+                        const uint32_t sbo = (uint32_t)lay.kh * 16u;
+                        const uint32_t idd = idesc_bf16(16);
+                        for (int kk = 0; kk < lay.kh / 16; ++kk)
+                            mma_bf16_ts(d_col + kHeadCol, d_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd,
+                                        kk > 0 ? 1u : 0u);
+                        mma_commit(bar_m);
+                    }
+                    pending = true;
+                    slot_prev = slot;
                 } else {
                     // head: z = Wo relu(pre) + bo in FP32 (Wo stored [width][4])
                     const float4* wo = reinterpret_cast<const float4*>(wbuf + lay.wo);
@@ -709,6 +789,9 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             leaf = leaf_n;
             id = id_n;
             t = t_next;
+        }
+        if constexpr (!F8) {
+            if (ok && pending) ok = finish_head();
         }
         if (!ok && tig == 0) atomicCAS(g.err, 0, kDevErrTimeout);
     }
@@ -811,9 +894,21 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
         w += width;
         kin = width;
     }
-    float* wo = reinterpret_cast<float*>(dst + lay.wo);
-    for (int k = 0; k < width; ++k)
-        for (int n = 0; n < 4; ++n) wo[(size_t)k * 4 + n] = w[(size_t)n * width + k];
+    if (f8) {
+        float* wo = reinterpret_cast<float*>(dst + lay.wo);
+        for (int k = 0; k < width; ++k)
+            for (int n = 0; n < 4; ++n) wo[(size_t)k * 4 + n] = w[(size_t)n * width + k];
+    } else {  // rows 0..3 of a 16 x kh BF16 matrix, the bias in column `width`
+        uint8_t* hb = dst + lay.wo;
+        for (int n = 0; n < 4; ++n) {
+            for (int k = 0; k < width; ++k) {
+                const uint16_t b = f2bf(w[(size_t)n * width + k]);
+                std::memcpy(hb + cm_offset(n, k, lay.kh), &b, 2);
+            }
+            const uint16_t bb = f2bf(w[(size_t)4 * width + n]);
+            std::memcpy(hb + cm_offset(n, width, lay.kh), &bb, 2);
+        }
+    }
     w += 4 * width;
     for (int n = 0; n < 4; ++n) bias[(size_t)hidden * width + n] = w[n];
 }
