@@ -149,11 +149,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase,
 
 __device__ __forceinline__ void wg_bar(int id) { asm volatile("barrier.sync %0, 128;" ::"r"(id) : "memory"); }
 
-// One thread of the group polls the mbarrier (bounded) while the other 127 sleep at
-// the group's named barrier, so waiting groups take no issue slots from working ones.
-// The flag carries the outcome to the whole group.
-__device__ __forceinline__ bool group_wait(uint32_t bar, uint32_t phase, int bar_id, volatile int* flag, int tig) {
-    if (tig == 0) *flag = mbar_wait_bounded(bar, phase) ? 1 : 0;
+// One thread of the group (its leader) polls the mbarrier (bounded) while the other
+// 127 sleep at the group's named barrier, so waiting groups take no issue slots from
+// working ones.  The flag carries the outcome to the whole group.
+__device__ __forceinline__ bool group_wait(uint32_t bar, uint32_t phase, int bar_id, volatile int* flag, bool leader) {
+    if (leader) *flag = mbar_wait_bounded(bar, phase) ? 1 : 0;
     wg_bar(bar_id);
     return *flag != 0;
 }
@@ -438,6 +438,9 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
     const int warp = threadIdx.x >> 5;
     const int q = warp & 3;             // TMEM lane quadrant of this warp
     const int bar_id = 1 + grp;
+    // the group's leader (MMA issue, waits, weight loads) sits in warp grp % 4 of the
+    // group, so the leaders of the 4 groups run on 4 different SM sub-partitions
+    const bool leader = tig == 32 * (grp & 3);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < n_groups; ++i) {
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             t_first = g.t_begin + wid;
             t_step = workers;
         } else if (g.schedule == kSchedDynamic) {
-            if (tig == 0) sh->next_tile[grp] = atomicAdd(g.tile_counter, 1u) + g.t_begin;
+            if (leader) sh->next_tile[grp] = atomicAdd(g.tile_counter, 1u) + g.t_begin;
             wg_bar(bar_id);
             t_first = sh->next_tile[grp];
         } else {  // contiguous (also each launch of the per-leaf loop)
@@ -500,7 +503,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         bool pending = false;
         uint64_t slot_prev = ~0ull;
         auto finish_head = [&]() -> bool {
-            const bool okh = group_wait(bar_m, ph_m, bar_id, flag, tig);
+            const bool okh = group_wait(bar_m, ph_m, bar_id, flag, leader);
             ph_m ^= 1u;
             pending = false;
             if (!okh) return false;
@@ -534,11 +537,11 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     if (pending && !(ok = finish_head())) break;  // the head MMA still reads the weights
                 }
                 wg_bar(bar_id);  // every row is done with the previous leaf's weights and biases
-                if (tig == 0) {
+                if (leader) {
                     fence_proxy_async();
                     bulk_load(w_addr, wall + (size_t)leaf * lay.stride, (uint32_t)lay.stride, bar_w);
                 }
-                ok = group_wait(bar_w, ph_w, bar_id, flag, tig);
+                ok = group_wait(bar_w, ph_w, bar_id, flag, leader);
                 ph_w ^= 1u;
                 if (!ok) break;
                 cur = leaf;
@@ -602,7 +605,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             // ---- hidden layers; the head runs on the CUDA cores in the last epilogue
             int kin = K0P;
             for (int l = 0; l < g.hidden && ok; ++l) {
-                if (tig == 0) {
+                if (leader) {
                     tc_fence_after();
                     const uint32_t b_base =
                         w_addr + (uint32_t)(l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * W * lay.kh * lay.es);
@@ -618,9 +621,9 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     }
                     mma_commit(bar_m);
                 }
-                if (l == 0 && g.schedule == kSchedDynamic && tig == 0)
+                if (l == 0 && g.schedule == kSchedDynamic && leader)
                     sh->next_tile[grp] = atomicAdd(g.tile_counter, 1u) + g.t_begin;
-                ok = group_wait(bar_m, ph_m, bar_id, flag, tig);
+                ok = group_wait(bar_m, ph_m, bar_id, flag, leader);
                 ph_m ^= 1u;
                 if (!ok) break;
                 tc_fence_after();
@@ -731,7 +734,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     tmem_st_wait();
                     tc_fence_before();
                     wg_bar(bar_id);
-                    if (tig == 0) {
+                    if (leader) {
                         tc_fence_after();
                         const uint32_t b_base = w_addr + (uint32_t)lay.wo;
                         const uint32_t sbo = (uint32_t)lay.kh * 16u;
@@ -793,7 +796,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         if constexpr (!F8) {
             if (ok && pending) ok = finish_head();
         }
-        if (!ok && tig == 0) atomicCAS(g.err, 0, kDevErrTimeout);
+        if (!ok && leader) atomicCAS(g.err, 0, kDevErrTimeout);
     }
     tc_fence_before();
     __syncthreads();
