@@ -5,11 +5,12 @@
 // tau = sigma * delta, e = exp(-tau), alpha = 1 - e, w = T alpha; C += w c,
 // D += w t, T = T e.  rgb = C + T bg, depth = D, opacity = 1 - T.
 //
-// One warp per ray handles 32 consecutive slots at a time: the per-sample factors e
-// are combined by a warp-shuffle multiplicative scan, so lane i gets the
-// transmittance in front of its sample (the carried T times the exclusive product);
-// lanes whose transmittance is below t_term are dropped (a prefix, since the
-// product only decreases), and the warp stops at the first chunk that terminates.
+// One warp per ray handles 64 consecutive slots per pass, two per lane: the per-lane
+// products of the factors e are combined by a warp-shuffle multiplicative scan, so
+// each lane gets the transmittance in front of its two samples (the carried T times
+// the exclusive product, then times its first factor); samples whose transmittance
+// is below t_term are dropped (a prefix, since the product only decreases), and the
+// warp stops at the first pass that terminates.
 // The sample position t and width delta are rebuilt from the crossing list in the
 // same FP32 operation order as the traversal/sampling step.  Optionally (training
 // targets of the proposal sampler) every composited weight is also added to the
@@ -49,33 +50,32 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_composite(
         const size_t sbase = (size_t)ray * cap;
         float T = 1.0f;
         float cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
-        // the next chunk's slot and crossing are loaded before this chunk is scanned
-        float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 xn = make_float2(0.f, 0.f);
-        if (lane < ns) {
-            vn = __ldg(slot_out + sbase + lane);
-            xn = __ldg(xing + xbase + lane / steps);
-        }
-        for (int s0 = 0; s0 < ns; s0 += 32) {
-            const int s = s0 + lane;
-            const bool valid = s < ns;
-            float e = 1.0f, sig = 0.f, t = 0.f;
-            const float4 v = vn;
-            const float2 x = xn;
-            if (s + 32 < ns) {
-                vn = __ldg(slot_out + sbase + s + 32);
-                xn = __ldg(xing + xbase + (s + 32) / steps);
-            }
-            if (valid) {
-                const int k = s / steps;
-                const int j = s - k * steps;
+        // 64 slots per pass, two consecutive slots per lane (one 32-byte load each)
+        for (int s0 = 0; s0 < ns; s0 += 64) {
+            const int sa = s0 + 2 * lane, sb = sa + 1;
+            const bool va = sa < ns, vb = sb < ns;
+            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+            if (va) v0 = __ldg(slot_out + sbase + sa);
+            if (vb) v1 = __ldg(slot_out + sbase + sb);
+            float e0 = 1.0f, e1 = 1.0f, t0 = 0.f, t1 = 0.f;
+            if (va) {
+                const int k = sa / steps;
+                const int j = sa - k * steps;
+                const float2 x = __ldg(xing + xbase + k);
                 const float delta = __fmul_rn(__fsub_rn(x.y, x.x), inv_steps);
-                t = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
-                sig = __fmul_rn(v.x, delta);
-                e = expf(-sig);
+                t0 = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
+                e0 = expf(-__fmul_rn(v0.x, delta));
             }
-            // inclusive multiplicative scan of e over the warp
-            float p = e;
+            if (vb) {
+                const int k = sb / steps;
+                const int j = sb - k * steps;
+                const float2 x = __ldg(xing + xbase + k);
+                const float delta = __fmul_rn(__fsub_rn(x.y, x.x), inv_steps);
+                t1 = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
+                e1 = expf(-__fmul_rn(v1.x, delta));
+            }
+            // inclusive multiplicative scan of the per-lane products e0 e1 over the warp
+            float p = e0 * e1;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const float y = __shfl_up_sync(0xffffffffu, p, o);
@@ -83,30 +83,46 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_composite(
             }
             float pex = __shfl_up_sync(0xffffffffu, p, 1);
             if (lane == 0) pex = 1.0f;
-            const float Tb = T * pex;          // transmittance in front of this sample
-            const bool active = valid && !(Tb < t_term);
-            if (active) {
-                const float w = Tb * (1.0f - e);
-                cr += w * v.y;
-                cg += w * v.z;
-                cb += w * v.w;
-                dd += w * t;
+            const float Ta = T * pex;  // transmittance in front of slot sa
+            const float Tb = Ta * e0;  // ... and of slot sb
+            const bool aa = va && !(Ta < t_term);
+            const bool ab = vb && aa && !(Tb < t_term);
+            if (aa) {
+                const float w = Ta * (1.0f - e0);
+                cr += w * v0.y;
+                cg += w * v0.z;
+                cb += w * v0.w;
+                dd += w * t0;
                 if (bins) {  // depth bin of the sample: floor((t - t0) / w), clamped to [0, 63]
-                    int k = bw > 0.0f ? (int)floorf(__fdiv_rn(__fsub_rn(t, r0), bw)) : 0;
+                    int k = bw > 0.0f ? (int)floorf(__fdiv_rn(__fsub_rn(t0, r0), bw)) : 0;
                     k = k < 0 ? 0 : (k > 63 ? 63 : k);
                     atomicAdd(&s_bins[wib][k], w);
                 }
             }
-            const unsigned act = __ballot_sync(0xffffffffu, active);
-            const unsigned val = __ballot_sync(0xffffffffu, valid);
-            composited += __popc(act);
-            const int last = 31 - __clz(act | 1u);  // last active lane (0 when none)
-            const float Tn = T * __shfl_sync(0xffffffffu, p, last);
-            if (act != val) {                       // terminated inside this chunk
-                T = act ? Tn : T;
+            if (ab) {
+                const float w = Tb * (1.0f - e1);
+                cr += w * v1.y;
+                cg += w * v1.z;
+                cb += w * v1.w;
+                dd += w * t1;
+                if (bins) {
+                    int k = bw > 0.0f ? (int)floorf(__fdiv_rn(__fsub_rn(t1, r0), bw)) : 0;
+                    k = k < 0 ? 0 : (k > 63 ? 63 : k);
+                    atomicAdd(&s_bins[wib][k], w);
+                }
+            }
+            const unsigned act_a = __ballot_sync(0xffffffffu, aa), act_b = __ballot_sync(0xffffffffu, ab);
+            const unsigned val_a = __ballot_sync(0xffffffffu, va), val_b = __ballot_sync(0xffffffffu, vb);
+            composited += __popc(act_a) + __popc(act_b);
+            if (act_a != val_a || act_b != val_b) {  // terminated inside this pass
+                // transmittance behind the last composited slot
+                const float after = ab ? Tb * e1 : Ta * e0;
+                const int last = 31 - __clz(act_a | 1u);
+                const float Tl = __shfl_sync(0xffffffffu, after, last);
+                T = act_a ? Tl : T;
                 break;
             }
-            T = Tn;
+            T = T * __shfl_sync(0xffffffffu, p, 31);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
