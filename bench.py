@@ -201,7 +201,14 @@ def run_ours(args):
     precs = [p for p in args.prec.split(",") if p]
     for prec in precs:
         try:
-            R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, prec)
+            if prec == "fp8s":  # E4M3 with static activation scales, calibrated on a view outside the timed set
+                R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, "fp32")
+                oc, dc = S.view_rays(cfg, 0, 1000 + rank, args.px, args.px)
+                amax = R.calibrate_fp8(torch.from_numpy(oc).cuda(), torch.from_numpy(dc).cuda(), cfg.hidden,
+                                       steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term)
+                R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, act_max=amax)
+            else:
+                R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, prec)
         except amnerf.AmnerfError as e:
             if e.status == amnerf.E_UNSUPPORTED:
                 continue
@@ -632,7 +639,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2")
-    ap.add_argument("--prec", default="fp32,bf16,fp8")
+    ap.add_argument("--prec", default="fp32,bf16,fp8,fp8s")
     ap.add_argument("--psnr-rays", type=int, default=262144)
     ap.add_argument("--ref-rays", type=int, default=16384)
     ap.add_argument("--views", type=int, default=None, help="views per GPU (default: the config's)")

@@ -210,6 +210,29 @@ AMNERF_API amnerf_status amnerf_get_tree(amnerf_ctx *ctx, amnerf_node *nodes_out
 AMNERF_API amnerf_status amnerf_load_mlps(amnerf_ctx *ctx, const amnerf_mlp_desc *desc, int n_leaves,
                                const float *weights_host);
 
+/* E4M3 networks with static activation scales.  Same as amnerf_load_mlps with
+ * desc->prec == AMNERF_FP8E4M3, except that every layer input is quantised with a
+ * fixed per-leaf, per-layer scale a_l = act_max[leaf][l] / 448 (instead of the
+ * default per-row scale max|row| / 448), folded at load time into the weight scales
+ * and biases, so the network epilogue does one fused multiply-add per value.
+ * act_max_host: HOST float32 [n_leaves][hidden], finite and >= 0: the largest
+ * |input| of hidden layer l (l = 0: the encoded input), e.g. from
+ * amnerf_calibrate_fp8; a zero entry selects scale 1.  Inputs beyond act_max
+ * saturate at +-448 a_l.  Synchronous.
+ * Errors: as amnerf_load_mlps; E_INVAL when desc->prec is not E4M3 or act_max is bad. */
+AMNERF_API amnerf_status amnerf_load_mlps_fp8_static(amnerf_ctx *ctx, const amnerf_mlp_desc *desc, int n_leaves,
+                                          const float *weights_host, const float *act_max_host);
+
+/* Calibration for amnerf_load_mlps_fp8_static: renders the rays with the loaded
+ * FP32 networks (amnerf_load_mlps with AMNERF_FP32) and records, per leaf and hidden
+ * layer l, the largest |input of layer l| over the samples of those rays.
+ * rays_o, rays_d: DEVICE float32 [n_rays][3]; params: as amnerf_render (the plain
+ * sampler).  act_max_host: HOST float32 [n_leaves][hidden] (leaves no sample reaches
+ * get 0).  Allocates temporary device buffers; synchronous.
+ * Errors: E_NOMLP, E_INVAL (not FP32, proposal requested, bad arguments), E_NOMEM, E_CUDA. */
+AMNERF_API amnerf_status amnerf_calibrate_fp8(amnerf_ctx *ctx, const float *rays_o, const float *rays_d,
+                                   int64_t n_rays, const amnerf_render_params *params, float *act_max_host);
+
 /* Render n_rays rays (the whole hot path: traverse, sample, group, network,
  * composite; Sec. 3.5 and Algorithm 1).
  * rays_o, rays_d: DEVICE float32 [n_rays][3] (x y z per ray); d need not be unit

@@ -69,6 +69,7 @@ def lib():
             _lib.or_encode.argtypes = [V, I, I, V]
             _lib.or_encode.restype = None
             _lib.or_mlp_eval.argtypes = [V, I, I, I, I, V, V, L, I, V, V]
+            _lib.or_mlp_input_absmax.argtypes = [V, I, I, I, I, V, V, L, V]
             _lib.or_render.argtypes = [V, V, V, I, V, I, I, I, I, V, V, L, I, I, D, V, I, I,
                                        V, V, V, V, V, V, V, V, V, V, V, V]
             _lib.or_prop_predict.argtypes = [V, V, V, V, L, V]
@@ -171,6 +172,17 @@ def mlp_eval(params_leaf, width: int, hidden: int, lx: int, ld: int, x, d, mode:
     if rc != 0:
         raise RuntimeError("oracle mlp failed")
     return out, raw
+
+
+def mlp_input_absmax(params_leaf, width: int, hidden: int, lx: int, ld: int, x, d) -> np.ndarray:
+    """Largest |input| of every hidden layer (layer 0: the encoding) over the samples
+    x, d of one leaf's network, in FP64."""
+    P = np.ascontiguousarray(params_leaf, F32)
+    x = np.ascontiguousarray(x, F64).reshape(-1, 3); d = np.ascontiguousarray(d, F64).reshape(-1, 3)
+    out = np.zeros(hidden, F64)
+    if lib().or_mlp_input_absmax(_p(P), width, hidden, lx, ld, _p(x), _p(d), len(x), _p(out)) != 0:
+        raise RuntimeError("oracle mlp failed")
+    return out
 
 
 def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, steps: int, cap: int,

@@ -442,13 +442,16 @@ static float or_sigmoid32(float z) { return 1.0f / (1.0f + expf(-z)); }
  * raw = W_o h_H + b_o (4 wide); sigma = softplus(raw_0), rgb = sigmoid(raw_1..3).
  * Each dot product is summed over the input index in ascending order, then the bias
  * is added.  out = sigma, r, g, b; raw (may be NULL) = pre-activation head. */
-static void or_mlp64(const float *P, int width, int hidden, int k0, const double *in, double *out, double *raw)
+static void or_mlp64(const float *P, int width, int hidden, int k0, const double *in, double *out, double *raw,
+                     double *in_absmax)
 {
     double h[OR_MAXK], g[OR_MAXW];
     int kin = k0;
     for (int i = 0; i < k0; i++) h[i] = in[i];
     const float *w = P;
     for (int l = 0; l < hidden; l++) {
+        if (in_absmax)  /* largest |input| of layer l (the E4M3 activation scale's range) */
+            for (int i = 0; i < kin; i++) in_absmax[l] = fabs(h[i]) > in_absmax[l] ? fabs(h[i]) : in_absmax[l];
         const float *b = w + (size_t)width * kin;
         for (int o = 0; o < width; o++) {
             double acc = 0.0;
@@ -528,8 +531,27 @@ int or_mlp_eval(const float *P, int width, int hidden, int lx, int ld, const dou
             double in[OR_MAXK];
             or_encode64(x + 3 * s, lx, in);
             or_encode64(d + 3 * s, ld, in + kx);
-            or_mlp64(P, width, hidden, k0, in, out + 4 * s, raw ? raw + 4 * s : NULL);
+            or_mlp64(P, width, hidden, k0, in, out + 4 * s, raw ? raw + 4 * s : NULL, NULL);
         }
+    }
+    return 0;
+}
+
+/* Largest |input| of every hidden layer over n samples of one leaf's network (FP64):
+ * amax[l] for l < hidden, l = 0 being the encoded input.  The range an E4M3
+ * activation scale a_l = amax[l] / 448 must cover (a quantisation choice; the paper
+ * uses half-precision networks, Sec. 4.1). */
+int or_mlp_input_absmax(const float *P, int width, int hidden, int lx, int ld, const double *x, const double *d,
+                        int64_t n, double *amax)
+{
+    int kx = 3 + 6 * lx, kd = 3 + 6 * ld, k0 = kx + kd;
+    if (width > OR_MAXW || k0 > OR_MAXK || lx > 32 || ld > 32) return -1;
+    for (int l = 0; l < hidden; l++) amax[l] = 0.0;
+    for (int64_t s = 0; s < n; s++) {
+        double in[OR_MAXK], o4[4];
+        or_encode64(x + 3 * s, lx, in);
+        or_encode64(d + 3 * s, ld, in + kx);
+        or_mlp64(P, width, hidden, k0, in, o4, NULL, amax);
     }
     return 0;
 }
@@ -715,7 +737,7 @@ static void or_render_ray(const or_job *J, int64_t r)
                 double t, dl, p[3], o4[4];
                 or_sample64(tin[k], tout[k], J->steps, j, o64, d64, &t, &dl, p);
                 or_encode64(p, J->lx, din);
-                or_mlp64(P, J->width, J->hidden, k0, din, o4, NULL);
+                or_mlp64(P, J->width, J->hidden, k0, din, o4, NULL, NULL);
                 if (J->slot_out) for (int i = 0; i < 4; i++) J->slot_out[(r * J->cap + s) * 4 + i] = o4[i];
                 if (stopped) continue;
                 double e = exp(-o4[0] * dl);

@@ -96,6 +96,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "amnerf_build_tree": ([V, V, I, V, ctypes.POINTER(amnerf_tree_params), ctypes.POINTER(I)], S),
         "amnerf_get_tree": ([V, V, I, ctypes.POINTER(I)], S),
         "amnerf_load_mlps": ([V, ctypes.POINTER(amnerf_mlp_desc), I, V], S),
+        "amnerf_load_mlps_fp8_static": ([V, ctypes.POINTER(amnerf_mlp_desc), I, V, V], S),
+        "amnerf_calibrate_fp8": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V], S),
         "amnerf_render": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V, V], S),
         "amnerf_render_debug": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V,
                                  ctypes.POINTER(amnerf_debug), V], S),
@@ -201,6 +203,28 @@ def amnerf_load_mlps(ctx, weights: np.ndarray, n_leaves: int, width: int, hidden
     w = np.ascontiguousarray(weights, dtype=np.float32)
     desc = amnerf_mlp_desc(lx, ld, hidden, width, prec)
     _check(ctx, load().amnerf_load_mlps(ctx, ctypes.byref(desc), n_leaves, _hptr(w)), "amnerf_load_mlps")
+
+
+def amnerf_load_mlps_fp8_static(ctx, weights: np.ndarray, n_leaves: int, width: int, hidden: int, lx: int, ld: int,
+                                act_max: np.ndarray) -> None:
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    a = np.ascontiguousarray(act_max, dtype=np.float32)
+    if a.size != n_leaves * hidden:
+        raise ValueError("act_max must hold n_leaves x hidden values")
+    desc = amnerf_mlp_desc(lx, ld, hidden, width, FP8E4M3)
+    _check(ctx, load().amnerf_load_mlps_fp8_static(ctx, ctypes.byref(desc), n_leaves, _hptr(w), _hptr(a)),
+           "amnerf_load_mlps_fp8_static")
+
+
+def amnerf_calibrate_fp8(ctx, o, d, n_leaves: int, hidden: int, steps: int = 8, cap: int = 64,
+                         t_term: float = 1e-4, bg=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Largest |input| of every hidden layer per leaf over the samples of these rays
+    (FP32 networks must be loaded); returns float32 [n_leaves, hidden]."""
+    out = np.zeros((n_leaves, hidden), dtype=np.float32)
+    p = _params(steps, cap, t_term, bg)
+    _check(ctx, load().amnerf_calibrate_fp8(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _hptr(out)),
+           "amnerf_calibrate_fp8")
+    return out
 
 
 def _params(steps: int, cap: int, t_term: float, bg, proposal: bool = False, coverage: float = 0.99,
@@ -380,8 +404,18 @@ class Renderer:
         nodes.sort(key=lambda n: n.leaf_id)
         return np.array([list(n.cell_lo) + list(n.cell_hi) for n in nodes], dtype=np.int64)
 
-    def load_mlps(self, weights, width, hidden, lx, ld, prec="fp32") -> None:
-        amnerf_load_mlps(self.ctx, weights, self.n_leaves, width, hidden, lx, ld, PRECISIONS.get(prec, prec))
+    def load_mlps(self, weights, width, hidden, lx, ld, prec="fp32", act_max=None) -> None:
+        """prec: "fp32", "bf16", "fp8" (per-row activation scales) or, with act_max
+        (see calibrate_fp8), E4M3 with static per-leaf, per-layer activation scales."""
+        if act_max is not None:
+            amnerf_load_mlps_fp8_static(self.ctx, weights, self.n_leaves, width, hidden, lx, ld, act_max)
+        else:
+            amnerf_load_mlps(self.ctx, weights, self.n_leaves, width, hidden, lx, ld, PRECISIONS.get(prec, prec))
+
+    def calibrate_fp8(self, o, d, hidden, steps=8, cap=64, t_term=1e-4):
+        torch = self._torch
+        amnerf_set_stream(self.ctx, torch.cuda.current_stream(o.device).cuda_stream)
+        return amnerf_calibrate_fp8(self.ctx, o, d, self.n_leaves, hidden, steps=steps, cap=cap, t_term=t_term)
 
     def render(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0), stats=False, out=None,
                proposal=False, coverage=0.99, max_bins=16):

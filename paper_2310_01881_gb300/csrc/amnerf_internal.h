@@ -69,6 +69,8 @@ struct MlpArgs {
     int steps, maxc, cap;
     float4* slot_out;
     int* err;
+    float* amax;            // FP32 path, calibration: per leaf x hidden layer, max |input of layer l| (or NULL)
+    int act_static;         // E4M3 path: static per-leaf, per-layer activation scales folded into the blob
 };
 cudaError_t launch_mlp_simt(cudaStream_t s, const MlpArgs& a, int grid);
 cudaError_t launch_mlp_tc(cudaStream_t s, const MlpArgs& a, int grid, int prec);
@@ -79,6 +81,9 @@ cudaError_t prepare_mlp_simt(int width, int hidden, int k0);
 // Failure-detection self-test of the bounded device waits (see amnerf_selftest_wait).
 cudaError_t launch_wait_selftest(cudaStream_t s, unsigned long long limit, int* err);
 size_t tc_leaf_stride_bytes(int width, int hidden, int k0, int prec);
+// act_max (E4M3 only, may be NULL): per hidden layer l, the largest |input of layer l|
+// of this leaf; non-NULL folds static activation scales into the packed leaf.
+void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0, int prec, const float* act_max);
 size_t simt_leaf_stride_floats(int width, int hidden, int k0);
 
 // K-d: per-ray compositing.

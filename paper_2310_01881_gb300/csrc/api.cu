@@ -60,6 +60,10 @@ struct amnerf_ctx {
     uint64_t* d_mask = nullptr;
     uint8_t* d_fallback = nullptr;
     float2* d_root = nullptr;
+    // E4M3 static activation scales; FP32-path calibration output while calibrating
+    bool act_static = false;
+    float* d_amax = nullptr;   // [n_leaves][hidden]
+    bool calibrating = false;
     // timing
     bool timing = false;
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -184,11 +188,6 @@ static amnerf_status ensure_prop_scratch(amnerf_ctx* ctx, size_t n) {
     return AMNERF_OK;
 }
 
-// Tensor-core layouts are produced by the tensor-core translation unit.
-namespace amnerf {
-void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0, int prec);
-}
-
 extern "C" {
 
 const char* amnerf_status_string(amnerf_status s) {
@@ -260,6 +259,7 @@ void amnerf_destroy(amnerf_ctx* ctx) {
     free_ray_scratch(ctx);
     dfree(ctx->d_nodes);
     dfree(ctx->d_weights);
+    dfree(ctx->d_amax);
     dfree(ctx->d_counts);
     dfree(ctx->d_offsets);
     dfree(ctx->d_tile_off);
@@ -316,8 +316,8 @@ amnerf_status amnerf_get_tree(amnerf_ctx* ctx, amnerf_node* nodes_out, int cap, 
     return AMNERF_OK;
 }
 
-amnerf_status amnerf_load_mlps(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int n_leaves,
-                               const float* weights_host) {
+static amnerf_status load_impl(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int n_leaves,
+                               const float* weights_host, const float* act_max) {
     if (!ctx || !desc || !weights_host) return fail(ctx, AMNERF_E_INVAL, "NULL argument");
     if (ctx->nodes.empty()) return fail(ctx, AMNERF_E_NOTREE, "build the tree first");
     if (n_leaves != ctx->n_leaves) return fail(ctx, AMNERF_E_INVAL, "n_leaves does not match the tree");
@@ -346,7 +346,8 @@ amnerf_status amnerf_load_mlps(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int
         if (stride == 0) return fail(ctx, AMNERF_E_UNSUPPORTED, "precision not built");
         blob.assign(stride * n_leaves, 0);
         for (int l = 0; l < n_leaves; ++l)
-            pack_tc_leaf(weights_host + per * l, blob.data() + stride * l, m.width, m.hidden, k0, (int)m.prec);
+            pack_tc_leaf(weights_host + per * l, blob.data() + stride * l, m.width, m.hidden, k0, (int)m.prec,
+                         act_max ? act_max + (size_t)l * m.hidden : nullptr);
     }
     int max_groups = 1;
     if (m.prec == AMNERF_FP32) {
@@ -363,8 +364,25 @@ amnerf_status amnerf_load_mlps(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int
     ctx->k0 = k0;
     ctx->leaf_stride = stride;
     ctx->max_groups = max_groups;
+    ctx->act_static = act_max != nullptr;
     ctx->mlp_loaded = true;
     return AMNERF_OK;
+}
+
+amnerf_status amnerf_load_mlps(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int n_leaves,
+                               const float* weights_host) {
+    return load_impl(ctx, desc, n_leaves, weights_host, nullptr);
+}
+
+amnerf_status amnerf_load_mlps_fp8_static(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int n_leaves,
+                                         const float* weights_host, const float* act_max_host) {
+    if (!ctx || !desc || !act_max_host) return fail(ctx, AMNERF_E_INVAL, "NULL argument");
+    if (desc->prec != AMNERF_FP8E4M3) return fail(ctx, AMNERF_E_INVAL, "static activation scales are for E4M3");
+    if (desc->hidden < 1 || desc->hidden > 8 || n_leaves < 1) return fail(ctx, AMNERF_E_INVAL, "bad shape");
+    for (size_t i = 0; i < (size_t)n_leaves * desc->hidden; ++i)
+        if (!(act_max_host[i] >= 0.0f) || !std::isfinite(act_max_host[i]))
+            return fail(ctx, AMNERF_E_INVAL, "act_max must be finite and >= 0");
+    return load_impl(ctx, desc, n_leaves, weights_host, act_max_host);
 }
 
 static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* rd, int64_t n,
@@ -436,6 +454,8 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         a.cap = cap;
         a.slot_out = ctx->d_slot;
         a.err = ctx->d_err;
+        a.amax = ctx->calibrating ? ctx->d_amax : nullptr;
+        a.act_static = ctx->act_static ? 1 : 0;
         a.tile_counter = reinterpret_cast<uint32_t*>(ctx->d_stats + 6);
         a.t_begin = 0;
         a.t_end = 0xffffffffu;
@@ -530,6 +550,40 @@ amnerf_status amnerf_render(amnerf_ctx* ctx, const float* rays_o, const float* r
                             const amnerf_render_params* params, float* rgb, float* depth, float* opacity,
                             amnerf_stats* stats) {
     return render_impl(ctx, rays_o, rays_d, n_rays, params, rgb, depth, opacity, nullptr, stats);
+}
+
+amnerf_status amnerf_calibrate_fp8(amnerf_ctx* ctx, const float* rays_o, const float* rays_d, int64_t n_rays,
+                                   const amnerf_render_params* params, float* act_max_host) {
+    if (!ctx || !act_max_host) return fail(ctx, AMNERF_E_INVAL, "NULL argument");
+    if (!ctx->mlp_loaded) return fail(ctx, AMNERF_E_NOMLP, "load the FP32 networks first");
+    if (ctx->desc.prec != AMNERF_FP32) return fail(ctx, AMNERF_E_INVAL, "calibration runs the FP32 networks");
+    if (params && params->use_proposal) return fail(ctx, AMNERF_E_INVAL, "calibrate with the plain sampler");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t cnt = (size_t)ctx->n_leaves * ctx->desc.hidden;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    dfree(ctx->d_amax);
+    CK(cudaMalloc((void**)&ctx->d_amax, sizeof(float) * cnt), "calibration allocation");
+    CK(cudaMemsetAsync(ctx->d_amax, 0, sizeof(float) * cnt, ctx->stream), "memset");
+    float *rgb = nullptr, *aux = nullptr;
+    if (n_rays > 0) {
+        CK(cudaMalloc((void**)&rgb, sizeof(float) * 3 * (size_t)n_rays), "calibration allocation");
+        if (cudaMalloc((void**)&aux, sizeof(float) * 2 * (size_t)n_rays) != cudaSuccess) {
+            cudaFree(rgb);
+            cudaGetLastError();
+            return fail(ctx, AMNERF_E_NOMEM, "calibration allocation");
+        }
+    }
+    ctx->calibrating = true;
+    amnerf_status st = render_impl(ctx, rays_o, rays_d, n_rays, params, rgb, aux, aux + (n_rays > 0 ? n_rays : 0),
+                                   nullptr, nullptr);
+    ctx->calibrating = false;
+    if (st == AMNERF_OK) st = amnerf_sync(ctx);
+    if (st == AMNERF_OK &&
+        cudaMemcpy(act_max_host, ctx->d_amax, sizeof(float) * cnt, cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = fail(ctx, AMNERF_E_CUDA, "calibration copy");
+    cudaFree(rgb);
+    cudaFree(aux);
+    return st;
 }
 
 amnerf_status amnerf_render_debug(amnerf_ctx* ctx, const float* rays_o, const float* rays_d, int64_t n_rays,

@@ -110,6 +110,18 @@ __device__ __forceinline__ void encode_simt(const float p[3], int L, float* __re
     }
 }
 
+// Calibration: the largest value over the valid rows of a feature-major tile
+// (non-negative inputs), merged into *dst (one atomic per warp).
+__device__ __forceinline__ void tile_absmax(const float* __restrict__ t, int nfeat, int nvalid, float* dst) {
+    if (threadIdx.x >= kTileRows) return;
+    const int row = threadIdx.x;
+    float m = 0.0f;
+    if (row < nvalid)
+        for (int f = 0; f < nfeat; ++f) m = fmaxf(m, fabsf(t[(size_t)f * kTileRows + row]));
+    const unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(m));  // m >= 0: bit order = value order
+    if ((row & 31) == 0 && u) atomicMax(reinterpret_cast<unsigned*>(dst), u);
+}
+
 template <int W>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
     extern __shared__ __align__(16) float sm[];
@@ -166,6 +178,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
             sSlot[row] = slot;
         }
         __syncthreads();
+        // rows of this tile that hold samples (calibration counts only those)
+        const int nvalid = (int)min((uint32_t)kTileRows, (endc - first) * (uint32_t)g.steps);
+        float* amax = g.amax ? g.amax + (size_t)leaf * g.hidden : nullptr;
+        if (amax) tile_absmax(sA, g.k0, nvalid, amax);
         const float* w = sW;
         const float* in = sA;
         float* out = sH;
@@ -173,6 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
         for (int l = 0; l < g.hidden; ++l) {
             gemm_layer<W>(in, kin, w, w + (size_t)kin * W, out);
             __syncthreads();
+            if (amax && l + 1 < g.hidden) tile_absmax(out, W, nvalid, amax + l + 1);
             w += (size_t)kin * W + W;
             kin = W;
             float* tmp = const_cast<float*>(in);

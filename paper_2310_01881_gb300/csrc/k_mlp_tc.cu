@@ -65,9 +65,13 @@ __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / 
 // adds nothing; its head is a 16-row BF16 matrix (rows 0..3 used, bias in column
 // width) run as one more MMA.  E4M3 keeps kh = width, adds the FP32 bias in the
 // epilogue (an E4M3 bias would lose too much) and computes the head in FP32.
+// E4M3 with static activation scales (act_max known per leaf and layer) folds them
+// in at packing: layer l's pre-activation is acc * sw[l][n] + bias[l][n] with
+// sw = s_w a_l / a_(l+1), bias = b / a_(l+1) (the last layer: s_w a_l and b), where
+// a_l = act_max_l / 448, so relu(pre) is already the next layer's E4M3 input.
 struct TcLayout {
     int width, hidden, k0, k0p, kh, es;
-    size_t w0, wh, wo, sw, bias, stride;
+    size_t w0, wh, wo, sw, bias, enc, stride;
     __host__ __device__ TcLayout(int w, int h, int k, bool f8)
         : width(w), hidden(h), k0(k), k0p(round_up(f8 ? k : k + 1, f8 ? 32 : 16)), kh(f8 ? w : w + 16),
           es(f8 ? 1 : 2) {
@@ -76,7 +80,8 @@ struct TcLayout {
         wo = wh + (size_t)(h - 1) * w * kh * es;  // head: E4M3 path FP32 [width][4]; BF16 path 16 x kh BF16
         sw = wo + (f8 ? (size_t)w * 4 * 4 : (size_t)16 * kh * 2);
         bias = sw + (f8 ? (size_t)h * w * 4 : 0);
-        const size_t end = bias + (size_t)h * w * 4 + 16;
+        enc = bias + (size_t)h * w * 4 + 16;  // E4M3 static scales: 1 / (encoding scale)
+        const size_t end = enc + 16;
         stride = (end + 127) / 128 * 128;
     }
 };
@@ -238,6 +243,18 @@ __device__ __forceinline__ float2 mul_f32x2(float2 a, float2 b) {
     memcpy(&ua, &a, 8);
     memcpy(&ub, &b, 8);
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(ud) : "l"(ua), "l"(ub));
+    float2 d;
+    memcpy(&d, &ud, 8);
+    return d;
+}
+
+// (a0 * b0 + c0, a1 * b1 + c1) with one packed FP32 instruction.
+__device__ __forceinline__ float2 fma2v(float2 a, float2 b, float2 c) {
+    unsigned long long ua, ub, uc, ud;
+    memcpy(&ua, &a, 8);
+    memcpy(&ub, &b, 8);
+    memcpy(&uc, &c, 8);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(ud) : "l"(ua), "l"(ub), "l"(uc));
     float2 d;
     memcpy(&d, &ud, 8);
     return d;
@@ -574,11 +591,17 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     store_chunk<2>(a_row, f);
                 } else {
                     static_assert(K0P == 96, "E4M3 layer-0 input is stored as 16 + 8 columns");
-                    float m = 0.0f;
+                    float inv;
+                    if (g.act_static) {  // the leaf's static encoding scale (in the weight blob)
+                        inv = *reinterpret_cast<const float*>(wbuf + lay.enc);
+                        s_a = 1.0f;
+                    } else {  // this row's own scale
+                        float m = 0.0f;
 #pragma unroll
-                    for (int i = 0; i < K0; ++i) m = fmaxf(m, fabsf(f[i]));
-                    const float inv = m > 0.0f ? 448.0f / m : 0.0f;
-                    s_a = m > 0.0f ? m / 448.0f : 0.0f;
+                        for (int i = 0; i < K0; ++i) m = fmaxf(m, fabsf(f[i]));
+                        inv = m > 0.0f ? 448.0f / m : 0.0f;
+                        s_a = m > 0.0f ? m / 448.0f : 0.0f;
+                    }
                     uint32_t w[24];
 #pragma unroll
                     for (int i = 0; i < 24; ++i) {
@@ -649,10 +672,15 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     if constexpr (F8) {
                         const float4 bb = *reinterpret_cast<const float4*>(b + c0);
                         const float4 ss = *reinterpret_cast<const float4*>(sw + c0);
-                        p01 = fma_f32x2(s_a, mul_f32x2(make_float2(v[0], v[1]), make_float2(ss.x, ss.y)),
-                                        make_float2(bb.x, bb.y));
-                        p23 = fma_f32x2(s_a, mul_f32x2(make_float2(v[2], v[3]), make_float2(ss.z, ss.w)),
-                                        make_float2(bb.z, bb.w));
+                        if (g.act_static) {  // scales folded into sw and the bias
+                            p01 = fma2v(make_float2(v[0], v[1]), make_float2(ss.x, ss.y), make_float2(bb.x, bb.y));
+                            p23 = fma2v(make_float2(v[2], v[3]), make_float2(ss.z, ss.w), make_float2(bb.z, bb.w));
+                        } else {
+                            p01 = fma_f32x2(s_a, mul_f32x2(make_float2(v[0], v[1]), make_float2(ss.x, ss.y)),
+                                            make_float2(bb.x, bb.y));
+                            p23 = fma_f32x2(s_a, mul_f32x2(make_float2(v[2], v[3]), make_float2(ss.z, ss.w)),
+                                            make_float2(bb.z, bb.w));
+                        }
                     } else {  // the bias is already in the accumulator
                         p01 = make_float2(v[0], v[1]);
                         p23 = make_float2(v[2], v[3]);
@@ -678,6 +706,23 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                             uint32_t c8[8] = {pack_bf16(1.0f, 0.0f), 0u, 0u, 0u, 0u, 0u, 0u, 0u};
                             tmem_st8(a_row + (uint32_t)(W / 2), c8);
                         }
+                    } else if (g.act_static) {
+                        // relu(pre) is already in the next layer's E4M3 scale
+                        uint32_t pk[W / 4];
+#pragma unroll
+                        for (int h = 0; h < W / 32; ++h) {
+                            float v[32];
+                            tmem_ld32(d_row + 32u * h, v);
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                float2 p01, p23;
+                                pre4(v + 4 * c, 32 * h + 4 * c, p01, p23);
+                                pk[8 * h + c] = pack_e4m3x4(fmaxf(p01.x, 0.f), fmaxf(p01.y, 0.f), fmaxf(p23.x, 0.f),
+                                                            fmaxf(p23.y, 0.f));
+                            }
+                        }
+                        if constexpr (W / 4 == 16) tmem_st16(a_row, pk);
+                        else tmem_st8(a_row, pk);
                     } else {
                         float hv[W];
 #pragma unroll
@@ -864,9 +909,11 @@ size_t tc_leaf_stride_bytes(int width, int hidden, int k0, int prec) {
     return TcLayout(width, hidden, k0, prec == 2).stride;
 }
 
-void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0, int prec) {
+void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0, int prec, const float* act_max) {
     const bool f8 = prec == 2;
     const TcLayout lay(width, hidden, k0, f8);
+    // static activation scale of layer l's input (1 when the activations are all zero)
+    auto act_scale = [&](int l) { return act_max[l] > 0.0f ? act_max[l] / 448.0f : 1.0f; };
     std::memset(dst, 0, lay.stride);
     const float* w = src;
     float* bias = reinterpret_cast<float*>(dst + lay.bias);
@@ -894,9 +941,18 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
         }
         w += (size_t)width * kin;
         for (int n = 0; n < width; ++n) bias[(size_t)l * width + n] = w[n];
+        if (f8 && act_max) {  // fold a_l and 1 / a_(l+1) into the channel scale and bias
+            const float al = act_scale(l);
+            const float inv_next = l + 1 < hidden ? 1.0f / act_scale(l + 1) : 1.0f;
+            for (int n = 0; n < width; ++n) {
+                sw[(size_t)l * width + n] = sw[(size_t)l * width + n] * al * inv_next;
+                bias[(size_t)l * width + n] *= inv_next;
+            }
+        }
         w += width;
         kin = width;
     }
+    if (f8 && act_max) *reinterpret_cast<float*>(dst + lay.enc) = 1.0f / act_scale(0);
     if (f8) {
         float* wo = reinterpret_cast<float*>(dst + lay.wo);
         for (int k = 0; k < width; ++k)

@@ -352,6 +352,87 @@ def test_c2_fp8_sampled_psnr(R):
 
 
 # ----------------------------------------------------------------------------------
+# E4M3 with static per-leaf, per-layer activation scales: the calibration (FP32
+# networks on the GPU) against the oracle's input ranges over the same samples, then
+# the network with those scales against the FP64 oracle, calibrated on another view.
+# ----------------------------------------------------------------------------------
+
+def _gpu_weights(R, cfg, grid, seed):
+    return S.xavier_weights(seed, S.leaf_mean_density(grid, R.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+
+
+def test_fp8_calibration_matches_oracle_input_ranges(R):
+    cfg = S.CONFIGS["c1"]
+    _, tree, P = _setup(R, cfg, 0, prec="fp32")
+    o, d = _rays(cfg, 0)
+    got = R.calibrate_fp8(_dev(o), _dev(d), cfg.hidden, steps=cfg.steps, cap=cfg.cap)
+    maxc = cfg.cap // cfg.steps
+    nx, leaf, tin, tout = O.traverse(tree, o, d, maxc, mode=1)
+    _, _, x = O.samples(o, d, nx, tin, tout, maxc, cfg.steps, cfg.cap, mode=1)
+    Pl = np.asarray(P).reshape(tree.n_leaves, -1)
+    want = np.zeros((tree.n_leaves, cfg.hidden))
+    valid = np.arange(maxc)[None, :] < nx[:, None]
+    for lf in range(tree.n_leaves):
+        rr, kk = np.nonzero(valid & (leaf == lf))
+        if len(rr) == 0:
+            continue
+        slots = (kk[:, None] * cfg.steps + np.arange(cfg.steps)[None, :]).ravel()
+        rows = np.repeat(rr, cfg.steps)
+        want[lf] = O.mlp_input_absmax(Pl[lf], cfg.width, cfg.hidden, cfg.lx, cfg.ld, x[rows, slots], d[rows])
+    assert (want > 0).any()
+    np.testing.assert_allclose(got, want, rtol=2e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("seed", [0, 2])
+def test_c1_fp8_static_scales_against_fp64_oracle(R, seed):
+    cfg = S.CONFIGS["c1"]
+    grid, tree, P = _setup(R, cfg, seed, prec="fp32")
+    oc, dc = S.view_rays(cfg, seed, 7, 64, 64)  # calibration view, not the test view
+    amax = R.calibrate_fp8(_dev(oc), _dev(dc), cfg.hidden, steps=cfg.steps, cap=cfg.cap)
+    R.load_mlps(_gpu_weights(R, cfg, grid, seed), cfg.width, cfg.hidden, cfg.lx, cfg.ld, act_max=amax)
+    o, d = _rays(cfg, seed)
+    rgb, depth, opac = [t.cpu().numpy() for t in R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)]
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=0, threads=8)
+    psnr = _psnr(rgb, ref["rgb"])
+    err = np.abs(rgb - ref["rgb"]).max()
+    print(f"fp8 static c1 seed {seed}: PSNR {psnr:.2f} dB, max abs rgb {err:.3e}")
+    assert np.all(np.isfinite(rgb))
+    assert psnr >= 30.0
+    assert err <= 0.1
+
+
+def test_c2_fp8_static_scales_sampled_psnr(R):
+    cfg = S.CONFIGS["c2"]
+    grid, tree, P = _setup(R, cfg, 0, prec="fp32")
+    oc, dc = S.view_rays(cfg, 0, 100, 400, 400)  # calibration view outside the 8 test views
+    amax = R.calibrate_fp8(_dev(oc), _dev(dc), cfg.hidden, steps=cfg.steps, cap=cfg.cap)
+    R.load_mlps(_gpu_weights(R, cfg, grid, 0), cfg.width, cfg.hidden, cfg.lx, cfg.ld, act_max=amax)
+    o, d = _rays(cfg, 0, cfg.views)
+    rgb = R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)[0].cpu().numpy()
+    idx = S.ray_subset(len(o), 4096, 2)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o[idx], d[idx], cfg.steps, cfg.cap, mode=0,
+                   threads=16)
+    psnr = _psnr(rgb[idx], ref["rgb"])
+    print(f"fp8 static c2: PSNR {psnr:.2f} dB, max abs {np.abs(rgb[idx] - ref['rgb']).max():.3e}")
+    assert np.all(np.isfinite(rgb)) and psnr >= 30.0
+
+
+def test_fp8_static_entry_points_reject_bad_use(R):
+    from paper_2310_01881_gb300 import amnerf
+    cfg = S.CONFIGS["c1"]
+    grid, _, _ = _setup(R, cfg, 0, prec="bf16")
+    o, d = _rays(cfg, 0, 1, 8, 8)
+    with pytest.raises(amnerf.AmnerfError) as e:        # calibration needs the FP32 networks
+        R.calibrate_fp8(_dev(o), _dev(d), cfg.hidden, steps=cfg.steps, cap=cfg.cap)
+    assert e.value.status == amnerf.E_INVAL
+    W = _gpu_weights(R, cfg, grid, 0)
+    bad = np.full((R.n_leaves, cfg.hidden), np.nan, np.float32)
+    with pytest.raises(amnerf.AmnerfError) as e:
+        R.load_mlps(W, cfg.width, cfg.hidden, cfg.lx, cfg.ld, act_max=bad)
+    assert e.value.status == amnerf.E_INVAL
+
+
+# ----------------------------------------------------------------------------------
 # Launch configurations, CUDA-graph capture and 64-bit sample slots.  A sample's
 # network output does not depend on which worker computes it, so every schedule
 # must give bit-identical pixels.

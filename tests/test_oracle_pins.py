@@ -385,6 +385,28 @@ def test_mlp_matches_library_matmul_chain():
     np.testing.assert_allclose(out32, out, atol=2e-4)
 
 
+def test_mlp_input_absmax_matches_matmul_chain():
+    """Per-layer input ranges (the E4M3 static scales' calibration) against the same
+    numpy float64 chain: layer 0 is the encoding, layer l the ReLU output of l - 1."""
+    width, hidden, lx, ld = 64, 4, 10, 4
+    rng = np.random.default_rng(11)
+    P = S.xavier_weights(2, np.array([3.0]), width, hidden, lx, ld)
+    P = P + rng.normal(0, 0.05, P.shape).astype(np.float32)
+    x = rng.uniform(-1, 1, (48, 3)); d = rng.normal(size=(48, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+    got = O.mlp_input_absmax(P, width, hidden, lx, ld, x, d)
+    feats = np.stack([np.concatenate([O.encode(a, lx), O.encode(b, ld)]) for a, b in zip(x, d)])
+    k0 = feats.shape[1]
+    want, h, ofs, kin = [], feats, 0, k0
+    for _ in range(hidden):
+        want.append(np.abs(h).max())
+        W = P[ofs: ofs + width * kin].astype(np.float64).reshape(width, kin); ofs += width * kin
+        b = P[ofs: ofs + width].astype(np.float64); ofs += width
+        h = np.maximum(h @ W.T + b, 0.0)
+        kin = width
+    np.testing.assert_allclose(got, want, rtol=1e-12)
+    assert 0.999 <= got[0] <= max(1.0, np.abs(x).max(), np.abs(d).max())   # sin/cos of many octaves near 1
+
+
 def test_mlp_one_hot_routing_closed_form():
     """W0 routes input feature f to hidden unit 0, identities pass it on, the head
     copies it: a transposed operand or a wrong offset breaks the equalities."""
