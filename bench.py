@@ -131,6 +131,14 @@ def workload(cfg, rank: int, views: int | None = None, px: int | None = None):
     return grid, np.concatenate(os_), np.concatenate(ds_)
 
 
+def workload_name(cfg, args) -> str:
+    """The benchmark workload, as both arms name it in `config`."""
+    return (f"{cfg.name}: {args.px or cfg.px_w}x{args.px or cfg.px_h} x {args.views or cfg.views} views per GPU, "
+            f"{cfg.G}^3 guidance grid, depth<={cfg.max_depth}"
+            + (f" (mass<=1/{round(1 / cfg.leaf_mass_frac)})" if cfg.leaf_mass_frac > 0 else "")
+            + f", {cfg.hidden}x{cfg.width} MLP per leaf, {cfg.steps} samples/crossing, cap {cfg.cap}")
+
+
 def barrier():
     """Barrier over the ranks of the default process group (no-op for one rank)."""
     import torch.distributed as dist
@@ -328,9 +336,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[head],
         "data": "synthetic",
-        "config": {"workload": f"{cfg.name}: {args.px or cfg.px_w}x{args.px or cfg.px_h} x {args.views or cfg.views} views per GPU, "
-                               f"{cfg.G}^3 guidance grid, "
-                               f"depth<=8 (mass<=1/256), 4x64 MLP per leaf, 8 samples/crossing, cap 192",
+        "config": {"workload": workload_name(cfg, args),
                    "rays_per_step": rays_all, "samples_per_step": samples_all, "leaves": R.n_leaves,
                    "l2": "inputs larger than L2 (per-step working set ~10 GB)", "parallelism": f"replicas x{world}"},
         "mrays_per_s": round(rays_all / (hr["ms"] * 1e-3) / 1e6, 3),
@@ -623,7 +629,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Msamples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t * 1e3 / len(times), 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{cfg.name}: 800x800 x {cfg.views} views, {per_step} seeded rays per step"},
+        "config": {"workload": workload_name(cfg, args), "sample_rays_per_step": per_step},
         "mrays_per_s": round(per_step * len(times) / tot_t / 1e6, 6),
         "cpu_baseline": {"value": round(value, 6), "unit": "Msamples/s", "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} seeded rays per step of the 800x800x8 workload"},
