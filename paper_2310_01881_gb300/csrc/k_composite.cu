@@ -5,12 +5,13 @@
 // tau = sigma * delta, e = exp(-tau), alpha = 1 - e, w = T alpha; C += w c,
 // D += w t, T = T e.  rgb = C + T bg, depth = D, opacity = 1 - T.
 //
-// One warp per ray handles 64 consecutive slots per pass, two per lane: the per-lane
-// products of the factors e are combined by a warp-shuffle multiplicative scan, so
-// each lane gets the transmittance in front of its two samples (the carried T times
-// the exclusive product, then times its first factor); samples whose transmittance
-// is below t_term are dropped (a prefix, since the product only decreases), and the
-// warp stops at the first pass that terminates.
+// One warp per ray handles 32 SPL consecutive slots per pass, SPL per lane (1 for
+// rays of at most 32 samples, else 2): the per-lane products of the factors e are
+// combined by a warp-shuffle multiplicative scan, so each lane gets the
+// transmittance in front of its samples (the carried T times the exclusive product,
+// then times its earlier factors); samples whose transmittance is below t_term are
+// dropped (a prefix, since the product only decreases), and the warp stops at the
+// first pass that terminates.
 // The sample position t and width delta are rebuilt from the crossing list in the
 // same FP32 operation order as the traversal/sampling step.  Optionally (training
 // targets of the proposal sampler) every composited weight is also added to the
@@ -22,7 +23,93 @@ namespace {
 
 constexpr int kWarpsPerBlock = 8;
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_composite(
+struct RayAcc {
+    float T, cr, cg, cb, dd;
+    uint32_t composited;
+};
+
+// One ray by one warp, SPL consecutive slots per lane (32 SPL slots per pass).
+template <int SPL>
+__device__ __forceinline__ void composite_ray(const float2* __restrict__ xing, const float4* __restrict__ slot_out,
+                                              int ns, int steps, float inv_steps, size_t xbase, size_t sbase,
+                                              float t_term, int lane, float r0, float bw, float* sbins, RayAcc& A) {
+    for (int s0 = 0; s0 < ns; s0 += 32 * SPL) {
+        float4 v[SPL];
+        float e[SPL], t[SPL];
+        bool val[SPL];
+#pragma unroll
+        for (int i = 0; i < SPL; ++i) {
+            const int s = s0 + SPL * lane + i;
+            val[i] = s < ns;
+            v[i] = val[i] ? __ldg(slot_out + sbase + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < SPL; ++i) {
+            e[i] = 1.0f;
+            t[i] = 0.f;
+            if (val[i]) {
+                const int s = s0 + SPL * lane + i;
+                const int k = s / steps;
+                const int j = s - k * steps;
+                const float2 x = __ldg(xing + xbase + k);
+                const float delta = __fmul_rn(__fsub_rn(x.y, x.x), inv_steps);
+                t[i] = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
+                e[i] = expf(-__fmul_rn(v[i].x, delta));
+            }
+        }
+        // inclusive multiplicative scan of the per-lane products over the warp
+        float p = e[0];
+#pragma unroll
+        for (int i = 1; i < SPL; ++i) p *= e[i];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(0xffffffffu, p, o);
+            if (lane >= o) p = p * y;
+        }
+        float pex = __shfl_up_sync(0xffffffffu, p, 1);
+        if (lane == 0) pex = 1.0f;
+        float Tc = A.T * pex;  // transmittance in front of this lane's first slot
+        float after = Tc;      // ... and behind its last composited slot
+        bool prev = true;
+        unsigned act_bits[SPL], val_bits[SPL];
+#pragma unroll
+        for (int i = 0; i < SPL; ++i) {
+            const bool act = val[i] && prev && !(Tc < t_term);
+            if (act) {
+                const float w = Tc * (1.0f - e[i]);
+                A.cr += w * v[i].y;
+                A.cg += w * v[i].z;
+                A.cb += w * v[i].w;
+                A.dd += w * t[i];
+                if (sbins) {  // depth bin of the sample: floor((t - t0) / w), clamped to [0, 63]
+                    int k = bw > 0.0f ? (int)floorf(__fdiv_rn(__fsub_rn(t[i], r0), bw)) : 0;
+                    k = k < 0 ? 0 : (k > 63 ? 63 : k);
+                    atomicAdd(&sbins[k], w);
+                }
+                after = Tc * e[i];
+            }
+            Tc = Tc * e[i];
+            prev = act;
+            act_bits[i] = __ballot_sync(0xffffffffu, act);
+            val_bits[i] = __ballot_sync(0xffffffffu, val[i]);
+        }
+        bool term = false;
+#pragma unroll
+        for (int i = 0; i < SPL; ++i) {
+            A.composited += __popc(act_bits[i]);
+            term = term || act_bits[i] != val_bits[i];
+        }
+        if (term) {  // terminated inside this pass: T behind the last composited slot
+            const int last = 31 - __clz(act_bits[0] | 1u);
+            const float Tl = __shfl_sync(0xffffffffu, after, last);
+            A.T = act_bits[0] ? Tl : A.T;
+            break;
+        }
+        A.T = A.T * __shfl_sync(0xffffffffu, p, 31);
+    }
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
     const uint8_t* __restrict__ n_x, const float2* __restrict__ xing, const float4* __restrict__ slot_out,
     uint32_t n, int steps, int maxc, int cap, float t_term, float bg0, float bg1, float bg2,
     float* __restrict__ rgb, float* __restrict__ depth, float* __restrict__ opacity,
@@ -48,82 +135,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_composite(
         const float inv_steps = 1.0f / (float)steps;  // exact: steps is a power of two
         const size_t xbase = (size_t)ray * maxc;
         const size_t sbase = (size_t)ray * cap;
-        float T = 1.0f;
-        float cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
-        // 64 slots per pass, two consecutive slots per lane (one 32-byte load each)
-        for (int s0 = 0; s0 < ns; s0 += 64) {
-            const int sa = s0 + 2 * lane, sb = sa + 1;
-            const bool va = sa < ns, vb = sb < ns;
-            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-            if (va) v0 = __ldg(slot_out + sbase + sa);
-            if (vb) v1 = __ldg(slot_out + sbase + sb);
-            float e0 = 1.0f, e1 = 1.0f, t0 = 0.f, t1 = 0.f;
-            if (va) {
-                const int k = sa / steps;
-                const int j = sa - k * steps;
-                const float2 x = __ldg(xing + xbase + k);
-                const float delta = __fmul_rn(__fsub_rn(x.y, x.x), inv_steps);
-                t0 = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
-                e0 = expf(-__fmul_rn(v0.x, delta));
-            }
-            if (vb) {
-                const int k = sb / steps;
-                const int j = sb - k * steps;
-                const float2 x = __ldg(xing + xbase + k);
-                const float delta = __fmul_rn(__fsub_rn(x.y, x.x), inv_steps);
-                t1 = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
-                e1 = expf(-__fmul_rn(v1.x, delta));
-            }
-            // inclusive multiplicative scan of the per-lane products e0 e1 over the warp
-            float p = e0 * e1;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float y = __shfl_up_sync(0xffffffffu, p, o);
-                if (lane >= o) p = p * y;
-            }
-            float pex = __shfl_up_sync(0xffffffffu, p, 1);
-            if (lane == 0) pex = 1.0f;
-            const float Ta = T * pex;  // transmittance in front of slot sa
-            const float Tb = Ta * e0;  // ... and of slot sb
-            const bool aa = va && !(Ta < t_term);
-            const bool ab = vb && aa && !(Tb < t_term);
-            if (aa) {
-                const float w = Ta * (1.0f - e0);
-                cr += w * v0.y;
-                cg += w * v0.z;
-                cb += w * v0.w;
-                dd += w * t0;
-                if (bins) {  // depth bin of the sample: floor((t - t0) / w), clamped to [0, 63]
-                    int k = bw > 0.0f ? (int)floorf(__fdiv_rn(__fsub_rn(t0, r0), bw)) : 0;
-                    k = k < 0 ? 0 : (k > 63 ? 63 : k);
-                    atomicAdd(&s_bins[wib][k], w);
-                }
-            }
-            if (ab) {
-                const float w = Tb * (1.0f - e1);
-                cr += w * v1.y;
-                cg += w * v1.z;
-                cb += w * v1.w;
-                dd += w * t1;
-                if (bins) {
-                    int k = bw > 0.0f ? (int)floorf(__fdiv_rn(__fsub_rn(t1, r0), bw)) : 0;
-                    k = k < 0 ? 0 : (k > 63 ? 63 : k);
-                    atomicAdd(&s_bins[wib][k], w);
-                }
-            }
-            const unsigned act_a = __ballot_sync(0xffffffffu, aa), act_b = __ballot_sync(0xffffffffu, ab);
-            const unsigned val_a = __ballot_sync(0xffffffffu, va), val_b = __ballot_sync(0xffffffffu, vb);
-            composited += __popc(act_a) + __popc(act_b);
-            if (act_a != val_a || act_b != val_b) {  // terminated inside this pass
-                // transmittance behind the last composited slot
-                const float after = ab ? Tb * e1 : Ta * e0;
-                const int last = 31 - __clz(act_a | 1u);
-                const float Tl = __shfl_sync(0xffffffffu, after, last);
-                T = act_a ? Tl : T;
-                break;
-            }
-            T = T * __shfl_sync(0xffffffffu, p, 31);
-        }
+        RayAcc A{1.0f, 0.f, 0.f, 0.f, 0.f, 0u};
+        float* sb = bins ? s_bins[wib] : nullptr;
+        // short rays: one slot per lane; longer ones: two (twice the bytes in flight)
+        if (ns <= 32) composite_ray<1>(xing, slot_out, ns, steps, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
+        else composite_ray<2>(xing, slot_out, ns, steps, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
+        float T = A.T, cr = A.cr, cg = A.cg, cb = A.cb, dd = A.dd;
+        composited = A.composited;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             cr += __shfl_xor_sync(0xffffffffu, cr, o);
