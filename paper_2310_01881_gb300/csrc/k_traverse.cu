@@ -2,9 +2,10 @@
 // (Sec. 3.5, Algorithm 1 "Traverse"; sampling of Algorithm 1 "Sampling" is defined
 // on the emitted crossings and is evaluated where the samples are consumed).
 //
-// One thread per ray walks the tree front to back with a short stack (near child
-// first: the child on the origin's side of the split plane).  Every visited node is
-// tested with the slab method in a fixed FP32 operation order -- per axis
+// One thread per ray walks the tree front to back (near child first: the child on
+// the origin's side of the split plane; far children wait on a short register
+// stack).  Every visited node is tested with the slab method in a fixed FP32
+// operation order -- per axis
 // t0 = (lo - o) * inv, t1 = (hi - o) * inv with inv = 1 / d correctly rounded, no
 // fused multiply-add, NaN-ignoring min/max, entry clamped at 0 -- so the crossing
 // list is reproducible bit for bit.  A node whose interval is empty is pruned (its
@@ -82,9 +83,12 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
             d[a] = __ldg(rd + 3 * (size_t)r + a);
             inv[a] = __frcp_rn(d[a]);
         }
-        int stack[kStackDepth];
+        // The near child is visited next; far children wait on a stack of 16-bit node
+        // indices held in four 64-bit registers (the top entry in the low bits of st0).
+        uint64_t st0 = 0, st1 = 0, st2 = 0, st3 = 0;
         int sp = 0;
-        stack[sp++] = 0;
+        int nd = 0;
+        bool have = true;  // nd is a node still to visit
         int cnt = 0;
         const size_t base = (size_t)r * (size_t)maxc;
         // proposal sampler: the root interval and this ray's kept depth bins
@@ -98,8 +102,17 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
         const uint64_t kept_bins = (mask && !__ldg(fallback + r)) ? __ldg(mask + r) : 0ull;
         const bool masked = mask && !__ldg(fallback + r);
         const float bw = __fmul_rn(__fsub_rn(r1, r0), 0.015625f);  // bin width (t1 - t0) / 64
-        while (sp > 0 && cnt < maxc) {
-            const int nd = stack[--sp];
+        while (cnt < maxc) {
+            if (!have) {
+                if (sp == 0) break;
+                nd = (int)(st0 & 0xffffu);
+                st0 = (st0 >> 16) | (st1 << 48);
+                st1 = (st1 >> 16) | (st2 << 48);
+                st2 = (st2 >> 16) | (st3 << 48);
+                st3 >>= 16;
+                --sp;
+            }
+            have = false;
             const float4 A = __ldg(&nodes[nd].a);
             const float4 B = __ldg(&nodes[nd].b);
             float tin, tout;
@@ -120,12 +133,18 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
             const bool near_left = oa < A.w || (oa == A.w && da <= 0.0f);
             const int left = nd + 1;
             const int right = (int)(meta >> 2);
-            if (sp + 2 > kStackDepth) {  // unreachable for depth <= 12; recorded, never trapped
+            if (sp + 1 > kStackDepth) {  // unreachable for depth <= 12; recorded, never trapped
                 atomicCAS(err, 0, kDevErrStack);
                 break;
             }
-            stack[sp++] = near_left ? right : left;
-            stack[sp++] = near_left ? left : right;
+            const uint64_t far = (uint64_t)(near_left ? right : left);
+            st3 = (st3 << 16) | (st2 >> 48);
+            st2 = (st2 << 16) | (st1 >> 48);
+            st1 = (st1 << 16) | (st0 >> 48);
+            st0 = (st0 << 16) | far;
+            ++sp;
+            nd = near_left ? left : right;
+            have = true;
         }
         n_x[r] = (uint8_t)cnt;
     }
