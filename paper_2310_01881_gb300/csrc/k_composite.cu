@@ -31,7 +31,8 @@ struct RayAcc {
 // One ray by one warp, SPL consecutive slots per lane (32 SPL slots per pass).
 template <int SPL>
 __device__ __forceinline__ void composite_ray(const float2* __restrict__ xing, const float4* __restrict__ slot_out,
-                                              int ns, int steps, float inv_steps, size_t xbase, size_t sbase,
+                                              int ns, int steps, int lg_steps, float inv_steps, size_t xbase,
+                                              size_t sbase,
                                               float t_term, int lane, float r0, float bw, float* sbins, RayAcc& A) {
     for (int s0 = 0; s0 < ns; s0 += 32 * SPL) {
         float4 v[SPL];
@@ -49,8 +50,8 @@ __device__ __forceinline__ void composite_ray(const float2* __restrict__ xing, c
             t[i] = 0.f;
             if (val[i]) {
                 const int s = s0 + SPL * lane + i;
-                const int k = s / steps;
-                const int j = s - k * steps;
+                const int k = s >> lg_steps;  // steps is a power of two
+                const int j = s & (steps - 1);
                 const float2 x = __ldg(xing + xbase + k);
                 const float delta = __fmul_rn(__fsub_rn(x.y, x.x), inv_steps);
                 t[i] = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
@@ -138,8 +139,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
         RayAcc A{1.0f, 0.f, 0.f, 0.f, 0.f, 0u};
         float* sb = bins ? s_bins[wib] : nullptr;
         // short rays: one slot per lane; longer ones: two (twice the bytes in flight)
-        if (ns <= 32) composite_ray<1>(xing, slot_out, ns, steps, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
-        else composite_ray<2>(xing, slot_out, ns, steps, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
+        const int lg = __ffs(steps) - 1;
+        if (ns <= 32)
+            composite_ray<1>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
+        else
+            composite_ray<2>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
         float T = A.T, cr = A.cr, cg = A.cg, cb = A.cb, dd = A.dd;
         composited = A.composited;
 #pragma unroll

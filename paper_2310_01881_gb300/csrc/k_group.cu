@@ -98,20 +98,39 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __re
     for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) s_cnt[i] = 0u;
     __syncthreads();
     const uint32_t base = blockIdx.x * (uint32_t)(kScatterThreads * kScatterItems);
+    // s / maxc as a multiply-high: with m = ceil(2^32 / maxc), q = floor(s m / 2^32) is
+    // the quotient or one more (s m / 2^32 < s / maxc + 1), which one compare fixes
+    const uint32_t m = maxc > 1 ? (uint32_t)(((1ull << 32) + (uint64_t)maxc - 1ull) / (uint64_t)maxc) : 0u;
+    auto ray_of = [&](uint32_t s) -> uint32_t {
+        if (maxc == 1) return s;
+        uint32_t q = __umulhi(s, m);
+        if ((uint64_t)q * (uint32_t)maxc > s) --q;
+        return q;
+    };
     uint16_t lf[kScatterItems];
     uint32_t rk[kScatterItems];
+    uint8_t nx[kScatterItems];
+    // all loads first (the slot's leaf is read whether or not the slot holds a crossing;
+    // slots past a ray's count are ignored)
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        const uint32_t s = base + (uint32_t)(i * kScatterThreads) + threadIdx.x;
+        lf[i] = 0;
+        nx[i] = 0;
+        if (s < n_slots) {
+            const uint32_t ray = ray_of(s);
+            nx[i] = __ldg(n_x + ray);
+            lf[i] = __ldg(xleaf + s);
+        }
+    }
 #pragma unroll
     for (int i = 0; i < kScatterItems; ++i) {
         const uint32_t s = base + (uint32_t)(i * kScatterThreads) + threadIdx.x;
         rk[i] = 0xffffffffu;
-        lf[i] = 0;
         if (s < n_slots) {
-            const uint32_t ray = s / (uint32_t)maxc;
+            const uint32_t ray = ray_of(s);
             const uint32_t k = s - ray * (uint32_t)maxc;
-            if (k < (uint32_t)__ldg(n_x + ray)) {
-                lf[i] = __ldg(xleaf + s);
-                rk[i] = atomicAdd(&s_cnt[lf[i]], 1u);
-            }
+            if (k < (uint32_t)nx[i]) rk[i] = atomicAdd(&s_cnt[lf[i]], 1u);
         }
     }
     __syncthreads();

@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
                 const uint32_t ray = id / (uint32_t)g.maxc;
                 const uint32_t k = id - ray * (uint32_t)g.maxc;
                 const float2 xi = __ldg(g.xing + id);
-                const float delta = __fdiv_rn(__fsub_rn(xi.y, xi.x), (float)g.steps);
+                // steps is a power of two: the product by its reciprocal is the exact quotient
+                const float delta = __fmul_rn(__fsub_rn(xi.y, xi.x), __frcp_rn((float)g.steps));
                 const float tj = __fadd_rn(xi.x, __fmul_rn((float)j + 0.5f, delta));
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {

@@ -569,7 +569,8 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             if (id != 0xffffffffu) {
                 const uint32_t ray = id / (uint32_t)g.maxc;
                 const uint32_t k = id - ray * (uint32_t)g.maxc;
-                const float delta = __fdiv_rn(__fsub_rn(xi.y, xi.x), (float)g.steps);
+                // steps is a power of two: the product by its reciprocal is the exact quotient
+                const float delta = __fmul_rn(__fsub_rn(xi.y, xi.x), __frcp_rn((float)g.steps));
                 const float tj = __fadd_rn(xi.x, __fmul_rn((float)j + 0.5f, delta));
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
