@@ -67,6 +67,8 @@ struct MlpArgs {
     size_t leaf_stride;     // bytes per leaf
     int width, hidden, lx, ld, k0;
     int steps, maxc, cap;
+    uint32_t maxc_magic;    // ceil(2^32 / maxc) (maxc >= 2): id / maxc by multiply-high (see div_maxc)
+    int lg_steps;           // log2(steps)
     float4* slot_out;
     int* err;
     float* amax;            // FP32 path, calibration: per leaf x hidden layer, max |input of layer l| (or NULL)

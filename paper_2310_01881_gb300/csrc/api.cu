@@ -451,6 +451,9 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         a.k0 = ctx->k0;
         a.steps = steps;
         a.maxc = maxc;
+        a.maxc_magic = maxc > 1 ? (uint32_t)(((1ull << 32) + (uint64_t)maxc - 1ull) / (uint64_t)maxc) : 0u;
+        a.lg_steps = 0;
+        while ((1 << a.lg_steps) < steps) ++a.lg_steps;
         a.cap = cap;
         a.slot_out = ctx->d_slot;
         a.err = ctx->d_err;

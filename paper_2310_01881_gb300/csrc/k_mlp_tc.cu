@@ -408,9 +408,18 @@ struct TcShared {
     uint32_t tmem_base;
 };
 
+// id / maxc: q = floor(id m / 2^32) with m = ceil(2^32 / maxc) is the quotient or one
+// more (id m / 2^32 < id / maxc + 1); one compare fixes it.
+__device__ __forceinline__ uint32_t div_maxc(const MlpArgs& g, uint32_t id) {
+    if (g.maxc == 1) return id;
+    uint32_t q = __umulhi(id, g.maxc_magic);
+    if ((uint64_t)q * (uint32_t)g.maxc > id) --q;
+    return q;
+}
+
 // Crossing of this row in tile t of `leaf` (0xffffffff past the leaf's end).
 __device__ __forceinline__ uint32_t row_crossing(const MlpArgs& g, int leaf, uint32_t t, int ci) {
-    const uint32_t first = __ldg(g.offsets + leaf) + (t - __ldg(g.tile_off + leaf)) * (uint32_t)(kTileRows / g.steps);
+    const uint32_t first = __ldg(g.offsets + leaf) + (t - __ldg(g.tile_off + leaf)) * (uint32_t)(kTileRows >> g.lg_steps);
     const uint32_t c = first + (uint32_t)ci;
     return c < __ldg(g.offsets + leaf + 1) ? __ldg(g.order + c) : 0xffffffffu;
 }
@@ -418,7 +427,7 @@ __device__ __forceinline__ uint32_t row_crossing(const MlpArgs& g, int leaf, uin
 // Crossing interval and ray of crossing `id`.
 __device__ __forceinline__ void crossing_data(const MlpArgs& g, uint32_t id, float2& xi, float o[3], float d[3]) {
     if (id == 0xffffffffu) return;
-    const uint32_t ray = id / (uint32_t)g.maxc;
+    const uint32_t ray = div_maxc(g, id);
     xi = __ldg(g.xing + id);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -575,7 +584,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             uint64_t slot = ~0ull;  // 64-bit: rays * cap may exceed 2^32
             float x[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f};
             if (id != 0xffffffffu) {
-                const uint32_t ray = id / (uint32_t)g.maxc;
+                const uint32_t ray = div_maxc(g, id);
                 const uint32_t k = id - ray * (uint32_t)g.maxc;
                 // steps is a power of two: the product by its reciprocal is the exact quotient
                 const float delta = __fmul_rn(__fsub_rn(xi.y, xi.x), __frcp_rn((float)g.steps));
