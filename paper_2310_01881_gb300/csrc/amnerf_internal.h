@@ -96,10 +96,12 @@ cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* x
 
 // Proposal sampler (k_proposal.cu).
 int proposal_param_count();
-cudaError_t prepare_proposal();
-cudaError_t launch_prop_infer(cudaStream_t s, const float* params, const float root_box[6], const float* ro,
-                              const float* rd, uint32_t n, float coverage, int max_bins, uint64_t* mask,
-                              uint8_t* fallback, unsigned long long* n_fallback, float* q_out);
+// Kernel attributes on the current device; *infer_grid gets the resident CTAs of the
+// inference kernel there (its persistent grid).
+cudaError_t prepare_proposal(int* infer_grid);
+cudaError_t launch_prop_infer(cudaStream_t s, int infer_grid, const float* params, const float root_box[6],
+                              const float* ro, const float* rd, uint32_t n, float coverage, int max_bins,
+                              uint64_t* mask, uint8_t* fallback, unsigned long long* n_fallback, float* q_out);
 cudaError_t launch_prop_grad(cudaStream_t s, const float* params, const float* ro, const float* rd,
                              const float2* root, const float* targets, uint32_t n, uint32_t batch, uint64_t seed,
                              uint64_t step, float* grad, float* loss);

@@ -54,6 +54,7 @@ struct amnerf_ctx {
     std::vector<uint32_t> h_tile_off;  // per-leaf launches: host copy of tile offsets
     // proposal sampler
     bool prop_loaded = false;
+    int prop_grid = 0;        // persistent grid of the inference kernel on this device
     int prop_step = 0;
     float* d_prop = nullptr;  // params | m | v | grad | loss (5 x NPAR floats + 1)
     size_t cap_prop_rays = 0;
@@ -416,7 +417,7 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         if (st != AMNERF_OK) return st;
         const amnerf_node& root = ctx->nodes[0];
         const float box[6] = {root.lo[0], root.lo[1], root.lo[2], root.hi[0], root.hi[1], root.hi[2]};
-        CK(launch_prop_infer(s, ctx->d_prop, box, ro, rd, nn, p->coverage, p->max_bins, ctx->d_mask, ctx->d_fallback,
+        CK(launch_prop_infer(s, ctx->prop_grid, ctx->d_prop, box, ro, rd, nn, p->coverage, p->max_bins, ctx->d_mask, ctx->d_fallback,
                              reinterpret_cast<unsigned long long*>(ctx->d_stats + 3), nullptr),
            "proposal launch");
         if (ctx->timing) cudaEventRecord(ctx->ev[5], s);
@@ -646,7 +647,7 @@ amnerf_status amnerf_proposal_set(amnerf_ctx* ctx, const float* params, const fl
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (!ctx->d_prop) {
         CK(cudaMalloc((void**)&ctx->d_prop, sizeof(float) * (5 * (size_t)np + 1)), "proposal allocation");
-        CK(prepare_proposal(), "proposal kernel setup");
+        CK(prepare_proposal(&ctx->prop_grid), "proposal kernel setup");
     }
     CK(cudaMemset(ctx->d_prop, 0, sizeof(float) * (5 * (size_t)np + 1)), "memset");
     CK(cudaMemcpy(prop_params(ctx), params, sizeof(float) * np, cudaMemcpyHostToDevice), "proposal upload");
@@ -746,7 +747,7 @@ amnerf_status amnerf_proposal_predict(amnerf_ctx* ctx, const float* ro, const fl
     const amnerf_node& r = ctx->nodes[0];
     const float box[6] = {r.lo[0], r.lo[1], r.lo[2], r.hi[0], r.hi[1], r.hi[2]};
     CK(cudaMemsetAsync(ctx->d_stats + 3, 0, 8, ctx->stream), "memset");
-    CK(launch_prop_infer(ctx->stream, prop_params(ctx), box, ro, rd, (uint32_t)n, coverage, max_bins, mask, fallback,
+    CK(launch_prop_infer(ctx->stream, ctx->prop_grid, prop_params(ctx), box, ro, rd, (uint32_t)n, coverage, max_bins, mask, fallback,
                          reinterpret_cast<unsigned long long*>(ctx->d_stats + 3), probs),
        "proposal launch");
     return AMNERF_OK;

@@ -277,19 +277,28 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane (load + wait in one block).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
+// 32 consecutive FP32 columns of this thread's TMEM lane, without waiting (pair with
+// tmem_ld_wait before the values are used).
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%"
-        "20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
+        "20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
           "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr)
         : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane (load + wait; the E4M3
+// epilogues, whose register budget is tighter, read a row in two halves).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    tmem_ld32_nowait(taddr, r);
+    tmem_ld_wait();
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -305,6 +314,17 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
         : "memory");
 #pragma unroll
     for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The W FP32 columns of this thread's TMEM lane: all loads issued, then one wait.
+template <int W>
+__device__ __forceinline__ void tmem_ld_row(uint32_t taddr, float (&v)[W]) {
+    uint32_t r[W];
+#pragma unroll
+    for (int h = 0; h < W / 32; ++h) tmem_ld32_nowait(taddr + 32u * h, r + 32 * h);
+    tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < W; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
@@ -708,11 +728,12 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 };
                 if (!last) {
                     if constexpr (!F8) {
+                        float vr[W];
+                        tmem_ld_row<W>(d_row, vr);
 #pragma unroll
                         for (int h = 0; h < W / 32; ++h) {
-                            float v[32];
+                            const float* v = vr + 32 * h;
                             uint32_t pk[16];
-                            tmem_ld32(d_row + 32u * h, v);
 #pragma unroll
                             for (int c = 0; c < 8; ++c) {
                                 float2 p01, p23;
@@ -780,11 +801,12 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     // relu(h) as BF16 into this group's D columns (each 32-column block is
                     // read before it is overwritten), the constant 1 of the head bias after
                     // it, then the head MMA (16 x kh) into D columns kHeadCol..+15
+                    float vr[W];
+                    tmem_ld_row<W>(d_row, vr);
 #pragma unroll
                     for (int h = 0; h < W / 32; ++h) {
-                        float v[32];
+                        const float* v = vr + 32 * h;
                         uint32_t pk[16];
-                        tmem_ld32(d_row + 32u * h, v);
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
                             pk[2 * c + 0] = pack_relu_bf16(v[4 * c + 0], v[4 * c + 1]);

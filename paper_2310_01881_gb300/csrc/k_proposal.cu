@@ -493,31 +493,31 @@ __global__ void k_prop_adam(float* __restrict__ P, float* __restrict__ g, float*
 int proposal_param_count() { return NPAR; }
 
 constexpr size_t kInferSmem = sizeof(InferWeights) + kInferGroups * sizeof(InferTile);
-int g_infer_grid = 0;  // resident CTAs of k_prop_infer on this device
 
-cudaError_t launch_prop_infer(cudaStream_t s, const float* params, const float root_box[6], const float* ro,
-                              const float* rd, uint32_t n, float coverage, int max_bins, uint64_t* mask,
-                              uint8_t* fallback, unsigned long long* n_fallback, float* q_out) {
+cudaError_t launch_prop_infer(cudaStream_t s, int infer_grid, const float* params, const float root_box[6],
+                              const float* ro, const float* rd, uint32_t n, float coverage, int max_bins,
+                              uint64_t* mask, uint8_t* fallback, unsigned long long* n_fallback, float* q_out) {
     if (n == 0) return cudaSuccess;
+    if (infer_grid < 1) return cudaErrorNotReady;  // prepare_proposal was not called
     const uint32_t tiles = (n + kRays - 1) / kRays;
     const uint32_t ctas = (tiles + kInferGroups - 1) / kInferGroups;
-    const unsigned grid = ctas < (uint32_t)g_infer_grid ? ctas : (unsigned)g_infer_grid;
-    if (grid == 0) return cudaErrorNotReady;  // prepare_proposal was not called
+    const unsigned grid = ctas < (uint32_t)infer_grid ? ctas : (unsigned)infer_grid;
     k_prop_infer<<<grid, kRays * kInferGroups, kInferSmem, s>>>(params, root_box[0], root_box[1], root_box[2],
-                                                           root_box[3], root_box[4], root_box[5], ro, rd, n,
-                                                           coverage, max_bins, mask, fallback, n_fallback, q_out);
+                                                                root_box[3], root_box[4], root_box[5], ro, rd, n,
+                                                                coverage, max_bins, mask, fallback, n_fallback,
+                                                                q_out);
     return cudaGetLastError();
 }
 
-cudaError_t prepare_proposal() {
+cudaError_t prepare_proposal(int* infer_grid) {
     cudaError_t e = cudaFuncSetAttribute(k_prop_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prop_infer, kRays * kInferGroups, kInferSmem)) != cudaSuccess)
-        return e;
-    g_infer_grid = sms * (per_sm > 0 ? per_sm : 1);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prop_infer, kRays * kInferGroups, kInferSmem);
+    if (e != cudaSuccess) return e;
+    *infer_grid = sms * (per_sm > 0 ? per_sm : 1);
     return cudaFuncSetAttribute(k_prop_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GradSmem));
 }
 
