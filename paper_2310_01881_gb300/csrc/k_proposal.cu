@@ -140,6 +140,17 @@ static_assert(PO <= PIN, "logits 32..64 live in feature rows");
 
 __device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(g + 1) : "memory"); }
 
+// Barrier of warpgroup g that also returns whether v holds for any of its threads.
+__device__ __forceinline__ bool group_any(int g, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbarrier.red.or.pred q, %2, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(g + 1)
+        : "memory");
+    return r != 0;
+}
+
 // (a * b0 + c0, a * b1 + c1) with one packed FP32 instruction; each half is an
 // ordinary correctly rounded fused multiply-add.
 __device__ __forceinline__ float2 fma_f32x2(float a, float2 b, float2 c) {
@@ -307,7 +318,15 @@ __global__ void __launch_bounds__(kRays * kInferGroups, 1) k_prop_infer(
             if (!hit) t0 = t1 = 0.f;  // as the traversal reports the root interval of a miss
         }
         prop_features<kRays>(o, d, t0, &T.A[0][t]);
-        group_sync(g);
+        // a tile whose rays all miss the root box keeps no bins (it has no crossings):
+        // the network is skipped unless the predictions themselves are requested
+        if (!group_any(g, hit) && !q_out) {
+            if (r < n) {
+                mask[r] = 0ull;
+                fallback[r] = 0;
+            }
+            continue;
+        }
         tile_layer<PIN, PH, true>(T.A, &S.W1t[0][0], S.b1, 0, T.B);   // H1 -> B
         group_sync(g);
         tile_layer<PH, PH, true>(T.B, &S.W2t[0][0], S.b2, 0, T.A);    // H2 -> A rows 0..31
