@@ -11,14 +11,18 @@
 // crosses a leaf boundary.  Per tile: 128 threads rebuild their sample (crossing ->
 // t_j = t_in + (j + 1/2) delta, x_j = o + t_j d, in the traversal's FP32 operation
 // order), encode it into a feature-major shared tile, then every layer is a
-// 128 x width register-blocked FP32 GEMM from shared memory; the head writes
+// 128 x width register-blocked FP32 GEMM from shared memory (512 threads with 4 x 4
+// blocks for width 64: the leaf's FP32 weights fill shared memory, so the CTA is
+// alone on its SM and needs the warps itself); the head writes
 // (sigma, r, g, b) to the sample's slot ray * cap + k * steps + j.
 #include "amnerf_internal.h"
 
 namespace amnerf {
 namespace {
 
-constexpr int kThreads = 256;
+// threads per CTA: 512 for width 64 (4 x 4 register blocks, 16 warps per SM), 256 for 32
+template <int W>
+constexpr int kThreadsFor = W == 64 ? 512 : 256;
 constexpr int kMaxK0 = 128;
 
 // Leaf layout (floats): W0^T [k0][W], b0 [W], then per layer l>0: W_l^T [W][W], b_l [W],
@@ -37,7 +41,7 @@ template <int W>
 __device__ __forceinline__ void gemm_layer(const float* __restrict__ in, int kin, const float* __restrict__ wt,
                                            const float* __restrict__ bias, float* __restrict__ out) {
     constexpr int CG = W / 4;            // column groups of 4
-    constexpr int RG = kThreads / CG;    // row groups
+    constexpr int RG = kThreadsFor<W> / CG;  // row groups
     constexpr int RPT = kTileRows / RG;  // rows per thread (8 for W=64, 4 for W=32)
     const int rg = threadIdx.x % RG;
     const int cg = threadIdx.x / RG;
@@ -123,7 +127,7 @@ __device__ __forceinline__ void tile_absmax(const float* __restrict__ t, int nfe
 }
 
 template <int W>
-__global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
+__global__ void __launch_bounds__(kThreadsFor<W>, 1) k_mlp_simt(MlpArgs g) {
     extern __shared__ __align__(16) float sm[];
     const size_t wstride = simt_stride(W, g.hidden, g.k0);
     float* sW = sm;                                   // [wstride]
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_simt(MlpArgs g) {
             __syncthreads();
             const float4* src = reinterpret_cast<const float4*>(wall + (size_t)leaf * wstride);
             float4* dst = reinterpret_cast<float4*>(sW);
-            for (size_t i = threadIdx.x; i < wstride / 4; i += kThreads) dst[i] = __ldg(src + i);
+            for (size_t i = threadIdx.x; i < wstride / 4; i += kThreadsFor<W>) dst[i] = __ldg(src + i);
             cur = leaf;
         }
         const uint32_t first = __ldg(g.offsets + leaf) + (t - __ldg(g.tile_off + leaf)) * (uint32_t)cpt;
@@ -238,7 +242,7 @@ cudaError_t prepare_w(int hidden, int k0) {
 
 template <int W>
 cudaError_t launch_w(cudaStream_t s, const MlpArgs& a, int grid) {
-    k_mlp_simt<W><<<grid, kThreads, simt_smem<W>(a.hidden, a.k0), s>>>(a);
+    k_mlp_simt<W><<<grid, kThreadsFor<W>, simt_smem<W>(a.hidden, a.k0), s>>>(a);
     return cudaGetLastError();
 }
 
