@@ -37,14 +37,15 @@ __device__ __forceinline__ float sigmoid_f(float z) { return 1.0f / (1.0f + expf
 
 // out[n][128] = ReLU(in[k][128]^T W^T[k][n] + b), rows interleaved so a warp reads
 // contiguous rows.  W = width; thread tile = RPT rows x 4 columns.
-template <int W>
-__device__ __forceinline__ void gemm_layer(const float* __restrict__ in, int kin, const float* __restrict__ wt,
+template <int W, int KIN>
+__device__ __forceinline__ void gemm_layer(const float* __restrict__ in, int kin_rt, const float* __restrict__ wt,
                                            const float* __restrict__ bias, float* __restrict__ out) {
     constexpr int CG = W / 4;            // column groups of 4
     constexpr int RG = kThreadsFor<W> / CG;  // row groups
-    constexpr int RPT = kTileRows / RG;  // rows per thread (8 for W=64, 4 for W=32)
+    constexpr int RPT = kTileRows / RG;  // rows per thread (4 for both widths)
     const int rg = threadIdx.x % RG;
     const int cg = threadIdx.x / RG;
+    const int kin = KIN > 0 ? KIN : kin_rt;
     float acc[RPT][4];
     const float4 b4 = *reinterpret_cast<const float4*>(bias + 4 * cg);
 #pragma unroll
@@ -126,7 +127,8 @@ __device__ __forceinline__ void tile_absmax(const float* __restrict__ t, int nfe
     if ((row & 31) == 0 && u) atomicMax(reinterpret_cast<unsigned*>(dst), u);
 }
 
-template <int W>
+// HC > 0: the hidden-layer count and input width (90) fixed at compile time.
+template <int W, int HC>
 __global__ void __launch_bounds__(kThreadsFor<W>, 1) k_mlp_simt(MlpArgs g) {
     extern __shared__ __align__(16) float sm[];
     const size_t wstride = simt_stride(W, g.hidden, g.k0);
@@ -191,8 +193,12 @@ __global__ void __launch_bounds__(kThreadsFor<W>, 1) k_mlp_simt(MlpArgs g) {
         const float* in = sA;
         float* out = sH;
         int kin = g.k0;
-        for (int l = 0; l < g.hidden; ++l) {
-            gemm_layer<W>(in, kin, w, w + (size_t)kin * W, out);
+        const int hidden = HC > 0 ? HC : g.hidden;
+#pragma unroll
+        for (int l = 0; l < hidden; ++l) {
+            if (HC > 0 && l == 0) gemm_layer<W, 90>(in, kin, w, w + (size_t)kin * W, out);
+            else if (HC > 0) gemm_layer<W, W>(in, kin, w, w + (size_t)kin * W, out);
+            else gemm_layer<W, 0>(in, kin, w, w + (size_t)kin * W, out);
             __syncthreads();
             if (amax && l + 1 < g.hidden) tile_absmax(out, W, nvalid, amax + l + 1);
             w += (size_t)kin * W + W;
@@ -237,12 +243,19 @@ size_t simt_smem(int hidden, int k0) {
 template <int W>
 cudaError_t prepare_w(int hidden, int k0) {
     const size_t smem = simt_smem<W>(hidden, k0);
-    return cudaFuncSetAttribute(k_mlp_simt<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_simt<W, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_mlp_simt<W, W == 64 ? 4 : 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
 }
 
 template <int W>
 cudaError_t launch_w(cudaStream_t s, const MlpArgs& a, int grid) {
-    k_mlp_simt<W><<<grid, kThreadsFor<W>, simt_smem<W>(a.hidden, a.k0), s>>>(a);
+    constexpr int HS = W == 64 ? 4 : 2;
+    if (a.hidden == HS && a.k0 == 90)
+        k_mlp_simt<W, HS><<<grid, kThreadsFor<W>, simt_smem<W>(a.hidden, a.k0), s>>>(a);
+    else
+        k_mlp_simt<W, 0><<<grid, kThreadsFor<W>, simt_smem<W>(a.hidden, a.k0), s>>>(a);
     return cudaGetLastError();
 }
 
