@@ -62,23 +62,23 @@ __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / 
 // b_0..b_{hidden-1} [width] and bo [4].  BF16 folds each hidden layer's bias into the
 // contraction: input column k_in (90 for layer 0, width for the others) holds the
 // bias and the activation row carries 1 there, so kh = width + 16 and the epilogue
-// adds nothing; its head is a 16-row BF16 matrix (rows 0..3 used, bias in column
-// width) run as one more MMA.  E4M3 keeps kh = width, adds the FP32 bias in the
-// epilogue (an E4M3 bias would lose too much) and computes the head in FP32.
+// adds nothing.  E4M3 keeps kh = width and adds the FP32 bias in the epilogue (an
+// E4M3 bias would lose too much).  Both run the head as one more BF16 MMA: a 16-row
+// matrix (rows 0..3 used) of khead = width + 16 columns with the bias in column width.
 // E4M3 with static activation scales (act_max known per leaf and layer) folds them
 // in at packing: layer l's pre-activation is acc * sw[l][n] + bias[l][n] with
 // sw = s_w a_l / a_(l+1), bias = b / a_(l+1) (the last layer: s_w a_l and b), where
 // a_l = act_max_l / 448, so relu(pre) is already the next layer's E4M3 input.
 struct TcLayout {
-    int width, hidden, k0, k0p, kh, es;
+    int width, hidden, k0, k0p, kh, khead, es;
     size_t w0, wh, wo, sw, bias, enc, stride;
     __host__ __device__ TcLayout(int w, int h, int k, bool f8)
         : width(w), hidden(h), k0(k), k0p(round_up(f8 ? k : k + 1, f8 ? 32 : 16)), kh(f8 ? w : w + 16),
-          es(f8 ? 1 : 2) {
+          khead(w + 16), es(f8 ? 1 : 2) {
         w0 = 0;
         wh = w0 + (size_t)w * k0p * es;
-        wo = wh + (size_t)(h - 1) * w * kh * es;  // head: E4M3 path FP32 [width][4]; BF16 path 16 x kh BF16
-        sw = wo + (f8 ? (size_t)w * 4 * 4 : (size_t)16 * kh * 2);
+        wo = wh + (size_t)(h - 1) * w * kh * es;  // head: 16 x khead BF16 (both precisions)
+        sw = wo + (size_t)16 * khead * 2;
         bias = sw + (f8 ? (size_t)h * w * 4 : 0);
         enc = bias + (size_t)h * w * 4 + 16;  // E4M3 static scales: 1 / (encoding scale)
         const size_t end = enc + 16;
@@ -226,17 +226,6 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* w) {
 
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// (a0 + b0, a1 + b1) with one packed FP32 instruction.
-__device__ __forceinline__ float2 add_f32x2(float2 a, float2 b) {
-    unsigned long long ua, ub, ud;
-    memcpy(&ua, &a, 8);
-    memcpy(&ub, &b, 8);
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(ud) : "l"(ua), "l"(ub));
-    float2 d;
-    memcpy(&d, &ud, 8);
-    return d;
-}
-
 // (a0 * b0, a1 * b1) with one packed FP32 instruction.
 __device__ __forceinline__ float2 mul_f32x2(float2 a, float2 b) {
     unsigned long long ua, ub, ud;
@@ -344,6 +333,14 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
     uint16_t lo, hi;
     asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
     asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+// relu of four values to E4M3 (round to nearest even, saturating), first in the low byte.
+__device__ __forceinline__ uint32_t pack_relu_e4m3x4(float a, float b, float c, float d) {
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
     return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
@@ -587,9 +584,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
 
         for (uint32_t t = t_first; t < t_stop && ok;) {
             if (leaf != cur) {
-                if constexpr (!F8) {
-                    if (pending && !(ok = finish_head())) break;  // the head MMA still reads the weights
-                }
+                if (pending && !(ok = finish_head())) break;  // the head MMA still reads the weights
                 wg_bar(bar_id);  // every row is done with the previous leaf's weights and biases
                 if (leader) {
                     fence_proxy_async();
@@ -655,9 +650,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             tmem_st_wait();
             tc_fence_before();
             wg_bar(bar_id);
-            if constexpr (!F8) {
-                if (pending && !(ok = finish_head())) break;
-            }
+            if (pending && !(ok = finish_head())) break;
 
             int leaf_n = leaf;
             uint32_t id_n = 0xffffffffu;
@@ -758,8 +751,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                             for (int c = 0; c < 8; ++c) {
                                 float2 p01, p23;
                                 pre4(v + 4 * c, 32 * h + 4 * c, p01, p23);
-                                pk[8 * h + c] = pack_e4m3x4(fmaxf(p01.x, 0.f), fmaxf(p01.y, 0.f), fmaxf(p23.x, 0.f),
-                                                            fmaxf(p23.y, 0.f));
+                                pk[8 * h + c] = pack_relu_e4m3x4(p01.x, p01.y, p23.x, p23.y);
                             }
                         }
                         if constexpr (W / 4 == 16) tmem_st16(a_row, pk);
@@ -797,22 +789,39 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     tc_fence_before();
                     wg_bar(bar_id);
                     kin = lay.kh;
-                } else if constexpr (!F8) {
+                } else {
                     // relu(h) as BF16 into this group's D columns (each 32-column block is
                     // read before it is overwritten), the constant 1 of the head bias after
-                    // it, then the head MMA (16 x kh) into D columns kHeadCol..+15
-                    float vr[W];
-                    tmem_ld_row<W>(d_row, vr);
+                    // it, then the head MMA (16 x khead) into D columns kHeadCol..+15
+                    if constexpr (!F8) {
+                        float vr[W];
+                        tmem_ld_row<W>(d_row, vr);
 #pragma unroll
-                    for (int h = 0; h < W / 32; ++h) {
-                        const float* v = vr + 32 * h;
-                        uint32_t pk[16];
+                        for (int h = 0; h < W / 32; ++h) {
+                            const float* v = vr + 32 * h;
+                            uint32_t pk[16];
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            pk[2 * c + 0] = pack_relu_bf16(v[4 * c + 0], v[4 * c + 1]);
-                            pk[2 * c + 1] = pack_relu_bf16(v[4 * c + 2], v[4 * c + 3]);
+                            for (int c = 0; c < 8; ++c) {
+                                pk[2 * c + 0] = pack_relu_bf16(v[4 * c + 0], v[4 * c + 1]);
+                                pk[2 * c + 1] = pack_relu_bf16(v[4 * c + 2], v[4 * c + 3]);
+                            }
+                            tmem_st16(d_row + 16u * h, pk);
                         }
-                        tmem_st16(d_row + 16u * h, pk);
+                    } else {  // the pre-activation needs the E4M3 scales and the bias
+#pragma unroll
+                        for (int h = 0; h < W / 32; ++h) {
+                            float v[32];
+                            uint32_t pk[16];
+                            tmem_ld32(d_row + 32u * h, v);
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                float2 p01, p23;
+                                pre4(v + 4 * c, 32 * h + 4 * c, p01, p23);
+                                pk[2 * c + 0] = pack_relu_bf16(p01.x, p01.y);
+                                pk[2 * c + 1] = pack_relu_bf16(p23.x, p23.y);
+                            }
+                            tmem_st16(d_row + 16u * h, pk);
+                        }
                     }
                     {
                         uint32_t c8[8] = {pack_bf16(1.0f, 0.0f), 0u, 0u, 0u, 0u, 0u, 0u, 0u};
@@ -824,65 +833,22 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     if (leader) {
                         tc_fence_after();
                         const uint32_t b_base = w_addr + (uint32_t)lay.wo;
-                        const uint32_t sbo = (uint32_t)lay.kh * 16u;
+                        const uint32_t sbo = (uint32_t)lay.khead * 16u;
                         const uint32_t idd = idesc_bf16(16);
-                        for (int kk = 0; kk < lay.kh / 16; ++kk)
+                        for (int kk = 0; kk < lay.khead / 16; ++kk)
                             mma_bf16_ts(d_col + kHeadCol, d_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd,
                                         kk > 0 ? 1u : 0u);
                         mma_commit(bar_m);
                     }
                     pending = true;
                     slot_prev = slot;
-                } else {
-                    // head: z = Wo relu(pre) + bo in FP32 (Wo stored [width][4])
-                    const float4* wo = reinterpret_cast<const float4*>(wbuf + lay.wo);
-                    const float* bo = bias + (size_t)hidden * W;
-                    float2 z01 = make_float2(bo[0], bo[1]);
-                    float2 z23 = make_float2(bo[2], bo[3]);
-                    float2 y01 = make_float2(0.f, 0.f), y23 = make_float2(0.f, 0.f);  // odd inputs
-#pragma unroll
-                    for (int h = 0; h < W / 32; ++h) {
-                        float v[32];
-                        tmem_ld32(d_row + 32u * h, v);
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            float2 p01, p23;
-                            pre4(v + 4 * c, 32 * h + 4 * c, p01, p23);
-                            const float hq[4] = {fmaxf(p01.x, 0.f), fmaxf(p01.y, 0.f), fmaxf(p23.x, 0.f),
-                                                 fmaxf(p23.y, 0.f)};
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const float4 w4 = wo[32 * h + 4 * c + i];
-                                if (i & 1) {
-                                    y01 = fma_f32x2(hq[i], make_float2(w4.x, w4.y), y01);
-                                    y23 = fma_f32x2(hq[i], make_float2(w4.z, w4.w), y23);
-                                } else {
-                                    z01 = fma_f32x2(hq[i], make_float2(w4.x, w4.y), z01);
-                                    z23 = fma_f32x2(hq[i], make_float2(w4.z, w4.w), z23);
-                                }
-                            }
-                        }
-                    }
-                    z01 = add_f32x2(z01, y01);
-                    z23 = add_f32x2(z23, y23);
-                    if (slot != ~0ull) {
-                        float4 o;
-                        o.x = softplus_f(z01.x);
-                        o.y = sigmoid_f(z01.y);
-                        o.z = sigmoid_f(z23.x);
-                        o.w = sigmoid_f(z23.y);
-                        g.slot_out[slot] = o;
-                    }
-                    tc_fence_before();
                 }
             }
             leaf = leaf_n;
             id = id_n;
             t = t_next;
         }
-        if constexpr (!F8) {
-            if (ok && pending) ok = finish_head();
-        }
+        if (ok && pending) ok = finish_head();
         if (!ok && leader) atomicCAS(g.err, 0, kDevErrTimeout);
     }
     tc_fence_before();
@@ -999,19 +965,15 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
         kin = width;
     }
     if (f8 && act_max) *reinterpret_cast<float*>(dst + lay.enc) = 1.0f / act_scale(0);
-    if (f8) {
-        float* wo = reinterpret_cast<float*>(dst + lay.wo);
-        for (int k = 0; k < width; ++k)
-            for (int n = 0; n < 4; ++n) wo[(size_t)k * 4 + n] = w[(size_t)n * width + k];
-    } else {  // rows 0..3 of a 16 x kh BF16 matrix, the bias in column `width`
+    {  // head: rows 0..3 of a 16 x khead BF16 matrix, the bias in column `width`
         uint8_t* hb = dst + lay.wo;
         for (int n = 0; n < 4; ++n) {
             for (int k = 0; k < width; ++k) {
                 const uint16_t b = f2bf(w[(size_t)n * width + k]);
-                std::memcpy(hb + cm_offset(n, k, lay.kh), &b, 2);
+                std::memcpy(hb + cm_offset(n, k, lay.khead), &b, 2);
             }
             const uint16_t bb = f2bf(w[(size_t)4 * width + n]);
-            std::memcpy(hb + cm_offset(n, width, lay.kh), &bb, 2);
+            std::memcpy(hb + cm_offset(n, width, lay.khead), &bb, 2);
         }
     }
     w += 4 * width;
