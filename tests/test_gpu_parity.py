@@ -304,6 +304,36 @@ def test_c2_bf16_sampled_psnr(R):
     assert psnr >= 45.0
 
 
+def test_c4_full_size_grouped_launch_sampled(R):
+    """The batching workload at its full size, in the benchmark's launch: 4096 leaves,
+    16 views of 1920x1080 (33.2 M rays, about 2.5 G samples) in one persistent
+    grouped BF16 launch.  Tree bit-exact; a seeded subset of rays: crossing counts equal
+    to the FP32-mode oracle's and pixels >= 45 dB against the FP64 oracle."""
+    from paper_2310_01881_gb300 import amnerf
+    cfg = S.CONFIGS["c4"]
+    _, tree, P = _setup(R, cfg, 0, prec="bf16")
+    _compare_tree(R, tree)
+    o, d = _rays(cfg, 0, cfg.views)
+    assert len(o) == 16 * 1920 * 1080
+    do, dd = _dev(o), _dev(d)
+    rgb, depth, opac, st = R.render(do, dd, steps=cfg.steps, cap=cfg.cap, stats=True)
+    rgb = rgb.cpu().numpy()
+    assert np.all(np.isfinite(rgb))
+    idx = S.ray_subset(len(o), 4096, 5)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o[idx], d[idx], cfg.steps, cfg.cap, mode=0,
+                   threads=16)
+    psnr = _psnr(rgb[idx], ref["rgb"])
+    print(f"bf16 c4 full size: {st['samples_generated'] / 1e9:.2f} G samples, PSNR {psnr:.2f} dB on 4096 rays")
+    assert st["samples_generated"] > 2e9
+    assert psnr >= 45.0
+    # the sampled rays' crossing counts, through the FP32-mode oracle (bit-exact traversal)
+    nx, _, _, _ = O.traverse(tree, o[idx], d[idx], cfg.cap // cfg.steps, mode=1)
+    sub = R.render_debug(_dev(o[idx]), _dev(d[idx]), steps=cfg.steps, cap=cfg.cap)[3]
+    np.testing.assert_array_equal(sub["n_x"].astype(np.int64), nx)
+    del do, dd
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("steps,cap", [(1, 24), (4, 16), (16, 64), (32, 96)])
 def test_bf16_sampling_rates(R, steps, cap):
     cfg = S.CONFIGS["c1"]
