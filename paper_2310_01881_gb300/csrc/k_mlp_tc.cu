@@ -16,22 +16,25 @@
 //   D (128 x N, FP32)               -- accumulator in TMEM
 //
 // Measured on GB300, an SM retires one 128 x 64 x 16 MMA about every 50 cycles
-// whichever warp issues it, so these small layers are bound by MMA instruction
-// count and by the latency of the per-layer chain; keeping A in TMEM removes the
-// shared-memory activation stores and proxy fences from that chain.
+// whichever warp issues it, so these small layers are bound by MMA issue and by the
+// latency of the per-layer chain; keeping A in TMEM removes the shared-memory
+// activation stores and proxy fences from that chain.
 //
-// Thread r of a warpgroup owns sample row r: it rebuilds
-// the sample, encodes gamma(x) ++ gamma(d) and writes it into its TMEM lane
-// (tcgen05.st 32x32b); after each MMA it reads its row of D (tcgen05.ld 32x32b:
-// warp q of the group owns lanes 32q..32q+31), adds the bias (packed f32x2 adds),
-// applies ReLU while converting to BF16 (cvt.rn.relu.bf16x2) and writes the next
-// layer's A back into TMEM.  The 4-wide head is too narrow for an MMA: the last
-// hidden epilogue computes z = Wo relu(h) + bo in FP32 from the activations it holds
-// in registers (FP32 head weights), then sigma = softplus, rgb = sigmoid.
+// Thread r of a warpgroup owns sample row r: it rebuilds the sample, encodes
+// gamma(x) ++ gamma(d) and writes it into its TMEM lane (tcgen05.st 32x32b); after
+// each MMA it reads its row of D (tcgen05.ld 32x32b: warp q of the group owns lanes
+// 32q..32q+31) and writes the next layer's A back into TMEM.  BF16 folds every bias
+// into its contraction (a weight column against a constant-1 input column), so the
+// epilogue is only ReLU with the conversion (cvt.rn.relu.bf16x2); E4M3 applies its
+// channel scales and bias with one packed FMA per pair first.  The 4-wide head is one
+// more BF16 MMA (16 rows, 4 used) on relu(h) written into the group's D columns; it
+// runs while the group encodes its next tile, and its outputs (sigma = softplus,
+// rgb = sigmoid) are read just before that tile's first MMA.
 //
 // Several warpgroups per CTA work on different tiles, so one group's epilogue
-// overlaps another's MMA.  Each group issues its own MMAs from one thread and
-// tracks completion with tcgen05.commit on its own mbarrier.  Every wait is bounded
+// overlaps another's MMA.  Each group's leader thread (in warp grp % 4, so the
+// leaders run on different SM sub-partitions) issues the group's MMAs and tracks
+// completion with tcgen05.commit on the group's mbarrier.  Every wait is bounded
 // (clock64 deadline); on expiry the group records AMNERF_E_TIMEOUT in the status
 // word, leaves its tile loop, and the CTA still frees its TMEM before returning.
 //
