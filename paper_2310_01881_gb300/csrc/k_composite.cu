@@ -146,19 +146,27 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
             composite_ray<2>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
         float T = A.T, cr = A.cr, cg = A.cg, cb = A.cb, dd = A.dd;
         composited = A.composited;
+        // warp sums of (cr, cg, cb, dd) in 6 shuffles: each exchange halves the values a
+        // lane carries until lanes 8i hold sum i (i = 0..3) after the last three steps;
+        // three more bring them to lane 0
+        const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+        const float s0 = __shfl_xor_sync(0xffffffffu, h16 ? cr : cb, 16);
+        const float s1 = __shfl_xor_sync(0xffffffffu, h16 ? cg : dd, 16);
+        const float w0 = (h16 ? cb : cr) + s0;  // cr | cb over lane pairs
+        const float w1 = (h16 ? dd : cg) + s1;  // cg | dd
+        float x = (h8 ? w1 : w0) + __shfl_xor_sync(0xffffffffu, h8 ? w0 : w1, 8);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            cr += __shfl_xor_sync(0xffffffffu, cr, o);
-            cg += __shfl_xor_sync(0xffffffffu, cg, o);
-            cb += __shfl_xor_sync(0xffffffffu, cb, o);
-            dd += __shfl_xor_sync(0xffffffffu, dd, o);
-        }
+        for (int o = 4; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (bins) {
             __syncwarp();
             if (lane == 0) s_bins[wib][64] = T;
             __syncwarp();
             for (int b = lane; b < 65; b += 32) bins[(size_t)ray * 65 + b] = s_bins[wib][b];
         }
+        cr = x;
+        cg = __shfl_sync(0xffffffffu, x, 8);
+        cb = __shfl_sync(0xffffffffu, x, 16);
+        dd = __shfl_sync(0xffffffffu, x, 24);
         if (lane == 0) {
             rgb[3 * (size_t)ray + 0] = cr + T * bg0;
             rgb[3 * (size_t)ray + 1] = cg + T * bg1;
