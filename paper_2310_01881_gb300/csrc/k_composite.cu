@@ -5,7 +5,9 @@
 // tau = sigma * delta, e = exp(-tau), alpha = 1 - e, w = T alpha; C += w c,
 // D += w t, T = T e.  rgb = C + T bg, depth = D, opacity = 1 - T.
 //
-// One warp per ray handles 32 SPL consecutive slots per pass, SPL per lane (1 for
+// Persistent warps take rays in a grid-stride loop (the next ray's crossing count is
+// loaded while the current one is composited).  A warp handles a ray 32 SPL
+// consecutive slots per pass, SPL per lane (1 for
 // rays of at most 32 samples, else 2): the per-lane products of the factors e are
 // combined by a warp-shuffle multiplicative scan, so each lane gets the
 // transmittance in front of its samples (the carried T times the exclusive product,
@@ -119,33 +121,38 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
     __shared__ float s_bins[kWarpsPerBlock][65];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const uint32_t ray = blockIdx.x * kWarpsPerBlock + wib;
+    const uint32_t stride = gridDim.x * kWarpsPerBlock;
     uint32_t composited = 0;
-    float r0 = 0.f, bw = 0.f;
-    if (bins) {
-        for (int b = lane; b < 65; b += 32) s_bins[wib][b] = 0.0f;
-        if (ray < n) {
+    const float inv_steps = 1.0f / (float)steps;  // exact: steps is a power of two
+    const int lg = __ffs(steps) - 1;
+    // each warp takes rays ray, ray + stride, ...; the next ray's crossing count is
+    // loaded while the current ray is composited
+    uint32_t ray = blockIdx.x * kWarpsPerBlock + wib;
+    int nx_next = ray < n ? (int)__ldg(n_x + ray) : 0;
+    for (; ray < n; ray += stride) {
+        const int ns = nx_next * steps;
+        const uint32_t ray2 = ray + stride;
+        nx_next = ray2 < n ? (int)__ldg(n_x + ray2) : 0;
+        float r0 = 0.f, bw = 0.f;
+        if (bins) {
+            __syncwarp();
+            for (int b = lane; b < 65; b += 32) s_bins[wib][b] = 0.0f;
             const float2 rt = __ldg(root + ray);
             r0 = rt.x;
             bw = __fmul_rn(__fsub_rn(rt.y, rt.x), 0.015625f);
+            __syncwarp();
         }
-        __syncwarp();
-    }
-    if (ray < n) {
-        const int ns = (int)__ldg(n_x + ray) * steps;
-        const float inv_steps = 1.0f / (float)steps;  // exact: steps is a power of two
         const size_t xbase = (size_t)ray * maxc;
         const size_t sbase = (size_t)ray * cap;
         RayAcc A{1.0f, 0.f, 0.f, 0.f, 0.f, 0u};
         float* sb = bins ? s_bins[wib] : nullptr;
         // short rays: one slot per lane; longer ones: two (twice the bytes in flight)
-        const int lg = __ffs(steps) - 1;
         if (ns <= 32)
             composite_ray<1>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
         else
             composite_ray<2>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
         float T = A.T, cr = A.cr, cg = A.cg, cb = A.cb, dd = A.dd;
-        composited = A.composited;
+        composited += A.composited;
         // warp sums of (cr, cg, cb, dd) in 6 shuffles: each exchange halves the values a
         // lane carries until lanes 8i hold sum i (i = 0..3) after the last three steps;
         // three more bring them to lane 0
@@ -191,7 +198,20 @@ cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* x
                              float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
                              const float2* root, float* bins) {
     if (n == 0) return cudaSuccess;
-    const unsigned blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    unsigned blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    // resident CTAs per device, cached: only a cap on the launch size (any grid gives
+    // the same result, the warps stride over the rays)
+    static int cap_blocks[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+        if (!cap_blocks[dev]) {
+            int sms = 0, per = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_composite, kWarpsPerBlock * 32, 0);
+            cap_blocks[dev] = sms * (per > 0 ? per : 1);
+        }
+        if (cap_blocks[dev] > 0 && blocks > (unsigned)cap_blocks[dev]) blocks = (unsigned)cap_blocks[dev];
+    }
     k_composite<<<blocks, kWarpsPerBlock * 32, 0, s>>>(n_x, xing, slot_out, n, steps, maxc, cap, t_term, bg0, bg1,
                                                        bg2, rgb, depth, opacity,
                                                        reinterpret_cast<unsigned long long*>(stats + 2), root, bins);
