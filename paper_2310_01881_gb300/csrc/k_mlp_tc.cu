@@ -388,13 +388,21 @@ __device__ __forceinline__ void encode_freq(const float p[3], float (&f)[N]) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) sincospi_anchor(p[a], 5, &s[a], &c[a]);
         } else if (k > 0) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float t = s[a] + s[a];
-                const float sn = t * c[a];
-                c[a] = fmaf(-t, s[a], 1.0f);
-                s[a] = sn;
-            }
+            // coordinates 0 and 1 as packed pairs, 2 alone; the same operations per
+            // value: t = s + s, s' = t c, c' = fma(-t, s, 1) (-t = -2 s exactly)
+            const float2 s01 = make_float2(s[0], s[1]), c01 = make_float2(c[0], c[1]);
+            const float2 t01 = mul_f32x2(s01, make_float2(2.0f, 2.0f));
+            const float2 tn01 = mul_f32x2(s01, make_float2(-2.0f, -2.0f));
+            const float2 sn01 = mul_f32x2(t01, c01);
+            const float2 cn01 = fma2v(tn01, s01, make_float2(1.0f, 1.0f));
+            s[0] = sn01.x;
+            s[1] = sn01.y;
+            c[0] = cn01.x;
+            c[1] = cn01.y;
+            const float t = s[2] + s[2];
+            const float sn = t * c[2];
+            c[2] = fmaf(-t, s[2], 1.0f);
+            s[2] = sn;
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
