@@ -290,6 +290,33 @@ def test_c1_bf16_against_fp64_oracle(R, seed):
     assert np.max(np.abs(so[:, 0] - ro[:, 0]) / np.maximum(1.0, ro[:, 0])) <= 5e-2
 
 
+@pytest.mark.parametrize("width,hidden", [(64, 1), (64, 3), (32, 5)])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8", "fp8s"])
+def test_network_shapes_outside_the_specialised_ones(R, width, hidden, prec):
+    """The network kernels are specialised for the 4 x 64 and 2 x 32 shapes; every other
+    shape runs the generic instantiation (hidden count read at run time).  c1 scene
+    and view with these shapes, against the FP64 oracle: the FP32 path to 1e-5 of the
+    FP32-mode oracle, the others by PSNR."""
+    import dataclasses
+    cfg = dataclasses.replace(S.CONFIGS["c1"], width=width, hidden=hidden)
+    grid, tree, P = _setup(R, cfg, 1, prec="fp32" if prec == "fp8s" else prec)
+    o, d = _rays(cfg, 1)
+    if prec == "fp8s":
+        oc, dc = S.view_rays(cfg, 1, 7, 64, 64)
+        amax = R.calibrate_fp8(_dev(oc), _dev(dc), cfg.hidden, steps=cfg.steps, cap=cfg.cap)
+        R.load_mlps(_gpu_weights(R, cfg, grid, 1), cfg.width, cfg.hidden, cfg.lx, cfg.ld, act_max=amax)
+    rgb, depth, opac = [t.cpu().numpy() for t in R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)]
+    assert np.all(np.isfinite(rgb))
+    if prec == "fp32":
+        ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1, threads=8)
+        _check_pixels(rgb, depth, opac, ref)
+        return
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=0, threads=8)
+    psnr = _psnr(rgb, ref["rgb"])
+    print(f"{prec} {hidden} x {width}: PSNR {psnr:.2f} dB")
+    assert psnr >= (45.0 if prec == "bf16" else 30.0)
+
+
 def test_c2_bf16_sampled_psnr(R):
     cfg = S.CONFIGS["c2"]
     _, tree, P = _setup(R, cfg, 0, prec="bf16")
