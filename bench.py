@@ -20,6 +20,7 @@ against) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -487,6 +488,9 @@ def run_c5(args):
     torch.cuda.set_device(0)
     build.build()
     cfg = S.CONFIGS["c1"]
+    if args.leaf_net:  # another leaf network shape, e.g. "4x64" (the scene is unchanged)
+        h, w = (int(v) for v in args.leaf_net.lower().split("x"))
+        cfg = dataclasses.replace(cfg, hidden=h, width=w)
     grid = S.density_grid(S.scene_for(cfg.scene, 0), cfg.G) * np.float32(args.density_scale)
     R = amnerf.Renderer(0)
     R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
@@ -581,7 +585,8 @@ def run_c5(args):
         "value": head["Mrays/s"], "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "dtype": "bf16",
         "data": "synthetic",
-        "config": {"workload": f"config-1 scene x{args.density_scale:g} density (<=16 leaves, 2x32 BF16 MLPs); "
+        "config": {"workload": f"config-1 scene x{args.density_scale:g} density (<=16 leaves, "
+                               f"{cfg.hidden}x{cfg.width} BF16 MLPs); "
                                f"proposal trained on {n_train_views} views at {tw}x{th}, evaluated on {views} "
                                f"held-out views at {px_w}x{px_h}",
                    "rays_per_step": n, "density_scale": args.density_scale, "oracle_rays": len(idx)},
@@ -652,6 +657,7 @@ def main():
     ap.add_argument("--train-views", type=int, default=64, help="c5: plain-rendered training views")
     ap.add_argument("--train-steps", type=int, default=3000, help="c5: Adam steps")
     ap.add_argument("--density-scale", type=float, default=1.0, help="c5: factor on every density of the scene")
+    ap.add_argument("--leaf-net", default="", help="c5: leaf network shape HxW (default: the config's 2x32)")
     ap.add_argument("--px", type=int, default=None, help="square image size (default: the config's)")
     args = ap.parse_args()
     if args.warmup < 3:
