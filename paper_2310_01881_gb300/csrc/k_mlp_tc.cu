@@ -23,10 +23,12 @@
 // Thread r of a warpgroup owns sample row r: it rebuilds the sample, encodes
 // gamma(x) ++ gamma(d) and writes it into its TMEM lane (tcgen05.st 32x32b); after
 // each MMA it reads its row of D (tcgen05.ld 32x32b: warp q of the group owns lanes
-// 32q..32q+31) and writes the next layer's A back into TMEM.  BF16 folds every bias
-// into its contraction (a weight column against a constant-1 input column), so the
-// epilogue is only ReLU with the conversion (cvt.rn.relu.bf16x2); E4M3 applies its
-// channel scales and bias with one packed FMA per pair first.  The 4-wide head is one
+// 32q..32q+31) and writes the next layer's A back into TMEM.  BF16 folds layer 0's
+// bias into its contraction (a weight column against a constant-1 input column) and
+// starts every later layer's accumulator at its FP32 bias (written by the epilogue
+// before), so the epilogue is ReLU with the conversion (cvt.rn.relu.bf16x2) and the
+// bias store; E4M3 applies its channel scales and bias with one packed FMA per pair
+// first.  The 4-wide head is one
 // more BF16 MMA (16 rows, 4 used) on relu(h) written into the group's D columns; it
 // runs while the group encodes its next tile, and its outputs (sigma = softplus,
 // rgb = sigmoid) are read just before that tile's first MMA.
@@ -61,13 +63,15 @@ __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / 
 
 // ---- per-leaf weight blob layout (bytes) -------------------------------------------
 // W0 [width x k0p], W1.. [width x kh] in the operand type (BF16, or E4M3 with FP32
-// per-output-channel scales sw [hidden][width]); head Wo FP32 [width][4]; FP32 biases
-// b_0..b_{hidden-1} [width] and bo [4].  BF16 folds each hidden layer's bias into the
-// contraction: input column k_in (90 for layer 0, width for the others) holds the
-// bias and the activation row carries 1 there, so kh = width + 16 and the epilogue
-// adds nothing.  E4M3 keeps kh = width and adds the FP32 bias in the epilogue (an
-// E4M3 bias would lose too much).  Both run the head as one more BF16 MMA: a 16-row
-// matrix (rows 0..3 used) of khead = width + 16 columns with the bias in column width.
+// per-output-channel scales sw [hidden][width]); head Wo BF16 [16 x khead]; FP32
+// biases b_0..b_{hidden-1} [width] and bo [4].  kh = khead = width.  BF16 folds layer
+// 0's bias into its contraction (input column 90, inside the padding to k0p = 96,
+// holds the bias and the encoded row carries 1 there); for every later BF16 layer and
+// for the head the epilogue of the layer before writes the FP32 bias into the
+// accumulator columns, and the MMAs accumulate onto it (a folded bias would cost one
+// more K = 16 step per layer).  E4M3 adds its FP32 bias in the epilogue, after the
+// scales (an E4M3 bias would lose too much).  Both run the head as one more BF16 MMA
+// of a 16-row matrix (rows 0..3 used).
 // E4M3 with static activation scales (act_max known per leaf and layer) folds them
 // in at packing: layer l's pre-activation is acc * sw[l][n] + bias[l][n] with
 // sw = s_w a_l / a_(l+1), bias = b / a_(l+1) (the last layer: s_w a_l and b), where
@@ -76,8 +80,8 @@ struct TcLayout {
     int width, hidden, k0, k0p, kh, khead, es;
     size_t w0, wh, wo, sw, bias, enc, stride;
     __host__ __device__ TcLayout(int w, int h, int k, bool f8)
-        : width(w), hidden(h), k0(k), k0p(round_up(f8 ? k : k + 1, f8 ? 32 : 16)), kh(f8 ? w : w + 16),
-          khead(w + 16), es(f8 ? 1 : 2) {
+        : width(w), hidden(h), k0(k), k0p(round_up(f8 ? k : k + 1, f8 ? 32 : 16)), kh(w),
+          khead(w), es(f8 ? 1 : 2) {
         w0 = 0;
         wh = w0 + (size_t)w * k0p * es;
         wo = wh + (size_t)(h - 1) * w * kh * es;  // head: 16 x khead BF16 (both precisions)
@@ -225,6 +229,29 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* w) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(w[0]),
                  "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
                  : "memory");
+}
+
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(__float_as_uint(v[0])),
+                 "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3]))
+                 : "memory");
+}
+
+// The N FP32 values at shared address b (the same for every row) into columns [0, N)
+// of this thread's TMEM lane: the initial accumulator of a layer's MMAs.
+template <int N>
+__device__ __forceinline__ void tmem_st_bias(uint32_t taddr, uint32_t b) {
+#pragma unroll
+    for (int c = 0; c < N / 16; ++c) {
+        uint32_t w[16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(w[4 * i + 0]), "=r"(w[4 * i + 1]), "=r"(w[4 * i + 2]), "=r"(w[4 * i + 3])
+                         : "r"(b + 64u * c + 16u * i)
+                         : "memory");
+        tmem_st16(taddr + 16u * c, w);
+    }
 }
 
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
@@ -534,6 +561,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         const uint32_t d_row = d_col + lane;                          // this warp's lanes
         const uint32_t a_row = a_col + lane;
         const float* bias = reinterpret_cast<const float*>(wbuf + lay.bias);
+        const uint32_t bias_s = smem_u32(bias);
         const uint8_t* wall = reinterpret_cast<const uint8_t*>(g.weights);
 
         // ---- tile schedule of this worker (one warpgroup)
@@ -683,8 +711,11 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                             mma_e4m3_ts(d_col, a_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd, kk > 0 ? 1u : 0u);
                     } else {
                         const uint32_t idd = idesc_bf16(W);
+                        // layer 0 starts from zero (its bias is folded in); later layers
+                        // accumulate onto the bias the previous epilogue wrote
                         for (int kk = 0; kk < kin / KI; ++kk)
-                            mma_bf16_ts(d_col, a_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd, kk > 0 ? 1u : 0u);
+                            mma_bf16_ts(d_col, a_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd,
+                                        (kk > 0 || l > 0) ? 1u : 0u);
                     }
                     mma_commit(bar_m);
                 }
@@ -747,10 +778,11 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                             }
                             tmem_st16(a_row + 16u * h, pk);
                         }
-                        if (l == 0) {  // input column W of the hidden layers: the constant 1 of the bias
-                            uint32_t c8[8] = {pack_bf16(1.0f, 0.0f), 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-                            tmem_st8(a_row + (uint32_t)(W / 2), c8);
-                        }
+                        // layer l + 1 accumulates onto its bias.  The source registers of
+                        // a tcgen05.st stay reserved until its wait, so A's stores are
+                        // waited for first (else A and the bias take 3 W/2 registers).
+                        tmem_st_wait();
+                        tmem_st_bias<W>(d_row, bias_s + 4u * (uint32_t)((l + 1) * W));
                     } else if (g.act_static) {
                         // relu(pre) is already in the next layer's E4M3 scale
                         uint32_t pk[W / 4];
@@ -802,8 +834,8 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     kin = lay.kh;
                 } else {
                     // relu(h) as BF16 into this group's D columns (each 32-column block is
-                    // read before it is overwritten), the constant 1 of the head bias after
-                    // it, then the head MMA (16 x khead) into D columns kHeadCol..+15
+                    // read before it is overwritten), the head bias into D columns
+                    // kHeadCol..+3, then the head MMA (16 x khead) accumulates onto it
                     if constexpr (!F8) {
                         float vr[W];
                         tmem_ld_row<W>(d_row, vr);
@@ -834,10 +866,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                             tmem_st16(d_row + 16u * h, pk);
                         }
                     }
-                    {
-                        uint32_t c8[8] = {pack_bf16(1.0f, 0.0f), 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-                        tmem_st8(d_row + (uint32_t)(W / 2), c8);
-                    }
+                    tmem_st4(d_row + kHeadCol, bias + (size_t)hidden * W);
                     tmem_st_wait();
                     tc_fence_before();
                     wg_bar(bar_id);
@@ -847,8 +876,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                         const uint32_t sbo = (uint32_t)lay.khead * 16u;
                         const uint32_t idd = idesc_bf16(16);
                         for (int kk = 0; kk < lay.khead / 16; ++kk)
-                            mma_bf16_ts(d_col + kHeadCol, d_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd,
-                                        kk > 0 ? 1u : 0u);
+                            mma_bf16_ts(d_col + kHeadCol, d_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd, 1u);
                         mma_commit(bar_m);
                     }
                     pending = true;
@@ -958,8 +986,10 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
                     const uint16_t b = f2bf(row[k]);
                     std::memcpy(base + cm_offset(n, k, K), &b, 2);
                 }
-                const uint16_t bb = f2bf(w[(size_t)width * kin + n]);  // folded bias at input column kin
-                std::memcpy(base + cm_offset(n, kin, K), &bb, 2);
+                if (l == 0) {  // layer 0's bias folded in at input column kin (inside the padding)
+                    const uint16_t bb = f2bf(w[(size_t)width * kin + n]);
+                    std::memcpy(base + cm_offset(n, kin, K), &bb, 2);
+                }
             }
         }
         w += (size_t)width * kin;
@@ -976,15 +1006,13 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
         kin = width;
     }
     if (f8 && act_max) *reinterpret_cast<float*>(dst + lay.enc) = 1.0f / act_scale(0);
-    {  // head: rows 0..3 of a 16 x khead BF16 matrix, the bias in column `width`
+    {  // head: rows 0..3 of a 16 x khead BF16 matrix (its bias stays FP32)
         uint8_t* hb = dst + lay.wo;
         for (int n = 0; n < 4; ++n) {
             for (int k = 0; k < width; ++k) {
                 const uint16_t b = f2bf(w[(size_t)n * width + k]);
                 std::memcpy(hb + cm_offset(n, k, lay.khead), &b, 2);
             }
-            const uint16_t bb = f2bf(w[(size_t)4 * width + n]);
-            std::memcpy(hb + cm_offset(n, width, lay.khead), &bb, 2);
         }
     }
     w += 4 * width;
