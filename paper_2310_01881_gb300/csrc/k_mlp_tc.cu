@@ -30,8 +30,10 @@
 // bias store; E4M3 applies its channel scales and bias with one packed FMA per pair
 // first.  The 4-wide head is one
 // more BF16 MMA (16 rows, 4 used) on relu(h) written into the group's D columns; it
-// runs while the group encodes its next tile, and its outputs (sigma = softplus,
-// rgb = sigmoid) are read just before that tile's first MMA.
+// runs while the group encodes its next tile.  Its accumulator sits in 16 TMEM
+// columns that no layer writes, so its outputs (sigma = softplus, rgb = sigmoid) are
+// read with the next tile's layer-0 accumulator and activated and stored while that
+// tile's layer-1 MMAs run.
 //
 // Several warpgroups per CTA work on different tiles, so one group's epilogue
 // overlaps another's MMA.  Each group's leader thread (in warp grp % 4, so the
@@ -72,10 +74,13 @@ __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / 
 // more K = 16 step per layer).  E4M3 adds its FP32 bias in the epilogue, after the
 // scales (an E4M3 bias would lose too much).  Both run the head as one more BF16 MMA
 // of a 16-row matrix (rows 0..3 used).
-// E4M3 with static activation scales (act_max known per leaf and layer) folds them
-// in at packing: layer l's pre-activation is acc * sw[l][n] + bias[l][n] with
-// sw = s_w a_l / a_(l+1), bias = b / a_(l+1) (the last layer: s_w a_l and b), where
-// a_l = act_max_l / 448, so relu(pre) is already the next layer's E4M3 input.
+// E4M3 with static activation scales (act_max known per leaf and layer) uses one
+// weight scale per layer, chosen so that the accumulator needs no rescaling: with
+// a_0 = act_max_0 / 448 and a_(l+1) = a_l * beta_l, layer l's weights are stored as
+// W / beta_l and its bias as b / a_(l+1), so relu(acc + bias) is already layer l+1's
+// E4M3 input (beta_l >= max|W| / 448 keeps the weights in range, and
+// a_(l+1) >= act_max_(l+1) / 448 the activations); the head weights take a_hidden.
+// Like BF16, every layer after the first starts its accumulator at its bias.
 struct TcLayout {
     int width, hidden, k0, k0p, kh, khead, es;
     size_t w0, wh, wo, sw, bias, enc, stride;
@@ -322,17 +327,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 4 consecutive FP32 columns of this thread's TMEM lane (load + wait).
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
-    uint32_t r[4];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+// 4 consecutive FP32 columns of this thread's TMEM lane, without waiting.
+__device__ __forceinline__ void tmem_ld4_nowait(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
 }
 
 // The W FP32 columns of this thread's TMEM lane: all loads issued, then one wait.
@@ -491,17 +491,20 @@ __device__ __forceinline__ void crossing_data(const MlpArgs& g, uint32_t id, flo
     }
 }
 
-// TMEM columns per warpgroup: D (accumulator, up to 64 FP32 columns) then A (up to
-// 48 columns = 96 BF16 features per lane).
+// TMEM columns per warpgroup: D (accumulator, up to 64 FP32 columns), A (up to 48
+// columns = 96 BF16 features per lane), then the head accumulator (16 columns), which
+// no layer writes: a tile's head result is read during the next tile's layers.
 constexpr uint32_t kGroupCols = 128;
 constexpr uint32_t kACol = 64;
-constexpr uint32_t kHeadCol = 48;  // BF16 head accumulator (16 columns) inside the D columns
+constexpr uint32_t kHeadCol = 112;
 
 // F8 = false: BF16 operands (kind::f16, K = 16 per MMA, 2 features per TMEM column).
-// F8 = true:  E4M3 operands (kind::f8f6f4, K = 32 per MMA, 4 features per column) with
-//             per-output-channel weight scales and a per-row activation scale: each
-//             row is quantized as q = h * 448 / max|h_row| and the next accumulator is
-//             rescaled by (max|h_row| / 448) * sw[n] before its bias is added.
+// F8 = true:  E4M3 operands (kind::f8f6f4, K = 32 per MMA, 4 features per column).
+//   ST = false: per-output-channel weight scales and a per-row activation scale: each
+//               row is quantized as q = h * 448 / max|h_row| and the next accumulator
+//               is rescaled by (max|h_row| / 448) * sw[n] before its bias is added.
+//   ST = true:  static per-layer scales folded in at packing (see TcLayout): the
+//               epilogue is ReLU and the conversion, as for BF16.
 // HC > 0: the number of hidden layers fixed at compile time, so the layer loop is
 // unrolled and every layout offset is a constant (about 12 % faster on the 4 x 64
 // network); HC = 0 reads it from the arguments.  The shapes of the workloads here
@@ -509,14 +512,14 @@ constexpr uint32_t kHeadCol = 48;  // BF16 head accumulator (16 columns) inside 
 template <int W>
 constexpr int kHiddenFor = W == 64 ? 4 : 2;
 
-template <int W, bool F8, int HC>
+template <int W, bool F8, bool ST, int HC>
 __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n_groups, uint32_t tmem_cols) {
     const int hidden = HC > 0 ? HC : g.hidden;  // hidden layers (a compile-time constant when HC > 0)
     constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
     constexpr int KI = F8 ? 32 : 16;        // K per MMA instruction
     constexpr int EPW = F8 ? 4 : 2;         // elements per 32-bit TMEM column
     constexpr int K0P = round_up(F8 ? K0 : K0 + 1, KI);  // BF16: + the bias column
-    static_assert(K0P / EPW <= (int)(kGroupCols - kACol), "layer-0 input does not fit the A columns");
+    static_assert(K0P / EPW <= (int)(kHeadCol - kACol), "layer-0 input does not fit the A columns");
     static_assert(W <= (int)kACol, "accumulator does not fit the D columns");
     extern __shared__ __align__(1024) uint8_t smem[];
     const TcLayout lay(W, hidden, K0, F8);
@@ -588,29 +591,33 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         uint32_t ph_w = 0, ph_m = 0;
         int cur = -1;
         bool ok = true;
-        // BF16: the head MMA of a tile runs while the group encodes its next tile; its
-        // outputs are read (and stored to slot_prev) just before that tile's first MMA
-        bool pending = false;
-        uint64_t slot_prev = ~0ull;
-        auto finish_head = [&]() -> bool {
+        // The head MMA of a tile runs while the group encodes its next tile.  Before that
+        // tile's first MMA only the leader waits for it (the head reads D, which layer 0
+        // overwrites); its result, in columns no layer writes, is read with the layer-0
+        // accumulator and activated and stored while the layer-1 MMAs run.
+        bool pending = false;   // head MMA issued, its completion not yet consumed
+        bool have_out = false;  // a head result in TMEM waits to be read
+        bool zpend = false;     // a head result in registers waits to be stored
+        bool head_bad = false;  // the leader's wait for a head MMA ran out
+        uint64_t slot_prev = ~0ull, slot_z = ~0ull;
+        uint32_t zr[4] = {0u, 0u, 0u, 0u};
+        auto store_head = [&]() {
+            if (slot_z != ~0ull) {
+                float4 o;
+                o.x = softplus_f(__uint_as_float(zr[0]));
+                o.y = sigmoid_f(__uint_as_float(zr[1]));
+                o.z = sigmoid_f(__uint_as_float(zr[2]));
+                o.w = sigmoid_f(__uint_as_float(zr[3]));
+                g.slot_out[slot_z] = o;
+            }
+            zpend = false;
+        };
+        // the whole group waits for the head MMA (a leaf change: it reads the weights)
+        auto head_group_wait = [&]() -> bool {
             const bool okh = group_wait(bar_m, ph_m, bar_id, flag, leader);
             ph_m ^= 1u;
             pending = false;
-            if (!okh) return false;
-            tc_fence_after();
-            float z[4];
-            tmem_ld4(d_row + kHeadCol, z);
-            if (slot_prev != ~0ull) {
-                float4 o;
-                o.x = softplus_f(z[0]);
-                o.y = sigmoid_f(z[1]);
-                o.z = sigmoid_f(z[2]);
-                o.w = sigmoid_f(z[3]);
-                g.slot_out[slot_prev] = o;
-            }
-            tc_fence_before();
-            wg_bar(bar_id);  // every row has read the head accumulator before D is reused
-            return true;
+            return okh;
         };
 
         // software pipeline: the crossing id of the next tile is fetched after the first
@@ -623,7 +630,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
 
         for (uint32_t t = t_first; t < t_stop && ok;) {
             if (leaf != cur) {
-                if (pending && !(ok = finish_head())) break;  // the head MMA still reads the weights
+                if (pending && !(ok = head_group_wait())) break;  // the head MMA still reads the weights
                 wg_bar(bar_id);  // every row is done with the previous leaf's weights and biases
                 if (leader) {
                     fence_proxy_async();
@@ -664,7 +671,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 } else {
                     static_assert(K0P == 96, "E4M3 layer-0 input is stored as 16 + 8 columns");
                     float inv;
-                    if (g.act_static) {  // the leaf's static encoding scale (in the weight blob)
+                    if constexpr (ST) {  // the leaf's static encoding scale (in the weight blob)
                         inv = *reinterpret_cast<const float*>(wbuf + lay.enc);
                         s_a = 1.0f;
                     } else {  // this row's own scale
@@ -689,7 +696,13 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             tmem_st_wait();
             tc_fence_before();
             wg_bar(bar_id);
-            if (pending && !(ok = finish_head())) break;
+            if (pending) {
+                // on expiry the leader issues no more MMAs, so the group's next wait runs
+                // out too and the whole group leaves through it
+                if (leader && !mbar_wait_bounded(bar_m, ph_m)) head_bad = true;
+                ph_m ^= 1u;
+                pending = false;
+            }
 
             int leaf_n = leaf;
             uint32_t id_n = 0xffffffffu;
@@ -700,15 +713,18 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
 #pragma unroll
             for (int l = 0; l < hidden; ++l) {
                 if (!ok) break;
-                if (leader) {
+                if (leader && !head_bad) {
                     tc_fence_after();
                     const uint32_t b_base =
                         w_addr + (uint32_t)(l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * W * lay.kh * lay.es);
                     const uint32_t sbo = (uint32_t)kin * (F8 ? 8u : 16u);  // 8-row group stride in bytes
                     if constexpr (F8) {
                         const uint32_t idd = idesc_e4m3(W);
+                        // static scales: layers after the first accumulate onto their bias
+                        const bool onto = l > 0 && ST;
                         for (int kk = 0; kk < kin / KI; ++kk)
-                            mma_e4m3_ts(d_col, a_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd, kk > 0 ? 1u : 0u);
+                            mma_e4m3_ts(d_col, a_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd,
+                                        (kk > 0 || onto) ? 1u : 0u);
                     } else {
                         const uint32_t idd = idesc_bf16(W);
                         // layer 0 starts from zero (its bias is folded in); later layers
@@ -719,15 +735,9 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     }
                     mma_commit(bar_m);
                 }
-                if (l == 0 && g.schedule == kSchedDynamic && leader)
-                    sh->next_tile[grp] = atomicAdd(g.tile_counter, 1u) + g.t_begin;
-                ok = group_wait(bar_m, ph_m, bar_id, flag, leader);
-                ph_m ^= 1u;
-                if (!ok) break;
-                tc_fence_after();
-                if (l == 0) {
-                    // next tile of this worker, its leaf and this row's crossing id
-                    t_next = g.schedule == kSchedDynamic ? sh->next_tile[grp] : t + t_step;
+                // next tile of this worker, its leaf and this row's crossing id
+                auto next_lookup = [&](uint32_t tn) {
+                    t_next = tn;
                     if (t_next < t_stop) {
                         if (t_next - t <= 8u) {
                             while (__ldg(g.tile_off + leaf_n + 1) <= t_next) ++leaf_n;
@@ -736,21 +746,49 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                         }
                         id_n = row_crossing(g, leaf_n, t_next, ci);
                     }
-                }
-                // next tile's interval and ray, one layer after its id was requested
-                if (l == (hidden > 1 ? 1 : 0)) crossing_data(g, id_n, xi, ro, rd);
+                };
+                const bool dyn = g.schedule == kSchedDynamic;
+                if (l == 0 && dyn && leader) sh->next_tile[grp] = atomicAdd(g.tile_counter, 1u) + g.t_begin;
+                // static schedules know the next tile already: its dependent loads (leaf,
+                // crossing id, then one layer later interval and ray) are issued before
+                // the MMA wait, so their latency overlaps the MMAs
+                if (!dyn && l == 0) next_lookup(t + t_step);
+                if (!dyn && hidden > 1 && l == 1) crossing_data(g, id_n, xi, ro, rd);
+                if (zpend) store_head();  // the previous tile's outputs, during this layer's MMAs
+                ok = group_wait(bar_m, ph_m, bar_id, flag, leader);
+                ph_m ^= 1u;
+                if (!ok) break;
+                tc_fence_after();
+                if (dyn && l == 0) next_lookup(sh->next_tile[grp]);  // published by the wait's barrier
+                if ((dyn || hidden == 1) && l == (hidden > 1 ? 1 : 0)) crossing_data(g, id_n, xi, ro, rd);
                 const float* b = bias + (size_t)l * W;
                 const float* sw = reinterpret_cast<const float*>(wbuf + lay.sw) + (size_t)l * W;
                 const bool last = l + 1 == hidden;
+                // the previous tile's head result: loaded now, waited for with D below
+                if (l == 0 && have_out) {
+                    tmem_ld4_nowait(d_row + kHeadCol, zr);
+                    slot_z = slot_prev;
+                    have_out = false;
+                    zpend = true;
+                }
                 // pre-activation of 4 consecutive columns c0..c0+3 of this row
                 auto pre4 = [&](const float* v, int c0, float2& p01, float2& p23) {
                     if constexpr (F8) {
-                        const float4 bb = *reinterpret_cast<const float4*>(b + c0);
-                        const float4 ss = *reinterpret_cast<const float4*>(sw + c0);
-                        if (g.act_static) {  // scales folded into sw and the bias
-                            p01 = fma2v(make_float2(v[0], v[1]), make_float2(ss.x, ss.y), make_float2(bb.x, bb.y));
-                            p23 = fma2v(make_float2(v[2], v[3]), make_float2(ss.z, ss.w), make_float2(bb.z, bb.w));
+                        if constexpr (ST) {
+                            // per-layer scales: the accumulator is already in the next layer's
+                            // units; layer 0 adds its (scaled) bias here, the others start
+                            // from it
+                            if (l == 0) {
+                                const float4 bb = *reinterpret_cast<const float4*>(b + c0);
+                                p01 = make_float2(v[0] + bb.x, v[1] + bb.y);
+                                p23 = make_float2(v[2] + bb.z, v[3] + bb.w);
+                            } else {
+                                p01 = make_float2(v[0], v[1]);
+                                p23 = make_float2(v[2], v[3]);
+                            }
                         } else {
+                            const float4 bb = *reinterpret_cast<const float4*>(b + c0);
+                            const float4 ss = *reinterpret_cast<const float4*>(sw + c0);
                             p01 = fma_f32x2(s_a, mul_f32x2(make_float2(v[0], v[1]), make_float2(ss.x, ss.y)),
                                             make_float2(bb.x, bb.y));
                             p23 = fma_f32x2(s_a, mul_f32x2(make_float2(v[2], v[3]), make_float2(ss.z, ss.w)),
@@ -783,22 +821,22 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                         // waited for first (else A and the bias take 3 W/2 registers).
                         tmem_st_wait();
                         tmem_st_bias<W>(d_row, bias_s + 4u * (uint32_t)((l + 1) * W));
-                    } else if (g.act_static) {
-                        // relu(pre) is already in the next layer's E4M3 scale
+                    } else if constexpr (ST) {
+                        // relu(pre) is already the next layer's E4M3 input; then the next
+                        // layer's accumulator starts from its scaled bias
                         uint32_t pk[W / 4];
+                        float vr[W];
+                        tmem_ld_row<W>(d_row, vr);
 #pragma unroll
-                        for (int h = 0; h < W / 32; ++h) {
-                            float v[32];
-                            tmem_ld32(d_row + 32u * h, v);
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) {
-                                float2 p01, p23;
-                                pre4(v + 4 * c, 32 * h + 4 * c, p01, p23);
-                                pk[8 * h + c] = pack_relu_e4m3x4(p01.x, p01.y, p23.x, p23.y);
-                            }
+                        for (int c = 0; c < W / 4; ++c) {
+                            float2 p01, p23;
+                            pre4(vr + 4 * c, 4 * c, p01, p23);
+                            pk[c] = pack_relu_e4m3x4(p01.x, p01.y, p23.x, p23.y);
                         }
                         if constexpr (W / 4 == 16) tmem_st16(a_row, pk);
                         else tmem_st8(a_row, pk);
+                        tmem_st_wait();
+                        tmem_st_bias<W>(d_row, bias_s + 4u * (uint32_t)((l + 1) * W));
                     } else {
                         float hv[W];
 #pragma unroll
@@ -880,14 +918,23 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                         mma_commit(bar_m);
                     }
                     pending = true;
+                    have_out = true;
                     slot_prev = slot;
                 }
             }
+            if (zpend) store_head();  // one hidden layer: stored after the head MMA issue
             leaf = leaf_n;
             id = id_n;
             t = t_next;
         }
-        if (ok && pending) ok = finish_head();
+        if (ok && pending) ok = head_group_wait();
+        if (ok && have_out) {
+            tc_fence_after();
+            tmem_ld4_nowait(d_row + kHeadCol, zr);
+            tmem_ld_wait();
+            slot_z = slot_prev;
+            store_head();
+        }
         if (!ok && leader) atomicCAS(g.err, 0, kDevErrTimeout);
     }
     tc_fence_before();
@@ -927,10 +974,13 @@ cudaError_t prepare_w(int hidden, int* max_groups) {
     if (e != cudaSuccess) return e;
     *max_groups = max_groups_for<W, F8>(hidden, max_smem);
     if (*max_groups < 1) return cudaErrorInvalidConfiguration;
-    e = cudaFuncSetAttribute(k_mlp_tc<W, F8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_mlp_tc<W, F8, kHiddenFor<W>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                max_smem);
+    const void* fns[4] = {(const void*)k_mlp_tc<W, F8, false, 0>, (const void*)k_mlp_tc<W, F8, false, kHiddenFor<W>>,
+                          (const void*)k_mlp_tc<W, F8, F8, 0>, (const void*)k_mlp_tc<W, F8, F8, kHiddenFor<W>>};
+    for (const void* f : fns) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <int W, bool F8>
@@ -947,8 +997,14 @@ cudaError_t launch_w(cudaStream_t s, const MlpArgs& a, int grid) {
     // resident on the SM and wait in tcgen05.alloc for columns this CTA holds
     size_t smem = lay.stride * groups + sizeof(TcShared) + 64;
     if (smem < (size_t)max_smem / 2 + 1024) smem = (size_t)max_smem / 2 + 1024;
-    if (a.hidden == kHiddenFor<W>) k_mlp_tc<W, F8, kHiddenFor<W>><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
-    else k_mlp_tc<W, F8, 0><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
+    const bool hc = a.hidden == kHiddenFor<W>;
+    if (F8 && a.act_static) {
+        if (hc) k_mlp_tc<W, F8, F8, kHiddenFor<W>><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
+        else k_mlp_tc<W, F8, F8, 0><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
+    } else {
+        if (hc) k_mlp_tc<W, F8, false, kHiddenFor<W>><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
+        else k_mlp_tc<W, F8, false, 0><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
+    }
     return cudaGetLastError();
 }
 
@@ -962,23 +1018,39 @@ size_t tc_leaf_stride_bytes(int width, int hidden, int k0, int prec) {
 
 void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0, int prec, const float* act_max) {
     const bool f8 = prec == 2;
+    const bool stat = f8 && act_max;
     const TcLayout lay(width, hidden, k0, f8);
-    // static activation scale of layer l's input (1 when the activations are all zero)
-    auto act_scale = [&](int l) { return act_max[l] > 0.0f ? act_max[l] / 448.0f : 1.0f; };
     std::memset(dst, 0, lay.stride);
     const float* w = src;
     float* bias = reinterpret_cast<float*>(dst + lay.bias);
     float* sw = reinterpret_cast<float*>(dst + lay.sw);
+    // E4M3 with static scales: alpha is the scale of the current layer's input (real =
+    // alpha * E4M3 value), starting from the encoding's act_max_0 / 448; layer l's
+    // weights take one scale beta for the whole layer, at least max|W| / 448 and large
+    // enough that alpha * beta (the next input's scale) maps act_max_(l+1) into range.
+    // The accumulator is then already the next input in its scale, the bias is stored
+    // divided by alpha * beta, and the head weights take the last alpha.
+    float alpha = stat ? (act_max[0] > 0.0f ? act_max[0] / 448.0f : 1.0f) : 1.0f;
     int kin = k0;
     for (int l = 0; l < hidden; ++l) {
         const int K = l == 0 ? lay.k0p : lay.kh;
         uint8_t* base = dst + (l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * width * lay.kh * lay.es);
+        float beta = 1.0f;
+        if (stat) {
+            float m = 0.0f;
+            for (size_t i = 0; i < (size_t)width * kin; ++i) m = std::fmax(m, std::fabs(w[i]));
+            beta = m > 0.0f ? m / 448.0f : 1.0f;
+            if (l + 1 < hidden) beta = std::fmax(beta, act_max[l + 1] / (448.0f * alpha));
+        }
         for (int n = 0; n < width; ++n) {
             const float* row = w + (size_t)n * kin;
             if (f8) {
-                float m = 0.0f;
-                for (int k = 0; k < kin; ++k) m = std::fmax(m, std::fabs(row[k]));
-                const float s = m > 0.0f ? m / 448.0f : 1.0f;  // per-leaf, per-layer, per-output-channel
+                float s = beta;
+                if (!stat) {  // per-output-channel scale (per-row activation scales at run time)
+                    float m = 0.0f;
+                    for (int k = 0; k < kin; ++k) m = std::fmax(m, std::fabs(row[k]));
+                    s = m > 0.0f ? m / 448.0f : 1.0f;
+                }
                 sw[(size_t)l * width + n] = s;
                 for (int k = 0; k < kin; ++k) base[cm_offset8(n, k, K)] = f2e4m3(row[k] / s);
             } else {
@@ -993,24 +1065,18 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
             }
         }
         w += (size_t)width * kin;
-        for (int n = 0; n < width; ++n) bias[(size_t)l * width + n] = w[n];
-        if (f8 && act_max) {  // fold a_l and 1 / a_(l+1) into the channel scale and bias
-            const float al = act_scale(l);
-            const float inv_next = l + 1 < hidden ? 1.0f / act_scale(l + 1) : 1.0f;
-            for (int n = 0; n < width; ++n) {
-                sw[(size_t)l * width + n] = sw[(size_t)l * width + n] * al * inv_next;
-                bias[(size_t)l * width + n] *= inv_next;
-            }
-        }
+        const float next = alpha * beta;  // scale of this layer's output (1 unless static E4M3)
+        for (int n = 0; n < width; ++n) bias[(size_t)l * width + n] = stat ? w[n] / next : w[n];
+        alpha = next;
         w += width;
         kin = width;
     }
-    if (f8 && act_max) *reinterpret_cast<float*>(dst + lay.enc) = 1.0f / act_scale(0);
+    if (stat) *reinterpret_cast<float*>(dst + lay.enc) = act_max[0] > 0.0f ? 448.0f / act_max[0] : 1.0f;
     {  // head: rows 0..3 of a 16 x khead BF16 matrix (its bias stays FP32)
         uint8_t* hb = dst + lay.wo;
         for (int n = 0; n < 4; ++n) {
             for (int k = 0; k < width; ++k) {
-                const uint16_t b = f2bf(w[(size_t)n * width + k]);
+                const uint16_t b = f2bf(w[(size_t)n * width + k] * alpha);
                 std::memcpy(hb + cm_offset(n, k, lay.khead), &b, 2);
             }
         }
