@@ -374,10 +374,15 @@ __device__ __forceinline__ uint32_t pack_relu_e4m3x4(float a, float b, float c, 
     return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
-// Head activations with the SFU exp/log (relative error ~1e-6, far below the BF16/E4M3
-// operand rounding of this path).
+// Head activations with the SFU exp/log/reciprocal (relative error ~1e-6, far below the
+// BF16/E4M3 operand rounding of this path).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ float softplus_f(float z) { return z > 20.0f ? z : __logf(1.0f + __expf(z)); }
-__device__ __forceinline__ float sigmoid_f(float z) { return __frcp_rn(1.0f + __expf(-z)); }
+__device__ __forceinline__ float sigmoid_f(float z) { return rcp_approx(1.0f + __expf(-z)); }
 
 __device__ __forceinline__ int leaf_of_tile(const uint32_t* __restrict__ tile_off, int n_leaves, uint32_t t) {
     int lo = 0, hi = n_leaves;
@@ -708,7 +713,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             uint32_t id_n = 0xffffffffu;
             uint32_t t_next = t_stop;
 
-            // ---- hidden layers; the head runs on the CUDA cores in the last epilogue
+            // ---- hidden layers; the last epilogue issues the head MMA
             int kin = K0P;
 #pragma unroll
             for (int l = 0; l < hidden; ++l) {
@@ -749,18 +754,22 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 };
                 const bool dyn = g.schedule == kSchedDynamic;
                 if (l == 0 && dyn && leader) sh->next_tile[grp] = atomicAdd(g.tile_counter, 1u) + g.t_begin;
-                // static schedules know the next tile already: its dependent loads (leaf,
-                // crossing id, then one layer later interval and ray) are issued before
-                // the MMA wait, so their latency overlaps the MMAs
+                // The next tile's dependent loads are spread over the layers, each issued
+                // while MMAs run and consumed a layer later: static schedules know the next
+                // tile already, so its leaf and crossing id are looked up before the layer-0
+                // wait; its interval and ray at layer l_xd; the previous tile's outputs are
+                // stored at layer l_sh.
+                const int l_xd = hidden > 2 ? 2 : hidden - 1;
+                const int l_sh = hidden > 3 ? 3 : hidden - 1;
                 if (!dyn && l == 0) next_lookup(t + t_step);
-                if (!dyn && hidden > 1 && l == 1) crossing_data(g, id_n, xi, ro, rd);
-                if (zpend) store_head();  // the previous tile's outputs, during this layer's MMAs
+                if (!dyn && l > 0 && l == l_xd) crossing_data(g, id_n, xi, ro, rd);
+                if (zpend && l == l_sh) store_head();
                 ok = group_wait(bar_m, ph_m, bar_id, flag, leader);
                 ph_m ^= 1u;
                 if (!ok) break;
                 tc_fence_after();
                 if (dyn && l == 0) next_lookup(sh->next_tile[grp]);  // published by the wait's barrier
-                if ((dyn || hidden == 1) && l == (hidden > 1 ? 1 : 0)) crossing_data(g, id_n, xi, ro, rd);
+                if ((dyn || l_xd == 0) && l == l_xd) crossing_data(g, id_n, xi, ro, rd);
                 const float* b = bias + (size_t)l * W;
                 const float* sw = reinterpret_cast<const float*>(wbuf + lay.sw) + (size_t)l * W;
                 const bool last = l + 1 == hidden;
