@@ -570,6 +570,12 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         const uint32_t a_row = a_col + lane;
         const float* bias = reinterpret_cast<const float*>(wbuf + lay.bias);
         const uint32_t bias_s = smem_u32(bias);
+        // shared-memory descriptors of the first core matrix of W0, W1 and the head; the
+        // start-address field holds address / 16 in 14 bits, and every address here is
+        // below 2^18, so later core matrices are these plus (offset / 16)
+        const uint64_t desc_w0 = sdesc(w_addr + (uint32_t)lay.w0, (uint32_t)K0P * (F8 ? 8u : 16u));
+        const uint64_t desc_wh = sdesc(w_addr + (uint32_t)lay.wh, (uint32_t)lay.kh * (F8 ? 8u : 16u));
+        const uint64_t desc_wo = sdesc(w_addr + (uint32_t)lay.wo, (uint32_t)lay.khead * 16u);
         const uint8_t* wall = reinterpret_cast<const uint8_t*>(g.weights);
 
         // ---- tile schedule of this worker (one warpgroup)
@@ -720,23 +726,23 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 if (!ok) break;
                 if (leader && !head_bad) {
                     tc_fence_after();
-                    const uint32_t b_base =
-                        w_addr + (uint32_t)(l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * W * lay.kh * lay.es);
-                    const uint32_t sbo = (uint32_t)kin * (F8 ? 8u : 16u);  // 8-row group stride in bytes
+                    // this layer's first weight core matrix, then 256 B (16 descriptor
+                    // units) per K step
+                    const uint64_t b_desc =
+                        l == 0 ? desc_w0
+                               : desc_wh + (uint64_t)(((size_t)(l - 1) * W * lay.kh * lay.es) >> 4);
                     if constexpr (F8) {
                         const uint32_t idd = idesc_e4m3(W);
                         // static scales: layers after the first accumulate onto their bias
                         const bool onto = l > 0 && ST;
                         for (int kk = 0; kk < kin / KI; ++kk)
-                            mma_e4m3_ts(d_col, a_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd,
-                                        (kk > 0 || onto) ? 1u : 0u);
+                            mma_e4m3_ts(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, (kk > 0 || onto) ? 1u : 0u);
                     } else {
                         const uint32_t idd = idesc_bf16(W);
                         // layer 0 starts from zero (its bias is folded in); later layers
                         // accumulate onto the bias the previous epilogue wrote
                         for (int kk = 0; kk < kin / KI; ++kk)
-                            mma_bf16_ts(d_col, a_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd,
-                                        (kk > 0 || l > 0) ? 1u : 0u);
+                            mma_bf16_ts(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, (kk > 0 || l > 0) ? 1u : 0u);
                     }
                     mma_commit(bar_m);
                 }
@@ -919,11 +925,9 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     wg_bar(bar_id);
                     if (leader) {
                         tc_fence_after();
-                        const uint32_t b_base = w_addr + (uint32_t)lay.wo;
-                        const uint32_t sbo = (uint32_t)lay.khead * 16u;
                         const uint32_t idd = idesc_bf16(16);
                         for (int kk = 0; kk < lay.khead / 16; ++kk)
-                            mma_bf16_ts(d_col + kHeadCol, d_col + 8u * kk, sdesc(b_base + 256u * kk, sbo), idd, 1u);
+                            mma_bf16_ts(d_col + kHeadCol, d_col + 8u * kk, desc_wo + 16u * kk, idd, 1u);
                         mma_commit(bar_m);
                     }
                     pending = true;
