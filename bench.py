@@ -168,8 +168,11 @@ def sum_over_ranks(x: float, device="cuda") -> float:
     return _reduce(x, "sum", device)
 
 
-def _algorithmic(cfg, st):
-    """Algorithmic work of one step (bytes / flops), per the unit counts of the step."""
+def _algorithmic(cfg, st, slot_bytes=16):
+    """Algorithmic work of one step (bytes / flops), per the unit counts of the step.
+
+    slot_bytes: per-sample output (sigma, rgb) as written by the network and read by the
+    compositing: 16 (FP32 path) or 8 (4 x FP16, tensor-core paths)."""
     rays, xs, samples = st["rays"], st["crossings"], st["samples_generated"]
     k0 = S.mlp_input_width(cfg.lx, cfg.ld)
     w, h = cfg.width, cfg.hidden
@@ -177,8 +180,8 @@ def _algorithmic(cfg, st):
     return {
         "traverse_bytes": 24 * rays + 1 * rays + 10 * xs,
         "group_bytes": 1 * rays + 6 * xs,
-        "network_bytes": 24 * rays + 12 * xs + 16 * samples,
-        "composite_bytes": 21 * rays + 8 * xs + 16 * samples,
+        "network_bytes": 24 * rays + 12 * xs + slot_bytes * samples,
+        "composite_bytes": 21 * rays + 8 * xs + slot_bytes * samples,
         "network_flops": flops_per_sample * samples,
         "flops_per_sample": flops_per_sample,
     }
@@ -300,7 +303,7 @@ def run_ours(args):
                      "max_abs_rgb": float(np.abs(rgb - ref["rgb"]).max()),
                      "max_abs_opacity": float(np.abs(r["pixels"][2][idx] - ref["opacity"]).max())}
 
-    alg = _algorithmic(cfg, st)
+    alg = _algorithmic(cfg, st, 16 if head == "fp32" else 8)
     net_ms = hr["stage_ms"][2]
     if head == "fp32":
         peak = N_SM * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12

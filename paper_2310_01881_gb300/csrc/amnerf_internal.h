@@ -69,7 +69,7 @@ struct MlpArgs {
     int steps, maxc, cap;
     uint32_t maxc_magic;    // ceil(2^32 / maxc) (maxc >= 2): id / maxc by multiply-high (see div_maxc)
     int lg_steps;           // log2(steps)
-    float4* slot_out;
+    void* slot_out;         // per-sample outputs: float4 (FP32 path) or 4 x FP16 (tensor-core paths)
     int* err;
     float* amax;            // FP32 path, calibration: per leaf x hidden layer, max |input of layer l| (or NULL)
     int act_static;         // E4M3 path: static per-leaf, per-layer activation scales folded into the blob
@@ -89,10 +89,14 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
 size_t simt_leaf_stride_floats(int width, int hidden, int k0);
 
 // K-d: per-ray compositing.
-cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* xing, const float4* slot_out,
-                             uint32_t n, int steps, int maxc, int cap, float t_term, float bg0, float bg1,
-                             float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
+// slot_half: slot_out holds 4 x FP16 per sample (sigma, r, g, b), else float4.
+cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* xing, const void* slot_out,
+                             int slot_half, uint32_t n, int steps, int maxc, int cap, float t_term, float bg0,
+                             float bg1, float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
                              const float2* root = nullptr, float* bins = nullptr);
+// The generated slots (j < n_x[r] * steps) of 4 x FP16 per-sample outputs as float4.
+cudaError_t launch_slots_to_f32(cudaStream_t s, const uint8_t* n_x, const void* slot_half, float4* out, uint32_t n,
+                                int steps, int cap);
 
 // Proposal sampler (k_proposal.cu).
 int proposal_param_count();

@@ -490,8 +490,8 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         }
     }
     if (ctx->timing) cudaEventRecord(ctx->ev[3], s);
-    CK(launch_composite(s, ctx->d_nx, ctx->d_xing, ctx->d_slot, nn, steps, maxc, cap, p->t_term, p->bg[0], p->bg[1],
-                        p->bg[2], rgb, depth, opacity, ctx->d_stats, root_out, bins_out),
+    CK(launch_composite(s, ctx->d_nx, ctx->d_xing, ctx->d_slot, ctx->desc.prec != AMNERF_FP32, nn, steps, maxc, cap,
+                        p->t_term, p->bg[0], p->bg[1], p->bg[2], rgb, depth, opacity, ctx->d_stats, root_out, bins_out),
        "composite launch");
     if (ctx->timing) cudaEventRecord(ctx->ev[4], s);
 
@@ -515,9 +515,15 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
                "debug copy");
         if (dbg->order)
             CK(cudaMemcpyAsync(dbg->order, ctx->d_order, slots * 4, cudaMemcpyDeviceToDevice, s), "debug copy");
-        if (dbg->slot_out)
-            CK(cudaMemcpyAsync(dbg->slot_out, ctx->d_slot, (size_t)n * cap * 16, cudaMemcpyDeviceToDevice, s),
-               "debug copy");
+        if (dbg->slot_out) {
+            if (ctx->desc.prec != AMNERF_FP32)  // the tensor-core paths keep 4 x FP16 per sample
+                CK(launch_slots_to_f32(s, ctx->d_nx, ctx->d_slot, reinterpret_cast<float4*>(dbg->slot_out), (uint32_t)n,
+                                       steps, cap),
+                   "debug copy");
+            else
+                CK(cudaMemcpyAsync(dbg->slot_out, ctx->d_slot, (size_t)n * cap * 16, cudaMemcpyDeviceToDevice, s),
+                   "debug copy");
+        }
         if (dbg->prop_mask && mask)
             CK(cudaMemcpyAsync(dbg->prop_mask, mask, (size_t)n * 8, cudaMemcpyDeviceToDevice, s), "debug copy");
         if (dbg->prop_fallback && fallback)

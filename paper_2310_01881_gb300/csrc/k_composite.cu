@@ -18,6 +18,8 @@
 // same FP32 operation order as the traversal/sampling step.  Optionally (training
 // targets of the proposal sampler) every composited weight is also added to the
 // depth bin of its sample, and the residual transmittance is stored as bin 64.
+#include <cuda_fp16.h>
+
 #include "amnerf_internal.h"
 
 namespace amnerf {
@@ -30,9 +32,43 @@ struct RayAcc {
     uint32_t composited;
 };
 
+// Slot s of the per-sample outputs: float4, or 4 x FP16 (sigma, r, g, b) when HALF.
+template <bool HALF>
+__device__ __forceinline__ float4 load_slot(const void* __restrict__ slot_out, size_t s) {
+    if constexpr (HALF) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(slot_out) + s);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        return __ldg(reinterpret_cast<const float4*>(slot_out) + s);
+    }
+}
+
+// load_slot as a volatile load: issued where it stands, so a thread's loads of a whole
+// crossing are all in flight before the first of them is used.
+template <bool HALF>
+__device__ __forceinline__ float4 load_slot_now(const void* __restrict__ slot_out, size_t s) {
+    if constexpr (HALF) {
+        uint32_t a, b;
+        asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];"
+                     : "=r"(a), "=r"(b)
+                     : "l"(reinterpret_cast<const uint2*>(slot_out) + s));
+        const float2 fa = __half22float2(*reinterpret_cast<const __half2*>(&a));
+        const float2 fb = __half22float2(*reinterpret_cast<const __half2*>(&b));
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    } else {
+        float4 v;
+        asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "l"(reinterpret_cast<const float4*>(slot_out) + s));
+        return v;
+    }
+}
+
 // One ray by one warp, SPL consecutive slots per lane (32 SPL slots per pass).
-template <int SPL>
-__device__ __forceinline__ void composite_ray(const float2* __restrict__ xing, const float4* __restrict__ slot_out,
+template <int SPL, bool HALF>
+__device__ __forceinline__ void composite_ray(const float2* __restrict__ xing, const void* __restrict__ slot_out,
                                               int ns, int steps, int lg_steps, float inv_steps, size_t xbase,
                                               size_t sbase,
                                               float t_term, int lane, float r0, float bw, float* sbins, RayAcc& A) {
@@ -44,7 +80,7 @@ __device__ __forceinline__ void composite_ray(const float2* __restrict__ xing, c
         for (int i = 0; i < SPL; ++i) {
             const int s = s0 + SPL * lane + i;
             val[i] = s < ns;
-            v[i] = val[i] ? __ldg(slot_out + sbase + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[i] = val[i] ? load_slot<HALF>(slot_out, sbase + s) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < SPL; ++i) {
@@ -112,8 +148,9 @@ __device__ __forceinline__ void composite_ray(const float2* __restrict__ xing, c
     }
 }
 
+template <bool HALF>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
-    const uint8_t* __restrict__ n_x, const float2* __restrict__ xing, const float4* __restrict__ slot_out,
+    const uint8_t* __restrict__ n_x, const float2* __restrict__ xing, const void* __restrict__ slot_out,
     uint32_t n, int steps, int maxc, int cap, float t_term, float bg0, float bg1, float bg2,
     float* __restrict__ rgb, float* __restrict__ depth, float* __restrict__ opacity,
     unsigned long long* __restrict__ n_comp, const float2* __restrict__ root, float* __restrict__ bins) {
@@ -148,9 +185,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
         float* sb = bins ? s_bins[wib] : nullptr;
         // short rays: one slot per lane; longer ones: two (twice the bytes in flight)
         if (ns <= 32)
-            composite_ray<1>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
+            composite_ray<1, HALF>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
         else
-            composite_ray<2>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
+            composite_ray<2, HALF>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
         float T = A.T, cr = A.cr, cg = A.cg, cb = A.cb, dd = A.dd;
         composited += A.composited;
         // warp sums of (cr, cg, cb, dd) in 6 shuffles: each exchange halves the values a
@@ -191,13 +228,89 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
     }
 }
 
+// One thread per ray, 8 samples per crossing (the workloads' setting): the thread
+// composites its ray front to back in the definition's own order.  A crossing's 8
+// slots are one aligned 128-byte row piece (64 bytes as FP16), all loaded before the
+// crossing is composited, so every thread has a whole line in flight; the warp runs
+// until its last ray ends or terminates.
+template <bool HALF>
+__global__ void __launch_bounds__(256) k_composite_lane(
+    const uint8_t* __restrict__ n_x, const float2* __restrict__ xing, const void* __restrict__ slot_out, uint32_t n,
+    int maxc, int cap, float t_term, float bg0, float bg1, float bg2, float* __restrict__ rgb,
+    float* __restrict__ depth, float* __restrict__ opacity, unsigned long long* __restrict__ n_comp) {
+    constexpr int kSteps = 8;
+    const uint32_t ray = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t comp = 0;
+    if (ray < n) {
+        float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
+        const int nx = (int)__ldg(n_x + ray);
+        const float2* xr = xing + (size_t)ray * maxc;
+        const size_t row = (size_t)ray * cap;
+        bool alive = true;
+        for (int k = 0; k < nx && alive; ++k) {
+            const float2 x = __ldg(xr + k);
+            float4 v[kSteps];
+#pragma unroll
+            for (int j = 0; j < kSteps; ++j) v[j] = load_slot_now<HALF>(slot_out, row + (size_t)(k * kSteps + j));
+            // same FP32 operations as the sampling step: delta = (t_out - t_in) / steps
+            // (exact: a power of two), t_j = t_in + (j + 1/2) delta
+            const float delta = __fmul_rn(__fsub_rn(x.y, x.x), 1.0f / kSteps);
+#pragma unroll
+            for (int j = 0; j < kSteps; ++j) {
+                alive = alive && !(T < t_term);  // stop once T < t_term
+                if (alive) {
+                    const float t = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
+                    const float e = expf(-__fmul_rn(v[j].x, delta));
+                    const float w = T * (1.0f - e);
+                    cr += w * v[j].y;
+                    cg += w * v[j].z;
+                    cb += w * v[j].w;
+                    dd += w * t;
+                    T = T * e;
+                    ++comp;
+                }
+            }
+        }
+        rgb[3 * (size_t)ray + 0] = cr + T * bg0;
+        rgb[3 * (size_t)ray + 1] = cg + T * bg1;
+        rgb[3 * (size_t)ray + 2] = cb + T * bg2;
+        depth[ray] = dd;
+        opacity[ray] = 1.0f - T;
+    }
+    // composited samples: warp sums, one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) comp += __shfl_xor_sync(0xffffffffu, comp, o);
+    if ((threadIdx.x & 31) == 0 && comp) atomicAdd(n_comp, (unsigned long long)comp);
+}
+
+// Debug view: generated slots (j < n_x[r] * steps) of 4 x FP16 outputs as float4.
+__global__ void k_slots_to_f32(const uint8_t* __restrict__ n_x, const void* __restrict__ slot_half,
+                               float4* __restrict__ out, uint32_t n, int steps, int cap) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)n * cap) return;
+    const uint32_t r = (uint32_t)(i / (size_t)cap);
+    const int j = (int)(i - (size_t)r * cap);
+    if (j < (int)n_x[r] * steps) out[i] = load_slot<true>(slot_half, i);
+}
+
 }  // namespace
 
-cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* xing, const float4* slot_out,
-                             uint32_t n, int steps, int maxc, int cap, float t_term, float bg0, float bg1,
-                             float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
+cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* xing, const void* slot_out,
+                             int slot_half, uint32_t n, int steps, int maxc, int cap, float t_term, float bg0,
+                             float bg1, float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
                              const float2* root, float* bins) {
     if (n == 0) return cudaSuccess;
+    if (!bins && steps == 8) {  // one thread per ray
+        auto* stc = reinterpret_cast<unsigned long long*>(stats + 2);
+        const unsigned lb = (n + 255) / 256;
+        if (slot_half)
+            k_composite_lane<true><<<lb, 256, 0, s>>>(n_x, xing, slot_out, n, maxc, cap, t_term, bg0, bg1, bg2, rgb,
+                                                      depth, opacity, stc);
+        else
+            k_composite_lane<false><<<lb, 256, 0, s>>>(n_x, xing, slot_out, n, maxc, cap, t_term, bg0, bg1, bg2, rgb,
+                                                       depth, opacity, stc);
+        return cudaGetLastError();
+    }
     unsigned blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
     // resident CTAs per device, cached: only a cap on the launch size (any grid gives
     // the same result, the warps stride over the rays)
@@ -205,16 +318,30 @@ cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* x
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
         if (!cap_blocks[dev]) {
-            int sms = 0, per = 0;
+            int sms = 0, per = 0, per_h = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_composite, kWarpsPerBlock * 32, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_composite<false>, kWarpsPerBlock * 32, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_composite<true>, kWarpsPerBlock * 32, 0);
+            per = per_h > 0 && per_h < per ? per_h : per;
             cap_blocks[dev] = sms * (per > 0 ? per : 1);
         }
         if (cap_blocks[dev] > 0 && blocks > (unsigned)cap_blocks[dev]) blocks = (unsigned)cap_blocks[dev];
     }
-    k_composite<<<blocks, kWarpsPerBlock * 32, 0, s>>>(n_x, xing, slot_out, n, steps, maxc, cap, t_term, bg0, bg1,
-                                                       bg2, rgb, depth, opacity,
-                                                       reinterpret_cast<unsigned long long*>(stats + 2), root, bins);
+    auto* st = reinterpret_cast<unsigned long long*>(stats + 2);
+    if (slot_half)
+        k_composite<true><<<blocks, kWarpsPerBlock * 32, 0, s>>>(n_x, xing, slot_out, n, steps, maxc, cap, t_term, bg0,
+                                                                 bg1, bg2, rgb, depth, opacity, st, root, bins);
+    else
+        k_composite<false><<<blocks, kWarpsPerBlock * 32, 0, s>>>(n_x, xing, slot_out, n, steps, maxc, cap, t_term,
+                                                                  bg0, bg1, bg2, rgb, depth, opacity, st, root, bins);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slots_to_f32(cudaStream_t s, const uint8_t* n_x, const void* slot_half, float4* out, uint32_t n,
+                                int steps, int cap) {
+    const size_t total = (size_t)n * cap;
+    if (total == 0) return cudaSuccess;
+    k_slots_to_f32<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n_x, slot_half, out, n, steps, cap);
     return cudaGetLastError();
 }
 

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kThreadsFor<W>, 1) k_mlp_simt(MlpArgs g) {
                 o.y = sigmoid_f(z1 + bo[1]);
                 o.z = sigmoid_f(z2 + bo[2]);
                 o.w = sigmoid_f(z3 + bo[3]);
-                g.slot_out[slot] = o;
+                static_cast<float4*>(g.slot_out)[slot] = o;
             }
         }
         __syncthreads();

@@ -352,6 +352,12 @@ __device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
     return d;
 }
 
+__device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     uint32_t d;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
@@ -613,13 +619,11 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         uint64_t slot_prev = ~0ull, slot_z = ~0ull;
         uint32_t zr[4] = {0u, 0u, 0u, 0u};
         auto store_head = [&]() {
-            if (slot_z != ~0ull) {
-                float4 o;
-                o.x = softplus_f(__uint_as_float(zr[0]));
-                o.y = sigmoid_f(__uint_as_float(zr[1]));
-                o.z = sigmoid_f(__uint_as_float(zr[2]));
-                o.w = sigmoid_f(__uint_as_float(zr[3]));
-                g.slot_out[slot_z] = o;
+            if (slot_z != ~0ull) {  // 4 x FP16; sigma saturates at the FP16 maximum
+                uint2 o;
+                o.x = pack_f16(fminf(softplus_f(__uint_as_float(zr[0])), 65504.0f), sigmoid_f(__uint_as_float(zr[1])));
+                o.y = pack_f16(sigmoid_f(__uint_as_float(zr[2])), sigmoid_f(__uint_as_float(zr[3])));
+                static_cast<uint2*>(g.slot_out)[slot_z] = o;
             }
             zpend = false;
         };
