@@ -45,24 +45,58 @@ __device__ __forceinline__ float4 load_slot(const void* __restrict__ slot_out, s
     }
 }
 
-// load_slot as a volatile load: issued where it stands, so a thread's loads of a whole
-// crossing are all in flight before the first of them is used.
+// A slot as stored (uint2 = 4 x FP16, or float4), loaded with a volatile load: issued
+// where it stands, so a thread's loads of whole crossings are in flight before the
+// first of them is used; slot_value converts it.
 template <bool HALF>
-__device__ __forceinline__ float4 load_slot_now(const void* __restrict__ slot_out, size_t s) {
+struct RawSlot {
+    uint32_t a, b, c, d;  // HALF uses a, b
+};
+
+template <bool HALF>
+__device__ __forceinline__ RawSlot<HALF> load_slot_now(const void* __restrict__ slot_out, size_t s) {
+    RawSlot<HALF> r{0u, 0u, 0u, 0u};
     if constexpr (HALF) {
-        uint32_t a, b;
         asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];"
-                     : "=r"(a), "=r"(b)
+                     : "=r"(r.a), "=r"(r.b)
                      : "l"(reinterpret_cast<const uint2*>(slot_out) + s));
-        const float2 fa = __half22float2(*reinterpret_cast<const __half2*>(&a));
-        const float2 fb = __half22float2(*reinterpret_cast<const __half2*>(&b));
+    } else {
+        asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r.a), "=r"(r.b), "=r"(r.c), "=r"(r.d)
+                     : "l"(reinterpret_cast<const float4*>(slot_out) + s));
+    }
+    return r;
+}
+
+// Slots s and s + 1 (s even: 16-byte aligned in the FP16 layout) with one 16-byte load.
+__device__ __forceinline__ void load_slot_pair_now(const void* __restrict__ slot_out, size_t s, RawSlot<true>& r0,
+                                                   RawSlot<true>& r1) {
+    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0.a), "=r"(r0.b), "=r"(r1.a), "=r"(r1.b)
+                 : "l"(reinterpret_cast<const uint2*>(slot_out) + s));
+}
+
+// All kSteps slots of crossing k (slots k * kSteps ...): 16-byte loads.
+template <bool HALF, int kSteps>
+__device__ __forceinline__ void load_crossing_now(const void* __restrict__ slot_out, size_t first,
+                                                  RawSlot<HALF> (&v)[kSteps]) {
+    if constexpr (HALF) {
+#pragma unroll
+        for (int j = 0; j < kSteps; j += 2) load_slot_pair_now(slot_out, first + j, v[j], v[j + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kSteps; ++j) v[j] = load_slot_now<HALF>(slot_out, first + j);
+    }
+}
+
+template <bool HALF>
+__device__ __forceinline__ float4 slot_value(const RawSlot<HALF>& r) {
+    if constexpr (HALF) {
+        const float2 fa = __half22float2(*reinterpret_cast<const __half2*>(&r.a));
+        const float2 fb = __half22float2(*reinterpret_cast<const __half2*>(&r.b));
         return make_float4(fa.x, fa.y, fb.x, fb.y);
     } else {
-        float4 v;
-        asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                     : "l"(reinterpret_cast<const float4*>(slot_out) + s));
-        return v;
+        return make_float4(__uint_as_float(r.a), __uint_as_float(r.b), __uint_as_float(r.c), __uint_as_float(r.d));
     }
 }
 
@@ -247,11 +281,15 @@ __global__ void __launch_bounds__(256) k_composite_lane(
         const float2* xr = xing + (size_t)ray * maxc;
         const size_t row = (size_t)ray * cap;
         bool alive = true;
+        // crossing k + 1's slots are loaded while crossing k is composited
+        RawSlot<HALF> vn[kSteps];
+        if (nx > 0) load_crossing_now<HALF, kSteps>(slot_out, row, vn);
         for (int k = 0; k < nx && alive; ++k) {
             const float2 x = __ldg(xr + k);
-            float4 v[kSteps];
+            RawSlot<HALF> v[kSteps];
 #pragma unroll
-            for (int j = 0; j < kSteps; ++j) v[j] = load_slot_now<HALF>(slot_out, row + (size_t)(k * kSteps + j));
+            for (int j = 0; j < kSteps; ++j) v[j] = vn[j];
+            if (k + 1 < nx) load_crossing_now<HALF, kSteps>(slot_out, row + (size_t)((k + 1) * kSteps), vn);
             // same FP32 operations as the sampling step: delta = (t_out - t_in) / steps
             // (exact: a power of two), t_j = t_in + (j + 1/2) delta
             const float delta = __fmul_rn(__fsub_rn(x.y, x.x), 1.0f / kSteps);
@@ -259,12 +297,13 @@ __global__ void __launch_bounds__(256) k_composite_lane(
             for (int j = 0; j < kSteps; ++j) {
                 alive = alive && !(T < t_term);  // stop once T < t_term
                 if (alive) {
+                    const float4 vj = slot_value<HALF>(v[j]);
                     const float t = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
-                    const float e = expf(-__fmul_rn(v[j].x, delta));
+                    const float e = expf(-__fmul_rn(vj.x, delta));
                     const float w = T * (1.0f - e);
-                    cr += w * v[j].y;
-                    cg += w * v[j].z;
-                    cb += w * v[j].w;
+                    cr += w * vj.y;
+                    cg += w * vj.z;
+                    cb += w * vj.w;
                     dd += w * t;
                     T = T * e;
                     ++comp;
