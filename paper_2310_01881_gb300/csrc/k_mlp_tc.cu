@@ -80,7 +80,10 @@ __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / 
 // W / beta_l and its bias as b / a_(l+1), so relu(acc + bias) is already layer l+1's
 // E4M3 input (beta_l >= max|W| / 448 keeps the weights in range, and
 // a_(l+1) >= act_max_(l+1) / 448 the activations); the head weights take a_hidden.
-// Like BF16, every layer after the first starts its accumulator at its bias.
+// Like BF16, every layer after the first starts its accumulator at its bias.  Layer
+// 0's bias B = b / a_1 is folded into input columns 90..92 as three E4M3 terms
+// (hi + mid + lo = B / c, about 2^-12 relative) against a constant input c, a power of
+// two per leaf that keeps the terms in range; enc holds 1 / a_0 and c.
 struct TcLayout {
     int width, hidden, k0, k0p, kh, khead, es;
     size_t w0, wh, wo, sw, bias, enc, stride;
@@ -127,6 +130,13 @@ uint8_t f2e4m3(float x) {
     if (E > 8 || (E == 8 && r > 14.0f)) return sign | 0x7e;
     if (r < 8.0f) return sign | (uint8_t)r;          // subnormal (E == -6)
     return sign | (uint8_t)(((E + 7) << 3) | ((int)r - 8));
+}
+
+float e4m3_to_float(uint8_t v) {  // exact: E4M3 values are dyadic rationals
+    const float sign = (v & 0x80) ? -1.0f : 1.0f;
+    const int e = (v >> 3) & 0xf, m = v & 7;
+    if (e == 0) return sign * std::ldexp((float)m, -9);  // subnormal: m 2^-9
+    return sign * std::ldexp(1.0f + (float)m / 8.0f, e - 7);
 }
 
 uint16_t f2bf(float f) {  // round to nearest even (inputs are finite)
@@ -686,8 +696,10 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 } else {
                     static_assert(K0P == 96, "E4M3 layer-0 input is stored as 16 + 8 columns");
                     float inv;
+                    float cbias = 0.0f;  // static scales: the constant input of layer 0's folded bias
                     if constexpr (ST) {  // the leaf's static encoding scale (in the weight blob)
                         inv = *reinterpret_cast<const float*>(wbuf + lay.enc);
+                        cbias = *reinterpret_cast<const float*>(wbuf + lay.enc + 4);
                         s_a = 1.0f;
                     } else {  // this row's own scale
                         float m = 0.0f;
@@ -699,9 +711,24 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     uint32_t w[24];
 #pragma unroll
                     for (int i = 0; i < 24; ++i) {
+                        // features scaled in pairs; inputs K0 .. K0 + 2 carry the constant of
+                        // the folded bias (static scales), the rest of the padding is zero
                         float e[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) e[u] = (4 * i + u < K0) ? f[(4 * i + u < K0) ? 4 * i + u : 0] * inv : 0.0f;
+                        for (int u = 0; u < 4; u += 2) {
+                            const int f0 = 4 * i + u;
+                            if (ST && f0 + 1 < K0) {
+                                const float2 pr = mul_f32x2(make_float2(f[f0], f[f0 + 1]), make_float2(inv, inv));
+                                e[u] = pr.x;
+                                e[u + 1] = pr.y;
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < 2; ++q) {
+                                    const int fq = f0 + q;
+                                    e[u + q] = fq < K0 ? f[fq < K0 ? fq : 0] * inv : (fq < K0 + 3 ? cbias : 0.0f);
+                                }
+                            }
+                        }
                         w[i] = pack_e4m3x4(e[0], e[1], e[2], e[3]);
                     }
                     tmem_st16(a_row, w);
@@ -795,16 +822,9 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     if constexpr (F8) {
                         if constexpr (ST) {
                             // per-layer scales: the accumulator is already in the next layer's
-                            // units; layer 0 adds its (scaled) bias here, the others start
-                            // from it
-                            if (l == 0) {
-                                const float4 bb = *reinterpret_cast<const float4*>(b + c0);
-                                p01 = make_float2(v[0] + bb.x, v[1] + bb.y);
-                                p23 = make_float2(v[2] + bb.z, v[3] + bb.w);
-                            } else {
-                                p01 = make_float2(v[0], v[1]);
-                                p23 = make_float2(v[2], v[3]);
-                            }
+                            // units, its bias folded in (layer 0) or its starting value
+                            p01 = make_float2(v[0], v[1]);
+                            p23 = make_float2(v[2], v[3]);
                         } else {
                             const float4 bb = *reinterpret_cast<const float4*>(b + c0);
                             const float4 ss = *reinterpret_cast<const float4*>(sw + c0);
@@ -1084,11 +1104,28 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
         w += (size_t)width * kin;
         const float next = alpha * beta;  // scale of this layer's output (1 unless static E4M3)
         for (int n = 0; n < width; ++n) bias[(size_t)l * width + n] = stat ? w[n] / next : w[n];
+        if (stat && l == 0) {
+            // layer 0's bias in the contraction: three E4M3 terms per output channel at
+            // inputs k0 .. k0 + 2, each of those inputs the constant c
+            float bmax = 0.0f;
+            for (int n = 0; n < width; ++n) bmax = std::fmax(bmax, std::fabs(w[n] / next));
+            float c = 1.0f;
+            while (bmax / c > 224.0f && c < 256.0f) c *= 2.0f;
+            reinterpret_cast<float*>(dst + lay.enc)[1] = c;
+            for (int n = 0; n < width; ++n) {
+                float r = w[n] / next / c;
+                for (int q = 0; q < 3; ++q) {
+                    const uint8_t e = f2e4m3(r);
+                    base[cm_offset8(n, k0 + q, K)] = e;
+                    r -= e4m3_to_float(e);
+                }
+            }
+        }
         alpha = next;
         w += width;
         kin = width;
     }
-    if (stat) *reinterpret_cast<float*>(dst + lay.enc) = act_max[0] > 0.0f ? 448.0f / act_max[0] : 1.0f;
+    if (stat) reinterpret_cast<float*>(dst + lay.enc)[0] = act_max[0] > 0.0f ? 448.0f / act_max[0] : 1.0f;
     {  // head: rows 0..3 of a 16 x khead BF16 matrix (its bias stays FP32)
         uint8_t* hb = dst + lay.wo;
         for (int n = 0; n < 4; ++n) {
