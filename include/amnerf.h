@@ -259,7 +259,10 @@ AMNERF_API amnerf_status amnerf_render_debug(amnerf_ctx *ctx, const float *rays_
 
 /* amnerf_render with HOST inputs and outputs (same layouts): copies the rays to
  * library-owned device buffers, renders, copies the pixels back and synchronises.
- * Page-locked host buffers make the copies asynchronous DMA. */
+ * Page-locked host buffers make the copies asynchronous DMA.  Without `stats`, a
+ * batch of at least 2 M rays is rendered in up to 4 chunks whose uploads and
+ * downloads run on a second stream, overlapping the other chunks' rendering; the
+ * pixels are the same as one amnerf_render of the whole batch. */
 AMNERF_API amnerf_status amnerf_render_host(amnerf_ctx *ctx, const float *rays_o_host, const float *rays_d_host,
                                  int64_t n_rays, const amnerf_render_params *params, float *rgb_host,
                                  float *depth_host, float *opacity_host, amnerf_stats *stats);

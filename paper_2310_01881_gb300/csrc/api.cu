@@ -48,6 +48,10 @@ struct amnerf_ctx {
     // host-buffer path
     size_t cap_host_rays = 0;
     float* d_hbuf = nullptr;  // o, d, rgb, depth, opacity
+    // chunked host path: copies on their own stream, ordered by events
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_up[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_done[4] = {nullptr, nullptr, nullptr, nullptr};
     // network kernel schedule (autotuned or set by the caller)
     int max_groups = 1;
     amnerf_tuning tuning{0, AMNERF_SCHED_CONTIGUOUS};
@@ -274,6 +278,14 @@ void amnerf_destroy(amnerf_ctx* ctx) {
     dfree(ctx->d_root);
     for (int i = 0; i < 6; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    for (int i = 0; i < 4; ++i) {
+        if (ctx->ev_up[i]) cudaEventDestroy(ctx->ev_up[i]);
+        if (ctx->ev_done[i]) cudaEventDestroy(ctx->ev_done[i]);
+    }
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
     delete ctx;
 }
 
@@ -623,6 +635,47 @@ amnerf_status amnerf_render_host(amnerf_ctx* ctx, const float* ro, const float* 
     float* ddep = drgb + 3 * ctx->cap_host_rays;
     float* dop = ddep + ctx->cap_host_rays;
     cudaStream_t s = ctx->stream;
+    // Large batches without statistics go in up to 4 chunks of >= 1 M rays: the copy
+    // stream uploads every chunk up front and downloads chunk i once it is rendered,
+    // so the copies overlap the rendering of the other chunks.
+    constexpr size_t kChunkMin = (size_t)1 << 20;
+    const int chunks = stats ? 1 : (int)std::min<size_t>(4, nn / kChunkMin);
+    if (chunks >= 2) {
+        if (!ctx->copy_stream) {
+            CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "copy stream");
+            for (int i = 0; i < 4; ++i) {
+                CK(cudaEventCreateWithFlags(&ctx->ev_up[i], cudaEventDisableTiming), "event");
+                CK(cudaEventCreateWithFlags(&ctx->ev_done[i], cudaEventDisableTiming), "event");
+            }
+        }
+        cudaStream_t cs = ctx->copy_stream;
+        // the buffers are free: the previous call synchronised before returning
+        size_t b[5];
+        for (int i = 0; i <= chunks; ++i) b[i] = nn * (size_t)i / (size_t)chunks;
+        for (int i = 0; i < chunks; ++i) {
+            const size_t m = b[i + 1] - b[i];
+            CK(cudaMemcpyAsync(dro + 3 * b[i], ro + 3 * b[i], m * 12, cudaMemcpyHostToDevice, cs), "ray upload");
+            CK(cudaMemcpyAsync(drd + 3 * b[i], rd + 3 * b[i], m * 12, cudaMemcpyHostToDevice, cs), "ray upload");
+            CK(cudaEventRecord(ctx->ev_up[i], cs), "event");
+        }
+        for (int i = 0; i < chunks; ++i) {
+            const size_t m = b[i + 1] - b[i];
+            CK(cudaStreamWaitEvent(s, ctx->ev_up[i], 0), "event wait");
+            amnerf_status st = render_impl(ctx, dro + 3 * b[i], drd + 3 * b[i], (int64_t)m, p, drgb + 3 * b[i],
+                                           ddep + b[i], dop + b[i], nullptr, nullptr);
+            if (st != AMNERF_OK) {
+                cudaStreamSynchronize(cs);
+                return st;
+            }
+            CK(cudaEventRecord(ctx->ev_done[i], s), "event");
+            CK(cudaStreamWaitEvent(cs, ctx->ev_done[i], 0), "event wait");
+            CK(cudaMemcpyAsync(rgb + 3 * b[i], drgb + 3 * b[i], m * 12, cudaMemcpyDeviceToHost, cs), "pixel download");
+            CK(cudaMemcpyAsync(depth + b[i], ddep + b[i], m * 4, cudaMemcpyDeviceToHost, cs), "pixel download");
+            CK(cudaMemcpyAsync(opacity + b[i], dop + b[i], m * 4, cudaMemcpyDeviceToHost, cs), "pixel download");
+        }
+        CK(cudaStreamSynchronize(cs), "stream sync");  // it waited for the last chunk's render
+        return AMNERF_OK;
+    }
     if (nn) {
         CK(cudaMemcpyAsync(dro, ro, nn * 12, cudaMemcpyHostToDevice, s), "ray upload");
         CK(cudaMemcpyAsync(drd, rd, nn * 12, cudaMemcpyHostToDevice, s), "ray upload");

@@ -219,6 +219,21 @@ def test_host_buffer_entry_point_matches_device(R):
     np.testing.assert_array_equal(h[2], opac)
 
 
+def test_host_buffer_entry_point_in_chunks_matches_device(R):
+    """2.1 M rays: the host path renders in chunks with overlapped copies."""
+    from paper_2310_01881_gb300 import amnerf
+    cfg = S.CONFIGS["c1"]
+    _setup(R, cfg, 0, prec="bf16")
+    o, d = S.view_rays(cfg, 0, 0, 1448, 1448)
+    rgb, depth, opac = [t.cpu().numpy() for t in R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)]
+    h = [torch.empty((len(o), 3)).pin_memory().numpy(), torch.empty(len(o)).pin_memory().numpy(),
+         torch.empty(len(o)).pin_memory().numpy()]
+    amnerf.amnerf_render_host(R.ctx, o, d, *h, steps=cfg.steps, cap=cfg.cap)
+    np.testing.assert_array_equal(h[0], rgb)
+    np.testing.assert_array_equal(h[1], depth)
+    np.testing.assert_array_equal(h[2], opac)
+
+
 def test_invalid_arguments_are_rejected(R):
     from paper_2310_01881_gb300 import amnerf
     cfg = S.CONFIGS["c1"]
