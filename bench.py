@@ -39,9 +39,9 @@ from paper_2310_01881_gb300 import scenes as S  # noqa: E402
 METRIC = "Msamples/s, Mrays/s at 800x800: plain FP32 vs BF16 grouped @ PSNR≥45dB vs FP64"
 # DRAM bytes per launch of the BF16 network kernel on the c2 step, from one ncu capture
 # of a one-view 400x400 case scaled by samples (profiles/dram_c2_400x400x1.md:
-# 108.2 MB x 324.09 M / 10.60 M samples); reported only for that kernel version and
+# 104.0 MB x 324.09 M / 10.60 M samples); reported only for that kernel version and
 # workload.
-NETWORK_TRAFFIC_BF16_C2 = 3.31e9
+NETWORK_TRAFFIC_BF16_C2 = 3.18e9
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 N_SM = 152
 FP32_LANES = 128
