@@ -64,13 +64,18 @@ def lib():
             V, I, L, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
             _lib.or_build_tree.argtypes = [V, I, V, I, D, I, V, V, V, V, V, V]
             _lib.or_traverse.argtypes = [V, V, V, I, V, V, L, I, I, I, V, V, V, V]
-            _lib.or_samples.argtypes = [V, V, L, V, V, V, I, I, I, I, V, V, V]
+            U = ctypes.c_uint64
+            _lib.or_samples.argtypes = [V, V, L, V, V, V, I, I, I, I, U, V, V, V]
             _lib.or_group.argtypes = [V, V, L, I, I, I, V, V, V]
+            _lib.or_splitmix64_mix.argtypes = [U]
+            _lib.or_splitmix64_mix.restype = U
+            _lib.or_jitter_fraction.argtypes = [U, V, V, I, I, I]
+            _lib.or_jitter_fraction.restype = ctypes.c_float
             _lib.or_encode.argtypes = [V, I, I, V]
             _lib.or_encode.restype = None
             _lib.or_mlp_eval.argtypes = [V, I, I, I, I, V, V, L, I, V, V]
             _lib.or_mlp_input_absmax.argtypes = [V, I, I, I, I, V, V, L, V]
-            _lib.or_render.argtypes = [V, V, V, I, V, I, I, I, I, V, V, L, I, I, D, V, I, I,
+            _lib.or_render.argtypes = [V, V, V, I, V, I, I, I, I, V, V, L, I, I, D, V, I, U, I,
                                        V, V, V, V, V, V, V, V, V, V, V, V]
             _lib.or_prop_predict.argtypes = [V, V, V, V, L, V]
             _lib.or_prop_loss_grad.argtypes = [V, V, V, V, V, L, V, V]
@@ -135,14 +140,26 @@ def traverse(tree: Tree, o, d, maxc: int, mode: int = 0, method: int = 0):
     return nx, leaf, tin, tout
 
 
-def samples(o, d, nx, tin, tout, maxc: int, steps: int, cap: int, mode: int = 0):
-    """Slot arrays t, delta (n, cap) and x (n, cap, 3); unused slots are zero."""
+def samples(o, d, nx, tin, tout, maxc: int, steps: int, cap: int, mode: int = 0, jitter: int = 0):
+    """Slot arrays t, delta (n, cap) and x (n, cap, 3); unused slots are zero.
+    jitter: 0 = stratum midpoints, else the seed of the stratified jitter."""
     o = np.ascontiguousarray(o, F32); d = np.ascontiguousarray(d, F32)
     n = len(o)
     t = np.zeros((n, cap), F64); dl = np.zeros((n, cap), F64); x = np.zeros((n, cap, 3), F64)
     lib().or_samples(_p(o), _p(d), n, _p(np.ascontiguousarray(nx, I32)), _p(np.ascontiguousarray(tin, F64)),
-                     _p(np.ascontiguousarray(tout, F64)), maxc, steps, cap, mode, _p(t), _p(dl), _p(x))
+                     _p(np.ascontiguousarray(tout, F64)), maxc, steps, cap, mode, int(jitter), _p(t), _p(dl), _p(x))
     return t, dl, x
+
+
+def splitmix64_mix(z: int) -> int:
+    """The splitmix64 finaliser of the stratified-jitter generator."""
+    return int(lib().or_splitmix64_mix(z & ((1 << 64) - 1)))
+
+
+def jitter_fraction(seed: int, o, d, k: int, steps: int, j: int) -> float:
+    """Fraction u of its stratum at which sample j of crossing k of ray (o, d) sits."""
+    o = np.ascontiguousarray(o, F32); d = np.ascontiguousarray(d, F32)
+    return float(lib().or_jitter_fraction(seed, _p(o), _p(d), k, steps, j))
 
 
 def group(nx, leaf, maxc: int, steps: int, n_leaves: int):
@@ -187,8 +204,9 @@ def mlp_input_absmax(params_leaf, width: int, hidden: int, lx: int, ld: int, x, 
 
 def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, steps: int, cap: int,
            t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), mode: int = 0, threads: int = 1, full: bool = False,
-           mask=None, fallback=None, bins: bool = False):
+           mask=None, fallback=None, bins: bool = False, jitter: int = 0):
     """Full render of every ray; returns a dict of float64 / int32 arrays.
+    jitter: 0 = samples at stratum midpoints, else the seed of the stratified jitter.
     mask/fallback (proposal sampler): per-ray kept-bin masks and fallback flags;
     bins: also return the compositing weight per depth bin (n, 65)."""
     params = np.ascontiguousarray(params, F32)
@@ -211,7 +229,7 @@ def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, 
         res["bins"] = np.zeros((n, 65), F64)
     bgv = np.asarray(bg, F64)
     rc = lib().or_render(_p(tree.box), _p(tree.info), _p(tree.split), tree.n_nodes, _p(params), width, hidden,
-                         lx, ld, _p(o), _p(d), n, steps, cap, float(t_term), _p(bgv), mode, threads,
+                         lx, ld, _p(o), _p(d), n, steps, cap, float(t_term), _p(bgv), mode, int(jitter), threads,
                          _p(res["rgb"]), _p(res["depth"]), _p(res["opacity"]), _p(res["n_gen"]),
                          _p(res["n_eval"]), _p(res["ert_margin"]),
                          _p(so) if so is not None else None, _p(sw) if sw is not None else None,

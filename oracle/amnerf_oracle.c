@@ -24,7 +24,9 @@
  *              KD-tree traversal that records one interval per leaf crossed.
  *   sampling   Sec. 3.5, Algorithm 1 (Sampling) and Fig. "prop": every interval is
  *              normalised and gets the same number of samples, stored per ray at
- *              ray * max_cell_count + j; placed at stratum midpoints.
+ *              ray * max_cell_count + j; placed at stratum midpoints, or (the paper's
+ *              "uniform random" placement) at one uniform point per stratum drawn
+ *              from a counter-based generator keyed by the ray (see or_jitter_u).
  *   grouping   Sec. 3.5 and Fig. "parallel": samples sorted by node id so that each
  *              node's network runs as one batch.
  *   network    Sec. 3.1 (F_Theta(x, d) -> (c, sigma)), Sec. 3.2 and 4.1 (one small
@@ -304,14 +306,58 @@ int or_traverse(const float *box, const int *info, const float *split, int n_nod
 /* Sampling (Sec. 3.5, Algorithm 1 Sampling; Fig. "prop")                   */
 /* ======================================================================== */
 
-/* Sample j of a crossing: delta = (exit - entry) / steps, t_j = entry + (j + 1/2) delta,
- * x_j = o + t_j d per component (multiply, round, add, round). */
-static void or_sample32(float e, float x, int steps, int j, const float o[3], const float d[3],
+/* Stratified jitter (Sec. 3.5: "uniform random ... samples are filled within each
+ * intersection interval"): sample j of crossing k of a ray sits at fraction u of its
+ * stratum, u = (splitmix64 output >> 40) / 2^24 in [0, 1).  splitmix64 (Steele, Lea
+ * and Flood, 2014) finalises z: z ^= z >> 30, z *= 0xbf58476d1ce4e5b9, z ^= z >> 27,
+ * z *= 0x94d049bb133111eb, z ^= z >> 31.  The ray's key folds the bit patterns of its
+ * origin and direction into the seed with three finalisations (so a ray draws the
+ * same points whatever batch it is rendered in); the sample's input is the key plus
+ * the golden gamma 0x9e3779b97f4a7c15 times (k * steps + j + 1).  Seed 0 means
+ * midpoints (u = 1/2). */
+static uint64_t or_mix64(uint64_t z)
+{
+    z ^= z >> 30; z *= 0xbf58476d1ce4e5b9ULL;
+    z ^= z >> 27; z *= 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    return z;
+}
+
+static uint64_t or_ray_key(uint64_t seed, const float o[3], const float d[3])
+{
+    uint32_t b[6];
+    memcpy(b, o, 12);
+    memcpy(b + 3, d, 12);
+    uint64_t k = or_mix64(seed ^ ((uint64_t)b[0] | ((uint64_t)b[1] << 32)));
+    k = or_mix64(k ^ ((uint64_t)b[2] | ((uint64_t)b[3] << 32)));
+    k = or_mix64(k ^ ((uint64_t)b[4] | ((uint64_t)b[5] << 32)));
+    return k;
+}
+
+static float or_jitter_u(uint64_t seed, uint64_t key, int k, int steps, int j)
+{
+    if (seed == 0) return 0.5f;
+    uint64_t z = or_mix64(key + 0x9e3779b97f4a7c15ULL * (uint64_t)(k * steps + j + 1));
+    return (float)(z >> 40) * (1.0f / 16777216.0f);
+}
+
+/* The generator's pieces, for the pins: the finaliser, and sample j's fraction. */
+uint64_t or_splitmix64_mix(uint64_t z) { return or_mix64(z); }
+
+float or_jitter_fraction(uint64_t seed, const float *o, const float *d, int k, int steps, int j)
+{
+    return or_jitter_u(seed, or_ray_key(seed, o, d), k, steps, j);
+}
+
+/* Sample j of a crossing at fraction u of its stratum: delta = (exit - entry) / steps,
+ * t_j = entry + (j + u) delta, x_j = o + t_j d per component (multiply, round, add,
+ * round). */
+static void or_sample32(float e, float x, int steps, int j, float u, const float o[3], const float d[3],
                         float *t, float *dl, float p[3])
 {
     float len = x - e;
     float delta = len / (float)steps;
-    float fj = (float)j + 0.5f;
+    float fj = (float)j + u;
     float off = fj * delta;
     float tj = e + off;
     for (int a = 0; a < 3; a++) {
@@ -321,27 +367,29 @@ static void or_sample32(float e, float x, int steps, int j, const float o[3], co
     *t = tj; *dl = delta;
 }
 
-static void or_sample64(double e, double x, int steps, int j, const double o[3], const double d[3],
+static void or_sample64(double e, double x, int steps, int j, double u, const double o[3], const double d[3],
                         double *t, double *dl, double p[3])
 {
     double delta = (x - e) / (double)steps;
-    double tj = e + ((double)j + 0.5) * delta;
+    double tj = e + ((double)j + u) * delta;
     for (int a = 0; a < 3; a++) p[a] = o[a] + tj * d[a];
     *t = tj; *dl = delta;
 }
 
 /* Samples of every ray in slot layout (slot = ray * cap + k * steps + j). */
 int or_samples(const float *o, const float *d, int64_t n, const int *n_x, const double *tin,
-               const double *tout, int maxc, int steps, int cap, int mode,
+               const double *tout, int maxc, int steps, int cap, int mode, uint64_t jitter,
                double *t_out, double *delta_out, double *x_out)
 {
     for (int64_t r = 0; r < n; r++) {
+        const uint64_t key = or_ray_key(jitter, o + 3 * r, d + 3 * r);
         for (int k = 0; k < n_x[r]; k++) {
             for (int j = 0; j < steps; j++) {
                 int64_t s = r * cap + (int64_t)k * steps + j;
+                const float u = or_jitter_u(jitter, key, k, steps, j);
                 if (mode == 1) {
                     float t, dl, p[3];
-                    or_sample32((float)tin[r * maxc + k], (float)tout[r * maxc + k], steps, j,
+                    or_sample32((float)tin[r * maxc + k], (float)tout[r * maxc + k], steps, j, u,
                                 o + 3 * r, d + 3 * r, &t, &dl, p);
                     t_out[s] = t; delta_out[s] = dl;
                     for (int a = 0; a < 3; a++) x_out[3 * s + a] = p[a];
@@ -349,7 +397,7 @@ int or_samples(const float *o, const float *d, int64_t n, const int *n_x, const 
                     double o64[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
                     double d64[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
                     double t, dl, p[3];
-                    or_sample64(tin[r * maxc + k], tout[r * maxc + k], steps, j, o64, d64, &t, &dl, p);
+                    or_sample64(tin[r * maxc + k], tout[r * maxc + k], steps, j, (double)u, o64, d64, &t, &dl, p);
                     t_out[s] = t; delta_out[s] = dl;
                     for (int a = 0; a < 3; a++) x_out[3 * s + a] = p[a];
                 }
@@ -568,7 +616,7 @@ typedef struct {
     /* rays */
     const float *o, *d; int64_t n;
     /* render params */
-    int steps, cap; double t_term; double bg[3]; int mode;
+    int steps, cap; double t_term; double bg[3]; int mode; uint64_t jitter;
     /* outputs */
     double *rgb, *depth, *opacity; int *n_gen, *n_eval; double *ert_margin;
     double *slot_out; /* (n, cap, 4) sigma rgb; may be NULL */
@@ -679,6 +727,7 @@ static void or_render_ray(const or_job *J, int64_t r)
     int nev = 0, stopped = 0;
     double margin = INFINITY;
     double lt = log(J->t_term);
+    const uint64_t key = or_ray_key(J->jitter, J->o + 3 * r, J->d + 3 * r);
     if (J->slot_w) for (int s = 0; s < J->cap; s++) J->slot_w[r * J->cap + s] = 0.0;
     if (J->mode == 1) {
         float T = 1.0f, C[3] = {0, 0, 0}, D = 0.0f;
@@ -696,7 +745,8 @@ static void or_render_ray(const or_job *J, int64_t r)
                 }
                 if (stopped && !full) break;
                 float t, dl, p[3], o4[4];
-                or_sample32((float)tin[k], (float)tout[k], J->steps, j, of, df, &t, &dl, p);
+                or_sample32((float)tin[k], (float)tout[k], J->steps, j, or_jitter_u(J->jitter, key, k, J->steps, j), of,
+                            df, &t, &dl, p);
                 or_encode32(p, J->lx, din);
                 or_mlp32(P, J->width, J->hidden, k0, din, o4, NULL);
                 if (J->slot_out) for (int i = 0; i < 4; i++) J->slot_out[(r * J->cap + s) * 4 + i] = o4[i];
@@ -735,7 +785,8 @@ static void or_render_ray(const or_job *J, int64_t r)
                 }
                 if (stopped && !full) break;
                 double t, dl, p[3], o4[4];
-                or_sample64(tin[k], tout[k], J->steps, j, o64, d64, &t, &dl, p);
+                or_sample64(tin[k], tout[k], J->steps, j, (double)or_jitter_u(J->jitter, key, k, J->steps, j), o64,
+                            d64, &t, &dl, p);
                 or_encode64(p, J->lx, din);
                 or_mlp64(P, J->width, J->hidden, k0, din, o4, NULL, NULL);
                 if (J->slot_out) for (int i = 0; i < 4; i++) J->slot_out[(r * J->cap + s) * 4 + i] = o4[i];
@@ -771,7 +822,7 @@ static void *or_render_worker(void *arg)
 int or_render(const float *box, const int *info, const float *split, int n_nodes,
               const float *params, int width, int hidden, int lx, int ld,
               const float *o, const float *d, int64_t n,
-              int steps, int cap, double t_term, const double *bg, int mode, int n_threads,
+              int steps, int cap, double t_term, const double *bg, int mode, uint64_t jitter, int n_threads,
               double *rgb, double *depth, double *opacity, int *n_gen, int *n_eval, double *ert_margin,
               double *slot_out, double *slot_w, double *t_final, const uint64_t *mask, const int *fallback,
               double *bins)
@@ -787,6 +838,7 @@ int or_render(const float *box, const int *info, const float *split, int n_nodes
     base.o = o; base.d = d; base.n = n; base.steps = steps; base.cap = cap; base.t_term = t_term;
     for (int c = 0; c < 3; c++) base.bg[c] = bg[c];
     base.mode = mode;
+    base.jitter = jitter;
     base.rgb = rgb; base.depth = depth; base.opacity = opacity; base.n_gen = n_gen; base.n_eval = n_eval;
     base.ert_margin = ert_margin; base.slot_out = slot_out; base.slot_w = slot_w; base.t_final = t_final;
     base.mask = mask; base.fallback = fallback; base.bins = bins;

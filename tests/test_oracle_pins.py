@@ -299,6 +299,64 @@ def test_samples_lie_in_their_leaf_and_fill_the_hit(mode, c1_scene):
         assert dl[r, :n].sum() == pytest.approx(float((tout[r, :nx[r]] - tin[r, :nx[r]]).sum()), rel=1e-6)
 
 
+def test_splitmix64_finaliser_matches_published_sequence():
+    """splitmix64 (Steele, Lea and Flood, 2014) from state 0 -- the state advanced by the
+    golden gamma 0x9e3779b97f4a7c15 before each finalisation -- starts with these
+    outputs in its reference implementation."""
+    gamma = 0x9E3779B97F4A7C15
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    got = [O.splitmix64_mix((k * gamma) & ((1 << 64) - 1)) for k in (1, 2, 3)]
+    assert got == want
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_jittered_samples_stay_in_their_strata_and_are_uniform(mode, c1_scene):
+    """Sec. 3.5 'uniform random' placement: one sample per stratum, uniform within it."""
+    cfg, _, tree = c1_scene
+    o, d = _camera_rays(800, 67)
+    maxc = cfg.cap // cfg.steps
+    nx, leaf, tin, tout = O.traverse(tree, o, d, maxc, mode=mode)
+    t, dl, x = O.samples(o, d, nx, tin, tout, maxc, cfg.steps, cfg.cap, mode=mode, jitter=12345)
+    tm, dlm, _ = O.samples(o, d, nx, tin, tout, maxc, cfg.steps, cfg.cap, mode=mode, jitter=0)
+    us = []
+    for r in range(len(o)):
+        n = nx[r] * cfg.steps
+        e = np.repeat(tin[r, :nx[r]], cfg.steps)
+        j = np.tile(np.arange(cfg.steps), nx[r])
+        np.testing.assert_array_equal(dl[r, :n], dlm[r, :n])          # the strata are unchanged
+        u = (t[r, :n] - e) / dl[r, :n] - j
+        # FP32: t is rounded to its ulp, which is a larger fraction of short strata
+        tol = 1e-9 if mode == 0 else 4.0 * 2.0 ** -24 * np.maximum(np.abs(t[r, :n]), np.abs(e)) / dl[r, :n] + 1e-6
+        assert np.all(u >= -tol) and np.all(u < 1 + tol)
+        # midpoints for seed 0
+        assert np.all(np.abs((tm[r, :n] - e) / dlm[r, :n] - j - 0.5) <= tol)
+        us.append(u)
+    u = np.concatenate(us)
+    assert len(u) > 20000
+    assert abs(u.mean() - 0.5) < 0.01
+    # Kolmogorov-Smirnov distance to U[0, 1)
+    s = np.sort(np.clip(u, 0.0, 1.0))
+    ks = np.max(np.abs(s - (np.arange(len(s)) + 0.5) / len(s)))
+    assert ks < 1.6 / np.sqrt(len(s))
+
+
+def test_jitter_is_keyed_by_the_ray_not_its_batch_position(c1_scene):
+    cfg, _, tree = c1_scene
+    o, d = _camera_rays(64, 71)
+    maxc = cfg.cap // cfg.steps
+    nx, leaf, tin, tout = O.traverse(tree, o, d, maxc, mode=1)
+    t, _, _ = O.samples(o, d, nx, tin, tout, maxc, cfg.steps, cfg.cap, mode=1, jitter=99)
+    p = np.arange(len(o))[::-1]
+    tr, _, _ = O.samples(o[p], d[p], nx[p], tin[p], tout[p], maxc, cfg.steps, cfg.cap, mode=1, jitter=99)
+    np.testing.assert_array_equal(tr, t[p])
+    # different seeds move the samples
+    t2, _, _ = O.samples(o, d, nx, tin, tout, maxc, cfg.steps, cfg.cap, mode=1, jitter=100)
+    gen = np.arange(cfg.cap)[None, :] < (nx * cfg.steps)[:, None]
+    assert np.mean(t2[gen] != t[gen]) > 0.99
+    assert O.jitter_fraction(99, o[3], d[3], 0, cfg.steps, 0) == pytest.approx(
+        float((t[3, 0] - tin[3, 0]) / ((tout[3, 0] - tin[3, 0]) / cfg.steps)), abs=2e-5)
+
+
 # ----------------------------------------------------------------------------------
 # grouping (Sec. 3.5)
 # ----------------------------------------------------------------------------------
@@ -445,7 +503,10 @@ def _constant_params(n_leaves, width, hidden, lx, ld, sigma, rgb):
     return P.reshape(-1)
 
 
-def test_constant_density_closed_form(c1_scene):
+@pytest.mark.parametrize("jitter", [0, 4242])
+def test_constant_density_closed_form(jitter, c1_scene):
+    """T = exp(-sigma L) for a constant density, with samples at midpoints or jittered
+    inside their strata (the strata widths, hence the quadrature, are the same)."""
     cfg, _, tree = c1_scene
     sigma, rgb = 0.8, (0.2, 0.5, 0.7)
     P = _constant_params(tree.n_leaves, cfg.width, cfg.hidden, cfg.lx, cfg.ld, sigma, rgb)
@@ -457,7 +518,7 @@ def test_constant_density_closed_form(c1_scene):
     L = np.array([2.0, 2.0, 2 * s3, 0.0])
     bg = (0.1, 0.0, 0.3)
     res = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, 512, t_term=0.0,
-                   bg=bg, mode=0)
+                   bg=bg, mode=0, jitter=jitter)
     Tf = np.exp(-s_eff * L)
     np.testing.assert_allclose(res["opacity"], 1 - Tf, atol=2e-7)
     for c in range(3):
