@@ -138,7 +138,8 @@ def workload_name(cfg, args) -> str:
     return (f"{cfg.name}: {args.px or cfg.px_w}x{args.px or cfg.px_h} x {args.views or cfg.views} views per GPU, "
             f"{cfg.G}^3 guidance grid, depth<={cfg.max_depth}"
             + (f" (mass<=1/{round(1 / cfg.leaf_mass_frac)})" if cfg.leaf_mass_frac > 0 else "")
-            + f", {cfg.hidden}x{cfg.width} MLP per leaf, {cfg.steps} samples/crossing, cap {cfg.cap}")
+            + f", {cfg.hidden}x{cfg.width} MLP per leaf, {cfg.steps} samples/crossing, cap {cfg.cap}"
+            + (f", stratified jitter (seed {args.jitter})" if getattr(args, "jitter", 0) else ""))
 
 
 def barrier():
@@ -227,8 +228,8 @@ def run_ours(args):
                 continue
             raise
         for _ in range(args.warmup):
-            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out)
-        _, _, _, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out)
+            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter)
+        _, _, _, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter)
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -236,7 +237,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             e0.record(stream)
             for _ in range(args.steps):
-                R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out)
+                R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter)
             e1.record(stream)
             torch.cuda.synchronize()
         barrier()
@@ -246,7 +247,7 @@ def run_ours(args):
         amnerf.amnerf_set_timing(R.ctx, True)
         stage = np.zeros(4)
         for _ in range(args.steps):
-            *_, s2 = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out)
+            *_, s2 = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter)
             stage += np.array(s2["ms"])
         amnerf.amnerf_set_timing(R.ctx, False)
         stage /= args.steps
@@ -270,11 +271,13 @@ def run_ours(args):
             torch.empty(n, dtype=torch.float32).pin_memory().numpy(),
             torch.empty(n, dtype=torch.float32).pin_memory().numpy()]
     for _ in range(max(1, args.warmup)):
-        amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term)
+        amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term,
+                                  jitter=args.jitter)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term)
+        amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term,
+                                  jitter=args.jitter)
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
     barrier()
 
@@ -292,7 +295,7 @@ def run_ours(args):
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     ref = O.render(tree, P_or, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps, cfg.cap,
-                   cfg.t_term, mode=0, threads=cores)
+                   cfg.t_term, mode=0, threads=cores, jitter=args.jitter)
     cpu_s = time.perf_counter() - t0
     cpu_samples = int(ref["n_gen"].sum())
     acc = {}
@@ -627,7 +630,7 @@ def run_reference(args):
         idx = S.ray_subset(len(o_np), per_step, 100 + i)
         t0 = time.perf_counter()
         ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps, cfg.cap,
-                       cfg.t_term, mode=0, threads=cores)
+                       cfg.t_term, mode=0, threads=cores, jitter=args.jitter)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -663,6 +666,8 @@ def main():
     ap.add_argument("--density-scale", type=float, default=1.0, help="c5: factor on every density of the scene")
     ap.add_argument("--leaf-net", default="", help="c5: leaf network shape HxW (default: the config's 2x32)")
     ap.add_argument("--px", type=int, default=None, help="square image size (default: the config's)")
+    ap.add_argument("--jitter", type=int, default=0,
+                    help="sample placement: 0 = stratum midpoints, else the stratified jitter's seed (c1/c2)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

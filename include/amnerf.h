@@ -115,6 +115,15 @@ typedef struct {
     int use_proposal;
     float coverage;   /* e.g. 0.99 */
     int max_bins;     /* in [1, 64], e.g. 16 */
+    /* Sample placement (Sec. 3.5: "uniform random ... samples are filled within each
+     * intersection interval"): 0 = the midpoint of each of the steps_per_leaf equal
+     * strata of a crossing; otherwise the seed of a stratified jitter, one uniform
+     * point per stratum, t_j = t_in + (j + u_j) delta.  u_j = (splitmix64 finaliser
+     * of key + 0x9e3779b97f4a7c15 * (k * steps_per_leaf + j + 1)) >> 40, over 2^24,
+     * for sample j of crossing k; the ray's key folds the bit patterns of (o.x, o.y),
+     * (o.z, d.x) and (d.y, d.z) into the seed with three finalisations, so a ray draws
+     * the same points in any batch.  The quadrature widths are the strata either way. */
+    uint64_t jitter_seed;
 } amnerf_render_params;
 
 /* Schedule of the network step's tiles over the persistent workers (warpgroups). */

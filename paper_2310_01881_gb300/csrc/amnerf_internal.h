@@ -24,6 +24,32 @@ constexpr int kMaxLeaves = 4096; // 2^12 leaves at depth 12
 constexpr int kMaxDepth = 12;
 constexpr int kStackDepth = 16;  // traversal stack (depth + 1 entries suffice)
 
+#ifdef __CUDACC__
+// ---- stratified jitter of the sample positions (Sec. 3.5, "uniform random" samples) --
+// u = (splitmix64 finaliser of key + 0x9e3779b97f4a7c15 (k steps + j + 1)) >> 40, over
+// 2^24, for sample j of crossing k; the ray's key folds the bit patterns of (o.x, o.y),
+// (o.z, d.x), (d.y, d.z) into the seed with three finalisations.  Seed 0: u = 1/2.
+// The finaliser is splitmix64's (Steele, Lea and Flood, 2014).
+__device__ __forceinline__ uint64_t jit_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t jit_ray_key(uint64_t seed, const float o[3], const float d[3]) {
+    uint64_t k = jit_mix64(seed ^ ((uint64_t)__float_as_uint(o[0]) | ((uint64_t)__float_as_uint(o[1]) << 32)));
+    k = jit_mix64(k ^ ((uint64_t)__float_as_uint(o[2]) | ((uint64_t)__float_as_uint(d[0]) << 32)));
+    return jit_mix64(k ^ ((uint64_t)__float_as_uint(d[1]) | ((uint64_t)__float_as_uint(d[2]) << 32)));
+}
+
+// Fraction of its stratum at which sample j of crossing k sits (exact in FP32).
+__device__ __forceinline__ float jit_fraction(uint64_t seed, uint64_t key, int k, int steps, int j) {
+    if (seed == 0) return 0.5f;
+    const uint64_t z = jit_mix64(key + 0x9e3779b97f4a7c15ull * (uint64_t)(k * steps + j + 1));
+    return (float)(uint32_t)(z >> 40) * (1.0f / 16777216.0f);
+}
+#endif
+
 // Error word values written by kernels (first error wins).
 constexpr int kDevErrTimeout = 1;
 constexpr int kDevErrStack = 2;
@@ -73,6 +99,7 @@ struct MlpArgs {
     int* err;
     float* amax;            // FP32 path, calibration: per leaf x hidden layer, max |input of layer l| (or NULL)
     int act_static;         // E4M3 path: static per-leaf, per-layer activation scales folded into the blob
+    uint64_t jitter;        // sample placement: 0 = stratum midpoints, else the stratified jitter's seed
 };
 cudaError_t launch_mlp_simt(cudaStream_t s, const MlpArgs& a, int grid);
 cudaError_t launch_mlp_tc(cudaStream_t s, const MlpArgs& a, int grid, int prec);
@@ -90,9 +117,12 @@ size_t simt_leaf_stride_floats(int width, int hidden, int k0);
 
 // K-d: per-ray compositing.
 // slot_half: slot_out holds 4 x FP16 per sample (sigma, r, g, b), else float4.
+// jitter != 0: samples at the stratified jitter of that seed (ro, rd: the rays, for
+// their keys); 0: stratum midpoints (ro, rd unused).
 cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* xing, const void* slot_out,
                              int slot_half, uint32_t n, int steps, int maxc, int cap, float t_term, float bg0,
                              float bg1, float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
+                             uint64_t jitter, const float* ro, const float* rd,
                              const float2* root = nullptr, float* bins = nullptr);
 // The generated slots (j < n_x[r] * steps) of 4 x FP16 per-sample outputs as float4.
 cudaError_t launch_slots_to_f32(cudaStream_t s, const uint8_t* n_x, const void* slot_half, float4* out, uint32_t n,

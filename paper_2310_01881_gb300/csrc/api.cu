@@ -472,6 +472,7 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         a.err = ctx->d_err;
         a.amax = ctx->calibrating ? ctx->d_amax : nullptr;
         a.act_static = ctx->act_static ? 1 : 0;
+        a.jitter = p->jitter_seed;
         a.tile_counter = reinterpret_cast<uint32_t*>(ctx->d_stats + 6);
         a.t_begin = 0;
         a.t_end = 0xffffffffu;
@@ -503,7 +504,8 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
     }
     if (ctx->timing) cudaEventRecord(ctx->ev[3], s);
     CK(launch_composite(s, ctx->d_nx, ctx->d_xing, ctx->d_slot, ctx->desc.prec != AMNERF_FP32, nn, steps, maxc, cap,
-                        p->t_term, p->bg[0], p->bg[1], p->bg[2], rgb, depth, opacity, ctx->d_stats, root_out, bins_out),
+                        p->t_term, p->bg[0], p->bg[1], p->bg[2], rgb, depth, opacity, ctx->d_stats, p->jitter_seed,
+                        ro, rd, root_out, bins_out),
        "composite launch");
     if (ctx->timing) cudaEventRecord(ctx->ev[4], s);
 

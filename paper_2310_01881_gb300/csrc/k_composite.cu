@@ -15,7 +15,8 @@
 // dropped (a prefix, since the product only decreases), and the warp stops at the
 // first pass that terminates.
 // The sample position t and width delta are rebuilt from the crossing list in the
-// same FP32 operation order as the traversal/sampling step.  Optionally (training
+// same FP32 operation order as the traversal/sampling step (t at the stratum
+// midpoint, or at the stratified jitter's fraction of it: jit_fraction).  Optionally (training
 // targets of the proposal sampler) every composited weight is also added to the
 // depth bin of its sample, and the residual transmittance is stored as bin 64.
 #include <cuda_fp16.h>
@@ -101,10 +102,11 @@ __device__ __forceinline__ float4 slot_value(const RawSlot<HALF>& r) {
 }
 
 // One ray by one warp, SPL consecutive slots per lane (32 SPL slots per pass).
+// Samples sit at fraction jit_fraction(jitter, key, k, steps, j) of their strata.
 template <int SPL, bool HALF>
 __device__ __forceinline__ void composite_ray(const float2* __restrict__ xing, const void* __restrict__ slot_out,
                                               int ns, int steps, int lg_steps, float inv_steps, size_t xbase,
-                                              size_t sbase,
+                                              size_t sbase, uint64_t jitter, uint64_t key,
                                               float t_term, int lane, float r0, float bw, float* sbins, RayAcc& A) {
     for (int s0 = 0; s0 < ns; s0 += 32 * SPL) {
         float4 v[SPL];
@@ -126,7 +128,8 @@ __device__ __forceinline__ void composite_ray(const float2* __restrict__ xing, c
                 const int j = s & (steps - 1);
                 const float2 x = __ldg(xing + xbase + k);
                 const float delta = __fmul_rn(__fsub_rn(x.y, x.x), inv_steps);
-                t[i] = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
+                const float u = jitter ? jit_fraction(jitter, key, k, steps, j) : 0.5f;
+                t[i] = __fadd_rn(x.x, __fmul_rn(__fadd_rn((float)j, u), delta));
                 e[i] = expf(-__fmul_rn(v[i].x, delta));
             }
         }
@@ -187,7 +190,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
     const uint8_t* __restrict__ n_x, const float2* __restrict__ xing, const void* __restrict__ slot_out,
     uint32_t n, int steps, int maxc, int cap, float t_term, float bg0, float bg1, float bg2,
     float* __restrict__ rgb, float* __restrict__ depth, float* __restrict__ opacity,
-    unsigned long long* __restrict__ n_comp, const float2* __restrict__ root, float* __restrict__ bins) {
+    unsigned long long* __restrict__ n_comp, uint64_t jitter, const float* __restrict__ ro,
+    const float* __restrict__ rd, const float2* __restrict__ root, float* __restrict__ bins) {
     __shared__ uint32_t s_comp[kWarpsPerBlock];
     __shared__ float s_bins[kWarpsPerBlock][65];
     const int lane = threadIdx.x & 31;
@@ -217,11 +221,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
         const size_t sbase = (size_t)ray * cap;
         RayAcc A{1.0f, 0.f, 0.f, 0.f, 0.f, 0u};
         float* sb = bins ? s_bins[wib] : nullptr;
+        uint64_t key = 0;
+        if (jitter) {  // the ray's jitter key (the same loads in every lane)
+            float o[3], d[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o[a] = __ldg(ro + 3 * (size_t)ray + a);
+                d[a] = __ldg(rd + 3 * (size_t)ray + a);
+            }
+            key = jit_ray_key(jitter, o, d);
+        }
         // short rays: one slot per lane; longer ones: two (twice the bytes in flight)
         if (ns <= 32)
-            composite_ray<1, HALF>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
+            composite_ray<1, HALF>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, jitter, key, t_term, lane,
+                                   r0, bw, sb, A);
         else
-            composite_ray<2, HALF>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, t_term, lane, r0, bw, sb, A);
+            composite_ray<2, HALF>(xing, slot_out, ns, steps, lg, inv_steps, xbase, sbase, jitter, key, t_term, lane,
+                                   r0, bw, sb, A);
         float T = A.T, cr = A.cr, cg = A.cg, cb = A.cb, dd = A.dd;
         composited += A.composited;
         // warp sums of (cr, cg, cb, dd) in 6 shuffles: each exchange halves the values a
@@ -267,17 +283,28 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
 // slots are one aligned 128-byte row piece (64 bytes as FP16), all loaded before the
 // crossing is composited, so every thread has a whole line in flight; the warp runs
 // until its last ray ends or terminates.
-template <bool HALF>
+template <bool HALF, bool JIT>
 __global__ void __launch_bounds__(256) k_composite_lane(
     const uint8_t* __restrict__ n_x, const float2* __restrict__ xing, const void* __restrict__ slot_out, uint32_t n,
     int maxc, int cap, float t_term, float bg0, float bg1, float bg2, float* __restrict__ rgb,
-    float* __restrict__ depth, float* __restrict__ opacity, unsigned long long* __restrict__ n_comp) {
+    float* __restrict__ depth, float* __restrict__ opacity, unsigned long long* __restrict__ n_comp,
+    uint64_t jitter, const float* __restrict__ ro, const float* __restrict__ rd) {
     constexpr int kSteps = 8;
     const uint32_t ray = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t comp = 0;
     if (ray < n) {
         float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
         const int nx = (int)__ldg(n_x + ray);
+        uint64_t key = 0;
+        if constexpr (JIT) {  // the ray's jitter key
+            float o[3], d[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o[a] = __ldg(ro + 3 * (size_t)ray + a);
+                d[a] = __ldg(rd + 3 * (size_t)ray + a);
+            }
+            key = jit_ray_key(jitter, o, d);
+        }
         const float2* xr = xing + (size_t)ray * maxc;
         const size_t row = (size_t)ray * cap;
         bool alive = true;
@@ -298,7 +325,8 @@ __global__ void __launch_bounds__(256) k_composite_lane(
                 alive = alive && !(T < t_term);  // stop once T < t_term
                 if (alive) {
                     const float4 vj = slot_value<HALF>(v[j]);
-                    const float t = __fadd_rn(x.x, __fmul_rn((float)j + 0.5f, delta));
+                    const float u = JIT ? jit_fraction(jitter, key, k, kSteps, j) : 0.5f;
+                    const float t = __fadd_rn(x.x, __fmul_rn(__fadd_rn((float)j, u), delta));
                     const float e = expf(-__fmul_rn(vj.x, delta));
                     const float w = T * (1.0f - e);
                     cr += w * vj.y;
@@ -337,17 +365,22 @@ __global__ void k_slots_to_f32(const uint8_t* __restrict__ n_x, const void* __re
 cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* xing, const void* slot_out,
                              int slot_half, uint32_t n, int steps, int maxc, int cap, float t_term, float bg0,
                              float bg1, float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
-                             const float2* root, float* bins) {
+                             uint64_t jitter, const float* ro, const float* rd, const float2* root, float* bins) {
     if (n == 0) return cudaSuccess;
     if (!bins && steps == 8) {  // one thread per ray
         auto* stc = reinterpret_cast<unsigned long long*>(stats + 2);
         const unsigned lb = (n + 255) / 256;
-        if (slot_half)
-            k_composite_lane<true><<<lb, 256, 0, s>>>(n_x, xing, slot_out, n, maxc, cap, t_term, bg0, bg1, bg2, rgb,
-                                                      depth, opacity, stc);
-        else
-            k_composite_lane<false><<<lb, 256, 0, s>>>(n_x, xing, slot_out, n, maxc, cap, t_term, bg0, bg1, bg2, rgb,
-                                                       depth, opacity, stc);
+#define AMNERF_LANE(H, J)                                                                                        \
+    k_composite_lane<H, J><<<lb, 256, 0, s>>>(n_x, xing, slot_out, n, maxc, cap, t_term, bg0, bg1, bg2, rgb, depth, \
+                                              opacity, stc, jitter, ro, rd)
+        if (slot_half) {
+            if (jitter) AMNERF_LANE(true, true);
+            else AMNERF_LANE(true, false);
+        } else {
+            if (jitter) AMNERF_LANE(false, true);
+            else AMNERF_LANE(false, false);
+        }
+#undef AMNERF_LANE
         return cudaGetLastError();
     }
     unsigned blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
@@ -369,10 +402,12 @@ cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* x
     auto* st = reinterpret_cast<unsigned long long*>(stats + 2);
     if (slot_half)
         k_composite<true><<<blocks, kWarpsPerBlock * 32, 0, s>>>(n_x, xing, slot_out, n, steps, maxc, cap, t_term, bg0,
-                                                                 bg1, bg2, rgb, depth, opacity, st, root, bins);
+                                                                 bg1, bg2, rgb, depth, opacity, st, jitter, ro, rd,
+                                                                 root, bins);
     else
         k_composite<false><<<blocks, kWarpsPerBlock * 32, 0, s>>>(n_x, xing, slot_out, n, steps, maxc, cap, t_term,
-                                                                  bg0, bg1, bg2, rgb, depth, opacity, st, root, bins);
+                                                                  bg0, bg1, bg2, rgb, depth, opacity, st, jitter, ro,
+                                                                  rd, root, bins);
     return cudaGetLastError();
 }
 

@@ -171,13 +171,17 @@ __global__ void __launch_bounds__(kThreadsFor<W>, 1) k_mlp_simt(MlpArgs g) {
                 const float2 xi = __ldg(g.xing + id);
                 // steps is a power of two: the product by its reciprocal is the exact quotient
                 const float delta = __fmul_rn(__fsub_rn(xi.y, xi.x), __frcp_rn((float)g.steps));
-                const float tj = __fadd_rn(xi.x, __fmul_rn((float)j + 0.5f, delta));
+                float o[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const float o = __ldg(g.ro + 3 * (size_t)ray + a);
+                    o[a] = __ldg(g.ro + 3 * (size_t)ray + a);
                     d[a] = __ldg(g.rd + 3 * (size_t)ray + a);
-                    x[a] = __fadd_rn(o, __fmul_rn(tj, d[a]));
                 }
+                // sample j at fraction u of its stratum (midpoint, or the stratified jitter)
+                const float u = g.jitter ? jit_fraction(g.jitter, jit_ray_key(g.jitter, o, d), (int)k, g.steps, j) : 0.5f;
+                const float tj = __fadd_rn(xi.x, __fmul_rn(__fadd_rn((float)j, u), delta));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(tj, d[a]));
                 slot = (uint64_t)ray * (uint64_t)g.cap + (uint64_t)(k * (uint32_t)g.steps + (uint32_t)j);
             }
             encode_simt(x, g.lx, sA, 0, row);

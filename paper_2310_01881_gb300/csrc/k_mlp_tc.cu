@@ -533,7 +533,9 @@ constexpr uint32_t kHeadCol = 112;
 template <int W>
 constexpr int kHiddenFor = W == 64 ? 4 : 2;
 
-template <int W, bool F8, bool ST, int HC>
+// JIT: samples at the stratified jitter's fractions of their strata (g.jitter != 0), else
+// at the midpoints.
+template <int W, bool F8, bool ST, int HC, bool JIT>
 __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n_groups, uint32_t tmem_cols) {
     const int hidden = HC > 0 ? HC : g.hidden;  // hidden layers (a compile-time constant when HC > 0)
     constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
@@ -674,7 +676,8 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 const uint32_t k = id - ray * (uint32_t)g.maxc;
                 // steps is a power of two: the product by its reciprocal is the exact quotient
                 const float delta = __fmul_rn(__fsub_rn(xi.y, xi.x), __frcp_rn((float)g.steps));
-                const float tj = __fadd_rn(xi.x, __fmul_rn((float)j + 0.5f, delta));
+                const float u = JIT ? jit_fraction(g.jitter, jit_ray_key(g.jitter, ro, rd), (int)k, g.steps, j) : 0.5f;
+                const float tj = __fadd_rn(xi.x, __fmul_rn(__fadd_rn((float)j, u), delta));
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     d[a] = rd[a];
@@ -1011,8 +1014,14 @@ cudaError_t prepare_w(int hidden, int* max_groups) {
     if (e != cudaSuccess) return e;
     *max_groups = max_groups_for<W, F8>(hidden, max_smem);
     if (*max_groups < 1) return cudaErrorInvalidConfiguration;
-    const void* fns[4] = {(const void*)k_mlp_tc<W, F8, false, 0>, (const void*)k_mlp_tc<W, F8, false, kHiddenFor<W>>,
-                          (const void*)k_mlp_tc<W, F8, F8, 0>, (const void*)k_mlp_tc<W, F8, F8, kHiddenFor<W>>};
+    const void* fns[8] = {(const void*)k_mlp_tc<W, F8, false, 0, false>,
+                          (const void*)k_mlp_tc<W, F8, false, kHiddenFor<W>, false>,
+                          (const void*)k_mlp_tc<W, F8, F8, 0, false>,
+                          (const void*)k_mlp_tc<W, F8, F8, kHiddenFor<W>, false>,
+                          (const void*)k_mlp_tc<W, F8, false, 0, true>,
+                          (const void*)k_mlp_tc<W, F8, false, kHiddenFor<W>, true>,
+                          (const void*)k_mlp_tc<W, F8, F8, 0, true>,
+                          (const void*)k_mlp_tc<W, F8, F8, kHiddenFor<W>, true>};
     for (const void* f : fns) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
@@ -1035,13 +1044,16 @@ cudaError_t launch_w(cudaStream_t s, const MlpArgs& a, int grid) {
     size_t smem = lay.stride * groups + sizeof(TcShared) + 64;
     if (smem < (size_t)max_smem / 2 + 1024) smem = (size_t)max_smem / 2 + 1024;
     const bool hc = a.hidden == kHiddenFor<W>;
-    if (F8 && a.act_static) {
-        if (hc) k_mlp_tc<W, F8, F8, kHiddenFor<W>><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
-        else k_mlp_tc<W, F8, F8, 0><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
+    const bool st = F8 && a.act_static;
+#define AMNERF_TC(ST_, HC_, J_) k_mlp_tc<W, F8, ST_, HC_, J_><<<grid, 128 * groups, smem, s>>>(a, groups, cols)
+    if (a.jitter) {
+        if (st) { if (hc) AMNERF_TC(F8, kHiddenFor<W>, true); else AMNERF_TC(F8, 0, true); }
+        else { if (hc) AMNERF_TC(false, kHiddenFor<W>, true); else AMNERF_TC(false, 0, true); }
     } else {
-        if (hc) k_mlp_tc<W, F8, false, kHiddenFor<W>><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
-        else k_mlp_tc<W, F8, false, 0><<<grid, 128 * groups, smem, s>>>(a, groups, cols);
+        if (st) { if (hc) AMNERF_TC(F8, kHiddenFor<W>, false); else AMNERF_TC(F8, 0, false); }
+        else { if (hc) AMNERF_TC(false, kHiddenFor<W>, false); else AMNERF_TC(false, 0, false); }
     }
+#undef AMNERF_TC
     return cudaGetLastError();
 }
 

@@ -206,6 +206,51 @@ def test_c2_scale_tree_and_sampled_pixels(R):
     assert st["samples_generated"] >= int(nx.sum()) * cfg.steps
 
 
+# ---- stratified jitter of the sample positions (Sec. 3.5 "uniform random" samples) ----
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_c1_fp32_jittered_pixels_match_fp32_oracle(R, seed):
+    cfg = S.CONFIGS["c1"]
+    _, tree, P = _setup(R, cfg, seed)
+    o, d = _rays(cfg, seed)
+    jit = 1000 + seed
+    rgb, depth, opac, dbg, st = R.render_debug(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap, jitter=jit)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1, threads=8,
+                   full=True, jitter=jit)
+    _check_pixels(rgb, depth, opac, ref)
+    gen = np.arange(cfg.cap)[None, :] < ref["n_gen"][:, None]
+    so = dbg["slot_out"][gen].astype(np.float64)
+    ro = ref["slot_out"][gen]
+    assert np.max(np.abs(so[:, 1:] - ro[:, 1:])) <= 2e-6
+    assert np.max(np.abs(so[:, 0] - ro[:, 0]) / np.maximum(1.0, ro[:, 0])) <= 2e-6
+    # the jitter moved the samples: the midpoint render differs
+    mid = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1, threads=8,
+                   full=True)
+    assert np.mean(np.abs(mid["slot_out"][gen][:, 0] - ro[:, 0]) > 1e-6) > 0.5
+
+
+def test_c1_bf16_jittered_against_fp64_oracle(R):
+    cfg = S.CONFIGS["c1"]
+    _, tree, P = _setup(R, cfg, 1, prec="bf16")
+    o, d = _rays(cfg, 1)
+    rgb = R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap, jitter=77)[0].cpu().numpy()
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=0, threads=8,
+                   jitter=77)
+    assert _psnr(rgb, ref["rgb"]) >= 45.0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_jitter_is_keyed_by_the_ray_not_its_batch_position(R, prec):
+    cfg = S.CONFIGS["c1"]
+    _setup(R, cfg, 2, prec=prec)
+    o, d = _rays(cfg, 2)
+    p = np.random.default_rng(5).permutation(len(o))
+    a = [t.cpu().numpy() for t in R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap, jitter=31)]
+    b = [t.cpu().numpy() for t in R.render(_dev(o[p]), _dev(d[p]), steps=cfg.steps, cap=cfg.cap, jitter=31)]
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x[p], y)
+
+
 def test_host_buffer_entry_point_matches_device(R):
     from paper_2310_01881_gb300 import amnerf
     cfg = S.CONFIGS["c1"]
