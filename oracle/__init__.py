@@ -75,8 +75,9 @@ def lib():
             _lib.or_encode.restype = None
             _lib.or_mlp_eval.argtypes = [V, I, I, I, I, V, V, L, I, V, V]
             _lib.or_mlp_input_absmax.argtypes = [V, I, I, I, I, V, V, L, V]
-            _lib.or_render.argtypes = [V, V, V, I, V, I, I, I, I, V, V, L, I, I, D, V, I, U, I,
+            _lib.or_render.argtypes = [V, V, V, I, V, I, I, I, I, V, V, L, I, I, D, V, I, U, V, I, V, D, I,
                                        V, V, V, V, V, V, V, V, V, V, V, V]
+            _lib.or_traverse_skip.argtypes = [V, V, V, I, V, V, L, I, I, I, I, U, V, I, V, D, V, V, V, V]
             _lib.or_prop_predict.argtypes = [V, V, V, V, L, V]
             _lib.or_prop_loss_grad.argtypes = [V, V, V, V, V, L, V, V]
             _lib.or_prop_adam.argtypes = [V, V, V, V, I, I, D, D, D, D]
@@ -127,12 +128,28 @@ def make_tree(box, info, split) -> Tree:
     return Tree(box, np.zeros((n, 6), I32), info, split, np.zeros(n, F64), int((info[:, 0] < 0).sum()))
 
 
-def traverse(tree: Tree, o, d, maxc: int, mode: int = 0, method: int = 0):
-    """Per ray: crossing count, leaf ids, entries, exits (ray-major, stride maxc)."""
+BBOX = (-1.0, -1.0, -1.0, 1.0, 1.0, 1.0)
+
+
+def traverse(tree: Tree, o, d, maxc: int, mode: int = 0, method: int = 0, skip=None):
+    """Per ray: crossing count, leaf ids, entries, exits (ray-major, stride maxc).
+    skip = (grid, threshold, steps, jitter): empty-space skipping -- a crossing is kept
+    only when one of its samples (placed as its index among the kept crossings) lies
+    in a grid cell of density > threshold."""
     o = np.ascontiguousarray(o, F32); d = np.ascontiguousarray(d, F32)
     n = len(o)
     nx = np.zeros(n, I32); leaf = np.full((n, maxc), -1, I32)
     tin = np.zeros((n, maxc), F64); tout = np.zeros((n, maxc), F64)
+    if skip is not None:
+        grid, thr, steps, jitter = skip
+        grid = np.ascontiguousarray(grid, F32)
+        bb = np.asarray(BBOX, F64)
+        rc = lib().or_traverse_skip(_p(tree.box), _p(tree.info), _p(tree.split), tree.n_nodes, _p(o), _p(d), n,
+                                    maxc, mode, method, steps, int(jitter), _p(grid), grid.shape[0], _p(bb),
+                                    float(thr), _p(nx), _p(leaf), _p(tin), _p(tout))
+        if rc != 0:
+            raise RuntimeError("oracle traversal failed")
+        return nx, leaf, tin, tout
     rc = lib().or_traverse(_p(tree.box), _p(tree.info), _p(tree.split), tree.n_nodes, _p(o), _p(d), n,
                            maxc, mode, method, _p(nx), _p(leaf), _p(tin), _p(tout))
     if rc != 0:
@@ -204,9 +221,10 @@ def mlp_input_absmax(params_leaf, width: int, hidden: int, lx: int, ld: int, x, 
 
 def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, steps: int, cap: int,
            t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), mode: int = 0, threads: int = 1, full: bool = False,
-           mask=None, fallback=None, bins: bool = False, jitter: int = 0):
+           mask=None, fallback=None, bins: bool = False, jitter: int = 0, skip=None):
     """Full render of every ray; returns a dict of float64 / int32 arrays.
     jitter: 0 = samples at stratum midpoints, else the seed of the stratified jitter.
+    skip = (grid, threshold): empty-space skipping over the guidance grid (see traverse).
     mask/fallback (proposal sampler): per-ray kept-bin masks and fallback flags;
     bins: also return the compositing weight per depth bin (n, 65)."""
     params = np.ascontiguousarray(params, F32)
@@ -228,8 +246,13 @@ def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, 
     if bins:
         res["bins"] = np.zeros((n, 65), F64)
     bgv = np.asarray(bg, F64)
+    og, oG, othr = None, 0, 0.0
+    if skip is not None:
+        og = np.ascontiguousarray(skip[0], F32); oG = og.shape[0]; othr = float(skip[1])
+    bb = np.asarray(BBOX, F64)
     rc = lib().or_render(_p(tree.box), _p(tree.info), _p(tree.split), tree.n_nodes, _p(params), width, hidden,
-                         lx, ld, _p(o), _p(d), n, steps, cap, float(t_term), _p(bgv), mode, int(jitter), threads,
+                         lx, ld, _p(o), _p(d), n, steps, cap, float(t_term), _p(bgv), mode, int(jitter),
+                         _p(og) if og is not None else None, oG, _p(bb), othr, threads,
                          _p(res["rgb"]), _p(res["depth"]), _p(res["opacity"]), _p(res["n_gen"]),
                          _p(res["n_eval"]), _p(res["ert_margin"]),
                          _p(so) if so is not None else None, _p(sw) if sw is not None else None,

@@ -408,6 +408,63 @@ int or_samples(const float *o, const float *d, int64_t n, const int *n_x, const 
 }
 
 /* ======================================================================== */
+/* Empty-space skipping (Sec. 4.1: the finer density grid also serves "empty */
+/* space detection")                                                         */
+/* ======================================================================== */
+
+/* The guidance grid as an occupancy grid: a cell is occupied when its density
+ * exceeds thr.  The cell of a coordinate p on axis a is floor((p - lo_a) * sc_a),
+ * sc_a = G / (hi_a - lo_a), clamped to [0, G - 1] (in the mode's precision, the
+ * FP32 product rounded once). */
+typedef struct {
+    const float *grid; int G; float thr;
+    float lo32[3], sc32[3]; double lo64[3], sc64[3];
+    int steps; uint64_t jitter;
+} or_occ;
+
+static int or_clampc(long long c, int G) { return c < 0 ? 0 : (c > G - 1 ? G - 1 : (int)c); }
+
+/* 1 when a sample of crossing [tin, tout], placed as the k-th kept crossing of the
+ * ray (its jitter depends on k), lies in an occupied cell. */
+static int or_crossing_occupied(const or_occ *oc, int mode, uint64_t key, const float of[3], const float df[3],
+                                double tin, double tout, int k)
+{
+    const int G = oc->G;
+    for (int j = 0; j < oc->steps; j++) {
+        const float u = or_jitter_u(oc->jitter, key, k, oc->steps, j);
+        int c[3];
+        if (mode == 1) {
+            float t, dl, p[3];
+            or_sample32((float)tin, (float)tout, oc->steps, j, u, of, df, &t, &dl, p);
+            for (int a = 0; a < 3; a++) {
+                float q = p[a] - oc->lo32[a];
+                float f = q * oc->sc32[a];
+                c[a] = or_clampc((long long)floorf(f), G);
+            }
+        } else {
+            double o64[3] = {of[0], of[1], of[2]}, d64[3] = {df[0], df[1], df[2]};
+            double t, dl, p[3];
+            or_sample64(tin, tout, oc->steps, j, (double)u, o64, d64, &t, &dl, p);
+            for (int a = 0; a < 3; a++) c[a] = or_clampc((long long)floor((p[a] - oc->lo64[a]) * oc->sc64[a]), G);
+        }
+        if (oc->grid[(size_t)c[0] + (size_t)G * ((size_t)c[1] + (size_t)G * (size_t)c[2])] > oc->thr) return 1;
+    }
+    return 0;
+}
+
+static void or_occ_init(or_occ *oc, const float *grid, int G, const double *bbox6, double thr, int steps,
+                        uint64_t jitter)
+{
+    oc->grid = grid; oc->G = G; oc->thr = (float)thr; oc->steps = steps; oc->jitter = jitter;
+    for (int a = 0; a < 3; a++) {
+        oc->lo64[a] = bbox6[a];
+        oc->sc64[a] = (double)G / (bbox6[3 + a] - bbox6[a]);
+        oc->lo32[a] = (float)bbox6[a];
+        oc->sc32[a] = (float)oc->sc64[a];
+    }
+}
+
+/* ======================================================================== */
 /* Grouping by leaf (Sec. 3.5, Fig. "parallel")                             */
 /* ======================================================================== */
 
@@ -617,6 +674,7 @@ typedef struct {
     const float *o, *d; int64_t n;
     /* render params */
     int steps, cap; double t_term; double bg[3]; int mode; uint64_t jitter;
+    const or_occ *occ;  /* empty-space skipping (NULL: off) */
     /* outputs */
     double *rgb, *depth, *opacity; int *n_gen, *n_eval; double *ert_margin;
     double *slot_out; /* (n, cap, 4) sigma rgb; may be NULL */
@@ -684,18 +742,48 @@ static int or_overlaps(int mode, double t0, double t1, int k, double a, double b
     return a < t0 + (k + 1) * w && b > t0 + k * w;
 }
 
-/* Keep, in order, the crossings that overlap a bin of `mask`, at most maxc. */
-static int or_keep_masked(int mode, double t0, double t1, uint64_t mask, int *leaf, double *tin, double *tout,
-                          int n, int maxc)
+/* Keep, in order and at most maxc, the crossings that overlap a bin of *mask (when
+ * mask != NULL) and have a sample in an occupied cell (when oc != NULL; the sample
+ * placed as the crossing's index among the kept ones). */
+static int or_keep(int mode, const uint64_t *mask, double t0, double t1, const or_occ *oc, uint64_t key,
+                   const float *of, const float *df, int *leaf, double *tin, double *tout, int n, int maxc)
 {
     int m = 0;
     for (int i = 0; i < n && m < maxc; i++) {
-        int keep = 0;
-        for (int k = 0; k < 64 && !keep; k++)
-            if ((mask >> k) & 1ull) keep = or_overlaps(mode, t0, t1, k, tin[i], tout[i]);
-        if (keep) { leaf[m] = leaf[i]; tin[m] = tin[i]; tout[m] = tout[i]; m++; }
+        if (mask) {
+            int keep = 0;
+            for (int k = 0; k < 64 && !keep; k++)
+                if ((*mask >> k) & 1ull) keep = or_overlaps(mode, t0, t1, k, tin[i], tout[i]);
+            if (!keep) continue;
+        }
+        if (oc && !or_crossing_occupied(oc, mode, key, of, df, tin[i], tout[i], m)) continue;
+        leaf[m] = leaf[i]; tin[m] = tin[i]; tout[m] = tout[i]; m++;
     }
     return m;
+}
+
+/* Traversal with empty-space skipping: every crossing in order, then the occupied
+ * ones kept (at most maxc), each tested with its samples placed as the kept index. */
+int or_traverse_skip(const float *box, const int *info, const float *split, int n_nodes,
+                     const float *o, const float *d, int64_t n, int maxc, int mode, int method, int steps,
+                     uint64_t jitter, const float *occ_grid, int occ_G, const double *occ_bbox, double occ_thr,
+                     int *n_x, int *leaf, double *tin, double *tout)
+{
+    or_occ oc;
+    or_occ_init(&oc, occ_grid, occ_G, occ_bbox, occ_thr, steps, jitter);
+    for (int64_t r = 0; r < n; r++) {
+        int lf[256];
+        double a[256], b[256];
+        int c = or_trav_ray(box, info, split, n_nodes, o + 3 * r, d + 3 * r, 256, mode, method, lf, a, b);
+        if (c < 0) return -1;
+        c = or_keep(mode, NULL, 0.0, 0.0, &oc, or_ray_key(jitter, o + 3 * r, d + 3 * r), o + 3 * r, d + 3 * r, lf, a,
+                    b, c, maxc);
+        for (int i = 0; i < c; i++) {
+            leaf[r * maxc + i] = lf[i]; tin[r * maxc + i] = a[i]; tout[r * maxc + i] = b[i];
+        }
+        n_x[r] = c;
+    }
+    return 0;
 }
 
 /* Compositing (NeRF quadrature, Sec. 3.1): T = 1; per sample in ray order, stop once
@@ -710,11 +798,14 @@ static void or_render_ray(const or_job *J, int64_t r)
     int nx;
     double root0 = 0.0, root1 = 0.0;
     int root_hit = or_root(J->box, J->o + 3 * r, J->d + 3 * r, J->mode, &root0, &root1);
-    if (J->mask && !J->fallback[r]) {
+    const int masked = J->mask && !J->fallback[r];
+    if (masked || J->occ) {
         nx = or_trav_ray(J->box, J->info, J->split, J->n_nodes, J->o + 3 * r, J->d + 3 * r,
                          256, J->mode, 0, leaf, tin, tout);
         if (nx < 0) nx = 0;
-        nx = or_keep_masked(J->mode, root0, root1, J->mask[r], leaf, tin, tout, nx, maxc);
+        nx = or_keep(J->mode, masked ? J->mask + r : NULL, root0, root1, J->occ,
+                     or_ray_key(J->jitter, J->o + 3 * r, J->d + 3 * r), J->o + 3 * r, J->d + 3 * r, leaf, tin,
+                     tout, nx, maxc);
     } else {
         nx = or_trav_ray(J->box, J->info, J->split, J->n_nodes, J->o + 3 * r, J->d + 3 * r,
                          maxc, J->mode, 0, leaf, tin, tout);
@@ -822,7 +913,8 @@ static void *or_render_worker(void *arg)
 int or_render(const float *box, const int *info, const float *split, int n_nodes,
               const float *params, int width, int hidden, int lx, int ld,
               const float *o, const float *d, int64_t n,
-              int steps, int cap, double t_term, const double *bg, int mode, uint64_t jitter, int n_threads,
+              int steps, int cap, double t_term, const double *bg, int mode, uint64_t jitter,
+              const float *occ_grid, int occ_G, const double *occ_bbox, double occ_thr, int n_threads,
               double *rgb, double *depth, double *opacity, int *n_gen, int *n_eval, double *ert_margin,
               double *slot_out, double *slot_w, double *t_final, const uint64_t *mask, const int *fallback,
               double *bins)
@@ -839,6 +931,11 @@ int or_render(const float *box, const int *info, const float *split, int n_nodes
     for (int c = 0; c < 3; c++) base.bg[c] = bg[c];
     base.mode = mode;
     base.jitter = jitter;
+    or_occ oc;
+    if (occ_grid) {
+        or_occ_init(&oc, occ_grid, occ_G, occ_bbox, occ_thr, steps, jitter);
+        base.occ = &oc;
+    }
     base.rgb = rgb; base.depth = depth; base.opacity = opacity; base.n_gen = n_gen; base.n_eval = n_eval;
     base.ert_margin = ert_margin; base.slot_out = slot_out; base.slot_w = slot_w; base.t_final = t_final;
     base.mask = mask; base.fallback = fallback; base.bins = bins;

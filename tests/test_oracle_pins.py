@@ -358,6 +358,75 @@ def test_jitter_is_keyed_by_the_ray_not_its_batch_position(c1_scene):
 
 
 # ----------------------------------------------------------------------------------
+# empty-space skipping over the guidance grid (Sec. 4.1 "empty space detection")
+# ----------------------------------------------------------------------------------
+
+def _brute_skip(tree, grid, thr, o, d, maxc, steps, jitter):
+    """Kept crossings by brute force: the full crossing list (FP64), then, in order,
+    those with a sample (placed as the crossing's index among the kept ones) in a cell
+    of density > thr; the cell of p is floor((p + 1) G / 2) clamped, over [-1, 1]^3."""
+    G = grid.shape[0]
+    nx, leaf, tin, tout = O.traverse(tree, o, d, 256, mode=0)
+    out = []
+    for r in range(len(o)):
+        kept = []
+        for i in range(nx[r]):
+            if len(kept) == maxc:
+                break
+            k = len(kept)
+            dl = (tout[r, i] - tin[r, i]) / steps
+            occ = False
+            for j in range(steps):
+                u = O.jitter_fraction(jitter, o[r], d[r], k, steps, j)
+                t = tin[r, i] + (j + u) * dl
+                p = o[r].astype(np.float64) + t * d[r].astype(np.float64)
+                c = np.clip(np.floor((p + 1.0) * (G / 2)), 0, G - 1).astype(int)
+                occ = occ or grid[c[2], c[1], c[0]] > thr
+            if occ:
+                kept.append(leaf[r, i])
+        out.append(kept)
+    return out
+
+
+@pytest.mark.parametrize("jitter", [0, 21])
+def test_skipping_keeps_exactly_the_occupied_crossings(jitter, mass_scene):
+    grid, tree = mass_scene
+    thr = float(np.quantile(grid, 0.6))          # about 60 % of the cells empty
+    o, d = _camera_rays(150, 83)
+    maxc, steps = 12, 8
+    nx, leaf, tin, tout = O.traverse(tree, o, d, maxc, mode=0, skip=(grid, thr, steps, jitter))
+    want = _brute_skip(tree, grid, thr, o, d, maxc, steps, jitter)
+    full, *_ = O.traverse(tree, o, d, maxc, mode=0)
+    assert sum(len(w) for w in want) < full.sum()   # the threshold does skip crossings
+    for r in range(len(o)):
+        assert list(leaf[r, :nx[r]]) == want[r]
+
+
+def test_skipping_below_every_density_is_the_plain_render(c1_scene):
+    cfg, grid, tree = c1_scene
+    P = S.xavier_weights(0, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    o, d = _camera_rays(200, 89)
+    for mode in (0, 1):
+        a = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=mode)
+        b = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=mode,
+                     skip=(grid, -1.0))
+        for key in ("rgb", "depth", "opacity", "n_gen"):
+            np.testing.assert_array_equal(a[key], b[key])
+
+
+def test_skipping_above_every_density_leaves_the_background(c1_scene):
+    cfg, grid, tree = c1_scene
+    P = S.xavier_weights(0, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    o, d = _camera_rays(50, 97)
+    bg = (0.25, 0.5, 0.75)
+    res = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, bg=bg, mode=0,
+                   skip=(grid, float(grid.max()) + 1.0))
+    assert np.all(res["n_gen"] == 0)
+    np.testing.assert_array_equal(res["rgb"], np.tile(bg, (len(o), 1)))
+    np.testing.assert_array_equal(res["opacity"], 0.0)
+
+
+# ----------------------------------------------------------------------------------
 # grouping (Sec. 3.5)
 # ----------------------------------------------------------------------------------
 
