@@ -139,7 +139,9 @@ def workload_name(cfg, args) -> str:
             f"{cfg.G}^3 guidance grid, depth<={cfg.max_depth}"
             + (f" (mass<=1/{round(1 / cfg.leaf_mass_frac)})" if cfg.leaf_mass_frac > 0 else "")
             + f", {cfg.hidden}x{cfg.width} MLP per leaf, {cfg.steps} samples/crossing, cap {cfg.cap}"
-            + (f", stratified jitter (seed {args.jitter})" if getattr(args, "jitter", 0) else ""))
+            + (f", stratified jitter (seed {args.jitter})" if getattr(args, "jitter", 0) else "")
+            + (f", empty-space skipping (density > {args.skip_empty:g})"
+               if getattr(args, "skip_empty", None) is not None else ""))
 
 
 def barrier():
@@ -228,8 +230,9 @@ def run_ours(args):
                 continue
             raise
         for _ in range(args.warmup):
-            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter)
-        _, _, _, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter)
+            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter, skip_empty=args.skip_empty)
+        _, _, _, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter,
+                                 skip_empty=args.skip_empty)
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -237,7 +240,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             e0.record(stream)
             for _ in range(args.steps):
-                R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter)
+                R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter, skip_empty=args.skip_empty)
             e1.record(stream)
             torch.cuda.synchronize()
         barrier()
@@ -247,7 +250,8 @@ def run_ours(args):
         amnerf.amnerf_set_timing(R.ctx, True)
         stage = np.zeros(4)
         for _ in range(args.steps):
-            *_, s2 = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter)
+            *_, s2 = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter,
+                                 skip_empty=args.skip_empty)
             stage += np.array(s2["ms"])
         amnerf.amnerf_set_timing(R.ctx, False)
         stage /= args.steps
@@ -272,12 +276,12 @@ def run_ours(args):
             torch.empty(n, dtype=torch.float32).pin_memory().numpy()]
     for _ in range(max(1, args.warmup)):
         amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term,
-                                  jitter=args.jitter)
+                                  jitter=args.jitter, skip_empty=args.skip_empty)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term,
-                                  jitter=args.jitter)
+                                  jitter=args.jitter, skip_empty=args.skip_empty)
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
     barrier()
 
@@ -295,7 +299,8 @@ def run_ours(args):
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     ref = O.render(tree, P_or, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps, cfg.cap,
-                   cfg.t_term, mode=0, threads=cores, jitter=args.jitter)
+                   cfg.t_term, mode=0, threads=cores, jitter=args.jitter,
+                   skip=(grid, args.skip_empty) if args.skip_empty is not None else None)
     cpu_s = time.perf_counter() - t0
     cpu_samples = int(ref["n_gen"].sum())
     acc = {}
@@ -630,7 +635,8 @@ def run_reference(args):
         idx = S.ray_subset(len(o_np), per_step, 100 + i)
         t0 = time.perf_counter()
         ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps, cfg.cap,
-                       cfg.t_term, mode=0, threads=cores, jitter=args.jitter)
+                       cfg.t_term, mode=0, threads=cores, jitter=args.jitter,
+                       skip=(grid, args.skip_empty) if args.skip_empty is not None else None)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -666,6 +672,8 @@ def main():
     ap.add_argument("--density-scale", type=float, default=1.0, help="c5: factor on every density of the scene")
     ap.add_argument("--leaf-net", default="", help="c5: leaf network shape HxW (default: the config's 2x32)")
     ap.add_argument("--px", type=int, default=None, help="square image size (default: the config's)")
+    ap.add_argument("--skip-empty", type=float, default=None,
+                    help="empty-space skipping: density threshold of the guidance grid (c1/c2); default off")
     ap.add_argument("--jitter", type=int, default=0,
                     help="sample placement: 0 = stratum midpoints, else the stratified jitter's seed (c1/c2)")
     args = ap.parse_args()

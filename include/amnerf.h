@@ -124,6 +124,15 @@ typedef struct {
      * (o.z, d.x) and (d.y, d.z) into the seed with three finalisations, so a ray draws
      * the same points in any batch.  The quadrature widths are the strata either way. */
     uint64_t jitter_seed;
+    /* Empty-space skipping (Sec. 4.1: the density grid also serves "empty space
+     * detection"): when skip_empty != 0 a leaf crossing is sampled only if one of its
+     * samples -- placed as it would be as the ray's next kept crossing -- lies in a
+     * guidance-grid cell (the grid given to amnerf_build_tree) of density >
+     * empty_threshold.  The cell of a coordinate p on axis a is floor((p - lo_a) *
+     * (G / (hi_a - lo_a))) in FP32, clamped to [0, G - 1].  Skipped crossings do not
+     * count toward max_samples. */
+    int skip_empty;
+    float empty_threshold;
 } amnerf_render_params;
 
 /* Schedule of the network step's tiles over the persistent workers (warpgroups). */

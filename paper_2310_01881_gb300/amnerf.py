@@ -47,7 +47,8 @@ class amnerf_mlp_desc(ctypes.Structure):
 class amnerf_render_params(ctypes.Structure):
     _fields_ = [("steps_per_leaf", ctypes.c_int), ("max_samples", ctypes.c_int), ("t_term", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("use_proposal", ctypes.c_int), ("coverage", ctypes.c_float),
-                ("max_bins", ctypes.c_int), ("jitter_seed", ctypes.c_uint64)]
+                ("max_bins", ctypes.c_int), ("jitter_seed", ctypes.c_uint64), ("skip_empty", ctypes.c_int),
+                ("empty_threshold", ctypes.c_float)]
 
 
 PROPOSAL_PARAMS = 6113
@@ -228,17 +229,19 @@ def amnerf_calibrate_fp8(ctx, o, d, n_leaves: int, hidden: int, steps: int = 8, 
 
 
 def _params(steps: int, cap: int, t_term: float, bg, proposal: bool = False, coverage: float = 0.99,
-            max_bins: int = 16, jitter: int = 0) -> amnerf_render_params:
-    """jitter: 0 = samples at stratum midpoints, else the seed of the stratified jitter."""
+            max_bins: int = 16, jitter: int = 0, skip_empty=None) -> amnerf_render_params:
+    """jitter: 0 = samples at stratum midpoints, else the seed of the stratified jitter.
+    skip_empty: None, or the density threshold of empty-space skipping."""
     return amnerf_render_params(steps, cap, t_term, (ctypes.c_float * 3)(*bg), int(proposal), coverage, max_bins,
-                                int(jitter) & ((1 << 64) - 1))
+                                int(jitter) & ((1 << 64) - 1), int(skip_empty is not None),
+                                float(skip_empty) if skip_empty is not None else 0.0)
 
 
 def amnerf_render(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
                   bg=(0.0, 0.0, 0.0), stats: bool = False, proposal: bool = False, coverage: float = 0.99,
-                  max_bins: int = 16, jitter: int = 0):
+                  max_bins: int = 16, jitter: int = 0, skip_empty=None):
     """Enqueue a render of CUDA tensors o, d (n, 3) into rgb (n, 3), depth, opacity (n,)."""
-    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter)
+    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter, skip_empty)
     sp = amnerf_stats() if stats else None
     st = load().amnerf_render(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
                               _ptr(opacity), ctypes.byref(sp) if sp is not None else None)
@@ -248,8 +251,8 @@ def amnerf_render(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64,
 
 def amnerf_render_debug(ctx, o, d, rgb, depth, opacity, dbg: dict, steps: int = 8, cap: int = 64,
                         t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), stats: bool = True, proposal: bool = False,
-                        coverage: float = 0.99, max_bins: int = 16, jitter: int = 0):
-    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter)
+                        coverage: float = 0.99, max_bins: int = 16, jitter: int = 0, skip_empty=None):
+    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter, skip_empty)
     db = amnerf_debug(*[_ptr(dbg.get(k)) for k, _ in amnerf_debug._fields_])
     sp = amnerf_stats() if stats else None
     st = load().amnerf_render_debug(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
@@ -260,12 +263,12 @@ def amnerf_render_debug(ctx, o, d, rgb, depth, opacity, dbg: dict, steps: int = 
 
 def amnerf_render_host(ctx, o: np.ndarray, d: np.ndarray, rgb: np.ndarray, depth: np.ndarray,
                        opacity: np.ndarray, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
-                       bg=(0.0, 0.0, 0.0), stats: bool = False, jitter: int = 0):
+                       bg=(0.0, 0.0, 0.0), stats: bool = False, jitter: int = 0, skip_empty=None):
     """Render from HOST arrays (page-locked buffers make the copies asynchronous)."""
     for a in (o, d, rgb, depth, opacity):
         if a.dtype != np.float32 or not a.flags.c_contiguous:
             raise ValueError("host buffers must be contiguous float32")
-    p = _params(steps, cap, t_term, bg, jitter=jitter)
+    p = _params(steps, cap, t_term, bg, jitter=jitter, skip_empty=skip_empty)
     sp = amnerf_stats() if stats else None
     st = load().amnerf_render_host(ctx, _hptr(o), _hptr(d), o.shape[0], ctypes.byref(p), _hptr(rgb),
                                    _hptr(depth), _hptr(opacity), ctypes.byref(sp) if sp is not None else None)
@@ -420,7 +423,7 @@ class Renderer:
         return amnerf_calibrate_fp8(self.ctx, o, d, self.n_leaves, hidden, steps=steps, cap=cap, t_term=t_term)
 
     def render(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0), stats=False, out=None,
-               proposal=False, coverage=0.99, max_bins=16, jitter=0):
+               proposal=False, coverage=0.99, max_bins=16, jitter=0, skip_empty=None):
         torch = self._torch
         n = o.shape[0]
         if out is None:
@@ -429,11 +432,12 @@ class Renderer:
                    torch.empty((n,), device=o.device, dtype=torch.float32))
         amnerf_set_stream(self.ctx, torch.cuda.current_stream(o.device).cuda_stream)
         s = amnerf_render(self.ctx, o, d, *out, steps=steps, cap=cap, t_term=t_term, bg=bg, stats=stats,
-                          proposal=proposal, coverage=coverage, max_bins=max_bins, jitter=jitter)
+                          proposal=proposal, coverage=coverage, max_bins=max_bins, jitter=jitter,
+                          skip_empty=skip_empty)
         return (*out, s) if stats else out
 
     def render_debug(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0), proposal=False, coverage=0.99,
-                     max_bins=16, jitter=0):
+                     max_bins=16, jitter=0, skip_empty=None):
         torch = self._torch
         n = o.shape[0]
         maxc = cap // steps
@@ -456,7 +460,8 @@ class Renderer:
         opac = torch.empty((n,), device=dev, dtype=torch.float32)
         amnerf_set_stream(self.ctx, torch.cuda.current_stream(dev).cuda_stream)
         s = amnerf_render_debug(self.ctx, o, d, rgb, depth, opac, dbg, steps=steps, cap=cap, t_term=t_term, bg=bg,
-                                proposal=proposal, coverage=coverage, max_bins=max_bins, jitter=jitter)
+                                proposal=proposal, coverage=coverage, max_bins=max_bins, jitter=jitter,
+                                skip_empty=skip_empty)
         host = {k: v.cpu().numpy() for k, v in dbg.items()}
         host["leaf"] = host["leaf"].view(np.uint16).astype(np.int64).reshape(n, maxc)
         host["t_in"] = host["t_in"].reshape(n, maxc)

@@ -57,11 +57,24 @@ constexpr int kDevErrBounds = 3;
 
 // ---- kernels (enqueue only; return cudaGetLastError) ------------------------------
 
+// Empty-space skipping (grid == nullptr: off): the guidance grid (x fastest, G^3),
+// the cell of p on axis a is floor((p - lo[a]) * sc[a]) clamped; occupied when the
+// density > thr.  Samples are placed as in the sampling step (steps, jitter).
+struct OccArgs {
+    const float* grid = nullptr;
+    int G = 0;
+    float lo[3] = {0.f, 0.f, 0.f}, sc[3] = {0.f, 0.f, 0.f};
+    float thr = 0.f;
+    int steps = 8;
+    uint64_t jitter = 0;
+};
+
 // K-a: traversal + crossing list + per-leaf crossing histogram.
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
                             int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
                             int n_leaves, int* err, const uint64_t* mask = nullptr,
-                            const uint8_t* fallback = nullptr, float2* root_out = nullptr);
+                            const uint8_t* fallback = nullptr, float2* root_out = nullptr,
+                            const OccArgs& occ = OccArgs());
 
 // K-b: exclusive scans (crossings and network tiles per leaf) and the grouped scatter.
 cudaError_t launch_scan(cudaStream_t s, const uint32_t* counts, int n_leaves, int cpt, uint32_t* offsets,

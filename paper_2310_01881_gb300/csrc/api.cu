@@ -23,6 +23,9 @@ struct amnerf_ctx {
     std::vector<amnerf_node> nodes;
     int n_leaves = 0;
     DevNode* d_nodes = nullptr;
+    float* d_grid = nullptr;  // the guidance grid (empty-space skipping)
+    int grid_G = 0;
+    float grid_lo[3] = {0.f, 0.f, 0.f}, grid_sc[3] = {0.f, 0.f, 0.f};
     // networks
     bool mlp_loaded = false;
     amnerf_mlp_desc desc{};
@@ -139,6 +142,8 @@ amnerf_status check_params(amnerf_ctx* ctx, const amnerf_render_params* p, int64
     maxc = p->max_samples / st;
     if (maxc > 255) return fail(ctx, AMNERF_E_INVAL, "max_samples / steps_per_leaf must be <= 255");
     if (!(p->t_term >= 0.0f) || !std::isfinite(p->t_term)) return fail(ctx, AMNERF_E_INVAL, "t_term must be >= 0");
+    if (p->skip_empty && !std::isfinite(p->empty_threshold))
+        return fail(ctx, AMNERF_E_INVAL, "empty_threshold must be finite");
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(p->bg[c])) return fail(ctx, AMNERF_E_INVAL, "bg must be finite");
     if (n < 0) return fail(ctx, AMNERF_E_INVAL, "n_rays < 0");
@@ -263,6 +268,7 @@ void amnerf_destroy(amnerf_ctx* ctx) {
     else cudaDeviceSynchronize();
     free_ray_scratch(ctx);
     dfree(ctx->d_nodes);
+    dfree(ctx->d_grid);
     dfree(ctx->d_weights);
     dfree(ctx->d_amax);
     dfree(ctx->d_counts);
@@ -310,8 +316,19 @@ amnerf_status amnerf_build_tree(amnerf_ctx* ctx, const float* grid_host, int G, 
     }
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     dfree(ctx->d_nodes);
+    dfree(ctx->d_grid);
+    ctx->grid_G = 0;
     CK(cudaMalloc((void**)&ctx->d_nodes, sizeof(DevNode) * dn.size()), "tree allocation");
     CK(cudaMemcpy(ctx->d_nodes, dn.data(), sizeof(DevNode) * dn.size(), cudaMemcpyHostToDevice), "tree upload");
+    // the guidance grid stays resident for empty-space skipping
+    const size_t cells = (size_t)G * G * G;
+    CK(cudaMalloc((void**)&ctx->d_grid, sizeof(float) * cells), "grid allocation");
+    CK(cudaMemcpy(ctx->d_grid, grid_host, sizeof(float) * cells, cudaMemcpyHostToDevice), "grid upload");
+    ctx->grid_G = G;
+    for (int a = 0; a < 3; ++a) {
+        ctx->grid_lo[a] = (float)bbox[a];
+        ctx->grid_sc[a] = (float)((double)G / (bbox[3 + a] - bbox[a]));
+    }
     ctx->nodes.swap(nodes);
     ctx->n_leaves = nl;
     ctx->mlp_loaded = false;
@@ -436,8 +453,20 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         mask = ctx->d_mask;
         fallback = ctx->d_fallback;
     }
+    OccArgs occ;
+    if (p->skip_empty) {
+        occ.grid = ctx->d_grid;
+        occ.G = ctx->grid_G;
+        for (int a = 0; a < 3; ++a) {
+            occ.lo[a] = ctx->grid_lo[a];
+            occ.sc[a] = ctx->grid_sc[a];
+        }
+        occ.thr = p->empty_threshold;
+        occ.steps = steps;
+        occ.jitter = p->jitter_seed;
+    }
     CK(launch_traverse(s, ro, rd, nn, ctx->d_nodes, maxc, ctx->d_nx, ctx->d_xing, ctx->d_xleaf, ctx->d_counts, L,
-                       ctx->d_err, mask, fallback, root_out),
+                       ctx->d_err, mask, fallback, root_out, occ),
        "traverse launch");
     if (ctx->timing) cudaEventRecord(ctx->ev[1], s);
     CK(launch_scan(s, ctx->d_counts, L, kTileRows / steps, ctx->d_offsets, ctx->d_tile_off, ctx->d_cursor,

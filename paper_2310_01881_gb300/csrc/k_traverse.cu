@@ -16,7 +16,11 @@
 // With the proposal sampler, a leaf crossing [t_in, t_out] is kept only when it
 // overlaps a kept depth bin [t0 + k w, t0 + (k + 1) w), w = (t1 - t0) / 64 of the
 // ray's root interval [t0, t1] (same FP32 operation order as the oracle); rays that
-// fell back keep every crossing.
+// fell back keep every crossing.  With empty-space skipping (Sec. 4.1: the density
+// grid also serves empty space detection) a leaf crossing is kept only when one of
+// its samples -- placed as it would be as the ray's next kept crossing, in the
+// sampling step's FP32 order -- lies in a guidance-grid cell above the threshold;
+// skipped crossings do not count toward maxc.
 #include "amnerf_internal.h"
 
 namespace amnerf {
@@ -63,13 +67,37 @@ __device__ __forceinline__ bool overlaps_kept(uint64_t kept, float r0, float bw,
     return (kept & run) != 0;
 }
 
+// Whether a sample of crossing [tin, tout], placed as kept crossing k, lies in an
+// occupied cell: t_j = tin + (j + u_j) delta, delta = (tout - tin) / steps, x = o + t d,
+// cell = floor((x - lo) * sc) clamped, occupied when the density > thr.
+__device__ __forceinline__ bool crossing_occupied(const OccArgs& oc, const float o[3], const float d[3],
+                                                  uint64_t key, float tin, float tout, int k) {
+    const float delta = __fmul_rn(__fsub_rn(tout, tin), __frcp_rn((float)oc.steps));  // steps: a power of two
+    const int G = oc.G;
+    for (int j = 0; j < oc.steps; ++j) {
+        const float u = jit_fraction(oc.jitter, key, k, oc.steps, j);
+        const float t = __fadd_rn(tin, __fmul_rn(__fadd_rn((float)j, u), delta));
+        int c[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float x = __fadd_rn(o[a], __fmul_rn(t, d[a]));
+            const int ci = (int)floorf(__fmul_rn(__fsub_rn(x, oc.lo[a]), oc.sc[a]));
+            c[a] = ci < 0 ? 0 : (ci > G - 1 ? G - 1 : ci);
+        }
+        if (__ldg(oc.grid + (size_t)c[0] + (size_t)G * ((size_t)c[1] + (size_t)G * (size_t)c[2])) > oc.thr)
+            return true;
+    }
+    return false;
+}
+
 __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, const float* __restrict__ rd,
                                                   uint32_t n, const DevNode* __restrict__ nodes, int maxc,
                                                   uint8_t* __restrict__ n_x, float2* __restrict__ xing,
                                                   uint16_t* __restrict__ xleaf, uint32_t* __restrict__ counts,
                                                   int n_leaves, int* __restrict__ err,
                                                   const uint64_t* __restrict__ mask,
-                                                  const uint8_t* __restrict__ fallback, float2* __restrict__ root_out) {
+                                                  const uint8_t* __restrict__ fallback, float2* __restrict__ root_out,
+                                                  const OccArgs occ) {
     extern __shared__ uint32_t s_cnt[];
     for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) s_cnt[i] = 0u;
     __syncthreads();
@@ -102,6 +130,7 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
         const uint64_t kept_bins = (mask && !__ldg(fallback + r)) ? __ldg(mask + r) : 0ull;
         const bool masked = mask && !__ldg(fallback + r);
         const float bw = __fmul_rn(__fsub_rn(r1, r0), 0.015625f);  // bin width (t1 - t0) / 64
+        const uint64_t key = (occ.grid && occ.jitter) ? jit_ray_key(occ.jitter, o, d) : 0ull;
         while (cnt < maxc) {
             if (!have) {
                 if (sp == 0) break;
@@ -121,6 +150,7 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
             const int axis = (int)(meta & 3u) - 1;
             if (axis < 0) {
                 if (masked && !overlaps_kept(kept_bins, r0, bw, tin, tout)) continue;
+                if (occ.grid && !crossing_occupied(occ, o, d, key, tin, tout, cnt)) continue;
                 const uint32_t leaf = meta >> 2;
                 xing[base + cnt] = make_float2(tin, tout);
                 xleaf[base + cnt] = (uint16_t)leaf;
@@ -160,13 +190,13 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
                             int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
                             int n_leaves, int* err, const uint64_t* mask, const uint8_t* fallback,
-                            float2* root_out) {
+                            float2* root_out, const OccArgs& occ) {
     if (n == 0) return cudaSuccess;
     const int threads = 256;
     const unsigned blocks = (n + threads - 1) / threads;
     const size_t smem = sizeof(uint32_t) * (size_t)n_leaves;
     k_traverse<<<blocks, threads, smem, s>>>(ro, rd, n, nodes, maxc, n_x, xing, xleaf, counts, n_leaves, err, mask,
-                                             fallback, root_out);
+                                             fallback, root_out, occ);
     return cudaGetLastError();
 }
 

@@ -251,6 +251,64 @@ def test_jitter_is_keyed_by_the_ray_not_its_batch_position(R, prec):
         np.testing.assert_array_equal(x[p], y)
 
 
+# ---- empty-space skipping over the guidance grid (Sec. 4.1 "empty space detection") ----
+
+@pytest.mark.parametrize("seed,jitter", [(0, 0), (3, 0), (1, 9)])
+def test_c1_skipping_crossings_bit_exact_and_fp32_pixels(R, seed, jitter):
+    cfg = S.CONFIGS["c1"]
+    grid, tree, P = _setup(R, cfg, seed)
+    thr = float(np.quantile(grid, 0.7))
+    o, d = _rays(cfg, seed)
+    ao, ad = _adversarial_rays()
+    o = np.concatenate([o, ao]); d = np.concatenate([d, ad])
+    maxc = cfg.cap // cfg.steps
+    rgb, depth, opac, dbg, st = R.render_debug(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap, jitter=jitter,
+                                               skip_empty=thr)
+    nx, leaf, tin, tout = O.traverse(tree, o, d, maxc, mode=1, skip=(grid, thr, cfg.steps, jitter))
+    np.testing.assert_array_equal(dbg["n_x"].astype(np.int64), nx)
+    valid = np.arange(maxc)[None, :] < nx[:, None]
+    np.testing.assert_array_equal(dbg["leaf"][valid], leaf[valid])
+    np.testing.assert_array_equal(dbg["t_in"][valid], tin[valid].astype(np.float32))
+    np.testing.assert_array_equal(dbg["t_out"][valid], tout[valid].astype(np.float32))
+    full, *_ = O.traverse(tree, o, d, maxc, mode=1)
+    assert nx.sum() < full.sum()                   # crossings were skipped
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1, threads=8,
+                   jitter=jitter, skip=(grid, thr))
+    _check_pixels(rgb, depth, opac, ref)
+    assert st["samples_generated"] == int(ref["n_gen"].sum())
+
+
+def test_c2_skipping_bf16_sampled_psnr(R):
+    cfg = S.CONFIGS["c2"]
+    grid, tree, P = _setup(R, cfg, 0, prec="bf16")
+    thr = 0.01
+    o, d = _rays(cfg, 0, 1, 400, 400)
+    rgb, _, _, st = R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap, stats=True, skip_empty=thr)
+    plain = R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap, stats=True)[3]
+    assert st["samples_generated"] < plain["samples_generated"]
+    idx = S.ray_subset(len(o), 2048, 3)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o[idx], d[idx], cfg.steps, cfg.cap, mode=0,
+                   threads=16, skip=(grid, thr))
+    assert _psnr(rgb.cpu().numpy()[idx], ref["rgb"]) >= 45.0
+
+
+def test_skipping_with_proposal_masks_matches_oracle(R):
+    from paper_2310_01881_gb300 import amnerf
+    cfg = S.CONFIGS["c1"]
+    grid, tree, P = _setup(R, cfg, 0)
+    amnerf.amnerf_proposal_set(R.ctx, S.proposal_init(11) * 3.0)
+    thr = float(np.quantile(grid, 0.6))
+    o, d = S.view_rays(cfg, 0, 4)
+    rgb, depth, opac, dbg, st = R.render_debug(_dev(o), _dev(d), cfg.steps, cfg.cap, proposal=True, coverage=0.7,
+                                               max_bins=64, skip_empty=thr)
+    mask, fb = dbg["prop_mask"], dbg["prop_fallback"].astype(np.int32)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1,
+                   mask=mask, fallback=fb, skip=(grid, thr))
+    np.testing.assert_array_equal(dbg["n_x"].astype(np.int64) * cfg.steps, ref["n_gen"])
+    ok = ref["ert_margin"] > 1e-3
+    assert np.abs(rgb - ref["rgb"]).max(axis=1)[ok].max() <= 1e-5
+
+
 def test_host_buffer_entry_point_matches_device(R):
     from paper_2310_01881_gb300 import amnerf
     cfg = S.CONFIGS["c1"]
