@@ -34,6 +34,7 @@ def _nvcc() -> str:
 def _deps() -> list[str]:
     out = [os.path.join(CSRC, s) for s in SOURCES]
     out.append(os.path.join(CSRC, "amnerf_internal.h"))
+    out.append(os.path.join(CSRC, "tc_common.cuh"))
     out.append(os.path.join(INCLUDE, "amnerf.h"))
     return out
 
@@ -49,7 +50,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile every translation unit and link libamnerf.so; returns its path."""
     os.makedirs(os.path.join(BUILD, "obj"), exist_ok=True)
     nvcc = _nvcc()
-    hdrs = [os.path.join(CSRC, "amnerf_internal.h"), os.path.join(INCLUDE, "amnerf.h")]
+    hdrs = [os.path.join(CSRC, "amnerf_internal.h"), os.path.join(CSRC, "tc_common.cuh"),
+            os.path.join(INCLUDE, "amnerf.h")]
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
