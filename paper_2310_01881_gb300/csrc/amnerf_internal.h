@@ -149,6 +149,10 @@ cudaError_t prepare_proposal(int* infer_grid);
 cudaError_t launch_prop_infer(cudaStream_t s, int infer_grid, const float* params, const float root_box[6],
                               const float* ro, const float* rd, uint32_t n, float coverage, int max_bins,
                               uint64_t* mask, uint8_t* fallback, unsigned long long* n_fallback, float* q_out);
+// The same selection for renders, the network on the tensor cores (BF16 operands).
+cudaError_t launch_prop_infer_tc(cudaStream_t s, const float* params, const float root_box[6], const float* ro,
+                                 const float* rd, uint32_t n, float coverage, int max_bins, uint64_t* mask,
+                                 uint8_t* fallback, unsigned long long* n_fallback, int* err);
 cudaError_t launch_prop_grad(cudaStream_t s, const float* params, const float* ro, const float* rd,
                              const float2* root, const float* targets, uint32_t n, uint32_t batch, uint64_t seed,
                              uint64_t step, float* grad, float* loss);

@@ -17,6 +17,13 @@
 //                  mass (ties to the lower index) until the mass reaches `coverage`
 //                  (the background counts toward it); more than max_bins depth bins
 //                  -> fallback to the plain sampler.
+//   k_prop_infer_tc the same for renders on the tensor cores: each CTA converts the FP32
+//                  parameters to BF16 operands in shared memory (the bias of each
+//                  layer as one more input column against a constant 1), and every
+//                  warpgroup runs a tile's three layers as tcgen05 MMAs (128 x 32 x 96,
+//                  128 x 32 x 48, 128 x 80 x 48; activations in TMEM), then the softmax
+//                  and the same bin selection.  amnerf_proposal_predict keeps the FP32
+//                  kernel (its probabilities are the FP32 ones).
 //   k_prop_grad    one CTA per 128 rays: each thread runs its ray forward and
 //                  backward and leaves its activations and deltas in shared memory;
 //                  the CTA then forms the gradient contractions (sum over its rays of
@@ -25,6 +32,7 @@
 #include <cstring>
 
 #include "amnerf_internal.h"
+#include "tc_common.cuh"
 
 namespace amnerf {
 namespace {
@@ -372,6 +380,201 @@ __global__ void __launch_bounds__(kRays * kInferGroups, 1) k_prop_infer(
     if ((threadIdx.x & 31) == 0 && n_fb) atomicAdd(n_fallback, (unsigned long long)n_fb);
 }
 
+// ---- inference on the tensor cores (renders) ---------------------------------------
+constexpr int kPTcGroups = 4;                      // warpgroups (tiles in flight) per CTA
+constexpr int kP1K = 96, kP2K = 48, kP3N = 80;     // layer 1 K (90 + bias, padded), layers 2-3 K, layer 3 N
+constexpr uint32_t kPW1 = 0;                                        // W1 [32 x 96]
+constexpr uint32_t kPW2 = kPW1 + PH * kP1K * 2;                     // W2 [32 x 48]
+constexpr uint32_t kPW3 = kPW2 + PH * kP2K * 2;                     // W3 [80 x 48]
+constexpr uint32_t kPWBytes = kPW3 + kP3N * kP2K * 2;               // 16 896 B
+struct PropTcTile {
+    float Q[PO][kRays];  // the tile's probabilities, [bin][ray]
+};
+struct PropTcCtl {
+    uint64_t bar_m[kPTcGroups];
+    int flag[kPTcGroups];
+    uint32_t tmem_base;
+};
+constexpr size_t kPTcSmem = kPWBytes + kPTcGroups * sizeof(PropTcTile) + sizeof(PropTcCtl);
+static_assert(kPWBytes % 1024 == 512 || kPWBytes % 128 == 0, "weight blob alignment");
+
+// TMEM per warpgroup (128 columns): D (the layer-3 accumulator, 80 FP32 columns; layers
+// 1-2 use 32) then A (48 columns: 96 BF16 inputs of layer 1, 48 of layers 2-3).
+constexpr uint32_t kPACol = 80;
+
+__global__ void __launch_bounds__(128 * kPTcGroups, 1) k_prop_infer_tc(
+    const float* __restrict__ params, float b0, float b1, float b2, float b3, float b4, float b5,
+    const float* __restrict__ ro, const float* __restrict__ rd, uint32_t n, float coverage, int max_bins,
+    uint64_t* __restrict__ mask, uint8_t* __restrict__ fallback, unsigned long long* __restrict__ n_fallback,
+    int* __restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t* wb = sm;
+    PropTcTile* tiles = reinterpret_cast<PropTcTile*>(sm + kPWBytes);
+    PropTcCtl* ctl = reinterpret_cast<PropTcCtl*>(sm + kPWBytes + kPTcGroups * sizeof(PropTcTile));
+    // BF16 operands, K-major core matrices; the bias is input column 90 (layer 1) or 32
+    for (int i = threadIdx.x; i < PH * kP1K + PH * kP2K + kP3N * kP2K; i += blockDim.x) {
+        float v = 0.0f;
+        uint32_t off;
+        if (i < PH * kP1K) {
+            const int nn = i / kP1K, k = i - nn * kP1K;
+            v = k < PIN ? params[OFF_W1 + nn * PIN + k] : (k == PIN ? params[OFF_B1 + nn] : 0.0f);
+            off = kPW1 + (uint32_t)tcx::cm_offset(nn, k, kP1K);
+        } else if (i < PH * kP1K + PH * kP2K) {
+            const int e = i - PH * kP1K, nn = e / kP2K, k = e - nn * kP2K;
+            v = k < PH ? params[OFF_W2 + nn * PH + k] : (k == PH ? params[OFF_B2 + nn] : 0.0f);
+            off = kPW2 + (uint32_t)tcx::cm_offset(nn, k, kP2K);
+        } else {
+            const int e = i - PH * kP1K - PH * kP2K, nn = e / kP2K, k = e - nn * kP2K;
+            if (nn < PO) v = k < PH ? params[OFF_W3 + nn * PH + k] : (k == PH ? params[OFF_B3 + nn] : 0.0f);
+            off = kPW3 + (uint32_t)tcx::cm_offset(nn, k, kP2K);
+        }
+        *reinterpret_cast<__nv_bfloat16*>(wb + off) = __float2bfloat16_rn(v);
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kPTcGroups; ++i) tcx::mbar_init(tcx::smem_u32(&ctl->bar_m[i]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tcx::fence_proxy_async();  // the operands written above are read by the MMAs (async proxy)
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tcx::smem_u32(&ctl->tmem_base)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tcx::tc_fence_before();
+    __syncthreads();
+    tcx::tc_fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+    const int g = threadIdx.x >> 7, t = threadIdx.x & 127, q = warp & 3;
+    const int bar_id = 1 + g;
+    const bool leader = t == 32 * (g & 3);
+    const uint32_t bar_m = tcx::smem_u32(&ctl->bar_m[g]);
+    volatile int* flag = &ctl->flag[g];
+    const uint32_t d_col = tmem + 128u * (uint32_t)g, a_col = d_col + kPACol;
+    const uint32_t lane = (uint32_t)(32 * q) << 16;
+    const uint32_t d_row = d_col + lane, a_row = a_col + lane;
+    const uint32_t w_addr = tcx::smem_u32(wb);
+    const uint64_t desc1 = tcx::sdesc(w_addr + kPW1, kP1K * 16u);
+    const uint64_t desc2 = tcx::sdesc(w_addr + kPW2, kP2K * 16u);
+    const uint64_t desc3 = tcx::sdesc(w_addr + kPW3, kP2K * 16u);
+    float (*Q)[kRays] = tiles[g].Q;
+    uint32_t ph = 0, n_fb = 0;
+    bool ok = true;
+    // one layer: MMAs over K = kin from A, into D, N columns; then the group waits
+    auto layer = [&](uint64_t desc, int kin, int nout) -> bool {
+        if (leader) {
+            tcx::tc_fence_after();
+            const uint32_t idd = tcx::idesc_bf16(nout);
+            for (int kk = 0; kk < kin / 16; ++kk)
+                tcx::mma_bf16_ts(d_col, a_col + 8u * kk, desc + 16u * kk, idd, kk > 0 ? 1u : 0u);
+            tcx::mma_commit(bar_m);
+        }
+        const bool got = tcx::group_wait(bar_m, ph, bar_id, flag, leader);
+        ph ^= 1u;
+        if (got) tcx::tc_fence_after();
+        return got;
+    };
+    // relu of D columns 0..31 as the next layer's A: inputs 0..31, the constant 1 at 32
+    auto hidden_to_a = [&]() {
+        uint32_t r[32], pk[16];
+        tcx::tmem_ld32_nowait(d_row, r);
+        tcx::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) pk[i] = tcx::pack_relu_bf16(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+        tcx::tmem_st16(a_row, pk);
+        uint32_t c8[8] = {tcx::pack_bf16(1.0f, 0.0f), 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        tcx::tmem_st8(a_row + 16u, c8);
+        tcx::tmem_st_wait();
+        tcx::tc_fence_before();
+        tcx::wg_bar(bar_id);
+    };
+    const uint32_t n_tiles = (n + kRays - 1) / kRays;
+    for (uint32_t tile = blockIdx.x * kPTcGroups + g; tile < n_tiles && ok; tile += gridDim.x * kPTcGroups) {
+        const uint32_t r = tile * kRays + t;
+        float o[3] = {0.f, 0.f, 0.f}, d[3] = {1.f, 0.f, 0.f}, t0 = 0.f, t1 = 0.f;
+        bool hit = false;
+        if (r < n) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o[a] = __ldg(ro + 3 * (size_t)r + a);
+                d[a] = __ldg(rd + 3 * (size_t)r + a);
+            }
+            const float box[6] = {b0, b1, b2, b3, b4, b5};
+            hit = root_slab(box, o, d, t0, t1);
+            if (!hit) t0 = t1 = 0.f;
+        }
+        if (!group_any(g, hit)) {  // no crossings in this tile: nothing to keep
+            if (r < n) {
+                mask[r] = 0ull;
+                fallback[r] = 0;
+            }
+            continue;
+        }
+        {  // layer-1 input: gamma_10(o + t0 d) ++ gamma_4(d) as BF16, the constant 1 at 90
+            float e[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) e[a] = __fadd_rn(o[a], __fmul_rn(t0, d[a]));
+            float f[PIN];
+            tcx::encode_freq<10, 0>(e, f);
+            tcx::encode_freq<4, 63>(d, f);
+            tcx::store_chunk<0>(a_row, f);
+            tcx::store_chunk<1>(a_row, f);
+            tcx::store_chunk<2>(a_row, f);
+            tcx::tmem_st_wait();
+            tcx::tc_fence_before();
+            tcx::wg_bar(bar_id);
+        }
+        if (!(ok = layer(desc1, kP1K, PH))) break;
+        hidden_to_a();
+        if (!(ok = layer(desc2, kP2K, PH))) break;
+        hidden_to_a();
+        if (!(ok = layer(desc3, kP2K, kP3N))) break;
+        // logits 0..64 -> this ray's column of Q, then the softmax in place
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            uint32_t v[32];
+            tcx::tmem_ld32_nowait(d_row + 32u * c, v);  // columns 80..95 (A) are read but not used
+            tcx::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (32 * c + i < PO) Q[32 * c + i][t] = __uint_as_float(v[i]);
+        }
+        tcx::tc_fence_before();
+        tcx::wg_bar(bar_id);  // every row has read D before the next tile's MMAs
+        if (r < n) {
+            float m = -INFINITY;
+#pragma unroll
+            for (int b = 0; b < PO; ++b) m = fmaxf(m, Q[b][t]);
+            float sum = 0.0f;
+#pragma unroll
+            for (int b = 0; b < PO; ++b) {
+                const float ex = __expf(Q[b][t] - m);
+                Q[b][t] = ex;
+                sum += ex;
+            }
+            const float inv = 1.0f / sum;
+#pragma unroll
+            for (int b = 0; b < PO; ++b) Q[b][t] *= inv;
+            uint64_t mk = 0;
+            bool fb = select_bins(Q, Q, t, coverage, max_bins, mk);
+            if (!hit) fb = false;
+            mask[r] = fb ? ~0ull : mk;
+            fallback[r] = fb ? 1 : 0;
+            n_fb += fb ? 1u : 0u;
+        }
+    }
+    if (!ok && leader) atomicCAS(err, 0, kDevErrTimeout);
+    n_fb = __reduce_add_sync(0xffffffffu, n_fb);
+    if ((threadIdx.x & 31) == 0 && n_fb) atomicAdd(n_fallback, (unsigned long long)n_fb);
+    tcx::tc_fence_before();
+    __syncthreads();
+    tcx::tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
 // splitmix64 finaliser: the ray index of batch element i of step s.
 __device__ __forceinline__ uint32_t batch_ray(uint64_t seed, uint64_t s, uint32_t i, uint32_t n) {
     uint64_t z = seed + 0x9E3779B97F4A7C15ull * (s * 0x100000001ull + i + 1);
@@ -528,8 +731,28 @@ cudaError_t launch_prop_infer(cudaStream_t s, int infer_grid, const float* param
     return cudaGetLastError();
 }
 
+cudaError_t launch_prop_infer_tc(cudaStream_t s, const float* params, const float root_box[6], const float* ro,
+                                 const float* rd, uint32_t n, float coverage, int max_bins, uint64_t* mask,
+                                 uint8_t* fallback, unsigned long long* n_fallback, int* err) {
+    if (n == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t tiles = (n + kRays - 1) / kRays;
+    const uint32_t ctas = (tiles + kPTcGroups - 1) / kPTcGroups;
+    const unsigned grid = ctas < (uint32_t)sms ? ctas : (unsigned)sms;  // one CTA per SM (it holds all of TMEM)
+    k_prop_infer_tc<<<grid, 128 * kPTcGroups, kPTcSmem, s>>>(params, root_box[0], root_box[1], root_box[2],
+                                                              root_box[3], root_box[4], root_box[5], ro, rd, n,
+                                                              coverage, max_bins, mask, fallback, n_fallback, err);
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_proposal(int* infer_grid) {
     cudaError_t e = cudaFuncSetAttribute(k_prop_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem);
+    if (e != cudaSuccess) return e;
+    // the tensor-core inference holds more than half of an SM's shared memory, so two of
+    // its CTAs never share an SM (each allocates the whole TMEM)
+    e = cudaFuncSetAttribute(k_prop_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPTcSmem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;

@@ -161,6 +161,36 @@ def test_masked_render_matches_oracle_with_the_same_masks(R):
         assert np.abs(opac - ref["opacity"])[ok].max() <= 1e-5
 
 
+def test_render_masks_from_tensor_cores_agree_with_fp32_predictions(R):
+    """Renders select the kept bins from the BF16 tensor-core network; the FP32
+    predictions (amnerf_proposal_predict) pick the same bins for most rays -- the rest
+    are rays whose selection sits on a near-tie of the sorted walk."""
+    from paper_2310_01881_gb300 import amnerf
+    cfg, tree, P = _c1(R)
+    amnerf.amnerf_proposal_set(R.ctx, S.proposal_init(5) * 3.0)
+    o, d = S.view_rays(cfg, 0, 2, 48, 48)
+    n = len(o)
+    do, dd = _dev(o), _dev(d)
+    q = torch.empty((n, 65), device="cuda")
+    mask = torch.empty(n, dtype=torch.int64, device="cuda")
+    fb = torch.empty(n, dtype=torch.uint8, device="cuda")
+    _, _, hit = O.root_interval(tree, o, d, mode=1)
+    for cov, mb in ((0.99, 16), (0.6, 64), (0.9, 8)):
+        amnerf.amnerf_proposal_predict(R.ctx, do, dd, q, mask, fb, coverage=cov, max_bins=mb)
+        *_, dbg, st = R.render_debug(do, dd, cfg.steps, cfg.cap, proposal=True, coverage=cov, max_bins=mb)
+        m32 = mask.cpu().numpy().view(np.uint64)[hit]
+        f32 = fb.cpu().numpy()[hit]
+        mtc = dbg["prop_mask"][hit]
+        ftc = dbg["prop_fallback"][hit]
+        same = (m32 == mtc) & (f32 == ftc)
+        print(f"coverage {cov}, max bins {mb}: {same.mean():.4f} of hit rays select the same bins")
+        assert same.mean() >= 0.85, (cov, mb, same.mean())
+        # where they differ, the kept sets still overlap
+        diff = ~same & (f32 == 0) & (ftc == 0)
+        if diff.any():
+            assert np.mean((m32[diff] & mtc[diff]) != 0) >= 0.9
+
+
 def test_training_gain_on_dense_config1_scene(R):
     """Proposal trained on plain-rendered views of the config-1 scene with every density
     x10 (BF16 leaves), evaluated on held-out views at coverage 0.95: samples per ray
