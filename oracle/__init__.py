@@ -17,6 +17,12 @@ Parity status per function (what pins it is in tests/test_oracle_pins.py):
   mlp_eval    pinned: numpy float64 matmul chain; zero-weight closed form.
   render      pinned: constant-density closed form, sum(w) + T = 1, midpoint-rule
               depth limit, early termination.
+Proposal sampler (pins in tests/test_oracle_proposal.py):
+  prop_loss_grad  pinned: central finite differences; entropy closed form at q = p.
+  prop_adam       pinned: first step from zero moments moves by lr against sign(g).
+  prop_select     pinned: hand-worked cases (ties, background, fallback); binary32
+                  mode: absorption of masses below half an ulp of the sum.
+  masked render   pinned: all-bins mask = plain render; kept crossings by brute force.
 """
 from __future__ import annotations
 
@@ -81,7 +87,7 @@ def lib():
             _lib.or_prop_predict.argtypes = [V, V, V, V, L, V]
             _lib.or_prop_loss_grad.argtypes = [V, V, V, V, V, L, V, V]
             _lib.or_prop_adam.argtypes = [V, V, V, V, I, I, D, D, D, D]
-            _lib.or_prop_select.argtypes = [V, L, D, I, V, V]
+            _lib.or_prop_select.argtypes = [V, L, D, I, V, V, I]
     return _lib
 
 
@@ -303,8 +309,12 @@ def prop_adam(P, g, m, v, t: int, lr: float = 1e-3, b1: float = 0.9, b2: float =
     lib().or_prop_adam(_p(P), _p(g), _p(m), _p(v), len(P), t, lr, b1, b2, eps)
 
 
-def prop_select(q, coverage: float = 0.99, max_bins: int = 16):
+def prop_select(q, coverage: float = 0.99, max_bins: int = 16, single: bool = False):
+    """Kept depth bins per ray (mask) and fallback flags.  single=True keeps the
+    running sum in binary32 (q is rounded to float32 first), as the GPU kernels do."""
+    if single:
+        q = np.asarray(q, F32)
     q = np.ascontiguousarray(q, F64)
     mask = np.zeros(len(q), np.uint64); fb = np.zeros(len(q), I32)
-    lib().or_prop_select(_p(q), len(q), coverage, max_bins, _p(mask), _p(fb))
+    lib().or_prop_select(_p(q), len(q), coverage, max_bins, _p(mask), _p(fb), int(single))
     return mask, fb

@@ -1100,9 +1100,14 @@ int or_prop_adam(double *P, const double *g, double *m, double *v, int n_par, in
 /* Kept depth bins of one ray: bins are visited by decreasing predicted mass (ties
  * to the lower index); their mass is added until it reaches `coverage`; the
  * background bin counts toward coverage but is not a depth bin.  When more than
- * max_bins depth bins would be needed the ray falls back to the plain sampler. */
-int or_prop_select(const double *q, int64_t n, double coverage, int max_bins, uint64_t *mask, int *fallback)
+ * max_bins depth bins would be needed the ray falls back to the plain sampler.
+ * single != 0: the running sum is kept in binary32 (each partial sum rounded to
+ * float, compared with the float coverage), the precision in which the GPU
+ * kernels take this decision; q must then hold float values. */
+int or_prop_select(const double *q, int64_t n, double coverage, int max_bins, uint64_t *mask, int *fallback,
+                   int single)
 {
+    const double cov = single ? (double)(float)coverage : coverage;
     for (int64_t r = 0; r < n; r++) {
         const double *qr = q + r * OR_PO;
         int used[OR_PO] = {0};
@@ -1110,13 +1115,14 @@ int or_prop_select(const double *q, int64_t n, double coverage, int max_bins, ui
         int kept = 0;
         uint64_t mk = 0;
         int fb = 0;
-        while (cum < coverage) {
+        while (cum < cov) {
             int best = -1;
             for (int b = 0; b < OR_PO; b++)
                 if (!used[b] && (best < 0 || qr[b] > qr[best])) best = b;
             if (best < 0) break;
             used[best] = 1;
             cum += qr[best];
+            if (single) cum = (double)(float)cum;   /* a float sum of two floats, rounded once */
             if (best < 64) {
                 if (kept == max_bins) { fb = 1; break; }
                 mk |= 1ull << best;

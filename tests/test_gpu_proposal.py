@@ -105,6 +105,49 @@ def test_predictions_and_bin_selection_match_oracle(R):
         assert same.mean() >= 0.99, (cov, mb, same.mean())   # the rest sit on FP32 ties
 
 
+def test_bin_selection_is_exact_on_the_kernels_own_masses(R):
+    """The kept bins and fallbacks of the prediction kernel equal the oracle's
+    selection applied to the kernel's own FP32 probabilities with the running sum in
+    binary32, as the kernel keeps it: exact on every hit ray.  Sharp and flat
+    distributions take both the top-8 path and the full sort; duplicated output rows
+    of the last layer make groups of 2 and 4 exactly tied masses."""
+    from paper_2310_01881_gb300 import amnerf
+    cfg, tree, P = _c1(R)
+    o, d = S.view_rays(cfg, 0, 2, 64, 64)
+    n = len(o)
+    do, dd = _dev(o), _dev(d)
+    t0, t1, hit = O.root_interval(tree, o, d, mode=1)
+    q = torch.empty((n, 65), device="cuda")
+    mask = torch.empty(n, dtype=torch.int64, device="cuda")
+    fb = torch.empty(n, dtype=torch.uint8, device="cuda")
+    w3, b3 = 90 * 32 + 32 + 32 * 32 + 32, 90 * 32 + 32 + 32 * 32 + 32 + 65 * 32
+    base = S.proposal_init(5)
+    n_short = n_long = n_tied = 0
+    for scale in (0.3, 3.0, 12.0):
+        for tie in (1, 2, 4):
+            p = (base * scale).astype(np.float32)
+            W = p[w3:b3].reshape(65, 32)
+            for k in range(64):
+                W[k] = W[k - k % tie]
+                p[b3 + k] = p[b3 + k - k % tie]
+            amnerf.amnerf_proposal_set(R.ctx, p)
+            for cov, mb in ((0.99, 16), (0.6, 64), (0.9, 8), (0.95, 3), (0.5, 64), (1.0, 64)):
+                amnerf.amnerf_proposal_predict(R.ctx, do, dd, q, mask, fb, coverage=cov, max_bins=mb)
+                qg = q.cpu().numpy()
+                m_ref, f_ref = O.prop_select(qg, cov, mb, single=True)
+                mg = mask.cpu().numpy().view(np.uint64)
+                fg = fb.cpu().numpy().astype(np.int32)
+                assert (fg[~hit] == 0).all()
+                bad = np.nonzero((mg[hit] != m_ref[hit]) | (fg[hit] != f_ref[hit]))[0]
+                assert len(bad) == 0, (scale, tie, cov, mb, len(bad), np.nonzero(hit)[0][bad[:4]])
+                kept = np.array([bin(int(m)).count("1") for m in m_ref[hit]])
+                n_short += int(((kept <= 8) & (f_ref[hit] == 0)).sum())
+                n_long += int(((kept > 8) | (f_ref[hit] == 1)).sum())
+                if tie > 1:
+                    n_tied += int((kept % tie != 0).sum())   # a tie group split by the walk
+    assert n_short > 1000 and n_long > 1000 and n_tied > 100, (n_short, n_long, n_tied)
+
+
 def _splitmix_batch(seed, step, B, n):
     """Ray indices of one training minibatch: splitmix64 of seed + golden * (step * 2^32
     + step + i + 1) (Steele, Lea and Flood, 2014), modulo n."""

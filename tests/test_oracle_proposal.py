@@ -100,6 +100,25 @@ def test_bin_selection_hand_cases():
     assert mask[3] == (1 << 1) | (1 << 2) and fb[3] == 0
     m2, f2 = O.prop_select(q[2:3], 0.99, 64)
     assert f2[0] == 0 and bin(int(m2[0])).count("1") == 64
+    # the same decisions with the running sum in binary32: the margins are wide
+    ms, fs = O.prop_select(q, 0.99, 16, single=True)
+    assert (ms == mask).all() and (fs == fb).all()
+
+
+def test_bin_selection_binary32_sum_absorbs_small_masses():
+    """In binary32 an increment below half an ulp of the running sum is lost: after
+    bin 0 (0.5), masses of 2^-26 leave the sum at 0.5, so a coverage of 0.5 + 2^-24
+    is never reached and the ray runs past max_bins; in binary64 four of them reach it."""
+    q = np.zeros((1, 65))
+    q[0, 0] = 0.5
+    q[0, 1:9] = 2.0 ** -26
+    cov = 0.5 + 2.0 ** -24
+    m64, f64 = O.prop_select(q, cov, 16)
+    assert f64[0] == 0 and m64[0] == 0b11111
+    m32, f32 = O.prop_select(q, cov, 16, single=True)
+    assert f32[0] == 1 and m32[0] == np.uint64(2 ** 64 - 1)
+    m32, f32 = O.prop_select(q, cov, 64, single=True)
+    assert f32[0] == 0 and m32[0] == np.uint64(2 ** 64 - 1)   # every depth bin, zeros included
 
 
 @pytest.mark.parametrize("mode", [0, 1])
