@@ -534,32 +534,34 @@ __global__ void __launch_bounds__(128 * kPTcGroups, 1) k_prop_infer_tc(
         if (!(ok = layer(desc2, kP2K, PH))) break;
         hidden_to_a();
         if (!(ok = layer(desc3, kP2K, kP3N))) break;
-        // logits 0..64 -> this ray's column of Q, then the softmax in place
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            uint32_t v[32];
-            tcx::tmem_ld32_nowait(d_row + 32u * c, v);  // columns 80..95 (A) are read but not used
+        // logits 0..64 to registers; once every row has read D, the softmax there and
+        // the probabilities to this ray's column of Q
+        float v[PO];
+        {
+            uint32_t lo[64], bg[4];
+            tcx::tmem_ld32_nowait(d_row, lo);
+            tcx::tmem_ld32_nowait(d_row + 32u, lo + 32);
+            tcx::tmem_ld4_nowait(d_row + 64u, bg);  // columns 65..67 are read but not used
             tcx::tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-                if (32 * c + i < PO) Q[32 * c + i][t] = __uint_as_float(v[i]);
+            for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(lo[i]);
+            v[64] = __uint_as_float(bg[0]);
         }
         tcx::tc_fence_before();
         tcx::wg_bar(bar_id);  // every row has read D before the next tile's MMAs
         if (r < n) {
             float m = -INFINITY;
 #pragma unroll
-            for (int b = 0; b < PO; ++b) m = fmaxf(m, Q[b][t]);
+            for (int b = 0; b < PO; ++b) m = fmaxf(m, v[b]);
             float sum = 0.0f;
 #pragma unroll
             for (int b = 0; b < PO; ++b) {
-                const float ex = __expf(Q[b][t] - m);
-                Q[b][t] = ex;
-                sum += ex;
+                v[b] = __expf(v[b] - m);
+                sum += v[b];
             }
             const float inv = 1.0f / sum;
 #pragma unroll
-            for (int b = 0; b < PO; ++b) Q[b][t] *= inv;
+            for (int b = 0; b < PO; ++b) Q[b][t] = v[b] * inv;
             uint64_t mk = 0;
             bool fb = select_bins(Q, Q, t, coverage, max_bins, mk);
             if (!hit) fb = false;
