@@ -362,7 +362,8 @@ AMNERF_API amnerf_status amnerf_proposal_grad(amnerf_ctx *ctx, const float *rays
                                               float *loss);
 
 /* Inference only: softmax outputs (DEVICE float [n_rays][65], may be NULL), kept-bin
- * masks (DEVICE uint64 [n_rays]) and fallback flags (DEVICE uint8 [n_rays]). */
+ * masks (DEVICE uint64 [n_rays]) and fallback flags (DEVICE uint8 [n_rays]).  A ray
+ * that misses the scene box gets mask 0 and no fallback. */
 AMNERF_API amnerf_status amnerf_proposal_predict(amnerf_ctx *ctx, const float *rays_o, const float *rays_d,
                                                  int64_t n_rays, float coverage, int max_bins, float *probs,
                                                  uint64_t *mask, uint8_t *fallback);

@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kRays * kInferGroups, 1) k_prop_infer(
             uint64_t mk = 0;
             bool fb = select_bins(T.B, T.A, t, coverage, max_bins, mk);
             if (!hit) fb = false;
-            mask[r] = fb ? ~0ull : mk;
+            mask[r] = fb ? ~0ull : (hit ? mk : 0ull);  // a ray that misses the box keeps nothing
             fallback[r] = fb ? 1 : 0;
             n_fb += fb ? 1u : 0u;
         }
@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(128 * kPTcGroups, 1) k_prop_infer_tc(
             uint64_t mk = 0;
             bool fb = select_bins(Q, Q, t, coverage, max_bins, mk);
             if (!hit) fb = false;
-            mask[r] = fb ? ~0ull : mk;
+            mask[r] = fb ? ~0ull : (hit ? mk : 0ull);  // a ray that misses the box keeps nothing
             fallback[r] = fb ? 1 : 0;
             n_fb += fb ? 1u : 0u;
         }

@@ -137,7 +137,7 @@ def test_bin_selection_is_exact_on_the_kernels_own_masses(R):
                 m_ref, f_ref = O.prop_select(qg, cov, mb, single=True)
                 mg = mask.cpu().numpy().view(np.uint64)
                 fg = fb.cpu().numpy().astype(np.int32)
-                assert (fg[~hit] == 0).all()
+                assert (fg[~hit] == 0).all() and (mg[~hit] == 0).all()
                 bad = np.nonzero((mg[hit] != m_ref[hit]) | (fg[hit] != f_ref[hit]))[0]
                 assert len(bad) == 0, (scale, tie, cov, mb, len(bad), np.nonzero(hit)[0][bad[:4]])
                 kept = np.array([bin(int(m)).count("1") for m in m_ref[hit]])
@@ -202,6 +202,40 @@ def test_masked_render_matches_oracle_with_the_same_masks(R):
         ok = ref["ert_margin"] > 1e-3
         assert np.abs(rgb - ref["rgb"]).max(axis=1)[ok].max() <= 1e-5
         assert np.abs(opac - ref["opacity"])[ok].max() <= 1e-5
+
+
+def test_full_view_proposal_render_sampled_against_oracle(R):
+    """One 1920x1080 view (2.07 M rays, a view of the proposal benchmark) in the launch
+    configuration the benchmark times.  The render's own kept-bin masks, read back,
+    drive the FP32-mode oracle on a seeded sample of rays: pixels within 1e-5 (FP32
+    leaves).  The fallback count matches the stats and rays that miss keep nothing."""
+    from paper_2310_01881_gb300 import amnerf
+    cfg, tree, P = _c1(R)
+    amnerf.amnerf_proposal_set(R.ctx, S.proposal_init(11) * 3.0)
+    o, d = S.view_rays(cfg, 0, 1, 1920, 1080)
+    n = len(o)
+    do, dd = _dev(o), _dev(d)
+    rgb = torch.empty((n, 3), device="cuda")
+    depth = torch.empty(n, device="cuda")
+    opac = torch.empty(n, device="cuda")
+    _, _, hit = O.root_interval(tree, o, d, mode=1)
+    idx = S.ray_subset(n, 600, 7)
+    for cov, mb in ((0.95, 64), (0.99, 16)):
+        dbg = {"prop_mask": torch.zeros(n, dtype=torch.int64, device="cuda"),
+               "prop_fallback": torch.zeros(n, dtype=torch.uint8, device="cuda")}
+        st = amnerf.amnerf_render_debug(R.ctx, do, dd, rgb, depth, opac, dbg, steps=cfg.steps, cap=cfg.cap,
+                                        proposal=True, coverage=cov, max_bins=mb)
+        mask = dbg["prop_mask"].cpu().numpy().view(np.uint64)
+        fb = dbg["prop_fallback"].cpu().numpy().astype(np.int32)
+        assert st["fallback_rays"] == int(fb.sum())
+        assert (mask[~hit] == 0).all() and (fb[~hit] == 0).all()
+        ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o[idx], d[idx], cfg.steps, cfg.cap, mode=1,
+                       mask=mask[idx], fallback=fb[idx])
+        ok = ref["ert_margin"] > 1e-3
+        assert ok.mean() > 0.9
+        assert np.abs(rgb.cpu().numpy()[idx] - ref["rgb"]).max(axis=1)[ok].max() <= 1e-5
+        assert np.abs(opac.cpu().numpy()[idx] - ref["opacity"])[ok].max() <= 1e-5
+        assert np.abs(depth.cpu().numpy()[idx] - ref["depth"])[ok].max() <= 1e-5
 
 
 def test_render_masks_from_tensor_cores_agree_with_fp32_predictions(R):
