@@ -141,7 +141,9 @@ def workload_name(cfg, args) -> str:
             + f", {cfg.hidden}x{cfg.width} MLP per leaf, {cfg.steps} samples/crossing, cap {cfg.cap}"
             + (f", stratified jitter (seed {args.jitter})" if getattr(args, "jitter", 0) else "")
             + (f", empty-space skipping (density > {args.skip_empty:g})"
-               if getattr(args, "skip_empty", None) is not None else ""))
+               if getattr(args, "skip_empty", None) is not None else "")
+            + (f", early ray termination in waves of {args.ert_wave} crossings"
+               if getattr(args, "ert_wave", 0) else ""))
 
 
 def barrier():
@@ -230,9 +232,10 @@ def run_ours(args):
                 continue
             raise
         for _ in range(args.warmup):
-            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter, skip_empty=args.skip_empty)
+            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter, skip_empty=args.skip_empty,
+                     ert_wave=args.ert_wave)
         _, _, _, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter,
-                                 skip_empty=args.skip_empty)
+                               skip_empty=args.skip_empty, ert_wave=args.ert_wave)
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -240,7 +243,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             e0.record(stream)
             for _ in range(args.steps):
-                R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter, skip_empty=args.skip_empty)
+                R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter, skip_empty=args.skip_empty,
+                         ert_wave=args.ert_wave)
             e1.record(stream)
             torch.cuda.synchronize()
         barrier()
@@ -251,7 +255,7 @@ def run_ours(args):
         stage = np.zeros(4)
         for _ in range(args.steps):
             *_, s2 = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter,
-                                 skip_empty=args.skip_empty)
+                              skip_empty=args.skip_empty, ert_wave=args.ert_wave)
             stage += np.array(s2["ms"])
         amnerf.amnerf_set_timing(R.ctx, False)
         stage /= args.steps
@@ -276,12 +280,12 @@ def run_ours(args):
             torch.empty(n, dtype=torch.float32).pin_memory().numpy()]
     for _ in range(max(1, args.warmup)):
         amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term,
-                                  jitter=args.jitter, skip_empty=args.skip_empty)
+                                  jitter=args.jitter, skip_empty=args.skip_empty, ert_wave=args.ert_wave)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term,
-                                  jitter=args.jitter, skip_empty=args.skip_empty)
+                                  jitter=args.jitter, skip_empty=args.skip_empty, ert_wave=args.ert_wave)
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
     barrier()
 
@@ -540,8 +544,8 @@ def run_c5(args):
     stream = torch.cuda.current_stream()
     points = [(0.99, 64), (0.99, 16), (0.95, 64)]   # (coverage, max_bins); the first is the headline
 
-    def timed(prop, cov=0.99, mb=64):
-        kw = dict(out=out, proposal=prop, coverage=cov, max_bins=mb)
+    def timed(prop, cov=0.99, mb=64, waves=0):
+        kw = dict(out=out, proposal=prop, coverage=cov, max_bins=mb, ert_wave=waves)
         for _ in range(args.warmup):
             R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, **kw)
         torch.cuda.synchronize()
@@ -559,6 +563,10 @@ def run_c5(args):
     with ClockSampler(0) as clk:
         ms_plain, st_plain, rgb_plain = timed(False)
         runs = [timed(True, cov, mb) for cov, mb in points]
+        # early ray termination in waves (--ert-wave W): the same renders, evaluating
+        # only the crossings before each ray's termination
+        wave_runs = [timed(prop, cov, mb, args.ert_wave) for prop, cov, mb in
+                     [(False, 0.99, 64)] + [(True, c, b) for c, b in points]] if args.ert_wave else []
     import oracle as O
     tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
     P_or = S.xavier_weights(0, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
@@ -591,6 +599,14 @@ def run_c5(args):
                                                                  3),
                                           "fallback_frac": round(float(fb.mean()), 4),
                                           "psnr_vs_plain_fp64": psnr(bound["rgb"], ref["rgb"])}})
+    waves = []
+    for i, (ms, st, rgb) in enumerate(wave_runs):
+        ref_rgb = rgb_plain if i == 0 else runs[i - 1][2]
+        waves.append({"sampler": "plain" if i == 0 else f"proposal {points[i - 1][0]}/{points[i - 1][1]}",
+                      "ert_wave": args.ert_wave, "ms": round(ms, 3), "Mrays/s": round(n / (ms * 1e-3) / 1e6, 3),
+                      "evaluated_per_ray": round(st["samples_evaluated"] / n, 3),
+                      "generated_per_ray": spr(st), "composited_per_ray": round(st["samples_composited"] / n, 3),
+                      "identical_to_one_pass": bool(np.array_equal(rgb, ref_rgb))})
     head = res[0]
     line = {
         "metric": "Mrays/s and samples per ray (learned proposal vs plain sampler)",
@@ -607,6 +623,7 @@ def run_c5(args):
                   "samples_per_ray": spr(st_plain), "psnr_vs_fp64": p_plain,
                   "composited_frac": round(st_plain["samples_composited"] / max(st_plain["samples_generated"], 1), 4)},
         "proposal": res,
+        **({"ert_waves": waves} if waves else {}),
         "spr_reduction": head["spr_reduction"],
         "delta_psnr_vs_fp64_db": head["delta_psnr_vs_fp64_db"],
         "training": {"rays": n_tr, "steps": args.train_steps, "batch": 8192, "lr": 3e-3,
@@ -674,6 +691,8 @@ def main():
     ap.add_argument("--px", type=int, default=None, help="square image size (default: the config's)")
     ap.add_argument("--skip-empty", type=float, default=None,
                     help="empty-space skipping: density threshold of the guidance grid (c1/c2); default off")
+    ap.add_argument("--ert-wave", type=int, default=0,
+                    help="early ray termination in waves of this many crossings (0: one pass)")
     ap.add_argument("--jitter", type=int, default=0,
                     help="sample placement: 0 = stratum midpoints, else the stratified jitter's seed (c1/c2)")
     args = ap.parse_args()

@@ -133,6 +133,16 @@ typedef struct {
      * count toward max_samples. */
     int skip_empty;
     float empty_threshold;
+    /* Early ray termination in waves: 0 = one pass (every generated sample goes
+     * through the network; compositing stops at T < t_term).  W in [1, 255] (needs
+     * steps_per_leaf = 8): crossings k in [0, W), [W, 2W), ... are grouped, evaluated
+     * and composited wave by wave, each wave only for the rays whose transmittance
+     * has not dropped below t_term, so samples behind an opaque part of the ray are
+     * not evaluated.  Pixels are bit-identical to the one-pass render.  The number of
+     * waves is ceil(floor(max_samples / 8) / W), fixed by the parameters (no host
+     * synchronisation).  With debug output, counts, offsets and order describe the
+     * last wave; stage times put the whole wave loop under the network step. */
+    int ert_wave;
 } amnerf_render_params;
 
 /* Schedule of the network step's tiles over the persistent workers (warpgroups). */
@@ -157,10 +167,12 @@ typedef struct {
     uint64_t crossings;           /* leaf crossings kept after the cap */
     uint64_t samples_generated;   /* steps_per_leaf x crossings */
     uint64_t samples_composited;  /* samples reached before early termination */
-    uint64_t tiles;               /* network tiles of 128 samples launched */
+    uint64_t tiles;               /* network tiles of 128 samples launched (all waves) */
     uint64_t fallback_rays;       /* proposal sampler: rays that used the plain sampler */
     float ms[4];                  /* stage times: traverse, group, network, composite */
     float proposal_ms;            /* proposal inference (part of ms[0]); 0 without the proposal */
+    uint64_t samples_evaluated;   /* samples through the network: samples_generated, or
+                                     fewer with ert_wave */
 } amnerf_stats;
 
 /* Optional copies of the intermediate results of one render (all DEVICE pointers

@@ -48,7 +48,7 @@ class amnerf_render_params(ctypes.Structure):
     _fields_ = [("steps_per_leaf", ctypes.c_int), ("max_samples", ctypes.c_int), ("t_term", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("use_proposal", ctypes.c_int), ("coverage", ctypes.c_float),
                 ("max_bins", ctypes.c_int), ("jitter_seed", ctypes.c_uint64), ("skip_empty", ctypes.c_int),
-                ("empty_threshold", ctypes.c_float)]
+                ("empty_threshold", ctypes.c_float), ("ert_wave", ctypes.c_int)]
 
 
 PROPOSAL_PARAMS = 6113
@@ -64,12 +64,14 @@ class amnerf_tuning(ctypes.Structure):
 class amnerf_stats(ctypes.Structure):
     _fields_ = [("rays", ctypes.c_uint64), ("crossings", ctypes.c_uint64), ("samples_generated", ctypes.c_uint64),
                 ("samples_composited", ctypes.c_uint64), ("tiles", ctypes.c_uint64),
-                ("fallback_rays", ctypes.c_uint64), ("ms", ctypes.c_float * 4), ("proposal_ms", ctypes.c_float)]
+                ("fallback_rays", ctypes.c_uint64), ("ms", ctypes.c_float * 4), ("proposal_ms", ctypes.c_float),
+                ("samples_evaluated", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {"rays": self.rays, "crossings": self.crossings, "samples_generated": self.samples_generated,
                 "samples_composited": self.samples_composited, "tiles": self.tiles,
-                "fallback_rays": self.fallback_rays, "ms": list(self.ms), "proposal_ms": self.proposal_ms}
+                "fallback_rays": self.fallback_rays, "ms": list(self.ms), "proposal_ms": self.proposal_ms,
+                "samples_evaluated": self.samples_evaluated}
 
 
 class amnerf_debug(ctypes.Structure):
@@ -229,19 +231,20 @@ def amnerf_calibrate_fp8(ctx, o, d, n_leaves: int, hidden: int, steps: int = 8, 
 
 
 def _params(steps: int, cap: int, t_term: float, bg, proposal: bool = False, coverage: float = 0.99,
-            max_bins: int = 16, jitter: int = 0, skip_empty=None) -> amnerf_render_params:
+            max_bins: int = 16, jitter: int = 0, skip_empty=None, ert_wave: int = 0) -> amnerf_render_params:
     """jitter: 0 = samples at stratum midpoints, else the seed of the stratified jitter.
-    skip_empty: None, or the density threshold of empty-space skipping."""
+    skip_empty: None, or the density threshold of empty-space skipping.
+    ert_wave: 0 = one pass, else crossings per wave of early ray termination."""
     return amnerf_render_params(steps, cap, t_term, (ctypes.c_float * 3)(*bg), int(proposal), coverage, max_bins,
                                 int(jitter) & ((1 << 64) - 1), int(skip_empty is not None),
-                                float(skip_empty) if skip_empty is not None else 0.0)
+                                float(skip_empty) if skip_empty is not None else 0.0, int(ert_wave))
 
 
 def amnerf_render(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
                   bg=(0.0, 0.0, 0.0), stats: bool = False, proposal: bool = False, coverage: float = 0.99,
-                  max_bins: int = 16, jitter: int = 0, skip_empty=None):
+                  max_bins: int = 16, jitter: int = 0, skip_empty=None, ert_wave: int = 0):
     """Enqueue a render of CUDA tensors o, d (n, 3) into rgb (n, 3), depth, opacity (n,)."""
-    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter, skip_empty)
+    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter, skip_empty, ert_wave)
     sp = amnerf_stats() if stats else None
     st = load().amnerf_render(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
                               _ptr(opacity), ctypes.byref(sp) if sp is not None else None)
@@ -251,8 +254,9 @@ def amnerf_render(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64,
 
 def amnerf_render_debug(ctx, o, d, rgb, depth, opacity, dbg: dict, steps: int = 8, cap: int = 64,
                         t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), stats: bool = True, proposal: bool = False,
-                        coverage: float = 0.99, max_bins: int = 16, jitter: int = 0, skip_empty=None):
-    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter, skip_empty)
+                        coverage: float = 0.99, max_bins: int = 16, jitter: int = 0, skip_empty=None,
+                        ert_wave: int = 0):
+    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter, skip_empty, ert_wave)
     db = amnerf_debug(*[_ptr(dbg.get(k)) for k, _ in amnerf_debug._fields_])
     sp = amnerf_stats() if stats else None
     st = load().amnerf_render_debug(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
@@ -263,12 +267,13 @@ def amnerf_render_debug(ctx, o, d, rgb, depth, opacity, dbg: dict, steps: int = 
 
 def amnerf_render_host(ctx, o: np.ndarray, d: np.ndarray, rgb: np.ndarray, depth: np.ndarray,
                        opacity: np.ndarray, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
-                       bg=(0.0, 0.0, 0.0), stats: bool = False, jitter: int = 0, skip_empty=None):
+                       bg=(0.0, 0.0, 0.0), stats: bool = False, jitter: int = 0, skip_empty=None,
+                       ert_wave: int = 0):
     """Render from HOST arrays (page-locked buffers make the copies asynchronous)."""
     for a in (o, d, rgb, depth, opacity):
         if a.dtype != np.float32 or not a.flags.c_contiguous:
             raise ValueError("host buffers must be contiguous float32")
-    p = _params(steps, cap, t_term, bg, jitter=jitter, skip_empty=skip_empty)
+    p = _params(steps, cap, t_term, bg, jitter=jitter, skip_empty=skip_empty, ert_wave=ert_wave)
     sp = amnerf_stats() if stats else None
     st = load().amnerf_render_host(ctx, _hptr(o), _hptr(d), o.shape[0], ctypes.byref(p), _hptr(rgb),
                                    _hptr(depth), _hptr(opacity), ctypes.byref(sp) if sp is not None else None)
@@ -423,7 +428,7 @@ class Renderer:
         return amnerf_calibrate_fp8(self.ctx, o, d, self.n_leaves, hidden, steps=steps, cap=cap, t_term=t_term)
 
     def render(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0), stats=False, out=None,
-               proposal=False, coverage=0.99, max_bins=16, jitter=0, skip_empty=None):
+               proposal=False, coverage=0.99, max_bins=16, jitter=0, skip_empty=None, ert_wave=0):
         torch = self._torch
         n = o.shape[0]
         if out is None:
@@ -433,11 +438,11 @@ class Renderer:
         amnerf_set_stream(self.ctx, torch.cuda.current_stream(o.device).cuda_stream)
         s = amnerf_render(self.ctx, o, d, *out, steps=steps, cap=cap, t_term=t_term, bg=bg, stats=stats,
                           proposal=proposal, coverage=coverage, max_bins=max_bins, jitter=jitter,
-                          skip_empty=skip_empty)
+                          skip_empty=skip_empty, ert_wave=ert_wave)
         return (*out, s) if stats else out
 
     def render_debug(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0), proposal=False, coverage=0.99,
-                     max_bins=16, jitter=0, skip_empty=None):
+                     max_bins=16, jitter=0, skip_empty=None, ert_wave=0):
         torch = self._torch
         n = o.shape[0]
         maxc = cap // steps
@@ -461,7 +466,7 @@ class Renderer:
         amnerf_set_stream(self.ctx, torch.cuda.current_stream(dev).cuda_stream)
         s = amnerf_render_debug(self.ctx, o, d, rgb, depth, opac, dbg, steps=steps, cap=cap, t_term=t_term, bg=bg,
                                 proposal=proposal, coverage=coverage, max_bins=max_bins, jitter=jitter,
-                                skip_empty=skip_empty)
+                                skip_empty=skip_empty, ert_wave=ert_wave)
         host = {k: v.cpu().numpy() for k, v in dbg.items()}
         host["leaf"] = host["leaf"].view(np.uint16).astype(np.int64).reshape(n, maxc)
         host["t_in"] = host["t_in"].reshape(n, maxc)

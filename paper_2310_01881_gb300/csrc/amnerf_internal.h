@@ -77,10 +77,17 @@ cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, ui
                             const OccArgs& occ = OccArgs());
 
 // K-b: exclusive scans (crossings and network tiles per leaf) and the grouped scatter.
+// acc (may be NULL) accumulates (crossings, tiles) over the waves of one render.
 cudaError_t launch_scan(cudaStream_t s, const uint32_t* counts, int n_leaves, int cpt, uint32_t* offsets,
-                        uint32_t* tile_off, uint32_t* cursor, uint64_t* stats);
+                        uint32_t* tile_off, uint32_t* cursor, uint64_t* stats, uint64_t* acc = nullptr);
+// Crossing k of ray r takes part when k_lo <= k < min(n_x[r], k_hi) and alive[r]
+// (alive == NULL: every ray); the defaults select every crossing.
 cudaError_t launch_scatter(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
-                           uint32_t* cursor, uint32_t* order, int n_leaves);
+                           uint32_t* cursor, uint32_t* order, int n_leaves, int k_lo = 0, int k_hi = 256,
+                           const uint8_t* alive = nullptr);
+// Per-leaf totals of the crossings that take part (added to counts, zeroed by the caller).
+cudaError_t launch_count_wave(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
+                              int k_lo, int k_hi, const uint8_t* alive, uint32_t* counts, int n_leaves);
 
 // Tile schedules of the network kernels (values of amnerf_tuning.schedule).
 constexpr int kSchedContiguous = 0;   // worker w takes tiles [w * per, (w + 1) * per)
@@ -132,11 +139,15 @@ size_t simt_leaf_stride_floats(int width, int hidden, int k0);
 // slot_half: slot_out holds 4 x FP16 per sample (sigma, r, g, b), else float4.
 // jitter != 0: samples at the stratified jitter of that seed (ro, rd: the rays, for
 // their keys); 0: stratum midpoints (ro, rd unused).
+// Waves (st_c != NULL; 8 samples per crossing, no bins): crossings k_lo <= k < k_hi
+// only, resuming from and storing the per-ray state (st_c: rgb, T; st_d: depth) and
+// whether the ray goes on (alive).
 cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* xing, const void* slot_out,
                              int slot_half, uint32_t n, int steps, int maxc, int cap, float t_term, float bg0,
                              float bg1, float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
                              uint64_t jitter, const float* ro, const float* rd,
-                             const float2* root = nullptr, float* bins = nullptr);
+                             const float2* root = nullptr, float* bins = nullptr, int k_lo = 0, int k_hi = 256,
+                             float4* st_c = nullptr, float* st_d = nullptr, uint8_t* alive = nullptr);
 // The generated slots (j < n_x[r] * steps) of 4 x FP16 per-sample outputs as float4.
 cudaError_t launch_slots_to_f32(cudaStream_t s, const uint8_t* n_x, const void* slot_half, float4* out, uint32_t n,
                                 int steps, int cap);

@@ -14,6 +14,8 @@
 
 using namespace amnerf;
 
+constexpr int kStatSlots = 10;  // device statistics words (see amnerf_ctx::d_stats)
+
 struct amnerf_ctx {
     int device = 0;
     int sm_count = 0;
@@ -37,7 +39,9 @@ struct amnerf_ctx {
     uint32_t* d_offsets = nullptr;
     uint32_t* d_tile_off = nullptr;
     uint32_t* d_cursor = nullptr;
-    uint64_t* d_stats = nullptr;  // [0] crossings [1] tiles [2] composited
+    // [0] crossings [1] tiles [2] composited [3] fallback rays [4] [5] one wave's
+    // crossings and tiles [6] dynamic tile counter [8] [9] crossings and tiles over waves
+    uint64_t* d_stats = nullptr;
     int* d_err = nullptr;
     // per-ray scratch
     size_t cap_slots = 0;   // n_rays * maxc capacity
@@ -68,6 +72,11 @@ struct amnerf_ctx {
     uint64_t* d_mask = nullptr;
     uint8_t* d_fallback = nullptr;
     float2* d_root = nullptr;
+    // wave-by-wave rendering (early ray termination): per-ray state between waves
+    size_t cap_wave_rays = 0;
+    float4* d_wst_c = nullptr;  // rgb, T
+    float* d_wst_d = nullptr;   // depth
+    uint8_t* d_alive = nullptr;
     // E4M3 static activation scales; FP32-path calibration output while calibrating
     bool act_static = false;
     float* d_amax = nullptr;   // [n_leaves][hidden]
@@ -153,6 +162,8 @@ amnerf_status check_params(amnerf_ctx* ctx, const amnerf_render_params* p, int64
     }
     if ((uint64_t)n * (uint64_t)maxc >= (1ull << 32))
         return fail(ctx, AMNERF_E_INVAL, "n_rays * floor(max_samples / steps_per_leaf) must be < 2^32 (split the batch)");
+    if (p->ert_wave < 0 || p->ert_wave > 255) return fail(ctx, AMNERF_E_INVAL, "ert_wave must be in [0, 255]");
+    if (p->ert_wave > 0 && st != 8) return fail(ctx, AMNERF_E_INVAL, "ert_wave needs steps_per_leaf = 8");
     return AMNERF_OK;
 }
 
@@ -181,6 +192,23 @@ void pack_simt(const float* src, float* dst, int width, int hidden, int k0) {
 }  // namespace
 
 // Per-ray proposal scratch (masks, fallback flags, root intervals).
+static amnerf_status ensure_wave_scratch(amnerf_ctx* ctx, size_t n) {
+    if (n <= ctx->cap_wave_rays) return AMNERF_OK;
+    dfree(ctx->d_wst_c);
+    dfree(ctx->d_wst_d);
+    dfree(ctx->d_alive);
+    ctx->cap_wave_rays = 0;
+    cudaError_t e;
+    if ((e = cudaMalloc((void**)&ctx->d_wst_c, n * sizeof(float4))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_wst_d, n * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_alive, n)) != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "wave scratch allocation");
+    }
+    ctx->cap_wave_rays = n;
+    return AMNERF_OK;
+}
+
 static amnerf_status ensure_prop_scratch(amnerf_ctx* ctx, size_t n) {
     if (n <= ctx->cap_prop_rays) return AMNERF_OK;
     dfree(ctx->d_mask);
@@ -238,7 +266,7 @@ amnerf_status amnerf_create(amnerf_ctx** out, int device, void* cuda_stream) {
         (e = cudaMalloc((void**)&ctx->d_offsets, sizeof(uint32_t) * (kMaxLeaves + 1))) != cudaSuccess ||
         (e = cudaMalloc((void**)&ctx->d_tile_off, sizeof(uint32_t) * (kMaxLeaves + 1))) != cudaSuccess ||
         (e = cudaMalloc((void**)&ctx->d_cursor, sizeof(uint32_t) * kMaxLeaves)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&ctx->d_stats, sizeof(uint64_t) * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_stats, sizeof(uint64_t) * kStatSlots)) != cudaSuccess ||
         (e = cudaMalloc((void**)&ctx->d_err, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(ctx->d_err, 0, sizeof(int))) != cudaSuccess) {
         amnerf_destroy(ctx);
@@ -282,6 +310,9 @@ void amnerf_destroy(amnerf_ctx* ctx) {
     dfree(ctx->d_mask);
     dfree(ctx->d_fallback);
     dfree(ctx->d_root);
+    dfree(ctx->d_wst_c);
+    dfree(ctx->d_wst_d);
+    dfree(ctx->d_alive);
     for (int i = 0; i < 6; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     for (int i = 0; i < 4; ++i) {
@@ -437,7 +468,7 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
     const uint32_t nn = (uint32_t)n;
     if (ctx->timing) cudaEventRecord(ctx->ev[0], s);
     CK(cudaMemsetAsync(ctx->d_counts, 0, sizeof(uint32_t) * L, s), "memset");
-    CK(cudaMemsetAsync(ctx->d_stats, 0, sizeof(uint64_t) * 8, s), "memset");
+    CK(cudaMemsetAsync(ctx->d_stats, 0, sizeof(uint64_t) * kStatSlots, s), "memset");
     const uint64_t* mask = nullptr;
     const uint8_t* fallback = nullptr;
     if (p->use_proposal && n > 0) {
@@ -473,14 +504,25 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
     CK(launch_scan(s, ctx->d_counts, L, kTileRows / steps, ctx->d_offsets, ctx->d_tile_off, ctx->d_cursor,
                    ctx->d_stats),
        "scan launch");
-    CK(launch_scatter(s, ctx->d_nx, ctx->d_xleaf, nn, maxc, ctx->d_cursor, ctx->d_order, L), "scatter launch");
+    // waves: the rays' crossings in groups of ert_wave, each group only for the rays
+    // that have not terminated, so that samples behind an opaque crossing are never
+    // evaluated (the number of waves depends only on maxc: no host synchronisation)
+    const bool waves = p->ert_wave > 0 && n > 0 && !bins_out;
+    if (waves) {
+        st = ensure_wave_scratch(ctx, (size_t)n);
+        if (st != AMNERF_OK) return st;
+    } else {
+        CK(launch_scatter(s, ctx->d_nx, ctx->d_xleaf, nn, maxc, ctx->d_cursor, ctx->d_order, L), "scatter launch");
+    }
     if (ctx->timing) cudaEventRecord(ctx->ev[2], s);
-    if (n > 0) {
+    // the network over the grouped crossings whose per-wave counts (crossings, tiles)
+    // sit at wstats[0], wstats[1]
+    auto run_network = [&](uint64_t* wstats) -> amnerf_status {
         MlpArgs a;
         a.order = ctx->d_order;
         a.offsets = ctx->d_offsets;
         a.tile_off = ctx->d_tile_off;
-        a.stats = ctx->d_stats;
+        a.stats = wstats;
         a.n_leaves = L;
         a.xing = ctx->d_xing;
         a.ro = ro;
@@ -531,12 +573,42 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "network launch");
             }
         }
+        return AMNERF_OK;
+    };
+    if (!waves) {
+        if (n > 0) {
+            st = run_network(ctx->d_stats);
+            if (st != AMNERF_OK) return st;
+        }
+        if (ctx->timing) cudaEventRecord(ctx->ev[3], s);
+        CK(launch_composite(s, ctx->d_nx, ctx->d_xing, ctx->d_slot, ctx->desc.prec != AMNERF_FP32, nn, steps, maxc,
+                            cap, p->t_term, p->bg[0], p->bg[1], p->bg[2], rgb, depth, opacity, ctx->d_stats,
+                            p->jitter_seed, ro, rd, root_out, bins_out),
+           "composite launch");
+    } else {
+        const int W = p->ert_wave;
+        for (int k_lo = 0; k_lo < maxc; k_lo += W) {
+            const int k_hi = std::min(maxc, k_lo + W);
+            const uint8_t* alive = k_lo > 0 ? ctx->d_alive : nullptr;
+            CK(cudaMemsetAsync(ctx->d_counts, 0, sizeof(uint32_t) * L, s), "memset");
+            CK(launch_count_wave(s, ctx->d_nx, ctx->d_xleaf, nn, maxc, k_lo, k_hi, alive, ctx->d_counts, L),
+               "wave count launch");
+            CK(launch_scan(s, ctx->d_counts, L, kTileRows / steps, ctx->d_offsets, ctx->d_tile_off, ctx->d_cursor,
+                           ctx->d_stats + 4, ctx->d_stats + 8),
+               "scan launch");
+            CK(launch_scatter(s, ctx->d_nx, ctx->d_xleaf, nn, maxc, ctx->d_cursor, ctx->d_order, L, k_lo, k_hi, alive),
+               "scatter launch");
+            CK(cudaMemsetAsync(ctx->d_stats + 6, 0, sizeof(uint64_t), s), "memset");  // dynamic tile counter
+            st = run_network(ctx->d_stats + 4);
+            if (st != AMNERF_OK) return st;
+            CK(launch_composite(s, ctx->d_nx, ctx->d_xing, ctx->d_slot, ctx->desc.prec != AMNERF_FP32, nn, steps,
+                                maxc, cap, p->t_term, p->bg[0], p->bg[1], p->bg[2], rgb, depth, opacity, ctx->d_stats,
+                                p->jitter_seed, ro, rd, nullptr, nullptr, k_lo, k_hi, ctx->d_wst_c, ctx->d_wst_d,
+                                ctx->d_alive),
+               "composite launch");
+        }
+        if (ctx->timing) cudaEventRecord(ctx->ev[3], s);
     }
-    if (ctx->timing) cudaEventRecord(ctx->ev[3], s);
-    CK(launch_composite(s, ctx->d_nx, ctx->d_xing, ctx->d_slot, ctx->desc.prec != AMNERF_FP32, nn, steps, maxc, cap,
-                        p->t_term, p->bg[0], p->bg[1], p->bg[2], rgb, depth, opacity, ctx->d_stats, p->jitter_seed,
-                        ro, rd, root_out, bins_out),
-       "composite launch");
     if (ctx->timing) cudaEventRecord(ctx->ev[4], s);
 
     if (dbg && n > 0) {
@@ -574,13 +646,14 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
             CK(cudaMemcpyAsync(dbg->prop_fallback, fallback, (size_t)n, cudaMemcpyDeviceToDevice, s), "debug copy");
     }
     if (stats) {
-        uint64_t h[8];
+        uint64_t h[kStatSlots];
         CK(cudaMemcpyAsync(h, ctx->d_stats, sizeof h, cudaMemcpyDeviceToHost, s), "stats copy");
         CK(cudaStreamSynchronize(s), "stream sync");
         stats->rays = (uint64_t)n;
         stats->crossings = h[0];
         stats->samples_generated = h[0] * (uint64_t)steps;
-        stats->tiles = h[1];
+        stats->tiles = waves ? h[9] : h[1];
+        stats->samples_evaluated = (waves ? h[8] : h[0]) * (uint64_t)steps;
         stats->samples_composited = h[2];
         stats->fallback_rays = h[3];
         for (int i = 0; i < 4; ++i) {

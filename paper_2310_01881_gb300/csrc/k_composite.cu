@@ -283,18 +283,33 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
 // slots are one aligned 128-byte row piece (64 bytes as FP16), all loaded before the
 // crossing is composited, so every thread has a whole line in flight; the warp runs
 // until its last ray ends or terminates.
+// Waves (st_c != NULL): only crossings k_lo <= k < k_hi are composited.  A later wave
+// resumes from the state (rgb and T in st_c, depth in st_d) of the rays still alive,
+// and every wave stores the state, whether the ray goes on (alive), and the pixel;
+// the operations and their order are those of one pass.
 template <bool HALF, bool JIT>
 __global__ void __launch_bounds__(256) k_composite_lane(
     const uint8_t* __restrict__ n_x, const float2* __restrict__ xing, const void* __restrict__ slot_out, uint32_t n,
     int maxc, int cap, float t_term, float bg0, float bg1, float bg2, float* __restrict__ rgb,
     float* __restrict__ depth, float* __restrict__ opacity, unsigned long long* __restrict__ n_comp,
-    uint64_t jitter, const float* __restrict__ ro, const float* __restrict__ rd) {
+    uint64_t jitter, const float* __restrict__ ro, const float* __restrict__ rd, int k_lo, int k_hi,
+    float4* __restrict__ st_c, float* __restrict__ st_d, uint8_t* __restrict__ alive_io) {
     constexpr int kSteps = 8;
     const uint32_t ray = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t comp = 0;
-    if (ray < n) {
+    // a ray that ended in an earlier wave keeps its pixel
+    if (ray < n && (!st_c || k_lo == 0 || alive_io[ray])) {
         float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
-        const int nx = (int)__ldg(n_x + ray);
+        if (st_c && k_lo > 0) {
+            const float4 c = st_c[ray];
+            cr = c.x;
+            cg = c.y;
+            cb = c.z;
+            T = c.w;
+            dd = st_d[ray];
+        }
+        const int nx_all = (int)__ldg(n_x + ray);
+        const int nx = nx_all < k_hi ? nx_all : k_hi;
         uint64_t key = 0;
         if constexpr (JIT) {  // the ray's jitter key
             float o[3], d[3];
@@ -310,8 +325,8 @@ __global__ void __launch_bounds__(256) k_composite_lane(
         bool alive = true;
         // crossing k + 1's slots are loaded while crossing k is composited
         RawSlot<HALF> vn[kSteps];
-        if (nx > 0) load_crossing_now<HALF, kSteps>(slot_out, row, vn);
-        for (int k = 0; k < nx && alive; ++k) {
+        if (k_lo < nx) load_crossing_now<HALF, kSteps>(slot_out, row + (size_t)(k_lo * kSteps), vn);
+        for (int k = k_lo; k < nx && alive; ++k) {
             const float2 x = __ldg(xr + k);
             RawSlot<HALF> v[kSteps];
 #pragma unroll
@@ -343,6 +358,11 @@ __global__ void __launch_bounds__(256) k_composite_lane(
         rgb[3 * (size_t)ray + 2] = cb + T * bg2;
         depth[ray] = dd;
         opacity[ray] = 1.0f - T;
+        if (st_c) {
+            st_c[ray] = make_float4(cr, cg, cb, T);
+            st_d[ray] = dd;
+            alive_io[ray] = (!(T < t_term) && nx < nx_all) ? 1 : 0;
+        }
     }
     // composited samples: warp sums, one atomic per warp
 #pragma unroll
@@ -365,14 +385,16 @@ __global__ void k_slots_to_f32(const uint8_t* __restrict__ n_x, const void* __re
 cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* xing, const void* slot_out,
                              int slot_half, uint32_t n, int steps, int maxc, int cap, float t_term, float bg0,
                              float bg1, float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
-                             uint64_t jitter, const float* ro, const float* rd, const float2* root, float* bins) {
+                             uint64_t jitter, const float* ro, const float* rd, const float2* root, float* bins,
+                             int k_lo, int k_hi, float4* st_c, float* st_d, uint8_t* alive) {
     if (n == 0) return cudaSuccess;
+    if (st_c && (bins || steps != 8)) return cudaErrorInvalidValue;  // waves: the per-ray kernel only
     if (!bins && steps == 8) {  // one thread per ray
         auto* stc = reinterpret_cast<unsigned long long*>(stats + 2);
         const unsigned lb = (n + 255) / 256;
 #define AMNERF_LANE(H, J)                                                                                        \
     k_composite_lane<H, J><<<lb, 256, 0, s>>>(n_x, xing, slot_out, n, maxc, cap, t_term, bg0, bg1, bg2, rgb, depth, \
-                                              opacity, stc, jitter, ro, rd)
+                                              opacity, stc, jitter, ro, rd, k_lo, k_hi, st_c, st_d, alive)
         if (slot_half) {
             if (jitter) AMNERF_LANE(true, true);
             else AMNERF_LANE(true, false);

@@ -20,7 +20,8 @@ constexpr int kScanPer = kMaxLeaves / kScanThreads;  // 4 leaves per thread
 __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restrict__ counts, int n_leaves, int cpt,
                                                        uint32_t* __restrict__ offsets,
                                                        uint32_t* __restrict__ tile_off,
-                                                       uint32_t* __restrict__ cursor, uint64_t* __restrict__ stats) {
+                                                       uint32_t* __restrict__ cursor, uint64_t* __restrict__ stats,
+                                                       uint64_t* __restrict__ acc) {
     __shared__ uint32_t s_c[32], s_t[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t c[kScanPer], t[kScanPer];
@@ -82,16 +83,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
         tile_off[n_leaves] = rt;
         stats[0] = rc;  // crossings
         stats[1] = rt;  // tiles
+        if (acc) {      // running totals over the waves of one render
+            acc[0] += rc;
+            acc[1] += rt;
+        }
     }
 }
 
 constexpr int kScatterThreads = 256;
 constexpr int kScatterItems = 16;
 
+// COUNT: only the per-leaf totals (added to cursor, which then holds counts), for a
+// wave whose crossings K-a's histogram does not give.  A crossing takes part when
+// k_lo <= k < min(n_x, k_hi) and its ray is alive (alive == NULL: every ray).
+template <bool COUNT>
 __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __restrict__ n_x,
                                                              const uint16_t* __restrict__ xleaf, uint32_t n_slots,
                                                              int maxc, uint32_t* __restrict__ cursor,
-                                                             uint32_t* __restrict__ order, int n_leaves) {
+                                                             uint32_t* __restrict__ order, int n_leaves, int k_lo,
+                                                             int k_hi, const uint8_t* __restrict__ alive) {
     extern __shared__ uint32_t sm[];
     uint32_t* s_cnt = sm;
     uint32_t* s_base = sm + n_leaves;
@@ -119,7 +129,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __re
         nx[i] = 0;
         if (s < n_slots) {
             const uint32_t ray = ray_of(s);
-            nx[i] = __ldg(n_x + ray);
+            nx[i] = (!alive || __ldg(alive + ray)) ? __ldg(n_x + ray) : 0;
             lf[i] = __ldg(xleaf + s);
         }
     }
@@ -130,7 +140,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __re
         if (s < n_slots) {
             const uint32_t ray = ray_of(s);
             const uint32_t k = s - ray * (uint32_t)maxc;
-            if (k < (uint32_t)nx[i]) rk[i] = atomicAdd(&s_cnt[lf[i]], 1u);
+            if (k < (uint32_t)nx[i] && k >= (uint32_t)k_lo && k < (uint32_t)k_hi) rk[i] = atomicAdd(&s_cnt[lf[i]], 1u);
         }
     }
     __syncthreads();
@@ -138,6 +148,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __re
         const uint32_t c = s_cnt[i];
         s_base[i] = c ? atomicAdd(&cursor[i], c) : 0u;
     }
+    if (COUNT) return;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kScatterItems; ++i) {
@@ -151,20 +162,36 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __re
 }  // namespace
 
 cudaError_t launch_scan(cudaStream_t s, const uint32_t* counts, int n_leaves, int cpt, uint32_t* offsets,
-                        uint32_t* tile_off, uint32_t* cursor, uint64_t* stats) {
-    k_scan<<<1, kScanThreads, 0, s>>>(counts, n_leaves, cpt, offsets, tile_off, cursor, stats);
+                        uint32_t* tile_off, uint32_t* cursor, uint64_t* stats, uint64_t* acc) {
+    k_scan<<<1, kScanThreads, 0, s>>>(counts, n_leaves, cpt, offsets, tile_off, cursor, stats, acc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
-                           uint32_t* cursor, uint32_t* order, int n_leaves) {
+static cudaError_t scatter_launch(cudaStream_t s, bool count, const uint8_t* n_x, const uint16_t* xleaf,
+                                  uint32_t n_rays, int maxc, uint32_t* cursor, uint32_t* order, int n_leaves, int k_lo,
+                                  int k_hi, const uint8_t* alive) {
     const uint64_t n_slots = (uint64_t)n_rays * (uint64_t)maxc;
     if (n_slots == 0) return cudaSuccess;
     const uint64_t per = (uint64_t)kScatterThreads * kScatterItems;
     const unsigned blocks = (unsigned)((n_slots + per - 1) / per);
     const size_t smem = 2 * sizeof(uint32_t) * (size_t)n_leaves;
-    k_scatter<<<blocks, kScatterThreads, smem, s>>>(n_x, xleaf, (uint32_t)n_slots, maxc, cursor, order, n_leaves);
+    if (count)
+        k_scatter<true><<<blocks, kScatterThreads, smem, s>>>(n_x, xleaf, (uint32_t)n_slots, maxc, cursor, order,
+                                                              n_leaves, k_lo, k_hi, alive);
+    else
+        k_scatter<false><<<blocks, kScatterThreads, smem, s>>>(n_x, xleaf, (uint32_t)n_slots, maxc, cursor, order,
+                                                               n_leaves, k_lo, k_hi, alive);
     return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
+                           uint32_t* cursor, uint32_t* order, int n_leaves, int k_lo, int k_hi, const uint8_t* alive) {
+    return scatter_launch(s, false, n_x, xleaf, n_rays, maxc, cursor, order, n_leaves, k_lo, k_hi, alive);
+}
+
+cudaError_t launch_count_wave(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
+                              int k_lo, int k_hi, const uint8_t* alive, uint32_t* counts, int n_leaves) {
+    return scatter_launch(s, true, n_x, xleaf, n_rays, maxc, counts, nullptr, n_leaves, k_lo, k_hi, alive);
 }
 
 }  // namespace amnerf

@@ -30,8 +30,8 @@ def R():
     r.close()
 
 
-def _setup(R, cfg, seed=0, G=None, prec="fp32"):
-    grid = S.density_grid(S.scene_for(cfg.scene, seed), G or cfg.G)
+def _setup(R, cfg, seed=0, G=None, prec="fp32", scale=1.0):
+    grid = S.density_grid(S.scene_for(cfg.scene, seed), G or cfg.G) * np.float32(scale)
     nl = R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
     tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
     assert nl == tree.n_leaves
@@ -307,6 +307,81 @@ def test_skipping_with_proposal_masks_matches_oracle(R):
     np.testing.assert_array_equal(dbg["n_x"].astype(np.int64) * cfg.steps, ref["n_gen"])
     ok = ref["ert_margin"] > 1e-3
     assert np.abs(rgb - ref["rgb"]).max(axis=1)[ok].max() <= 1e-5
+
+
+@pytest.mark.parametrize("prec,jitter,scale", [("fp32", 0, 1000.0), ("bf16", 5, 1000.0), ("fp32", 3, 1.0),
+                                               ("bf16", 0, 30.0)])
+def test_waves_bit_identical_to_one_pass(R, prec, jitter, scale):
+    """Early ray termination in waves changes which samples are evaluated, not the
+    pixels: every wave size gives the one-pass render bit for bit, with the same
+    composited samples and fewer or equally many evaluated."""
+    cfg = S.CONFIGS["c1"]
+    _setup(R, cfg, 0, prec=prec, scale=scale)
+    o, d = _rays(cfg, 0, views=2)
+    do, dd = _dev(o), _dev(d)
+    *ref, st0 = R.render(do, dd, cfg.steps, cfg.cap, jitter=jitter, stats=True)
+    ref = [t.cpu().numpy() for t in ref]
+    assert st0["samples_evaluated"] == st0["samples_generated"]
+    for W in (1, 2, 3, 8):
+        *out, st = R.render(do, dd, cfg.steps, cfg.cap, jitter=jitter, stats=True, ert_wave=W)
+        for a, b in zip(ref, out):
+            np.testing.assert_array_equal(a, b.cpu().numpy())
+        assert st["samples_composited"] == st0["samples_composited"]
+        assert st["crossings"] == st0["crossings"] and st["samples_generated"] == st0["samples_generated"]
+        assert st["samples_composited"] <= st["samples_evaluated"] <= st["samples_generated"]
+
+
+def test_waves_evaluate_only_up_to_the_terminating_wave(R):
+    """On the x1000 density scene most rays end inside their first crossings.  With
+    waves of W crossings a ray is evaluated through the wave in which T drops below
+    t_term: min(n_x, W ceil(composited / (8 W))) crossings, or all n_x when it never
+    terminates.  The total matches that count from the FP32-mode oracle's composited
+    samples (rays within 1e-3 of the termination threshold may differ by their
+    crossings), and it is well below the samples generated."""
+    cfg = S.CONFIGS["c1"]
+    _, tree, P = _setup(R, cfg, 0, scale=1000.0)
+    o, d = _rays(cfg, 0)
+    do, dd = _dev(o), _dev(d)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1, threads=8)
+    comp, gen = ref["n_eval"].astype(np.int64), ref["n_gen"].astype(np.int64)
+    nx = gen // cfg.steps
+    amb = ref["ert_margin"] < 1e-3
+    for W in (1, 2):
+        per = W * cfg.steps
+        waves_run = np.where(comp < gen, (comp + per - 1) // per, -1)
+        xc = np.where(comp < gen, np.minimum(nx, waves_run * W), nx)
+        *_, st = R.render(do, dd, cfg.steps, cfg.cap, stats=True, ert_wave=W)
+        expect = int(xc.sum()) * cfg.steps
+        assert abs(st["samples_evaluated"] - expect) <= int(nx[amb].sum()) * cfg.steps
+        assert st["samples_evaluated"] < (0.9 if W == 1 else 1.0) * st["samples_generated"]
+
+
+def test_waves_with_proposal_masks_and_skipping(R):
+    """Waves run on whatever crossings the traversal kept (proposal masks, empty-space
+    skipping): the pixels are those of the one-pass render with the same options."""
+    from paper_2310_01881_gb300 import amnerf
+    cfg = S.CONFIGS["c1"]
+    _setup(R, cfg, 0, prec="bf16", scale=100.0)
+    amnerf.amnerf_proposal_set(R.ctx, S.proposal_init(11) * 3.0)
+    o, d = _rays(cfg, 0)
+    do, dd = _dev(o), _dev(d)
+    for kw in (dict(proposal=True, coverage=0.9, max_bins=64), dict(skip_empty=0.01),
+               dict(proposal=True, coverage=0.99, max_bins=16, skip_empty=0.01, jitter=9)):
+        ref = [t.cpu().numpy() for t in R.render(do, dd, cfg.steps, cfg.cap, **kw)]
+        out = [t.cpu().numpy() for t in R.render(do, dd, cfg.steps, cfg.cap, ert_wave=1, **kw)]
+        for a, b in zip(ref, out):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_wave_parameters_are_checked(R):
+    from paper_2310_01881_gb300 import amnerf
+    cfg = S.CONFIGS["c1"]
+    _setup(R, cfg, 0)
+    o = _dev(np.zeros((4, 3)))
+    for steps, cap, W in ((8, 64, 256), (8, 64, -1), (4, 64, 1)):
+        with pytest.raises(amnerf.AmnerfError) as ei:
+            R.render(o, o, steps, cap, ert_wave=W)
+        assert ei.value.status == amnerf.E_INVAL
 
 
 def test_host_buffer_entry_point_matches_device(R):
