@@ -80,14 +80,14 @@ cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, ui
 // acc (may be NULL) accumulates (crossings, tiles) over the waves of one render.
 cudaError_t launch_scan(cudaStream_t s, const uint32_t* counts, int n_leaves, int cpt, uint32_t* offsets,
                         uint32_t* tile_off, uint32_t* cursor, uint64_t* stats, uint64_t* acc = nullptr);
-// Crossing k of ray r takes part when k_lo <= k < min(n_x[r], k_hi) and alive[r]
-// (alive == NULL: every ray); the defaults select every crossing.
 cudaError_t launch_scatter(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
-                           uint32_t* cursor, uint32_t* order, int n_leaves, int k_lo = 0, int k_hi = 256,
-                           const uint8_t* alive = nullptr);
-// Per-leaf totals of the crossings that take part (added to counts, zeroed by the caller).
-cudaError_t launch_count_wave(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
-                              int k_lo, int k_hi, const uint8_t* alive, uint32_t* counts, int n_leaves);
+                           uint32_t* cursor, uint32_t* order, int n_leaves);
+// One wave: crossing k of ray r takes part when k_lo <= k < min(n_x[r], k_hi) and
+// alive[r] (alive == NULL: every ray).  count: only the per-leaf totals, added to
+// cursor (zeroed by the caller); else the grouped scatter from the scanned cursor.
+cudaError_t launch_scatter_wave(cudaStream_t s, bool count, const uint8_t* n_x, const uint16_t* xleaf,
+                                uint32_t n_rays, int maxc, int k_lo, int k_hi, const uint8_t* alive, uint32_t* cursor,
+                                uint32_t* order, int n_leaves);
 
 // Tile schedules of the network kernels (values of amnerf_tuning.schedule).
 constexpr int kSchedContiguous = 0;   // worker w takes tiles [w * per, (w + 1) * per)

@@ -591,12 +591,14 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
             const int k_hi = std::min(maxc, k_lo + W);
             const uint8_t* alive = k_lo > 0 ? ctx->d_alive : nullptr;
             CK(cudaMemsetAsync(ctx->d_counts, 0, sizeof(uint32_t) * L, s), "memset");
-            CK(launch_count_wave(s, ctx->d_nx, ctx->d_xleaf, nn, maxc, k_lo, k_hi, alive, ctx->d_counts, L),
+            CK(launch_scatter_wave(s, true, ctx->d_nx, ctx->d_xleaf, nn, maxc, k_lo, k_hi, alive, ctx->d_counts,
+                                   nullptr, L),
                "wave count launch");
             CK(launch_scan(s, ctx->d_counts, L, kTileRows / steps, ctx->d_offsets, ctx->d_tile_off, ctx->d_cursor,
                            ctx->d_stats + 4, ctx->d_stats + 8),
                "scan launch");
-            CK(launch_scatter(s, ctx->d_nx, ctx->d_xleaf, nn, maxc, ctx->d_cursor, ctx->d_order, L, k_lo, k_hi, alive),
+            CK(launch_scatter_wave(s, false, ctx->d_nx, ctx->d_xleaf, nn, maxc, k_lo, k_hi, alive, ctx->d_cursor,
+                                   ctx->d_order, L),
                "scatter launch");
             CK(cudaMemsetAsync(ctx->d_stats + 6, 0, sizeof(uint64_t), s), "memset");  // dynamic tile counter
             st = run_network(ctx->d_stats + 4);

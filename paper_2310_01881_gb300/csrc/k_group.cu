@@ -93,15 +93,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
 constexpr int kScatterThreads = 256;
 constexpr int kScatterItems = 16;
 
-// COUNT: only the per-leaf totals (added to cursor, which then holds counts), for a
-// wave whose crossings K-a's histogram does not give.  A crossing takes part when
-// k_lo <= k < min(n_x, k_hi) and its ray is alive (alive == NULL: every ray).
-template <bool COUNT>
 __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __restrict__ n_x,
                                                              const uint16_t* __restrict__ xleaf, uint32_t n_slots,
                                                              int maxc, uint32_t* __restrict__ cursor,
-                                                             uint32_t* __restrict__ order, int n_leaves, int k_lo,
-                                                             int k_hi, const uint8_t* __restrict__ alive) {
+                                                             uint32_t* __restrict__ order, int n_leaves) {
     extern __shared__ uint32_t sm[];
     uint32_t* s_cnt = sm;
     uint32_t* s_base = sm + n_leaves;
@@ -129,7 +124,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __re
         nx[i] = 0;
         if (s < n_slots) {
             const uint32_t ray = ray_of(s);
-            nx[i] = (!alive || __ldg(alive + ray)) ? __ldg(n_x + ray) : 0;
+            nx[i] = __ldg(n_x + ray);
             lf[i] = __ldg(xleaf + s);
         }
     }
@@ -140,7 +135,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __re
         if (s < n_slots) {
             const uint32_t ray = ray_of(s);
             const uint32_t k = s - ray * (uint32_t)maxc;
-            if (k < (uint32_t)nx[i] && k >= (uint32_t)k_lo && k < (uint32_t)k_hi) rk[i] = atomicAdd(&s_cnt[lf[i]], 1u);
+            if (k < (uint32_t)nx[i]) rk[i] = atomicAdd(&s_cnt[lf[i]], 1u);
         }
     }
     __syncthreads();
@@ -148,7 +143,6 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __re
         const uint32_t c = s_cnt[i];
         s_base[i] = c ? atomicAdd(&cursor[i], c) : 0u;
     }
-    if (COUNT) return;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kScatterItems; ++i) {
@@ -159,6 +153,53 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __re
     }
 }
 
+// One wave of a render: crossings k_lo <= k < min(n_x, k_lo + W) of the rays still
+// alive (alive == NULL: every ray), visited as n_rays x W items (ray-major), so a wave
+// reads only its own slots.  COUNT: only the per-leaf totals (added to cursor, which
+// then holds counts) for the scan; else the same binning as k_scatter.
+template <bool COUNT>
+__global__ void __launch_bounds__(kScatterThreads) k_scatter_wave(const uint8_t* __restrict__ n_x,
+                                                                  const uint16_t* __restrict__ xleaf,
+                                                                  uint32_t n_items, int maxc, int k_lo, int W,
+                                                                  const uint8_t* __restrict__ alive,
+                                                                  uint32_t* __restrict__ cursor,
+                                                                  uint32_t* __restrict__ order, int n_leaves) {
+    extern __shared__ uint32_t sm[];
+    uint32_t* s_cnt = sm;
+    uint32_t* s_base = sm + n_leaves;
+    for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) s_cnt[i] = 0u;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * (uint32_t)(kScatterThreads * kScatterItems);
+    uint16_t lf[kScatterItems];
+    uint32_t rk[kScatterItems], sl[kScatterItems];
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        const uint32_t it = base + (uint32_t)(i * kScatterThreads) + threadIdx.x;
+        lf[i] = 0;
+        sl[i] = 0xffffffffu;
+        if (it < n_items) {
+            const uint32_t ray = it / (uint32_t)W;
+            const uint32_t k = (uint32_t)k_lo + (it - ray * (uint32_t)W);
+            if ((!alive || __ldg(alive + ray)) && k < (uint32_t)__ldg(n_x + ray)) {
+                sl[i] = ray * (uint32_t)maxc + k;
+                lf[i] = __ldg(xleaf + sl[i]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) rk[i] = sl[i] != 0xffffffffu ? atomicAdd(&s_cnt[lf[i]], 1u) : 0xffffffffu;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) {
+        const uint32_t c = s_cnt[i];
+        s_base[i] = c ? atomicAdd(&cursor[i], c) : 0u;
+    }
+    if (COUNT) return;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i)
+        if (rk[i] != 0xffffffffu) order[s_base[lf[i]] + rk[i]] = sl[i];
+}
+
 }  // namespace
 
 cudaError_t launch_scan(cudaStream_t s, const uint32_t* counts, int n_leaves, int cpt, uint32_t* offsets,
@@ -167,31 +208,33 @@ cudaError_t launch_scan(cudaStream_t s, const uint32_t* counts, int n_leaves, in
     return cudaGetLastError();
 }
 
-static cudaError_t scatter_launch(cudaStream_t s, bool count, const uint8_t* n_x, const uint16_t* xleaf,
-                                  uint32_t n_rays, int maxc, uint32_t* cursor, uint32_t* order, int n_leaves, int k_lo,
-                                  int k_hi, const uint8_t* alive) {
+cudaError_t launch_scatter(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
+                           uint32_t* cursor, uint32_t* order, int n_leaves) {
     const uint64_t n_slots = (uint64_t)n_rays * (uint64_t)maxc;
     if (n_slots == 0) return cudaSuccess;
     const uint64_t per = (uint64_t)kScatterThreads * kScatterItems;
     const unsigned blocks = (unsigned)((n_slots + per - 1) / per);
     const size_t smem = 2 * sizeof(uint32_t) * (size_t)n_leaves;
-    if (count)
-        k_scatter<true><<<blocks, kScatterThreads, smem, s>>>(n_x, xleaf, (uint32_t)n_slots, maxc, cursor, order,
-                                                              n_leaves, k_lo, k_hi, alive);
-    else
-        k_scatter<false><<<blocks, kScatterThreads, smem, s>>>(n_x, xleaf, (uint32_t)n_slots, maxc, cursor, order,
-                                                               n_leaves, k_lo, k_hi, alive);
+    k_scatter<<<blocks, kScatterThreads, smem, s>>>(n_x, xleaf, (uint32_t)n_slots, maxc, cursor, order, n_leaves);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
-                           uint32_t* cursor, uint32_t* order, int n_leaves, int k_lo, int k_hi, const uint8_t* alive) {
-    return scatter_launch(s, false, n_x, xleaf, n_rays, maxc, cursor, order, n_leaves, k_lo, k_hi, alive);
-}
-
-cudaError_t launch_count_wave(cudaStream_t s, const uint8_t* n_x, const uint16_t* xleaf, uint32_t n_rays, int maxc,
-                              int k_lo, int k_hi, const uint8_t* alive, uint32_t* counts, int n_leaves) {
-    return scatter_launch(s, true, n_x, xleaf, n_rays, maxc, counts, nullptr, n_leaves, k_lo, k_hi, alive);
+cudaError_t launch_scatter_wave(cudaStream_t s, bool count, const uint8_t* n_x, const uint16_t* xleaf,
+                                uint32_t n_rays, int maxc, int k_lo, int k_hi, const uint8_t* alive, uint32_t* cursor,
+                                uint32_t* order, int n_leaves) {
+    const int W = k_hi - k_lo;
+    const uint64_t n_items = (uint64_t)n_rays * (uint64_t)W;
+    if (n_items == 0 || W <= 0) return cudaSuccess;
+    const uint64_t per = (uint64_t)kScatterThreads * kScatterItems;
+    const unsigned blocks = (unsigned)((n_items + per - 1) / per);
+    const size_t smem = 2 * sizeof(uint32_t) * (size_t)n_leaves;
+    if (count)
+        k_scatter_wave<true><<<blocks, kScatterThreads, smem, s>>>(n_x, xleaf, (uint32_t)n_items, maxc, k_lo, W, alive,
+                                                                   cursor, order, n_leaves);
+    else
+        k_scatter_wave<false><<<blocks, kScatterThreads, smem, s>>>(n_x, xleaf, (uint32_t)n_items, maxc, k_lo, W,
+                                                                    alive, cursor, order, n_leaves);
+    return cudaGetLastError();
 }
 
 }  // namespace amnerf
