@@ -45,3 +45,37 @@ def test_status_strings_without_a_gpu():
     assert st in (0, amnerf.E_DEVICE)
     if st == 0:
         lib.amnerf_destroy(ctx)
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Every struct of include/amnerf.h has the size and field offsets that the ctypes
+    binding assumes (gcc compiles a probe that prints sizeof and offsetof)."""
+    import json
+    import shutil
+    import subprocess
+
+    import pytest
+    from paper_2310_01881_gb300 import amnerf
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not found")
+    structs = ["amnerf_tree_params", "amnerf_node", "amnerf_mlp_desc", "amnerf_render_params", "amnerf_tuning",
+               "amnerf_stats", "amnerf_debug"]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "amnerf.h"', "int main(void) {",
+             '    printf("{");']
+    for i, name in enumerate(structs):
+        cls = getattr(amnerf, name)
+        parts = [f'\\"size\\": %zu'] + [f'\\"{f}\\": %zu' for f, _ in cls._fields_]
+        args = [f"sizeof({name})"] + [f"offsetof({name}, {f})" for f, _ in cls._fields_]
+        sep = "," if i + 1 < len(structs) else ""
+        lines.append(f'    printf("\\"{name}\\": {{{", ".join(parts)}}}{sep}", {", ".join(args)});')
+    lines += ['    printf("}\\n");', "    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = json.loads(subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout)
+    for name in structs:
+        cls = getattr(amnerf, name)
+        assert got[name]["size"] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[name][f] == getattr(cls, f).offset, (name, f)
