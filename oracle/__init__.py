@@ -18,6 +18,7 @@ Parity status per function (what pins it is in tests/test_oracle_pins.py):
   render      pinned: constant-density closed form, sum(w) + T = 1, midpoint-rule
               depth limit, early termination.
 Proposal sampler (pins in tests/test_oracle_proposal.py):
+  prop_predict    pinned: numpy float64 matmul chain with a library softmax.
   prop_loss_grad  pinned: central finite differences; entropy closed form at q = p.
   prop_adam       pinned: first step from zero moments moves by lr against sign(g).
   prop_select     pinned: hand-worked cases (ties, background, fallback); binary32

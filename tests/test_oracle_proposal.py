@@ -165,3 +165,31 @@ def test_binned_weights_sum_to_one(c1):
                        bins=True)
         np.testing.assert_allclose(res["bins"].sum(1), 1.0, atol=tol)
         np.testing.assert_allclose(res["bins"][:, 64], 1 - res["opacity"], atol=tol)
+
+
+def test_proposal_forward_matches_library_matmul_chain():
+    """The proposal network's forward pass is gamma_10(o + t0 d) ++ gamma_4(d) (the
+    encoding is pinned on its own), then W1, ReLU, W2, ReLU, W3 and a softmax, with
+    the weights stored row-major as [output][input] and the biases after each matrix.
+    A numpy float64 chain of matmuls and a library softmax gives the same q; a
+    transposed operand, a dropped bias or a swapped feature block would not."""
+    from scipy.special import softmax
+    rng = np.random.default_rng(17)
+    P = S.proposal_init(3) * 2.0
+    P[2880:2912] = rng.normal(size=32) * 0.3      # b1
+    P[3936:3968] = rng.normal(size=32) * 0.3      # b2
+    P[6048:6113] = rng.normal(size=65) * 0.3      # b3
+    n = 40
+    o = (rng.normal(size=(n, 3)) * 2.0).astype(np.float32)
+    d = rng.normal(size=(n, 3)); d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    t0 = rng.uniform(0.0, 3.0, size=n)
+    e = o + t0.astype(np.float32)[:, None] * d          # the sample point in FP32, as the rays are given
+    feat = np.stack([np.concatenate([O.encode(e[r], 10), O.encode(d[r], 4)]) for r in range(n)])
+    W1 = P[:2880].reshape(32, 90); b1 = P[2880:2912]
+    W2 = P[2912:3936].reshape(32, 32); b2 = P[3936:3968]
+    W3 = P[3968:6048].reshape(65, 32); b3 = P[6048:6113]
+    h1 = np.maximum(feat @ W1.T + b1, 0.0)
+    h2 = np.maximum(h1 @ W2.T + b2, 0.0)
+    q_ref = softmax(h2 @ W3.T + b3, axis=1)
+    q = O.prop_predict(P.astype(np.float64), o, d, t0)
+    np.testing.assert_allclose(q, q_ref, rtol=1e-10, atol=1e-14)
