@@ -188,6 +188,10 @@ typedef struct {
  *   slot_out float  [n_rays * max_samples * 4]  sigma, r, g, b of sample j of ray r at
  *                                         slot r*max_samples+j (unused slots untouched)
  *   prop_mask, prop_fallback              the proposal sampler's per-ray decisions
+ *   prop_q   float  [n_rays * 65]         the proposal network's softmax outputs as the
+ *                                         render's tensor-core inference computed them
+ *                                         (rows of rays in a 128-ray tile where no ray
+ *                                         hits the scene box are left untouched)
  * Entries past the valid ones are left untouched. */
 typedef struct {
     uint8_t *n_x;
@@ -200,6 +204,7 @@ typedef struct {
     float *slot_out;
     uint64_t *prop_mask;      /* [n_rays] kept depth bins (proposal renders only) */
     uint8_t *prop_fallback;   /* [n_rays] 1 = plain sampler used (proposal renders only) */
+    float *prop_q;            /* [n_rays][65] proposal probabilities (proposal renders only) */
 } amnerf_debug;
 
 /* Create a context on CUDA device `device`, enqueuing on `cuda_stream` (a
@@ -325,8 +330,14 @@ AMNERF_API amnerf_status amnerf_set_timing(amnerf_ctx *ctx, int enable);
  * Leaf ids >= n_leaves are ignored.  Enqueued on cuda_stream of the current device;
  * asynchronous.  Scratch: one file-scope device array of about 33 KB per device,
  * resident until exit, sized for n_leaves <= 4096 (E_INVAL beyond).  The first call
- * on a device looks the array up with cudaGetSymbolAddress -- make it before any
- * stream capture.  Calls share the array: calls that overlap on the GPU race.
+ * on a device is a warm-up: it looks the array up with cudaGetSymbolAddress, which
+ * with lazy module loading (the CUDA default) may load the library's device code and
+ * data -- an allocation and a synchronisation of its own -- so make it once, outside
+ * the region where allocation is banned and before any stream capture (e.g. with
+ * n_rays = 0 right after amnerf_create).  Later calls only enqueue work.  The address
+ * is kept per device for the life of the process: after cudaDeviceReset (or a reset
+ * of the primary context) this entry point must not be called again.  Calls share
+ * the array: calls that overlap on the GPU race.
  * Errors: E_INVAL (sizes, NULL buffers), E_CUDA. */
 AMNERF_API amnerf_status amnerf_group_by_leaf_static(const uint8_t *n_x, const uint16_t *leaf, int64_t n_rays,
                                                      int maxc, int n_leaves, uint32_t *counts, uint32_t *offsets,

@@ -23,6 +23,10 @@ Proposal sampler (pins in tests/test_oracle_proposal.py):
   prop_adam       pinned: first step from zero moments moves by lr against sign(g).
   prop_select     pinned: hand-worked cases (ties, background, fallback); binary32
                   mode: absorption of masses below half an ulp of the sum.
+  prop_predict(bf16=True)  pinned: bf16_round against hand-worked ties and a library
+                  bfloat16 conversion; the same numpy chain on rounded operands.
+  bin_indices     pinned: hand-worked rays with samples on, just below and just above
+                  the bin edges (both modes); brute-force edge counting in numpy.
   masked render   pinned: all-bins mask = plain render; kept crossings by brute force.
 """
 from __future__ import annotations
@@ -85,7 +89,11 @@ def lib():
             _lib.or_render.argtypes = [V, V, V, I, V, I, I, I, I, V, V, L, I, I, D, V, I, U, V, I, V, D, I,
                                        V, V, V, V, V, V, V, V, V, V, V, V]
             _lib.or_traverse_skip.argtypes = [V, V, V, I, V, V, L, I, I, I, I, U, V, I, V, D, V, V, V, V]
-            _lib.or_prop_predict.argtypes = [V, V, V, V, L, V]
+            _lib.or_prop_predict.argtypes = [V, V, V, V, L, V, I]
+            _lib.or_bin_indices.argtypes = [I, V, V, V, L, V]
+            _lib.or_bf16_round.argtypes = [D]
+            _lib.or_bf16_round.restype = D
+            _lib.or_bf16_round_n.argtypes = [V, L, V]
             _lib.or_prop_loss_grad.argtypes = [V, V, V, V, V, L, V, V]
             _lib.or_prop_adam.argtypes = [V, V, V, V, I, I, D, D, D, D]
             _lib.or_prop_select.argtypes = [V, L, D, I, V, V, I]
@@ -286,12 +294,35 @@ def root_interval(tree: Tree, o, d, mode: int = 0):
     return tin[:, 0], tout[:, 0], nx > 0
 
 
-def prop_predict(P, o, d, t0):
+def prop_predict(P, o, d, t0, bf16: bool = False):
+    """Softmax outputs (n, 65).  bf16=True rounds every operand of the three affine
+    maps (inputs, weights, biases, hidden activations) to bfloat16 and accumulates
+    in double: the operand rounding of a BF16 tensor-core evaluation."""
     P = np.ascontiguousarray(P, F64); o = np.ascontiguousarray(o, F32); d = np.ascontiguousarray(d, F32)
     t0 = np.ascontiguousarray(t0, F64)
     q = np.zeros((len(o), 65), F64)
-    lib().or_prop_predict(_p(P), _p(o), _p(d), _p(t0), len(o), _p(q))
+    lib().or_prop_predict(_p(P), _p(o), _p(d), _p(t0), len(o), _p(q), int(bf16))
     return q
+
+
+def bf16_round(x):
+    """x (a number or an array) rounded to the nearest bfloat16 value (ties to even)."""
+    if np.ndim(x) == 0:
+        return float(lib().or_bf16_round(float(x)))
+    a = np.ascontiguousarray(x, F64)
+    out = np.empty_like(a)
+    lib().or_bf16_round_n(_p(a), a.size, _p(out))
+    return out
+
+
+def bin_indices(t0, t1, t, mode: int = 0) -> np.ndarray:
+    """Depth bin of samples at t on rays with root interval [t0, t1] (the training
+    targets' binning): floor((t - t0) / w), w = (t1 - t0) / 64, clamped to [0, 63],
+    in the mode's precision."""
+    t0 = np.ascontiguousarray(t0, F64); t1 = np.ascontiguousarray(t1, F64); t = np.ascontiguousarray(t, F64)
+    out = np.zeros(len(t), I32)
+    lib().or_bin_indices(int(mode), _p(t0), _p(t1), _p(t), len(t), _p(out))
+    return out
 
 
 def prop_loss_grad(P, o, d, t0, targets):

@@ -729,6 +729,13 @@ static int or_bin_of(int mode, double t0, double t1, double t)
     return k < 0 ? 0 : (k > 63 ? 63 : k);
 }
 
+/* Bins of n samples (training-target binning, exported for its pins). */
+int or_bin_indices(int mode, const double *t0, const double *t1, const double *t, int64_t n, int *out)
+{
+    for (int64_t i = 0; i < n; i++) out[i] = or_bin_of(mode, t0[i], t1[i], t[i]);
+    return 0;
+}
+
 /* Does crossing [a, b] overlap bin k?  a < hi_k and b > lo_k. */
 static int or_overlaps(int mode, double t0, double t1, int k, double a, double b)
 {
@@ -994,42 +1001,69 @@ static void or_prop_input(const float *of, const float *df, double t0, double *i
     or_encode64(d, 4, in + 63);
 }
 
-/* Forward pass of one ray; h1, h2: post-ReLU activations, q: softmax output. */
-static void or_prop_forward(const double *P, const double *in, double *h1, double *h2, double *z, double *q)
+/* Round to the nearest bfloat16 value (8 significant bits, ties to even); the
+ * operand precision of a tensor-core evaluation.  Finite inputs in the normal range
+ * of bfloat16; zero stays zero.  x = m 2^e with m in [0.5, 1): m 2^8 is rounded to
+ * an integer in [128, 256] (nearbyint rounds ties to even in the default mode). */
+static double or_bf16(double x)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    double m = frexp(x, &e);
+    return ldexp(nearbyint(ldexp(m, 8)), e - 8);
+}
+
+double or_bf16_round(double x) { return or_bf16(x); }
+
+int or_bf16_round_n(const double *x, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; i++) out[i] = or_bf16(x[i]);
+    return 0;
+}
+
+/* Forward pass of one ray; h1, h2: post-ReLU activations, q: softmax output.
+ * bf != 0: every operand of the three affine maps -- inputs, weights, biases and
+ * the post-ReLU activations fed to the next layer -- is first rounded to bfloat16;
+ * products and sums stay in double (the operand rounding of a BF16 tensor-core
+ * evaluation of the same network, with exact accumulation). */
+static void or_prop_forward(const double *P, const double *in, double *h1, double *h2, double *z, double *q, int bf)
 {
     const double *W1 = P, *b1 = W1 + OR_PH * OR_PIN, *W2 = b1 + OR_PH, *b2 = W2 + OR_PH * OR_PH;
     const double *W3 = b2 + OR_PH, *b3 = W3 + OR_PO * OR_PH;
+#define OR_OP(v) (bf ? or_bf16(v) : (v))
     for (int o = 0; o < OR_PH; o++) {
         double acc = 0.0;
-        for (int i = 0; i < OR_PIN; i++) acc += W1[o * OR_PIN + i] * in[i];
-        acc += b1[o];
+        for (int i = 0; i < OR_PIN; i++) acc += OR_OP(W1[o * OR_PIN + i]) * OR_OP(in[i]);
+        acc += OR_OP(b1[o]);
         h1[o] = acc > 0.0 ? acc : 0.0;
     }
     for (int o = 0; o < OR_PH; o++) {
         double acc = 0.0;
-        for (int i = 0; i < OR_PH; i++) acc += W2[o * OR_PH + i] * h1[i];
-        acc += b2[o];
+        for (int i = 0; i < OR_PH; i++) acc += OR_OP(W2[o * OR_PH + i]) * OR_OP(h1[i]);
+        acc += OR_OP(b2[o]);
         h2[o] = acc > 0.0 ? acc : 0.0;
     }
     double m = -INFINITY;
     for (int o = 0; o < OR_PO; o++) {
         double acc = 0.0;
-        for (int i = 0; i < OR_PH; i++) acc += W3[o * OR_PH + i] * h2[i];
-        z[o] = acc + b3[o];
+        for (int i = 0; i < OR_PH; i++) acc += OR_OP(W3[o * OR_PH + i]) * OR_OP(h2[i]);
+        z[o] = acc + OR_OP(b3[o]);
         if (z[o] > m) m = z[o];
     }
+#undef OR_OP
     double s = 0.0;
     for (int o = 0; o < OR_PO; o++) { q[o] = exp(z[o] - m); s += q[o]; }
     for (int o = 0; o < OR_PO; o++) q[o] /= s;
 }
 
-/* Softmax outputs of n rays (q: n x 65).  t0: root entry per ray. */
-int or_prop_predict(const double *P, const float *o, const float *d, const double *t0, int64_t n, double *q)
+/* Softmax outputs of n rays (q: n x 65).  t0: root entry per ray.  bf != 0: the
+ * operands rounded to bfloat16 (see or_prop_forward). */
+int or_prop_predict(const double *P, const float *o, const float *d, const double *t0, int64_t n, double *q, int bf)
 {
     double in[OR_PIN], h1[OR_PH], h2[OR_PH], z[OR_PO];
     for (int64_t r = 0; r < n; r++) {
         or_prop_input(o + 3 * r, d + 3 * r, t0[r], in);
-        or_prop_forward(P, in, h1, h2, z, q + r * OR_PO);
+        or_prop_forward(P, in, h1, h2, z, q + r * OR_PO, bf);
     }
     return 0;
 }
@@ -1048,7 +1082,7 @@ int or_prop_loss_grad(const double *P, const float *o, const float *d, const dou
     for (int64_t r = 0; r < n; r++) {
         const double *pr = p + r * OR_PO;
         or_prop_input(o + 3 * r, d + 3 * r, t0[r], in);
-        or_prop_forward(P, in, h1, h2, z, q);
+        or_prop_forward(P, in, h1, h2, z, q, 0);
         double ps = 0.0;
         for (int b = 0; b < OR_PO; b++) {
             if (pr[b] > 0.0) L -= pr[b] * log(q[b]);

@@ -76,7 +76,7 @@ class amnerf_stats(ctypes.Structure):
 
 class amnerf_debug(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("n_x", "leaf", "t_in", "t_out", "counts", "offsets", "order",
-                                               "slot_out", "prop_mask", "prop_fallback")]
+                                               "slot_out", "prop_mask", "prop_fallback", "prop_q")]
 
 
 _lib = None
@@ -460,6 +460,7 @@ class Renderer:
         if proposal:
             dbg["prop_mask"] = torch.zeros(max(n, 1), dtype=torch.int64, device=dev)
             dbg["prop_fallback"] = torch.zeros(max(n, 1), dtype=torch.uint8, device=dev)
+            dbg["prop_q"] = torch.full((max(n, 1) * 65,), float("nan"), dtype=torch.float32, device=dev)
         rgb = torch.empty((n, 3), device=dev, dtype=torch.float32)
         depth = torch.empty((n,), device=dev, dtype=torch.float32)
         opac = torch.empty((n,), device=dev, dtype=torch.float32)
@@ -478,6 +479,7 @@ class Renderer:
         if proposal:
             host["prop_mask"] = host["prop_mask"][:n].view(np.uint64)
             host["prop_fallback"] = host["prop_fallback"][:n]
+            host["prop_q"] = host["prop_q"][: n * 65].reshape(n, 65)
         return rgb.cpu().numpy(), depth.cpu().numpy(), opac.cpu().numpy(), host, s
 
     def sync(self):

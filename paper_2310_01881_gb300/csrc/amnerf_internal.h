@@ -161,9 +161,12 @@ cudaError_t launch_prop_infer(cudaStream_t s, int infer_grid, const float* param
                               const float* ro, const float* rd, uint32_t n, float coverage, int max_bins,
                               uint64_t* mask, uint8_t* fallback, unsigned long long* n_fallback, float* q_out);
 // The same selection for renders, the network on the tensor cores (BF16 operands).
+// q_out (may be NULL): the probabilities [n][65] of every ray in a tile with at least
+// one ray that hits the scene box (other rows untouched).
 cudaError_t launch_prop_infer_tc(cudaStream_t s, const float* params, const float root_box[6], const float* ro,
                                  const float* rd, uint32_t n, float coverage, int max_bins, uint64_t* mask,
-                                 uint8_t* fallback, unsigned long long* n_fallback, int* err);
+                                 uint8_t* fallback, unsigned long long* n_fallback, int* err,
+                                 float* q_out = nullptr);
 cudaError_t launch_prop_grad(cudaStream_t s, const float* params, const float* ro, const float* rd,
                              const float2* root, const float* targets, uint32_t n, uint32_t batch, uint64_t seed,
                              uint64_t step, float* grad, float* loss);

@@ -479,7 +479,8 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         const float box[6] = {root.lo[0], root.lo[1], root.lo[2], root.hi[0], root.hi[1], root.hi[2]};
         // renders predict the kept bins with the proposal network on the tensor cores
         CK(launch_prop_infer_tc(s, ctx->d_prop, box, ro, rd, nn, p->coverage, p->max_bins, ctx->d_mask,
-                                ctx->d_fallback, reinterpret_cast<unsigned long long*>(ctx->d_stats + 3), ctx->d_err),
+                                ctx->d_fallback, reinterpret_cast<unsigned long long*>(ctx->d_stats + 3), ctx->d_err,
+                                dbg ? dbg->prop_q : nullptr),
            "proposal launch");
         if (ctx->timing) cudaEventRecord(ctx->ev[5], s);
         mask = ctx->d_mask;

@@ -19,7 +19,12 @@
 //     streams, no ordering between them) race on the array.
 //   - The first call on a device resolves the array's device address with
 //     cudaGetSymbolAddress (a host-side name of a __device__ array is not a device
-//     address).  Make that first call before any stream capture.
+//     address).  With lazy module loading that lookup may load this library's device
+//     code and data, which allocates and synchronises: the first call is a warm-up
+//     to make outside any no-allocation region and before any stream capture.
+//   - The address is cached per device index for the life of the process; a device
+//     or primary-context reset invalidates it, so the entry point must not be called
+//     after one.
 #include <mutex>
 
 #include "amnerf_internal.h"

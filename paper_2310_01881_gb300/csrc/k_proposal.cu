@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(128 * kPTcGroups, 1) k_prop_infer_tc(
     const float* __restrict__ params, float b0, float b1, float b2, float b3, float b4, float b5,
     const float* __restrict__ ro, const float* __restrict__ rd, uint32_t n, float coverage, int max_bins,
     uint64_t* __restrict__ mask, uint8_t* __restrict__ fallback, unsigned long long* __restrict__ n_fallback,
-    int* __restrict__ err) {
+    int* __restrict__ err, float* __restrict__ q_out) {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t* wb = sm;
     PropTcTile* tiles = reinterpret_cast<PropTcTile*>(sm + kPWBytes);
@@ -562,6 +562,10 @@ __global__ void __launch_bounds__(128 * kPTcGroups, 1) k_prop_infer_tc(
             const float inv = 1.0f / sum;
 #pragma unroll
             for (int b = 0; b < PO; ++b) Q[b][t] = v[b] * inv;
+            if (q_out) {  // debug copy of this ray's probabilities
+#pragma unroll
+                for (int b = 0; b < PO; ++b) q_out[(size_t)r * PO + b] = Q[b][t];
+            }
             uint64_t mk = 0;
             bool fb = select_bins(Q, Q, t, coverage, max_bins, mk);
             if (!hit) fb = false;
@@ -738,7 +742,7 @@ cudaError_t launch_prop_infer(cudaStream_t s, int infer_grid, const float* param
 
 cudaError_t launch_prop_infer_tc(cudaStream_t s, const float* params, const float root_box[6], const float* ro,
                                  const float* rd, uint32_t n, float coverage, int max_bins, uint64_t* mask,
-                                 uint8_t* fallback, unsigned long long* n_fallback, int* err) {
+                                 uint8_t* fallback, unsigned long long* n_fallback, int* err, float* q_out) {
     if (n == 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -748,7 +752,8 @@ cudaError_t launch_prop_infer_tc(cudaStream_t s, const float* params, const floa
     const unsigned grid = ctas < (uint32_t)sms ? ctas : (unsigned)sms;  // one CTA per SM (it holds all of TMEM)
     k_prop_infer_tc<<<grid, 128 * kPTcGroups, kPTcSmem, s>>>(params, root_box[0], root_box[1], root_box[2],
                                                               root_box[3], root_box[4], root_box[5], ro, rd, n,
-                                                              coverage, max_bins, mask, fallback, n_fallback, err);
+                                                              coverage, max_bins, mask, fallback, n_fallback, err,
+                                                              q_out);
     return cudaGetLastError();
 }
 

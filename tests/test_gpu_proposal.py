@@ -238,6 +238,100 @@ def test_full_view_proposal_render_sampled_against_oracle(R):
         assert np.abs(depth.cpu().numpy()[idx] - ref["depth"])[ok].max() <= 1e-5
 
 
+def _bf16_log_q_sigma(P, feat, coord, enc_err=1e-5):
+    """Standard deviation of log q_b of the proposal network evaluated with bfloat16
+    operands, by first-order (linearised) propagation of independent operand rounding
+    errors, each uniform on [-u, u] relative (u = 2^-9; the probabilistic model of
+    rounding errors of Higham and Mary, 2019): every weight, bias, input feature and
+    post-ReLU activation is one rounding site, and the non-coordinate features also
+    carry the encoding's own error, uniform on [-enc_err, enc_err] (SFU anchors and
+    double-angle steps; the raw coordinates are bit-identical).  The sensitivity of
+    log q_b = z_b - logsumexp(z) to a site is the product of the layer Jacobians (ReLU
+    masks, weights) with d log q / d z = I - 1 q^T."""
+    u2 = 2.0 ** -18 / 3.0
+    W1 = P[:2880].reshape(32, 90); b1 = P[2880:2912]
+    W2 = P[2912:3936].reshape(32, 32); b2 = P[3936:3968]
+    W3 = P[3968:6048].reshape(65, 32); b3 = P[6048:6113]
+    z1 = feat @ W1.T + b1; m1 = (z1 > 0).astype(float); h1 = z1 * m1
+    z2 = h1 @ W2.T + b2; m2 = (z2 > 0).astype(float); h2 = z2 * m2
+    z3 = h2 @ W3.T + b3
+    q = np.exp(z3 - z3.max(1, keepdims=True)); q /= q.sum(1, keepdims=True)
+    A3 = np.eye(65)[None] - q[:, None, :]                         # d log q / d z3
+    G3 = np.einsum("rbc,cj->rbj", A3, W3)                         # d log q / d h2
+    A2 = G3 * m2[:, None, :]                                      # d log q / d z2
+    G2 = np.einsum("rbj,jk->rbk", A2, W2)                         # d log q / d h1
+    A1 = G2 * m1[:, None, :]                                      # d log q / d z1
+    G1 = np.einsum("rbk,ki->rbi", A1, W1)                         # d log q / d features
+    var = np.einsum("rbc,rc->rb", A3 ** 2, (h2 ** 2) @ (W3 ** 2).T + b3 ** 2) * u2
+    var += np.einsum("rbj,rj->rb", G3 ** 2, h2 ** 2) * u2
+    var += np.einsum("rbj,rj->rb", A2 ** 2, (h1 ** 2) @ (W2 ** 2).T + b2 ** 2) * u2
+    var += np.einsum("rbk,rk->rb", G2 ** 2, h1 ** 2) * u2
+    var += np.einsum("rbk,rk->rb", A1 ** 2, (feat ** 2) @ (W1 ** 2).T + b1 ** 2) * u2
+    fe = feat ** 2 * u2 + np.where(coord[None, :], 0.0, enc_err ** 2 / 3.0)
+    var += np.einsum("rbi,ri->rb", G1 ** 2, fe)
+    return np.sqrt(var), z3
+
+
+def test_tensor_core_proposal_inference_against_oracle(R):
+    """The proposal network as renders evaluate it (k_prop_infer_tc: BF16 operands,
+    FP32 accumulation in TMEM, softmax in registers), read back through the render's
+    debug output, against the oracle, at two weight scales (flat and sharp
+    distributions):
+      - every probability of every ray that hits the scene box is within the BF16
+        tolerance of the FP64 oracle: |log q_tc - log q| <= 10 sigma_b + the FP32
+        softmax's own error (__expf, the sum, the division), sigma_b the standard
+        deviation of the operand rounding's effect on log q_b (_bf16_log_q_sigma);
+      - the oracle with bfloat16 operands (prop_predict(bf16=True)) is, on average,
+        at most half as far from the kernel as the FP64 oracle: the difference is the
+        operand rounding;
+      - the kept bins and fallbacks are exactly the oracle's selection (running sum in
+        binary32) applied to the kernel's own probabilities; rays that miss keep
+        nothing."""
+    cfg, tree, P = _c1(R)
+    from paper_2310_01881_gb300 import amnerf
+    o, d = S.view_rays(cfg, 0, 2, 64, 64)
+    t0, t1, hit = O.root_interval(tree, o, d, mode=1)
+    t0h = np.where(hit, t0, 0.0)
+    e = (o + t0h.astype(np.float32)[:, None] * d).astype(np.float32)[hit]
+    feat = np.stack([np.concatenate([O.encode(e[r], 10), O.encode(d[hit][r], 4)]) for r in range(len(e))])
+    coord = np.zeros(90, bool)
+    coord[[0, 1, 2, 63, 64, 65]] = True
+    for scale in (1.0, 3.0):
+        params = S.proposal_init(5) * scale
+        rng = np.random.default_rng(41)
+        params[2880:2912] = rng.normal(size=32) * 0.2
+        params[6048:6113] = rng.normal(size=65) * 0.5
+        params = params.astype(np.float32)
+        amnerf.amnerf_proposal_set(R.ctx, params)
+        Pd = params.astype(np.float64)
+        q64 = O.prop_predict(Pd, o, d, t0h)[hit]
+        qbf = O.prop_predict(Pd, o, d, t0h, bf16=True)[hit]
+        sig, z = _bf16_log_q_sigma(Pd, feat, coord)
+        zr = z.max(1, keepdims=True) - z
+        e_sm = (5 + 2.4 * zr) * 2.0 ** -23 + 70 * 2.0 ** -24       # __expf of q_b and of the sum's terms
+        tol = 10 * sig + e_sm + 1e-5
+        for cov, mb in ((0.99, 16), (0.9, 8), (0.6, 64)):
+            *_, dbg, st = R.render_debug(_dev(o), _dev(d), cfg.steps, cfg.cap, proposal=True, coverage=cov,
+                                         max_bins=mb)
+            q = dbg["prop_q"][hit].astype(np.float64)
+            assert np.isfinite(q).all() and (q >= 0).all()
+            ok = q64 > 1e-25
+            assert (q[~ok] <= 1e-20).all()
+            lq = np.abs(np.log(np.maximum(q, 1e-300)) - np.log(q64))
+            ratio = np.where(ok, lq / tol, 0.0)
+            print(f"scale {scale}, coverage {cov}: |log q_tc/q| / sigma median "
+                  f"{np.median((lq / sig)[ok]):.2f}, max {(lq / sig)[ok].max():.2f}; tolerance used "
+                  f"{ratio.max():.2f}")
+            assert ratio.max() <= 1.0, (scale, cov, mb, float(ratio.max()))
+            big = q64 > 1e-6
+            assert np.abs(np.log(q[big] / qbf[big])).mean() <= 0.5 * np.abs(np.log(q[big] / q64[big])).mean()
+            m_ref, f_ref = O.prop_select(dbg["prop_q"][hit], cov, mb, single=True)
+            np.testing.assert_array_equal(dbg["prop_mask"][hit], m_ref)
+            np.testing.assert_array_equal(dbg["prop_fallback"][hit].astype(np.int32), f_ref)
+            assert (dbg["prop_mask"][~hit] == 0).all() and (dbg["prop_fallback"][~hit] == 0).all()
+            assert st["fallback_rays"] == int(f_ref.sum())
+
+
 def test_render_masks_from_tensor_cores_agree_with_fp32_predictions(R):
     """Renders select the kept bins from the BF16 tensor-core network; the FP32
     predictions (amnerf_proposal_predict) pick the same bins for most rays -- the rest

@@ -193,3 +193,108 @@ def test_proposal_forward_matches_library_matmul_chain():
     q_ref = softmax(h2 @ W3.T + b3, axis=1)
     q = O.prop_predict(P.astype(np.float64), o, d, t0)
     np.testing.assert_allclose(q, q_ref, rtol=1e-10, atol=1e-14)
+
+
+def test_target_bins_on_hand_worked_edges():
+    """The training targets put a sample at t into bin floor((t - t0) / w), w = (t1 -
+    t0) / 64, clamped to [0, 63].  Hand-worked rays whose bin edges are exact: a sample
+    on edge k is in bin k, one just below it in bin k - 1, one just above in bin k;
+    t1 itself is in bin 63.  A width of (t1 - t0) / 63, an off-by-one or rounding
+    instead of flooring fails one of these."""
+    # FP64: [0, 64] (w = 1) and [2, 3] (w = 1/64)
+    for t0, t1, w in ((0.0, 64.0, 1.0), (2.0, 3.0, 1.0 / 64.0)):
+        k = np.arange(64)
+        on = t0 + k * w
+        below = np.nextafter(on[1:], -np.inf)
+        above = np.nextafter(on, np.inf)
+        three_q = on + 0.75 * w
+        t = np.concatenate([on, below, above, three_q, [t1, t1 + 1.0, t0 - 1.0]])
+        want = np.concatenate([k, k[1:] - 1, k, k, [63, 63, 0]])
+        got = O.bin_indices(np.full(len(t), t0), np.full(len(t), t1), t, mode=0)
+        np.testing.assert_array_equal(got, want)
+    # FP32: [1, 5] (w = 4 * 2^-6 = 1/16 exactly); edges and their float neighbours
+    t0, t1 = 1.0, 5.0
+    k = np.arange(64)
+    on = (np.float32(t0) + k.astype(np.float32) * np.float32(0.0625)).astype(np.float32)
+    below = np.nextafter(on[1:], np.float32(-np.inf), dtype=np.float32)
+    above = np.nextafter(on, np.float32(np.inf), dtype=np.float32)
+    t = np.concatenate([on, below, above]).astype(np.float64)
+    want = np.concatenate([k, k[1:] - 1, k])
+    got = O.bin_indices(np.full(len(t), t0), np.full(len(t), t1), t, mode=1)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_target_bins_against_brute_force_edge_count():
+    """Brute force: the bin of t is the number of interior edges t0 + k w (k = 1..63)
+    at or below t.  Random rays and samples (away from the edges by more than the
+    rounding of the mode), both modes."""
+    rng = np.random.default_rng(23)
+    n = 20000
+    t0 = rng.uniform(0.0, 3.0, n)
+    t1 = t0 + rng.uniform(0.05, 4.0, n)
+    t = t0 + rng.uniform(0.0, 1.0, n) * (t1 - t0)
+    for mode in (0, 1):
+        if mode == 1:
+            t0m, t1m, tm = (a.astype(np.float32).astype(np.float64) for a in (t0, t1, t))
+        else:
+            t0m, t1m, tm = t0, t1, t
+        w = (t1m - t0m) / 64.0
+        edges = t0m[:, None] + np.arange(1, 64)[None, :] * w[:, None]
+        ref = (tm[:, None] >= edges).sum(1)
+        gap = np.abs(tm[:, None] - edges).min(1)
+        far = gap > (1e-12 if mode == 0 else 1e-5) * np.maximum(1.0, np.abs(tm))
+        assert far.mean() > 0.99
+        got = O.bin_indices(t0m, t1m, tm, mode=mode)
+        np.testing.assert_array_equal(got[far], ref[far])
+
+
+def test_bf16_rounding_hand_ties_and_library_conversion():
+    """bfloat16 keeps 8 significant bits, ties to even: 1 + 2^-8 lies halfway between
+    1 and 1 + 2^-7 and goes to 1; 1 + 3 2^-8 goes to 1 + 2^-6; 255.5 (nine bits) goes
+    to 256; just above a tie rounds up.  Random float32 values agree with torch's
+    bfloat16 conversion (a library routine)."""
+    cases = [(1 + 2 ** -8, 1.0), (1 + 3 * 2 ** -8, 1 + 2 ** -6), (-(1 + 2 ** -8), -1.0), (255.5, 256.0),
+             (1 + 2 ** -8 + 2 ** -20, 1 + 2 ** -7), (0.0, 0.0), (3.0, 3.0), (2 ** -100, 2 ** -100)]
+    for x, want in cases:
+        assert O.bf16_round(x) == want, x
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    x = (rng.uniform(-1, 1, 4000) * 10.0 ** rng.uniform(-4, 4, 4000)).astype(np.float32)
+    lib = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([O.bf16_round(float(v)) for v in x])
+    np.testing.assert_array_equal(got, lib)
+
+
+def test_bf16_proposal_forward_matches_library_chain_on_rounded_operands():
+    """prop_predict(bf16=True) is the numpy float64 chain of the proposal network with
+    every operand (features, weights, biases, hidden activations) rounded to bfloat16
+    by torch; the FP64 prediction differs from it by about the bfloat16 rounding."""
+    torch = pytest.importorskip("torch")
+    from scipy.special import softmax
+
+    def bf(a):
+        return torch.from_numpy(np.asarray(a, np.float64)).to(torch.float32).to(torch.bfloat16).to(
+            torch.float64).numpy()
+
+    rng = np.random.default_rng(29)
+    P = S.proposal_init(4) * 2.0
+    P[2880:2912] = rng.normal(size=32) * 0.3
+    P[3936:3968] = rng.normal(size=32) * 0.3
+    P[6048:6113] = rng.normal(size=65) * 0.3
+    n = 40
+    o = (rng.normal(size=(n, 3)) * 2.0).astype(np.float32)
+    d = rng.normal(size=(n, 3)); d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    t0 = rng.uniform(0.0, 3.0, size=n)
+    e = o + t0.astype(np.float32)[:, None] * d
+    feat = np.stack([np.concatenate([O.encode(e[r], 10), O.encode(d[r], 4)]) for r in range(n)])
+    W1 = P[:2880].reshape(32, 90); b1 = P[2880:2912]
+    W2 = P[2912:3936].reshape(32, 32); b2 = P[3936:3968]
+    W3 = P[3968:6048].reshape(65, 32); b3 = P[6048:6113]
+    h1 = np.maximum(bf(feat) @ bf(W1).T + bf(b1), 0.0)
+    h2 = np.maximum(bf(h1) @ bf(W2).T + bf(b2), 0.0)
+    q_ref = softmax(bf(h2) @ bf(W3).T + bf(b3), axis=1)
+    q = O.prop_predict(P.astype(np.float64), o, d, t0, bf16=True)
+    np.testing.assert_allclose(q, q_ref, rtol=1e-9, atol=1e-14)
+    q64 = O.prop_predict(P.astype(np.float64), o, d, t0)
+    rel = np.abs(np.log(q / q64))
+    assert 1e-5 < rel.max() < 0.2
