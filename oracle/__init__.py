@@ -87,7 +87,8 @@ def lib():
             _lib.or_mlp_eval.argtypes = [V, I, I, I, I, V, V, L, I, V, V]
             _lib.or_mlp_input_absmax.argtypes = [V, I, I, I, I, V, V, L, V]
             _lib.or_render.argtypes = [V, V, V, I, V, I, I, I, I, V, V, L, I, I, D, V, I, U, V, I, V, D, I,
-                                       V, V, V, V, V, V, V, V, V, V, V, V]
+                                       V, V, V, V, V, V, V, V, V, V, V, V, I]
+            _lib.or_f16_round_n.argtypes = [V, L, V]
             _lib.or_traverse_skip.argtypes = [V, V, V, I, V, V, L, I, I, I, I, U, V, I, V, D, V, V, V, V]
             _lib.or_prop_predict.argtypes = [V, V, V, V, L, V, I]
             _lib.or_bin_indices.argtypes = [I, V, V, V, L, V]
@@ -236,8 +237,10 @@ def mlp_input_absmax(params_leaf, width: int, hidden: int, lx: int, ld: int, x, 
 
 def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, steps: int, cap: int,
            t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), mode: int = 0, threads: int = 1, full: bool = False,
-           mask=None, fallback=None, bins: bool = False, jitter: int = 0, skip=None):
+           mask=None, fallback=None, bins: bool = False, jitter: int = 0, skip=None, slot_fp16: bool = False):
     """Full render of every ray; returns a dict of float64 / int32 arrays.
+    slot_fp16 (FP64 mode): each sample's sigma and rgb rounded to binary16 (sigma
+    limited to 65504) before compositing, to measure a half-precision store alone.
     jitter: 0 = samples at stratum midpoints, else the seed of the stratified jitter.
     skip = (grid, threshold): empty-space skipping over the guidance grid (see traverse).
     mask/fallback (proposal sampler): per-ray kept-bin masks and fallback flags;
@@ -272,10 +275,18 @@ def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, 
                          _p(res["n_eval"]), _p(res["ert_margin"]),
                          _p(so) if so is not None else None, _p(sw) if sw is not None else None,
                          _p(res["t_final"]), _p(mk) if mk is not None else None, _p(fb) if fb is not None else None,
-                         _p(res["bins"]) if bins else None)
+                         _p(res["bins"]) if bins else None, int(slot_fp16))
     if rc != 0:
         raise RuntimeError("oracle render failed")
     return res
+
+
+def f16_round(x) -> np.ndarray:
+    """x rounded to the nearest IEEE binary16 value (ties to even), as float64."""
+    a = np.ascontiguousarray(x, F64)
+    out = np.empty_like(a)
+    lib().or_f16_round_n(_p(a), a.size, _p(out))
+    return out
 
 
 # ---------------------------------------------------------------------------------

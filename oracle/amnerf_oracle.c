@@ -683,9 +683,30 @@ typedef struct {
     /* proposal: per-ray kept-bin mask and fallback flag (both NULL = plain) */
     const uint64_t *mask; const int *fallback;
     double *bins;     /* (n, 65) compositing weight per depth bin + residual T; may be NULL */
+    /* FP64 mode only: round each sample's (sigma, r, g, b) to binary16 before it is
+     * composited (sigma first limited to the largest binary16 value), to measure the
+     * effect of a half-precision per-sample store on its own */
+    int slot_f16;
     /* threading */
     int64_t r0, r1; int err;
 } or_job;
+
+/* Round to the nearest IEEE binary16 value (11 significant bits, ties to even;
+ * subnormal spacing 2^-24 below 2^-14).  Inputs are finite with |x| <= 65504. */
+static double or_f16(double x)
+{
+    if (x == 0.0) return x;
+    if (fabs(x) < ldexp(1.0, -14)) return ldexp(nearbyint(ldexp(x, 24)), -24);
+    int e;
+    double m = frexp(x, &e);
+    return ldexp(nearbyint(ldexp(m, 11)), e - 11);
+}
+
+int or_f16_round_n(const double *x, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; i++) out[i] = or_f16(x[i]);
+    return 0;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Proposal sampler support (not in the paper; a learned sampler in the      */
@@ -887,6 +908,10 @@ static void or_render_ray(const or_job *J, int64_t r)
                             d64, &t, &dl, p);
                 or_encode64(p, J->lx, din);
                 or_mlp64(P, J->width, J->hidden, k0, din, o4, NULL, NULL);
+                if (J->slot_f16) {
+                    if (o4[0] > 65504.0) o4[0] = 65504.0;
+                    for (int i = 0; i < 4; i++) o4[i] = or_f16(o4[i]);
+                }
                 if (J->slot_out) for (int i = 0; i < 4; i++) J->slot_out[(r * J->cap + s) * 4 + i] = o4[i];
                 if (stopped) continue;
                 double e = exp(-o4[0] * dl);
@@ -924,7 +949,7 @@ int or_render(const float *box, const int *info, const float *split, int n_nodes
               const float *occ_grid, int occ_G, const double *occ_bbox, double occ_thr, int n_threads,
               double *rgb, double *depth, double *opacity, int *n_gen, int *n_eval, double *ert_margin,
               double *slot_out, double *slot_w, double *t_final, const uint64_t *mask, const int *fallback,
-              double *bins)
+              double *bins, int slot_f16)
 {
     if (steps < 1 || cap < steps || cap / steps > 256 || width > OR_MAXW || lx > 32 || ld > 32) return -1;
     if (n_threads < 1) n_threads = 1;
@@ -946,6 +971,7 @@ int or_render(const float *box, const int *info, const float *split, int n_nodes
     base.rgb = rgb; base.depth = depth; base.opacity = opacity; base.n_gen = n_gen; base.n_eval = n_eval;
     base.ert_margin = ert_margin; base.slot_out = slot_out; base.slot_w = slot_w; base.t_final = t_final;
     base.mask = mask; base.fallback = fallback; base.bins = bins;
+    base.slot_f16 = mode == 0 ? slot_f16 : 0;
     if (n_threads == 1 || n < 64) {
         base.r0 = 0; base.r1 = n;
         or_render_worker(&base);

@@ -73,16 +73,14 @@ constexpr int kMaxGroups = 4;
 // more K = 16 step per layer).  E4M3 adds its FP32 bias in the epilogue, after the
 // scales (an E4M3 bias would lose too much).  Both run the head as one more BF16 MMA
 // of a 16-row matrix (rows 0..3 used).
-// E4M3 with static activation scales (act_max known per leaf and layer) uses one
-// weight scale per layer, chosen so that the accumulator needs no rescaling: with
-// a_0 = act_max_0 / 448 and a_(l+1) = a_l * beta_l, layer l's weights are stored as
-// W / beta_l and its bias as b / a_(l+1), so relu(acc + bias) is already layer l+1's
-// E4M3 input (beta_l >= max|W| / 448 keeps the weights in range, and
-// a_(l+1) >= act_max_(l+1) / 448 the activations); the head weights take a_hidden.
-// Like BF16, every layer after the first starts its accumulator at its bias.  Layer
-// 0's bias B = b / a_1 is folded into input columns 90..92 as three E4M3 terms
-// (hi + mid + lo = B / c, about 2^-12 relative) against a constant input c, a power of
-// two per leaf that keeps the terms in range; enc holds 1 / a_0 and c.
+// E4M3 with static activation scales (act_max known per leaf and layer) keeps the
+// per-output-channel weight scales s_(l,n) = max|W_l[n,:]| / 448 (W stored as W / s)
+// and gives every layer input one static scale a_l = act_max_l / 448 (a_hidden = 1:
+// the head's BF16 input is in real units).  The accumulator of output n of layer l
+// is then y_n / (a_l s_(l,n)) without its bias, and the next layer's E4M3 input is
+// relu(acc * C[l][n] + B[l][n]) with C = a_l s_(l,n) / a_(l+1) and B = b_n / a_(l+1):
+// one packed FMA per pair of values in the epilogue, C in the scale block and B in
+// the bias block of the blob; enc holds 1 / a_0 (the encoding's scale).
 struct TcLayout {
     int width, hidden, k0, k0p, kh, khead, es;
     size_t w0, wh, wo, sw, bias, enc, stride;
@@ -124,13 +122,6 @@ uint8_t f2e4m3(float x) {
     if (E > 8 || (E == 8 && r > 14.0f)) return sign | 0x7e;
     if (r < 8.0f) return sign | (uint8_t)r;          // subnormal (E == -6)
     return sign | (uint8_t)(((E + 7) << 3) | ((int)r - 8));
-}
-
-float e4m3_to_float(uint8_t v) {  // exact: E4M3 values are dyadic rationals
-    const float sign = (v & 0x80) ? -1.0f : 1.0f;
-    const int e = (v >> 3) & 0xf, m = v & 7;
-    if (e == 0) return sign * std::ldexp((float)m, -9);  // subnormal: m 2^-9
-    return sign * std::ldexp(1.0f + (float)m / 8.0f, e - 7);
 }
 
 struct TcShared {
@@ -356,10 +347,8 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 } else {
                     static_assert(K0P == 96, "E4M3 layer-0 input is stored as 16 + 8 columns");
                     float inv;
-                    float cbias = 0.0f;  // static scales: the constant input of layer 0's folded bias
                     if constexpr (ST) {  // the leaf's static encoding scale (in the weight blob)
                         inv = *reinterpret_cast<const float*>(wbuf + lay.enc);
-                        cbias = *reinterpret_cast<const float*>(wbuf + lay.enc + 4);
                         s_a = 1.0f;
                     } else {  // this row's own scale
                         float m = 0.0f;
@@ -371,8 +360,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     uint32_t w[24];
 #pragma unroll
                     for (int i = 0; i < 24; ++i) {
-                        // features scaled in pairs; inputs K0 .. K0 + 2 carry the constant of
-                        // the folded bias (static scales), the rest of the padding is zero
+                        // features scaled in pairs; the padding past K0 is zero
                         float e[4];
 #pragma unroll
                         for (int u = 0; u < 4; u += 2) {
@@ -385,7 +373,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
 #pragma unroll
                                 for (int q = 0; q < 2; ++q) {
                                     const int fq = f0 + q;
-                                    e[u + q] = fq < K0 ? f[fq < K0 ? fq : 0] * inv : (fq < K0 + 3 ? cbias : 0.0f);
+                                    e[u + q] = fq < K0 ? f[fq < K0 ? fq : 0] * inv : 0.0f;
                                 }
                             }
                         }
@@ -424,10 +412,9 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                                : desc_wh + (uint64_t)(((size_t)(l - 1) * W * lay.kh * lay.es) >> 4);
                     if constexpr (F8) {
                         const uint32_t idd = idesc_e4m3(W);
-                        // static scales: layers after the first accumulate onto their bias
-                        const bool onto = l > 0 && ST;
+                        // every E4M3 layer starts from zero (scales and bias in the epilogue)
                         for (int kk = 0; kk < kin / KI; ++kk)
-                            mma_e4m3_ts(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, (kk > 0 || onto) ? 1u : 0u);
+                            mma_e4m3_ts(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, kk > 0 ? 1u : 0u);
                     } else {
                         const uint32_t idd = idesc_bf16(W);
                         // layer 0 starts from zero (its bias is folded in); later layers
@@ -481,10 +468,12 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 auto pre4 = [&](const float* v, int c0, float2& p01, float2& p23) {
                     if constexpr (F8) {
                         if constexpr (ST) {
-                            // per-layer scales: the accumulator is already in the next layer's
-                            // units, its bias folded in (layer 0) or its starting value
-                            p01 = make_float2(v[0], v[1]);
-                            p23 = make_float2(v[2], v[3]);
+                            // per-output-channel weight scale and the next input's static
+                            // scale in C, the bias in B: one packed FMA per pair
+                            const float4 cc = *reinterpret_cast<const float4*>(sw + c0);
+                            const float4 bb = *reinterpret_cast<const float4*>(b + c0);
+                            p01 = fma2v(make_float2(v[0], v[1]), make_float2(cc.x, cc.y), make_float2(bb.x, bb.y));
+                            p23 = fma2v(make_float2(v[2], v[3]), make_float2(cc.z, cc.w), make_float2(bb.z, bb.w));
                         } else {
                             const float4 bb = *reinterpret_cast<const float4*>(b + c0);
                             const float4 ss = *reinterpret_cast<const float4*>(sw + c0);
@@ -521,8 +510,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                         tmem_st_wait();
                         tmem_st_bias<W>(d_row, bias_s + 4u * (uint32_t)((l + 1) * W));
                     } else if constexpr (ST) {
-                        // relu(pre) is already the next layer's E4M3 input; then the next
-                        // layer's accumulator starts from its scaled bias
+                        // relu(acc C + B) is the next layer's E4M3 input
                         uint32_t pk[W / 4];
                         float vr[W];
                         tmem_ld_row<W>(d_row, vr);
@@ -534,8 +522,6 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                         }
                         if constexpr (W / 4 == 16) tmem_st16(a_row, pk);
                         else tmem_st8(a_row, pk);
-                        tmem_st_wait();
-                        tmem_st_bias<W>(d_row, bias_s + 4u * (uint32_t)((l + 1) * W));
                     } else {
                         float hv[W];
 #pragma unroll
@@ -730,34 +716,24 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
     const float* w = src;
     float* bias = reinterpret_cast<float*>(dst + lay.bias);
     float* sw = reinterpret_cast<float*>(dst + lay.sw);
-    // E4M3 with static scales: alpha is the scale of the current layer's input (real =
-    // alpha * E4M3 value), starting from the encoding's act_max_0 / 448; layer l's
-    // weights take one scale beta for the whole layer, at least max|W| / 448 and large
-    // enough that alpha * beta (the next input's scale) maps act_max_(l+1) into range.
-    // The accumulator is then already the next input in its scale, the bias is stored
-    // divided by alpha * beta, and the head weights take the last alpha.
-    float alpha = stat ? (act_max[0] > 0.0f ? act_max[0] / 448.0f : 1.0f) : 1.0f;
+    // E4M3: per-output-channel weight scales s = max|W_row| / 448 (1 for a zero row).
+    // Static activation scales: a_l = act_max_l / 448 (1 when act_max_l is 0) is the
+    // scale of layer l's E4M3 input; the head's input is BF16 in real units (a = 1).
+    // The epilogue of layer l computes relu(acc C + B) with C = a_l s / a_(l+1) (the
+    // scale block) and B = b / a_(l+1) (the bias block).
+    auto act_scale = [&](int l) { return l < hidden && act_max[l] > 0.0f ? act_max[l] / 448.0f : 1.0f; };
     int kin = k0;
     for (int l = 0; l < hidden; ++l) {
         const int K = l == 0 ? lay.k0p : lay.kh;
         uint8_t* base = dst + (l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * width * lay.kh * lay.es);
-        float beta = 1.0f;
-        if (stat) {
-            float m = 0.0f;
-            for (size_t i = 0; i < (size_t)width * kin; ++i) m = std::fmax(m, std::fabs(w[i]));
-            beta = m > 0.0f ? m / 448.0f : 1.0f;
-            if (l + 1 < hidden) beta = std::fmax(beta, act_max[l + 1] / (448.0f * alpha));
-        }
+        const float a_in = stat ? act_scale(l) : 1.0f, a_out = stat ? act_scale(l + 1) : 1.0f;
         for (int n = 0; n < width; ++n) {
             const float* row = w + (size_t)n * kin;
             if (f8) {
-                float s = beta;
-                if (!stat) {  // per-output-channel scale (per-row activation scales at run time)
-                    float m = 0.0f;
-                    for (int k = 0; k < kin; ++k) m = std::fmax(m, std::fabs(row[k]));
-                    s = m > 0.0f ? m / 448.0f : 1.0f;
-                }
-                sw[(size_t)l * width + n] = s;
+                float m = 0.0f;
+                for (int k = 0; k < kin; ++k) m = std::fmax(m, std::fabs(row[k]));
+                const float s = m > 0.0f ? m / 448.0f : 1.0f;
+                sw[(size_t)l * width + n] = stat ? a_in * s / a_out : s;
                 for (int k = 0; k < kin; ++k) base[cm_offset8(n, k, K)] = f2e4m3(row[k] / s);
             } else {
                 for (int k = 0; k < kin; ++k) {
@@ -771,35 +747,16 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
             }
         }
         w += (size_t)width * kin;
-        const float next = alpha * beta;  // scale of this layer's output (1 unless static E4M3)
-        for (int n = 0; n < width; ++n) bias[(size_t)l * width + n] = stat ? w[n] / next : w[n];
-        if (stat && l == 0) {
-            // layer 0's bias in the contraction: three E4M3 terms per output channel at
-            // inputs k0 .. k0 + 2, each of those inputs the constant c
-            float bmax = 0.0f;
-            for (int n = 0; n < width; ++n) bmax = std::fmax(bmax, std::fabs(w[n] / next));
-            float c = 1.0f;
-            while (bmax / c > 224.0f && c < 256.0f) c *= 2.0f;
-            reinterpret_cast<float*>(dst + lay.enc)[1] = c;
-            for (int n = 0; n < width; ++n) {
-                float r = w[n] / next / c;
-                for (int q = 0; q < 3; ++q) {
-                    const uint8_t e = f2e4m3(r);
-                    base[cm_offset8(n, k0 + q, K)] = e;
-                    r -= e4m3_to_float(e);
-                }
-            }
-        }
-        alpha = next;
+        for (int n = 0; n < width; ++n) bias[(size_t)l * width + n] = w[n] / a_out;
         w += width;
         kin = width;
     }
-    if (stat) reinterpret_cast<float*>(dst + lay.enc)[0] = act_max[0] > 0.0f ? 448.0f / act_max[0] : 1.0f;
+    if (stat) reinterpret_cast<float*>(dst + lay.enc)[0] = 1.0f / act_scale(0);
     {  // head: rows 0..3 of a 16 x khead BF16 matrix (its bias stays FP32)
         uint8_t* hb = dst + lay.wo;
         for (int n = 0; n < 4; ++n) {
             for (int k = 0; k < width; ++k) {
-                const uint16_t b = f2bf(w[(size_t)n * width + k] * alpha);
+                const uint16_t b = f2bf(w[(size_t)n * width + k]);
                 std::memcpy(hb + cm_offset(n, k, lay.khead), &b, 2);
             }
         }

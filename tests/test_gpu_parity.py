@@ -667,6 +667,43 @@ def test_c2_fp8_static_scales_sampled_psnr(R):
     assert np.all(np.isfinite(rgb)) and psnr >= 30.0
 
 
+def test_fp8_static_weight_scales_are_per_output_channel(R):
+    """The rows of the last hidden layer of every leaf scaled by factors from 10^-3 to
+    10^3, and the head's columns by the inverse factors: the same network function
+    (ReLU is positively homogeneous).  With per-output-channel weight scales the scaled
+    rows quantise to the same E4M3 values and the scale moves into the epilogue's FMA,
+    so the render is as close to the FP64 oracle as the unscaled one's.  One weight
+    scale per layer would flush the rows scaled by 10^-3 (10^-6 of the layer's largest
+    weight) to zero."""
+    cfg = S.CONFIGS["c1"]
+    grid, tree, P = _setup(R, cfg, 0, prec="fp32")
+    W = _gpu_weights(R, cfg, grid, 0).reshape(R.n_leaves, -1).copy()
+    k0, w, h = S.mlp_input_width(cfg.lx, cfg.ld), cfg.width, cfg.hidden
+    last = w * k0 + w + (h - 2) * (w * w + w)          # start of the last hidden layer
+    head = last + w * w + w
+    f = 10.0 ** np.random.default_rng(9).uniform(-3, 3, w)
+    Ws = W.copy()
+    Ws[:, last:last + w * w] = (W[:, last:last + w * w].reshape(-1, w, w) * f[None, :, None]).reshape(len(W), -1)
+    Ws[:, last + w * w:head] = W[:, last + w * w:head] * f[None, :]
+    Ws[:, head:head + 4 * w] = (W[:, head:head + 4 * w].reshape(-1, 4, w) / f[None, None, :]).reshape(len(W), -1)
+    oc, dc = S.view_rays(cfg, 0, 7, 64, 64)
+    o, d = _rays(cfg, 0)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=0, threads=8)
+    out = {}
+    for name, Wx in (("plain", W), ("scaled", Ws)):
+        Wx = Wx.astype(np.float32).reshape(-1)
+        R.load_mlps(Wx, cfg.width, cfg.hidden, cfg.lx, cfg.ld, "fp32")
+        amax = R.calibrate_fp8(_dev(oc), _dev(dc), cfg.hidden, steps=cfg.steps, cap=cfg.cap)
+        R.load_mlps(Wx, cfg.width, cfg.hidden, cfg.lx, cfg.ld, act_max=amax)
+        out[name] = R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)[0].cpu().numpy()
+    p_plain, p_scaled = _psnr(out["plain"], ref["rgb"]), _psnr(out["scaled"], ref["rgb"])
+    p_pair = _psnr(out["scaled"], out["plain"])
+    print(f"fp8 static, rows x 10^-3..10^3: PSNR vs FP64 {p_scaled:.2f} dB (unscaled {p_plain:.2f}); "
+          f"scaled vs unscaled render {p_pair:.2f} dB")
+    assert p_scaled >= 30.0 and p_scaled >= p_plain - 1.0
+    assert p_pair >= p_plain + 6.0
+
+
 def test_fp8_static_entry_points_reject_bad_use(R):
     from paper_2310_01881_gb300 import amnerf
     cfg = S.CONFIGS["c1"]
