@@ -386,10 +386,34 @@ def run_ours(args):
     }
     if "fp32" in results and head != "fp32":
         line["speedup_vs_fp32"] = round(results["fp32"]["ms"] / hr["ms"], 3)
-    print(json.dumps(line))
     R.close()
+    if world == 1 and cfg.name == "c2" and args.views is None and args.px is None and not args.no_extras:
+        line.update(_extras(args))
+    print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def _extras(args) -> dict:
+    """The batching (c4) and learned-proposal (c5) workloads, summarised for the default
+    line: one GPU, 16 views of 1920x1080 each, the 4096-leaf scene."""
+    import torch
+    a = argparse.Namespace(**vars(args))
+    a.steps = min(args.steps, 10)
+    a.views, a.px = None, None
+    a.c5_scene, a.leaf_net, a.density_scale, a.ert_wave = "c4", "", 1.0, 0
+    cfg4 = S.CONFIGS["c4"]
+    grid = S.density_grid(S.scene_for(cfg4.scene, 0), cfg4.G)
+    c4 = run_c4(a, emit=False, grid=grid)
+    torch.cuda.empty_cache()
+    c5 = run_c5(a, emit=False, grid=grid)
+    torch.cuda.empty_cache()
+    keep4 = ("value", "unit", "ms_per_step", "mrays_per_s", "graph_ms", "stream_ms", "per_leaf_launch_ms",
+             "speedup_vs_per_leaf", "stage_ms", "stage_ms_per_leaf", "autotuned", "leaf_counts", "vs_fp64", "clocks")
+    keep5 = ("value", "unit", "ms_per_step", "plain", "proposal", "spr_reduction", "delta_psnr_vs_fp64_db",
+             "training", "clocks")
+    return {"c4": {"workload": c4["config"]["workload"], **{k: c4[k] for k in keep4 if k in c4}},
+            "c5": {"workload": c5["config"]["workload"], **{k: c5[k] for k in keep5 if k in c5}}}
 
 
 def _zipf_exponent(counts: np.ndarray) -> float:
@@ -401,10 +425,11 @@ def _zipf_exponent(counts: np.ndarray) -> float:
     return float(-slope)
 
 
-def run_c4(args):
+def run_c4(args, emit: bool = True, grid=None) -> dict:
     """Imbalanced batching workload: 4096-leaf tree, 16 views of 1920x1080 (33.2 M rays)
     rendered as ONE batch (one persistent grouped network launch), autotuned, replayed
-    from a CUDA graph, next to the per-leaf-launch baseline."""
+    from a CUDA graph, next to the per-leaf-launch baseline.  Returns the JSON line
+    (printed when `emit`)."""
     import ctypes
 
     import torch
@@ -415,9 +440,11 @@ def run_c4(args):
     build.build()
     cfg = S.CONFIGS["c4"]
     views = args.views or cfg.views
-    grid, o_np, d_np = workload(cfg, 0, views, None)
-    if args.px:
-        grid, o_np, d_np = workload(cfg, 0, views, args.px)
+    if grid is None:
+        grid = S.density_grid(S.scene_for(cfg.scene, 0), cfg.G)
+    rays = [S.view_rays(cfg, 0, v, args.px, args.px) for v in range(views)]
+    o_np = np.concatenate([r[0] for r in rays]); d_np = np.concatenate([r[1] for r in rays])
+    del rays
     n = len(o_np)
     R = amnerf.Renderer(0)
     nl = R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
@@ -500,26 +527,32 @@ def run_c4(args):
                     "max_abs_rgb": float(np.abs(rgb[idx] - ref["rgb"]).max()), "rays": int(len(idx))},
         "clocks": clk.summary(),
     }
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
     R.close()
+    return line
 
 
-def run_c5(args):
-    """Learned proposal on the config-1 scene with BF16 leaves (optionally with every
-    density scaled): trained on plain-rendered views, evaluated on held-out views
-    against the plain sampler, the FP64 oracle, and the oracle's own bound -- the
-    samples per ray when the kept bins come from the true (plain-render) weights."""
+def run_c5(args, emit: bool = True, grid=None) -> dict:
+    """Learned proposal with BF16 leaves: trained on plain-rendered views, evaluated on
+    held-out views against the plain sampler, the FP64 oracle, and the oracle's own
+    bound -- the samples per ray when the kept bins come from the true (plain-render)
+    weights.  The scene is the 4096-leaf imbalanced one (--c5-scene c4, the default,
+    with its 4 x 64 leaf networks) or the config-1 scene (--c5-scene c1, 2 x 32 leaves),
+    optionally with every density scaled.  Returns the JSON line (printed when `emit`)."""
     import torch
 
     from paper_2310_01881_gb300 import amnerf, build
 
     torch.cuda.set_device(0)
     build.build()
-    cfg = S.CONFIGS["c1"]
+    cfg = S.CONFIGS[args.c5_scene]
     if args.leaf_net:  # another leaf network shape, e.g. "4x64" (the scene is unchanged)
         h, w = (int(v) for v in args.leaf_net.lower().split("x"))
         cfg = dataclasses.replace(cfg, hidden=h, width=w)
-    grid = S.density_grid(S.scene_for(cfg.scene, 0), cfg.G) * np.float32(args.density_scale)
+    if grid is None:
+        grid = S.density_grid(S.scene_for(cfg.scene, 0), cfg.G)
+    grid = grid * np.float32(args.density_scale)
     R = amnerf.Renderer(0)
     R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
     P = S.xavier_weights(0, S.leaf_mean_density(grid, R.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
@@ -582,7 +615,7 @@ def run_c5(args):
     import oracle as O
     tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
     P_or = S.xavier_weights(0, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
-    idx = S.ray_subset(n, args.psnr_rays // 4, 11)
+    idx = S.ray_subset(n, args.psnr_rays // (16 if cfg.width * cfg.hidden > 64 else 4), 11)
     threads = os.cpu_count() or 1
     ref = O.render(tree, P_or, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps, cfg.cap,
                    cfg.t_term, mode=0, threads=threads, bins=True)
@@ -625,8 +658,8 @@ def run_c5(args):
         "value": head["Mrays/s"], "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "dtype": "bf16",
         "data": "synthetic",
-        "config": {"workload": f"config-1 scene x{args.density_scale:g} density (<=16 leaves, "
-                               f"{cfg.hidden}x{cfg.width} BF16 MLPs); "
+        "config": {"workload": f"{cfg.name} scene x{args.density_scale:g} density ({R.n_leaves} leaves, "
+                               f"{cfg.hidden}x{cfg.width} BF16 MLPs, cap {cfg.cap}); "
                                f"proposal trained on {n_train_views} views at {tw}x{th}, evaluated on {views} "
                                f"held-out views at {px_w}x{px_h}",
                    "rays_per_step": n, "density_scale": args.density_scale, "oracle_rays": len(idx)},
@@ -643,8 +676,10 @@ def run_c5(args):
                      "targets_s": round(t_targets, 2), "train_s": round(t_train, 2)},
         "clocks": clk.summary(),
     }
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
     R.close()
+    return line
 
 
 def run_reference(args):
@@ -699,7 +734,11 @@ def main():
     ap.add_argument("--train-views", type=int, default=64, help="c5: plain-rendered training views")
     ap.add_argument("--train-steps", type=int, default=3000, help="c5: Adam steps")
     ap.add_argument("--density-scale", type=float, default=1.0, help="c5: factor on every density of the scene")
-    ap.add_argument("--leaf-net", default="", help="c5: leaf network shape HxW (default: the config's 2x32)")
+    ap.add_argument("--leaf-net", default="", help="c5: leaf network shape HxW (default: the scene config's)")
+    ap.add_argument("--c5-scene", default="c4", choices=["c4", "c1"],
+                    help="c5: the scene the proposal is trained and evaluated on (default: the 4096-leaf one)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="c2: skip the c4 batching and c5 proposal summaries of the default line")
     ap.add_argument("--px", type=int, default=None, help="square image size (default: the config's)")
     ap.add_argument("--skip-empty", type=float, default=None,
                     help="empty-space skipping: density threshold of the guidance grid (c1/c2); default off")

@@ -510,15 +510,19 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                         tmem_st_wait();
                         tmem_st_bias<W>(d_row, bias_s + 4u * (uint32_t)((l + 1) * W));
                     } else if constexpr (ST) {
-                        // relu(acc C + B) is the next layer's E4M3 input
+                        // relu(acc C + B) is the next layer's E4M3 input; the row is read
+                        // in 32-column halves (the scales and biases take registers too)
                         uint32_t pk[W / 4];
-                        float vr[W];
-                        tmem_ld_row<W>(d_row, vr);
 #pragma unroll
-                        for (int c = 0; c < W / 4; ++c) {
-                            float2 p01, p23;
-                            pre4(vr + 4 * c, 4 * c, p01, p23);
-                            pk[c] = pack_relu_e4m3x4(p01.x, p01.y, p23.x, p23.y);
+                        for (int h = 0; h < W / 32; ++h) {
+                            float v[32];
+                            tmem_ld32(d_row + 32u * h, v);
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                float2 p01, p23;
+                                pre4(v + 4 * c, 32 * h + 4 * c, p01, p23);
+                                pk[8 * h + c] = pack_relu_e4m3x4(p01.x, p01.y, p23.x, p23.y);
+                            }
                         }
                         if constexpr (W / 4 == 16) tmem_st16(a_row, pk);
                         else tmem_st8(a_row, pk);
