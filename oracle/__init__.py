@@ -74,7 +74,7 @@ def lib():
             _lib = ctypes.CDLL(build())
             V, I, L, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
             _lib.or_build_tree.argtypes = [V, I, V, I, D, I, V, V, V, V, V, V]
-            _lib.or_traverse.argtypes = [V, V, V, I, V, V, L, I, I, I, V, V, V, V]
+            _lib.or_traverse.argtypes = [V, V, V, I, V, V, L, I, I, I, V, V, V, V, D]
             U = ctypes.c_uint64
             _lib.or_samples.argtypes = [V, V, L, V, V, V, I, I, I, I, U, V, V, V]
             _lib.or_group.argtypes = [V, V, L, I, I, I, V, V, V]
@@ -87,9 +87,9 @@ def lib():
             _lib.or_mlp_eval.argtypes = [V, I, I, I, I, V, V, L, I, V, V]
             _lib.or_mlp_input_absmax.argtypes = [V, I, I, I, I, V, V, L, V]
             _lib.or_render.argtypes = [V, V, V, I, V, I, I, I, I, V, V, L, I, I, D, V, I, U, V, I, V, D, I,
-                                       V, V, V, V, V, V, V, V, V, V, V, V, I]
+                                       V, V, V, V, V, V, V, V, V, V, V, V, I, D]
             _lib.or_f16_round_n.argtypes = [V, L, V]
-            _lib.or_traverse_skip.argtypes = [V, V, V, I, V, V, L, I, I, I, I, U, V, I, V, D, V, V, V, V]
+            _lib.or_traverse_skip.argtypes = [V, V, V, I, V, V, L, I, I, I, I, U, V, I, V, D, V, V, V, V, D]
             _lib.or_prop_predict.argtypes = [V, V, V, V, L, V, I]
             _lib.or_bin_indices.argtypes = [I, V, V, V, L, V]
             _lib.or_bf16_round.argtypes = [D]
@@ -120,6 +120,15 @@ class Tree:
     def leaf_cells(self) -> np.ndarray:
         return self.cells[self.leaves()]
 
+    def network_nodes(self) -> np.ndarray:
+        """Node indices in network order: the leaves by leaf id, then the inner nodes
+        in preorder (the networks of adaptive hierarchical sampling)."""
+        inner = np.nonzero(self.info[:, 0] >= 0)[0]
+        return np.concatenate([self.leaves(), inner])
+
+    def network_cells(self) -> np.ndarray:
+        return self.cells[self.network_nodes()]
+
 
 def build_tree(grid: np.ndarray, max_depth: int, leaf_frac: float = 0.0,
                bbox=(-1.0, -1.0, -1.0, 1.0, 1.0, 1.0)) -> Tree:
@@ -147,11 +156,15 @@ def make_tree(box, info, split) -> Tree:
 BBOX = (-1.0, -1.0, -1.0, 1.0, 1.0, 1.0)
 
 
-def traverse(tree: Tree, o, d, maxc: int, mode: int = 0, method: int = 0, skip=None):
-    """Per ray: crossing count, leaf ids, entries, exits (ray-major, stride maxc).
+def traverse(tree: Tree, o, d, maxc: int, mode: int = 0, method: int = 0, skip=None, lod: float = 0.0):
+    """Per ray: crossing count, network ids, entries, exits (ray-major, stride maxc).
     skip = (grid, threshold, steps, jitter): empty-space skipping -- a crossing is kept
     only when one of its samples (placed as its index among the kept crossings) lies
-    in a grid cell of density > threshold."""
+    in a grid cell of density > threshold.
+    lod > 0: adaptive hierarchical sampling -- an inner node is descended only while
+    its extent along its split axis exceeds lod x the ray's entry distance into it,
+    else it is one crossing with its own network (ids: leaves 0..L-1 by leaf id, then
+    inner nodes in preorder, L + rank; see Tree.network_nodes)."""
     o = np.ascontiguousarray(o, F32); d = np.ascontiguousarray(d, F32)
     n = len(o)
     nx = np.zeros(n, I32); leaf = np.full((n, maxc), -1, I32)
@@ -162,12 +175,12 @@ def traverse(tree: Tree, o, d, maxc: int, mode: int = 0, method: int = 0, skip=N
         bb = np.asarray(BBOX, F64)
         rc = lib().or_traverse_skip(_p(tree.box), _p(tree.info), _p(tree.split), tree.n_nodes, _p(o), _p(d), n,
                                     maxc, mode, method, steps, int(jitter), _p(grid), grid.shape[0], _p(bb),
-                                    float(thr), _p(nx), _p(leaf), _p(tin), _p(tout))
+                                    float(thr), _p(nx), _p(leaf), _p(tin), _p(tout), float(lod))
         if rc != 0:
             raise RuntimeError("oracle traversal failed")
         return nx, leaf, tin, tout
     rc = lib().or_traverse(_p(tree.box), _p(tree.info), _p(tree.split), tree.n_nodes, _p(o), _p(d), n,
-                           maxc, mode, method, _p(nx), _p(leaf), _p(tin), _p(tout))
+                           maxc, mode, method, _p(nx), _p(leaf), _p(tin), _p(tout), float(lod))
     if rc != 0:
         raise RuntimeError("oracle traversal failed")
     return nx, leaf, tin, tout
@@ -237,10 +250,13 @@ def mlp_input_absmax(params_leaf, width: int, hidden: int, lx: int, ld: int, x, 
 
 def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, steps: int, cap: int,
            t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), mode: int = 0, threads: int = 1, full: bool = False,
-           mask=None, fallback=None, bins: bool = False, jitter: int = 0, skip=None, slot_fp16: bool = False):
+           mask=None, fallback=None, bins: bool = False, jitter: int = 0, skip=None, slot_fp16: bool = False,
+           lod: float = 0.0):
     """Full render of every ray; returns a dict of float64 / int32 arrays.
     slot_fp16 (FP64 mode): each sample's sigma and rgb rounded to binary16 (sigma
     limited to 65504) before compositing, to measure a half-precision store alone.
+    lod > 0: adaptive hierarchical sampling (see traverse); params then hold one network
+    per node in network order (Tree.network_nodes).
     jitter: 0 = samples at stratum midpoints, else the seed of the stratified jitter.
     skip = (grid, threshold): empty-space skipping over the guidance grid (see traverse).
     mask/fallback (proposal sampler): per-ray kept-bin masks and fallback flags;
@@ -275,7 +291,7 @@ def render(tree: Tree, params, width: int, hidden: int, lx: int, ld: int, o, d, 
                          _p(res["n_eval"]), _p(res["ert_margin"]),
                          _p(so) if so is not None else None, _p(sw) if sw is not None else None,
                          _p(res["t_final"]), _p(mk) if mk is not None else None, _p(fb) if fb is not None else None,
-                         _p(res["bins"]) if bins else None, int(slot_fp16))
+                         _p(res["bins"]) if bins else None, int(slot_fp16), float(lod))
     if rc != 0:
         raise RuntimeError("oracle render failed")
     return res

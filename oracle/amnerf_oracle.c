@@ -217,14 +217,61 @@ static int or_slab64(const float *box, const double o[3], const double inv[3], d
     return x > e;
 }
 
-/* One ray: ordered list of leaf crossings, at most maxc.  method 0 = stack
- * traversal (near child first: the child on the origin's side of the split plane;
- * an origin on the plane goes left when d <= 0 along the axis), method 1 = every
- * leaf tested, positive crossings sorted by entry (the definition the stack form
- * must reproduce). */
+/* Adaptive hierarchical sampling (Sec. 3.5, Algorithm 1's HCheck; Fig. 1 (c)): the
+ * paper leaves HCheck undefined beyond "scene density and camera-to-scene distance".
+ * Reading: a ray's footprint grows linearly with the distance travelled, so a node
+ * whose subdivision is finer than the footprint cannot be resolved and its own
+ * network takes the whole crossing.  An inner node is descended (HCheck true) iff
+ * its extent along its split axis exceeds lod times the ray's entry distance into it
+ * (lod = the footprint per unit distance times the number of footprints a node must
+ * span to be refined); otherwise the inner node is emitted as one crossing with its
+ * own network.  The density enters through the tree: density-median splits make
+ * nodes small where the scene is dense, so dense distant parts stop early.  lod <= 0
+ * descends everywhere (leaves only).  In FP32 mode the test is size > lod * entry
+ * with the size hi - lo of the box along the axis (exact for dyadic boxes) and the
+ * product rounded to float.  Networks: leaves 0 .. L-1 by leaf id, then the inner
+ * nodes in preorder, L + rank. */
+typedef struct or_hier_s {
+    double lod;
+    const int *net;   /* network id of every node */
+    const int *parent;
+} or_hier;
+
+static int or_descends(const or_hier *H, int mode, const float *bx, int ax, double tin)
+{
+    if (!H || !(H->lod > 0.0)) return 1;
+    if (mode == 1) {
+        float size = bx[3 + ax] - bx[ax];
+        float thr = (float)H->lod * (float)tin;
+        return size > thr;
+    }
+    return ((double)bx[3 + ax] - (double)bx[ax]) > H->lod * tin;
+}
+
+/* Network ids and parents of every node (net: L + preorder rank for inner nodes). */
+static void or_hier_tables(const int *info, int n_nodes, int *net, int *parent)
+{
+    int nl = 0, ni = 0;
+    for (int i = 0; i < n_nodes; i++) if (info[6 * i] < 0) nl++;
+    for (int i = 0; i < n_nodes; i++) parent[i] = -1;
+    for (int i = 0; i < n_nodes; i++) {
+        if (info[6 * i] < 0) { net[i] = info[6 * i + 3]; continue; }
+        net[i] = nl + ni++;
+        parent[info[6 * i + 1]] = i;
+        parent[info[6 * i + 2]] = i;
+    }
+}
+
+/* One ray: ordered list of crossings (network id, entry, exit), at most maxc.
+ * method 0 = stack traversal (near child first: the child on the origin's side of the
+ * split plane; an origin on the plane goes left when d <= 0 along the axis), method 1 =
+ * the definition the stack form must reproduce: every leaf with a positive crossing
+ * sorted by entry; with hierarchical sampling (H, lod > 0) every node with a positive
+ * crossing whose strict ancestors all have positive crossings and descend, and which
+ * is a leaf or does not descend, sorted by entry. */
 static int or_trav_ray(const float *box, const int *info, const float *split, int n_nodes,
                        const float of[3], const float df[3], int maxc, int mode, int method,
-                       int *leaf, double *tin, double *tout)
+                       const or_hier *H, int *leaf, double *tin, double *tout)
 {
     float inv32[3];
     double o64[3], inv64[3];
@@ -234,6 +281,44 @@ static int or_trav_ray(const float *box, const int *info, const float *split, in
         inv64[a] = 1.0 / (double)df[a];
     }
     int cnt = 0;
+    const int hier = H && H->lod > 0.0;
+    if (method == 1 && hier) {
+        int nl = 0;
+        for (int i = 0; i < n_nodes; i++) {
+            double a0 = 0.0, a1 = 0.0;
+            int ok = 1;
+            /* the node itself, then its ancestors up to the root */
+            for (int j = i, first = 1; j >= 0 && ok; j = H->parent[j], first = 0) {
+                double e, x;
+                int hit;
+                if (mode == 1) {
+                    float ef, xf;
+                    hit = or_slab32(box + 6 * j, of, inv32, &ef, &xf);
+                    e = ef; x = xf;
+                } else {
+                    hit = or_slab64(box + 6 * j, o64, inv64, &e, &x);
+                }
+                if (!hit) { ok = 0; break; }
+                const int ax = info[6 * j];
+                const int desc = ax >= 0 && or_descends(H, mode, box + 6 * j, ax, e);
+                if (first) {
+                    if (desc) ok = 0;          /* an inner node that descends emits nothing */
+                    a0 = e; a1 = x;
+                } else if (!desc) {
+                    ok = 0;                    /* an ancestor stopped above this node */
+                }
+            }
+            if (!ok) continue;
+            int p = nl;
+            while (p > 0 && tin[p - 1] > a0) {
+                if (p < maxc) { leaf[p] = leaf[p - 1]; tin[p] = tin[p - 1]; tout[p] = tout[p - 1]; }
+                p--;
+            }
+            if (p < maxc) { leaf[p] = H->net[i]; tin[p] = a0; tout[p] = a1; }
+            if (nl < maxc) nl++;
+        }
+        return nl;
+    }
     if (method == 1) {
         int nl = 0;
         for (int i = 0; i < n_nodes; i++) {
@@ -279,6 +364,10 @@ static int or_trav_ray(const float *box, const int *info, const float *split, in
             continue;
         }
         int ax = inf[0];
+        if (hier && !or_descends(H, mode, box + 6 * nd, ax, a0)) {
+            leaf[cnt] = H->net[nd]; tin[cnt] = a0; tout[cnt] = a1; cnt++;
+            continue;
+        }
         int near_left = of[ax] < split[nd] || (of[ax] == split[nd] && df[ax] <= 0.0f);
         int nearc = near_left ? inf[1] : inf[2];
         int farc = near_left ? inf[2] : inf[1];
@@ -289,17 +378,32 @@ static int or_trav_ray(const float *box, const int *info, const float *split, in
     return cnt;
 }
 
+/* Hierarchical-sampling context for lod > 0 (NULL otherwise); free with free(). */
+static or_hier *or_hier_new(const int *info, int n_nodes, double lod)
+{
+    if (!(lod > 0.0)) return NULL;
+    or_hier *H = (or_hier *)malloc(sizeof(or_hier) + 2 * sizeof(int) * (size_t)n_nodes);
+    int *net = (int *)(H + 1);
+    int *parent = net + n_nodes;
+    or_hier_tables(info, n_nodes, net, parent);
+    H->lod = lod; H->net = net; H->parent = parent;
+    return H;
+}
+
 int or_traverse(const float *box, const int *info, const float *split, int n_nodes,
                 const float *o, const float *d, int64_t n, int maxc, int mode, int method,
-                int *n_x, int *leaf, double *tin, double *tout)
+                int *n_x, int *leaf, double *tin, double *tout, double lod)
 {
-    for (int64_t r = 0; r < n; r++) {
-        int c = or_trav_ray(box, info, split, n_nodes, o + 3 * r, d + 3 * r, maxc, mode, method,
+    or_hier *H = or_hier_new(info, n_nodes, lod);
+    int rc = 0;
+    for (int64_t r = 0; r < n && rc == 0; r++) {
+        int c = or_trav_ray(box, info, split, n_nodes, o + 3 * r, d + 3 * r, maxc, mode, method, H,
                             leaf + r * maxc, tin + r * maxc, tout + r * maxc);
-        if (c < 0) return -1;
-        n_x[r] = c;
+        if (c < 0) rc = -1;
+        else n_x[r] = c;
     }
-    return 0;
+    free(H);
+    return rc;
 }
 
 /* ======================================================================== */
@@ -687,6 +791,9 @@ typedef struct {
      * composited (sigma first limited to the largest binary16 value), to measure the
      * effect of a half-precision per-sample store on its own */
     int slot_f16;
+    /* adaptive hierarchical sampling (NULL: leaves only); crossings then carry
+     * network ids, leaves first, inner nodes after them in preorder */
+    const struct or_hier_s *hier;
     /* threading */
     int64_t r0, r1; int err;
 } or_job;
@@ -795,15 +902,16 @@ static int or_keep(int mode, const uint64_t *mask, double t0, double t1, const o
 int or_traverse_skip(const float *box, const int *info, const float *split, int n_nodes,
                      const float *o, const float *d, int64_t n, int maxc, int mode, int method, int steps,
                      uint64_t jitter, const float *occ_grid, int occ_G, const double *occ_bbox, double occ_thr,
-                     int *n_x, int *leaf, double *tin, double *tout)
+                     int *n_x, int *leaf, double *tin, double *tout, double lod)
 {
     or_occ oc;
     or_occ_init(&oc, occ_grid, occ_G, occ_bbox, occ_thr, steps, jitter);
+    or_hier *H = or_hier_new(info, n_nodes, lod);
     for (int64_t r = 0; r < n; r++) {
         int lf[256];
         double a[256], b[256];
-        int c = or_trav_ray(box, info, split, n_nodes, o + 3 * r, d + 3 * r, 256, mode, method, lf, a, b);
-        if (c < 0) return -1;
+        int c = or_trav_ray(box, info, split, n_nodes, o + 3 * r, d + 3 * r, 256, mode, method, H, lf, a, b);
+        if (c < 0) { free(H); return -1; }
         c = or_keep(mode, NULL, 0.0, 0.0, &oc, or_ray_key(jitter, o + 3 * r, d + 3 * r), o + 3 * r, d + 3 * r, lf, a,
                     b, c, maxc);
         for (int i = 0; i < c; i++) {
@@ -811,6 +919,7 @@ int or_traverse_skip(const float *box, const int *info, const float *split, int 
         }
         n_x[r] = c;
     }
+    free(H);
     return 0;
 }
 
@@ -829,14 +938,14 @@ static void or_render_ray(const or_job *J, int64_t r)
     const int masked = J->mask && !J->fallback[r];
     if (masked || J->occ) {
         nx = or_trav_ray(J->box, J->info, J->split, J->n_nodes, J->o + 3 * r, J->d + 3 * r,
-                         256, J->mode, 0, leaf, tin, tout);
+                         256, J->mode, 0, J->hier, leaf, tin, tout);
         if (nx < 0) nx = 0;
         nx = or_keep(J->mode, masked ? J->mask + r : NULL, root0, root1, J->occ,
                      or_ray_key(J->jitter, J->o + 3 * r, J->d + 3 * r), J->o + 3 * r, J->d + 3 * r, leaf, tin,
                      tout, nx, maxc);
     } else {
         nx = or_trav_ray(J->box, J->info, J->split, J->n_nodes, J->o + 3 * r, J->d + 3 * r,
-                         maxc, J->mode, 0, leaf, tin, tout);
+                         maxc, J->mode, 0, J->hier, leaf, tin, tout);
         if (nx < 0) nx = 0;
     }
     double *bins = J->bins ? J->bins + r * 65 : NULL;
@@ -949,7 +1058,7 @@ int or_render(const float *box, const int *info, const float *split, int n_nodes
               const float *occ_grid, int occ_G, const double *occ_bbox, double occ_thr, int n_threads,
               double *rgb, double *depth, double *opacity, int *n_gen, int *n_eval, double *ert_margin,
               double *slot_out, double *slot_w, double *t_final, const uint64_t *mask, const int *fallback,
-              double *bins, int slot_f16)
+              double *bins, int slot_f16, double lod)
 {
     if (steps < 1 || cap < steps || cap / steps > 256 || width > OR_MAXW || lx > 32 || ld > 32) return -1;
     if (n_threads < 1) n_threads = 1;
@@ -972,9 +1081,12 @@ int or_render(const float *box, const int *info, const float *split, int n_nodes
     base.ert_margin = ert_margin; base.slot_out = slot_out; base.slot_w = slot_w; base.t_final = t_final;
     base.mask = mask; base.fallback = fallback; base.bins = bins;
     base.slot_f16 = mode == 0 ? slot_f16 : 0;
+    or_hier *H = or_hier_new(info, n_nodes, lod);
+    base.hier = H;
     if (n_threads == 1 || n < 64) {
         base.r0 = 0; base.r1 = n;
         or_render_worker(&base);
+        free(H);
         return 0;
     }
     or_job *jobs = (or_job *)malloc(sizeof(or_job) * (size_t)n_threads);
@@ -993,7 +1105,7 @@ int or_render(const float *box, const int *info, const float *split, int n_nodes
         started = i + 1;
     }
     for (int i = 0; i < started; i++) if (th[i]) pthread_join(th[i], NULL);
-    free(jobs); free(th);
+    free(jobs); free(th); free(H);
     return 0;
 }
 
