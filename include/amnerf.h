@@ -143,6 +143,15 @@ typedef struct {
      * synchronisation).  With debug output, counts, offsets and order describe the
      * last wave; stage times put the whole wave loop under the network step. */
     int ert_wave;
+    /* Adaptive hierarchical sampling (Sec. 3.5, Algorithm 1's HCheck; Fig. 1 (c)):
+     * 0 = leaves only.  lod > 0 (finite): an inner node is descended only while its
+     * extent along its split axis exceeds lod x the ray's entry distance into it (FP32:
+     * hi - lo > lod * t_in); otherwise the inner node is one crossing, sampled like a
+     * leaf crossing and evaluated by the inner node's own network.  lod is the ray
+     * footprint per unit distance (about the pixel angle) times the number of
+     * footprints a node must span to be refined.  Needs one network per node
+     * (amnerf_load_mlps with the tree's node count). */
+    float lod;
 } amnerf_render_params;
 
 /* Schedule of the network step's tiles over the persistent workers (warpgroups). */
@@ -177,14 +186,15 @@ typedef struct {
 
 /* Optional copies of the intermediate results of one render (all DEVICE pointers
  * owned by the caller; any may be NULL).  maxc = floor(max_samples / steps).
+ * "Network" is the leaf id, or with lod > 0 the network id (leaves, then inner nodes).
  *   n_x      uint8  [n_rays]              crossings per ray
- *   leaf     uint16 [n_rays * maxc]       leaf id of crossing k of ray r at r*maxc+k
+ *   leaf     uint16 [n_rays * maxc]       network of crossing k of ray r at r*maxc+k
  *   t_in     float  [n_rays * maxc]       crossing entry
  *   t_out    float  [n_rays * maxc]       crossing exit
- *   counts   uint32 [n_leaves]            crossings per leaf (samples = steps x counts)
- *   offsets  uint32 [n_leaves + 1]        exclusive scan of counts
- *   order    uint32 [n_rays * maxc]       crossing ids r*maxc+k grouped by leaf; the
- *                                         order inside a leaf is unspecified
+ *   counts   uint32 [n_networks]          crossings per network (samples = steps x counts)
+ *   offsets  uint32 [n_networks + 1]      exclusive scan of counts
+ *   order    uint32 [n_rays * maxc]       crossing ids r*maxc+k grouped by network; the
+ *                                         order inside a network is unspecified
  *   slot_out float  [n_rays * max_samples * 4]  sigma, r, g, b of sample j of ray r at
  *                                         slot r*max_samples+j (unused slots untouched)
  *   prop_mask, prop_fallback              the proposal sampler's per-ray decisions
@@ -234,14 +244,19 @@ AMNERF_API amnerf_status amnerf_build_tree(amnerf_ctx *ctx, const float *grid_ho
  * the node count.  E_INVAL when cap is too small (*n_nodes still set). */
 AMNERF_API amnerf_status amnerf_get_tree(amnerf_ctx *ctx, amnerf_node *nodes_out, int cap, int *n_nodes);
 
-/* Load one network per leaf (Sec. 3.2: same shape for all leaves).
- * weights_host: HOST float32, leaf-major; per leaf, for each hidden layer W_l
+/* Load one network per leaf (Sec. 3.2: same shape for all leaves), or one per node
+ * (Sec. 3.3: inner nodes carry networks too; used by adaptive hierarchical sampling).
+ * n_leaves:     the tree's leaf count (leaf networks, by leaf id) or its node count
+ *               (networks 0 .. L-1 are the leaves by leaf id, then the inner nodes in
+ *               preorder: network L + r is the r-th inner node of amnerf_get_tree's
+ *               order).
+ * weights_host: HOST float32, network-major; per network, for each hidden layer W_l
  *               (width x fan_in, row = output, row-major) then b_l (width); then the
- *               head W_o (4 x width) and b_o (4).  n_leaves must equal the tree's.
+ *               head W_o (4 x width) and b_o (4).
  * The library repacks the weights into the layout of desc->prec (FP32 transposed
  * tiles, BF16 or E4M3 tcgen05 core-matrix tiles; E4M3 per-leaf, per-layer,
  * per-output-channel scales s = max|W_row| / 448).  Synchronous.
- * Errors: E_NOTREE, E_INVAL (shape unsupported or n_leaves mismatch), E_NOMEM. */
+ * Errors: E_NOTREE, E_INVAL (shape unsupported or n_leaves neither count), E_NOMEM. */
 AMNERF_API amnerf_status amnerf_load_mlps(amnerf_ctx *ctx, const amnerf_mlp_desc *desc, int n_leaves,
                                const float *weights_host);
 

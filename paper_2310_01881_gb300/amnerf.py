@@ -48,7 +48,7 @@ class amnerf_render_params(ctypes.Structure):
     _fields_ = [("steps_per_leaf", ctypes.c_int), ("max_samples", ctypes.c_int), ("t_term", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("use_proposal", ctypes.c_int), ("coverage", ctypes.c_float),
                 ("max_bins", ctypes.c_int), ("jitter_seed", ctypes.c_uint64), ("skip_empty", ctypes.c_int),
-                ("empty_threshold", ctypes.c_float), ("ert_wave", ctypes.c_int)]
+                ("empty_threshold", ctypes.c_float), ("ert_wave", ctypes.c_int), ("lod", ctypes.c_float)]
 
 
 PROPOSAL_PARAMS = 6113
@@ -220,31 +220,33 @@ def amnerf_load_mlps_fp8_static(ctx, weights: np.ndarray, n_leaves: int, width: 
 
 
 def amnerf_calibrate_fp8(ctx, o, d, n_leaves: int, hidden: int, steps: int = 8, cap: int = 64,
-                         t_term: float = 1e-4, bg=(0.0, 0.0, 0.0)) -> np.ndarray:
-    """Largest |input| of every hidden layer per leaf over the samples of these rays
-    (FP32 networks must be loaded); returns float32 [n_leaves, hidden]."""
+                         t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), lod: float = 0.0) -> np.ndarray:
+    """Largest |input| of every hidden layer per network over the samples of these rays
+    (FP32 networks must be loaded); returns float32 [n_networks, hidden]."""
     out = np.zeros((n_leaves, hidden), dtype=np.float32)
-    p = _params(steps, cap, t_term, bg)
+    p = _params(steps, cap, t_term, bg, lod=lod)
     _check(ctx, load().amnerf_calibrate_fp8(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _hptr(out)),
            "amnerf_calibrate_fp8")
     return out
 
 
 def _params(steps: int, cap: int, t_term: float, bg, proposal: bool = False, coverage: float = 0.99,
-            max_bins: int = 16, jitter: int = 0, skip_empty=None, ert_wave: int = 0) -> amnerf_render_params:
+            max_bins: int = 16, jitter: int = 0, skip_empty=None, ert_wave: int = 0,
+            lod: float = 0.0) -> amnerf_render_params:
     """jitter: 0 = samples at stratum midpoints, else the seed of the stratified jitter.
     skip_empty: None, or the density threshold of empty-space skipping.
-    ert_wave: 0 = one pass, else crossings per wave of early ray termination."""
+    ert_wave: 0 = one pass, else crossings per wave of early ray termination.
+    lod: 0 = leaves only, else the adaptive hierarchical sampling threshold."""
     return amnerf_render_params(steps, cap, t_term, (ctypes.c_float * 3)(*bg), int(proposal), coverage, max_bins,
                                 int(jitter) & ((1 << 64) - 1), int(skip_empty is not None),
-                                float(skip_empty) if skip_empty is not None else 0.0, int(ert_wave))
+                                float(skip_empty) if skip_empty is not None else 0.0, int(ert_wave), float(lod))
 
 
 def amnerf_render(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
                   bg=(0.0, 0.0, 0.0), stats: bool = False, proposal: bool = False, coverage: float = 0.99,
-                  max_bins: int = 16, jitter: int = 0, skip_empty=None, ert_wave: int = 0):
+                  max_bins: int = 16, jitter: int = 0, skip_empty=None, ert_wave: int = 0, lod: float = 0.0):
     """Enqueue a render of CUDA tensors o, d (n, 3) into rgb (n, 3), depth, opacity (n,)."""
-    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter, skip_empty, ert_wave)
+    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter, skip_empty, ert_wave, lod)
     sp = amnerf_stats() if stats else None
     st = load().amnerf_render(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
                               _ptr(opacity), ctypes.byref(sp) if sp is not None else None)
@@ -255,8 +257,8 @@ def amnerf_render(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64,
 def amnerf_render_debug(ctx, o, d, rgb, depth, opacity, dbg: dict, steps: int = 8, cap: int = 64,
                         t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), stats: bool = True, proposal: bool = False,
                         coverage: float = 0.99, max_bins: int = 16, jitter: int = 0, skip_empty=None,
-                        ert_wave: int = 0):
-    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter, skip_empty, ert_wave)
+                        ert_wave: int = 0, lod: float = 0.0):
+    p = _params(steps, cap, t_term, bg, proposal, coverage, max_bins, jitter, skip_empty, ert_wave, lod)
     db = amnerf_debug(*[_ptr(dbg.get(k)) for k, _ in amnerf_debug._fields_])
     sp = amnerf_stats() if stats else None
     st = load().amnerf_render_debug(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
@@ -268,12 +270,12 @@ def amnerf_render_debug(ctx, o, d, rgb, depth, opacity, dbg: dict, steps: int = 
 def amnerf_render_host(ctx, o: np.ndarray, d: np.ndarray, rgb: np.ndarray, depth: np.ndarray,
                        opacity: np.ndarray, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
                        bg=(0.0, 0.0, 0.0), stats: bool = False, jitter: int = 0, skip_empty=None,
-                       ert_wave: int = 0):
+                       ert_wave: int = 0, lod: float = 0.0):
     """Render from HOST arrays (page-locked buffers make the copies asynchronous)."""
     for a in (o, d, rgb, depth, opacity):
         if a.dtype != np.float32 or not a.flags.c_contiguous:
             raise ValueError("host buffers must be contiguous float32")
-    p = _params(steps, cap, t_term, bg, jitter=jitter, skip_empty=skip_empty, ert_wave=ert_wave)
+    p = _params(steps, cap, t_term, bg, jitter=jitter, skip_empty=skip_empty, ert_wave=ert_wave, lod=lod)
     sp = amnerf_stats() if stats else None
     st = load().amnerf_render_host(ctx, _hptr(o), _hptr(d), o.shape[0], ctypes.byref(p), _hptr(rgb),
                                    _hptr(depth), _hptr(opacity), ctypes.byref(sp) if sp is not None else None)
@@ -303,9 +305,9 @@ def amnerf_get_tuning(ctx) -> tuple[int, int, int]:
 
 
 def amnerf_autotune(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
-                    bg=(0.0, 0.0, 0.0), reps: int = 3) -> tuple[int, int, float]:
+                    bg=(0.0, 0.0, 0.0), reps: int = 3, lod: float = 0.0) -> tuple[int, int, float]:
     """Time every launch configuration on this batch; returns (groups, schedule, ms)."""
-    p = _params(steps, cap, t_term, bg)
+    p = _params(steps, cap, t_term, bg, lod=lod)
     best = amnerf_tuning()
     ms = ctypes.c_float()
     st = load().amnerf_autotune(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
@@ -390,6 +392,7 @@ class Renderer:
         torch.cuda.set_device(self.device)
         self.ctx = amnerf_create(self.device, torch.cuda.current_stream(self.device).cuda_stream)
         self.n_leaves = 0
+        self.n_nets = 0
 
     def close(self):
         if getattr(self, "ctx", None) is not None:
@@ -414,21 +417,33 @@ class Renderer:
         nodes.sort(key=lambda n: n.leaf_id)
         return np.array([list(n.cell_lo) + list(n.cell_hi) for n in nodes], dtype=np.int64)
 
+    def network_cells(self) -> np.ndarray:
+        """Cell ranges of every node in network order: the leaves by leaf id, then the
+        inner nodes in preorder (one network per node, adaptive hierarchical sampling)."""
+        tree = self.tree()
+        leaves = sorted((n for n in tree if n.axis < 0), key=lambda n: n.leaf_id)
+        inner = [n for n in tree if n.axis >= 0]
+        return np.array([list(n.cell_lo) + list(n.cell_hi) for n in leaves + inner], dtype=np.int64)
+
     def load_mlps(self, weights, width, hidden, lx, ld, prec="fp32", act_max=None) -> None:
         """prec: "fp32", "bf16", "fp8" (per-row activation scales) or, with act_max
-        (see calibrate_fp8), E4M3 with static per-leaf, per-layer activation scales."""
+        (see calibrate_fp8), E4M3 with static per-leaf, per-layer activation scales.
+        One network per leaf, or per node when the weights hold that many."""
+        per = (3 + 6 * lx + 3 + 6 * ld) * width + width + (hidden - 1) * (width * width + width) + 4 * width + 4
+        self.n_nets = int(np.asarray(weights).size // per)
         if act_max is not None:
-            amnerf_load_mlps_fp8_static(self.ctx, weights, self.n_leaves, width, hidden, lx, ld, act_max)
+            amnerf_load_mlps_fp8_static(self.ctx, weights, self.n_nets, width, hidden, lx, ld, act_max)
         else:
-            amnerf_load_mlps(self.ctx, weights, self.n_leaves, width, hidden, lx, ld, PRECISIONS.get(prec, prec))
+            amnerf_load_mlps(self.ctx, weights, self.n_nets, width, hidden, lx, ld, PRECISIONS.get(prec, prec))
 
-    def calibrate_fp8(self, o, d, hidden, steps=8, cap=64, t_term=1e-4):
+    def calibrate_fp8(self, o, d, hidden, steps=8, cap=64, t_term=1e-4, lod=0.0):
         torch = self._torch
         amnerf_set_stream(self.ctx, torch.cuda.current_stream(o.device).cuda_stream)
-        return amnerf_calibrate_fp8(self.ctx, o, d, self.n_leaves, hidden, steps=steps, cap=cap, t_term=t_term)
+        return amnerf_calibrate_fp8(self.ctx, o, d, self.n_nets, hidden, steps=steps, cap=cap, t_term=t_term,
+                                    lod=lod)
 
     def render(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0), stats=False, out=None,
-               proposal=False, coverage=0.99, max_bins=16, jitter=0, skip_empty=None, ert_wave=0):
+               proposal=False, coverage=0.99, max_bins=16, jitter=0, skip_empty=None, ert_wave=0, lod=0.0):
         torch = self._torch
         n = o.shape[0]
         if out is None:
@@ -438,11 +453,11 @@ class Renderer:
         amnerf_set_stream(self.ctx, torch.cuda.current_stream(o.device).cuda_stream)
         s = amnerf_render(self.ctx, o, d, *out, steps=steps, cap=cap, t_term=t_term, bg=bg, stats=stats,
                           proposal=proposal, coverage=coverage, max_bins=max_bins, jitter=jitter,
-                          skip_empty=skip_empty, ert_wave=ert_wave)
+                          skip_empty=skip_empty, ert_wave=ert_wave, lod=lod)
         return (*out, s) if stats else out
 
     def render_debug(self, o, d, steps=8, cap=64, t_term=1e-4, bg=(0.0, 0.0, 0.0), proposal=False, coverage=0.99,
-                     max_bins=16, jitter=0, skip_empty=None, ert_wave=0):
+                     max_bins=16, jitter=0, skip_empty=None, ert_wave=0, lod=0.0):
         torch = self._torch
         n = o.shape[0]
         maxc = cap // steps
@@ -452,8 +467,8 @@ class Renderer:
             "leaf": torch.zeros(n * maxc, dtype=torch.int16, device=dev),
             "t_in": torch.zeros(n * maxc, dtype=torch.float32, device=dev),
             "t_out": torch.zeros(n * maxc, dtype=torch.float32, device=dev),
-            "counts": torch.zeros(max(self.n_leaves, 1), dtype=torch.int32, device=dev),
-            "offsets": torch.zeros(self.n_leaves + 1, dtype=torch.int32, device=dev),
+            "counts": torch.zeros(max(self.n_nets, 1), dtype=torch.int32, device=dev),
+            "offsets": torch.zeros(self.n_nets + 1, dtype=torch.int32, device=dev),
             "order": torch.zeros(max(n * maxc, 1), dtype=torch.int32, device=dev),
             "slot_out": torch.zeros(max(n * cap * 4, 1), dtype=torch.float32, device=dev),
         }
@@ -467,13 +482,13 @@ class Renderer:
         amnerf_set_stream(self.ctx, torch.cuda.current_stream(dev).cuda_stream)
         s = amnerf_render_debug(self.ctx, o, d, rgb, depth, opac, dbg, steps=steps, cap=cap, t_term=t_term, bg=bg,
                                 proposal=proposal, coverage=coverage, max_bins=max_bins, jitter=jitter,
-                                skip_empty=skip_empty, ert_wave=ert_wave)
+                                skip_empty=skip_empty, ert_wave=ert_wave, lod=lod)
         host = {k: v.cpu().numpy() for k, v in dbg.items()}
         host["leaf"] = host["leaf"].view(np.uint16).astype(np.int64).reshape(n, maxc)
         host["t_in"] = host["t_in"].reshape(n, maxc)
         host["t_out"] = host["t_out"].reshape(n, maxc)
         host["order"] = host["order"].view(np.uint32).astype(np.int64)
-        host["counts"] = host["counts"].view(np.uint32).astype(np.int64)[: self.n_leaves]
+        host["counts"] = host["counts"].view(np.uint32).astype(np.int64)[: self.n_nets]
         host["offsets"] = host["offsets"].view(np.uint32).astype(np.int64)
         host["slot_out"] = host["slot_out"][: n * cap * 4].reshape(n, cap, 4)
         if proposal:

@@ -21,6 +21,7 @@ struct DevNode {
 
 constexpr int kTileRows = 128;   // samples per network tile (tcgen05 M)
 constexpr int kMaxLeaves = 4096; // 2^12 leaves at depth 12
+constexpr int kMaxNets = 2 * kMaxLeaves;  // one network per node: leaves, then inner nodes (< 8192)
 constexpr int kMaxDepth = 12;
 constexpr int kStackDepth = 16;  // traversal stack (depth + 1 entries suffice)
 
@@ -69,12 +70,20 @@ struct OccArgs {
     uint64_t jitter = 0;
 };
 
-// K-a: traversal + crossing list + per-leaf crossing histogram.
+// Adaptive hierarchical sampling (lod <= 0 or node_net == nullptr: leaves only): an
+// inner node is descended only while its extent along its split axis exceeds lod x the
+// ray's entry distance into it; otherwise it is one crossing of network node_net[node].
+struct HierArgs {
+    float lod = 0.f;
+    const uint16_t* node_net = nullptr;
+};
+
+// K-a: traversal + crossing list + per-network crossing histogram (n_nets counters).
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
                             int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
-                            int n_leaves, int* err, const uint64_t* mask = nullptr,
+                            int n_nets, int* err, const uint64_t* mask = nullptr,
                             const uint8_t* fallback = nullptr, float2* root_out = nullptr,
-                            const OccArgs& occ = OccArgs());
+                            const OccArgs& occ = OccArgs(), const HierArgs& hier = HierArgs());
 
 // K-b: exclusive scans (crossings and network tiles per leaf) and the grouped scatter.
 // acc (may be NULL) accumulates (crossings, tiles) over the waves of one render.
@@ -88,6 +97,9 @@ cudaError_t launch_scatter(cudaStream_t s, const uint8_t* n_x, const uint16_t* x
 cudaError_t launch_scatter_wave(cudaStream_t s, bool count, const uint8_t* n_x, const uint16_t* xleaf,
                                 uint32_t n_rays, int maxc, int k_lo, int k_hi, const uint8_t* alive, uint32_t* cursor,
                                 uint32_t* order, int n_leaves);
+// Kernel attributes of the grouping kernels (their shared memory grows with the number
+// of networks, up to kMaxNets); call once per device before a render.
+cudaError_t prepare_group();
 
 // Tile schedules of the network kernels (values of amnerf_tuning.schedule).
 constexpr int kSchedContiguous = 0;   // worker w takes tiles [w * per, (w + 1) * per)

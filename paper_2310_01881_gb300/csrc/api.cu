@@ -25,16 +25,18 @@ struct amnerf_ctx {
     std::vector<amnerf_node> nodes;
     int n_leaves = 0;
     DevNode* d_nodes = nullptr;
+    uint16_t* d_node_net = nullptr;  // network id of every node (leaves: leaf id; inner: L + preorder rank)
     float* d_grid = nullptr;  // the guidance grid (empty-space skipping)
     int grid_G = 0;
     float grid_lo[3] = {0.f, 0.f, 0.f}, grid_sc[3] = {0.f, 0.f, 0.f};
     // networks
     bool mlp_loaded = false;
+    int n_nets = 0;           // networks loaded: n_leaves, or one per node (hierarchical sampling)
     amnerf_mlp_desc desc{};
     int k0 = 0;
     size_t leaf_stride = 0;  // bytes
     void* d_weights = nullptr;
-    // per-leaf scratch (sized for kMaxLeaves)
+    // per-network scratch (sized for kMaxNets)
     uint32_t* d_counts = nullptr;
     uint32_t* d_offsets = nullptr;
     uint32_t* d_tile_off = nullptr;
@@ -164,6 +166,7 @@ amnerf_status check_params(amnerf_ctx* ctx, const amnerf_render_params* p, int64
         return fail(ctx, AMNERF_E_INVAL, "n_rays * floor(max_samples / steps_per_leaf) must be < 2^32 (split the batch)");
     if (p->ert_wave < 0 || p->ert_wave > 255) return fail(ctx, AMNERF_E_INVAL, "ert_wave must be in [0, 255]");
     if (p->ert_wave > 0 && st != 8) return fail(ctx, AMNERF_E_INVAL, "ert_wave needs steps_per_leaf = 8");
+    if (!(p->lod >= 0.0f) || !std::isfinite(p->lod)) return fail(ctx, AMNERF_E_INVAL, "lod must be finite and >= 0");
     return AMNERF_OK;
 }
 
@@ -262,10 +265,11 @@ amnerf_status amnerf_create(amnerf_ctx** out, int device, void* cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
     cudaError_t e;
     if ((e = cudaSetDevice(device)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&ctx->d_counts, sizeof(uint32_t) * kMaxLeaves)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&ctx->d_offsets, sizeof(uint32_t) * (kMaxLeaves + 1))) != cudaSuccess ||
-        (e = cudaMalloc((void**)&ctx->d_tile_off, sizeof(uint32_t) * (kMaxLeaves + 1))) != cudaSuccess ||
-        (e = cudaMalloc((void**)&ctx->d_cursor, sizeof(uint32_t) * kMaxLeaves)) != cudaSuccess ||
+        (e = prepare_group()) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_counts, sizeof(uint32_t) * kMaxNets)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_offsets, sizeof(uint32_t) * (kMaxNets + 1))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_tile_off, sizeof(uint32_t) * (kMaxNets + 1))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_cursor, sizeof(uint32_t) * kMaxNets)) != cudaSuccess ||
         (e = cudaMalloc((void**)&ctx->d_stats, sizeof(uint64_t) * kStatSlots)) != cudaSuccess ||
         (e = cudaMalloc((void**)&ctx->d_err, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(ctx->d_err, 0, sizeof(int))) != cudaSuccess) {
@@ -296,6 +300,7 @@ void amnerf_destroy(amnerf_ctx* ctx) {
     else cudaDeviceSynchronize();
     free_ray_scratch(ctx);
     dfree(ctx->d_nodes);
+    dfree(ctx->d_node_net);
     dfree(ctx->d_grid);
     dfree(ctx->d_weights);
     dfree(ctx->d_amax);
@@ -336,6 +341,9 @@ amnerf_status amnerf_build_tree(amnerf_ctx* ctx, const float* grid_host, int G, 
     if (!build_kdtree(grid_host, G, bbox, params->max_depth, params->leaf_mass_frac, nodes, nl, err))
         return fail(ctx, AMNERF_E_INVAL, err);
     std::vector<DevNode> dn(nodes.size());
+    std::vector<uint16_t> net(nodes.size());
+    for (size_t i = 0, inner = 0; i < nodes.size(); ++i)
+        net[i] = (uint16_t)(nodes[i].axis < 0 ? nodes[i].leaf_id : nl + (int)inner++);
     for (size_t i = 0; i < nodes.size(); ++i) {
         const amnerf_node& s = nodes[i];
         const uint32_t payload = s.axis < 0 ? (uint32_t)s.leaf_id : (uint32_t)s.right;
@@ -347,10 +355,14 @@ amnerf_status amnerf_build_tree(amnerf_ctx* ctx, const float* grid_host, int G, 
     }
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     dfree(ctx->d_nodes);
+    dfree(ctx->d_node_net);
     dfree(ctx->d_grid);
     ctx->grid_G = 0;
     CK(cudaMalloc((void**)&ctx->d_nodes, sizeof(DevNode) * dn.size()), "tree allocation");
     CK(cudaMemcpy(ctx->d_nodes, dn.data(), sizeof(DevNode) * dn.size(), cudaMemcpyHostToDevice), "tree upload");
+    CK(cudaMalloc((void**)&ctx->d_node_net, sizeof(uint16_t) * net.size()), "tree allocation");
+    CK(cudaMemcpy(ctx->d_node_net, net.data(), sizeof(uint16_t) * net.size(), cudaMemcpyHostToDevice),
+       "tree upload");
     // the guidance grid stays resident for empty-space skipping
     const size_t cells = (size_t)G * G * G;
     CK(cudaMalloc((void**)&ctx->d_grid, sizeof(float) * cells), "grid allocation");
@@ -381,7 +393,8 @@ static amnerf_status load_impl(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int
                                const float* weights_host, const float* act_max) {
     if (!ctx || !desc || !weights_host) return fail(ctx, AMNERF_E_INVAL, "NULL argument");
     if (ctx->nodes.empty()) return fail(ctx, AMNERF_E_NOTREE, "build the tree first");
-    if (n_leaves != ctx->n_leaves) return fail(ctx, AMNERF_E_INVAL, "n_leaves does not match the tree");
+    if (n_leaves != ctx->n_leaves && n_leaves != (int)ctx->nodes.size())
+        return fail(ctx, AMNERF_E_INVAL, "n_networks must be the tree's leaf count or its node count");
     const amnerf_mlp_desc& m = *desc;
     if ((m.width != 32 && m.width != 64) || m.hidden < 1 || m.hidden > 8 || m.lx < 0 || m.lx > 12 || m.ld < 0 ||
         m.ld > 6)
@@ -422,6 +435,7 @@ static amnerf_status load_impl(amnerf_ctx* ctx, const amnerf_mlp_desc* desc, int
     CK(cudaMalloc(&ctx->d_weights, blob.size()), "weight allocation");
     CK(cudaMemcpy(ctx->d_weights, blob.data(), blob.size(), cudaMemcpyHostToDevice), "weight upload");
     ctx->desc = m;
+    ctx->n_nets = n_leaves;
     ctx->k0 = k0;
     ctx->leaf_stride = stride;
     ctx->max_groups = max_groups;
@@ -439,7 +453,8 @@ amnerf_status amnerf_load_mlps_fp8_static(amnerf_ctx* ctx, const amnerf_mlp_desc
                                          const float* weights_host, const float* act_max_host) {
     if (!ctx || !desc || !act_max_host) return fail(ctx, AMNERF_E_INVAL, "NULL argument");
     if (desc->prec != AMNERF_FP8E4M3) return fail(ctx, AMNERF_E_INVAL, "static activation scales are for E4M3");
-    if (desc->hidden < 1 || desc->hidden > 8 || n_leaves < 1) return fail(ctx, AMNERF_E_INVAL, "bad shape");
+    if (desc->hidden < 1 || desc->hidden > 8 || n_leaves < 1 || n_leaves > kMaxNets)
+        return fail(ctx, AMNERF_E_INVAL, "bad shape");
     for (size_t i = 0; i < (size_t)n_leaves * desc->hidden; ++i)
         if (!(act_max_host[i] >= 0.0f) || !std::isfinite(act_max_host[i]))
             return fail(ctx, AMNERF_E_INVAL, "act_max must be finite and >= 0");
@@ -463,9 +478,14 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         st = ensure_scratch(ctx, (size_t)n, maxc, cap);
         if (st != AMNERF_OK) return st;
     }
+    if (p->lod > 0.0f && ctx->n_nets != (int)ctx->nodes.size())
+        return fail(ctx, AMNERF_E_INVAL, "lod > 0 needs one network per node");
     cudaStream_t s = ctx->stream;
-    const int L = ctx->n_leaves;
+    const int L = ctx->n_nets;  // networks: the grouping keys
     const uint32_t nn = (uint32_t)n;
+    HierArgs hier;
+    hier.lod = p->lod;
+    hier.node_net = ctx->d_node_net;
     if (ctx->timing) cudaEventRecord(ctx->ev[0], s);
     CK(cudaMemsetAsync(ctx->d_counts, 0, sizeof(uint32_t) * L, s), "memset");
     CK(cudaMemsetAsync(ctx->d_stats, 0, sizeof(uint64_t) * kStatSlots, s), "memset");
@@ -499,7 +519,7 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         occ.jitter = p->jitter_seed;
     }
     CK(launch_traverse(s, ro, rd, nn, ctx->d_nodes, maxc, ctx->d_nx, ctx->d_xing, ctx->d_xleaf, ctx->d_counts, L,
-                       ctx->d_err, mask, fallback, root_out, occ),
+                       ctx->d_err, mask, fallback, root_out, occ, hier),
        "traverse launch");
     if (ctx->timing) cudaEventRecord(ctx->ev[1], s);
     CK(launch_scan(s, ctx->d_counts, L, kTileRows / steps, ctx->d_offsets, ctx->d_tile_off, ctx->d_cursor,
@@ -689,7 +709,7 @@ amnerf_status amnerf_calibrate_fp8(amnerf_ctx* ctx, const float* rays_o, const f
     if (ctx->desc.prec != AMNERF_FP32) return fail(ctx, AMNERF_E_INVAL, "calibration runs the FP32 networks");
     if (params && params->use_proposal) return fail(ctx, AMNERF_E_INVAL, "calibrate with the plain sampler");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const size_t cnt = (size_t)ctx->n_leaves * ctx->desc.hidden;
+    const size_t cnt = (size_t)ctx->n_nets * ctx->desc.hidden;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     dfree(ctx->d_amax);
     CK(cudaMalloc((void**)&ctx->d_amax, sizeof(float) * cnt), "calibration allocation");

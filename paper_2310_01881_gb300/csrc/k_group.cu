@@ -1,8 +1,8 @@
 // k_group.cu -- K-b: group crossings by leaf (Sec. 3.5 and Fig. "parallel": samples
 // are sorted by node id so that every node's network runs as one dense batch).
 //
-// The keys are small integers (leaf ids < 4096), so the sort is a one-digit counting
-// sort.  Per-leaf totals come from K-a's histogram; one CTA scans them into crossing
+// The keys are small integers (network ids < 8192: leaves, and inner nodes with
+// adaptive hierarchical sampling), so the sort is a one-digit counting sort.  Per-leaf totals come from K-a's histogram; one CTA scans them into crossing
 // offsets and network-tile offsets (a tile holds 128 / steps crossings of one leaf).
 // The scatter stages its binning in shared memory: each CTA ranks its crossings per
 // leaf with shared atomics, reserves one contiguous range per touched leaf with a
@@ -15,7 +15,7 @@ namespace amnerf {
 namespace {
 
 constexpr int kScanThreads = 1024;
-constexpr int kScanPer = kMaxLeaves / kScanThreads;  // 4 leaves per thread
+constexpr int kScanPer = kMaxNets / kScanThreads;  // 8 networks per thread
 
 __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restrict__ counts, int n_leaves, int cpt,
                                                        uint32_t* __restrict__ offsets,
@@ -235,6 +235,17 @@ cudaError_t launch_scatter_wave(cudaStream_t s, bool count, const uint8_t* n_x, 
         k_scatter_wave<false><<<blocks, kScatterThreads, smem, s>>>(n_x, xleaf, (uint32_t)n_items, maxc, k_lo, W,
                                                                     alive, cursor, order, n_leaves);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_group() {
+    // two counters per network: up to 64 KB of dynamic shared memory
+    const int smem = (int)(2 * sizeof(uint32_t) * kMaxNets);
+    cudaError_t e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_scatter_wave<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_scatter_wave<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
 }
 
 }  // namespace amnerf

@@ -21,6 +21,12 @@
 // its samples -- placed as it would be as the ray's next kept crossing, in the
 // sampling step's FP32 order -- lies in a guidance-grid cell above the threshold;
 // skipped crossings do not count toward maxc.
+// With adaptive hierarchical sampling (Sec. 3.5, Algorithm 1's HCheck; Fig. 1 (c)) an
+// inner node is descended only while its extent along its split axis, hi - lo (exact
+// for the dyadic boxes of the tree), exceeds lod x entry (the product rounded to FP32):
+// a subdivision finer than the ray's footprint at that distance is not resolved, and
+// the inner node becomes one crossing of its own network (id L + preorder rank of the
+// inner node); the proposal and empty-space rules apply to it as to a leaf.
 #include "amnerf_internal.h"
 
 namespace amnerf {
@@ -97,7 +103,7 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
                                                   int n_leaves, int* __restrict__ err,
                                                   const uint64_t* __restrict__ mask,
                                                   const uint8_t* __restrict__ fallback, float2* __restrict__ root_out,
-                                                  const OccArgs occ) {
+                                                  const OccArgs occ, const HierArgs hier) {
     extern __shared__ uint32_t s_cnt[];
     for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) s_cnt[i] = 0u;
     __syncthreads();
@@ -148,13 +154,19 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
             if (!slab(A, B, o, inv, tin, tout)) continue;
             const uint32_t meta = __float_as_uint(B.w);
             const int axis = (int)(meta & 3u) - 1;
-            if (axis < 0) {
+            // HCheck: an inner node finer than the footprint is one crossing of its own network
+            bool emit = axis < 0;
+            if (!emit && hier.node_net) {
+                const float ext = axis == 0 ? __fsub_rn(B.x, A.x) : (axis == 1 ? __fsub_rn(B.y, A.y) : __fsub_rn(B.z, A.z));
+                emit = !(ext > __fmul_rn(hier.lod, tin));
+            }
+            if (emit) {
                 if (masked && !overlaps_kept(kept_bins, r0, bw, tin, tout)) continue;
                 if (occ.grid && !crossing_occupied(occ, o, d, key, tin, tout, cnt)) continue;
-                const uint32_t leaf = meta >> 2;
+                const uint32_t net = axis < 0 ? meta >> 2 : (uint32_t)__ldg(hier.node_net + nd);
                 xing[base + cnt] = make_float2(tin, tout);
-                xleaf[base + cnt] = (uint16_t)leaf;
-                atomicAdd(&s_cnt[leaf], 1u);
+                xleaf[base + cnt] = (uint16_t)net;
+                atomicAdd(&s_cnt[net], 1u);
                 ++cnt;
                 continue;
             }
@@ -190,13 +202,15 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
                             int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
                             int n_leaves, int* err, const uint64_t* mask, const uint8_t* fallback,
-                            float2* root_out, const OccArgs& occ) {
+                            float2* root_out, const OccArgs& occ, const HierArgs& hier) {
     if (n == 0) return cudaSuccess;
     const int threads = 256;
     const unsigned blocks = (n + threads - 1) / threads;
     const size_t smem = sizeof(uint32_t) * (size_t)n_leaves;
+    HierArgs h = hier;
+    if (!(h.lod > 0.0f)) h.node_net = nullptr;
     k_traverse<<<blocks, threads, smem, s>>>(ro, rd, n, nodes, maxc, n_x, xing, xleaf, counts, n_leaves, err, mask,
-                                             fallback, root_out, occ);
+                                             fallback, root_out, occ, h);
     return cudaGetLastError();
 }
 
