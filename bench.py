@@ -22,6 +22,7 @@ from __future__ import annotations
 import argparse
 import dataclasses
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -152,7 +153,14 @@ def workload_name(cfg, args) -> str:
             + (f", empty-space skipping (density > {args.skip_empty:g})"
                if getattr(args, "skip_empty", None) is not None else "")
             + (f", early ray termination in waves of {args.ert_wave} crossings"
-               if getattr(args, "ert_wave", 0) else ""))
+               if getattr(args, "ert_wave", 0) else "")
+            + (f", adaptive hierarchical sampling (nodes refined while wider than {args.lod_px:g} pixels)"
+               if getattr(args, "lod_px", 0) else ""))
+
+
+def pixel_angle(cfg, px=None) -> float:
+    """Vertical angle of one pixel of the workload's camera (radians)."""
+    return 2.0 * math.tan(math.radians(cfg.fov_deg / 2.0)) / (px or cfg.px_h)
 
 
 def barrier():
@@ -217,7 +225,9 @@ def run_ours(args):
     n = len(o_np)
     R = amnerf.Renderer(local)
     R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
-    P = S.xavier_weights(0, S.leaf_mean_density(grid, R.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    lod = args.lod_px * pixel_angle(cfg, args.px) if args.lod_px else 0.0
+    cells = R.network_cells() if lod > 0 else R.leaf_cells()   # one network per node with hierarchical sampling
+    P = S.xavier_weights(0, S.leaf_mean_density(grid, cells), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
     o = torch.from_numpy(o_np).cuda()
     d = torch.from_numpy(d_np).cuda()
     out = (torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"), torch.empty(n, device="cuda"))
@@ -231,15 +241,15 @@ def run_ours(args):
             R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, "fp32")
             oc, dc = S.view_rays(cfg, 0, 1000 + rank, args.px, args.px)
             amax = R.calibrate_fp8(torch.from_numpy(oc).cuda(), torch.from_numpy(dc).cuda(), cfg.hidden,
-                                   steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term)
+                                   steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term, lod=lod)
             R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, act_max=amax)
         else:
             R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, prec)
         for _ in range(args.warmup):
             R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter, skip_empty=args.skip_empty,
-                     ert_wave=args.ert_wave)
+                     ert_wave=args.ert_wave, lod=lod)
         _, _, _, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter,
-                               skip_empty=args.skip_empty, ert_wave=args.ert_wave)
+                               skip_empty=args.skip_empty, ert_wave=args.ert_wave, lod=lod)
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -248,7 +258,7 @@ def run_ours(args):
             e0.record(stream)
             for _ in range(args.steps):
                 R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter, skip_empty=args.skip_empty,
-                         ert_wave=args.ert_wave)
+                         ert_wave=args.ert_wave, lod=lod)
             e1.record(stream)
             torch.cuda.synchronize()
         barrier()
@@ -259,7 +269,7 @@ def run_ours(args):
         stage = np.zeros(4)
         for _ in range(args.steps):
             *_, s2 = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter,
-                              skip_empty=args.skip_empty, ert_wave=args.ert_wave)
+                              skip_empty=args.skip_empty, ert_wave=args.ert_wave, lod=lod)
             stage += np.array(s2["ms"])
         amnerf.amnerf_set_timing(R.ctx, False)
         stage /= args.steps
@@ -284,12 +294,12 @@ def run_ours(args):
             torch.empty(n, dtype=torch.float32).pin_memory().numpy()]
     for _ in range(max(1, args.warmup)):
         amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term,
-                                  jitter=args.jitter, skip_empty=args.skip_empty, ert_wave=args.ert_wave)
+                                  jitter=args.jitter, skip_empty=args.skip_empty, ert_wave=args.ert_wave, lod=lod)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         amnerf.amnerf_render_host(R.ctx, ho, hd, *hout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term,
-                                  jitter=args.jitter, skip_empty=args.skip_empty, ert_wave=args.ert_wave)
+                                  jitter=args.jitter, skip_empty=args.skip_empty, ert_wave=args.ert_wave, lod=lod)
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
     barrier()
 
@@ -302,13 +312,14 @@ def run_ours(args):
     # accuracy against the FP64 oracle on a seeded ray subset + the oracle's own speed
     import oracle as O
     tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
-    P_or = S.xavier_weights(0, S.leaf_mean_density(grid, tree.leaf_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    cells_or = tree.network_cells() if lod > 0 else tree.leaf_cells()
+    P_or = S.xavier_weights(0, S.leaf_mean_density(grid, cells_or), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
     idx = S.ray_subset(n, args.psnr_rays, 7)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     ref = O.render(tree, P_or, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps, cfg.cap,
                    cfg.t_term, mode=0, threads=cores, jitter=args.jitter,
-                   skip=(grid, args.skip_empty) if args.skip_empty is not None else None)
+                   skip=(grid, args.skip_empty) if args.skip_empty is not None else None, lod=lod)
     cpu_s = time.perf_counter() - t0
     cpu_samples = int(ref["n_gen"].sum())
     acc = {}
@@ -394,6 +405,68 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_ahs(args, grid=None, lods_px=(64.0, 128.0)) -> dict:
+    """Adaptive hierarchical sampling on the 4096-leaf workload (16 views of 1920x1080,
+    one network per node, BF16): leaf-only against nodes refined only while wider than
+    K pixels at the ray's entry distance.  Per setting: time per step, samples per ray,
+    and PSNR against the FP64 oracle of the same method on a seeded ray subset."""
+    import torch
+
+    from paper_2310_01881_gb300 import amnerf, build
+
+    torch.cuda.set_device(0)
+    build.build()
+    cfg = S.CONFIGS["c4"]
+    if grid is None:
+        grid = S.density_grid(S.scene_for(cfg.scene, 0), cfg.G)
+    rays = [S.view_rays(cfg, 0, v) for v in range(cfg.views)]
+    o_np = np.concatenate([r[0] for r in rays]); d_np = np.concatenate([r[1] for r in rays])
+    del rays
+    n = len(o_np)
+    R = amnerf.Renderer(0)
+    R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    P = S.xavier_weights(0, S.leaf_mean_density(grid, R.network_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, "bf16")
+    o = torch.from_numpy(o_np).cuda(); d = torch.from_numpy(d_np).cuda()
+    out = (torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"), torch.empty(n, device="cuda"))
+    stream = torch.cuda.current_stream()
+    import oracle as O
+    tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    P_or = S.xavier_weights(0, S.leaf_mean_density(grid, tree.network_cells()), cfg.width, cfg.hidden, cfg.lx, cfg.ld)
+    idx = S.ray_subset(n, 4096, 13)
+    rows = []
+    with ClockSampler(0) as clk:
+        for k in (0.0,) + tuple(lods_px):
+            lod = k * pixel_angle(cfg)
+            for _ in range(args.warmup):
+                R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, lod=lod)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, lod=lod)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            *_, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, lod=lod)
+            rgb = out[0].cpu().numpy().astype(np.float64)
+            ref = O.render(tree, P_or, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o_np[idx], d_np[idx], cfg.steps,
+                           cfg.cap, cfg.t_term, mode=0, threads=os.cpu_count() or 1, lod=lod)
+            mse = float(np.mean((rgb[idx] - ref["rgb"]) ** 2))
+            rows.append({"refine_above_px": k, "lod": lod, "ms": round(ms, 3),
+                         "Mrays/s": round(n / (ms * 1e-3) / 1e6, 3),
+                         "Msamples/s": round(st["samples_generated"] / (ms * 1e-3) / 1e6, 3),
+                         "samples_per_ray": round(st["samples_generated"] / n, 3),
+                         "psnr_vs_fp64_same_method": round(10 * np.log10(1.0 / max(mse, 1e-30)), 2)})
+    base = rows[0]
+    for r in rows[1:]:
+        r["spr_reduction"] = round(base["samples_per_ray"] / r["samples_per_ray"], 3)
+        r["speedup"] = round(base["ms"] / r["ms"], 3)
+    R.close()
+    return {"workload": f"c4: {cfg.views} views x {cfg.px_w}x{cfg.px_h}, {tree.n_leaves} leaves, one 4x64 BF16 "
+                        f"network per node ({tree.n_nodes})", "settings": rows, "clocks": clk.summary()}
+
+
 def _extras(args) -> dict:
     """The batching (c4) and learned-proposal (c5) workloads, summarised for the default
     line: one GPU, 16 views of 1920x1080 each, the 4096-leaf scene."""
@@ -408,12 +481,15 @@ def _extras(args) -> dict:
     torch.cuda.empty_cache()
     c5 = run_c5(a, emit=False, grid=grid)
     torch.cuda.empty_cache()
+    ahs = run_ahs(a, grid=grid)
+    torch.cuda.empty_cache()
     keep4 = ("value", "unit", "ms_per_step", "mrays_per_s", "graph_ms", "stream_ms", "per_leaf_launch_ms",
              "speedup_vs_per_leaf", "stage_ms", "stage_ms_per_leaf", "autotuned", "leaf_counts", "vs_fp64", "clocks")
     keep5 = ("value", "unit", "ms_per_step", "plain", "proposal", "spr_reduction", "delta_psnr_vs_fp64_db",
              "training", "clocks")
     return {"c4": {"workload": c4["config"]["workload"], **{k: c4[k] for k in keep4 if k in c4}},
-            "c5": {"workload": c5["config"]["workload"], **{k: c5[k] for k in keep5 if k in c5}}}
+            "c5": {"workload": c5["config"]["workload"], **{k: c5[k] for k in keep5 if k in c5}},
+            "hierarchical_sampling": ahs}
 
 
 def _zipf_exponent(counts: np.ndarray) -> float:
@@ -744,6 +820,9 @@ def main():
                     help="empty-space skipping: density threshold of the guidance grid (c1/c2); default off")
     ap.add_argument("--ert-wave", type=int, default=0,
                     help="early ray termination in waves of this many crossings (0: one pass)")
+    ap.add_argument("--lod-px", type=float, default=0.0,
+                    help="adaptive hierarchical sampling: an inner node is refined only while wider than this "
+                         "many pixels at the ray's entry distance (0: leaves only)")
     ap.add_argument("--jitter", type=int, default=0,
                     help="sample placement: 0 = stratum midpoints, else the stratified jitter's seed (c1/c2)")
     args = ap.parse_args()
@@ -755,6 +834,8 @@ def main():
         run_c4(args)
     elif args.config == "c5":
         run_c5(args)
+    elif args.config == "ahs":
+        print(json.dumps(run_ahs(args)))
     else:
         run_ours(args)
 

@@ -72,8 +72,8 @@ def test_c1_crossings_grouping_and_fp32_pixels_against_oracle(R, seed):
         rgb, depth, opac, dbg, st = R.render_debug(_dev(o), _dev(d), cfg.steps, cfg.cap, lod=lod)
         nx, net = _check_crossings(cfg, tree, dbg, o, d, lod)
         counts, offsets, _ = O.group(nx, net, cfg.cap // cfg.steps, cfg.steps, n_nets)
-        np.testing.assert_array_equal(dbg["counts"], counts)
-        np.testing.assert_array_equal(dbg["offsets"], offsets)
+        np.testing.assert_array_equal(dbg["counts"] * cfg.steps, counts)     # the oracle counts samples
+        np.testing.assert_array_equal(dbg["offsets"] * cfg.steps, offsets)
         if lod >= 0.3:
             assert counts[tree.n_leaves:].sum() > 0   # inner networks take crossings
         ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1, lod=lod)
@@ -134,8 +134,8 @@ def test_c4_tree_all_8191_networks(R):
     maxc = cfg.cap // cfg.steps
     nx, net, tin, tout = O.traverse(tree, o, d, maxc, mode=1, lod=lod)
     counts, offsets, _ = O.group(nx, net, maxc, cfg.steps, tree.n_nodes)
-    np.testing.assert_array_equal(dbg["counts"], counts)
-    np.testing.assert_array_equal(dbg["offsets"], offsets)
+    np.testing.assert_array_equal(dbg["counts"] * cfg.steps, counts)         # the oracle counts samples
+    np.testing.assert_array_equal(dbg["offsets"] * cfg.steps, offsets)
     assert (counts[tree.n_leaves:] > 0).sum() > 500
     idx = S.ray_subset(len(o), 2048, 6)
     sub = {k: dbg[k][idx] for k in ("n_x", "leaf", "t_in", "t_out")}
