@@ -531,7 +531,7 @@ def run_c4(args, emit: bool = True, grid=None) -> dict:
     out = (torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"), torch.empty(n, device="cuda"))
     # autotune on the first view, then fix the configuration
     nv = n // views
-    g_best, s_best, ms_best = amnerf.amnerf_autotune(R.ctx, o[:nv], d[:nv], out[0][:nv], out[1][:nv], out[2][:nv],
+    g_best, s_best, ws_best, ms_best = amnerf.amnerf_autotune(R.ctx, o[:nv], d[:nv], out[0][:nv], out[1][:nv], out[2][:nv],
                                                      steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term, reps=2)
     _, _, _, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out)
     # realised per-leaf crossing counts
@@ -566,14 +566,14 @@ def run_c4(args, emit: bool = True, grid=None) -> dict:
         *_, s2 = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out)
         stage += np.array(s2["ms"]) / 2
     # per-leaf-launch baseline (one network launch per leaf)
-    amnerf.amnerf_set_tuning(R.ctx, g_best, amnerf.SCHED_PER_LEAF)
+    amnerf.amnerf_set_tuning(R.ctx, g_best, amnerf.SCHED_PER_LEAF, ws_best)
     stage_pl = np.zeros(4)
     for _ in range(2):
         *_, s3 = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out)
         stage_pl += np.array(s3["ms"]) / 2
     amnerf.amnerf_set_timing(R.ctx, False)
     ms_pl = timed(lambda: R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out), max(1, args.steps // 2))
-    amnerf.amnerf_set_tuning(R.ctx, g_best, s_best)
+    amnerf.amnerf_set_tuning(R.ctx, g_best, s_best, ws_best)
     R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out)
     rgb = out[0].cpu().numpy().astype(np.float64)
     import oracle as O
@@ -596,7 +596,8 @@ def run_c4(args, emit: bool = True, grid=None) -> dict:
         "graph_ms": round(ms_graph, 3), "stream_ms": round(ms_plain, 3), "per_leaf_launch_ms": round(ms_pl, 3),
         "speedup_vs_per_leaf": round(ms_pl / ms_graph, 3),
         "stage_ms": [round(x, 3) for x in stage], "stage_ms_per_leaf": [round(x, 3) for x in stage_pl],
-        "autotuned": {"groups": g_best, "schedule": names.get(s_best, s_best), "ms_one_view": round(ms_best, 3)},
+        "autotuned": {"groups": g_best, "schedule": names.get(s_best, s_best), "width_split": ws_best,
+                      "ms_one_view": round(ms_best, 3)},
         "leaf_counts": {"leaves": nl, "nonempty": int((cnt > 0).sum()), "max": int(cnt.max()),
                         "median_nonempty": float(np.median(cnt[cnt > 0])), "zipf_exponent_fit": round(_zipf_exponent(cnt), 3)},
         "vs_fp64": {"psnr_db": round(10 * np.log10(1.0 / max(mse, 1e-30)), 2),

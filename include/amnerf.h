@@ -163,11 +163,18 @@ typedef enum {
                                       render then synchronises once to read tile offsets) */
 } amnerf_schedule;
 
-/* Launch configuration of the network step.  groups = tensor-core warpgroups per CTA
- * (tiles in flight per SM), 0 = the largest that fits; ignored on the FP32 path. */
+/* Launch configuration of the network step (tensor-core paths; the FP32 path ignores it).
+ * groups:      warpgroup sets per CTA = tiles in flight per SM, 0 = the largest that fits.
+ * schedule:    how the tiles are spread over the groups.
+ * width_split: hidden-width tiling of the BF16 kernel: 1 = one thread per sample row
+ *              holds all `width` accumulator columns; 2 = two threads per row, each
+ *              with width / 2 columns and half of the layer-0 encoding (twice the warps
+ *              per tile); 0 = the library's default.  E4M3 always uses 1.  Every setting
+ *              gives the same pixels. */
 typedef struct {
     int groups;
     amnerf_schedule schedule;
+    int width_split;
 } amnerf_tuning;
 
 /* Filled by a render when a non-NULL pointer is passed (this synchronises). */
@@ -413,9 +420,10 @@ AMNERF_API amnerf_status amnerf_get_tuning(amnerf_ctx *ctx, amnerf_tuning *tunin
 
 /* Autotuner: renders the caller's batch (DEVICE buffers as in amnerf_render) once
  * per candidate configuration to warm up, then `reps` times under CUDA events, for
- * every group count 1..max and the contiguous, interleaved and dynamic schedules
- * (FP32 path: one candidate), keeps the fastest in the context and returns it with
- * its time per render.  Synchronous; the outputs hold the last render.
+ * every group count 1..max, the contiguous, interleaved and dynamic schedules and (BF16)
+ * width splits 1 and 2 (FP32 path: one candidate), keeps the fastest in the context
+ * and returns it with its time per render.  Synchronous; the outputs hold the last
+ * render.
  * Errors: as amnerf_render, E_INVAL (reps < 1). */
 AMNERF_API amnerf_status amnerf_autotune(amnerf_ctx *ctx, const float *rays_o, const float *rays_d, int64_t n_rays,
                                          const amnerf_render_params *params, float *rgb, float *depth,

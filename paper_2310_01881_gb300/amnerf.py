@@ -58,7 +58,7 @@ SCHED_CONTIGUOUS, SCHED_INTERLEAVED, SCHED_DYNAMIC, SCHED_PER_LEAF = range(4)
 
 
 class amnerf_tuning(ctypes.Structure):
-    _fields_ = [("groups", ctypes.c_int), ("schedule", ctypes.c_int)]
+    _fields_ = [("groups", ctypes.c_int), ("schedule", ctypes.c_int), ("width_split", ctypes.c_int)]
 
 
 class amnerf_stats(ctypes.Structure):
@@ -291,29 +291,30 @@ def amnerf_group_by_leaf_static(n_x, leaf, n_rays: int, maxc: int, n_leaves: int
     _check(None, st, "amnerf_group_by_leaf_static")
 
 
-def amnerf_set_tuning(ctx, groups: int = 0, schedule: int = SCHED_CONTIGUOUS) -> None:
-    t = amnerf_tuning(groups, schedule)
+def amnerf_set_tuning(ctx, groups: int = 0, schedule: int = SCHED_CONTIGUOUS, width_split: int = 0) -> None:
+    t = amnerf_tuning(groups, schedule, width_split)
     _check(ctx, load().amnerf_set_tuning(ctx, ctypes.byref(t)), "amnerf_set_tuning")
 
 
-def amnerf_get_tuning(ctx) -> tuple[int, int, int]:
-    """(groups, schedule, largest group count the loaded network shape allows)."""
+def amnerf_get_tuning(ctx) -> tuple[int, int, int, int]:
+    """(groups, schedule, largest group count the loaded network shape allows, width_split)."""
     t = amnerf_tuning()
     mg = ctypes.c_int()
     _check(ctx, load().amnerf_get_tuning(ctx, ctypes.byref(t), ctypes.byref(mg)), "amnerf_get_tuning")
-    return t.groups, t.schedule, mg.value
+    return t.groups, t.schedule, mg.value, t.width_split
 
 
 def amnerf_autotune(ctx, o, d, rgb, depth, opacity, steps: int = 8, cap: int = 64, t_term: float = 1e-4,
-                    bg=(0.0, 0.0, 0.0), reps: int = 3, lod: float = 0.0) -> tuple[int, int, float]:
-    """Time every launch configuration on this batch; returns (groups, schedule, ms)."""
+                    bg=(0.0, 0.0, 0.0), reps: int = 3, lod: float = 0.0) -> tuple[int, int, int, float]:
+    """Time every launch configuration on this batch; returns (groups, schedule,
+    width_split, ms) of the fastest, which the context keeps."""
     p = _params(steps, cap, t_term, bg, lod=lod)
     best = amnerf_tuning()
     ms = ctypes.c_float()
     st = load().amnerf_autotune(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
                                 _ptr(opacity), reps, ctypes.byref(best), ctypes.byref(ms))
     _check(ctx, st, "amnerf_autotune")
-    return best.groups, best.schedule, ms.value
+    return best.groups, best.schedule, best.width_split, ms.value
 
 
 def amnerf_proposal_set(ctx, params: np.ndarray, adam_m=None, adam_v=None, step: int = 0) -> None:

@@ -117,6 +117,7 @@ struct MlpArgs {
     uint32_t t_begin, t_end;// tile range of this launch (t_end == 0xffffffff: up to stats[1])
     int schedule;           // kSched*
     int groups;             // tcgen05 kernel: warpgroups per CTA (1..4)
+    int width_split;        // tcgen05 BF16: threads per sample row, each with width / split columns (1, 2)
     int n_leaves;
     const float2* xing;
     const float* ro;

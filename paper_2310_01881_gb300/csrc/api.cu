@@ -15,6 +15,7 @@
 using namespace amnerf;
 
 constexpr int kStatSlots = 10;  // device statistics words (see amnerf_ctx::d_stats)
+constexpr int kDefaultWidthSplit = 1;  // BF16 hidden-width tiling when the caller sets none
 
 struct amnerf_ctx {
     int device = 0;
@@ -63,7 +64,7 @@ struct amnerf_ctx {
     cudaEvent_t ev_done[4] = {nullptr, nullptr, nullptr, nullptr};
     // network kernel schedule (autotuned or set by the caller)
     int max_groups = 1;
-    amnerf_tuning tuning{0, AMNERF_SCHED_CONTIGUOUS};
+    amnerf_tuning tuning{0, AMNERF_SCHED_CONTIGUOUS, 0};
     std::vector<uint32_t> h_tile_off;  // per-leaf launches: host copy of tile offsets
     // proposal sampler
     bool prop_loaded = false;
@@ -571,6 +572,9 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         a.t_end = 0xffffffffu;
         const bool tc = ctx->desc.prec != AMNERF_FP32;
         a.groups = ctx->tuning.groups > 0 ? std::min(ctx->tuning.groups, ctx->max_groups) : ctx->max_groups;
+        a.width_split = ctx->desc.prec == AMNERF_BF16 ? (ctx->tuning.width_split > 0 ? ctx->tuning.width_split
+                                                                                       : kDefaultWidthSplit)
+                                                      : 1;
         int sched = ctx->tuning.schedule;
         if (!tc && sched != AMNERF_SCHED_PER_LEAF) sched = AMNERF_SCHED_CONTIGUOUS;
         a.schedule = sched == AMNERF_SCHED_PER_LEAF ? kSchedContiguous : sched;
@@ -942,7 +946,8 @@ amnerf_status amnerf_proposal_predict(amnerf_ctx* ctx, const float* ro, const fl
 
 amnerf_status amnerf_set_tuning(amnerf_ctx* ctx, const amnerf_tuning* t) {
     if (!ctx || !t) return AMNERF_E_INVAL;
-    if (t->groups < 0 || t->groups > 4 || t->schedule < AMNERF_SCHED_CONTIGUOUS || t->schedule > AMNERF_SCHED_PER_LEAF)
+    if (t->groups < 0 || t->groups > 4 || t->schedule < AMNERF_SCHED_CONTIGUOUS || t->schedule > AMNERF_SCHED_PER_LEAF ||
+        t->width_split < 0 || t->width_split > 2)
         return fail(ctx, AMNERF_E_INVAL, "tuning out of range");
     ctx->tuning = *t;
     return AMNERF_OK;
@@ -964,11 +969,13 @@ amnerf_status amnerf_autotune(amnerf_ctx* ctx, const float* ro, const float* rd,
     const bool tc = ctx->desc.prec != AMNERF_FP32;
     std::vector<amnerf_tuning> cand;
     if (tc) {
-        for (int g = 1; g <= ctx->max_groups; ++g)
-            for (int sc = AMNERF_SCHED_CONTIGUOUS; sc <= AMNERF_SCHED_DYNAMIC; ++sc)
-                cand.push_back(amnerf_tuning{g, (amnerf_schedule)sc});
+        const int max_split = ctx->desc.prec == AMNERF_BF16 ? 2 : 1;
+        for (int ws = 1; ws <= max_split; ++ws)
+            for (int g = 1; g <= ctx->max_groups; ++g)
+                for (int sc = AMNERF_SCHED_CONTIGUOUS; sc <= AMNERF_SCHED_DYNAMIC; ++sc)
+                    cand.push_back(amnerf_tuning{g, (amnerf_schedule)sc, ws});
     } else {
-        cand.push_back(amnerf_tuning{0, AMNERF_SCHED_CONTIGUOUS});
+        cand.push_back(amnerf_tuning{0, AMNERF_SCHED_CONTIGUOUS, 1});
     }
     const amnerf_tuning saved = ctx->tuning;
     const bool saved_timing = ctx->timing;

@@ -340,10 +340,10 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 encode_freq<kLX, 0>(x, f);
                 encode_freq<kLD, NX>(d, f);
                 if constexpr (!F8) {
-                    static_assert(K0P % 32 == 0, "layer-0 input is stored in 32-feature chunks");
-                    store_chunk<0>(a_row, f);
-                    store_chunk<1>(a_row, f);
-                    store_chunk<2>(a_row, f);
+                    static_assert(K0P == 96, "layer-0 input is stored in three 32-feature chunks");
+                    store_chunk_perm<0>(a_row, f);
+                    store_chunk_perm<1>(a_row, f);
+                    store_chunk_perm<2>(a_row, f);
                 } else {
                     static_assert(K0P == 96, "E4M3 layer-0 input is stored as 16 + 8 columns");
                     float inv;
@@ -631,6 +631,349 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
+// ---- BF16 network with two threads per sample row ------------------------------------
+// The same network, tiles, weights and TMEM layout as k_mlp_tc<W, false, ...>, with
+// 256 threads per warpgroup pair: warps 0-3 of a group handle the low half of every
+// row (TMEM lane quadrant = warp % 4), warps 4-7 the high half.  A row's encoding is
+// split by column half (kperm: each half from its own SFU anchors), and every epilogue
+// reads, converts and stores W/2 of the row's accumulator columns per thread, so a
+// tile's ALU work is spread over twice as many warps (more latency hidden per SM)
+// without more TMEM.  The head MMA reads relu(h) from the A columns like a hidden
+// layer; the next tile's encoding is computed while it runs and stored into A once it
+// has completed.
+constexpr int kTPR = 2;  // threads per sample row
+
+__device__ __forceinline__ void bar_sync(int id, int n) {
+    asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ bool group_wait_n(uint32_t bar, uint32_t phase, int bar_id, int n, volatile int* flag,
+                                             bool leader) {
+    if (leader) *flag = mbar_wait_bounded(bar, phase) ? 1 : 0;
+    bar_sync(bar_id, n);
+    return *flag != 0;
+}
+
+// N consecutive FP32 columns of this thread's TMEM lane (N = 16 or 32), one wait.
+template <int N>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[N]) {
+    uint32_t r[32];
+    if constexpr (N == 32) {
+        tmem_ld32_nowait(taddr, r);
+    } else {
+        static_assert(N == 16, "16 or 32 columns");
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+    }
+    tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// N packed words into this thread's TMEM lane (N = 8 or 16).
+template <int N>
+__device__ __forceinline__ void tmem_st_words(uint32_t taddr, const uint32_t* w) {
+    if constexpr (N == 16) tmem_st16(taddr, w);
+    else tmem_st8(taddr, w);
+}
+
+// The layer-0 input half `half` of a row (48 features in kperm order) packed into 24
+// words: half 0 = p_x, x octaves 0-4, p_d, d octaves 0-1; half 1 = x octaves 5-9,
+// d octaves 2-3, the bias input 1 and zero padding.  The anchors are those of
+// encode_freq (x at octaves 0 and 5, d at 0), so the features are bit-identical.
+__device__ __forceinline__ void encode_half(int half, const float x[3], const float d[3], uint32_t (&w)[24]) {
+    float f[48];
+    if (half == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            f[a] = x[a];
+            f[33 + a] = d[a];
+        }
+        encode_octaves<0, 5, 3>(x, f);
+        encode_octaves<0, 2, 36>(d, f);
+    } else {
+        encode_octaves<5, 10, 0>(x, f);
+        // d's octaves 2-3 from the anchor at octave 0, as the one-thread-per-row kernel
+        // computes them (both kernels give the same features)
+        float fd[24];
+        encode_octaves<0, 4, 0>(d, fd);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) f[30 + i] = fd[12 + i];
+        f[42] = 1.0f;
+#pragma unroll
+        for (int i = 43; i < 48; ++i) f[i] = 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < 24; ++i) w[i] = pack_bf16(f[2 * i], f[2 * i + 1]);
+}
+
+// MAXG: the most groups a launch of this instantiation uses (its register budget is
+// 65536 / (256 MAXG) per thread: 64 at four groups, 80 at three).
+template <int W, int HC, bool JIT, int MAXG>
+__global__ void __launch_bounds__(128 * kTPR * MAXG, 1) k_mlp_tc2(MlpArgs g, int n_groups, uint32_t tmem_cols) {
+    const int hidden = HC > 0 ? HC : g.hidden;
+    constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
+    constexpr int K0P = 96;
+    static_assert(K0 + 1 <= K0P && kLX == 10 && kLD == 4, "kperm is laid out for gamma_10(x) ++ gamma_4(d)");
+    constexpr int CPT = W / kTPR;  // accumulator columns per thread
+    constexpr int GT = 128 * kTPR; // threads per group
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const TcLayout lay(W, hidden, K0, false);
+    TcShared* sh = reinterpret_cast<TcShared*>(smem + lay.stride * n_groups);
+
+    const int grp = threadIdx.x / GT;
+    const int tig = threadIdx.x % GT;
+    const int wig = tig >> 5;            // warp within the group
+    const int q = wig & 3;               // TMEM lane quadrant (global warp index % 4)
+    const int half = wig >> 2;           // column half of the row
+    const int row = 32 * q + (tig & 31); // sample row = TMEM lane
+    const int warp = threadIdx.x >> 5;
+    const int bar_id = 1 + grp;
+    const bool leader = tig == 32 * (grp & 3);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n_groups; ++i) {
+            mbar_init(smem_u32(&sh->bar_w[i]), 1);
+            mbar_init(smem_u32(&sh->bar_m[i]), 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    if (grp < n_groups) {
+        uint8_t* wbuf = smem + lay.stride * grp;
+        const uint32_t w_addr = smem_u32(wbuf);
+        const uint32_t bar_w = smem_u32(&sh->bar_w[grp]);
+        const uint32_t bar_m = smem_u32(&sh->bar_m[grp]);
+        const uint32_t lane = (uint32_t)(32 * q) << 16;
+        const uint32_t d_col = tmem + kGroupCols * (uint32_t)grp;
+        const uint32_t a_col = d_col + kACol;
+        const uint32_t d_row = d_col + lane;
+        const uint32_t a_row = a_col + lane;
+        const float* bias = reinterpret_cast<const float*>(wbuf + lay.bias);
+        const uint32_t bias_s = smem_u32(bias);
+        const uint64_t desc_w0 = sdesc(w_addr + (uint32_t)lay.w0, (uint32_t)K0P * 16u);
+        const uint64_t desc_wh = sdesc(w_addr + (uint32_t)lay.wh, (uint32_t)lay.kh * 16u);
+        const uint64_t desc_wo = sdesc(w_addr + (uint32_t)lay.wo, (uint32_t)lay.khead * 16u);
+        const uint8_t* wall = reinterpret_cast<const uint8_t*>(g.weights);
+
+        const uint32_t t_end = g.t_end == 0xffffffffu ? (uint32_t)g.stats[1] : g.t_end;
+        const uint32_t workers = gridDim.x * (uint32_t)n_groups;
+        const uint32_t wid = blockIdx.x * (uint32_t)n_groups + (uint32_t)grp;
+        uint32_t t_stop = t_end, t_step = 1, t_first;
+        if (g.schedule == kSchedInterleaved) {
+            t_first = g.t_begin + wid;
+            t_step = workers;
+        } else if (g.schedule == kSchedDynamic) {
+            if (leader) sh->next_tile[grp] = atomicAdd(g.tile_counter, 1u) + g.t_begin;
+            bar_sync(bar_id, GT);
+            t_first = sh->next_tile[grp];
+        } else {
+            const uint32_t span = t_end > g.t_begin ? t_end - g.t_begin : 0u;
+            const uint32_t per = (span + workers - 1) / workers;
+            t_first = min(g.t_begin + wid * per, t_end);
+            t_stop = min(t_first + per, t_end);
+        }
+        volatile int* flag = &sh->flag[grp];
+        const int ci = row / g.steps;
+        const int j = row - ci * g.steps;
+        uint32_t ph_w = 0, ph_m = 0;
+        int cur = -1;
+        bool ok = true;
+        bool pending = false;   // head MMA issued, its completion not yet consumed
+        bool have_out = false;  // a head result in TMEM waits to be read
+        bool zpend = false;     // a head result in registers waits to be stored (half 0)
+        uint64_t slot_prev = ~0ull, slot_z = ~0ull;
+        uint32_t zr[4] = {0u, 0u, 0u, 0u};
+        auto store_head = [&]() {
+            if (slot_z != ~0ull) {
+                uint2 o;
+                o.x = pack_f16(fminf(softplus_f(__uint_as_float(zr[0])), 65504.0f), sigmoid_f(__uint_as_float(zr[1])));
+                o.y = pack_f16(sigmoid_f(__uint_as_float(zr[2])), sigmoid_f(__uint_as_float(zr[3])));
+                static_cast<uint2*>(g.slot_out)[slot_z] = o;
+            }
+            zpend = false;
+        };
+
+        int leaf = t_first < t_stop ? leaf_of_tile(g.tile_off, g.n_leaves, t_first) : 0;
+        uint32_t id = t_first < t_stop ? row_crossing(g, leaf, t_first, ci) : 0xffffffffu;
+        float2 xi = make_float2(0.f, 0.f);
+        float ro[3] = {0.f, 0.f, 0.f}, rd[3] = {0.f, 0.f, 0.f};
+        crossing_data(g, id, xi, ro, rd);
+
+        for (uint32_t t = t_first; t < t_stop && ok;) {
+            if (leaf != cur) {
+                if (pending) {  // the head MMA still reads the weights
+                    ok = group_wait_n(bar_m, ph_m, bar_id, GT, flag, leader);
+                    ph_m ^= 1u;
+                    pending = false;
+                    if (!ok) break;
+                }
+                bar_sync(bar_id, GT);
+                if (leader) {
+                    fence_proxy_async();
+                    bulk_load(w_addr, wall + (size_t)leaf * lay.stride, (uint32_t)lay.stride, bar_w);
+                }
+                ok = group_wait_n(bar_w, ph_w, bar_id, GT, flag, leader);
+                ph_w ^= 1u;
+                if (!ok) break;
+                cur = leaf;
+            }
+            // ---- this row's sample and its half of the layer-0 input
+            uint64_t slot = ~0ull;
+            float x[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f};
+            if (id != 0xffffffffu) {
+                const uint32_t ray = div_maxc(g, id);
+                const uint32_t k = id - ray * (uint32_t)g.maxc;
+                const float delta = __fmul_rn(__fsub_rn(xi.y, xi.x), __frcp_rn((float)g.steps));
+                const float u = JIT ? jit_fraction(g.jitter, jit_ray_key(g.jitter, ro, rd), (int)k, g.steps, j) : 0.5f;
+                const float tj = __fadd_rn(xi.x, __fmul_rn(__fadd_rn((float)j, u), delta));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    d[a] = rd[a];
+                    x[a] = __fadd_rn(ro[a], __fmul_rn(tj, rd[a]));
+                }
+                slot = (uint64_t)ray * (uint64_t)g.cap + (uint64_t)(k * (uint32_t)g.steps + (uint32_t)j);
+            }
+            {
+                uint32_t w[24];
+                encode_half(half, x, d, w);
+                if (pending) {  // the previous tile's head MMA reads the A columns
+                    ok = group_wait_n(bar_m, ph_m, bar_id, GT, flag, leader);
+                    ph_m ^= 1u;
+                    pending = false;
+                    if (!ok) break;
+                    tc_fence_after();
+                }
+                tmem_st16(a_row + 24u * (uint32_t)half, w);
+                tmem_st8(a_row + 24u * (uint32_t)half + 16u, w + 16);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            bar_sync(bar_id, GT);
+
+            int leaf_n = leaf;
+            uint32_t id_n = 0xffffffffu;
+            uint32_t t_next = t_stop;
+            int kin = K0P;
+#pragma unroll
+            for (int l = 0; l < hidden; ++l) {
+                if (!ok) break;
+                if (leader) {
+                    tc_fence_after();
+                    const uint64_t b_desc = l == 0 ? desc_w0 : desc_wh + (uint64_t)(((size_t)(l - 1) * W * lay.kh * 2) >> 4);
+                    const uint32_t idd = idesc_bf16(W);
+                    for (int kk = 0; kk < kin / 16; ++kk)
+                        mma_bf16_ts(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, (kk > 0 || l > 0) ? 1u : 0u);
+                    mma_commit(bar_m);
+                }
+                auto next_lookup = [&](uint32_t tn) {
+                    t_next = tn;
+                    if (t_next < t_stop) {
+                        if (t_next - t <= 8u) {
+                            while (__ldg(g.tile_off + leaf_n + 1) <= t_next) ++leaf_n;
+                        } else {
+                            leaf_n = leaf_of_tile(g.tile_off, g.n_leaves, t_next);
+                        }
+                        id_n = row_crossing(g, leaf_n, t_next, ci);
+                    }
+                };
+                const bool dyn = g.schedule == kSchedDynamic;
+                if (l == 0 && dyn && leader) sh->next_tile[grp] = atomicAdd(g.tile_counter, 1u) + g.t_begin;
+                const int l_xd = hidden > 2 ? 2 : hidden - 1;
+                const int l_sh = hidden > 3 ? 3 : hidden - 1;
+                if (!dyn && l == 0) next_lookup(t + t_step);
+                if (!dyn && l > 0 && l == l_xd) crossing_data(g, id_n, xi, ro, rd);
+                if (zpend && l == l_sh) store_head();
+                ok = group_wait_n(bar_m, ph_m, bar_id, GT, flag, leader);
+                ph_m ^= 1u;
+                if (!ok) break;
+                tc_fence_after();
+                if (dyn && l == 0) next_lookup(sh->next_tile[grp]);
+                if ((dyn || l_xd == 0) && l == l_xd) crossing_data(g, id_n, xi, ro, rd);
+                const bool last = l + 1 == hidden;
+                if (l == 0 && have_out && half == 0) {  // the previous tile's head result
+                    tmem_ld4_nowait(d_row + kHeadCol, zr);
+                    slot_z = slot_prev;
+                    zpend = true;
+                }
+                if (l == 0) have_out = false;
+                // relu of this thread's accumulator half, as BF16, into the next input's
+                // A columns (also for the head, whose MMA reads the A columns)
+                {
+                    float v[CPT];
+                    tmem_ld_cols<CPT>(d_row + (uint32_t)(CPT * half), v);
+                    uint32_t pk[CPT / 2];
+#pragma unroll
+                    for (int c = 0; c < CPT / 2; ++c) pk[c] = pack_relu_bf16(v[2 * c], v[2 * c + 1]);
+                    tmem_st_words<CPT / 2>(a_row + (uint32_t)(CPT / 2 * half), pk);
+                }
+                if (!last) {
+                    // layer l + 1 accumulates onto its bias (this thread's columns)
+                    tmem_st_wait();
+                    tmem_st_bias<CPT>(d_row + (uint32_t)(CPT * half),
+                                      bias_s + 4u * (uint32_t)((l + 1) * W + CPT * half));
+                    tmem_st_wait();
+                    tc_fence_before();
+                    bar_sync(bar_id, GT);
+                    kin = lay.kh;
+                } else {
+                    if (half == 0) tmem_st4(d_row + kHeadCol, bias + (size_t)hidden * W);
+                    tmem_st_wait();
+                    tc_fence_before();
+                    bar_sync(bar_id, GT);
+                    if (leader) {
+                        tc_fence_after();
+                        const uint32_t idd = idesc_bf16(16);
+                        for (int kk = 0; kk < lay.khead / 16; ++kk)
+                            mma_bf16_ts(d_col + kHeadCol, a_col + 8u * kk, desc_wo + 16u * kk, idd, 1u);
+                        mma_commit(bar_m);
+                    }
+                    pending = true;
+                    have_out = true;
+                    slot_prev = slot;
+                }
+            }
+            if (zpend) store_head();  // one hidden layer: stored after the head MMA issue
+            leaf = leaf_n;
+            id = id_n;
+            t = t_next;
+        }
+        if (ok && pending) {
+            ok = group_wait_n(bar_m, ph_m, bar_id, GT, flag, leader);
+            ph_m ^= 1u;
+            pending = false;
+        }
+        if (ok && have_out && half == 0) {
+            tc_fence_after();
+            tmem_ld4_nowait(d_row + kHeadCol, zr);
+            tmem_ld_wait();
+            slot_z = slot_prev;
+            store_head();
+        }
+        if (!ok && leader) atomicCAS(g.err, 0, kDevErrTimeout);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
 // Failure-detection self-test: waits, with the network kernel's bounded-wait helper,
 // on an mbarrier phase that nothing completes; the wait runs out after `limit`
 // cycles and the kernel records a timeout in the status word and returns.
@@ -674,6 +1017,51 @@ cudaError_t prepare_w(int hidden, int* max_groups) {
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// BF16 with two threads per row (k_mlp_tc2): the same shared memory per group.
+template <int W>
+cudaError_t prepare_w2() {
+    int dev = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const void* fns[8] = {(const void*)k_mlp_tc2<W, 0, false, 3>, (const void*)k_mlp_tc2<W, kHiddenFor<W>, false, 3>,
+                          (const void*)k_mlp_tc2<W, 0, true, 3>, (const void*)k_mlp_tc2<W, kHiddenFor<W>, true, 3>,
+                          (const void*)k_mlp_tc2<W, 0, false, 4>, (const void*)k_mlp_tc2<W, kHiddenFor<W>, false, 4>,
+                          (const void*)k_mlp_tc2<W, 0, true, 4>, (const void*)k_mlp_tc2<W, kHiddenFor<W>, true, 4>};
+    for (const void* f : fns) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <int W>
+cudaError_t launch_w2(cudaStream_t s, const MlpArgs& a, int grid) {
+    constexpr int K0 = (3 + 6 * kLX) + (3 + 6 * kLD);
+    const TcLayout lay(W, a.hidden, K0, false);
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int groups = a.groups;
+    if (groups < 1 || groups > max_groups_for<W, false>(a.hidden, max_smem)) return cudaErrorInvalidConfiguration;
+    const uint32_t cols = 512;
+    size_t smem = lay.stride * groups + sizeof(TcShared) + 64;
+    if (smem < (size_t)max_smem / 2 + 1024) smem = (size_t)max_smem / 2 + 1024;
+    const bool hc = a.hidden == kHiddenFor<W>;
+    const int threads = 128 * kTPR * groups;
+#define AMNERF_TC2(HC_, J_, G_) k_mlp_tc2<W, HC_, J_, G_><<<grid, threads, smem, s>>>(a, groups, cols)
+    if (groups <= 3) {
+        if (a.jitter) { if (hc) AMNERF_TC2(kHiddenFor<W>, true, 3); else AMNERF_TC2(0, true, 3); }
+        else { if (hc) AMNERF_TC2(kHiddenFor<W>, false, 3); else AMNERF_TC2(0, false, 3); }
+    } else {
+        if (a.jitter) { if (hc) AMNERF_TC2(kHiddenFor<W>, true, 4); else AMNERF_TC2(0, true, 4); }
+        else { if (hc) AMNERF_TC2(kHiddenFor<W>, false, 4); else AMNERF_TC2(0, false, 4); }
+    }
+#undef AMNERF_TC2
+    return cudaGetLastError();
 }
 
 template <int W, bool F8>
@@ -739,14 +1127,18 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
                 const float s = m > 0.0f ? m / 448.0f : 1.0f;
                 sw[(size_t)l * width + n] = stat ? a_in * s / a_out : s;
                 for (int k = 0; k < kin; ++k) base[cm_offset8(n, k, K)] = f2e4m3(row[k] / s);
+            } else if (l == 0) {
+                // layer 0 in the kernels' column order (kperm), its bias at the bias input
+                for (int k = 0; k < K; ++k) {
+                    const int c = kperm(k);
+                    const float v = c >= 0 ? row[c] : (c == -1 ? w[(size_t)width * kin + n] : 0.0f);
+                    const uint16_t b = f2bf(v);
+                    std::memcpy(base + cm_offset(n, k, K), &b, 2);
+                }
             } else {
                 for (int k = 0; k < kin; ++k) {
                     const uint16_t b = f2bf(row[k]);
                     std::memcpy(base + cm_offset(n, k, K), &b, 2);
-                }
-                if (l == 0) {  // layer 0's bias folded in at input column kin (inside the padding)
-                    const uint16_t bb = f2bf(w[(size_t)width * kin + n]);
-                    std::memcpy(base + cm_offset(n, kin, K), &bb, 2);
                 }
             }
         }
@@ -777,14 +1169,27 @@ cudaError_t launch_wait_selftest(cudaStream_t s, unsigned long long limit, int* 
 cudaError_t prepare_mlp_tc(int width, int hidden, int k0, int prec, int* max_groups) {
     if ((prec != 1 && prec != 2) || k0 != (3 + 6 * kLX) + (3 + 6 * kLD)) return cudaErrorNotSupported;
     const bool f8 = prec == 2;
-    if (width == 64) return f8 ? prepare_w<64, true>(hidden, max_groups) : prepare_w<64, false>(hidden, max_groups);
-    if (width == 32) return f8 ? prepare_w<32, true>(hidden, max_groups) : prepare_w<32, false>(hidden, max_groups);
+    if (width == 64) {
+        if (f8) return prepare_w<64, true>(hidden, max_groups);
+        const cudaError_t e = prepare_w<64, false>(hidden, max_groups);
+        return e != cudaSuccess ? e : prepare_w2<64>();
+    }
+    if (width == 32) {
+        if (f8) return prepare_w<32, true>(hidden, max_groups);
+        const cudaError_t e = prepare_w<32, false>(hidden, max_groups);
+        return e != cudaSuccess ? e : prepare_w2<32>();
+    }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_mlp_tc(cudaStream_t s, const MlpArgs& a, int grid, int prec) {
     const bool f8 = prec == 2;
     if (prec != 1 && prec != 2) return cudaErrorNotSupported;
+    if (!f8 && a.width_split == 2) {  // BF16, two threads per sample row
+        if (a.width == 64) return launch_w2<64>(s, a, grid);
+        if (a.width == 32) return launch_w2<32>(s, a, grid);
+        return cudaErrorInvalidValue;
+    }
     if (a.width == 64) return f8 ? launch_w<64, true>(s, a, grid) : launch_w<64, false>(s, a, grid);
     if (a.width == 32) return f8 ? launch_w<32, true>(s, a, grid) : launch_w<32, false>(s, a, grid);
     return cudaErrorInvalidValue;

@@ -347,6 +347,66 @@ __device__ __forceinline__ void encode_freq(const float p[3], float (&f)[N]) {
     }
 }
 
+// Octaves LO .. HI-1 of gamma(p) into f[F0 ..]: octave k's sin(pi 2^k p) at
+// F0 + 6 (k - LO) + a and its cos three later; the anchor is octave LO (SFU after an
+// exact argument reduction), the later octaves follow by double-angle steps.
+template <int LO, int HI, int F0, int N>
+__device__ __forceinline__ void encode_octaves(const float p[3], float (&f)[N]) {
+    float s[3], c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sincospi_anchor(p[a], LO, &s[a], &c[a]);
+#pragma unroll
+    for (int k = LO; k < HI; ++k) {
+        if (k > LO) {
+            const float2 s01 = make_float2(s[0], s[1]), c01 = make_float2(c[0], c[1]);
+            const float2 t01 = mul_f32x2(s01, make_float2(2.0f, 2.0f));
+            const float2 tn01 = mul_f32x2(s01, make_float2(-2.0f, -2.0f));
+            const float2 sn01 = mul_f32x2(t01, c01);
+            const float2 cn01 = fma2v(tn01, s01, make_float2(1.0f, 1.0f));
+            s[0] = sn01.x;
+            s[1] = sn01.y;
+            c[0] = cn01.x;
+            c[1] = cn01.y;
+            const float t = s[2] + s[2];
+            const float sn = t * c[2];
+            c[2] = fmaf(-t, s[2], 1.0f);
+            s[2] = sn;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            f[F0 + 6 * (k - LO) + a] = s[a];
+            f[F0 + 6 * (k - LO) + 3 + a] = c[a];
+        }
+    }
+}
+
+// Column order of the leaf networks' layer-0 input on the tensor cores (BF16): the
+// encoding gamma_10(x) ++ gamma_4(d) (canonical feature c, 90 features) is stored so
+// that the first 48 columns hold p_x and x's octaves 0-4, p_d and d's octaves 0-1, and
+// the last 48 hold x's octaves 5-9, d's octaves 2-3, the bias input (column 90, a
+// constant 1) and zero padding: each half of a row is encoded by its own thread from
+// its own anchors.  kperm(k) is the canonical feature of column k, -1 for the bias
+// input and -2 for padding.
+__host__ __device__ constexpr int kperm(int k) {
+    return k < 33 ? k : (k < 48 ? k + 30 : (k < 78 ? k - 15 : (k < 90 ? k : (k == 90 ? -1 : -2))));
+}
+
+// Columns [32 C, 32 C + 32) of the layer-0 input in kperm order, from the canonical
+// features f, packed two per word and written to this thread's TMEM lane.
+template <int C, int N>
+__device__ __forceinline__ void store_chunk_perm(uint32_t a_row, const float (&f)[N]) {
+    uint32_t w[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int k0 = 32 * C + 2 * i, k1 = k0 + 1;
+        const int c0 = kperm(k0), c1 = kperm(k1);
+        const float v0 = c0 >= 0 ? f[c0 >= 0 ? c0 : 0] : (c0 == -1 ? 1.0f : 0.0f);
+        const float v1 = c1 >= 0 ? f[c1 >= 0 ? c1 : 0] : (c1 == -1 ? 1.0f : 0.0f);
+        w[i] = pack_bf16(v0, v1);
+    }
+    tmem_st16(a_row + 16u * C, w);
+}
+
 // Features [32 c, 32 c + 32) of f packed two per word (even feature in the low half)
 // and written to this thread's TMEM lane at A column 16 c; feature N (one past the
 // last) is the constant 1 that multiplies the folded bias.

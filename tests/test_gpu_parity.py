@@ -732,16 +732,19 @@ def test_every_schedule_gives_identical_pixels(R, prec):
     _setup(R, cfg, 0, prec=prec)
     o, d = _rays(cfg, 0, 1, 256, 256)
     do, dd = _dev(o), _dev(d)
-    amnerf.amnerf_set_tuning(R.ctx, 0, amnerf.SCHED_CONTIGUOUS)
+    amnerf.amnerf_set_tuning(R.ctx, 0, amnerf.SCHED_CONTIGUOUS, 1)
     ref = [t.cpu().numpy() for t in R.render(do, dd, cfg.steps, cfg.cap)]
-    _, _, max_groups = amnerf.amnerf_get_tuning(R.ctx)
+    _, _, max_groups, _ = amnerf.amnerf_get_tuning(R.ctx)
     groups = range(1, max_groups + 1) if prec != "fp32" else [0]
-    for g in groups:
-        for sched in (amnerf.SCHED_CONTIGUOUS, amnerf.SCHED_INTERLEAVED, amnerf.SCHED_DYNAMIC, amnerf.SCHED_PER_LEAF):
-            amnerf.amnerf_set_tuning(R.ctx, g, sched)
-            got = [t.cpu().numpy() for t in R.render(do, dd, cfg.steps, cfg.cap)]
-            for a, b in zip(got, ref):
-                np.testing.assert_array_equal(a, b, err_msg=f"groups {g} schedule {sched}")
+    splits = (1, 2) if prec == "bf16" else (1,)
+    for ws in splits:     # hidden-width tiling: one or two threads per sample row
+        for g in groups:
+            for sched in (amnerf.SCHED_CONTIGUOUS, amnerf.SCHED_INTERLEAVED, amnerf.SCHED_DYNAMIC,
+                          amnerf.SCHED_PER_LEAF):
+                amnerf.amnerf_set_tuning(R.ctx, g, sched, ws)
+                got = [t.cpu().numpy() for t in R.render(do, dd, cfg.steps, cfg.cap)]
+                for a, b in zip(got, ref):
+                    np.testing.assert_array_equal(a, b, err_msg=f"groups {g} schedule {sched} width split {ws}")
     amnerf.amnerf_set_tuning(R.ctx, 0, amnerf.SCHED_CONTIGUOUS)
 
 
@@ -753,10 +756,10 @@ def test_autotune_picks_a_valid_configuration(R):
     do, dd = _dev(o), _dev(d)
     ref = [t.cpu().numpy() for t in R.render(do, dd, cfg.steps, cfg.cap)]
     out = (torch.empty((len(o), 3), device="cuda"), torch.empty(len(o), device="cuda"), torch.empty(len(o), device="cuda"))
-    g, sched, ms = amnerf.amnerf_autotune(R.ctx, do, dd, *out, steps=cfg.steps, cap=cfg.cap, reps=2)
-    _, _, max_groups = amnerf.amnerf_get_tuning(R.ctx)
-    assert 1 <= g <= max_groups and sched in (0, 1, 2) and ms > 0
-    assert amnerf.amnerf_get_tuning(R.ctx)[:2] == (g, sched)
+    g, sched, ws, ms = amnerf.amnerf_autotune(R.ctx, do, dd, *out, steps=cfg.steps, cap=cfg.cap, reps=2)
+    g2, s2, max_groups, ws2 = amnerf.amnerf_get_tuning(R.ctx)
+    assert 1 <= g <= max_groups and sched in (0, 1, 2) and ws in (1, 2) and ms > 0
+    assert (g2, s2, ws2) == (g, sched, ws)
     got = [t.cpu().numpy() for t in R.render(do, dd, cfg.steps, cfg.cap)]
     for a, b in zip(got, ref):
         np.testing.assert_array_equal(a, b)
