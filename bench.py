@@ -484,7 +484,8 @@ def _extras(args) -> dict:
     ahs = run_ahs(a, grid=grid)
     torch.cuda.empty_cache()
     keep4 = ("value", "unit", "ms_per_step", "mrays_per_s", "graph_ms", "stream_ms", "per_leaf_launch_ms",
-             "speedup_vs_per_leaf", "stage_ms", "stage_ms_per_leaf", "autotuned", "leaf_counts", "vs_fp64", "clocks")
+             "speedup_vs_per_leaf", "stage_ms", "stage_ms_per_leaf", "autotuned", "leaf_counts", "vs_fp64",
+             "zipf_network_microbench", "clocks")
     keep5 = ("value", "unit", "ms_per_step", "plain", "proposal", "spr_reduction", "delta_psnr_vs_fp64_db",
              "training", "clocks")
     return {"c4": {"workload": c4["config"]["workload"], **{k: c4[k] for k in keep4 if k in c4}},
@@ -573,6 +574,33 @@ def run_c4(args, emit: bool = True, grid=None) -> dict:
         stage_pl += np.array(s3["ms"]) / 2
     amnerf.amnerf_set_timing(R.ctx, False)
     ms_pl = timed(lambda: R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out), max(1, args.steps // 2))
+    # network microbench: crossing lists whose per-leaf counts are drawn from Zipf s = 1.1
+    # over the 4096 leaves (seeded rank permutation), grouped launch vs per-leaf launches
+    zn = min(n, 2_000_000)
+    maxc = cfg.cap // cfg.steps
+    zx, zl, za, zb = S.zipf_crossings(zn, maxc, nl, 1.1, 0)
+    zc = np.bincount(zl.reshape(-1).astype(np.int64), minlength=nl)
+    zargs = (o[:zn], d[:zn], torch.from_numpy(zx).cuda(), torch.from_numpy(zl.view(np.int16).reshape(-1)).cuda(),
+             torch.from_numpy(za.reshape(-1)).cuda(), torch.from_numpy(zb.reshape(-1)).cuda())
+    del zx, zl, za, zb
+    zout = (out[0][:zn], out[1][:zn], out[2][:zn])
+    zipf = {"rays": zn, "crossings": zn * maxc, "samples": zn * maxc * cfg.steps, "zipf_s": 1.1,
+            "zipf_exponent_fit": round(_zipf_exponent(zc), 3), "max_leaf_crossings": int(zc.max()),
+            "min_leaf_crossings": int(zc.min())}
+    amnerf.amnerf_set_timing(R.ctx, True)
+    for name_, sched_ in (("grouped", s_best), ("per_leaf", amnerf.SCHED_PER_LEAF)):
+        amnerf.amnerf_set_tuning(R.ctx, g_best, sched_, ws_best)
+        amnerf.amnerf_render_crossings(R.ctx, *zargs, *zout, steps=cfg.steps, cap=cfg.cap, t_term=cfg.t_term)
+        net = []
+        for _ in range(3):
+            zst = amnerf.amnerf_render_crossings(R.ctx, *zargs, *zout, steps=cfg.steps, cap=cfg.cap,
+                                                 t_term=cfg.t_term, stats=True)
+            net.append(zst["ms"][2])
+        nm = float(np.median(net))
+        zipf[name_] = {"network_ms": round(nm, 3), "network_Msamples/s": round(zipf["samples"] / (nm * 1e-3) / 1e6, 1)}
+    amnerf.amnerf_set_timing(R.ctx, False)
+    zipf["speedup_vs_per_leaf"] = round(zipf["per_leaf"]["network_ms"] / zipf["grouped"]["network_ms"], 3)
+    del zargs
     amnerf.amnerf_set_tuning(R.ctx, g_best, s_best, ws_best)
     R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out)
     rgb = out[0].cpu().numpy().astype(np.float64)
@@ -602,6 +630,7 @@ def run_c4(args, emit: bool = True, grid=None) -> dict:
                         "median_nonempty": float(np.median(cnt[cnt > 0])), "zipf_exponent_fit": round(_zipf_exponent(cnt), 3)},
         "vs_fp64": {"psnr_db": round(10 * np.log10(1.0 / max(mse, 1e-30)), 2),
                     "max_abs_rgb": float(np.abs(rgb[idx] - ref["rgb"]).max()), "rays": int(len(idx))},
+        "zipf_network_microbench": zipf,
         "clocks": clk.summary(),
     }
     if emit:

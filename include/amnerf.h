@@ -314,6 +314,26 @@ AMNERF_API amnerf_status amnerf_render_debug(amnerf_ctx *ctx, const float *rays_
                                   const amnerf_render_params *params, float *rgb, float *depth,
                                   float *opacity, const amnerf_debug *dbg, amnerf_stats *stats);
 
+/* The render from the grouping on (grouping, network, compositing; Sec. 3.5 Fig.
+ * "parallel", Sec. 3.1) over crossings given by the caller instead of the traversal:
+ * for ray r, n_x[r] <= floor(max_samples / steps_per_leaf) = maxc crossings k, each
+ * with its network leaf[r maxc + k] (a leaf id, or with per-node networks a network
+ * id) and its interval t_in / t_out at r maxc + k, sampled as the traversal's
+ * crossings are.  DEVICE buffers in the layout of amnerf_debug (n_x uint8 [n_rays],
+ * leaf uint16, t_in, t_out float [n_rays * maxc]); rays, outputs and stats as in
+ * amnerf_render.  Crossings the traversal would produce render exactly as
+ * amnerf_render does.  Used to drive the grouped network with arbitrary per-network
+ * counts (e.g. Zipf-distributed), and by the tests.  params must not ask for the
+ * proposal sampler, empty-space skipping or lod.  A network id >= the networks loaded
+ * or a count above maxc is recorded in the sticky status word (amnerf_sync, or a
+ * stats render, returns E_INVAL) and replaced by network 0 / maxc.
+ * Errors: as amnerf_render. */
+AMNERF_API amnerf_status amnerf_render_crossings(amnerf_ctx *ctx, const float *rays_o, const float *rays_d,
+                                                 int64_t n_rays, const amnerf_render_params *params,
+                                                 const uint8_t *n_x, const uint16_t *leaf, const float *t_in,
+                                                 const float *t_out, float *rgb, float *depth, float *opacity,
+                                                 amnerf_stats *stats);
+
 /* amnerf_render with HOST inputs and outputs (same layouts): copies the rays to
  * library-owned device buffers, renders, copies the pixels back and synchronises.
  * Page-locked host buffers make the copies asynchronous DMA.  Without `stats`, a
@@ -325,7 +345,8 @@ AMNERF_API amnerf_status amnerf_render_host(amnerf_ctx *ctx, const float *rays_o
                                  float *depth_host, float *opacity_host, amnerf_stats *stats);
 
 /* Wait for the context stream and return (then clear) the sticky device status:
- * E_TIMEOUT when a bounded device wait ran out, E_CUDA on an asynchronous CUDA error. */
+ * E_TIMEOUT when a bounded device wait ran out, E_INVAL when given crossings were out
+ * of range (amnerf_render_crossings), E_CUDA on an asynchronous CUDA error. */
 AMNERF_API amnerf_status amnerf_sync(amnerf_ctx *ctx);
 
 /* Failure-detection self-test (no counterpart in the paper): launches a kernel that

@@ -105,6 +105,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "amnerf_render_debug": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V,
                                  ctypes.POINTER(amnerf_debug), V], S),
         "amnerf_render_host": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V, V], S),
+        "amnerf_render_crossings": ([V, V, V, L, ctypes.POINTER(amnerf_render_params), V, V, V, V, V, V, V, V], S),
         "amnerf_sync": ([V], S),
         "amnerf_selftest_wait": ([V, ctypes.c_uint64], S),
         "amnerf_group_by_leaf_static": ([V, V, L, I, I, V, V, V, V], S),
@@ -264,6 +265,20 @@ def amnerf_render_debug(ctx, o, d, rgb, depth, opacity, dbg: dict, steps: int = 
     st = load().amnerf_render_debug(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(rgb), _ptr(depth),
                                     _ptr(opacity), ctypes.byref(db), ctypes.byref(sp) if sp is not None else None)
     _check(ctx, st, "amnerf_render_debug")
+    return sp.as_dict() if sp is not None else None
+
+
+def amnerf_render_crossings(ctx, o, d, n_x, leaf, t_in, t_out, rgb, depth, opacity, steps: int = 8,
+                            cap: int = 64, t_term: float = 1e-4, bg=(0.0, 0.0, 0.0), stats: bool = False,
+                            jitter: int = 0, ert_wave: int = 0):
+    """Render from crossings given as CUDA tensors (n_x uint8 [n]; leaf int16 and t_in,
+    t_out float32 [n * maxc], maxc = cap // steps)."""
+    p = _params(steps, cap, t_term, bg, jitter=jitter, ert_wave=ert_wave)
+    sp = amnerf_stats() if stats else None
+    st = load().amnerf_render_crossings(ctx, _ptr(o), _ptr(d), o.shape[0], ctypes.byref(p), _ptr(n_x), _ptr(leaf),
+                                        _ptr(t_in), _ptr(t_out), _ptr(rgb), _ptr(depth), _ptr(opacity),
+                                        ctypes.byref(sp) if sp is not None else None)
+    _check(ctx, st, "amnerf_render_crossings")
     return sp.as_dict() if sp is not None else None
 
 

@@ -100,6 +100,11 @@ cudaError_t launch_scatter_wave(cudaStream_t s, bool count, const uint8_t* n_x, 
 // Kernel attributes of the grouping kernels (their shared memory grows with the number
 // of networks, up to kMaxNets); call once per device before a render.
 cudaError_t prepare_group();
+// Crossings given by the caller instead of the traversal (render from crossings): copied
+// into the crossing list, counted per network; bad ids / counts set kDevErrBounds.
+cudaError_t launch_load_crossings(cudaStream_t s, const uint8_t* n_x_in, const uint16_t* leaf_in, const float* t_in,
+                                  const float* t_out, uint32_t n_rays, int maxc, int n_nets, uint8_t* n_x,
+                                  float2* xing, uint16_t* xleaf, uint32_t* counts, int* err);
 
 // Tile schedules of the network kernels (values of amnerf_tuning.schedule).
 constexpr int kSchedContiguous = 0;   // worker w takes tiles [w * per, (w + 1) * per)

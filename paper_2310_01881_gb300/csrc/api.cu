@@ -462,10 +462,22 @@ amnerf_status amnerf_load_mlps_fp8_static(amnerf_ctx* ctx, const amnerf_mlp_desc
     return load_impl(ctx, desc, n_leaves, weights_host, act_max_host);
 }
 
+// Crossings given by the caller (amnerf_render_crossings), in the debug layout.
+struct CrossingsIn {
+    const uint8_t* n_x;
+    const uint16_t* leaf;
+    const float* t_in;
+    const float* t_out;
+};
+
+static amnerf_status device_status(int herr) {
+    return herr == kDevErrTimeout ? AMNERF_E_TIMEOUT : (herr == kDevErrBounds ? AMNERF_E_INVAL : AMNERF_E_CUDA);
+}
+
 static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* rd, int64_t n,
                                  const amnerf_render_params* p, float* rgb, float* depth, float* opacity,
                                  const amnerf_debug* dbg, amnerf_stats* stats, float* bins_out = nullptr,
-                                 float2* root_out = nullptr) {
+                                 float2* root_out = nullptr, const CrossingsIn* cin = nullptr) {
     if (!ctx) return AMNERF_E_INVAL;
     if (ctx->nodes.empty()) return fail(ctx, AMNERF_E_NOTREE, "build the tree first");
     if (!ctx->mlp_loaded) return fail(ctx, AMNERF_E_NOMLP, "load the networks first");
@@ -481,6 +493,10 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
     }
     if (p->lod > 0.0f && ctx->n_nets != (int)ctx->nodes.size())
         return fail(ctx, AMNERF_E_INVAL, "lod > 0 needs one network per node");
+    if (cin && (p->use_proposal || p->skip_empty || p->lod > 0.0f || bins_out || root_out))
+        return fail(ctx, AMNERF_E_INVAL, "given crossings take no proposal, skipping, lod or targets");
+    if (cin && n > 0 && (!cin->n_x || !cin->leaf || !cin->t_in || !cin->t_out))
+        return fail(ctx, AMNERF_E_INVAL, "NULL crossing buffer");
     cudaStream_t s = ctx->stream;
     const int L = ctx->n_nets;  // networks: the grouping keys
     const uint32_t nn = (uint32_t)n;
@@ -519,9 +535,15 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         occ.steps = steps;
         occ.jitter = p->jitter_seed;
     }
-    CK(launch_traverse(s, ro, rd, nn, ctx->d_nodes, maxc, ctx->d_nx, ctx->d_xing, ctx->d_xleaf, ctx->d_counts, L,
-                       ctx->d_err, mask, fallback, root_out, occ, hier),
-       "traverse launch");
+    if (cin) {
+        CK(launch_load_crossings(s, cin->n_x, cin->leaf, cin->t_in, cin->t_out, nn, maxc, L, ctx->d_nx, ctx->d_xing,
+                                 ctx->d_xleaf, ctx->d_counts, ctx->d_err),
+           "crossing load launch");
+    } else {
+        CK(launch_traverse(s, ro, rd, nn, ctx->d_nodes, maxc, ctx->d_nx, ctx->d_xing, ctx->d_xleaf, ctx->d_counts, L,
+                           ctx->d_err, mask, fallback, root_out, occ, hier),
+           "traverse launch");
+    }
     if (ctx->timing) cudaEventRecord(ctx->ev[1], s);
     CK(launch_scan(s, ctx->d_counts, L, kTileRows / steps, ctx->d_offsets, ctx->d_tile_off, ctx->d_cursor,
                    ctx->d_stats),
@@ -694,10 +716,19 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         CK(cudaMemcpy(&herr, ctx->d_err, sizeof herr, cudaMemcpyDeviceToHost), "status copy");
         if (herr) {
             cudaMemset(ctx->d_err, 0, sizeof(int));
-            return fail(ctx, herr == kDevErrTimeout ? AMNERF_E_TIMEOUT : AMNERF_E_CUDA, "device status word set");
+            return fail(ctx, device_status(herr), "device status word set");
         }
     }
     return AMNERF_OK;
+}
+
+amnerf_status amnerf_render_crossings(amnerf_ctx* ctx, const float* rays_o, const float* rays_d, int64_t n_rays,
+                                      const amnerf_render_params* params, const uint8_t* n_x, const uint16_t* leaf,
+                                      const float* t_in, const float* t_out, float* rgb, float* depth, float* opacity,
+                                      amnerf_stats* stats) {
+    const CrossingsIn cin{n_x, leaf, t_in, t_out};
+    return render_impl(ctx, rays_o, rays_d, n_rays, params, rgb, depth, opacity, nullptr, stats, nullptr, nullptr,
+                       &cin);
 }
 
 amnerf_status amnerf_render(amnerf_ctx* ctx, const float* rays_o, const float* rays_d, int64_t n_rays,
@@ -1035,7 +1066,7 @@ amnerf_status amnerf_sync(amnerf_ctx* ctx) {
     CK(cudaMemcpy(&herr, ctx->d_err, sizeof herr, cudaMemcpyDeviceToHost), "status copy");
     if (herr) {
         cudaMemset(ctx->d_err, 0, sizeof(int));
-        return fail(ctx, herr == kDevErrTimeout ? AMNERF_E_TIMEOUT : AMNERF_E_CUDA, "device status word set");
+        return fail(ctx, device_status(herr), "device status word set");
     }
     return AMNERF_OK;
 }

@@ -237,6 +237,63 @@ cudaError_t launch_scatter_wave(cudaStream_t s, bool count, const uint8_t* n_x, 
     return cudaGetLastError();
 }
 
+namespace {
+
+// Crossings given by the caller (render from crossings): per ray r, n_x[r] <= maxc
+// crossings k with network leaf[r maxc + k] and interval (t_in, t_out).  Copies them
+// into the render's crossing list and counts them per network (shared-memory
+// histogram, one atomic per touched network per CTA).  A network id >= n_nets or a
+// count above maxc is recorded in the error word and replaced by 0 / maxc, so later
+// stages stay in bounds.
+__global__ void __launch_bounds__(256) k_load_crossings(const uint8_t* __restrict__ n_x_in,
+                                                        const uint16_t* __restrict__ leaf_in,
+                                                        const float* __restrict__ t_in, const float* __restrict__ t_out,
+                                                        uint32_t n_rays, int maxc, int n_nets,
+                                                        uint8_t* __restrict__ n_x, float2* __restrict__ xing,
+                                                        uint16_t* __restrict__ xleaf, uint32_t* __restrict__ counts,
+                                                        int* __restrict__ err) {
+    extern __shared__ uint32_t s_cnt[];
+    for (int i = threadIdx.x; i < n_nets; i += blockDim.x) s_cnt[i] = 0u;
+    __syncthreads();
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n_rays) {
+        int c = __ldg(n_x_in + r);
+        if (c > maxc) {
+            atomicCAS(err, 0, kDevErrBounds);
+            c = maxc;
+        }
+        n_x[r] = (uint8_t)c;
+        const size_t base = (size_t)r * (size_t)maxc;
+        for (int k = 0; k < c; ++k) {
+            uint32_t l = __ldg(leaf_in + base + k);
+            if (l >= (uint32_t)n_nets) {
+                atomicCAS(err, 0, kDevErrBounds);
+                l = 0u;
+            }
+            xleaf[base + k] = (uint16_t)l;
+            xing[base + k] = make_float2(__ldg(t_in + base + k), __ldg(t_out + base + k));
+            atomicAdd(&s_cnt[l], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_nets; i += blockDim.x) {
+        const uint32_t c = s_cnt[i];
+        if (c) atomicAdd(&counts[i], c);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_load_crossings(cudaStream_t s, const uint8_t* n_x_in, const uint16_t* leaf_in, const float* t_in,
+                                  const float* t_out, uint32_t n_rays, int maxc, int n_nets, uint8_t* n_x,
+                                  float2* xing, uint16_t* xleaf, uint32_t* counts, int* err) {
+    if (n_rays == 0) return cudaSuccess;
+    const unsigned blocks = (n_rays + 255) / 256;
+    k_load_crossings<<<blocks, 256, sizeof(uint32_t) * (size_t)n_nets, s>>>(n_x_in, leaf_in, t_in, t_out, n_rays, maxc,
+                                                                           n_nets, n_x, xing, xleaf, counts, err);
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_group() {
     // two counters per network: up to 64 KB of dynamic shared memory
     const int smem = (int)(2 * sizeof(uint32_t) * kMaxNets);

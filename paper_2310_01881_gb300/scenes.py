@@ -29,7 +29,7 @@ import numpy as np
 __all__ = [
     "Scene", "RenderConfig", "CONFIGS", "scene_for", "density_grid", "camera_rays",
     "view_rays", "params_per_leaf", "mlp_input_width", "leaf_mean_density",
-    "xavier_weights", "ray_subset", "proposal_init", "PROPOSAL_PARAMS",
+    "xavier_weights", "ray_subset", "proposal_init", "PROPOSAL_PARAMS", "zipf_crossings",
 ]
 
 
@@ -205,6 +205,25 @@ def view_rays(cfg: RenderConfig, seed: int, view: int, px_w: int | None = None,
     rng = np.random.default_rng([seed, 0xCA3E7A, view])
     u = rng.normal(size=3)
     return camera_rays(u, px_w or cfg.px_w, px_h or cfg.px_h, cfg.fov_deg, cfg.radius)
+
+
+def zipf_crossings(n_rays: int, maxc: int, n_nets: int, s: float, seed: int):
+    """Synthetic crossing lists whose per-network counts follow a Zipf law: every ray
+    has maxc crossings; each crossing's network is drawn independently with
+    probability proportional to rank^-s over ranks 1..n_nets, the ranks mapped to
+    network ids by a seeded permutation.  Crossing k of a ray spans
+    [2 + 0.03 k, 2.03 + 0.03 k].  Returns n_x uint8 [n], leaf uint16 [n, maxc], t_in,
+    t_out float32 [n, maxc] (the layout of the render's crossing list)."""
+    rng = np.random.default_rng([seed, 0x21FF])
+    p = np.arange(1, n_nets + 1, dtype=np.float64) ** (-float(s))
+    p /= p.sum()
+    perm = rng.permutation(n_nets)
+    ranks = rng.choice(n_nets, size=(n_rays, maxc), p=p)
+    leaf = perm[ranks].astype(np.uint16)
+    k = np.arange(maxc, dtype=np.float32)
+    t_in = np.broadcast_to(np.float32(2.0) + np.float32(0.03) * k, (n_rays, maxc)).astype(np.float32)
+    t_out = (t_in + np.float32(0.03)).astype(np.float32)
+    return np.full(n_rays, maxc, np.uint8), leaf, t_in, t_out
 
 
 def ray_subset(n_total: int, k: int, seed: int) -> np.ndarray:
