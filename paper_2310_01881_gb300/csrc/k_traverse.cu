@@ -96,6 +96,9 @@ __device__ __forceinline__ bool crossing_occupied(const OccArgs& oc, const float
     return false;
 }
 
+// HIER: adaptive hierarchical sampling compiled in (its HCheck costs registers, so the
+// leaf-only walk is a separate instantiation).
+template <bool HIER>
 __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, const float* __restrict__ rd,
                                                   uint32_t n, const DevNode* __restrict__ nodes, int maxc,
                                                   uint8_t* __restrict__ n_x, float2* __restrict__ xing,
@@ -156,14 +159,14 @@ __global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, 
             const int axis = (int)(meta & 3u) - 1;
             // HCheck: an inner node finer than the footprint is one crossing of its own network
             bool emit = axis < 0;
-            if (!emit && hier.node_net) {
+            if (HIER && !emit) {
                 const float ext = axis == 0 ? __fsub_rn(B.x, A.x) : (axis == 1 ? __fsub_rn(B.y, A.y) : __fsub_rn(B.z, A.z));
                 emit = !(ext > __fmul_rn(hier.lod, tin));
             }
             if (emit) {
                 if (masked && !overlaps_kept(kept_bins, r0, bw, tin, tout)) continue;
                 if (occ.grid && !crossing_occupied(occ, o, d, key, tin, tout, cnt)) continue;
-                const uint32_t net = axis < 0 ? meta >> 2 : (uint32_t)__ldg(hier.node_net + nd);
+                const uint32_t net = (!HIER || axis < 0) ? meta >> 2 : (uint32_t)__ldg(hier.node_net + nd);
                 xing[base + cnt] = make_float2(tin, tout);
                 xleaf[base + cnt] = (uint16_t)net;
                 atomicAdd(&s_cnt[net], 1u);
@@ -209,7 +212,8 @@ cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, ui
     const size_t smem = sizeof(uint32_t) * (size_t)n_leaves;
     HierArgs h = hier;
     if (!(h.lod > 0.0f)) h.node_net = nullptr;
-    k_traverse<<<blocks, threads, smem, s>>>(ro, rd, n, nodes, maxc, n_x, xing, xleaf, counts, n_leaves, err, mask,
+    auto kern = h.node_net ? k_traverse<true> : k_traverse<false>;
+    kern<<<blocks, threads, smem, s>>>(ro, rd, n, nodes, maxc, n_x, xing, xleaf, counts, n_leaves, err, mask,
                                              fallback, root_out, occ, h);
     return cudaGetLastError();
 }

@@ -12,6 +12,7 @@ import pytest
 
 import oracle as O
 from paper_2310_01881_gb300 import scenes as S
+from pixtol import check_pixels
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -77,10 +78,8 @@ def test_c1_crossings_grouping_and_fp32_pixels_against_oracle(R, seed):
         if lod >= 0.3:
             assert counts[tree.n_leaves:].sum() > 0   # inner networks take crossings
         ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1, lod=lod)
-        ok = ref["ert_margin"] > 1e-3
-        assert np.abs(rgb - ref["rgb"]).max(axis=1)[ok].max() <= 1e-5
-        assert np.abs(opac - ref["opacity"])[ok].max() <= 1e-5
-        assert np.abs(depth - ref["depth"])[ok].max() <= 1e-5
+        check_pixels(((rgb, ref["rgb"]), (depth, ref["depth"]), (opac, ref["opacity"])), ref["ert_margin"],
+                     f"hierarchical c1 seed {seed} lod {lod}")
         assert st["samples_generated"] == int(ref["n_gen"].sum())
 
 

@@ -17,8 +17,7 @@ from paper_2310_01881_gb300 import scenes as S
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PIX_TOL = 1e-5
-ERT_TOL = 2e-4
+from pixtol import ERT_TOL, PIX_TOL, check_pixels  # noqa: F401
 
 
 @pytest.fixture(scope="module")
@@ -93,12 +92,9 @@ def _check_crossings(dbg, tree, o, d, maxc, steps):
         np.testing.assert_array_equal(np.sort(got[a:b]), np.sort(order[a:b]))
 
 
-def _check_pixels(rgb, depth, opac, ref, tol=PIX_TOL):
-    amb = ref["ert_margin"] < 1e-3
-    for got, exp in ((rgb, ref["rgb"]), (depth[:, None], ref["depth"][:, None]), (opac[:, None], ref["opacity"][:, None])):
-        err = np.abs(got.astype(np.float64) - exp).max(axis=1)
-        assert err[~amb].max(initial=0.0) <= tol, err[~amb].max()
-        assert err[amb].max(initial=0.0) <= ERT_TOL
+def _check_pixels(rgb, depth, opac, ref, tol=PIX_TOL, label="FP32 pixels"):
+    return check_pixels(((rgb, ref["rgb"]), (depth, ref["depth"]), (opac, ref["opacity"])), ref["ert_margin"], label,
+                        tol)
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
@@ -305,8 +301,7 @@ def test_skipping_with_proposal_masks_matches_oracle(R):
     ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1,
                    mask=mask, fallback=fb, skip=(grid, thr))
     np.testing.assert_array_equal(dbg["n_x"].astype(np.int64) * cfg.steps, ref["n_gen"])
-    ok = ref["ert_margin"] > 1e-3
-    assert np.abs(rgb - ref["rgb"]).max(axis=1)[ok].max() <= 1e-5
+    check_pixels(((rgb, ref["rgb"]),), ref["ert_margin"], "skipping with proposal masks")
 
 
 @pytest.mark.parametrize("prec,jitter,scale", [("fp32", 0, 1000.0), ("bf16", 5, 1000.0), ("fp32", 3, 1.0),
