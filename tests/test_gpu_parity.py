@@ -129,6 +129,19 @@ def test_c1_fp32_pixels_match_fp32_oracle(R, seed):
         abs(st["samples_composited"] - int(ref["n_eval"].sum())) <= int((ref["ert_margin"] < 1e-3).sum())
 
 
+def test_c1_fp32_pixels_on_an_opaque_scene(R):
+    """Every density x1000: most rays terminate inside their first crossings, so the
+    early ray termination of the compositing is exercised; pixels within 1e-5 of the
+    FP32-mode oracle, rays near the threshold reported (and held to 2e-4)."""
+    cfg = S.CONFIGS["c1"]
+    _, tree, P = _setup(R, cfg, 0, scale=1000.0)
+    o, d = _rays(cfg, 0, views=2)
+    rgb, depth, opac, dbg, st = R.render_debug(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)
+    ref = O.render(tree, P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=1, threads=8)
+    assert (ref["n_eval"] < ref["n_gen"]).mean() > 0.3          # termination happens on most hit rays
+    _check_pixels(rgb, depth, opac, ref, label="FP32 pixels, opaque scene (density x1000)")
+
+
 def test_c1_fp32_close_to_fp64_definition(R):
     cfg = S.CONFIGS["c1"]
     _, tree, P = _setup(R, cfg, 0)
