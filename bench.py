@@ -68,33 +68,57 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons.  Each row carries
+    nvidia-smi's own timestamp, so a sampler started before the warm-up keeps only
+    the rows taken between mark_start() and mark_stop() (the timed region), with the
+    first row after the region as a stand-in when the region is shorter than the
+    sampling interval."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 100
 
     def __init__(self, index: int):
         self.index = index
         self.rows = []
         self.proc = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.INTERVAL_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
             self.proc = None
         return self
 
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_stop(self):
+        self.t1 = time.time()
+        if self.proc is not None:   # let the row that follows the region arrive
+            time.sleep(2.5 * self.INTERVAL_MS / 1000)
+
+    @staticmethod
+    def _stamp(x: str):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(x, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
     def _read(self):
         for line in self.proc.stdout:
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 8:
-                self.rows.append(parts)
+            if len(parts) >= 9:
+                self.rows.append([self._stamp(parts[0])] + parts[1:])
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -106,7 +130,15 @@ class ClockSampler:
             self.thread.join(timeout=2)
 
     def summary(self) -> dict:
-        if not self.rows:
+        rows, window = self.rows, "whole sampler"
+        if self.t0 is not None and self.t1 is not None and all(r[0] is not None for r in rows):
+            inside = [r for r in rows if self.t0 <= r[0] <= self.t1]
+            after = [r for r in rows if r[0] > self.t1]
+            if inside:
+                rows, window = inside, "timed region"
+            else:
+                rows, window = after[:1], "first sample after the timed region"
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
 
         def num(x):
@@ -115,12 +147,12 @@ class ClockSampler:
             except ValueError:
                 return None
 
-        sm = [num(r[0]) for r in self.rows if num(r[0]) is not None]
-        mx = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows), "window": window}
 
 
 def _dist():
@@ -245,22 +277,24 @@ def run_ours(args):
             R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, act_max=amax)
         else:
             R.load_mlps(P, cfg.width, cfg.hidden, cfg.lx, cfg.ld, prec)
-        for _ in range(args.warmup):
-            R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter, skip_empty=args.skip_empty,
-                     ert_wave=args.ert_wave, lod=lod)
-        _, _, _, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter,
-                               skip_empty=args.skip_empty, ert_wave=args.ert_wave, lod=lod)
-        torch.cuda.synchronize()
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
+        with ClockSampler(local) as clk:       # started before the warm-up: sampling when the timed region opens
+            for _ in range(args.warmup):
+                R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter,
+                         skip_empty=args.skip_empty, ert_wave=args.ert_wave, lod=lod)
+            _, _, _, st = R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, stats=True, out=out, jitter=args.jitter,
+                                   skip_empty=args.skip_empty, ert_wave=args.ert_wave, lod=lod)
             torch.cuda.synchronize()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            clk.mark_start()
             e0.record(stream)
             for _ in range(args.steps):
                 R.render(o, d, cfg.steps, cfg.cap, cfg.t_term, out=out, jitter=args.jitter, skip_empty=args.skip_empty,
                          ert_wave=args.ert_wave, lod=lod)
             e1.record(stream)
             torch.cuda.synchronize()
+            clk.mark_stop()
         barrier()
         ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
         R.sync()
