@@ -25,10 +25,11 @@
 // each MMA it reads its row of D (tcgen05.ld 32x32b: warp q of the group owns lanes
 // 32q..32q+31) and writes the next layer's A back into TMEM.  BF16 folds layer 0's
 // bias into its contraction (a weight column against a constant-1 input column) and
-// starts every later layer's accumulator at its FP32 bias (written by the epilogue
-// before), so the epilogue is ReLU with the conversion (cvt.rn.relu.bf16x2) and the
-// bias store; E4M3 applies its channel scales and bias with one packed FMA per pair
-// first.  The 4-wide head is one
+// writes every later layer's FP32 bias into its accumulator with one more K = 16 MMA
+// (three constant-1 input columns of layer 0, still in TMEM, against the bias split
+// into three BF16 parts), so the epilogue is ReLU with the conversion
+// (cvt.rn.relu.bf16x2) and nothing else; E4M3 applies its channel scales and bias
+// with one packed FMA per pair first.  The 4-wide head is one
 // more BF16 MMA (16 rows, 4 used) on relu(h) written into the group's D columns; it
 // runs while the group encodes its next tile.  Its accumulator sits in 16 TMEM
 // columns that no layer writes, so its outputs (sigma = softplus, rgb = sigmoid) are
@@ -67,12 +68,13 @@ constexpr int kMaxGroups = 4;
 // per-output-channel scales sw [hidden][width]); head Wo BF16 [16 x khead]; FP32
 // biases b_0..b_{hidden-1} [width] and bo [4].  kh = khead = width.  BF16 folds layer
 // 0's bias into its contraction (input column 90, inside the padding to k0p = 96,
-// holds the bias and the encoded row carries 1 there); for every later BF16 layer and
-// for the head the epilogue of the layer before writes the FP32 bias into the
-// accumulator columns, and the MMAs accumulate onto it (a folded bias would cost one
-// more K = 16 step per layer).  E4M3 adds its FP32 bias in the epilogue, after the
-// scales (an E4M3 bias would lose too much).  Both run the head as one more BF16 MMA
-// of a 16-row matrix (rows 0..3 used).
+// holds the bias and the encoded row carries 1 there).  For every later BF16 layer
+// one more K = 16 MMA writes the FP32 bias into the accumulator (block bb, below) in
+// the one-thread-per-row kernel; the two-threads-per-row kernel and the head have the
+// epilogue of the layer before write the FP32 bias (block bias) into the accumulator
+// columns.  The MMAs accumulate onto it.  E4M3 adds its FP32 bias in the epilogue,
+// after the scales (an E4M3 bias would lose too much).  Both run the head as one more
+// BF16 MMA of a 16-row matrix (rows 0..3 used).
 // E4M3 with static activation scales (act_max known per leaf and layer) keeps the
 // per-output-channel weight scales s_(l,n) = max|W_l[n,:]| / 448 (W stored as W / s)
 // and gives every layer input one static scale a_l = act_max_l / 448 (a_hidden = 1:
@@ -81,9 +83,17 @@ constexpr int kMaxGroups = 4;
 // relu(acc * C[l][n] + B[l][n]) with C = a_l s_(l,n) / a_(l+1) and B = b_n / a_(l+1):
 // one packed FMA per pair of values in the epilogue, C in the scale block and B in
 // the bias block of the blob; enc holds 1 / a_0 (the encoding's scale).
+// BF16 also holds, for each hidden layer l >= 1, its bias as a width x 16 B operand
+// (block bb): K columns 10, 11, 12 carry the bias split into three BF16 parts
+// (hi = bf16(b), mid = bf16(b - hi), lo = bf16(b - hi - mid); together the 24 bits
+// of an FP32 significand), the other columns zero.  Against layer-0 input columns
+// 80..95, whose columns 90..92 are constant ones and which no later layer
+// overwrites, one K = 16 MMA writes exactly b into the accumulator; the layer's own
+// MMAs then accumulate onto it.
+constexpr int kBiasK = 16;
 struct TcLayout {
     int width, hidden, k0, k0p, kh, khead, es;
-    size_t w0, wh, wo, sw, bias, enc, stride;
+    size_t w0, wh, wo, sw, bias, enc, bb, stride;
     __host__ __device__ TcLayout(int w, int h, int k, bool f8)
         : width(w), hidden(h), k0(k), k0p(round_up(f8 ? k : k + 1, f8 ? 32 : 16)), kh(w),
           khead(w), es(f8 ? 1 : 2) {
@@ -93,7 +103,8 @@ struct TcLayout {
         sw = wo + (size_t)16 * khead * 2;
         bias = sw + (f8 ? (size_t)h * w * 4 : 0);
         enc = bias + (size_t)h * w * 4 + 16;  // E4M3 static scales: 1 / (encoding scale)
-        const size_t end = enc + 16;
+        bb = (enc + 16 + 127) / 128 * 128;
+        const size_t end = bb + (f8 ? 0 : (size_t)(h - 1) * w * kBiasK * 2);
         stride = (end + 127) / 128 * 128;
     }
 };
@@ -235,13 +246,13 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         const uint32_t d_row = d_col + lane;                          // this warp's lanes
         const uint32_t a_row = a_col + lane;
         const float* bias = reinterpret_cast<const float*>(wbuf + lay.bias);
-        const uint32_t bias_s = smem_u32(bias);
         // shared-memory descriptors of the first core matrix of W0, W1 and the head; the
         // start-address field holds address / 16 in 14 bits, and every address here is
         // below 2^18, so later core matrices are these plus (offset / 16)
         const uint64_t desc_w0 = sdesc(w_addr + (uint32_t)lay.w0, (uint32_t)K0P * (F8 ? 8u : 16u));
         const uint64_t desc_wh = sdesc(w_addr + (uint32_t)lay.wh, (uint32_t)lay.kh * (F8 ? 8u : 16u));
         const uint64_t desc_wo = sdesc(w_addr + (uint32_t)lay.wo, (uint32_t)lay.khead * 16u);
+        const uint64_t desc_bb = sdesc(w_addr + (uint32_t)lay.bb, (uint32_t)kBiasK * 16u);
         const uint8_t* wall = reinterpret_cast<const uint8_t*>(g.weights);
 
         // ---- tile schedule of this worker (one warpgroup)
@@ -417,8 +428,12 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                             mma_e4m3_ts(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, kk > 0 ? 1u : 0u);
                     } else {
                         const uint32_t idd = idesc_bf16(W);
-                        // layer 0 starts from zero (its bias is folded in); later layers
-                        // accumulate onto the bias the previous epilogue wrote
+                        // layer 0 starts from zero (its bias is folded in); a later layer
+                        // first writes its bias (the constant-1 input columns against the
+                        // layer's bias operand), then accumulates onto it
+                        if (l > 0)
+                            mma_bf16_ts(d_col, a_col + (uint32_t)(kOnesStep / 2),
+                                        desc_bb + (uint64_t)(((size_t)(l - 1) * W * kBiasK * 2) >> 4), idd, 0u);
                         for (int kk = 0; kk < kin / KI; ++kk)
                             mma_bf16_ts(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, (kk > 0 || l > 0) ? 1u : 0u);
                     }
@@ -504,11 +519,6 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                             }
                             tmem_st16(a_row + 16u * h, pk);
                         }
-                        // layer l + 1 accumulates onto its bias.  The source registers of
-                        // a tcgen05.st stay reserved until its wait, so A's stores are
-                        // waited for first (else A and the bias take 3 W/2 registers).
-                        tmem_st_wait();
-                        tmem_st_bias<W>(d_row, bias_s + 4u * (uint32_t)((l + 1) * W));
                     } else if constexpr (ST) {
                         // relu(acc C + B) is the next layer's E4M3 input; the row is read
                         // in 32-column halves (the scales and biases take registers too)
@@ -683,7 +693,7 @@ __device__ __forceinline__ void tmem_st_words(uint32_t taddr, const uint32_t* w)
 
 // The layer-0 input half `half` of a row (48 features in kperm order) packed into 24
 // words: half 0 = p_x, x octaves 0-4, p_d, d octaves 0-1; half 1 = x octaves 5-9,
-// d octaves 2-3, the bias input 1 and zero padding.  The anchors are those of
+// d octaves 2-3, the three constant-1 columns and zero padding.  The anchors are those of
 // encode_freq (x at octaves 0 and 5, d at 0), so the features are bit-identical.
 __device__ __forceinline__ void encode_half(int half, const float x[3], const float d[3], uint32_t (&w)[24]) {
     float f[48];
@@ -703,9 +713,9 @@ __device__ __forceinline__ void encode_half(int half, const float x[3], const fl
         encode_octaves<0, 4, 0>(d, fd);
 #pragma unroll
         for (int i = 0; i < 12; ++i) f[30 + i] = fd[12 + i];
-        f[42] = 1.0f;
+        f[42] = f[43] = f[44] = 1.0f;   // columns 90..92 (kperm)
 #pragma unroll
-        for (int i = 43; i < 48; ++i) f[i] = 0.0f;
+        for (int i = 45; i < 48; ++i) f[i] = 0.0f;
     }
 #pragma unroll
     for (int i = 0; i < 24; ++i) w[i] = pack_bf16(f[2 * i], f[2 * i + 1]);
@@ -769,6 +779,7 @@ __global__ void __launch_bounds__(128 * kTPR * MAXG, 1) k_mlp_tc2(MlpArgs g, int
         const uint64_t desc_w0 = sdesc(w_addr + (uint32_t)lay.w0, (uint32_t)K0P * 16u);
         const uint64_t desc_wh = sdesc(w_addr + (uint32_t)lay.wh, (uint32_t)lay.kh * 16u);
         const uint64_t desc_wo = sdesc(w_addr + (uint32_t)lay.wo, (uint32_t)lay.khead * 16u);
+        const uint64_t desc_bb = sdesc(w_addr + (uint32_t)lay.bb, (uint32_t)kBiasK * 16u);
         const uint8_t* wall = reinterpret_cast<const uint8_t*>(g.weights);
 
         const uint32_t t_end = g.t_end == 0xffffffffu ? (uint32_t)g.stats[1] : g.t_end;
@@ -1159,6 +1170,27 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
     }
     w += 4 * width;
     for (int n = 0; n < 4; ++n) bias[(size_t)hidden * width + n] = w[n];
+    if (!f8) {  // hidden layers 1.. : the bias as a three-part BF16 operand (block bb)
+        auto bf_value = [](uint16_t b) {
+            const uint32_t u = (uint32_t)b << 16;
+            float f;
+            std::memcpy(&f, &u, 4);
+            return f;
+        };
+        for (int l = 1; l < hidden; ++l) {
+            uint8_t* base = dst + lay.bb + (size_t)(l - 1) * width * kBiasK * 2;
+            for (int n = 0; n < width; ++n) {
+                const float b = bias[(size_t)l * width + n];
+                const uint16_t hi = f2bf(b);
+                const float r1 = b - bf_value(hi);  // exact: b and hi share their leading bits
+                const uint16_t mid = f2bf(r1);
+                const uint16_t lo = f2bf(r1 - bf_value(mid));
+                const uint16_t parts[3] = {hi, mid, lo};
+                for (int i = 0; i < 3; ++i)
+                    std::memcpy(base + cm_offset(n, kOnesCol - kOnesStep + i, kBiasK), &parts[i], 2);
+            }
+        }
+    }
 }
 
 cudaError_t launch_wait_selftest(cudaStream_t s, unsigned long long limit, int* err) {

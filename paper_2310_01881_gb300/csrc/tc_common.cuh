@@ -384,12 +384,20 @@ __device__ __forceinline__ void encode_octaves(const float p[3], float (&f)[N]) 
 // encoding gamma_10(x) ++ gamma_4(d) (canonical feature c, 90 features) is stored so
 // that the first 48 columns hold p_x and x's octaves 0-4, p_d and d's octaves 0-1, and
 // the last 48 hold x's octaves 5-9, d's octaves 2-3, the bias input (column 90, a
-// constant 1) and zero padding: each half of a row is encoded by its own thread from
-// its own anchors.  kperm(k) is the canonical feature of column k, -1 for the bias
-// input and -2 for padding.
+// constant 1), two more constant-1 columns (91, 92) whose layer-0 weights are zero,
+// and zero padding: each half of a row is encoded by its own thread from its own
+// anchors.  Columns 80..95 stay in TMEM through the tile's later layers, so the
+// constant-1 columns 90..92 also serve as the inputs of those layers' bias terms (one
+// K = 16 MMA against the bias split into three BF16 parts).  kperm(k) is the
+// canonical feature of column k, -1 for the layer-0 bias input, -3 for the other
+// constant-1 columns and -2 for padding.
 __host__ __device__ constexpr int kperm(int k) {
-    return k < 33 ? k : (k < 48 ? k + 30 : (k < 78 ? k - 15 : (k < 90 ? k : (k == 90 ? -1 : -2))));
+    return k < 33 ? k
+                  : (k < 48 ? k + 30
+                            : (k < 78 ? k - 15 : (k < 90 ? k : (k == 90 ? -1 : (k <= 92 ? -3 : -2)))));
 }
+constexpr int kOnesStep = 80;  // first column of the K = 16 step that holds the constant-1 columns
+constexpr int kOnesCol = 90;   // the constant-1 columns are kOnesCol .. kOnesCol + 2
 
 // Columns [32 C, 32 C + 32) of the layer-0 input in kperm order, from the canonical
 // features f, packed two per word and written to this thread's TMEM lane.
@@ -400,8 +408,8 @@ __device__ __forceinline__ void store_chunk_perm(uint32_t a_row, const float (&f
     for (int i = 0; i < 16; ++i) {
         const int k0 = 32 * C + 2 * i, k1 = k0 + 1;
         const int c0 = kperm(k0), c1 = kperm(k1);
-        const float v0 = c0 >= 0 ? f[c0 >= 0 ? c0 : 0] : (c0 == -1 ? 1.0f : 0.0f);
-        const float v1 = c1 >= 0 ? f[c1 >= 0 ? c1 : 0] : (c1 == -1 ? 1.0f : 0.0f);
+        const float v0 = c0 >= 0 ? f[c0 >= 0 ? c0 : 0] : (c0 == -2 ? 0.0f : 1.0f);
+        const float v1 = c1 >= 0 ? f[c1 >= 0 ? c1 : 0] : (c1 == -2 ? 0.0f : 1.0f);
         w[i] = pack_bf16(v0, v1);
     }
     tmem_st16(a_row + 16u * C, w);
