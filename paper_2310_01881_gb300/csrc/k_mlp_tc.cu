@@ -37,11 +37,14 @@
 // tile's layer-1 MMAs run.
 //
 // Several warpgroups per CTA work on different tiles, so one group's epilogue
-// overlaps another's MMA.  Each group's leader thread (in warp grp % 4, so the
-// leaders run on different SM sub-partitions) issues the group's MMAs and tracks
-// completion with tcgen05.commit on the group's mbarrier.  Every wait is bounded
-// (clock64 deadline); on expiry the group records AMNERF_E_TIMEOUT in the status
-// word, leaves its tile loop, and the CTA still frees its TMEM before returning.
+// overlaps another's MMA.  Each group's leader warp (warp grp % 4 of the group, so
+// the leader warps run on different SM sub-partitions) issues the group's MMAs
+// converged, one lane elected per instruction, and tracks completion with
+// tcgen05.commit on the group's mbarrier, on which every thread of the group then
+// waits itself.  Every wait is bounded (clock64 deadline); a wait that runs out is
+// ORed over the group at its next barrier, the group records AMNERF_E_TIMEOUT in
+// the status word and leaves its tile loop together, and the CTA still frees its
+// TMEM before returning.
 //
 // Encoding: sin/cos(pi 2^k p) at k = 0 and k = 5 come from the SFU after an exact
 // argument reduction; the other octaves follow by the double-angle recurrence
@@ -215,6 +218,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
     // the group's leader (MMA issue, waits, weight loads) sits in warp grp % 4 of the
     // group, so the leaders of the 4 groups run on 4 different SM sub-partitions
     const bool leader = tig == 32 * (grp & 3);
+    const bool leader_warp = warp == 4 * grp + (grp & 3);  // the leader's warp: issues the MMAs, converged
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < n_groups; ++i) {
@@ -400,7 +404,10 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
             if (pending) {
                 // on expiry the leader issues no more MMAs, so the group's next wait runs
                 // out too and the whole group leaves through it
-                if (leader && !mbar_wait_bounded(bar_m, ph_m)) head_bad = true;
+                if (leader_warp) {
+                    const bool okw = mbar_wait_bounded(bar_m, ph_m);
+                    if (!__all_sync(0xffffffffu, okw)) head_bad = true;
+                }
                 ph_m ^= 1u;
                 pending = false;
             }
@@ -414,7 +421,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
 #pragma unroll
             for (int l = 0; l < hidden; ++l) {
                 if (!ok) break;
-                if (leader && !head_bad) {
+                if (leader_warp && !head_bad) {
                     tc_fence_after();
                     // this layer's first weight core matrix, then 256 B (16 descriptor
                     // units) per K step
@@ -425,19 +432,20 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                         const uint32_t idd = idesc_e4m3(W);
                         // every E4M3 layer starts from zero (scales and bias in the epilogue)
                         for (int kk = 0; kk < kin / KI; ++kk)
-                            mma_e4m3_ts(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, kk > 0 ? 1u : 0u);
+                            mma_e4m3_ts_warp(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, kk > 0 ? 1u : 0u);
                     } else {
                         const uint32_t idd = idesc_bf16(W);
                         // layer 0 starts from zero (its bias is folded in); a later layer
                         // first writes its bias (the constant-1 input columns against the
                         // layer's bias operand), then accumulates onto it
                         if (l > 0)
-                            mma_bf16_ts(d_col, a_col + (uint32_t)(kOnesStep / 2),
-                                        desc_bb + (uint64_t)(((size_t)(l - 1) * W * kBiasK * 2) >> 4), idd, 0u);
+                            mma_bf16_ts_warp(d_col, a_col + (uint32_t)(kOnesStep / 2),
+                                             desc_bb + (uint64_t)(((size_t)(l - 1) * W * kBiasK * 2) >> 4), idd, 0u);
                         for (int kk = 0; kk < kin / KI; ++kk)
-                            mma_bf16_ts(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, (kk > 0 || l > 0) ? 1u : 0u);
+                            mma_bf16_ts_warp(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd,
+                                             (kk > 0 || l > 0) ? 1u : 0u);
                     }
-                    mma_commit(bar_m);
+                    mma_commit_warp(bar_m);
                 }
                 // next tile of this worker, its leaf and this row's crossing id
                 auto next_lookup = [&](uint32_t tn) {
@@ -463,7 +471,13 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 if (!dyn && l == 0) next_lookup(t + t_step);
                 if (!dyn && l > 0 && l == l_xd) crossing_data(g, id_n, xi, ro, rd);
                 if (zpend && l == l_sh) store_head();
-                ok = group_wait(bar_m, ph_m, bar_id, flag, leader);
+                // Every thread waits for the MMAs itself (the dynamic schedule's first
+                // layer keeps the group barrier, which publishes the next tile).  A thread
+                // whose wait ran out carries that to the group's next barrier, where the
+                // whole group learns of it and leaves together.
+                bool late = false;
+                if (dyn && l == 0) ok = group_wait(bar_m, ph_m, bar_id, flag, leader);
+                else late = !mbar_wait_bounded(bar_m, ph_m);
                 ph_m ^= 1u;
                 if (!ok) break;
                 tc_fence_after();
@@ -567,7 +581,10 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     }
                     tmem_st_wait();
                     tc_fence_before();
-                    wg_bar(bar_id);
+                    if (wg_bar_any(bar_id, late)) {
+                        ok = false;
+                        break;
+                    }
                     kin = lay.kh;
                 } else {
                     // relu(h) as BF16 into this group's D columns (each 32-column block is
@@ -606,13 +623,16 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     tmem_st4(d_row + kHeadCol, bias + (size_t)hidden * W);
                     tmem_st_wait();
                     tc_fence_before();
-                    wg_bar(bar_id);
-                    if (leader) {
+                    if (wg_bar_any(bar_id, late)) {
+                        ok = false;
+                        break;
+                    }
+                    if (leader_warp) {
                         tc_fence_after();
                         const uint32_t idd = idesc_bf16(16);
                         for (int kk = 0; kk < lay.khead / 16; ++kk)
-                            mma_bf16_ts(d_col + kHeadCol, d_col + 8u * kk, desc_wo + 16u * kk, idd, 1u);
-                        mma_commit(bar_m);
+                            mma_bf16_ts_warp(d_col + kHeadCol, d_col + 8u * kk, desc_wo + 16u * kk, idd, 1u);
+                        mma_commit_warp(bar_m);
                     }
                     pending = true;
                     have_out = true;
@@ -744,6 +764,7 @@ __global__ void __launch_bounds__(128 * kTPR * MAXG, 1) k_mlp_tc2(MlpArgs g, int
     const int warp = threadIdx.x >> 5;
     const int bar_id = 1 + grp;
     const bool leader = tig == 32 * (grp & 3);
+    const bool leader_warp = wig == (grp & 3);  // the leader's warp: issues the MMAs, converged
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < n_groups; ++i) {
@@ -884,13 +905,13 @@ __global__ void __launch_bounds__(128 * kTPR * MAXG, 1) k_mlp_tc2(MlpArgs g, int
 #pragma unroll
             for (int l = 0; l < hidden; ++l) {
                 if (!ok) break;
-                if (leader) {
+                if (leader_warp) {
                     tc_fence_after();
                     const uint64_t b_desc = l == 0 ? desc_w0 : desc_wh + (uint64_t)(((size_t)(l - 1) * W * lay.kh * 2) >> 4);
                     const uint32_t idd = idesc_bf16(W);
                     for (int kk = 0; kk < kin / 16; ++kk)
-                        mma_bf16_ts(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, (kk > 0 || l > 0) ? 1u : 0u);
-                    mma_commit(bar_m);
+                        mma_bf16_ts_warp(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, (kk > 0 || l > 0) ? 1u : 0u);
+                    mma_commit_warp(bar_m);
                 }
                 auto next_lookup = [&](uint32_t tn) {
                     t_next = tn;
@@ -947,12 +968,12 @@ __global__ void __launch_bounds__(128 * kTPR * MAXG, 1) k_mlp_tc2(MlpArgs g, int
                     tmem_st_wait();
                     tc_fence_before();
                     bar_sync(bar_id, GT);
-                    if (leader) {
+                    if (leader_warp) {
                         tc_fence_after();
                         const uint32_t idd = idesc_bf16(16);
                         for (int kk = 0; kk < lay.khead / 16; ++kk)
-                            mma_bf16_ts(d_col + kHeadCol, a_col + 8u * kk, desc_wo + 16u * kk, idd, 1u);
-                        mma_commit(bar_m);
+                            mma_bf16_ts_warp(d_col + kHeadCol, a_col + 8u * kk, desc_wo + 16u * kk, idd, 1u);
+                        mma_commit_warp(bar_m);
                     }
                     pending = true;
                     have_out = true;

@@ -453,6 +453,7 @@ __global__ void __launch_bounds__(128 * kPTcGroups, 1) k_prop_infer_tc(
     const int g = threadIdx.x >> 7, t = threadIdx.x & 127, q = warp & 3;
     const int bar_id = 1 + g;
     const bool leader = t == 32 * (g & 3);
+    const bool leader_warp = warp == 4 * g + (g & 3);  // issues the MMAs, converged (one lane elected)
     const uint32_t bar_m = tcx::smem_u32(&ctl->bar_m[g]);
     volatile int* flag = &ctl->flag[g];
     const uint32_t d_col = tmem + 128u * (uint32_t)g, a_col = d_col + kPACol;
@@ -467,12 +468,12 @@ __global__ void __launch_bounds__(128 * kPTcGroups, 1) k_prop_infer_tc(
     bool ok = true;
     // one layer: MMAs over K = kin from A, into D, N columns; then the group waits
     auto layer = [&](uint64_t desc, int kin, int nout) -> bool {
-        if (leader) {
+        if (leader_warp) {
             tcx::tc_fence_after();
             const uint32_t idd = tcx::idesc_bf16(nout);
             for (int kk = 0; kk < kin / 16; ++kk)
-                tcx::mma_bf16_ts(d_col, a_col + 8u * kk, desc + 16u * kk, idd, kk > 0 ? 1u : 0u);
-            tcx::mma_commit(bar_m);
+                tcx::mma_bf16_ts_warp(d_col, a_col + 8u * kk, desc + 16u * kk, idd, kk > 0 ? 1u : 0u);
+            tcx::mma_commit_warp(bar_m);
         }
         const bool got = tcx::group_wait(bar_m, ph, bar_id, flag, leader);
         ph ^= 1u;
