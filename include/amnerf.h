@@ -267,15 +267,20 @@ AMNERF_API amnerf_status amnerf_get_tree(amnerf_ctx *ctx, amnerf_node *nodes_out
 AMNERF_API amnerf_status amnerf_load_mlps(amnerf_ctx *ctx, const amnerf_mlp_desc *desc, int n_leaves,
                                const float *weights_host);
 
-/* E4M3 networks with static activation scales.  Same as amnerf_load_mlps with
- * desc->prec == AMNERF_FP8E4M3, except that every layer input is quantised with a
- * fixed per-leaf, per-layer scale a_l = act_max[leaf][l] / 448 (instead of the
- * default per-row scale max|row| / 448), folded at load time into the weight scales
- * and biases, so the network epilogue does one fused multiply-add per value.
+/* E4M3 networks with static scales.  Same as amnerf_load_mlps with
+ * desc->prec == AMNERF_FP8E4M3, except that the layer inputs are quantised with
+ * fixed scales instead of the default per-row scale max|row| / 448: the encoded
+ * input as it is (its features lie within +-448), and input channel n of hidden
+ * layer l + 1 with the per-output-channel scale of layer l,
+ * s_(l,n) = max(max_k |W_l[n,k] alpha_k|, act_max[leaf][l + 1]) / 448 (alpha_k:
+ * the scales of layer l's own input channels, 1 for layer 0; the last hidden layer
+ * without the second term).  Every scale is folded at load time into the stored
+ * weights (the next layer's columns, the head's BF16 weights) and the bias, which
+ * enters through one BF16 MMA, so the network epilogue is ReLU and the conversion.
  * act_max_host: HOST float32 [n_leaves][hidden], finite and >= 0: the largest
- * |input| of hidden layer l (l = 0: the encoded input), e.g. from
- * amnerf_calibrate_fp8; a zero entry selects scale 1.  Inputs beyond act_max
- * saturate at +-448 a_l.  Synchronous.
+ * |input| of hidden layer l (l = 0: the encoded input, not used for a scale), e.g.
+ * from amnerf_calibrate_fp8; zero entries drop their term (a scale that would be 0
+ * is 1).  Inputs beyond act_max saturate at +-448 times their scale.  Synchronous.
  * Errors: as amnerf_load_mlps; E_INVAL when desc->prec is not E4M3 or act_max is bad. */
 AMNERF_API amnerf_status amnerf_load_mlps_fp8_static(amnerf_ctx *ctx, const amnerf_mlp_desc *desc, int n_leaves,
                                           const float *weights_host, const float *act_max_host);

@@ -54,6 +54,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "amnerf_internal.h"
 #include "tc_common.cuh"
@@ -75,19 +76,20 @@ constexpr int kMaxGroups = 4;
 // one more K = 16 MMA writes the FP32 bias into the accumulator (block bb, below) in
 // the one-thread-per-row kernel; the two-threads-per-row kernel and the head have the
 // epilogue of the layer before write the FP32 bias (block bias) into the accumulator
-// columns.  The MMAs accumulate onto it.  E4M3 adds its FP32 bias in the epilogue,
-// after the scales (an E4M3 bias would lose too much).  Both run the head as one more
+// columns.  The MMAs accumulate onto it.  E4M3 with per-row scales adds its FP32
+// bias in the epilogue, after the scales (an E4M3 bias would lose too much); with
+// static scales it enters through a BF16 MMA (below).  Both run the head as one more
 // BF16 MMA of a 16-row matrix (rows 0..3 used).
-// E4M3 with static activation scales (act_max known per leaf and layer) keeps the
-// per-output-channel weight scales s_(l,n) = max|W_l[n,:]| / 448 (W stored as W / s)
-// and gives every layer input one static scale a_l = act_max_l / 448 (a_hidden = 1:
-// the head's BF16 input is in real units).  The accumulator of output n of layer l
-// is then y_n / (a_l s_(l,n)) without its bias, and the next layer's E4M3 input is
-// relu(acc * C[l][n] + B[l][n]) with C = a_l s_(l,n) / a_(l+1) and B = b_n / a_(l+1):
-// one packed FMA per pair of values in the epilogue, C in the scale block and B in
-// the bias block of the blob; enc holds 1 / a_0 (the encoding's scale).
-// BF16 also holds, for each hidden layer l >= 1, its bias as a width x 16 B operand
-// (block bb): K columns 10, 11, 12 carry the bias split into three BF16 parts
+// E4M3 with static scales (act_max known per leaf and layer; see pack_tc_leaf) folds
+// every scale into the weights: output channel n of layer l has one scale s_(l,n),
+// the next layer's E4M3 input of channel n is stored as relu(y_n) / s_(l,n) and that
+// scale is folded into the next layer's weight columns (the head's BF16 weights for
+// the last layer).  The accumulator is then (y - b) / s, the bias enters as b / s
+// through a BF16 bias MMA (block bb, one chunk per layer, against BF16 constant-1
+// columns that the kernel writes once into A columns 40..47), and the epilogue is
+// ReLU and the conversion; the encoded input is stored unscaled.
+// BF16 holds, for each hidden layer l >= 1, its bias as a width x 16 B operand
+// (block bb; E4M3 with static scales one for every layer): K columns 10, 11, 12 carry the bias split into three BF16 parts
 // (hi = bf16(b), mid = bf16(b - hi), lo = bf16(b - hi - mid); together the 24 bits
 // of an FP32 significand), the other columns zero.  Against layer-0 input columns
 // 80..95, whose columns 90..92 are constant ones and which no later layer
@@ -96,7 +98,7 @@ constexpr int kMaxGroups = 4;
 constexpr int kBiasK = 16;
 struct TcLayout {
     int width, hidden, k0, k0p, kh, khead, es;
-    size_t w0, wh, wo, sw, bias, enc, bb, stride;
+    size_t w0, wh, wo, sw, bias, bb, stride;
     __host__ __device__ TcLayout(int w, int h, int k, bool f8)
         : width(w), hidden(h), k0(k), k0p(round_up(f8 ? k : k + 1, f8 ? 32 : 16)), kh(w),
           khead(w), es(f8 ? 1 : 2) {
@@ -105,9 +107,8 @@ struct TcLayout {
         wo = wh + (size_t)(h - 1) * w * kh * es;  // head: 16 x khead BF16 (both precisions)
         sw = wo + (size_t)16 * khead * 2;
         bias = sw + (f8 ? (size_t)h * w * 4 : 0);
-        enc = bias + (size_t)h * w * 4 + 16;  // E4M3 static scales: 1 / (encoding scale)
-        bb = (enc + 16 + 127) / 128 * 128;
-        const size_t end = bb + (f8 ? 0 : (size_t)(h - 1) * w * kBiasK * 2);
+        bb = (bias + (size_t)h * w * 4 + 16 + 127) / 128 * 128;  // FP32 biases b_0.. and bo, then bb
+        const size_t end = bb + (size_t)(f8 ? h : h - 1) * w * kBiasK * 2;
         stride = (end + 127) / 128 * 128;
     }
 };
@@ -186,8 +187,9 @@ constexpr uint32_t kHeadCol = 112;
 //   ST = false: per-output-channel weight scales and a per-row activation scale: each
 //               row is quantized as q = h * 448 / max|h_row| and the next accumulator
 //               is rescaled by (max|h_row| / 448) * sw[n] before its bias is added.
-//   ST = true:  static per-layer scales folded in at packing (see TcLayout): the
-//               epilogue is ReLU and the conversion, as for BF16.
+//   ST = true:  static scales folded in at packing (see TcLayout): each layer's bias
+//               enters as one BF16 MMA and the epilogue is ReLU and the conversion,
+//               as for BF16.
 // HC > 0: the number of hidden layers fixed at compile time, so the layer loop is
 // unrolled and every layout offset is a constant (about 12 % faster on the 4 x 64
 // network); HC = 0 reads it from the arguments.  The shapes of the workloads here
@@ -258,6 +260,15 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         const uint64_t desc_wo = sdesc(w_addr + (uint32_t)lay.wo, (uint32_t)lay.khead * 16u);
         const uint64_t desc_bb = sdesc(w_addr + (uint32_t)lay.bb, (uint32_t)kBiasK * 16u);
         const uint8_t* wall = reinterpret_cast<const uint8_t*>(g.weights);
+        if constexpr (F8 && ST) {
+            // the BF16 constant-1 input columns of the bias MMAs (the K = 16 step at
+            // A columns 40..47, ones at its columns 10..12), which no E4M3 operand
+            // reaches (layer 0 fills A columns 0..23, later layers 0..W/4-1): written once
+            const uint32_t c8[8] = {0u, 0u, 0u, 0u, 0u, pack_bf16(1.0f, 1.0f), pack_bf16(1.0f, 0.0f), 0u};
+            static_assert((kOnesCol - kOnesStep) / 2 == 5, "ones at K-step columns 10..12");
+            tmem_st8(a_row + (uint32_t)(kOnesStep / 2), c8);
+            tmem_st_wait();
+        }
 
         // ---- tile schedule of this worker (one warpgroup)
         const uint32_t t_end = g.t_end == 0xffffffffu ? (uint32_t)g.stats[1] : g.t_end;
@@ -361,11 +372,8 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                     store_chunk_perm<2>(a_row, f);
                 } else {
                     static_assert(K0P == 96, "E4M3 layer-0 input is stored as 16 + 8 columns");
-                    float inv;
-                    if constexpr (ST) {  // the leaf's static encoding scale (in the weight blob)
-                        inv = *reinterpret_cast<const float*>(wbuf + lay.enc);
-                        s_a = 1.0f;
-                    } else {  // this row's own scale
+                    float inv = 1.0f;  // static scales: the features as they are
+                    if constexpr (!ST) {  // this row's own scale
                         float m = 0.0f;
 #pragma unroll
                         for (int i = 0; i < K0; ++i) m = fmaxf(m, fabsf(f[i]));
@@ -380,10 +388,9 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
 #pragma unroll
                         for (int u = 0; u < 4; u += 2) {
                             const int f0 = 4 * i + u;
-                            if (ST && f0 + 1 < K0) {
-                                const float2 pr = mul_f32x2(make_float2(f[f0], f[f0 + 1]), make_float2(inv, inv));
-                                e[u] = pr.x;
-                                e[u + 1] = pr.y;
+                            if (ST) {
+#pragma unroll
+                                for (int q = 0; q < 2; ++q) e[u + q] = f0 + q < K0 ? f[f0 + q < K0 ? f0 + q : 0] : 0.0f;
                             } else {
 #pragma unroll
                                 for (int q = 0; q < 2; ++q) {
@@ -430,9 +437,15 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                                : desc_wh + (uint64_t)(((size_t)(l - 1) * W * lay.kh * lay.es) >> 4);
                     if constexpr (F8) {
                         const uint32_t idd = idesc_e4m3(W);
-                        // every E4M3 layer starts from zero (scales and bias in the epilogue)
+                        // static scales: the layer's bias in accumulator units first (a BF16
+                        // MMA of the constant-1 columns against its three-part operand),
+                        // then the E4M3 steps accumulate onto it; per-row scales: every
+                        // layer starts from zero (scales and bias in the epilogue)
+                        if constexpr (ST)
+                            mma_bf16_ts_warp(d_col, a_col + (uint32_t)(kOnesStep / 2),
+                                             desc_bb + (uint64_t)(((size_t)l * W * kBiasK * 2) >> 4), idesc_bf16(W), 0u);
                         for (int kk = 0; kk < kin / KI; ++kk)
-                            mma_e4m3_ts_warp(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, kk > 0 ? 1u : 0u);
+                            mma_e4m3_ts_warp(d_col, a_col + 8u * kk, b_desc + 16u * kk, idd, (ST || kk > 0) ? 1u : 0u);
                     } else {
                         const uint32_t idd = idesc_bf16(W);
                         // layer 0 starts from zero (its bias is folded in); a later layer
@@ -495,23 +508,14 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 }
                 // pre-activation of 4 consecutive columns c0..c0+3 of this row
                 auto pre4 = [&](const float* v, int c0, float2& p01, float2& p23) {
-                    if constexpr (F8) {
-                        if constexpr (ST) {
-                            // per-output-channel weight scale and the next input's static
-                            // scale in C, the bias in B: one packed FMA per pair
-                            const float4 cc = *reinterpret_cast<const float4*>(sw + c0);
-                            const float4 bb = *reinterpret_cast<const float4*>(b + c0);
-                            p01 = fma2v(make_float2(v[0], v[1]), make_float2(cc.x, cc.y), make_float2(bb.x, bb.y));
-                            p23 = fma2v(make_float2(v[2], v[3]), make_float2(cc.z, cc.w), make_float2(bb.z, bb.w));
-                        } else {
-                            const float4 bb = *reinterpret_cast<const float4*>(b + c0);
-                            const float4 ss = *reinterpret_cast<const float4*>(sw + c0);
-                            p01 = fma_f32x2(s_a, mul_f32x2(make_float2(v[0], v[1]), make_float2(ss.x, ss.y)),
-                                            make_float2(bb.x, bb.y));
-                            p23 = fma_f32x2(s_a, mul_f32x2(make_float2(v[2], v[3]), make_float2(ss.z, ss.w)),
-                                            make_float2(bb.z, bb.w));
-                        }
-                    } else {  // the bias is already in the accumulator
+                    if constexpr (F8 && !ST) {
+                        const float4 bb = *reinterpret_cast<const float4*>(b + c0);
+                        const float4 ss = *reinterpret_cast<const float4*>(sw + c0);
+                        p01 = fma_f32x2(s_a, mul_f32x2(make_float2(v[0], v[1]), make_float2(ss.x, ss.y)),
+                                        make_float2(bb.x, bb.y));
+                        p23 = fma_f32x2(s_a, mul_f32x2(make_float2(v[2], v[3]), make_float2(ss.z, ss.w)),
+                                        make_float2(bb.z, bb.w));
+                    } else {  // the bias is already in the accumulator, the scales in the weights
                         p01 = make_float2(v[0], v[1]);
                         p23 = make_float2(v[2], v[3]);
                     }
@@ -534,20 +538,14 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                             tmem_st16(a_row + 16u * h, pk);
                         }
                     } else if constexpr (ST) {
-                        // relu(acc C + B) is the next layer's E4M3 input; the row is read
-                        // in 32-column halves (the scales and biases take registers too)
+                        // relu(acc) is the next layer's E4M3 input (its channel scales are
+                        // this layer's output-channel scales, folded into the next weights)
+                        float vr[W];
+                        tmem_ld_row<W>(d_row, vr);
                         uint32_t pk[W / 4];
 #pragma unroll
-                        for (int h = 0; h < W / 32; ++h) {
-                            float v[32];
-                            tmem_ld32(d_row + 32u * h, v);
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) {
-                                float2 p01, p23;
-                                pre4(v + 4 * c, 32 * h + 4 * c, p01, p23);
-                                pk[8 * h + c] = pack_relu_e4m3x4(p01.x, p01.y, p23.x, p23.y);
-                            }
-                        }
+                        for (int c = 0; c < W / 4; ++c)
+                            pk[c] = pack_relu_e4m3x4(vr[4 * c], vr[4 * c + 1], vr[4 * c + 2], vr[4 * c + 3]);
                         if constexpr (W / 4 == 16) tmem_st16(a_row, pk);
                         else tmem_st8(a_row, pk);
                     } else {
@@ -604,7 +602,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                             }
                             tmem_st16(d_row + 16u * h, pk);
                         }
-                    } else {  // the pre-activation needs the E4M3 scales and the bias
+                    } else {  // E4M3: per-row scales need the channel scales and the bias
 #pragma unroll
                         for (int h = 0; h < W / 32; ++h) {
                             float v[32];
@@ -1140,78 +1138,91 @@ void pack_tc_leaf(const float* src, uint8_t* dst, int width, int hidden, int k0,
     const float* w = src;
     float* bias = reinterpret_cast<float*>(dst + lay.bias);
     float* sw = reinterpret_cast<float*>(dst + lay.sw);
-    // E4M3: per-output-channel weight scales s = max|W_row| / 448 (1 for a zero row).
-    // Static activation scales: a_l = act_max_l / 448 (1 when act_max_l is 0) is the
-    // scale of layer l's E4M3 input; the head's input is BF16 in real units (a = 1).
-    // The epilogue of layer l computes relu(acc C + B) with C = a_l s / a_(l+1) (the
-    // scale block) and B = b / a_(l+1) (the bias block).
-    auto act_scale = [&](int l) { return l < hidden && act_max[l] > 0.0f ? act_max[l] / 448.0f : 1.0f; };
+    auto bf_value = [](uint16_t b) {
+        const uint32_t u = (uint32_t)b << 16;
+        float f;
+        std::memcpy(&f, &u, 4);
+        return f;
+    };
+    // the bias b of output n as three BF16 parts in bias operand `chunk` (block bb)
+    auto put_bias_operand = [&](int chunk, int n, float b) {
+        uint8_t* base = dst + lay.bb + (size_t)chunk * width * kBiasK * 2;
+        const uint16_t hi = f2bf(b);
+        const float r1 = b - bf_value(hi);  // exact: b and hi share their leading bits
+        const uint16_t mid = f2bf(r1);
+        const uint16_t lo = f2bf(r1 - bf_value(mid));
+        const uint16_t parts[3] = {hi, mid, lo};
+        for (int i = 0; i < 3; ++i) std::memcpy(base + cm_offset(n, kOnesCol - kOnesStep + i, kBiasK), &parts[i], 2);
+    };
+    // E4M3, per-row activation scales: per-output-channel weight scales
+    // s = max|W_row| / 448 (1 for a zero row); the epilogue rescales and adds the bias.
+    // E4M3, static scales: layer l's E4M3 input q has one scale per input channel,
+    // alpha_k (layer 0: 1, the encoded features are stored as they are: within +-448,
+    // and E4M3's absolute error is smallest on the small ones).
+    // Output channel n gets s_n = max(max_k |W[n,k] alpha_k|, act_max_(l+1)) / 448 (the
+    // second term below the last hidden layer; 1 when both are 0), so that the stored
+    // weights W alpha / s and the next layer's input relu(y) / s both stay within
+    // +-448.  The accumulator is then (y - b) / s: the bias enters as b / s (a BF16
+    // operand), the epilogue is relu and the conversion, the next layer's channel
+    // scales are these s, and the head's BF16 weights take the last layer's s.
+    std::vector<float> alpha((size_t)(k0 > width ? k0 : width), 1.0f), s_out((size_t)width);
     int kin = k0;
     for (int l = 0; l < hidden; ++l) {
         const int K = l == 0 ? lay.k0p : lay.kh;
         uint8_t* base = dst + (l == 0 ? lay.w0 : lay.wh + (size_t)(l - 1) * width * lay.kh * lay.es);
-        const float a_in = stat ? act_scale(l) : 1.0f, a_out = stat ? act_scale(l + 1) : 1.0f;
+        const float* bl = w + (size_t)width * kin;  // this layer's biases
         for (int n = 0; n < width; ++n) {
             const float* row = w + (size_t)n * kin;
             if (f8) {
                 float m = 0.0f;
-                for (int k = 0; k < kin; ++k) m = std::fmax(m, std::fabs(row[k]));
-                const float s = m > 0.0f ? m / 448.0f : 1.0f;
-                sw[(size_t)l * width + n] = stat ? a_in * s / a_out : s;
-                for (int k = 0; k < kin; ++k) base[cm_offset8(n, k, K)] = f2e4m3(row[k] / s);
+                for (int k = 0; k < kin; ++k) m = std::fmax(m, std::fabs(row[k] * alpha[k]));
+                float sc;
+                if (stat) {
+                    const float amax_next = l + 1 < hidden ? act_max[l + 1] : 0.0f;
+                    sc = std::fmax(m, amax_next) / 448.0f;
+                    if (!(sc > 0.0f)) sc = 1.0f;
+                } else {
+                    sc = m > 0.0f ? m / 448.0f : 1.0f;
+                }
+                s_out[n] = sc;
+                sw[(size_t)l * width + n] = sc;
+                for (int k = 0; k < kin; ++k) base[cm_offset8(n, k, K)] = f2e4m3(row[k] * alpha[k] / sc);
+                bias[(size_t)l * width + n] = stat ? bl[n] / sc : bl[n];
+                if (stat) put_bias_operand(l, n, bl[n] / sc);
             } else if (l == 0) {
                 // layer 0 in the kernels' column order (kperm), its bias at the bias input
                 for (int k = 0; k < K; ++k) {
                     const int c = kperm(k);
-                    const float v = c >= 0 ? row[c] : (c == -1 ? w[(size_t)width * kin + n] : 0.0f);
+                    const float v = c >= 0 ? row[c] : (c == -1 ? bl[n] : 0.0f);
                     const uint16_t b = f2bf(v);
                     std::memcpy(base + cm_offset(n, k, K), &b, 2);
                 }
+                bias[n] = bl[n];
             } else {
                 for (int k = 0; k < kin; ++k) {
                     const uint16_t b = f2bf(row[k]);
                     std::memcpy(base + cm_offset(n, k, K), &b, 2);
                 }
+                bias[(size_t)l * width + n] = bl[n];
+                put_bias_operand(l - 1, n, bl[n]);  // hidden layers 1.. : block bb, chunk l - 1
             }
         }
-        w += (size_t)width * kin;
-        for (int n = 0; n < width; ++n) bias[(size_t)l * width + n] = w[n] / a_out;
-        w += width;
+        if (stat)
+            for (int n = 0; n < width; ++n) alpha[n] = s_out[n];
+        w += (size_t)width * kin + width;
         kin = width;
     }
-    if (stat) reinterpret_cast<float*>(dst + lay.enc)[0] = 1.0f / act_scale(0);
     {  // head: rows 0..3 of a 16 x khead BF16 matrix (its bias stays FP32)
         uint8_t* hb = dst + lay.wo;
         for (int n = 0; n < 4; ++n) {
             for (int k = 0; k < width; ++k) {
-                const uint16_t b = f2bf(w[(size_t)n * width + k]);
+                const uint16_t b = f2bf(w[(size_t)n * width + k] * (stat ? alpha[k] : 1.0f));
                 std::memcpy(hb + cm_offset(n, k, lay.khead), &b, 2);
             }
         }
     }
     w += 4 * width;
     for (int n = 0; n < 4; ++n) bias[(size_t)hidden * width + n] = w[n];
-    if (!f8) {  // hidden layers 1.. : the bias as a three-part BF16 operand (block bb)
-        auto bf_value = [](uint16_t b) {
-            const uint32_t u = (uint32_t)b << 16;
-            float f;
-            std::memcpy(&f, &u, 4);
-            return f;
-        };
-        for (int l = 1; l < hidden; ++l) {
-            uint8_t* base = dst + lay.bb + (size_t)(l - 1) * width * kBiasK * 2;
-            for (int n = 0; n < width; ++n) {
-                const float b = bias[(size_t)l * width + n];
-                const uint16_t hi = f2bf(b);
-                const float r1 = b - bf_value(hi);  // exact: b and hi share their leading bits
-                const uint16_t mid = f2bf(r1);
-                const uint16_t lo = f2bf(r1 - bf_value(mid));
-                const uint16_t parts[3] = {hi, mid, lo};
-                for (int i = 0; i < 3; ++i)
-                    std::memcpy(base + cm_offset(n, kOnesCol - kOnesStep + i, kBiasK), &parts[i], 2);
-            }
-        }
-    }
 }
 
 cudaError_t launch_wait_selftest(cudaStream_t s, unsigned long long limit, int* err) {

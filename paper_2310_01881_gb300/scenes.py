@@ -276,6 +276,25 @@ def xavier_weights(seed: int, leaf_density: np.ndarray, width: int, hidden: int,
     return out.reshape(-1)
 
 
+def with_biases(params: np.ndarray, seed: int, width: int, hidden: int, lx: int, ld: int,
+                scale: float = 0.5) -> np.ndarray:
+    """A copy of per-leaf MLP parameters (the xavier_weights layout) with every bias
+    b_l and the head's b_o drawn from U[-scale, scale] (added to the density bias
+    b_o[0]), one PCG64 stream in leaf, layer order: networks whose every layer has a
+    nonzero bias."""
+    rng = np.random.default_rng([seed, 0xB1A5])
+    k0 = mlp_input_width(lx, ld)
+    per = params_per_leaf(width, hidden, lx, ld)
+    out = np.array(params, dtype=np.float32).reshape(-1, per).copy()
+    for leaf in range(out.shape[0]):
+        off = 0
+        for fi, fo in [(k0, width)] + [(width, width)] * (hidden - 1) + [(width, 4)]:
+            off += fi * fo
+            out[leaf, off:off + fo] += rng.uniform(-scale, scale, size=fo).astype(np.float32)
+            off += fo
+    return out.reshape(-1)
+
+
 PROPOSAL_PARAMS = 32 * 90 + 32 + 32 * 32 + 32 + 65 * 32 + 65
 
 
