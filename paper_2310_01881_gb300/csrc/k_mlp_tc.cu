@@ -328,6 +328,18 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         float2 xi = make_float2(0.f, 0.f);
         float ro[3] = {0.f, 0.f, 0.f}, rd[3] = {0.f, 0.f, 0.f};
         crossing_data(g, id, xi, ro, rd);
+        // the looked-up leaf's tile range and crossing range, kept in registers: they
+        // change only at leaf changes, so a tile's lookup is one load (its crossing id)
+        // instead of a chain of three (the small tables leave L1 under the streaming
+        // loads of the intervals and rays)
+        uint32_t lk_t0 = 0u, lk_t1 = 0u, lk_x0 = 0u, lk_x1 = 0u;
+        auto leaf_ranges = [&](int lf) {
+            lk_t0 = __ldg(g.tile_off + lf);
+            lk_t1 = __ldg(g.tile_off + lf + 1);
+            lk_x0 = __ldg(g.offsets + lf);
+            lk_x1 = __ldg(g.offsets + lf + 1);
+        };
+        if (t_first < t_stop) leaf_ranges(leaf);
 
         for (uint32_t t = t_first; t < t_stop && ok;) {
             if (leaf != cur) {
@@ -464,12 +476,16 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 auto next_lookup = [&](uint32_t tn) {
                     t_next = tn;
                     if (t_next < t_stop) {
-                        if (t_next - t <= 8u) {
-                            while (__ldg(g.tile_off + leaf_n + 1) <= t_next) ++leaf_n;
-                        } else {
-                            leaf_n = leaf_of_tile(g.tile_off, g.n_leaves, t_next);
+                        if (t_next >= lk_t1 || t_next < lk_t0) {  // another leaf (rare)
+                            if (t_next - t <= 8u && t_next >= lk_t1) {
+                                while (__ldg(g.tile_off + leaf_n + 1) <= t_next) ++leaf_n;
+                            } else {
+                                leaf_n = leaf_of_tile(g.tile_off, g.n_leaves, t_next);
+                            }
+                            leaf_ranges(leaf_n);
                         }
-                        id_n = row_crossing(g, leaf_n, t_next, ci);
+                        const uint32_t c = lk_x0 + (t_next - lk_t0) * (uint32_t)(kTileRows >> g.lg_steps) + (uint32_t)ci;
+                        id_n = c < lk_x1 ? __ldg(g.order + c) : 0xffffffffu;
                     }
                 };
                 const bool dyn = g.schedule == kSchedDynamic;
