@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
                 // tile already, so its leaf and crossing id are looked up before the layer-0
                 // wait; its interval and ray at layer l_xd; the previous tile's outputs are
                 // stored at layer l_sh.
-                const int l_xd = hidden > 2 ? 2 : hidden - 1;
+                const int l_xd = hidden > 1 ? 1 : 0;
                 const int l_sh = hidden > 3 ? 3 : hidden - 1;
                 if (!dyn && l == 0) next_lookup(t + t_step);
                 if (!dyn && l > 0 && l == l_xd) crossing_data(g, id_n, xi, ro, rd);
