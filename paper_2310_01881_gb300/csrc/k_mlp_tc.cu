@@ -15,10 +15,11 @@
 //                                      bulk-copied (TMA engine) once per leaf change
 //   D (128 x N, FP32)               -- accumulator in TMEM
 //
-// Measured on GB300, an SM retires one 128 x 64 x 16 MMA about every 50 cycles
-// whichever warp issues it, so these small layers are bound by MMA issue and by the
-// latency of the per-layer chain; keeping A in TMEM removes the shared-memory
-// activation stores and proxy fences from that chain.
+// Measured on GB300, the tensor pipe retires one 128 x 64 x 16 MMA about every 34
+// cycles when several warps issue, and a chain of five dependent ones takes about
+// 300 cycles from issue to completion, so these small layers are bound by the
+// latency of each tile's per-layer chain; keeping A in TMEM removes the
+// shared-memory activation stores and proxy fences from that chain.
 //
 // Thread r of a warpgroup owns sample row r: it rebuilds the sample, encodes
 // gamma(x) ++ gamma(d) and writes it into its TMEM lane (tcgen05.st 32x32b); after
@@ -28,13 +29,14 @@
 // writes every later layer's FP32 bias into its accumulator with one more K = 16 MMA
 // (three constant-1 input columns of layer 0, still in TMEM, against the bias split
 // into three BF16 parts), so the epilogue is ReLU with the conversion
-// (cvt.rn.relu.bf16x2) and nothing else; E4M3 applies its channel scales and bias
-// with one packed FMA per pair first.  The 4-wide head is one
-// more BF16 MMA (16 rows, 4 used) on relu(h) written into the group's D columns; it
-// runs while the group encodes its next tile.  Its accumulator sits in 16 TMEM
-// columns that no layer writes, so its outputs (sigma = softplus, rgb = sigmoid) are
-// read with the next tile's layer-0 accumulator and activated and stored while that
-// tile's layer-1 MMAs run.
+// (cvt.rn.relu.bf16x2) and nothing else.  E4M3 with static scales does the same
+// (its scales folded into the weights, its bias through a BF16 MMA); with per-row
+// scales it applies its channel scales and bias with one packed FMA per pair first.
+// The 4-wide head is one more BF16 MMA (16 rows, 4 used) on relu(h) written into the
+// group's D columns; it runs while the group encodes its next tile.  Its accumulator
+// sits in 16 TMEM columns that no layer writes, so its outputs (sigma = softplus,
+// rgb = sigmoid) are read with the next tile's layer-0 accumulator and activated and
+// stored while that tile's last layer's MMAs run.
 //
 // Several warpgroups per CTA work on different tiles, so one group's epilogue
 // overlaps another's MMA.  Each group's leader warp (warp grp % 4 of the group, so
@@ -295,13 +297,14 @@ __global__ void __launch_bounds__(128 * kMaxGroups, 1) k_mlp_tc(MlpArgs g, int n
         int cur = -1;
         bool ok = true;
         // The head MMA of a tile runs while the group encodes its next tile.  Before that
-        // tile's first MMA only the leader waits for it (the head reads D, which layer 0
-        // overwrites); its result, in columns no layer writes, is read with the layer-0
-        // accumulator and activated and stored while the layer-1 MMAs run.
+        // tile's first MMA only the leader warp waits for it (the head reads D, which
+        // layer 0 overwrites; the other warps see it complete through the layer-0
+        // commit); its result, in columns no layer writes, is read with the layer-0
+        // accumulator and activated and stored while a later layer's MMAs run.
         bool pending = false;   // head MMA issued, its completion not yet consumed
         bool have_out = false;  // a head result in TMEM waits to be read
         bool zpend = false;     // a head result in registers waits to be stored
-        bool head_bad = false;  // the leader's wait for a head MMA ran out
+        bool head_bad = false;  // the leader warp's wait for a head MMA ran out
         uint64_t slot_prev = ~0ull, slot_z = ~0ull;
         uint32_t zr[4] = {0u, 0u, 0u, 0u};
         auto store_head = [&]() {
