@@ -91,3 +91,34 @@ def test_tensor_core_paths_with_biases(R, scene, prec, width_split, floor):
     assert np.all(np.isfinite(rgb))
     assert psnr >= floor
     assert psnr > _psnr(rgb, ref0["rgb"]) + 10.0
+
+
+@pytest.mark.parametrize("width,hidden", [(64, 1), (64, 3), (32, 5), (64, 4)])
+@pytest.mark.parametrize("prec", ["bf16", "fp8s"])
+def test_bias_paths_across_network_shapes(R, width, hidden, prec):
+    """The bias operands are per hidden layer (block bb, chunk l - 1 for BF16, l for
+    E4M3 static): shapes outside the specialised ones run the generic instantiation,
+    one hidden layer has no BF16 bias MMA at all.  Each against the FP64 oracle."""
+    import dataclasses
+    cfg = dataclasses.replace(S.CONFIGS["c1"], width=width, hidden=hidden)
+    grid = S.density_grid(S.scene_for(cfg.scene, 4), cfg.G)
+    tree = O.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac)
+    assert R.build_tree(grid, cfg.max_depth, cfg.leaf_mass_frac) == tree.n_leaves
+    P0 = S.xavier_weights(4, S.leaf_mean_density(grid, tree.leaf_cells()), width, hidden, cfg.lx, cfg.ld)
+    P = S.with_biases(P0, 4, width, hidden, cfg.lx, cfg.ld)
+    if prec == "fp8s":
+        R.load_mlps(P, width, hidden, cfg.lx, cfg.ld, "fp32")
+        oc, dc = S.view_rays(cfg, 4, 7, 64, 64)
+        amax = R.calibrate_fp8(_dev(oc), _dev(dc), hidden, steps=cfg.steps, cap=cfg.cap)
+        R.load_mlps(P, width, hidden, cfg.lx, cfg.ld, act_max=amax)
+    else:
+        R.load_mlps(P, width, hidden, cfg.lx, cfg.ld, prec)
+    o, d = S.view_rays(cfg, 4, 0)
+    rgb = R.render(_dev(o), _dev(d), steps=cfg.steps, cap=cfg.cap)[0].cpu().numpy()
+    ref = O.render(tree, P, width, hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=0, threads=8)
+    ref0 = O.render(tree, P0, width, hidden, cfg.lx, cfg.ld, o, d, cfg.steps, cfg.cap, mode=0, threads=8)
+    psnr = _psnr(rgb, ref["rgb"])
+    print(f"{prec} {hidden} x {width} with biases: PSNR {psnr:.2f} dB (bias-free image {_psnr(ref['rgb'], ref0['rgb']):.2f} dB away)")
+    assert np.all(np.isfinite(rgb))
+    assert psnr >= (45.0 if prec == "bf16" else 30.0)
+    assert psnr > _psnr(rgb, ref0["rgb"]) + 10.0
