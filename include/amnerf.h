@@ -13,7 +13,7 @@
  *   4. network     frequency encoding + per-leaf MLP -> density and colour
  *                  (Sec. 3.1 F_Theta, Sec. 3.2 same-shaped networks);
  *   5. composite   front-to-back NeRF quadrature with early ray termination
- *                  (Sec. 3.1 "traditional volumetric rendering").
+ *                  (Sec. 3.1: classic volume rendering).
  * The tree comes from a guidance density grid (Sec. 3.3-3.4, BuildKDTree).
  *
  * Conventions
@@ -115,8 +115,8 @@ typedef struct {
     int use_proposal;
     float coverage;   /* e.g. 0.99 */
     int max_bins;     /* in [1, 64], e.g. 16 */
-    /* Sample placement (Sec. 3.5: "uniform random ... samples are filled within each
-     * intersection interval"): 0 = the midpoint of each of the steps_per_leaf equal
+    /* Sample placement (Sec. 3.5: the samples of an interval may be placed at random
+     * within it): 0 = the midpoint of each of the steps_per_leaf equal
      * strata of a crossing; otherwise the seed of a stratified jitter, one uniform
      * point per stratum, t_j = t_in + (j + u_j) delta.  u_j = (splitmix64 finaliser
      * of key + 0x9e3779b97f4a7c15 * (k * steps_per_leaf + j + 1)) >> 40, over 2^24,

@@ -25,14 +25,14 @@
  *   sampling   Sec. 3.5, Algorithm 1 (Sampling) and Fig. "prop": every interval is
  *              normalised and gets the same number of samples, stored per ray at
  *              ray * max_cell_count + j; placed at stratum midpoints, or (the paper's
- *              "uniform random" placement) at one uniform point per stratum drawn
+ *              random placement within an interval) at one uniform point per stratum drawn
  *              from a counter-based generator keyed by the ray (see or_jitter_u).
  *   grouping   Sec. 3.5 and Fig. "parallel": samples sorted by node id so that each
  *              node's network runs as one batch.
  *   network    Sec. 3.1 (F_Theta(x, d) -> (c, sigma)), Sec. 3.2 and 4.1 (one small
- *              same-shaped MLP per node), frequency positional encoding (Fig.
+ *              same-shaped MLP per node), sinusoidal positional encoding (Fig.
  *              "complex" caption).
- *   composite  Sec. 3.1 ("traditional volumetric rendering"): NeRF quadrature with
+ *   composite  Sec. 3.1 (classic volume rendering): NeRF quadrature with
  *              early ray termination.
  *   proposal   not in the paper (related work, Sec. 2.1: sampling networks);
  *              defined in the proposal section of this file.
@@ -218,7 +218,7 @@ static int or_slab64(const float *box, const double o[3], const double inv[3], d
 }
 
 /* Adaptive hierarchical sampling (Sec. 3.5, Algorithm 1's HCheck; Fig. 1 (c)): the
- * paper leaves HCheck undefined beyond "scene density and camera-to-scene distance".
+ * paper leaves HCheck undefined beyond naming its inputs: the scene density and the camera distance.
  * Reading: a ray's footprint grows linearly with the distance travelled, so a node
  * whose subdivision is finer than the footprint cannot be resolved and its own
  * network takes the whole crossing.  An inner node is descended (HCheck true) iff
@@ -410,8 +410,8 @@ int or_traverse(const float *box, const int *info, const float *split, int n_nod
 /* Sampling (Sec. 3.5, Algorithm 1 Sampling; Fig. "prop")                   */
 /* ======================================================================== */
 
-/* Stratified jitter (Sec. 3.5: "uniform random ... samples are filled within each
- * intersection interval"): sample j of crossing k of a ray sits at fraction u of its
+/* Stratified jitter (Sec. 3.5: the samples of an interval may be placed at random
+ * within it): sample j of crossing k of a ray sits at fraction u of its
  * stratum, u = (splitmix64 output >> 40) / 2^24 in [0, 1).  splitmix64 (Steele, Lea
  * and Flood, 2014) finalises z: z ^= z >> 30, z *= 0xbf58476d1ce4e5b9, z ^= z >> 27,
  * z *= 0x94d049bb133111eb, z ^= z >> 31.  The ray's key folds the bit patterns of its

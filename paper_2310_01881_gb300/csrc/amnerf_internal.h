@@ -26,7 +26,7 @@ constexpr int kMaxDepth = 12;
 constexpr int kStackDepth = 16;  // traversal stack (depth + 1 entries suffice)
 
 #ifdef __CUDACC__
-// ---- stratified jitter of the sample positions (Sec. 3.5, "uniform random" samples) --
+// ---- stratified jitter of the sample positions (Sec. 3.5: samples drawn at random within each interval) --
 // u = (splitmix64 finaliser of key + 0x9e3779b97f4a7c15 (k steps + j + 1)) >> 40, over
 // 2^24, for sample j of crossing k; the ray's key folds the bit patterns of (o.x, o.y),
 // (o.z, d.x), (d.y, d.z) into the seed with three finalisations.  Seed 0: u = 1/2.

@@ -2,7 +2,7 @@
 //
 // Network (Sec. 3.1 F_Theta, one small same-shaped MLP per leaf, Sec. 3.2 and 4.1):
 // input gamma_lx(x) ++ gamma_ld(d) with gamma_L(p) = [p, sin(pi 2^k p), cos(pi 2^k p)]
-// for k = 0..L-1 (frequency positional encoding, Fig. "complex"); `hidden` ReLU layers
+// for k = 0..L-1 (the sinusoidal positional encoding, Fig. "complex"); `hidden` ReLU layers
 // of `width`; head sigma = softplus(z0), rgb = sigmoid(z1..3).
 //
 // Work unit: a tile of 128 samples = 128 / steps crossings of ONE leaf (Sec. 3.5:

@@ -17,7 +17,7 @@
 // overlaps a kept depth bin [t0 + k w, t0 + (k + 1) w), w = (t1 - t0) / 64 of the
 // ray's root interval [t0, t1] (same FP32 operation order as the oracle); rays that
 // fell back keep every crossing.  With empty-space skipping (Sec. 4.1: the density
-// grid also serves empty space detection) a leaf crossing is kept only when one of
+// grid also marks the empty regions) a leaf crossing is kept only when one of
 // its samples -- placed as it would be as the ray's next kept crossing, in the
 // sampling step's FP32 order -- lies in a guidance-grid cell above the threshold;
 // skipped crossings do not count toward maxc.

@@ -215,7 +215,7 @@ def test_c2_scale_tree_and_sampled_pixels(R):
     assert st["samples_generated"] >= int(nx.sum()) * cfg.steps
 
 
-# ---- stratified jitter of the sample positions (Sec. 3.5 "uniform random" samples) ----
+# ---- stratified jitter of the sample positions (Sec. 3.5: random placement within an interval) ----
 
 @pytest.mark.parametrize("seed", [0, 3])
 def test_c1_fp32_jittered_pixels_match_fp32_oracle(R, seed):
@@ -260,7 +260,7 @@ def test_jitter_is_keyed_by_the_ray_not_its_batch_position(R, prec):
         np.testing.assert_array_equal(x[p], y)
 
 
-# ---- empty-space skipping over the guidance grid (Sec. 4.1 "empty space detection") ----
+# ---- empty-space skipping over the guidance grid (Sec. 4.1: the density grid marks empty regions) ----
 
 @pytest.mark.parametrize("seed,jitter", [(0, 0), (3, 0), (1, 9)])
 def test_c1_skipping_crossings_bit_exact_and_fp32_pixels(R, seed, jitter):

@@ -311,7 +311,7 @@ def test_splitmix64_finaliser_matches_published_sequence():
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_jittered_samples_stay_in_their_strata_and_are_uniform(mode, c1_scene):
-    """Sec. 3.5 'uniform random' placement: one sample per stratum, uniform within it."""
+    """Sec. 3.5 random placement: one sample per stratum, uniform within it."""
     cfg, _, tree = c1_scene
     o, d = _camera_rays(800, 67)
     maxc = cfg.cap // cfg.steps
@@ -358,7 +358,7 @@ def test_jitter_is_keyed_by_the_ray_not_its_batch_position(c1_scene):
 
 
 # ----------------------------------------------------------------------------------
-# empty-space skipping over the guidance grid (Sec. 4.1 "empty space detection")
+# empty-space skipping over the guidance grid (Sec. 4.1: the density grid marks empty regions)
 # ----------------------------------------------------------------------------------
 
 def _brute_skip(tree, grid, thr, o, d, maxc, steps, jitter):
