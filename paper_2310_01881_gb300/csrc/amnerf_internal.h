@@ -100,6 +100,9 @@ cudaError_t launch_scatter_wave(cudaStream_t s, bool count, const uint8_t* n_x, 
 // Kernel attributes of the grouping kernels (their shared memory grows with the number
 // of networks, up to kMaxNets); call once per device before a render.
 cudaError_t prepare_group();
+// Kernel attributes of the traversal (its shared memory holds a histogram over up to
+// kMaxNets networks and the stack of pending far children); call once per device.
+cudaError_t prepare_traverse();
 // Crossings given by the caller instead of the traversal (render from crossings): copied
 // into the crossing list, counted per network; bad ids / counts set kDevErrBounds.
 cudaError_t launch_load_crossings(cudaStream_t s, const uint8_t* n_x_in, const uint16_t* leaf_in, const float* t_in,

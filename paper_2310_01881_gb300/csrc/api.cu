@@ -267,6 +267,7 @@ amnerf_status amnerf_create(amnerf_ctx** out, int device, void* cuda_stream) {
     cudaError_t e;
     if ((e = cudaSetDevice(device)) != cudaSuccess ||
         (e = prepare_group()) != cudaSuccess ||
+        (e = prepare_traverse()) != cudaSuccess ||
         (e = cudaMalloc((void**)&ctx->d_counts, sizeof(uint32_t) * kMaxNets)) != cudaSuccess ||
         (e = cudaMalloc((void**)&ctx->d_offsets, sizeof(uint32_t) * (kMaxNets + 1))) != cudaSuccess ||
         (e = cudaMalloc((void**)&ctx->d_tile_off, sizeof(uint32_t) * (kMaxNets + 1))) != cudaSuccess ||

@@ -2,17 +2,37 @@
 // (Sec. 3.5, Algorithm 1 "Traverse"; sampling of Algorithm 1 "Sampling" is defined
 // on the emitted crossings and is evaluated where the samples are consumed).
 //
-// One thread per ray walks the tree front to back (near child first: the child on
-// the origin's side of the split plane; far children wait on a short register
-// stack).  Every visited node is tested with the slab method in a fixed FP32
-// operation order -- per axis
+// One thread per ray walks the tree front to back (near child first; a far child that
+// the ray also crosses waits on a short stack in shared memory).  The crossing
+// interval of a box is the slab test in a fixed FP32 operation order -- per axis
 // t0 = (lo - o) * inv, t1 = (hi - o) * inv with inv = 1 / d correctly rounded, no
-// fused multiply-add, NaN-ignoring min/max, entry clamped at 0 -- so the crossing
-// list is reproducible bit for bit.  A node whose interval is empty is pruned (its
-// leaves' intervals are subsets).  A leaf with exit > entry is emitted as
-// (entry, exit) at crossing slot ray * maxc + k and counted in a per-CTA shared-memory
-// histogram that is flushed to the per-leaf totals with one atomic per touched leaf.
-// Traversal stops after maxc crossings (whole crossings are kept under the cap).
+// fused multiply-add, NaN-ignoring min/max, entry = max over the axes of min(t0, t1)
+// clamped at 0, exit = min of max(t0, t1) -- so the crossing list is reproducible bit
+// for bit.  The walk evaluates it once, at the root, and then carries (entry, exit)
+// down.  A child's box differs from its parent's only in one face, the split plane s
+// on the split axis a, so its interval is the parent's with the axis-a pair replaced
+// by the min/max of (t(lo_a), t(s)) (left child) or (t(s), t(hi_a)) (right child).
+// Every face value t(f) = (f - o_a) * inv_a is the same rounded number wherever it is
+// computed and is monotone in f (for inv_a = +-inf it is -inf, NaN or +inf by the side
+// of o_a), so the child's axis-a entry is no smaller and its exit no larger than the
+// parent's: the max (min) over the axes is max(parent entry, child axis entry)
+// (min(parent exit, child axis exit)), the value the full slab test of the child
+// gives.  For d_a >= +0 the left child's axis-a entry is the parent's and its exit is
+// t(s), and the right child's entry is t(s) and its exit the parent's (mirrored for
+// d_a <= -0), so with ts = t(s) the child the ray meets first spans (e, min(x, ts)) and
+// the other (max(e, ts), x); a ts of NaN (d_a = 0 with o_a on the plane) leaves both
+// children empty.  Only children with exit > entry are entered or pushed (with their
+// interval), so empty boxes cost nothing, leaves need no test of their own, and an
+// inner node costs one subtraction and one multiplication.  When both children are
+// crossed, the ray meets the plane inside (e, x), after its origin, so the first child
+// is the one on the origin's side: the near child.
+// A leaf is emitted as (entry, exit) at crossing slot ray * maxc + k and counted in a
+// per-CTA shared-memory histogram that is flushed to the per-leaf totals with one
+// atomic per touched leaf.  Traversal stops after maxc crossings (whole crossings are
+// kept under the cap).  When maxc is a multiple of 8 the crossings are written in whole
+// 32-byte sectors (a group of four per store) and the network ids in 16-byte chunks,
+// each ray's row of ids written whole: a partly written sector costs the memory a read
+// of the rest of it when it leaves L2, and those scattered reads bounded the walk.
 // With the proposal sampler, a leaf crossing [t_in, t_out] is kept only when it
 // overlaps a kept depth bin [t0 + k w, t0 + (k + 1) w), w = (t1 - t0) / 64 of the
 // ray's root interval [t0, t1] (same FP32 operation order as the oracle); rays that
@@ -96,125 +116,281 @@ __device__ __forceinline__ bool crossing_occupied(const OccArgs& oc, const float
     return false;
 }
 
-// HIER: adaptive hierarchical sampling compiled in (its HCheck costs registers, so the
-// leaf-only walk is a separate instantiation).
-template <bool HIER>
-__global__ void __launch_bounds__(256) k_traverse(const float* __restrict__ ro, const float* __restrict__ rd,
-                                                  uint32_t n, const DevNode* __restrict__ nodes, int maxc,
-                                                  uint8_t* __restrict__ n_x, float2* __restrict__ xing,
-                                                  uint16_t* __restrict__ xleaf, uint32_t* __restrict__ counts,
-                                                  int n_leaves, int* __restrict__ err,
-                                                  const uint64_t* __restrict__ mask,
-                                                  const uint8_t* __restrict__ fallback, float2* __restrict__ root_out,
-                                                  const OccArgs occ, const HierArgs hier) {
-    extern __shared__ uint32_t s_cnt[];
+// Threads per traversal CTA; the stack of pending far children lives in shared memory
+// as [depth][thread] (node id and its (entry, exit)), after the per-CTA histogram.
+constexpr int kTravThreads = 256;
+constexpr int kTravStack = kMaxDepth;  // one pending far child per level at most
+
+__host__ __device__ constexpr size_t trav_hist_bytes(int n_nets) { return ((size_t)n_nets * 4 + 15) & ~(size_t)15; }
+__host__ __device__ constexpr size_t trav_smem_bytes(int n_nets) {
+    return trav_hist_bytes(n_nets) + (size_t)kTravStack * kTravThreads * (sizeof(float2) + sizeof(uint16_t));
+}
+
+// Launch-wide arguments of the walk.
+struct TravArgs {
+    const float* ro;
+    const float* rd;
+    uint32_t n;
+    const DevNode* nodes;
+    int maxc;
+    uint8_t* n_x;
+    float2* xing;
+    uint16_t* xleaf;
+    uint32_t* counts;
+    int* err;
+    const uint64_t* mask;
+    const uint8_t* fallback;
+    float2* root_out;
+    OccArgs occ;
+    HierArgs hier;
+};
+
+// Features compiled into one instantiation of the walk, so that a render keeps in
+// registers only the state its features use.
+constexpr int kFHier = 1;  // adaptive hierarchical sampling (HCheck)
+constexpr int kFMask = 2;  // proposal masks
+constexpr int kFOcc = 4;   // empty-space skipping
+constexpr int kFVec = 8;   // whole-sector stores (maxc a multiple of 8)
+
+// One ray's walk: its constants and the position of the walk.
+struct RayWalk {
+    float o[3], d[3], inv[3];
+    float r0, bw;         // proposal: root interval start, bin width
+    uint64_t kept_bins;   // proposal: kept depth bins
+    uint64_t key;         // empty-space skipping: jitter key
+    uint32_t r;
+    int nd, sp, cnt;
+    float e, x;           // interval of node nd (exit > entry)
+    bool masked;
+    // whole-sector stores: the first three crossings of the current group of four slots
+    // and the network ids of the current chunk of eight slots
+    float2 g0, g1, g2;
+    uint64_t l0, l1;
+};
+
+// Loads ray r and intersects the root; returns false when the ray misses the tree
+// (its crossing count is written then).
+template <int F>
+__device__ __forceinline__ bool walk_init(const TravArgs& t, RayWalk& w, uint32_t r) {
+    w.r = r;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        w.o[a] = __ldg(t.ro + 3 * (size_t)r + a);
+        w.d[a] = __ldg(t.rd + 3 * (size_t)r + a);
+        w.inv[a] = __frcp_rn(w.d[a]);
+    }
+    float r0 = 0.f, r1 = 0.f;
+    const float4 A = __ldg(&t.nodes[0].a);
+    const float4 B = __ldg(&t.nodes[0].b);
+    const bool hit = slab(A, B, w.o, w.inv, r0, r1);
+    if (!hit) r0 = r1 = 0.f;
+    if (t.root_out) t.root_out[r] = make_float2(r0, r1);
+    if (F & kFMask) {
+        w.masked = !__ldg(t.fallback + r);
+        w.kept_bins = w.masked ? __ldg(t.mask + r) : 0ull;
+        w.r0 = r0;
+        w.bw = __fmul_rn(__fsub_rn(r1, r0), 0.015625f);  // bin width (t1 - t0) / 64
+    }
+    if (F & kFOcc) w.key = t.occ.jitter ? jit_ray_key(t.occ.jitter, w.o, w.d) : 0ull;
+    w.nd = 0;
+    w.sp = 0;
+    w.cnt = 0;
+    w.e = r0;
+    w.x = r1;
+    if (!hit) t.n_x[r] = 0;
+    return hit;
+}
+
+__device__ __forceinline__ float sel3(int a, const float v[3]) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); }
+
+// Emits node nd as the ray's next crossing (after the proposal and empty-space
+// rules); returns false when the ray has reached maxc crossings.  kFVec: the crossings
+// are collected per group of four slots and written as one whole 32-byte sector, the
+// network ids per chunk of eight slots (16 bytes), so that no sector of the crossing
+// list is left partly written (see walk_flush).
+template <int F>
+__device__ __forceinline__ bool walk_emit(const TravArgs& t, RayWalk& w, uint32_t* s_cnt, uint32_t meta, int axis) {
+    if ((F & kFMask) && w.masked && !overlaps_kept(w.kept_bins, w.r0, w.bw, w.e, w.x)) return true;
+    if ((F & kFOcc) && !crossing_occupied(t.occ, w.o, w.d, w.key, w.e, w.x, w.cnt)) return true;
+    const uint32_t net = (!(F & kFHier) || axis < 0) ? meta >> 2 : (uint32_t)__ldg(t.hier.node_net + w.nd);
+    const size_t base = (size_t)w.r * (size_t)t.maxc;
+    if (F & kFVec) {
+        const int j = w.cnt & 3;
+        const float2 v = make_float2(w.e, w.x);
+        w.g0 = j == 0 ? v : w.g0;
+        w.g1 = j == 1 ? v : w.g1;
+        w.g2 = j == 2 ? v : w.g2;
+        if (j == 3) {
+            float4* p = reinterpret_cast<float4*>(t.xing + base + (w.cnt - 3));
+            p[0] = make_float4(w.g0.x, w.g0.y, w.g1.x, w.g1.y);
+            p[1] = make_float4(w.g2.x, w.g2.y, v.x, v.y);
+        }
+        const int k = w.cnt & 7;
+        const uint64_t bits = (uint64_t)net << (16 * (k & 3));
+        w.l0 = k == 0 ? bits : (k < 4 ? (w.l0 | bits) : w.l0);
+        w.l1 = k == 0 ? 0ull : (k >= 4 ? (w.l1 | bits) : w.l1);
+        if (k == 7)
+            *reinterpret_cast<uint4*>(t.xleaf + base + (w.cnt - 7)) =
+                make_uint4((uint32_t)w.l0, (uint32_t)(w.l0 >> 32), (uint32_t)w.l1, (uint32_t)(w.l1 >> 32));
+    } else {
+        t.xing[base + w.cnt] = make_float2(w.e, w.x);
+        t.xleaf[base + w.cnt] = (uint16_t)net;
+    }
+    atomicAdd(&s_cnt[net], 1u);
+    return ++w.cnt < t.maxc;
+}
+
+// kFVec: writes the ray's last, partly filled group and chunk, and zero chunks of
+// network ids to the end of its row: rows of ids are 16-byte aligned but share 32-byte
+// sectors with the next ray's row, so each row is written whole.  Slots at and past
+// the ray's crossing count hold no crossing.
+template <int F>
+__device__ __forceinline__ void walk_flush(const TravArgs& t, const RayWalk& w) {
+    if (!(F & kFVec) || w.cnt == 0) return;
+    const size_t base = (size_t)w.r * (size_t)t.maxc;
+    if (w.cnt & 3) {
+        float4* p = reinterpret_cast<float4*>(t.xing + base + (w.cnt & ~3));
+        p[0] = make_float4(w.g0.x, w.g0.y, w.g1.x, w.g1.y);
+        p[1] = make_float4(w.g2.x, w.g2.y, 0.f, 0.f);
+    }
+    int c = w.cnt >> 3;
+    uint4* q = reinterpret_cast<uint4*>(t.xleaf + base);
+    if (w.cnt & 7) {
+        q[c] = make_uint4((uint32_t)w.l0, (uint32_t)(w.l0 >> 32), (uint32_t)w.l1, (uint32_t)(w.l1 >> 32));
+        ++c;
+    }
+    for (; c < (t.maxc >> 3); ++c) q[c] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Moves to the children of inner node nd (split plane s on axis a).  The plane cuts
+// (e, x) at ts = (s - o_a) * inv_a: the child the ray meets first is (e, min(x, ts)),
+// the other (max(e, ts), x) -- the left child comes first for d_a >= +0, the right one
+// for d_a <= -0 -- and a ts of NaN (a ray inside the plane) crosses neither.  These are
+// the children's slab intervals (see the header).  Enters the first non-empty child
+// and pushes the other when both are; returns false when neither is.
+__device__ __forceinline__ bool walk_descend(const TravArgs& t, RayWalk& w, float2* s_ex, uint16_t* s_nd,
+                                             float split, uint32_t meta, int axis) {
+    const float oa = sel3(axis, w.o), ia = sel3(axis, w.inv);
+    const float ts = __fmul_rn(__fsub_rn(split, oa), ia);
+    const float x1 = fminf(w.x, ts);
+    const float e2 = fmaxf(w.e, ts);
+    const bool real = ts == ts;
+    const bool ok1 = real && x1 > w.e;
+    const bool ok2 = real && w.x > e2;
+    const bool neg = (__float_as_uint(ia) >> 31) != 0u;
+    const int left = w.nd + 1, right = (int)(meta >> 2);
+    const int c1 = neg ? right : left, c2 = neg ? left : right;
+    if (ok1 && ok2) {
+        if (w.sp >= kTravStack) {  // unreachable for depth <= kMaxDepth; recorded, never trapped
+            atomicCAS(t.err, 0, kDevErrStack);
+            return false;
+        }
+        s_nd[w.sp * kTravThreads] = (uint16_t)c2;
+        s_ex[w.sp * kTravThreads] = make_float2(e2, w.x);
+        ++w.sp;
+    }
+    if (ok1) {
+        w.nd = c1;
+        w.x = x1;
+    } else {
+        w.nd = c2;
+        w.e = e2;
+    }
+    return ok1 || ok2;
+}
+
+// Pops the next pending child; returns false when none is left.
+__device__ __forceinline__ bool walk_pop(RayWalk& w, const float2* s_ex, const uint16_t* s_nd) {
+    if (w.sp == 0) return false;
+    --w.sp;
+    w.nd = s_nd[w.sp * kTravThreads];
+    const float2 ex = s_ex[w.sp * kTravThreads];
+    w.e = ex.x;
+    w.x = ex.y;
+    return true;
+}
+
+// Whether node nd is emitted rather than descended: a leaf, or (kFHier) an inner node
+// whose extent along its split axis is not above lod x entry (HCheck).
+template <int F>
+__device__ __forceinline__ bool walk_stops(const TravArgs& t, const RayWalk& w, int axis) {
+    if (axis < 0) return true;
+    if (!(F & kFHier)) return false;
+    const float lo_a = __ldg(reinterpret_cast<const float*>(&t.nodes[w.nd].a) + axis);
+    const float hi_a = __ldg(reinterpret_cast<const float*>(&t.nodes[w.nd].b) + axis);
+    return !(__fsub_rn(hi_a, lo_a) > __fmul_rn(t.hier.lod, w.e));
+}
+
+// One thread per ray; each loop iteration visits one node (emits it or moves to its
+// children), then takes the next pending child when the walk below it is done.  Five
+// CTAs per SM: the whole-sector buffers fit in 48 registers (at six CTAs the spills
+// cost more than the occupancy gains).
+template <int F>
+__global__ void __launch_bounds__(kTravThreads, 5) k_traverse(const TravArgs t, int n_leaves) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_raw);
+    float2* s_ex = reinterpret_cast<float2*>(s_raw + trav_hist_bytes(n_leaves)) + threadIdx.x;
+    uint16_t* s_nd = reinterpret_cast<uint16_t*>(reinterpret_cast<float2*>(s_raw + trav_hist_bytes(n_leaves)) +
+                                                 kTravStack * kTravThreads) + threadIdx.x;
     for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) s_cnt[i] = 0u;
     __syncthreads();
-
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) {
-        float o[3], d[3], inv[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = __ldg(ro + 3 * (size_t)r + a);
-            d[a] = __ldg(rd + 3 * (size_t)r + a);
-            inv[a] = __frcp_rn(d[a]);
-        }
-        // The near child is visited next; far children wait on a stack of 16-bit node
-        // indices held in four 64-bit registers (the top entry in the low bits of st0).
-        uint64_t st0 = 0, st1 = 0, st2 = 0, st3 = 0;
-        int sp = 0;
-        int nd = 0;
-        bool have = true;  // nd is a node still to visit
-        int cnt = 0;
-        const size_t base = (size_t)r * (size_t)maxc;
-        // proposal sampler: the root interval and this ray's kept depth bins
-        float r0 = 0.f, r1 = 0.f;
-        {
-            const float4 A = __ldg(&nodes[0].a);
-            const float4 B = __ldg(&nodes[0].b);
-            if (!slab(A, B, o, inv, r0, r1)) r0 = r1 = 0.f;
-            if (root_out) root_out[r] = make_float2(r0, r1);
-        }
-        const uint64_t kept_bins = (mask && !__ldg(fallback + r)) ? __ldg(mask + r) : 0ull;
-        const bool masked = mask && !__ldg(fallback + r);
-        const float bw = __fmul_rn(__fsub_rn(r1, r0), 0.015625f);  // bin width (t1 - t0) / 64
-        const uint64_t key = (occ.grid && occ.jitter) ? jit_ray_key(occ.jitter, o, d) : 0ull;
-        while (cnt < maxc) {
-            if (!have) {
-                if (sp == 0) break;
-                nd = (int)(st0 & 0xffffu);
-                st0 = (st0 >> 16) | (st1 << 48);
-                st1 = (st1 >> 16) | (st2 << 48);
-                st2 = (st2 >> 16) | (st3 << 48);
-                st3 >>= 16;
-                --sp;
-            }
-            have = false;
-            const float4 A = __ldg(&nodes[nd].a);
-            const float4 B = __ldg(&nodes[nd].b);
-            float tin, tout;
-            if (!slab(A, B, o, inv, tin, tout)) continue;
-            const uint32_t meta = __float_as_uint(B.w);
+    RayWalk w;
+    if (r < t.n && walk_init<F>(t, w, r)) {
+        while (true) {
+            const uint32_t meta = __float_as_uint(__ldg(&t.nodes[w.nd].b.w));
             const int axis = (int)(meta & 3u) - 1;
-            // HCheck: an inner node finer than the footprint is one crossing of its own network
-            bool emit = axis < 0;
-            if (HIER && !emit) {
-                const float ext = axis == 0 ? __fsub_rn(B.x, A.x) : (axis == 1 ? __fsub_rn(B.y, A.y) : __fsub_rn(B.z, A.z));
-                emit = !(ext > __fmul_rn(hier.lod, tin));
+            bool next;
+            if (walk_stops<F>(t, w, axis)) {
+                if (!walk_emit<F>(t, w, s_cnt, meta, axis)) break;
+                next = walk_pop(w, s_ex, s_nd);
+            } else {
+                next = walk_descend(t, w, s_ex, s_nd, __ldg(&t.nodes[w.nd].a.w), meta, axis) ||
+                       walk_pop(w, s_ex, s_nd);
             }
-            if (emit) {
-                if (masked && !overlaps_kept(kept_bins, r0, bw, tin, tout)) continue;
-                if (occ.grid && !crossing_occupied(occ, o, d, key, tin, tout, cnt)) continue;
-                const uint32_t net = (!HIER || axis < 0) ? meta >> 2 : (uint32_t)__ldg(hier.node_net + nd);
-                xing[base + cnt] = make_float2(tin, tout);
-                xleaf[base + cnt] = (uint16_t)net;
-                atomicAdd(&s_cnt[net], 1u);
-                ++cnt;
-                continue;
-            }
-            const float oa = axis == 0 ? o[0] : (axis == 1 ? o[1] : o[2]);
-            const float da = axis == 0 ? d[0] : (axis == 1 ? d[1] : d[2]);
-            const bool near_left = oa < A.w || (oa == A.w && da <= 0.0f);
-            const int left = nd + 1;
-            const int right = (int)(meta >> 2);
-            if (sp + 1 > kStackDepth) {  // unreachable for depth <= 12; recorded, never trapped
-                atomicCAS(err, 0, kDevErrStack);
-                break;
-            }
-            const uint64_t far = (uint64_t)(near_left ? right : left);
-            st3 = (st3 << 16) | (st2 >> 48);
-            st2 = (st2 << 16) | (st1 >> 48);
-            st1 = (st1 << 16) | (st0 >> 48);
-            st0 = (st0 << 16) | far;
-            ++sp;
-            nd = near_left ? left : right;
-            have = true;
+            if (!next) break;
         }
-        n_x[r] = (uint8_t)cnt;
+        walk_flush<F>(t, w);
+        t.n_x[r] = (uint8_t)w.cnt;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) {
         const uint32_t c = s_cnt[i];
-        if (c) atomicAdd(&counts[i], c);
+        if (c) atomicAdd(&t.counts[i], c);
     }
 }
 
+using TravKernel = void (*)(const TravArgs, int);
+
+// The sixteen feature combinations, indexed by their flags.
+template <int... Fs>
+struct TravTable {
+    static constexpr TravKernel k[sizeof...(Fs)] = {k_traverse<Fs>...};
+};
+using Trav16 = TravTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15>;
+
 }  // namespace
+
+cudaError_t prepare_traverse() {
+    const int smem = (int)trav_smem_bytes(kMaxNets);
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < 16 && e == cudaSuccess; ++f)
+        e = cudaFuncSetAttribute(Trav16::k[f], cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
 
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
                             int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
                             int n_leaves, int* err, const uint64_t* mask, const uint8_t* fallback,
                             float2* root_out, const OccArgs& occ, const HierArgs& hier) {
     if (n == 0) return cudaSuccess;
-    const int threads = 256;
-    const unsigned blocks = (n + threads - 1) / threads;
-    const size_t smem = sizeof(uint32_t) * (size_t)n_leaves;
-    HierArgs h = hier;
-    if (!(h.lod > 0.0f)) h.node_net = nullptr;
-    auto kern = h.node_net ? k_traverse<true> : k_traverse<false>;
-    kern<<<blocks, threads, smem, s>>>(ro, rd, n, nodes, maxc, n_x, xing, xleaf, counts, n_leaves, err, mask,
-                                             fallback, root_out, occ, h);
+    if (n_leaves < 1 || n_leaves > kMaxNets) return cudaErrorInvalidValue;
+    TravArgs t{ro, rd, n, nodes, maxc, n_x, xing, xleaf, counts, err, mask, fallback, root_out, occ, hier};
+    const int f = ((hier.lod > 0.0f && hier.node_net) ? kFHier : 0) | (mask ? kFMask : 0) |
+                  (occ.grid ? kFOcc : 0) | ((maxc & 7) == 0 ? kFVec : 0);
+    const TravKernel kern = Trav16::k[f];
+    const unsigned blocks = (n + kTravThreads - 1) / kTravThreads;
+    kern<<<blocks, kTravThreads, trav_smem_bytes(n_leaves), s>>>(t, n_leaves);
     return cudaGetLastError();
 }
 
