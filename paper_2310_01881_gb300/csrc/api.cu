@@ -25,6 +25,7 @@ struct amnerf_ctx {
     // tree
     std::vector<amnerf_node> nodes;
     int n_leaves = 0;
+    int tree_depth = 0;  // depth of the deepest node (the traversal's stack size)
     DevNode* d_nodes = nullptr;
     uint16_t* d_node_net = nullptr;  // network id of every node (leaves: leaf id; inner: L + preorder rank)
     float* d_grid = nullptr;  // the guidance grid (empty-space skipping)
@@ -374,8 +375,11 @@ amnerf_status amnerf_build_tree(amnerf_ctx* ctx, const float* grid_host, int G, 
         ctx->grid_lo[a] = (float)bbox[a];
         ctx->grid_sc[a] = (float)((double)G / (bbox[3 + a] - bbox[a]));
     }
+    int depth = 0;
+    for (const amnerf_node& s : nodes) depth = std::max(depth, (int)s.depth);
     ctx->nodes.swap(nodes);
     ctx->n_leaves = nl;
+    ctx->tree_depth = depth;
     ctx->mlp_loaded = false;
     dfree(ctx->d_weights);
     if (n_leaves_out) *n_leaves_out = nl;
@@ -542,7 +546,7 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
            "crossing load launch");
     } else {
         CK(launch_traverse(s, ro, rd, nn, ctx->d_nodes, maxc, ctx->d_nx, ctx->d_xing, ctx->d_xleaf, ctx->d_counts, L,
-                           ctx->d_err, mask, fallback, root_out, occ, hier),
+                           ctx->d_err, mask, fallback, root_out, occ, hier, ctx->tree_depth),
            "traverse launch");
     }
     if (ctx->timing) cudaEventRecord(ctx->ev[1], s);

@@ -116,14 +116,21 @@ __device__ __forceinline__ bool crossing_occupied(const OccArgs& oc, const float
     return false;
 }
 
-// Threads per traversal CTA; the stack of pending far children lives in shared memory
-// as [depth][thread] (node id and its (entry, exit)), after the per-CTA histogram.
+// Threads per traversal CTA.  Shared memory, in this order: the per-CTA histogram;
+// with whole-sector stores, each thread's current group of four crossings
+// ([slot][thread] float2) and chunk of eight network ids ([slot][thread] uint16); the
+// stack of pending far children as [level][thread] (the (entry, exit) pairs, then the
+// node ids).  The stack holds one entry per level of the tree at most (a far child is
+// pushed only by an inner node on the current path), so it is sized by the tree's depth.
 constexpr int kTravThreads = 256;
-constexpr int kTravStack = kMaxDepth;  // one pending far child per level at most
 
 __host__ __device__ constexpr size_t trav_hist_bytes(int n_nets) { return ((size_t)n_nets * 4 + 15) & ~(size_t)15; }
-__host__ __device__ constexpr size_t trav_smem_bytes(int n_nets) {
-    return trav_hist_bytes(n_nets) + (size_t)kTravStack * kTravThreads * (sizeof(float2) + sizeof(uint16_t));
+__host__ __device__ constexpr size_t trav_stage_bytes(bool vec) {
+    return vec ? (size_t)kTravThreads * (4 * sizeof(float2) + 8 * sizeof(uint16_t)) : 0;
+}
+__host__ __device__ constexpr size_t trav_smem_bytes(int n_nets, int depth, bool vec) {
+    return trav_hist_bytes(n_nets) + trav_stage_bytes(vec) +
+           (size_t)depth * kTravThreads * (sizeof(float2) + sizeof(uint16_t));
 }
 
 // Launch-wide arguments of the walk.
@@ -143,6 +150,7 @@ struct TravArgs {
     float2* root_out;
     OccArgs occ;
     HierArgs hier;
+    int depth;  // stack entries per thread: the tree's depth
 };
 
 // Features compiled into one instantiation of the walk, so that a render keeps in
@@ -162,10 +170,15 @@ struct RayWalk {
     int nd, sp, cnt;
     float e, x;           // interval of node nd (exit > entry)
     bool masked;
-    // whole-sector stores: the first three crossings of the current group of four slots
-    // and the network ids of the current chunk of eight slots
-    float2 g0, g1, g2;
-    uint64_t l0, l1;
+};
+
+// This thread's columns of the shared-memory areas.
+struct TravSmem {
+    uint32_t* cnt;   // the CTA's histogram
+    float2* grp;     // group of four crossings, [slot * kTravThreads]
+    uint16_t* chk;   // chunk of eight network ids, [slot * kTravThreads]
+    float2* ex;      // pending (entry, exit), [level * kTravThreads]
+    uint16_t* nd;    // pending node ids, [level * kTravThreads]
 };
 
 // Loads ray r and intersects the root; returns false when the ray misses the tree
@@ -203,62 +216,62 @@ __device__ __forceinline__ bool walk_init(const TravArgs& t, RayWalk& w, uint32_
 
 __device__ __forceinline__ float sel3(int a, const float v[3]) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); }
 
+// The staged group of four crossings as one 32-byte sector at dst (32-byte aligned).
+__device__ __forceinline__ void store_group(float2* dst, const TravSmem& sm) {
+    const float2 a = sm.grp[0], b = sm.grp[kTravThreads], c = sm.grp[2 * kTravThreads],
+                 d = sm.grp[3 * kTravThreads];
+    float4* p = reinterpret_cast<float4*>(dst);
+    p[0] = make_float4(a.x, a.y, b.x, b.y);
+    p[1] = make_float4(c.x, c.y, d.x, d.y);
+}
+
+// The staged chunk of eight network ids as one 16-byte store at dst (16-byte aligned).
+__device__ __forceinline__ void store_chunk(uint16_t* dst, const TravSmem& sm) {
+    uint32_t v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        v[i] = (uint32_t)sm.chk[(2 * i) * kTravThreads] | ((uint32_t)sm.chk[(2 * i + 1) * kTravThreads] << 16);
+    *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
+}
+
 // Emits node nd as the ray's next crossing (after the proposal and empty-space
 // rules); returns false when the ray has reached maxc crossings.  kFVec: the crossings
-// are collected per group of four slots and written as one whole 32-byte sector, the
-// network ids per chunk of eight slots (16 bytes), so that no sector of the crossing
-// list is left partly written (see walk_flush).
+// are collected in shared memory per group of four slots and written as one whole
+// 32-byte sector, the network ids per chunk of eight slots (16 bytes), so that no
+// sector of the crossing list is left partly written (see walk_flush).
 template <int F>
-__device__ __forceinline__ bool walk_emit(const TravArgs& t, RayWalk& w, uint32_t* s_cnt, uint32_t meta, int axis) {
+__device__ __forceinline__ bool walk_emit(const TravArgs& t, RayWalk& w, const TravSmem& sm, uint32_t meta,
+                                          int axis) {
     if ((F & kFMask) && w.masked && !overlaps_kept(w.kept_bins, w.r0, w.bw, w.e, w.x)) return true;
     if ((F & kFOcc) && !crossing_occupied(t.occ, w.o, w.d, w.key, w.e, w.x, w.cnt)) return true;
     const uint32_t net = (!(F & kFHier) || axis < 0) ? meta >> 2 : (uint32_t)__ldg(t.hier.node_net + w.nd);
     const size_t base = (size_t)w.r * (size_t)t.maxc;
     if (F & kFVec) {
-        const int j = w.cnt & 3;
-        const float2 v = make_float2(w.e, w.x);
-        w.g0 = j == 0 ? v : w.g0;
-        w.g1 = j == 1 ? v : w.g1;
-        w.g2 = j == 2 ? v : w.g2;
-        if (j == 3) {
-            float4* p = reinterpret_cast<float4*>(t.xing + base + (w.cnt - 3));
-            p[0] = make_float4(w.g0.x, w.g0.y, w.g1.x, w.g1.y);
-            p[1] = make_float4(w.g2.x, w.g2.y, v.x, v.y);
-        }
-        const int k = w.cnt & 7;
-        const uint64_t bits = (uint64_t)net << (16 * (k & 3));
-        w.l0 = k == 0 ? bits : (k < 4 ? (w.l0 | bits) : w.l0);
-        w.l1 = k == 0 ? 0ull : (k >= 4 ? (w.l1 | bits) : w.l1);
-        if (k == 7)
-            *reinterpret_cast<uint4*>(t.xleaf + base + (w.cnt - 7)) =
-                make_uint4((uint32_t)w.l0, (uint32_t)(w.l0 >> 32), (uint32_t)w.l1, (uint32_t)(w.l1 >> 32));
+        const int j = w.cnt & 3, k = w.cnt & 7;
+        sm.grp[j * kTravThreads] = make_float2(w.e, w.x);
+        sm.chk[k * kTravThreads] = (uint16_t)net;
+        if (j == 3) store_group(t.xing + base + (w.cnt - 3), sm);
+        if (k == 7) store_chunk(t.xleaf + base + (w.cnt - 7), sm);
     } else {
         t.xing[base + w.cnt] = make_float2(w.e, w.x);
         t.xleaf[base + w.cnt] = (uint16_t)net;
     }
-    atomicAdd(&s_cnt[net], 1u);
+    atomicAdd(&sm.cnt[net], 1u);
     return ++w.cnt < t.maxc;
 }
 
 // kFVec: writes the ray's last, partly filled group and chunk, and zero chunks of
 // network ids to the end of its row: rows of ids are 16-byte aligned but share 32-byte
 // sectors with the next ray's row, so each row is written whole.  Slots at and past
-// the ray's crossing count hold no crossing.
+// the ray's crossing count hold no crossing (their contents are unspecified).
 template <int F>
-__device__ __forceinline__ void walk_flush(const TravArgs& t, const RayWalk& w) {
+__device__ __forceinline__ void walk_flush(const TravArgs& t, const RayWalk& w, const TravSmem& sm) {
     if (!(F & kFVec) || w.cnt == 0) return;
     const size_t base = (size_t)w.r * (size_t)t.maxc;
-    if (w.cnt & 3) {
-        float4* p = reinterpret_cast<float4*>(t.xing + base + (w.cnt & ~3));
-        p[0] = make_float4(w.g0.x, w.g0.y, w.g1.x, w.g1.y);
-        p[1] = make_float4(w.g2.x, w.g2.y, 0.f, 0.f);
-    }
+    if (w.cnt & 3) store_group(t.xing + base + (w.cnt & ~3), sm);
     int c = w.cnt >> 3;
+    if (w.cnt & 7) store_chunk(t.xleaf + base + 8 * c++, sm);
     uint4* q = reinterpret_cast<uint4*>(t.xleaf + base);
-    if (w.cnt & 7) {
-        q[c] = make_uint4((uint32_t)w.l0, (uint32_t)(w.l0 >> 32), (uint32_t)w.l1, (uint32_t)(w.l1 >> 32));
-        ++c;
-    }
     for (; c < (t.maxc >> 3); ++c) q[c] = make_uint4(0u, 0u, 0u, 0u);
 }
 
@@ -268,8 +281,8 @@ __device__ __forceinline__ void walk_flush(const TravArgs& t, const RayWalk& w) 
 // for d_a <= -0 -- and a ts of NaN (a ray inside the plane) crosses neither.  These are
 // the children's slab intervals (see the header).  Enters the first non-empty child
 // and pushes the other when both are; returns false when neither is.
-__device__ __forceinline__ bool walk_descend(const TravArgs& t, RayWalk& w, float2* s_ex, uint16_t* s_nd,
-                                             float split, uint32_t meta, int axis) {
+__device__ __forceinline__ bool walk_descend(const TravArgs& t, RayWalk& w, const TravSmem& sm, float split,
+                                             uint32_t meta, int axis) {
     const float oa = sel3(axis, w.o), ia = sel3(axis, w.inv);
     const float ts = __fmul_rn(__fsub_rn(split, oa), ia);
     const float x1 = fminf(w.x, ts);
@@ -281,12 +294,12 @@ __device__ __forceinline__ bool walk_descend(const TravArgs& t, RayWalk& w, floa
     const int left = w.nd + 1, right = (int)(meta >> 2);
     const int c1 = neg ? right : left, c2 = neg ? left : right;
     if (ok1 && ok2) {
-        if (w.sp >= kTravStack) {  // unreachable for depth <= kMaxDepth; recorded, never trapped
+        if (w.sp >= t.depth) {  // unreachable: one entry per level at most; recorded, never trapped
             atomicCAS(t.err, 0, kDevErrStack);
             return false;
         }
-        s_nd[w.sp * kTravThreads] = (uint16_t)c2;
-        s_ex[w.sp * kTravThreads] = make_float2(e2, w.x);
+        sm.nd[w.sp * kTravThreads] = (uint16_t)c2;
+        sm.ex[w.sp * kTravThreads] = make_float2(e2, w.x);
         ++w.sp;
     }
     if (ok1) {
@@ -300,11 +313,11 @@ __device__ __forceinline__ bool walk_descend(const TravArgs& t, RayWalk& w, floa
 }
 
 // Pops the next pending child; returns false when none is left.
-__device__ __forceinline__ bool walk_pop(RayWalk& w, const float2* s_ex, const uint16_t* s_nd) {
+__device__ __forceinline__ bool walk_pop(RayWalk& w, const TravSmem& sm) {
     if (w.sp == 0) return false;
     --w.sp;
-    w.nd = s_nd[w.sp * kTravThreads];
-    const float2 ex = s_ex[w.sp * kTravThreads];
+    w.nd = sm.nd[w.sp * kTravThreads];
+    const float2 ex = sm.ex[w.sp * kTravThreads];
     w.e = ex.x;
     w.x = ex.y;
     return true;
@@ -322,17 +335,23 @@ __device__ __forceinline__ bool walk_stops(const TravArgs& t, const RayWalk& w, 
 }
 
 // One thread per ray; each loop iteration visits one node (emits it or moves to its
-// children), then takes the next pending child when the walk below it is done.  Five
-// CTAs per SM: the whole-sector buffers fit in 48 registers (at six CTAs the spills
-// cost more than the occupancy gains).
+// children), then takes the next pending child when the walk below it is done.  Six
+// CTAs per SM (40 registers) when the shared memory allows it.
 template <int F>
-__global__ void __launch_bounds__(kTravThreads, 5) k_traverse(const TravArgs t, int n_leaves) {
+__global__ void __launch_bounds__(kTravThreads, 6) k_traverse(const TravArgs t, int n_leaves) {
     extern __shared__ __align__(16) unsigned char s_raw[];
-    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_raw);
-    float2* s_ex = reinterpret_cast<float2*>(s_raw + trav_hist_bytes(n_leaves)) + threadIdx.x;
-    uint16_t* s_nd = reinterpret_cast<uint16_t*>(reinterpret_cast<float2*>(s_raw + trav_hist_bytes(n_leaves)) +
-                                                 kTravStack * kTravThreads) + threadIdx.x;
-    for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) s_cnt[i] = 0u;
+    TravSmem sm;
+    unsigned char* p = s_raw;
+    sm.cnt = reinterpret_cast<uint32_t*>(p);
+    p += trav_hist_bytes(n_leaves);
+    sm.grp = reinterpret_cast<float2*>(p) + threadIdx.x;
+    if (F & kFVec) p += (size_t)4 * kTravThreads * sizeof(float2);
+    sm.ex = reinterpret_cast<float2*>(p) + threadIdx.x;
+    p += (size_t)t.depth * kTravThreads * sizeof(float2);
+    sm.chk = reinterpret_cast<uint16_t*>(p) + threadIdx.x;
+    if (F & kFVec) p += (size_t)8 * kTravThreads * sizeof(uint16_t);
+    sm.nd = reinterpret_cast<uint16_t*>(p) + threadIdx.x;
+    for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) sm.cnt[i] = 0u;
     __syncthreads();
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     RayWalk w;
@@ -342,20 +361,19 @@ __global__ void __launch_bounds__(kTravThreads, 5) k_traverse(const TravArgs t, 
             const int axis = (int)(meta & 3u) - 1;
             bool next;
             if (walk_stops<F>(t, w, axis)) {
-                if (!walk_emit<F>(t, w, s_cnt, meta, axis)) break;
-                next = walk_pop(w, s_ex, s_nd);
+                if (!walk_emit<F>(t, w, sm, meta, axis)) break;
+                next = walk_pop(w, sm);
             } else {
-                next = walk_descend(t, w, s_ex, s_nd, __ldg(&t.nodes[w.nd].a.w), meta, axis) ||
-                       walk_pop(w, s_ex, s_nd);
+                next = walk_descend(t, w, sm, __ldg(&t.nodes[w.nd].a.w), meta, axis) || walk_pop(w, sm);
             }
             if (!next) break;
         }
-        walk_flush<F>(t, w);
+        walk_flush<F>(t, w, sm);
         t.n_x[r] = (uint8_t)w.cnt;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) {
-        const uint32_t c = s_cnt[i];
+        const uint32_t c = sm.cnt[i];
         if (c) atomicAdd(&t.counts[i], c);
     }
 }
@@ -372,7 +390,7 @@ using Trav16 = TravTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15>;
 }  // namespace
 
 cudaError_t prepare_traverse() {
-    const int smem = (int)trav_smem_bytes(kMaxNets);
+    const int smem = (int)trav_smem_bytes(kMaxNets, kMaxDepth, true);
     cudaError_t e = cudaSuccess;
     for (int f = 0; f < 16 && e == cudaSuccess; ++f)
         e = cudaFuncSetAttribute(Trav16::k[f], cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -382,15 +400,16 @@ cudaError_t prepare_traverse() {
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
                             int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
                             int n_leaves, int* err, const uint64_t* mask, const uint8_t* fallback,
-                            float2* root_out, const OccArgs& occ, const HierArgs& hier) {
+                            float2* root_out, const OccArgs& occ, const HierArgs& hier, int depth) {
     if (n == 0) return cudaSuccess;
-    if (n_leaves < 1 || n_leaves > kMaxNets) return cudaErrorInvalidValue;
-    TravArgs t{ro, rd, n, nodes, maxc, n_x, xing, xleaf, counts, err, mask, fallback, root_out, occ, hier};
+    if (n_leaves < 1 || n_leaves > kMaxNets || depth < 0 || depth > kMaxDepth) return cudaErrorInvalidValue;
+    TravArgs t{ro, rd, n, nodes, maxc, n_x, xing, xleaf, counts, err, mask, fallback, root_out, occ, hier,
+               depth > 0 ? depth : 1};
     const int f = ((hier.lod > 0.0f && hier.node_net) ? kFHier : 0) | (mask ? kFMask : 0) |
                   (occ.grid ? kFOcc : 0) | ((maxc & 7) == 0 ? kFVec : 0);
     const TravKernel kern = Trav16::k[f];
     const unsigned blocks = (n + kTravThreads - 1) / kTravThreads;
-    kern<<<blocks, kTravThreads, trav_smem_bytes(n_leaves), s>>>(t, n_leaves);
+    kern<<<blocks, kTravThreads, trav_smem_bytes(n_leaves, t.depth, (f & kFVec) != 0), s>>>(t, n_leaves);
     return cudaGetLastError();
 }
 
