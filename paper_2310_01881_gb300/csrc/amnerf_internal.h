@@ -11,10 +11,9 @@
 
 namespace amnerf {
 
-// Device tree node: two float4 per node.
-//   a = (lo.x, lo.y, lo.z, split)
-//   b = (hi.x, hi.y, hi.z, meta) with meta bits: [0,2) axis + 1 (0 = leaf),
-//       [2,32) right-child index (inner) or leaf id (leaf).  Left child = node + 1.
+// Device tree node: eight floats, (lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, split, meta)
+// as two float4 (split and meta share one 8-byte load), meta bits: [0,2) axis + 1
+// (0 = leaf), [2,32) right-child index (inner) or leaf id (leaf).  Left child = node + 1.
 struct DevNode {
     float4 a, b;
 };

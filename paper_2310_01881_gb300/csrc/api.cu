@@ -351,10 +351,10 @@ amnerf_status amnerf_build_tree(amnerf_ctx* ctx, const float* grid_host, int G, 
         const amnerf_node& s = nodes[i];
         const uint32_t payload = s.axis < 0 ? (uint32_t)s.leaf_id : (uint32_t)s.right;
         const uint32_t meta = (uint32_t)(s.axis + 1) | (payload << 2);
-        dn[i].a = make_float4(s.lo[0], s.lo[1], s.lo[2], s.split);
         float fmeta;
         std::memcpy(&fmeta, &meta, sizeof fmeta);
-        dn[i].b = make_float4(s.hi[0], s.hi[1], s.hi[2], fmeta);
+        dn[i].a = make_float4(s.lo[0], s.lo[1], s.lo[2], s.hi[0]);
+        dn[i].b = make_float4(s.hi[1], s.hi[2], s.split, fmeta);
     }
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     dfree(ctx->d_nodes);

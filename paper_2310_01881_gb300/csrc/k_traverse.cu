@@ -55,7 +55,7 @@ namespace {
 __device__ __forceinline__ bool slab(const float4& A, const float4& B, const float o[3], const float inv[3],
                                      float& tin, float& tout) {
     const float lo[3] = {A.x, A.y, A.z};
-    const float hi[3] = {B.x, B.y, B.z};
+    const float hi[3] = {A.w, B.x, B.y};
     float tmin[3], tmax[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -329,8 +329,9 @@ template <int F>
 __device__ __forceinline__ bool walk_stops(const TravArgs& t, const RayWalk& w, int axis) {
     if (axis < 0) return true;
     if (!(F & kFHier)) return false;
-    const float lo_a = __ldg(reinterpret_cast<const float*>(&t.nodes[w.nd].a) + axis);
-    const float hi_a = __ldg(reinterpret_cast<const float*>(&t.nodes[w.nd].b) + axis);
+    const float* f = reinterpret_cast<const float*>(&t.nodes[w.nd]);
+    const float lo_a = __ldg(f + axis);
+    const float hi_a = __ldg(f + 3 + axis);
     return !(__fsub_rn(hi_a, lo_a) > __fmul_rn(t.hier.lod, w.e));
 }
 
@@ -357,14 +358,15 @@ __global__ void __launch_bounds__(kTravThreads, 6) k_traverse(const TravArgs t, 
     RayWalk w;
     if (r < t.n && walk_init<F>(t, w, r)) {
         while (true) {
-            const uint32_t meta = __float_as_uint(__ldg(&t.nodes[w.nd].b.w));
+            const float2 sm2 = __ldg(reinterpret_cast<const float2*>(&t.nodes[w.nd].b) + 1);  // split, meta
+            const uint32_t meta = __float_as_uint(sm2.y);
             const int axis = (int)(meta & 3u) - 1;
             bool next;
             if (walk_stops<F>(t, w, axis)) {
                 if (!walk_emit<F>(t, w, sm, meta, axis)) break;
                 next = walk_pop(w, sm);
             } else {
-                next = walk_descend(t, w, sm, __ldg(&t.nodes[w.nd].a.w), meta, axis) || walk_pop(w, sm);
+                next = walk_descend(t, w, sm, sm2.x, meta, axis) || walk_pop(w, sm);
             }
             if (!next) break;
         }
