@@ -6,7 +6,9 @@
 // offsets and network-tile offsets (a tile holds 128 / steps crossings of one leaf).
 // The scatter stages its binning in shared memory: each CTA ranks its crossings per
 // leaf with shared atomics, reserves one contiguous range per touched leaf with a
-// single global atomic, then writes every crossing id into its leaf's segment.
+// single global atomic, then writes every crossing id into its leaf's segment.  Up to
+// 32 crossings per ray, a thread takes one ray and reads only its ids; beyond, a
+// thread takes 16 slots of the crossing list.
 // Counts and offsets are exact; the order inside a segment is not specified (the
 // network result of a sample does not depend on its position in the batch).
 #include "amnerf_internal.h"
@@ -153,6 +155,63 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __re
     }
 }
 
+// The same binning with one thread per ray (maxc <= kRayScatterMaxc): a thread reads
+// only its own ray's network ids (16 bytes at a time when maxc is a multiple of 8)
+// instead of every slot of the crossing list, ranks them with shared atomics (ranks
+// and ids kept in shared memory as [slot][thread]), and after the CTA's one global
+// atomic per touched leaf writes the crossing ids into their segments.
+constexpr int kRayScatterThreads = 256;
+constexpr int kRayScatterMaxc = 32;
+
+template <bool VEC>
+__global__ void __launch_bounds__(kRayScatterThreads) k_scatter_rays(const uint8_t* __restrict__ n_x,
+                                                                     const uint16_t* __restrict__ xleaf,
+                                                                     uint32_t n_rays, int maxc,
+                                                                     uint32_t* __restrict__ cursor,
+                                                                     uint32_t* __restrict__ order, int n_leaves) {
+    extern __shared__ uint32_t sm[];
+    uint32_t* s_cnt = sm;
+    uint32_t* s_base = sm + n_leaves;
+    uint16_t* s_id = reinterpret_cast<uint16_t*>(sm + 2 * n_leaves) + threadIdx.x;
+    uint16_t* s_rk = s_id + (size_t)maxc * kRayScatterThreads;
+    for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) s_cnt[i] = 0u;
+    __syncthreads();
+    const uint32_t r = blockIdx.x * (uint32_t)kRayScatterThreads + threadIdx.x;
+    const int nx = r < n_rays ? min((int)__ldg(n_x + r), maxc) : 0;
+    const size_t base = (size_t)r * (size_t)maxc;
+    if (VEC) {
+        for (int k0 = 0; k0 < nx; k0 += 8) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(xleaf + base + k0));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = k0 + i;
+                if (k < nx) {
+                    const uint32_t id = (w[i >> 1] >> (16 * (i & 1))) & 0xffffu;
+                    s_id[k * kRayScatterThreads] = (uint16_t)id;
+                    s_rk[k * kRayScatterThreads] = (uint16_t)atomicAdd(&s_cnt[id], 1u);
+                }
+            }
+        }
+    } else {
+        for (int k = 0; k < nx; ++k) {
+            const uint32_t id = __ldg(xleaf + base + k);
+            s_id[k * kRayScatterThreads] = (uint16_t)id;
+            s_rk[k * kRayScatterThreads] = (uint16_t)atomicAdd(&s_cnt[id], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) {
+        const uint32_t c = s_cnt[i];
+        s_base[i] = c ? atomicAdd(&cursor[i], c) : 0u;
+    }
+    __syncthreads();
+    for (int k = 0; k < nx; ++k) {
+        const uint32_t id = s_id[k * kRayScatterThreads];
+        order[s_base[id] + s_rk[k * kRayScatterThreads]] = (uint32_t)(base + (size_t)k);
+    }
+}
+
 // One wave of a render: crossings k_lo <= k < min(n_x, k_lo + W) of the rays still
 // alive (alive == NULL: every ray), visited as n_rays x W items (ray-major), so a wave
 // reads only its own slots.  COUNT: only the per-leaf totals (added to cursor, which
@@ -212,6 +271,18 @@ cudaError_t launch_scatter(cudaStream_t s, const uint8_t* n_x, const uint16_t* x
                            uint32_t* cursor, uint32_t* order, int n_leaves) {
     const uint64_t n_slots = (uint64_t)n_rays * (uint64_t)maxc;
     if (n_slots == 0) return cudaSuccess;
+    if (maxc <= kRayScatterMaxc) {
+        const unsigned blocks = (n_rays + kRayScatterThreads - 1) / kRayScatterThreads;
+        const size_t smem = 2 * sizeof(uint32_t) * (size_t)n_leaves +
+                            2 * sizeof(uint16_t) * (size_t)maxc * kRayScatterThreads;
+        if ((maxc & 7) == 0)
+            k_scatter_rays<true><<<blocks, kRayScatterThreads, smem, s>>>(n_x, xleaf, n_rays, maxc, cursor, order,
+                                                                          n_leaves);
+        else
+            k_scatter_rays<false><<<blocks, kRayScatterThreads, smem, s>>>(n_x, xleaf, n_rays, maxc, cursor, order,
+                                                                           n_leaves);
+        return cudaGetLastError();
+    }
     const uint64_t per = (uint64_t)kScatterThreads * kScatterItems;
     const unsigned blocks = (unsigned)((n_slots + per - 1) / per);
     const size_t smem = 2 * sizeof(uint32_t) * (size_t)n_leaves;
@@ -302,6 +373,12 @@ cudaError_t prepare_group() {
         e = cudaFuncSetAttribute(k_scatter_wave<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_scatter_wave<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // the per-ray scatter also keeps each thread's ids and ranks
+    const int smem_r = smem + (int)(2 * sizeof(uint16_t) * kRayScatterMaxc * kRayScatterThreads);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_scatter_rays<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_r);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_scatter_rays<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_r);
     return e;
 }
 
