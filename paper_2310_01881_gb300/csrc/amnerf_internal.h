@@ -78,13 +78,15 @@ struct HierArgs {
 };
 
 // K-a: traversal + crossing list + per-network crossing histogram (n_nets counters);
-// depth: the tree's depth (0 .. kMaxDepth), which bounds the walk's stack.
+// depth: the tree's depth (0 .. kMaxDepth), which bounds the walk's stack;
+// ray_counter: a device word zeroed before the launch, from which persistent CTAs
+// take their rays (nullptr: one CTA per 256 rays).
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
                             int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
                             int n_nets, int* err, const uint64_t* mask = nullptr,
                             const uint8_t* fallback = nullptr, float2* root_out = nullptr,
                             const OccArgs& occ = OccArgs(), const HierArgs& hier = HierArgs(),
-                            int depth = kMaxDepth);
+                            int depth = kMaxDepth, uint32_t* ray_counter = nullptr);
 
 // K-b: exclusive scans (crossings and network tiles per leaf) and the grouped scatter.
 // acc (may be NULL) accumulates (crossings, tiles) over the waves of one render.

@@ -44,7 +44,8 @@ struct amnerf_ctx {
     uint32_t* d_tile_off = nullptr;
     uint32_t* d_cursor = nullptr;
     // [0] crossings [1] tiles [2] composited [3] fallback rays [4] [5] one wave's
-    // crossings and tiles [6] dynamic tile counter [8] [9] crossings and tiles over waves
+    // crossings and tiles [6] dynamic tile counter [7] traversal ray counter [8] [9]
+    // crossings and tiles over waves
     uint64_t* d_stats = nullptr;
     int* d_err = nullptr;
     // per-ray scratch
@@ -546,7 +547,8 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
            "crossing load launch");
     } else {
         CK(launch_traverse(s, ro, rd, nn, ctx->d_nodes, maxc, ctx->d_nx, ctx->d_xing, ctx->d_xleaf, ctx->d_counts, L,
-                           ctx->d_err, mask, fallback, root_out, occ, hier, ctx->tree_depth),
+                           ctx->d_err, mask, fallback, root_out, occ, hier, ctx->tree_depth,
+                           reinterpret_cast<uint32_t*>(ctx->d_stats + 7)),
            "traverse launch");
     }
     if (ctx->timing) cudaEventRecord(ctx->ev[1], s);
