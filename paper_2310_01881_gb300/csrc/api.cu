@@ -14,7 +14,7 @@
 
 using namespace amnerf;
 
-constexpr int kStatSlots = 10;  // device statistics words (see amnerf_ctx::d_stats)
+constexpr int kStatSlots = 11;  // device statistics words (see amnerf_ctx::d_stats)
 constexpr int kDefaultWidthSplit = 1;  // BF16 hidden-width tiling when the caller sets none
 
 struct amnerf_ctx {
@@ -45,7 +45,7 @@ struct amnerf_ctx {
     uint32_t* d_cursor = nullptr;
     // [0] crossings [1] tiles [2] composited [3] fallback rays [4] [5] one wave's
     // crossings and tiles [6] dynamic tile counter [7] traversal ray counter [8] [9]
-    // crossings and tiles over waves
+    // crossings and tiles over waves [10] compositing ray counter
     uint64_t* d_stats = nullptr;
     int* d_err = nullptr;
     // per-ray scratch

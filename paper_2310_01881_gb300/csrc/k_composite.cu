@@ -293,10 +293,20 @@ __global__ void __launch_bounds__(256) k_composite_lane(
     int maxc, int cap, float t_term, float bg0, float bg1, float bg2, float* __restrict__ rgb,
     float* __restrict__ depth, float* __restrict__ opacity, unsigned long long* __restrict__ n_comp,
     uint64_t jitter, const float* __restrict__ ro, const float* __restrict__ rd, int k_lo, int k_hi,
-    float4* __restrict__ st_c, float* __restrict__ st_d, uint8_t* __restrict__ alive_io) {
+    float4* __restrict__ st_c, float* __restrict__ st_d, uint8_t* __restrict__ alive_io,
+    uint32_t* __restrict__ next_ray) {
     constexpr int kSteps = 8;
-    const uint32_t ray = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t comp = 0;
+    const bool pers = next_ray != nullptr;
+    while (true) {
+    uint32_t ray = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pers) {  // persistent: the warp's next 32 rays
+        uint32_t f = 0;
+        if ((threadIdx.x & 31) == 0) f = atomicAdd(next_ray, 32u);
+        f = __shfl_sync(0xffffffffu, f, 0);
+        if (f >= n) break;
+        ray = f + (threadIdx.x & 31);
+    }
     // a ray that ended in an earlier wave keeps its pixel
     if (ray < n && (!st_c || k_lo == 0 || alive_io[ray])) {
         float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
@@ -364,6 +374,8 @@ __global__ void __launch_bounds__(256) k_composite_lane(
             alive_io[ray] = (!(T < t_term) && nx < nx_all) ? 1 : 0;
         }
     }
+    if (!pers) break;
+    }
     // composited samples: warp sums, one atomic per warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) comp += __shfl_xor_sync(0xffffffffu, comp, o);
@@ -391,10 +403,27 @@ cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* x
     if (st_c && (bins || steps != 8)) return cudaErrorInvalidValue;  // waves: the per-ray kernel only
     if (!bins && steps == 8) {  // one thread per ray
         auto* stc = reinterpret_cast<unsigned long long*>(stats + 2);
-        const unsigned lb = (n + 255) / 256;
+        unsigned lb = (n + 255) / 256;
+        // one pass: persistent CTAs, each warp taking its next 32 rays from stats word 10
+        // (zeroed with the others at the start of the render), so a CTA waits for its
+        // slowest ray once; waves keep one CTA per 256 rays
+        uint32_t* next = st_c ? nullptr : reinterpret_cast<uint32_t*>(stats + 10);
+        if (next) {
+            static int cap_lane[64] = {0};
+            int dev = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+                if (!cap_lane[dev]) {
+                    int sms = 0, per = 0;
+                    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_composite_lane<true, true>, 256, 0);
+                    cap_lane[dev] = sms * (per > 0 ? per : 1);
+                }
+                if (lb > (unsigned)cap_lane[dev]) lb = (unsigned)cap_lane[dev];
+            }
+        }
 #define AMNERF_LANE(H, J)                                                                                        \
     k_composite_lane<H, J><<<lb, 256, 0, s>>>(n_x, xing, slot_out, n, maxc, cap, t_term, bg0, bg1, bg2, rgb, depth, \
-                                              opacity, stc, jitter, ro, rd, k_lo, k_hi, st_c, st_d, alive)
+                                              opacity, stc, jitter, ro, rd, k_lo, k_hi, st_c, st_d, alive, next)
         if (slot_half) {
             if (jitter) AMNERF_LANE(true, true);
             else AMNERF_LANE(true, false);
