@@ -78,11 +78,12 @@ struct HierArgs {
 };
 
 // K-a: traversal + crossing list + per-network crossing histogram (n_nets counters);
+// walk: (split, meta) of every node, the part of a node the walk below the root reads;
 // depth: the tree's depth (0 .. kMaxDepth), which bounds the walk's stack;
 // ray_counter: a device word zeroed before the launch, from which persistent CTAs
 // take their rays (nullptr: one CTA per 256 rays).
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
-                            int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
+                            const float2* walk, int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
                             int n_nets, int* err, const uint64_t* mask = nullptr,
                             const uint8_t* fallback = nullptr, float2* root_out = nullptr,
                             const OccArgs& occ = OccArgs(), const HierArgs& hier = HierArgs(),

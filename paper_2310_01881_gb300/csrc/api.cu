@@ -28,6 +28,7 @@ struct amnerf_ctx {
     int tree_depth = 0;  // depth of the deepest node (the traversal's stack size)
     DevNode* d_nodes = nullptr;
     uint16_t* d_node_net = nullptr;  // network id of every node (leaves: leaf id; inner: L + preorder rank)
+    float2* d_walk = nullptr;        // (split, meta) of every node
     float* d_grid = nullptr;  // the guidance grid (empty-space skipping)
     int grid_G = 0;
     float grid_lo[3] = {0.f, 0.f, 0.f}, grid_sc[3] = {0.f, 0.f, 0.f};
@@ -305,6 +306,7 @@ void amnerf_destroy(amnerf_ctx* ctx) {
     free_ray_scratch(ctx);
     dfree(ctx->d_nodes);
     dfree(ctx->d_node_net);
+    dfree(ctx->d_walk);
     dfree(ctx->d_grid);
     dfree(ctx->d_weights);
     dfree(ctx->d_amax);
@@ -345,6 +347,7 @@ amnerf_status amnerf_build_tree(amnerf_ctx* ctx, const float* grid_host, int G, 
     if (!build_kdtree(grid_host, G, bbox, params->max_depth, params->leaf_mass_frac, nodes, nl, err))
         return fail(ctx, AMNERF_E_INVAL, err);
     std::vector<DevNode> dn(nodes.size());
+    std::vector<float2> wk(nodes.size());
     std::vector<uint16_t> net(nodes.size());
     for (size_t i = 0, inner = 0; i < nodes.size(); ++i)
         net[i] = (uint16_t)(nodes[i].axis < 0 ? nodes[i].leaf_id : nl + (int)inner++);
@@ -356,14 +359,18 @@ amnerf_status amnerf_build_tree(amnerf_ctx* ctx, const float* grid_host, int G, 
         std::memcpy(&fmeta, &meta, sizeof fmeta);
         dn[i].a = make_float4(s.lo[0], s.lo[1], s.lo[2], s.hi[0]);
         dn[i].b = make_float4(s.hi[1], s.hi[2], s.split, fmeta);
+        wk[i] = make_float2(s.split, fmeta);
     }
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     dfree(ctx->d_nodes);
     dfree(ctx->d_node_net);
+    dfree(ctx->d_walk);
     dfree(ctx->d_grid);
     ctx->grid_G = 0;
     CK(cudaMalloc((void**)&ctx->d_nodes, sizeof(DevNode) * dn.size()), "tree allocation");
     CK(cudaMemcpy(ctx->d_nodes, dn.data(), sizeof(DevNode) * dn.size(), cudaMemcpyHostToDevice), "tree upload");
+    CK(cudaMalloc((void**)&ctx->d_walk, sizeof(float2) * wk.size()), "tree allocation");
+    CK(cudaMemcpy(ctx->d_walk, wk.data(), sizeof(float2) * wk.size(), cudaMemcpyHostToDevice), "tree upload");
     CK(cudaMalloc((void**)&ctx->d_node_net, sizeof(uint16_t) * net.size()), "tree allocation");
     CK(cudaMemcpy(ctx->d_node_net, net.data(), sizeof(uint16_t) * net.size(), cudaMemcpyHostToDevice),
        "tree upload");
@@ -546,8 +553,8 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
                                  ctx->d_xleaf, ctx->d_counts, ctx->d_err),
            "crossing load launch");
     } else {
-        CK(launch_traverse(s, ro, rd, nn, ctx->d_nodes, maxc, ctx->d_nx, ctx->d_xing, ctx->d_xleaf, ctx->d_counts, L,
-                           ctx->d_err, mask, fallback, root_out, occ, hier, ctx->tree_depth,
+        CK(launch_traverse(s, ro, rd, nn, ctx->d_nodes, ctx->d_walk, maxc, ctx->d_nx, ctx->d_xing, ctx->d_xleaf,
+                           ctx->d_counts, L, ctx->d_err, mask, fallback, root_out, occ, hier, ctx->tree_depth,
                            reinterpret_cast<uint32_t*>(ctx->d_stats + 7)),
            "traverse launch");
     }

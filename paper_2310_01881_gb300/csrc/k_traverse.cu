@@ -139,6 +139,7 @@ struct TravArgs {
     const float* rd;
     uint32_t n;
     const DevNode* nodes;
+    const float2* walk;  // per node (split, meta as float bits): the walk's one 8-byte load
     int maxc;
     uint8_t* n_x;
     float2* xing;
@@ -160,6 +161,18 @@ constexpr int kFHier = 1;  // adaptive hierarchical sampling (HCheck)
 constexpr int kFMask = 2;  // proposal masks
 constexpr int kFOcc = 4;   // empty-space skipping
 constexpr int kFVec = 8;   // whole-sector stores (maxc a multiple of 8)
+
+// Streaming accesses (each ray's inputs are read once, its crossing rows written once)
+// bypass L1, which keeps the tree's nodes: the walk reads those about 35 times per ray.
+__device__ __forceinline__ float ld_stream(const float* p) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_stream(void* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.global.L1::no_allocate.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
 
 // One ray's walk: its constants and the position of the walk.
 struct RayWalk {
@@ -189,8 +202,8 @@ __device__ __forceinline__ bool walk_init(const TravArgs& t, RayWalk& w, uint32_
     w.r = r;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        w.o[a] = __ldg(t.ro + 3 * (size_t)r + a);
-        w.d[a] = __ldg(t.rd + 3 * (size_t)r + a);
+        w.o[a] = ld_stream(t.ro + 3 * (size_t)r + a);
+        w.d[a] = ld_stream(t.rd + 3 * (size_t)r + a);
         w.inv[a] = __frcp_rn(w.d[a]);
     }
     float r0 = 0.f, r1 = 0.f;
@@ -217,13 +230,14 @@ __device__ __forceinline__ bool walk_init(const TravArgs& t, RayWalk& w, uint32_
 
 __device__ __forceinline__ float sel3(int a, const float v[3]) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); }
 
+
 // The staged group of four crossings as one 32-byte sector at dst (32-byte aligned).
 __device__ __forceinline__ void store_group(float2* dst, const TravSmem& sm) {
     const float2 a = sm.grp[0], b = sm.grp[kTravThreads], c = sm.grp[2 * kTravThreads],
                  d = sm.grp[3 * kTravThreads];
     float4* p = reinterpret_cast<float4*>(dst);
-    p[0] = make_float4(a.x, a.y, b.x, b.y);
-    p[1] = make_float4(c.x, c.y, d.x, d.y);
+    st_stream(p, __float_as_uint(a.x), __float_as_uint(a.y), __float_as_uint(b.x), __float_as_uint(b.y));
+    st_stream(p + 1, __float_as_uint(c.x), __float_as_uint(c.y), __float_as_uint(d.x), __float_as_uint(d.y));
 }
 
 // The staged chunk of eight network ids as one 16-byte store at dst (16-byte aligned).
@@ -232,7 +246,7 @@ __device__ __forceinline__ void store_chunk(uint16_t* dst, const TravSmem& sm) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
         v[i] = (uint32_t)sm.chk[(2 * i) * kTravThreads] | ((uint32_t)sm.chk[(2 * i + 1) * kTravThreads] << 16);
-    *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
+    st_stream(dst, v[0], v[1], v[2], v[3]);
 }
 
 // Emits node nd as the ray's next crossing (after the proposal and empty-space
@@ -273,7 +287,7 @@ __device__ __forceinline__ void walk_flush(const TravArgs& t, const RayWalk& w, 
     int c = w.cnt >> 3;
     if (w.cnt & 7) store_chunk(t.xleaf + base + 8 * c++, sm);
     uint4* q = reinterpret_cast<uint4*>(t.xleaf + base);
-    for (; c < (t.maxc >> 3); ++c) q[c] = make_uint4(0u, 0u, 0u, 0u);
+    for (; c < (t.maxc >> 3); ++c) st_stream(q + c, 0u, 0u, 0u, 0u);
 }
 
 // Moves to the children of inner node nd (split plane s on axis a).  The plane cuts
@@ -372,7 +386,7 @@ __global__ void __launch_bounds__(kTravThreads, 6) k_traverse(const TravArgs t, 
         RayWalk w;
         if (r < t.n && walk_init<F>(t, w, r)) {
             while (true) {
-                const float2 sm2 = __ldg(reinterpret_cast<const float2*>(&t.nodes[w.nd].b) + 1);  // split, meta
+                const float2 sm2 = __ldg(t.walk + w.nd);  // split, meta
                 const uint32_t meta = __float_as_uint(sm2.y);
                 const int axis = (int)(meta & 3u) - 1;
                 bool next;
@@ -416,13 +430,13 @@ cudaError_t prepare_traverse() {
 }
 
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
-                            int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
+                            const float2* walk, int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
                             int n_leaves, int* err, const uint64_t* mask, const uint8_t* fallback,
                             float2* root_out, const OccArgs& occ, const HierArgs& hier, int depth,
                             uint32_t* ray_counter) {
     if (n == 0) return cudaSuccess;
     if (n_leaves < 1 || n_leaves > kMaxNets || depth < 0 || depth > kMaxDepth) return cudaErrorInvalidValue;
-    TravArgs t{ro, rd, n, nodes, maxc, n_x, xing, xleaf, counts, err, mask, fallback, root_out, occ, hier,
+    TravArgs t{ro, rd, n, nodes, walk, maxc, n_x, xing, xleaf, counts, err, mask, fallback, root_out, occ, hier,
                depth > 0 ? depth : 1, ray_counter};
     const int f = ((hier.lod > 0.0f && hier.node_net) ? kFHier : 0) | (mask ? kFMask : 0) |
                   (occ.grid ? kFOcc : 0) | ((maxc & 7) == 0 ? kFVec : 0);
