@@ -181,6 +181,7 @@ struct RayWalk {
     uint64_t kept_bins;   // proposal: kept depth bins
     uint64_t key;         // empty-space skipping: jitter key
     uint32_t r;
+    size_t base;          // the ray's first crossing slot
     int nd, sp, cnt;
     float e, x;           // interval of node nd (exit > entry)
     bool masked;
@@ -190,7 +191,7 @@ struct RayWalk {
 struct TravSmem {
     uint32_t* cnt;   // the CTA's histogram
     float2* grp;     // group of four crossings, [slot * kTravThreads]
-    uint16_t* chk;   // chunk of eight network ids, [slot * kTravThreads]
+    uint16_t* chk;   // chunk of eight network ids: ids 2i, 2i+1 in word [i * kTravThreads] (two halves)
     float2* ex;      // pending (entry, exit), [level * kTravThreads]
     uint16_t* nd;    // pending node ids, [level * kTravThreads]
 };
@@ -219,6 +220,7 @@ __device__ __forceinline__ bool walk_init(const TravArgs& t, RayWalk& w, uint32_
         w.bw = __fmul_rn(__fsub_rn(r1, r0), 0.015625f);  // bin width (t1 - t0) / 64
     }
     if (F & kFOcc) w.key = t.occ.jitter ? jit_ray_key(t.occ.jitter, w.o, w.d) : 0ull;
+    w.base = (size_t)r * (size_t)t.maxc;
     w.nd = 0;
     w.sp = 0;
     w.cnt = 0;
@@ -245,7 +247,7 @@ __device__ __forceinline__ void store_chunk(uint16_t* dst, const TravSmem& sm) {
     uint32_t v[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-        v[i] = (uint32_t)sm.chk[(2 * i) * kTravThreads] | ((uint32_t)sm.chk[(2 * i + 1) * kTravThreads] << 16);
+        v[i] = reinterpret_cast<const uint32_t*>(sm.chk)[i * kTravThreads];
     st_stream(dst, v[0], v[1], v[2], v[3]);
 }
 
@@ -260,11 +262,11 @@ __device__ __forceinline__ bool walk_emit(const TravArgs& t, RayWalk& w, const T
     if ((F & kFMask) && w.masked && !overlaps_kept(w.kept_bins, w.r0, w.bw, w.e, w.x)) return true;
     if ((F & kFOcc) && !crossing_occupied(t.occ, w.o, w.d, w.key, w.e, w.x, w.cnt)) return true;
     const uint32_t net = (!(F & kFHier) || axis < 0) ? meta >> 2 : (uint32_t)__ldg(t.hier.node_net + w.nd);
-    const size_t base = (size_t)w.r * (size_t)t.maxc;
+    const size_t base = w.base;
     if (F & kFVec) {
         const int j = w.cnt & 3, k = w.cnt & 7;
         sm.grp[j * kTravThreads] = make_float2(w.e, w.x);
-        sm.chk[k * kTravThreads] = (uint16_t)net;
+        sm.chk[2 * (k >> 1) * kTravThreads + (k & 1)] = (uint16_t)net;
         if (j == 3) store_group(t.xing + base + (w.cnt - 3), sm);
         if (k == 7) store_chunk(t.xleaf + base + (w.cnt - 7), sm);
     } else {
@@ -282,7 +284,7 @@ __device__ __forceinline__ bool walk_emit(const TravArgs& t, RayWalk& w, const T
 template <int F>
 __device__ __forceinline__ void walk_flush(const TravArgs& t, const RayWalk& w, const TravSmem& sm) {
     if (!(F & kFVec) || w.cnt == 0) return;
-    const size_t base = (size_t)w.r * (size_t)t.maxc;
+    const size_t base = w.base;
     if (w.cnt & 3) store_group(t.xing + base + (w.cnt & ~3), sm);
     int c = w.cnt >> 3;
     if (w.cnt & 7) store_chunk(t.xleaf + base + 8 * c++, sm);
@@ -368,7 +370,7 @@ __global__ void __launch_bounds__(kTravThreads, 6) k_traverse(const TravArgs t, 
     if (F & kFVec) p += (size_t)4 * kTravThreads * sizeof(float2);
     sm.ex = reinterpret_cast<float2*>(p) + threadIdx.x;
     p += (size_t)t.depth * kTravThreads * sizeof(float2);
-    sm.chk = reinterpret_cast<uint16_t*>(p) + threadIdx.x;
+    sm.chk = reinterpret_cast<uint16_t*>(p) + 2 * threadIdx.x;
     if (F & kFVec) p += (size_t)8 * kTravThreads * sizeof(uint16_t);
     sm.nd = reinterpret_cast<uint16_t*>(p) + threadIdx.x;
     for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) sm.cnt[i] = 0u;
