@@ -287,6 +287,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
 // resumes from the state (rgb and T in st_c, depth in st_d) of the rays still alive,
 // and every wave stores the state, whether the ray goes on (alive), and the pixel;
 // the operations and their order are those of one pass.
+// Persistent one-pass launch: rays per counter fetch = rounds x 32, rounds = 1 ..
+// kLaneMaxRounds chosen so that every warp still makes about 32 fetches (one atomic
+// per 32 rays made the counter the limit on large batches of short rays, eight rounds
+// on small batches a long tail).
+constexpr uint32_t kLaneMaxRounds = 8;
+
 template <bool HALF, bool JIT>
 __global__ void __launch_bounds__(256) k_composite_lane(
     const uint8_t* __restrict__ n_x, const float2* __restrict__ xing, const void* __restrict__ slot_out, uint32_t n,
@@ -294,18 +300,23 @@ __global__ void __launch_bounds__(256) k_composite_lane(
     float* __restrict__ depth, float* __restrict__ opacity, unsigned long long* __restrict__ n_comp,
     uint64_t jitter, const float* __restrict__ ro, const float* __restrict__ rd, int k_lo, int k_hi,
     float4* __restrict__ st_c, float* __restrict__ st_d, uint8_t* __restrict__ alive_io,
-    uint32_t* __restrict__ next_ray) {
+    uint32_t* __restrict__ next_ray, uint32_t rounds) {
     constexpr int kSteps = 8;
     uint32_t comp = 0;
     const bool pers = next_ray != nullptr;
+    uint32_t first = 0, round = rounds;  // persistent: rays first + 32 round + lane
     while (true) {
     uint32_t ray = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pers) {  // persistent: the warp's next 32 rays
-        uint32_t f = 0;
-        if ((threadIdx.x & 31) == 0) f = atomicAdd(next_ray, 32u);
-        f = __shfl_sync(0xffffffffu, f, 0);
-        if (f >= n) break;
-        ray = f + (threadIdx.x & 31);
+    if (pers) {  // the warp's next 32 rays, fetched rounds x 32 at a time
+        if (round == rounds) {
+            uint32_t f = 0;
+            if ((threadIdx.x & 31) == 0) f = atomicAdd(next_ray, 32u * rounds);
+            first = __shfl_sync(0xffffffffu, f, 0);
+            round = 0;
+        }
+        const uint32_t r0 = first + 32u * round++;
+        if (r0 >= n) break;
+        ray = r0 + (threadIdx.x & 31);
     }
     // a ray that ended in an earlier wave keeps its pixel
     if (ray < n && (!st_c || k_lo == 0 || alive_io[ray])) {
@@ -404,10 +415,11 @@ cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* x
     if (!bins && steps == 8) {  // one thread per ray
         auto* stc = reinterpret_cast<unsigned long long*>(stats + 2);
         unsigned lb = (n + 255) / 256;
-        // one pass: persistent CTAs, each warp taking its next 32 rays from stats word 10
-        // (zeroed with the others at the start of the render), so a CTA waits for its
-        // slowest ray once; waves keep one CTA per 256 rays
+        // one pass: persistent CTAs, each warp taking its rays from stats word 10 (zeroed
+        // with the others at the start of the render) rounds x 32 at a time, so a CTA
+        // waits for its slowest ray once; waves keep one CTA per 256 rays
         uint32_t* next = st_c ? nullptr : reinterpret_cast<uint32_t*>(stats + 10);
+        uint32_t rounds = 1;
         if (next) {
             static int cap_lane[64] = {0};
             int dev = 0;
@@ -420,10 +432,12 @@ cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* x
                 }
                 if (lb > (unsigned)cap_lane[dev]) lb = (unsigned)cap_lane[dev];
             }
+            const uint64_t r = (uint64_t)n / (32u * 32u * (uint64_t)lb * 8u);
+            rounds = (uint32_t)(r < 1 ? 1 : (r > kLaneMaxRounds ? kLaneMaxRounds : r));
         }
 #define AMNERF_LANE(H, J)                                                                                        \
     k_composite_lane<H, J><<<lb, 256, 0, s>>>(n_x, xing, slot_out, n, maxc, cap, t_term, bg0, bg1, bg2, rgb, depth, \
-                                              opacity, stc, jitter, ro, rd, k_lo, k_hi, st_c, st_d, alive, next)
+                                              opacity, stc, jitter, ro, rd, k_lo, k_hi, st_c, st_d, alive, next, rounds)
         if (slot_half) {
             if (jitter) AMNERF_LANE(true, true);
             else AMNERF_LANE(true, false);
