@@ -23,6 +23,12 @@ constexpr int kMaxLeaves = 4096; // 2^12 leaves at depth 12
 constexpr int kMaxNets = 2 * kMaxLeaves;  // one network per node: leaves, then inner nodes (< 8192)
 constexpr int kMaxDepth = 12;
 constexpr int kStackDepth = 16;  // traversal stack (depth + 1 entries suffice)
+// Persistent kernels take their rays 32 at a time from kRayCounters counters, one per
+// 128-byte line (warp w of a CTA uses counter w % kRayCounters, which hands out the
+// 32-ray blocks b with b % kRayCounters == its index): a single counter's atomics
+// limited large batches of short rays.
+constexpr int kRayCounters = 8;
+constexpr size_t kRayCounterBytes = 128 * kRayCounters;
 
 #ifdef __CUDACC__
 // ---- stratified jitter of the sample positions (Sec. 3.5: samples drawn at random within each interval) --
@@ -80,7 +86,7 @@ struct HierArgs {
 // K-a: traversal + crossing list + per-network crossing histogram (n_nets counters);
 // walk: (split, meta) of every node, the part of a node the walk below the root reads;
 // depth: the tree's depth (0 .. kMaxDepth), which bounds the walk's stack;
-// ray_counter: a device word zeroed before the launch, from which persistent CTAs
+// ray_counter: kRayCounterBytes zeroed before the launch, from which persistent CTAs
 // take their rays (nullptr: one CTA per 256 rays).
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
                             const float2* walk, int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
@@ -172,7 +178,8 @@ cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* x
                              float bg1, float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
                              uint64_t jitter, const float* ro, const float* rd,
                              const float2* root = nullptr, float* bins = nullptr, int k_lo = 0, int k_hi = 256,
-                             float4* st_c = nullptr, float* st_d = nullptr, uint8_t* alive = nullptr);
+                             float4* st_c = nullptr, float* st_d = nullptr, uint8_t* alive = nullptr,
+                             uint32_t* ray_counters = nullptr);
 // The generated slots (j < n_x[r] * steps) of 4 x FP16 per-sample outputs as float4.
 cudaError_t launch_slots_to_f32(cudaStream_t s, const uint8_t* n_x, const void* slot_half, float4* out, uint32_t n,
                                 int steps, int cap);

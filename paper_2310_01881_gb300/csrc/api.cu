@@ -14,7 +14,7 @@
 
 using namespace amnerf;
 
-constexpr int kStatSlots = 11;  // device statistics words (see amnerf_ctx::d_stats)
+constexpr int kStatSlots = 10;  // device statistics words (see amnerf_ctx::d_stats)
 constexpr int kDefaultWidthSplit = 1;  // BF16 hidden-width tiling when the caller sets none
 
 struct amnerf_ctx {
@@ -45,9 +45,11 @@ struct amnerf_ctx {
     uint32_t* d_tile_off = nullptr;
     uint32_t* d_cursor = nullptr;
     // [0] crossings [1] tiles [2] composited [3] fallback rays [4] [5] one wave's
-    // crossings and tiles [6] dynamic tile counter [7] traversal ray counter [8] [9]
-    // crossings and tiles over waves [10] compositing ray counter
+    // crossings and tiles [6] dynamic tile counter [8] [9] crossings and tiles over waves
     uint64_t* d_stats = nullptr;
+    // ray counters of the persistent traversal and compositing (kRayCounters each, one
+    // per 128-byte line), zeroed at the start of every render
+    uint32_t* d_ray_ctr = nullptr;
     int* d_err = nullptr;
     // per-ray scratch
     size_t cap_slots = 0;   // n_rays * maxc capacity
@@ -276,6 +278,7 @@ amnerf_status amnerf_create(amnerf_ctx** out, int device, void* cuda_stream) {
         (e = cudaMalloc((void**)&ctx->d_tile_off, sizeof(uint32_t) * (kMaxNets + 1))) != cudaSuccess ||
         (e = cudaMalloc((void**)&ctx->d_cursor, sizeof(uint32_t) * kMaxNets)) != cudaSuccess ||
         (e = cudaMalloc((void**)&ctx->d_stats, sizeof(uint64_t) * kStatSlots)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_ray_ctr, kRayCounterBytes * 2)) != cudaSuccess ||
         (e = cudaMalloc((void**)&ctx->d_err, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(ctx->d_err, 0, sizeof(int))) != cudaSuccess) {
         amnerf_destroy(ctx);
@@ -315,6 +318,7 @@ void amnerf_destroy(amnerf_ctx* ctx) {
     dfree(ctx->d_tile_off);
     dfree(ctx->d_cursor);
     dfree(ctx->d_stats);
+    dfree(ctx->d_ray_ctr);
     dfree(ctx->d_err);
     dfree(ctx->d_hbuf);
     dfree(ctx->d_prop);
@@ -519,6 +523,7 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
     if (ctx->timing) cudaEventRecord(ctx->ev[0], s);
     CK(cudaMemsetAsync(ctx->d_counts, 0, sizeof(uint32_t) * L, s), "memset");
     CK(cudaMemsetAsync(ctx->d_stats, 0, sizeof(uint64_t) * kStatSlots, s), "memset");
+    CK(cudaMemsetAsync(ctx->d_ray_ctr, 0, kRayCounterBytes * 2, s), "memset");
     const uint64_t* mask = nullptr;
     const uint8_t* fallback = nullptr;
     if (p->use_proposal && n > 0) {
@@ -555,7 +560,7 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
     } else {
         CK(launch_traverse(s, ro, rd, nn, ctx->d_nodes, ctx->d_walk, maxc, ctx->d_nx, ctx->d_xing, ctx->d_xleaf,
                            ctx->d_counts, L, ctx->d_err, mask, fallback, root_out, occ, hier, ctx->tree_depth,
-                           reinterpret_cast<uint32_t*>(ctx->d_stats + 7)),
+                           ctx->d_ray_ctr),
            "traverse launch");
     }
     if (ctx->timing) cudaEventRecord(ctx->ev[1], s);
@@ -644,7 +649,8 @@ static amnerf_status render_impl(amnerf_ctx* ctx, const float* ro, const float* 
         if (ctx->timing) cudaEventRecord(ctx->ev[3], s);
         CK(launch_composite(s, ctx->d_nx, ctx->d_xing, ctx->d_slot, ctx->desc.prec != AMNERF_FP32, nn, steps, maxc,
                             cap, p->t_term, p->bg[0], p->bg[1], p->bg[2], rgb, depth, opacity, ctx->d_stats,
-                            p->jitter_seed, ro, rd, root_out, bins_out),
+                            p->jitter_seed, ro, rd, root_out, bins_out, 0, 256, nullptr, nullptr, nullptr,
+                            ctx->d_ray_ctr + kRayCounterBytes / sizeof(uint32_t)),
            "composite launch");
     } else {
         const int W = p->ert_wave;

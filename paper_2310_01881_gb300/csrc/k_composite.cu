@@ -287,12 +287,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6) k_composite(
 // resumes from the state (rgb and T in st_c, depth in st_d) of the rays still alive,
 // and every wave stores the state, whether the ray goes on (alive), and the pixel;
 // the operations and their order are those of one pass.
-// Persistent one-pass launch: rays per counter fetch = rounds x 32, rounds = 1 ..
-// kLaneMaxRounds chosen so that every warp still makes about 32 fetches (one atomic
-// per 32 rays made the counter the limit on large batches of short rays, eight rounds
-// on small batches a long tail).
-constexpr uint32_t kLaneMaxRounds = 8;
-
 template <bool HALF, bool JIT>
 __global__ void __launch_bounds__(256) k_composite_lane(
     const uint8_t* __restrict__ n_x, const float2* __restrict__ xing, const void* __restrict__ slot_out, uint32_t n,
@@ -300,23 +294,20 @@ __global__ void __launch_bounds__(256) k_composite_lane(
     float* __restrict__ depth, float* __restrict__ opacity, unsigned long long* __restrict__ n_comp,
     uint64_t jitter, const float* __restrict__ ro, const float* __restrict__ rd, int k_lo, int k_hi,
     float4* __restrict__ st_c, float* __restrict__ st_d, uint8_t* __restrict__ alive_io,
-    uint32_t* __restrict__ next_ray, uint32_t rounds) {
+    uint32_t* __restrict__ next_ray) {
     constexpr int kSteps = 8;
     uint32_t comp = 0;
     const bool pers = next_ray != nullptr;
-    uint32_t first = 0, round = rounds;  // persistent: rays first + 32 round + lane
+    const uint32_t ctr = (threadIdx.x >> 5) % kRayCounters;  // this warp's counter
     while (true) {
     uint32_t ray = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pers) {  // the warp's next 32 rays, fetched rounds x 32 at a time
-        if (round == rounds) {
-            uint32_t f = 0;
-            if ((threadIdx.x & 31) == 0) f = atomicAdd(next_ray, 32u * rounds);
-            first = __shfl_sync(0xffffffffu, f, 0);
-            round = 0;
-        }
-        const uint32_t r0 = first + 32u * round++;
+    if (pers) {  // the next 32-ray block b of this warp's counter (b % kRayCounters == ctr)
+        uint32_t v = 0;
+        if ((threadIdx.x & 31) == 0) v = atomicAdd(next_ray + 32 * ctr, 1u);
+        v = __shfl_sync(0xffffffffu, v, 0);
+        const uint64_t r0 = ((uint64_t)v * kRayCounters + ctr) * 32u;
         if (r0 >= n) break;
-        ray = r0 + (threadIdx.x & 31);
+        ray = (uint32_t)r0 + (threadIdx.x & 31);
     }
     // a ray that ended in an earlier wave keeps its pixel
     if (ray < n && (!st_c || k_lo == 0 || alive_io[ray])) {
@@ -409,17 +400,17 @@ cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* x
                              int slot_half, uint32_t n, int steps, int maxc, int cap, float t_term, float bg0,
                              float bg1, float bg2, float* rgb, float* depth, float* opacity, uint64_t* stats,
                              uint64_t jitter, const float* ro, const float* rd, const float2* root, float* bins,
-                             int k_lo, int k_hi, float4* st_c, float* st_d, uint8_t* alive) {
+                             int k_lo, int k_hi, float4* st_c, float* st_d, uint8_t* alive,
+                             uint32_t* ray_counters) {
     if (n == 0) return cudaSuccess;
     if (st_c && (bins || steps != 8)) return cudaErrorInvalidValue;  // waves: the per-ray kernel only
     if (!bins && steps == 8) {  // one thread per ray
         auto* stc = reinterpret_cast<unsigned long long*>(stats + 2);
         unsigned lb = (n + 255) / 256;
-        // one pass: persistent CTAs, each warp taking its rays from stats word 10 (zeroed
-        // with the others at the start of the render) rounds x 32 at a time, so a CTA
-        // waits for its slowest ray once; waves keep one CTA per 256 rays
-        uint32_t* next = st_c ? nullptr : reinterpret_cast<uint32_t*>(stats + 10);
-        uint32_t rounds = 1;
+        // one pass: persistent CTAs, each warp taking its rays 32 at a time from one of the
+        // ray counters (zeroed at the start of the render), so a CTA waits for its slowest
+        // ray once; waves keep one CTA per 256 rays
+        uint32_t* next = st_c ? nullptr : ray_counters;
         if (next) {
             static int cap_lane[64] = {0};
             int dev = 0;
@@ -432,12 +423,10 @@ cudaError_t launch_composite(cudaStream_t s, const uint8_t* n_x, const float2* x
                 }
                 if (lb > (unsigned)cap_lane[dev]) lb = (unsigned)cap_lane[dev];
             }
-            const uint64_t r = (uint64_t)n / (32u * 32u * (uint64_t)lb * 8u);
-            rounds = (uint32_t)(r < 1 ? 1 : (r > kLaneMaxRounds ? kLaneMaxRounds : r));
         }
 #define AMNERF_LANE(H, J)                                                                                        \
     k_composite_lane<H, J><<<lb, 256, 0, s>>>(n_x, xing, slot_out, n, maxc, cap, t_term, bg0, bg1, bg2, rgb, depth, \
-                                              opacity, stc, jitter, ro, rd, k_lo, k_hi, st_c, st_d, alive, next, rounds)
+                                              opacity, stc, jitter, ro, rd, k_lo, k_hi, st_c, st_d, alive, next)
         if (slot_half) {
             if (jitter) AMNERF_LANE(true, true);
             else AMNERF_LANE(true, false);

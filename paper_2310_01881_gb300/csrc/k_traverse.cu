@@ -123,12 +123,6 @@ __device__ __forceinline__ bool crossing_occupied(const OccArgs& oc, const float
 // node ids).  The stack holds one entry per level of the tree at most (a far child is
 // pushed only by an inner node on the current path), so it is sized by the tree's depth.
 constexpr int kTravThreads = 256;
-// Persistent CTAs: a warp takes rounds x 32 consecutive rays per fetch from the ray
-// counter, rounds = 1 .. kTravMaxRounds chosen so that every warp still makes about 32
-// fetches: one atomic per 32 rays made the counter's atomics the limit on large
-// batches of short walks (33 M rays of a 16-leaf tree: 1.25 ms against 0.58), while
-// eight rounds on 5 M rays left a tail of up to 8 rounds per warp (0.78 against 0.40).
-constexpr uint32_t kTravMaxRounds = 8;
 
 __host__ __device__ constexpr size_t trav_hist_bytes(int n_nets) { return ((size_t)n_nets * 4 + 15) & ~(size_t)15; }
 __host__ __device__ constexpr size_t trav_stage_bytes(bool vec) {
@@ -158,8 +152,7 @@ struct TravArgs {
     OccArgs occ;
     HierArgs hier;
     int depth;  // stack entries per thread: the tree's depth
-    uint32_t* next_ray;  // persistent CTAs: each warp takes its next rays from this counter
-    uint32_t rounds;     // rounds of 32 rays per fetch
+    uint32_t* next_ray;  // persistent CTAs: kRayCounters ray counters (see the kernel)
 };
 
 // Features compiled into one instantiation of the walk, so that a render keeps in
@@ -361,8 +354,8 @@ __device__ __forceinline__ bool walk_stops(const TravArgs& t, const RayWalk& w, 
 
 // One thread per ray; each loop iteration visits one node (emits it or moves to its
 // children), then takes the next pending child when the walk below it is done.  With
-// a ray counter the CTAs are persistent (as many as fit on the SMs): each warp takes
-// its next 32 consecutive rays (of its batch of 256) when its current ones are done, so a
+// ray counters the CTAs are persistent (as many as fit on the SMs): each warp takes
+// its next 32 consecutive rays from its counter when its current ones are done, so a
 // CTA waits on its slowest ray once, at the end, instead of once per 256 rays (0.415
 // against 0.463 ms at 800x800 x 8).  Six CTAs per SM (40 registers) when the shared
 // memory allows it.
@@ -383,19 +376,16 @@ __global__ void __launch_bounds__(kTravThreads, 6) k_traverse(const TravArgs t, 
     for (int i = threadIdx.x; i < n_leaves; i += blockDim.x) sm.cnt[i] = 0u;
     __syncthreads();
     const bool pers = t.next_ray != nullptr;
-    uint32_t first = 0, round = t.rounds;  // persistent: rays first + 32 round + lane
+    const uint32_t ctr = (threadIdx.x >> 5) % kRayCounters;  // this warp's counter
     while (true) {
         uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-        if (pers) {
-            if (round == t.rounds) {  // the warp's next rounds x 32 rays
-                uint32_t f = 0;
-                if ((threadIdx.x & 31) == 0) f = atomicAdd(t.next_ray, 32u * t.rounds);
-                first = __shfl_sync(0xffffffffu, f, 0);
-                round = 0;
-            }
-            const uint32_t r0 = first + 32u * round++;
+        if (pers) {  // the next 32-ray block b of this warp's counter (b % kRayCounters == ctr)
+            uint32_t v = 0;
+            if ((threadIdx.x & 31) == 0) v = atomicAdd(t.next_ray + 32 * ctr, 1u);
+            v = __shfl_sync(0xffffffffu, v, 0);
+            const uint64_t r0 = ((uint64_t)v * kRayCounters + ctr) * 32u;
             if (r0 >= t.n) break;
-            r = r0 + (threadIdx.x & 31);
+            r = (uint32_t)r0 + (threadIdx.x & 31);
         }
         RayWalk w;
         if (r < t.n && walk_init<F>(t, w, r)) {
@@ -451,7 +441,7 @@ cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, ui
     if (n == 0) return cudaSuccess;
     if (n_leaves < 1 || n_leaves > kMaxNets || depth < 0 || depth > kMaxDepth) return cudaErrorInvalidValue;
     TravArgs t{ro, rd, n, nodes, walk, maxc, n_x, xing, xleaf, counts, err, mask, fallback, root_out, occ, hier,
-               depth > 0 ? depth : 1, ray_counter, 1u};
+               depth > 0 ? depth : 1, ray_counter};
     const int f = ((hier.lod > 0.0f && hier.node_net) ? kFHier : 0) | (mask ? kFMask : 0) |
                   (occ.grid ? kFOcc : 0) | ((maxc & 7) == 0 ? kFVec : 0);
     const TravKernel kern = Trav16::k[f];
@@ -465,9 +455,6 @@ cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, ui
         if (e != cudaSuccess) return e;
         const unsigned cap = (unsigned)(sms * (per > 0 ? per : 1));
         blocks = blocks < cap ? blocks : cap;
-        const uint64_t warps = (uint64_t)blocks * (kTravThreads / 32);
-        const uint64_t rounds = (uint64_t)n / (32u * 32u * warps);
-        t.rounds = (uint32_t)(rounds < 1 ? 1 : (rounds > kTravMaxRounds ? kTravMaxRounds : rounds));
     }
     kern<<<blocks, kTravThreads, smem, s>>>(t, n_leaves);
     return cudaGetLastError();
