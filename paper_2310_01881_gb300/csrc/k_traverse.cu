@@ -118,7 +118,8 @@ __device__ __forceinline__ bool crossing_occupied(const OccArgs& oc, const float
 
 // Threads per traversal CTA.  Shared memory, in this order: the per-CTA histogram;
 // with whole-sector stores, each thread's current group of four crossings
-// ([slot][thread] float2) and chunk of eight network ids ([slot][thread] uint16); the
+// ([slot][thread] float2) and chunk of eight network ids ([pair][thread], two uint16
+// per word); the
 // stack of pending far children as [level][thread] (the (entry, exit) pairs, then the
 // node ids).  The stack holds one entry per level of the tree at most (a far child is
 // pushed only by an inner node on the current path), so it is sized by the tree's depth.
@@ -231,7 +232,6 @@ __device__ __forceinline__ bool walk_init(const TravArgs& t, RayWalk& w, uint32_
 }
 
 __device__ __forceinline__ float sel3(int a, const float v[3]) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); }
-
 
 // The staged group of four crossings as one 32-byte sector at dst (32-byte aligned).
 __device__ __forceinline__ void store_group(float2* dst, const TravSmem& sm) {
@@ -434,8 +434,8 @@ cudaError_t prepare_traverse() {
 }
 
 cudaError_t launch_traverse(cudaStream_t s, const float* ro, const float* rd, uint32_t n, const DevNode* nodes,
-                            const float2* walk, int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf, uint32_t* counts,
-                            int n_leaves, int* err, const uint64_t* mask, const uint8_t* fallback,
+                            const float2* walk, int maxc, uint8_t* n_x, float2* xing, uint16_t* xleaf,
+                            uint32_t* counts, int n_leaves, int* err, const uint64_t* mask, const uint8_t* fallback,
                             float2* root_out, const OccArgs& occ, const HierArgs& hier, int depth,
                             uint32_t* ray_counter) {
     if (n == 0) return cudaSuccess;
