@@ -2,8 +2,9 @@
 // are sorted by node id so that every node's network runs as one dense batch).
 //
 // The keys are small integers (network ids < 8192: leaves, and inner nodes with
-// adaptive hierarchical sampling), so the sort is a one-digit counting sort.  Per-leaf totals come from K-a's histogram; one CTA scans them into crossing
-// offsets and network-tile offsets (a tile holds 128 / steps crossings of one leaf).
+// adaptive hierarchical sampling), so the sort is a one-digit counting sort.  Per-leaf
+// totals come from K-a's histogram; one CTA scans them into crossing offsets and
+// network-tile offsets (a tile holds 128 / steps crossings of one leaf).
 // The scatter stages its binning in shared memory: each CTA ranks its crossings per
 // leaf with shared atomics, reserves one contiguous range per touched leaf with a
 // single global atomic, then writes every crossing id into its leaf's segment.  Up to
