@@ -164,6 +164,20 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint8_t* __re
 constexpr int kRayScatterThreads = 256;
 constexpr int kRayScatterMaxc = 32;
 
+// Rank of this lane's crossing among the CTA's crossings of network id: the lanes of
+// the warp now at the same id (neighbouring rays usually cross the same leaves) take
+// one shared atomic together and are ranked by lane.
+__device__ __forceinline__ uint32_t warp_rank(uint32_t* s_cnt, uint32_t id) {
+    const uint32_t act = __activemask();
+    const uint32_t peers = __match_any_sync(act, id);
+    const int leader = __ffs(peers) - 1;
+    const int lane = (int)(threadIdx.x & 31);
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&s_cnt[id], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
 template <bool VEC>
 __global__ void __launch_bounds__(kRayScatterThreads) k_scatter_rays(const uint8_t* __restrict__ n_x,
                                                                      const uint16_t* __restrict__ xleaf,
@@ -190,7 +204,7 @@ __global__ void __launch_bounds__(kRayScatterThreads) k_scatter_rays(const uint8
                 if (k < nx) {
                     const uint32_t id = (w[i >> 1] >> (16 * (i & 1))) & 0xffffu;
                     s_id[k * kRayScatterThreads] = (uint16_t)id;
-                    s_rk[k * kRayScatterThreads] = (uint16_t)atomicAdd(&s_cnt[id], 1u);
+                    s_rk[k * kRayScatterThreads] = (uint16_t)warp_rank(s_cnt, id);
                 }
             }
         }
@@ -198,7 +212,7 @@ __global__ void __launch_bounds__(kRayScatterThreads) k_scatter_rays(const uint8
         for (int k = 0; k < nx; ++k) {
             const uint32_t id = __ldg(xleaf + base + k);
             s_id[k * kRayScatterThreads] = (uint16_t)id;
-            s_rk[k * kRayScatterThreads] = (uint16_t)atomicAdd(&s_cnt[id], 1u);
+            s_rk[k * kRayScatterThreads] = (uint16_t)warp_rank(s_cnt, id);
         }
     }
     __syncthreads();
