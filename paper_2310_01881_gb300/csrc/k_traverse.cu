@@ -296,17 +296,16 @@ __device__ __forceinline__ void walk_flush(const TravArgs& t, const RayWalk& w, 
 // (e, x) at ts = (s - o_a) * inv_a: the child the ray meets first is (e, min(x, ts)),
 // the other (max(e, ts), x) -- the left child comes first for d_a >= +0, the right one
 // for d_a <= -0 -- and a ts of NaN (a ray inside the plane) crosses neither.  These are
-// the children's slab intervals (see the header).  Enters the first non-empty child
-// and pushes the other when both are; returns false when neither is.
+// the children's slab intervals (see the header).  As x > e, the first child is
+// crossed iff ts > e and the other iff x > ts (a NaN fails both): when both are, the
+// plane splits (e, x) at ts; when one is, its interval is (e, x) itself.  Enters the
+// first crossed child and pushes the other when both are; returns false when neither is.
 __device__ __forceinline__ bool walk_descend(const TravArgs& t, RayWalk& w, const TravSmem& sm, float split,
                                              uint32_t meta, int axis) {
     const float oa = sel3(axis, w.o), ia = sel3(axis, w.inv);
     const float ts = __fmul_rn(__fsub_rn(split, oa), ia);
-    const float x1 = fminf(w.x, ts);
-    const float e2 = fmaxf(w.e, ts);
-    const bool real = ts == ts;
-    const bool ok1 = real && x1 > w.e;
-    const bool ok2 = real && w.x > e2;
+    const bool ok1 = ts > w.e;
+    const bool ok2 = w.x > ts;
     const bool neg = (__float_as_uint(ia) >> 31) != 0u;
     const int left = w.nd + 1, right = (int)(meta >> 2);
     const int c1 = neg ? right : left, c2 = neg ? left : right;
@@ -316,16 +315,11 @@ __device__ __forceinline__ bool walk_descend(const TravArgs& t, RayWalk& w, cons
             return false;
         }
         sm.nd[w.sp * kTravThreads] = (uint16_t)c2;
-        sm.ex[w.sp * kTravThreads] = make_float2(e2, w.x);
+        sm.ex[w.sp * kTravThreads] = make_float2(ts, w.x);
         ++w.sp;
+        w.x = ts;
     }
-    if (ok1) {
-        w.nd = c1;
-        w.x = x1;
-    } else {
-        w.nd = c2;
-        w.e = e2;
-    }
+    w.nd = ok1 ? c1 : c2;
     return ok1 || ok2;
 }
 

@@ -5,7 +5,9 @@ The kernel does not slab-test every box it visits: it slab-tests the root and ca
 (entry, exit) down, cutting it at each inner node's split plane ts = (s - o_a) * inv_a
 into (e, min(x, ts)) for the child the ray meets first (left for d_a >= +0, right for
 d_a <= -0) and (max(e, ts), x) for the other, with no child when ts is NaN; only
-children with exit > entry are entered or pushed.  The claim that these are the
+children with exit > entry are entered or pushed.  As x > e, that is ts > e for the
+first child and x > ts for the other (a NaN fails both), and a child crossed alone
+keeps (e, x).  The claim that these are the
 children's slab intervals, bit for bit, rests on face values being monotone in the
 face coordinate.  This model replays the walk in float32 scalar arithmetic (numpy
 scalars: correctly rounded, no fused multiply-add) and compares its crossings with the
@@ -66,17 +68,14 @@ def _walk(tree, o, d, maxc, lod=0.0, net=None):
             continue
         with np.errstate(all="ignore"):
             ts = F32(F32(split[nd] - o[ax]) * inv[ax])
-        real = not math.isnan(ts)
-        x1, e2 = _fmin(x, ts), _fmax(e, ts)
-        ok1, ok2 = real and x1 > e, real and x > e2
+        ok1, ok2 = ts > e, x > ts          # (e, min(x, ts)) and (max(e, ts), x) non-empty
         left, right = int(info[nd, 1]), int(info[nd, 2])
         c1, c2 = (right, left) if math.copysign(1.0, inv[ax]) < 0 else (left, right)
-        if ok1:
-            if ok2:
-                stack.append((c2, e2, x))
-            nd, x = c1, x1
-        elif ok2:
-            nd, e = c2, e2
+        if ok1 and ok2:
+            stack.append((c2, ts, x))
+            nd, x = c1, ts
+        elif ok1 or ok2:
+            nd = c1 if ok1 else c2
         elif stack:
             nd, e, x = stack.pop()
         else:
